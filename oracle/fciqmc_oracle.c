@@ -1,0 +1,908 @@
+/*
+ * fciqmc_oracle.c -- CPU oracle for the initiator-FCIQMC projector iteration.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, single-threaded
+ * restatement of the method of Guther et al., "NECI: N-Electron Configuration
+ * Interaction with an emphasis on state-of-the-art stochastic methods"
+ * (J. Chem. Phys. 153, 034107 (2020), arXiv:2006.14956).  It is used only by
+ * tests/, by __graft_entry__.smoke() and by the cpu_baseline leg of bench.py.
+ * The GPU library never links, loads or calls it, and it shares no code with
+ * the GPU library.
+ *
+ * Build: gcc -O2 -std=gnu11 -ffp-contract=off -fno-fast-math -shared -fPIC
+ * (-ffp-contract=off is essential: every floating-point expression below is
+ * evaluated as written, one IEEE-754 binary64 operation at a time, with no
+ * fused multiply-add.)
+ *
+ * What is computed, in the paper's order (Sec. I, Eq. (3) "fciqmc_dyn"):
+ *   (a) spawn:  sum_{j != i} -dtau H_ji C_i |D_j>, sampled with one excitation
+ *       per attempt, p_s = dtau |H_ij| / p_gen(j|i) (Sec. II, Eq. (4));
+ *   (b) death:  (1 - dtau (H_ii - S)) C_i, then stochastic rounding (Eq. (2));
+ *   (c) annihilation: all spawned contributions to a determinant are summed
+ *       into it, with the initiator rule (Sec. I) applied to spawns onto
+ *       unoccupied determinants, then stochastic rounding;
+ *   plus the shift update (Eq. (1), S(tau) "updated to match the ground
+ *   state energy"), the reference projected energy (Sec. IV, Eq. (8)), and
+ *   semi-stochastic projection (Sec. III, Eqs. (5)-(6)).
+ *
+ * Readings adopted where the paper is silent (each listed in the design notes):
+ *   R1  determinant = (alpha word, beta word); canonical operator order is
+ *       alpha_0 < ... < alpha_{N-1} < beta_0 < ... < beta_{N-1}.
+ *   R2  integrals are chemist (pq|rs), packed with 8-fold symmetry (FCIDUMP).
+ *   R3  random numbers: Philox4x64-10 (Salmon et al., SC'11), key = (seed, 0),
+ *       counter = (alpha, beta, iteration, (slot << 8) | purpose).
+ *   R4  every multi-term sum in a matrix element (H_ii, single-excitation H_ij)
+ *       and the sum of the spawns onto one determinant is the exact sum of its
+ *       binary64 terms, rounded once to nearest-even ("fsum").
+ *   R5  spawn weight w = -(H_ji * (lambda_c * (C_i / n_att))) with
+ *       lambda_c = dtau / p_gen(c); n_att = ceil(|C_i|).
+ *   R6  N_w = 2^-32 * sum floor(|C_i| 2^32) (exact integer sum).
+ *   R7  shift: S <- S - (zeta / (A dtau)) ln(N_w(t) / N_w(t - A)) every A
+ *       iterations once N_w first reaches the target (Booth, Thom and Alavi,
+ *       J. Chem. Phys. 131, 054106 (2009), cited by the paper); ln is the
+ *       argument-reduction + atanh-series recipe in orc_ln below.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+/* ------------------------------------------------------------------ */
+/* Philox4x64-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: */
+/* as easy as 1, 2, 3", SC'11): ten rounds of two 64x64->128 products. */
+/* ------------------------------------------------------------------ */
+#define PHILOX_M0 0xD2E7470EE14C6C93ULL
+#define PHILOX_M1 0xCA5A826395121157ULL
+#define PHILOX_W0 0x9E3779B97F4A7C15ULL /* golden ratio */
+#define PHILOX_W1 0xBB67AE8584CAA73BULL /* sqrt(3) - 1 */
+
+void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
+{
+    uint64_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) { k0 += PHILOX_W0; k1 += PHILOX_W1; }
+        u128 p0 = (u128)PHILOX_M0 * c0;
+        u128 p1 = (u128)PHILOX_M1 * c2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        uint64_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+enum { PURPOSE_SPAWN = 1, PURPOSE_DEATH = 2, PURPOSE_ANNIH = 3 };
+
+static void draw(uint64_t seed, uint64_t a, uint64_t b, int64_t iter, uint64_t slot,
+                 int purpose, uint64_t w[4])
+{
+    uint64_t ctr[4] = { a, b, (uint64_t)iter, (slot << 8) | (uint64_t)purpose };
+    uint64_t key[2] = { seed, 0 };
+    orc_philox4x64_10(ctr, key, w);
+}
+
+/* uniform double in [0,1) from the top 53 bits of a word */
+static double u53(uint64_t w) { return (double)(w >> 11) * 0x1p-53; }
+/* integer in [0, m): floor(w * m / 2^64) */
+static uint64_t pick(uint64_t w, uint64_t m) { return (uint64_t)(((u128)w * m) >> 64); }
+
+/* ------------------------------------------------------------------ */
+/* Exact summation (reading R4): a fixed-point accumulator spanning the  */
+/* whole binary64 range (Kulisch).  Digits are 32-bit, kept in int64    */
+/* so that carries can be deferred.  value = sum l[k] 2^(32k - 1088).   */
+/* ------------------------------------------------------------------ */
+#define XL 70
+typedef struct { int64_t l[XL]; int bad; } xacc;
+
+static void xacc_zero(xacc *x) { memset(x, 0, sizeof *x); }
+
+static void xacc_add(xacc *x, double v, int negate)
+{
+    uint64_t bits;
+    memcpy(&bits, &v, 8);
+    int ex = (int)((bits >> 52) & 0x7ff);
+    if (ex == 0x7ff) { x->bad = 1; return; }
+    uint64_t m = bits & ((1ULL << 52) - 1);
+    int e;
+    if (ex == 0) e = -1074; else { m |= 1ULL << 52; e = ex - 1075; }
+    if (m == 0) return;
+    int neg = (int)(bits >> 63) ^ (negate ? 1 : 0);
+    int pos = e + 1088;
+    int k = pos / 32, s = pos % 32;
+    u128 t = (u128)m << s;
+    int64_t d0 = (int64_t)(uint32_t)t, d1 = (int64_t)(uint32_t)(t >> 32), d2 = (int64_t)(uint32_t)(t >> 64);
+    if (neg) { x->l[k] -= d0; x->l[k + 1] -= d1; x->l[k + 2] -= d2; }
+    else     { x->l[k] += d0; x->l[k + 1] += d1; x->l[k + 2] += d2; }
+}
+
+static void xacc_merge(xacc *x, const xacc *y, int negate)
+{
+    for (int k = 0; k < XL; k++) x->l[k] += negate ? -y->l[k] : y->l[k];
+    x->bad |= y->bad;
+}
+
+/* round the exact value to the nearest binary64, ties to even */
+static double xacc_round(const xacc *x)
+{
+    if (x->bad) return NAN;
+    uint32_t d[XL];
+    int64_t carry = 0;
+    for (int k = 0; k < XL; k++) {
+        int64_t t = x->l[k] + carry;
+        d[k] = (uint32_t)t;
+        carry = t >> 32; /* arithmetic: floor division */
+    }
+    int neg = carry < 0;
+    if (neg) { /* two's complement negation of the digit string */
+        uint64_t c = 1;
+        for (int k = 0; k < XL; k++) {
+            uint64_t t = (uint64_t)(uint32_t)~d[k] + c;
+            d[k] = (uint32_t)t;
+            c = t >> 32;
+        }
+    }
+    int top = XL - 1;
+    while (top >= 0 && d[top] == 0) top--;
+    if (top < 0) return 0.0;
+    int msb = 32 * top + (31 - __builtin_clz(d[top]));
+    int lsb = msb - 52;
+    if (lsb < 14) lsb = 14; /* bit 14 has weight 2^-1074 */
+#define GETBIT(i) ((d[(i) >> 5] >> ((i) & 31)) & 1u)
+    uint64_t mant = 0;
+    for (int i = msb; i >= lsb; i--) mant = (mant << 1) | GETBIT(i);
+    int rb = 0, sticky = 0;
+    if (lsb - 1 >= 0) rb = (int)GETBIT(lsb - 1);
+    for (int i = lsb - 2; i >= 0 && !sticky; i--) sticky = (int)GETBIT(i);
+#undef GETBIT
+    if (rb && (sticky || (mant & 1))) mant++;
+    double r = ldexp((double)mant, lsb - 1088);
+    return neg ? -r : r;
+}
+
+double orc_fsum(const double *v, int64_t n)
+{
+    xacc x;
+    xacc_zero(&x);
+    for (int64_t i = 0; i < n; i++) xacc_add(&x, v[i], 0);
+    return xacc_round(&x);
+}
+
+/* ------------------------------------------------------------------ */
+/* Natural logarithm for the shift update (reading R7): write x = m 2^k  */
+/* with m in (sqrt(1/2), sqrt(2)], then ln x = k ln2 + 2 atanh(s),       */
+/* s = (m-1)/(m+1), with the atanh series summed to z^11 (z = s^2).     */
+/* ------------------------------------------------------------------ */
+double orc_ln(double x)
+{
+    if (!(x > 0.0) || isinf(x)) return NAN;
+    uint64_t bits;
+    memcpy(&bits, &x, 8);
+    int k;
+    if (((bits >> 52) & 0x7ff) == 0) { /* subnormal: scale into range first */
+        double y = x * 0x1p54;
+        memcpy(&bits, &y, 8);
+        k = (int)((bits >> 52) & 0x7ff) - 1023 - 54;
+    } else {
+        k = (int)((bits >> 52) & 0x7ff) - 1023;
+    }
+    bits = (bits & ((1ULL << 52) - 1)) | (1023ULL << 52);
+    double m;
+    memcpy(&m, &bits, 8);
+    if (m > 1.4142135623730951) { m = m * 0.5; k += 1; }
+    double s = (m - 1.0) / (m + 1.0);
+    double z = s * s;
+    double p = 2.0 / 23.0;
+    for (int j = 10; j >= 0; j--) p = 2.0 / (double)(2 * j + 1) + z * p;
+    double r = s * p;
+    const double ln2_hi = 0x1.62e42fefa39efp-1, ln2_lo = 0x1.abc9e3b39803fp-56;
+    return (double)k * ln2_hi + ((double)k * ln2_lo + r);
+}
+
+/* ------------------------------------------------------------------ */
+/* System: integrals and reference determinant                          */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    int norb, na, nb, kind; /* kind 0: ab initio, 1: Hubbard */
+    double ecore;
+    double *h;   /* norb x norb, row-major */
+    double *eri; /* packed 8-fold */
+    int lx, ly, z; /* Hubbard lattice; z neighbour slots per site */
+    double t, U;
+    int *nbr; /* nbr[site * 4 + k], -1 when absent */
+    uint64_t ref_a, ref_b;
+    xacc xref; /* exact diagonal sum X(D_ref) */
+    double eref;
+} orc_sys;
+
+void orc_sys_free(orc_sys *s);
+static int64_t pairidx(int64_t i, int64_t j) { return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i; }
+
+static double eri(const orc_sys *s, int p, int q, int r, int t)
+{
+    return s->eri[pairidx(pairidx(p, q), pairidx(r, t))];
+}
+
+static uint64_t lowmask(int p) { return p >= 64 ? ~0ULL : ((1ULL << p) - 1); }
+static int popc(uint64_t x) { return __builtin_popcountll(x); }
+
+/* exact diagonal sum X(D) = sum_occ h_pp + sum_{pairs} [(pp|qq) - delta_spin (pq|qp)] */
+static void xdiag(const orc_sys *s, uint64_t a, uint64_t b, xacc *x)
+{
+    int occ[128], spin[128], n = 0;
+    for (int p = 0; p < s->norb; p++) if ((a >> p) & 1) { occ[n] = p; spin[n] = 0; n++; }
+    for (int p = 0; p < s->norb; p++) if ((b >> p) & 1) { occ[n] = p; spin[n] = 1; n++; }
+    xacc_zero(x);
+    for (int i = 0; i < n; i++) xacc_add(x, s->h[occ[i] * s->norb + occ[i]], 0);
+    for (int i = 0; i < n; i++)
+        for (int j = i + 1; j < n; j++) {
+            xacc_add(x, eri(s, occ[i], occ[i], occ[j], occ[j]), 0);
+            if (spin[i] == spin[j]) xacc_add(x, eri(s, occ[i], occ[j], occ[j], occ[i]), 1);
+        }
+}
+
+/* H_ii - E_ref, rounded once from the exact difference (reading R4) */
+double orc_hdiag_rel(const orc_sys *s, uint64_t a, uint64_t b)
+{
+    xacc x;
+    xdiag(s, a, b, &x);
+    xacc_merge(&x, &s->xref, 1);
+    return xacc_round(&x);
+}
+
+double orc_eref(const orc_sys *s) { return s->eref; }
+
+/* occupation test / operator application on the canonical ordering */
+static int occupied(uint64_t a, uint64_t b, int norb, int pos)
+{
+    return pos < norb ? (int)((a >> pos) & 1) : (int)((b >> (pos - norb)) & 1);
+}
+static int n_before(uint64_t a, uint64_t b, int norb, int pos)
+{
+    return pos < norb ? popc(a & lowmask(pos)) : popc(a) + popc(b & lowmask(pos - norb));
+}
+static void flip(uint64_t *a, uint64_t *b, int norb, int pos)
+{
+    if (pos < norb) *a ^= 1ULL << pos; else *b ^= 1ULL << (pos - norb);
+}
+/* apply a_pos (create=0) or a+_pos (create=1); returns sign (+1/-1) or 0 */
+static int apply_op(uint64_t *a, uint64_t *b, int norb, int pos, int create)
+{
+    int o = occupied(*a, *b, norb, pos);
+    if (create == o) return 0;
+    int sg = (n_before(*a, *b, norb, pos) & 1) ? -1 : 1;
+    flip(a, b, norb, pos);
+    return sg;
+}
+
+/* <D_j|H|D_i> for D_j != D_i (Slater-Condon rules) */
+double orc_hoff(const orc_sys *s, uint64_t ia, uint64_t ib, uint64_t ja, uint64_t jb)
+{
+    int N = s->norb;
+    uint64_t da = ia ^ ja, db = ib ^ jb;
+    int nd = popc(da) + popc(db);
+    if (nd == 0 || nd > 4) return 0.0;
+    if (popc(ia) != popc(ja) || popc(ib) != popc(jb)) return 0.0;
+    int rem[2], add[2], nr = 0, nadd = 0;
+    for (int pos = 0; pos < 2 * N; pos++) {
+        int oi = occupied(ia, ib, N, pos), oj = occupied(ja, jb, N, pos);
+        if (oi && !oj) rem[nr++] = pos;
+        if (!oi && oj) add[nadd++] = pos;
+    }
+    if (nr == 1) {
+        int i = rem[0], a = add[0];
+        uint64_t xa = ia, xb = ib;
+        int g = apply_op(&xa, &xb, N, i, 0);
+        g *= apply_op(&xa, &xb, N, a, 1);
+        int sp = i >= N, oi = i % N, oa = a % N;
+        xacc x;
+        xacc_zero(&x);
+        xacc_add(&x, s->h[oa * N + oi], 0);
+        for (int k = 0; k < 2 * N; k++) {
+            if (k == i || !occupied(ia, ib, N, k)) continue;
+            int ok = k % N;
+            xacc_add(&x, eri(s, oa, oi, ok, ok), 0);
+            if ((k >= N) == sp) xacc_add(&x, eri(s, oa, ok, ok, oi), 1);
+        }
+        double v = xacc_round(&x);
+        return g < 0 ? -v : v;
+    }
+    /* double: i < j removed, a < b added; gamma from a+_a a+_b a_j a_i |D_i> */
+    int i = rem[0], j = rem[1], a = add[0], b = add[1];
+    uint64_t xa = ia, xb = ib;
+    int g = apply_op(&xa, &xb, N, i, 0);
+    g *= apply_op(&xa, &xb, N, j, 0);
+    g *= apply_op(&xa, &xb, N, b, 1);
+    g *= apply_op(&xa, &xb, N, a, 1);
+    int si = i >= N, sj = j >= N, sa = a >= N, sb = b >= N;
+    int oi = i % N, oj = j % N, oa = a % N, ob = b % N;
+    /* <ab|ij> = (ai|bj) d(sa,si) d(sb,sj);  <ab|ji> = (aj|bi) d(sa,sj) d(sb,si) */
+    int dir = (sa == si) && (sb == sj), exch = (sa == sj) && (sb == si);
+    double v;
+    if (dir && exch) v = eri(s, oa, oi, ob, oj) - eri(s, oa, oj, ob, oi);
+    else if (dir) v = eri(s, oa, oi, ob, oj);
+    else if (exch) v = -eri(s, oa, oj, ob, oi);
+    else v = 0.0;
+    return g < 0 ? -v : v;
+}
+
+static int sys_finish(orc_sys *s)
+{
+    if (popc(s->ref_a) != s->na || popc(s->ref_b) != s->nb) return -1;
+    if (s->norb < 64 && ((s->ref_a | s->ref_b) >> s->norb) != 0) return -1;
+    xdiag(s, s->ref_a, s->ref_b, &s->xref);
+    xacc x = s->xref;
+    xacc_add(&x, s->ecore, 0);
+    s->eref = xacc_round(&x);
+    return 0;
+}
+
+orc_sys *orc_sys_abinitio(int norb, int na, int nb, double ecore, const double *h,
+                          const double *eri_packed, const uint64_t *ref)
+{
+    if (norb < 1 || norb > 64 || na < 0 || nb < 0 || na > norb || nb > norb) return NULL;
+    orc_sys *s = calloc(1, sizeof *s);
+    s->norb = norb; s->na = na; s->nb = nb; s->kind = 0; s->ecore = ecore;
+    int64_t np = (int64_t)norb * (norb + 1) / 2, ne = np * (np + 1) / 2;
+    s->h = malloc(sizeof(double) * norb * norb);
+    s->eri = malloc(sizeof(double) * ne);
+    memcpy(s->h, h, sizeof(double) * norb * norb);
+    memcpy(s->eri, eri_packed, sizeof(double) * ne);
+    if (ref) { s->ref_a = ref[0]; s->ref_b = ref[1]; }
+    else { s->ref_a = lowmask(na); s->ref_b = lowmask(nb); } /* aufbau */
+    if (sys_finish(s)) { orc_sys_free(s); return NULL; }
+    return s;
+}
+
+/* Hubbard model: h_pq = -t for lattice neighbours, (pp|pp) = U.
+ * Sites are numbered x + lx*y; neighbour slots in the order -x, +x, -y, +y. */
+orc_sys *orc_sys_hubbard(int lx, int ly, int px, int py, double t, double U, int na, int nb,
+                         const uint64_t *ref)
+{
+    int ns = lx * ly;
+    if (ns < 1 || ns > 64 || (px && lx < 3 && lx > 1) || (py && ly < 3 && ly > 1)) return NULL;
+    orc_sys *s = calloc(1, sizeof *s);
+    s->norb = ns; s->na = na; s->nb = nb; s->kind = 1; s->lx = lx; s->ly = ly; s->t = t; s->U = U;
+    s->z = ly > 1 ? 4 : 2;
+    s->nbr = malloc(sizeof(int) * 4 * ns);
+    for (int y = 0; y < ly; y++)
+        for (int x = 0; x < lx; x++) {
+            int p = x + lx * y, *nb4 = s->nbr + 4 * p;
+            nb4[0] = x > 0 ? p - 1 : (px && lx > 1 ? p + lx - 1 : -1);
+            nb4[1] = x < lx - 1 ? p + 1 : (px && lx > 1 ? p - (lx - 1) : -1);
+            nb4[2] = y > 0 ? p - lx : (py && ly > 1 ? p + lx * (ly - 1) : -1);
+            nb4[3] = y < ly - 1 ? p + lx : (py && ly > 1 ? p - lx * (ly - 1) : -1);
+        }
+    int64_t np = (int64_t)ns * (ns + 1) / 2, ne = np * (np + 1) / 2;
+    s->h = calloc((size_t)ns * ns, sizeof(double));
+    s->eri = calloc((size_t)ne, sizeof(double));
+    for (int p = 0; p < ns; p++)
+        for (int k = 0; k < s->z; k++) {
+            int q = s->nbr[4 * p + k];
+            if (q >= 0) s->h[p * ns + q] = -t;
+        }
+    for (int p = 0; p < ns; p++) s->eri[pairidx(pairidx(p, p), pairidx(p, p))] = U;
+    if (ref) { s->ref_a = ref[0]; s->ref_b = ref[1]; }
+    else { /* Neel: alpha on (x+y) even, beta on (x+y) odd */
+        for (int y = 0; y < ly; y++)
+            for (int x = 0; x < lx; x++) {
+                if (((x + y) & 1) == 0) s->ref_a |= 1ULL << (x + lx * y);
+                else s->ref_b |= 1ULL << (x + lx * y);
+            }
+    }
+    if (sys_finish(s)) { orc_sys_free(s); return NULL; }
+    return s;
+}
+
+void orc_sys_free(orc_sys *s)
+{
+    if (!s) return;
+    free(s->h); free(s->eri); free(s->nbr); free(s);
+}
+
+void orc_sys_ref(const orc_sys *s, uint64_t out[2]) { out[0] = s->ref_a; out[1] = s->ref_b; }
+
+/* dense H - E_ref over a given list of determinants (for exact diagonalisation) */
+void orc_build_hamiltonian(const orc_sys *s, int64_t n, const uint64_t *da, const uint64_t *db, double *H)
+{
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t j = 0; j < n; j++)
+            H[i * n + j] = (i == j) ? orc_hdiag_rel(s, da[i], db[i]) : orc_hoff(s, da[j], db[j], da[i], db[i]);
+}
+
+/* ------------------------------------------------------------------ */
+/* Excitation generation (Sec. II; App. A, "Uniform excitation          */
+/* generation" with spin conditioning; lattice hops for Hubbard).       */
+/* ------------------------------------------------------------------ */
+enum { CLS_SINGLE_A = 0, CLS_SINGLE_B, CLS_DOUBLE_AB, CLS_DOUBLE_AA, CLS_DOUBLE_BB, CLS_HOP, NCLS };
+
+/* generation probability of one outcome of class c */
+double orc_pgen(const orc_sys *s, double p_single, int c)
+{
+    int n = s->na + s->nb, N = s->norb;
+    int64_t ma = N - s->na, mb = N - s->nb;
+    int64_t nn = (int64_t)n * (n - 1);
+    switch (c) {
+    case CLS_SINGLE_A: return p_single / ((double)n * (double)ma);
+    case CLS_SINGLE_B: return p_single / ((double)n * (double)mb);
+    case CLS_DOUBLE_AB: return ((1.0 - p_single) * 2.0) / ((double)nn * (double)(ma * mb));
+    case CLS_DOUBLE_AA: return ((1.0 - p_single) * 4.0) / ((double)nn * (double)(ma * (ma - 1)));
+    case CLS_DOUBLE_BB: return ((1.0 - p_single) * 4.0) / ((double)nn * (double)(mb * (mb - 1)));
+    case CLS_HOP: return 1.0 / ((double)n * (double)s->z);
+    }
+    return 0.0;
+}
+
+/* orbital of electron e (alpha electrons first, each spin ascending) */
+static int electron_orb(uint64_t a, uint64_t b, int na, int e, int *spin)
+{
+    uint64_t w = e < na ? a : b;
+    int k = e < na ? e : e - na;
+    *spin = e < na ? 0 : 1;
+    for (int p = 0; p < 64; p++)
+        if ((w >> p) & 1) { if (k == 0) return p; k--; }
+    return -1;
+}
+/* k-th empty orbital of a spin word */
+static int kth_empty(uint64_t w, int norb, int k)
+{
+    for (int p = 0; p < norb; p++)
+        if (!((w >> p) & 1)) { if (k == 0) return p; k--; }
+    return -1;
+}
+
+/* One generation from D = (a,b) with the four words of its draw.
+ * Returns the class, or -1 for a failed attempt; target in (*ta, *tb). */
+int orc_generate(const orc_sys *s, double p_single, uint64_t a, uint64_t b, const uint64_t w[4],
+                 uint64_t *ta, uint64_t *tb)
+{
+    int N = s->norb, n = s->na + s->nb;
+    *ta = a; *tb = b;
+    if (n == 0) return -1;
+    if (s->kind == 1) {
+        int sp, e = (int)pick(w[1], (uint64_t)n);
+        int p = electron_orb(a, b, s->na, e, &sp);
+        int q = s->nbr[4 * p + (int)pick(w[2], (uint64_t)s->z)];
+        if (q < 0) return -1;
+        uint64_t *x = sp ? tb : ta;
+        if ((*x >> q) & 1) return -1;
+        *x ^= (1ULL << p) | (1ULL << q);
+        return CLS_HOP;
+    }
+    int ma = N - s->na, mb = N - s->nb;
+    if (u53(w[0]) < p_single) {
+        int sp, e = (int)pick(w[1], (uint64_t)n);
+        int i = electron_orb(a, b, s->na, e, &sp);
+        int m = sp ? mb : ma;
+        if (m == 0) return -1;
+        uint64_t *x = sp ? tb : ta;
+        int h = kth_empty(*x, N, (int)pick(w[2], (uint64_t)m));
+        *x ^= (1ULL << i) | (1ULL << h);
+        return sp ? CLS_SINGLE_B : CLS_SINGLE_A;
+    }
+    if (n < 2) return -1;
+    uint64_t xe = pick(w[1], (uint64_t)n * (uint64_t)(n - 1));
+    int e1 = (int)(xe / (uint64_t)(n - 1)), r = (int)(xe % (uint64_t)(n - 1));
+    int e2 = r + (r >= e1 ? 1 : 0);
+    int s1, s2;
+    int o1 = electron_orb(a, b, s->na, e1, &s1), o2 = electron_orb(a, b, s->na, e2, &s2);
+    if (s1 != s2) {
+        if (ma == 0 || mb == 0) return -1;
+        int oa = s1 == 0 ? o1 : o2, ob = s1 == 0 ? o2 : o1;
+        uint64_t y = pick(w[2], (uint64_t)ma * (uint64_t)mb);
+        int ha = kth_empty(a, N, (int)(y / (uint64_t)mb)), hb = kth_empty(b, N, (int)(y % (uint64_t)mb));
+        *ta ^= (1ULL << oa) | (1ULL << ha);
+        *tb ^= (1ULL << ob) | (1ULL << hb);
+        return CLS_DOUBLE_AB;
+    }
+    int m = s1 ? mb : ma;
+    if (m < 2) return -1;
+    uint64_t *x = s1 ? tb : ta;
+    uint64_t y = pick(w[2], (uint64_t)m * (uint64_t)(m - 1));
+    int h1 = (int)(y / (uint64_t)(m - 1)), rr = (int)(y % (uint64_t)(m - 1));
+    int h2 = rr + (rr >= h1 ? 1 : 0);
+    int pa = kth_empty(*x, N, h1), pb = kth_empty(*x, N, h2);
+    *x ^= (1ULL << o1) | (1ULL << o2) | (1ULL << pa) | (1ULL << pb);
+    return s1 ? CLS_DOUBLE_BB : CLS_DOUBLE_AA;
+}
+
+/* ------------------------------------------------------------------ */
+/* FCIQMC run                                                           */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double tau, shift_damping, target_walkers, initial_walkers, initial_shift;
+    double initiator_threshold, c_min, p_single;
+    int64_t shift_interval;
+    uint64_t seed;
+    int64_t semistoch_size, semistoch_start;
+} orc_params;
+
+typedef struct { uint64_t a, b; double c, hd; int flags; } odet; /* flags: 1 ref, 2 in D */
+typedef struct { uint64_t a, b; double w; int init; } ospawn;
+
+typedef struct {
+    int64_t iter;
+    double nw, S, e_num, e_den;
+    int64_t ndet, attempts, spawns, rejected;
+    double annihilated;
+    int vary;
+} orc_stat;
+
+typedef struct {
+    orc_sys *s;
+    orc_params p;
+    double lam[NCLS];
+    odet *L;
+    int64_t n, cap;
+    int64_t iter;
+    double S;
+    int vary;
+    int64_t shift_start, cnt;
+    u128 nw_last;
+    /* semi-stochastic space: D sorted by key; CSR over D indices */
+    int64_t nd;
+    uint64_t *Da, *Db;
+    int64_t *rowptr, *col;
+    double *val;
+    orc_stat *st;
+    int64_t nst, stcap;
+    int err;
+} orc_run;
+
+static int cmp_key(uint64_t a1, uint64_t b1, uint64_t a2, uint64_t b2)
+{
+    if (a1 != a2) return a1 < a2 ? -1 : 1;
+    if (b1 != b2) return b1 < b2 ? -1 : 1;
+    return 0;
+}
+static int cmp_odet(const void *x, const void *y)
+{
+    const odet *p = x, *q = y;
+    return cmp_key(p->a, p->b, q->a, q->b);
+}
+static int cmp_ospawn(const void *x, const void *y)
+{
+    const ospawn *p = x, *q = y;
+    return cmp_key(p->a, p->b, q->a, q->b);
+}
+
+static int64_t find_det(const odet *L, int64_t n, uint64_t a, uint64_t b)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) / 2;
+        int c = cmp_key(L[mid].a, L[mid].b, a, b);
+        if (c == 0) return mid;
+        if (c < 0) lo = mid + 1; else hi = mid;
+    }
+    return -1;
+}
+static int64_t find_D(const orc_run *r, uint64_t a, uint64_t b)
+{
+    int64_t lo = 0, hi = r->nd;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) / 2;
+        int c = cmp_key(r->Da[mid], r->Db[mid], a, b);
+        if (c == 0) return mid;
+        if (c < 0) lo = mid + 1; else hi = mid;
+    }
+    return -1;
+}
+
+/* floor(|c| 2^32) as an integer (reading R6) */
+static u128 fx32(double c) { return (u128)(uint64_t)floor(fabs(c) * 4294967296.0); }
+
+orc_run *orc_create(orc_sys *s, const orc_params *p)
+{
+    orc_run *r = calloc(1, sizeof *r);
+    r->s = s;
+    r->p = *p;
+    for (int c = 0; c < NCLS; c++) r->lam[c] = p->tau / orc_pgen(s, p->p_single, c);
+    r->cap = 1024;
+    r->L = malloc(sizeof(odet) * r->cap);
+    r->n = 1;
+    r->L[0].a = s->ref_a; r->L[0].b = s->ref_b; r->L[0].c = p->initial_walkers;
+    r->L[0].hd = 0.0; r->L[0].flags = 1;
+    r->S = p->initial_shift;
+    r->stcap = 1024;
+    r->st = malloc(sizeof(orc_stat) * r->stcap);
+    return r;
+}
+
+void orc_destroy(orc_run *r)
+{
+    if (!r) return;
+    free(r->L); free(r->Da); free(r->Db); free(r->rowptr); free(r->col); free(r->val); free(r->st);
+    free(r);
+}
+
+/* top-N_D determinants by |C| (ties: ascending key), then H^D in CSR (Sec. III) */
+typedef struct { double m; uint64_t a, b; } ocand;
+static int cmp_cand(const void *x, const void *y)
+{
+    const ocand *p = x, *q = y;
+    if (p->m != q->m) return p->m > q->m ? -1 : 1;
+    return cmp_key(p->a, p->b, q->a, q->b);
+}
+static void build_D(orc_run *r)
+{
+    int64_t n = r->n, nd = r->p.semistoch_size < n ? r->p.semistoch_size : n;
+    ocand *cd = malloc(sizeof(ocand) * (n ? n : 1));
+    for (int64_t i = 0; i < n; i++) { cd[i].m = fabs(r->L[i].c); cd[i].a = r->L[i].a; cd[i].b = r->L[i].b; }
+    qsort(cd, n, sizeof(ocand), cmp_cand);
+    odet *tmp = malloc(sizeof(odet) * (nd ? nd : 1));
+    for (int64_t i = 0; i < nd; i++) { tmp[i].a = cd[i].a; tmp[i].b = cd[i].b; }
+    qsort(tmp, nd, sizeof(odet), cmp_odet);
+    r->nd = nd;
+    r->Da = malloc(sizeof(uint64_t) * (nd ? nd : 1));
+    r->Db = malloc(sizeof(uint64_t) * (nd ? nd : 1));
+    for (int64_t i = 0; i < nd; i++) { r->Da[i] = tmp[i].a; r->Db[i] = tmp[i].b; }
+    r->rowptr = malloc(sizeof(int64_t) * (nd + 1));
+    int64_t cap = 16, nnz = 0;
+    r->col = malloc(sizeof(int64_t) * cap);
+    r->val = malloc(sizeof(double) * cap);
+    r->rowptr[0] = 0;
+    for (int64_t i = 0; i < nd; i++) {
+        for (int64_t j = 0; j < nd; j++) {
+            double v;
+            if (i == j) v = orc_hdiag_rel(r->s, r->Da[i], r->Db[i]);
+            else {
+                int lev = popc(r->Da[i] ^ r->Da[j]) + popc(r->Db[i] ^ r->Db[j]);
+                if (lev > 4) continue;
+                v = orc_hoff(r->s, r->Da[j], r->Db[j], r->Da[i], r->Db[i]); /* <D_i|H|D_j> */
+                if (v == 0.0) continue;
+            }
+            if (nnz == cap) {
+                cap *= 2;
+                r->col = realloc(r->col, sizeof(int64_t) * cap);
+                r->val = realloc(r->val, sizeof(double) * cap);
+            }
+            r->col[nnz] = j; r->val[nnz] = v; nnz++;
+        }
+        r->rowptr[i + 1] = nnz;
+    }
+    for (int64_t i = 0; i < n; i++)
+        if (find_D(r, r->L[i].a, r->L[i].b) >= 0) r->L[i].flags |= 2;
+    free(cd); free(tmp);
+}
+
+int64_t orc_semistoch_info(const orc_run *r, int64_t *nnz)
+{
+    if (nnz) *nnz = r->nd ? r->rowptr[r->nd] : 0;
+    return r->nd;
+}
+
+static double round_stoch(double v, double cmin, double u)
+{
+    /* Eq. (2): keep |v| >= C_min; else sign(v) C_min with prob |v|/C_min, else 0 */
+    if (v == 0.0 || fabs(v) >= cmin) return v;
+    return u < fabs(v) / cmin ? copysign(cmin, v) : 0.0;
+}
+
+/* one projector iteration; returns 0 or a nonzero error code */
+static int one_iteration(orc_run *r)
+{
+    const orc_sys *s = r->s;
+    const orc_params *P = &r->p;
+    int64_t it = r->iter;
+    double cmin = P->c_min;
+
+    if (P->semistoch_size > 0 && r->nd == 0 && r->vary && it == r->shift_start + P->semistoch_start)
+        build_D(r);
+
+    /* (a) spawning from the start-of-iteration amplitudes */
+    int64_t ns = 0, scap = 1024, attempts = 0;
+    ospawn *sp = malloc(sizeof(ospawn) * scap);
+    for (int64_t i = 0; i < r->n; i++) {
+        odet *d = &r->L[i];
+        if (d->c == 0.0) continue;
+        double mag = fabs(d->c);
+        if (mag >= 0x1p40) { free(sp); return 3; }
+        uint64_t nat = (uint64_t)ceil(mag);
+        attempts += (int64_t)nat;
+        int init = mag > P->initiator_threshold || (d->flags & 3);
+        double cper = d->c / (double)nat;
+        for (uint64_t k = 0; k < nat; k++) {
+            uint64_t w[4], ta, tb;
+            draw(P->seed, d->a, d->b, it, k, PURPOSE_SPAWN, w);
+            int cls = orc_generate(s, P->p_single, d->a, d->b, w, &ta, &tb);
+            if (cls < 0) continue;
+            double H = orc_hoff(s, d->a, d->b, ta, tb);
+            if (H == 0.0) continue;
+            double ws = -(H * (r->lam[cls] * cper));
+            if (fabs(ws) < cmin) {
+                ws = round_stoch(ws, cmin, u53(w[3]));
+                if (ws == 0.0) continue;
+            }
+            if ((d->flags & 2) && find_D(r, ta, tb) >= 0) continue; /* D -> D is exact */
+            if (ns == scap) { scap *= 2; sp = realloc(sp, sizeof(ospawn) * scap); }
+            sp[ns].a = ta; sp[ns].b = tb; sp[ns].w = ws; sp[ns].init = init; ns++;
+        }
+    }
+
+    /* (b) death, in place; deterministic space: exact projection (Sec. III) */
+    double *c0 = malloc(sizeof(double) * (r->n ? r->n : 1));
+    for (int64_t i = 0; i < r->n; i++) c0[i] = r->L[i].c;
+    double *cd_new = NULL;
+    if (r->nd) {
+        double *cD = malloc(sizeof(double) * r->nd);
+        for (int64_t k = 0; k < r->nd; k++) {
+            int64_t i = find_det(r->L, r->n, r->Da[k], r->Db[k]);
+            cD[k] = i >= 0 ? c0[i] : 0.0;
+        }
+        cd_new = malloc(sizeof(double) * r->nd);
+        for (int64_t k = 0; k < r->nd; k++) {
+            double y = 0.0;
+            for (int64_t q = r->rowptr[k]; q < r->rowptr[k + 1]; q++) y = y + r->val[q] * cD[r->col[q]];
+            cd_new[k] = cD[k] - P->tau * (y - r->S * cD[k]);
+        }
+        free(cD);
+    }
+    for (int64_t i = 0; i < r->n; i++) {
+        odet *d = &r->L[i];
+        if (d->flags & 2) { d->c = cd_new[find_D(r, d->a, d->b)]; continue; }
+        double f = 1.0 - P->tau * (d->hd - r->S);
+        double cp = d->c * f;
+        if (cp != 0.0 && fabs(cp) < cmin) {
+            uint64_t w[4];
+            draw(P->seed, d->a, d->b, it, 0, PURPOSE_DEATH, w);
+            cp = round_stoch(cp, cmin, u53(w[0]));
+        }
+        d->c = cp;
+    }
+    free(cd_new);
+
+    /* (c) annihilation with the initiator rule */
+    qsort(sp, ns, sizeof(ospawn), cmp_ospawn);
+    int64_t outcap = r->n + ns + 1, no = 0, rejected = 0;
+    odet *out = malloc(sizeof(odet) * outcap);
+    i128 ann = 0;
+    int64_t li = 0, si = 0;
+    while (li < r->n || si < ns) {
+        int c;
+        if (li >= r->n) c = 1;
+        else if (si >= ns) c = -1;
+        else c = cmp_key(r->L[li].a, r->L[li].b, sp[si].a, sp[si].b);
+        odet d;
+        double cstart = 0.0;
+        int present = 0;
+        if (c <= 0) { d = r->L[li]; cstart = c0[li]; present = 1; li++; }
+        else { d.a = sp[si].a; d.b = sp[si].b; d.c = 0.0; d.hd = 0.0; d.flags = 0; }
+        double acc = d.c;
+        if (c >= 0) {
+            int occ = present && cstart != 0.0;
+            xacc x;
+            xacc_zero(&x);
+            int64_t nacc = 0;
+            i128 in = present ? (i128)fx32(d.c) : 0;
+            uint64_t ka = d.a, kb = d.b;
+            while (si < ns && sp[si].a == ka && sp[si].b == kb) {
+                if (sp[si].init || occ) { xacc_add(&x, sp[si].w, 0); in += (i128)fx32(sp[si].w); nacc++; }
+                else rejected++;
+                si++;
+            }
+            if (nacc > 0) {
+                double sw = xacc_round(&x);
+                acc = present ? d.c + sw : sw;
+                ann += in - (i128)fx32(acc);
+                if (!(d.flags & 2) && acc != 0.0 && fabs(acc) < cmin) {
+                    uint64_t w[4];
+                    draw(P->seed, d.a, d.b, it, 0, PURPOSE_ANNIH, w);
+                    acc = round_stoch(acc, cmin, u53(w[0]));
+                }
+            }
+        }
+        d.c = acc;
+        if (acc == 0.0 && !(d.flags & 3)) continue;
+        if (!present) d.hd = orc_hdiag_rel(s, d.a, d.b);
+        out[no++] = d;
+    }
+    free(sp); free(c0); free(r->L);
+    r->L = out; r->n = no; r->cap = outcap;
+
+    /* reductions: N_w (R6), E_num / E_den (Eq. (8)) */
+    u128 W = 0;
+    double e_num = 0.0, e_den = 0.0;
+    for (int64_t i = 0; i < no; i++) {
+        odet *d = &out[i];
+        if (fabs(d->c) >= 0x1p31) return 3;
+        W += fx32(d->c);
+        if (d->flags & 1) { e_den = d->c; continue; }
+        int lev = popc(d->a ^ s->ref_a) + popc(d->b ^ s->ref_b);
+        if (lev <= 4 && d->c != 0.0) e_num = e_num + orc_hoff(s, d->a, d->b, s->ref_a, s->ref_b) * d->c;
+    }
+    double nw = (double)W * 0x1p-32;
+    if (!(nw == nw)) return 3;
+
+    /* shift (reading R7) */
+    if (!r->vary) {
+        if (nw >= P->target_walkers) { r->vary = 1; r->shift_start = it; r->nw_last = W; r->cnt = 0; }
+    } else if (++r->cnt == P->shift_interval) {
+        double ratio = nw / ((double)r->nw_last * 0x1p-32);
+        double cz = P->shift_damping / ((double)P->shift_interval * P->tau);
+        r->S = r->S - cz * orc_ln(ratio);
+        r->nw_last = W;
+        r->cnt = 0;
+    }
+
+    if (r->nst == r->stcap) { r->stcap *= 2; r->st = realloc(r->st, sizeof(orc_stat) * r->stcap); }
+    orc_stat *t = &r->st[r->nst++];
+    t->iter = it; t->nw = nw; t->S = r->S; t->e_num = e_num; t->e_den = e_den;
+    t->ndet = no; t->attempts = attempts; t->spawns = ns; t->rejected = rejected;
+    t->annihilated = (double)ann * 0x1p-32; t->vary = r->vary;
+    r->iter = it + 1;
+    return 0;
+}
+
+int orc_step(orc_run *r, int64_t n)
+{
+    for (int64_t k = 0; k < n; k++) {
+        int e = one_iteration(r);
+        if (e) { r->err = e; return e; }
+    }
+    return 0;
+}
+
+int64_t orc_ndet(const orc_run *r) { return r->n; }
+int64_t orc_iter(const orc_run *r) { return r->iter; }
+double orc_shift(const orc_run *r) { return r->S; }
+
+/* list in ascending key order (the list is kept sorted) */
+void orc_export(const orc_run *r, uint64_t *a, uint64_t *b, double *c, double *hd, int32_t *flags)
+{
+    for (int64_t i = 0; i < r->n; i++) {
+        a[i] = r->L[i].a; b[i] = r->L[i].b; c[i] = r->L[i].c; hd[i] = r->L[i].hd; flags[i] = r->L[i].flags;
+    }
+}
+
+/* shift state: S, vary, shift_start, cnt, nw_last (hi, lo words) */
+void orc_export_shift(const orc_run *r, double *S, int64_t st[3], uint64_t nwl[2])
+{
+    *S = r->S; st[0] = r->vary; st[1] = r->shift_start; st[2] = r->cnt;
+    nwl[0] = (uint64_t)(r->nw_last >> 64); nwl[1] = (uint64_t)r->nw_last;
+}
+
+/* replace the state (used to time or check iterations from a given point);
+ * keys need not be sorted; pinned reference flag is re-derived; D is not imported */
+void orc_import(orc_run *r, int64_t n, const uint64_t *a, const uint64_t *b, const double *c,
+                int64_t iter, double S, int vary, int64_t shift_start, int64_t cnt, uint64_t nwl_hi, uint64_t nwl_lo)
+{
+    free(r->L);
+    r->cap = n + 1;
+    r->L = malloc(sizeof(odet) * r->cap);
+    for (int64_t i = 0; i < n; i++) {
+        r->L[i].a = a[i]; r->L[i].b = b[i]; r->L[i].c = c[i];
+        r->L[i].hd = orc_hdiag_rel(r->s, a[i], b[i]);
+        r->L[i].flags = (a[i] == r->s->ref_a && b[i] == r->s->ref_b) ? 1 : 0;
+    }
+    r->n = n;
+    qsort(r->L, n, sizeof(odet), cmp_odet);
+    r->iter = iter; r->S = S; r->vary = vary; r->shift_start = shift_start; r->cnt = cnt;
+    r->nw_last = ((u128)nwl_hi << 64) | nwl_lo;
+}
+
+int64_t orc_nstats(const orc_run *r) { return r->nst; }
+void orc_stats(const orc_run *r, int64_t i0, int64_t n, orc_stat *out)
+{
+    memcpy(out, r->st + i0, sizeof(orc_stat) * n);
+}
+int orc_stat_size(void) { return (int)sizeof(orc_stat); }
+int orc_params_size(void) { return (int)sizeof(orc_params); }
+
+/* E_num, E_den of the current list (Eq. (8)): E_num = sum_{j != ref} H_ref,j C_j
+ * summed in ascending key order, E_den = C_ref */
+void orc_proj_energy(const orc_run *r, double *num, double *den)
+{
+    const orc_sys *s = r->s;
+    double e_num = 0.0, e_den = 0.0;
+    for (int64_t i = 0; i < r->n; i++) {
+        const odet *d = &r->L[i];
+        if (d->a == s->ref_a && d->b == s->ref_b) { e_den = d->c; continue; }
+        int lev = popc(d->a ^ s->ref_a) + popc(d->b ^ s->ref_b);
+        if (lev <= 4 && d->c != 0.0) e_num = e_num + orc_hoff(s, d->a, d->b, s->ref_a, s->ref_b) * d->c;
+    }
+    *num = e_num; *den = e_den;
+}

@@ -1,0 +1,395 @@
+"""Pins of the CPU oracle to things other than itself (no GPU needed).
+
+Each test ties one part of the oracle to an independent source: a library
+routine (numpy Philox, math.fsum, numpy.log), brute-force operator algebra,
+closed-form energies, exact enumeration of generation probabilities, and the
+exact expectation value of one projector step (Eq. (1) of the paper).
+"""
+import itertools
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from tests import bruteforce
+
+MASK = (1 << 64) - 1
+
+
+# ----------------------------------------------------------------- Philox
+@pytest.mark.parametrize("key,ctr", [((0, 0), (0, 0, 0, 0)), ((5, 7), (1, 2, 3, 4)),
+                                     ((MASK, 12345), (MASK - 3, 99, 2 ** 63, 17)),
+                                     ((0x243F6A8885A308D3, 0x13198A2E03707344), (2 ** 40, 1, 0, 0x1234 << 8 | 1))])
+def test_philox_matches_numpy(key, ctr):
+    # numpy's Philox is Philox4x64-10; it increments the counter before the first block
+    bg = np.random.Philox(key=np.array(key, np.uint64), counter=np.array(ctr, np.uint64))
+    raw = bg.random_raw(8)
+    c1 = [(ctr[0] + 1) & MASK, ctr[1] + (1 if ctr[0] == MASK else 0), ctr[2], ctr[3]]
+    c2 = [(ctr[0] + 2) & MASK, ctr[1] + (1 if ctr[0] >= MASK - 1 else 0), ctr[2], ctr[3]]
+    np.testing.assert_array_equal(oracle.philox4x64_10(c1, key), raw[:4])
+    np.testing.assert_array_equal(oracle.philox4x64_10(c2, key), raw[4:])
+
+
+# ----------------------------------------------------------------- exact sums
+def test_fsum_matches_math_fsum():
+    rng = np.random.default_rng(11)
+    cases = [[1e16, 1.0, -1e16], [0.1] * 10, [1e308, 1e308, -1e308], [5e-324, 5e-324, -1e-323],
+             [2.0 ** -1074, 1.0, -1.0], [1.0, 2.0 ** -53, 2.0 ** -53], [1.0, 2.0 ** -53],
+             [1.0 + 2.0 ** -52, 2.0 ** -53], [-0.0], [], [3.0, -3.0]]
+    for _ in range(300):
+        n = int(rng.integers(1, 60))
+        mag = rng.uniform(-300, 300, size=n)
+        x = rng.standard_normal(n) * 10.0 ** mag
+        if rng.random() < 0.3:  # heavy cancellation
+            x = np.concatenate([x, -x[: n // 2] * (1 + 2.0 ** -50)])
+        cases.append(list(x))
+    for c in cases:
+        exact = float(sum((Fraction(v) for v in c), Fraction(0)))  # correctly rounded exact sum
+        assert oracle.fsum(c) == exact, c
+        try:
+            assert oracle.fsum(c) == math.fsum(c), c
+        except OverflowError:  # math.fsum refuses an intermediate overflow
+            pass
+
+
+# ----------------------------------------------------------------- logarithm
+def test_ln_within_error_bound():
+    rng = np.random.default_rng(3)
+    xs = np.concatenate([10.0 ** rng.uniform(-300, 300, 2000), 1.0 + rng.uniform(-0.3, 0.3, 2000),
+                         [1.0, 2.0, 0.5, math.sqrt(2.0), np.nextafter(1.0, 2.0), np.nextafter(1.0, 0.0),
+                          5e-324, 1.7e308]])
+    for x in xs:
+        got, ref = oracle.ln(float(x)), float(np.log(x))
+        tol = 2.0 * np.spacing(abs(ref)) if ref != 0.0 else 0.0
+        assert abs(got - ref) <= tol, (x, got, ref)
+    assert oracle.ln(1.0) == 0.0
+
+
+# ----------------------------------------------------------------- Slater-Condon
+def _hubbard_integrals(lx, ly, px, py, t, U):
+    n = lx * ly
+    h = np.zeros((n, n))
+    for y in range(ly):
+        for x in range(lx):
+            p = x + lx * y
+            nbrs = []
+            if lx > 1:
+                nbrs += [((x - 1) % lx, y) if (x > 0 or px) else None, ((x + 1) % lx, y) if (x < lx - 1 or px) else None]
+            if ly > 1:
+                nbrs += [(x, (y - 1) % ly) if (y > 0 or py) else None, (x, (y + 1) % ly) if (y < ly - 1 or py) else None]
+            for nb in nbrs:
+                if nb is not None:
+                    h[p, nb[0] + lx * nb[1]] = -t
+    g = np.zeros((n,) * 4)
+    for p in range(n):
+        g[p, p, p, p] = U
+    return h, g
+
+
+@pytest.mark.parametrize("norb,na,nb", [(4, 2, 2), (5, 3, 2), (4, 1, 3), (5, 2, 0)])
+def test_slater_condon_abinitio_vs_bruteforce(norb, na, nb):
+    h, eri = workloads.synthetic_abinitio(norb, 3 * norb, 100 + norb + na)
+    ecore = 0.75
+    s = oracle.System.abinitio(h, eri, na, nb, ecore)
+    dets = s.determinants()
+    _, Hrel = s.hamiltonian(dets)
+    Hb = bruteforce.hamiltonian(norb, h, bruteforce.eri_full(norb, eri), ecore, dets)
+    Ho = Hrel + np.eye(len(dets)) * s.eref
+    scale = np.max(np.abs(Hb))
+    np.testing.assert_allclose(Ho, Hb, rtol=0, atol=1e-12 * scale)
+    # sign and magnitude of every off-diagonal element, symmetric matrix
+    np.testing.assert_allclose(Ho, Ho.T, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("lx,ly,px,py,na,nb", [(4, 1, 1, 0, 2, 2), (5, 1, 1, 0, 2, 3), (3, 2, 1, 0, 2, 2),
+                                               (2, 2, 0, 0, 2, 1)])
+def test_slater_condon_hubbard_vs_bruteforce(lx, ly, px, py, na, nb):
+    t, U = 1.0, 3.5
+    neel = na == nb and 2 * na == lx * ly
+    s = oracle.System.hubbard(lx, ly, px, py, t, U, na, nb, ref=None if neel else [(1 << na) - 1, (1 << nb) - 1])
+    dets = s.determinants()
+    _, Hrel = s.hamiltonian(dets)
+    h, g = _hubbard_integrals(lx, ly, px, py, t, U)
+    Hb = bruteforce.hamiltonian(lx * ly, h, g, 0.0, dets)
+    np.testing.assert_allclose(Hrel + np.eye(len(dets)) * s.eref, Hb, rtol=0, atol=1e-13)
+
+
+# ----------------------------------------------------------------- exact energies
+@pytest.mark.parametrize("lx,ly,na,nb", [(6, 1, 3, 3), (8, 1, 4, 4), (3, 4, 2, 2), (4, 3, 3, 1)])
+def test_u0_hubbard_closed_form(lx, ly, na, nb):
+    s = oracle.System.hubbard(lx, ly, 1, 1 if ly > 1 else 0, 1.0, 0.0, na, nb,
+                              ref=None if (na == nb and 2 * na == lx * ly) else [(1 << na) - 1, (1 << nb) - 1])
+    e0, _, _ = s.exact_ground_state()
+    exact = oracle.hubbard_u0_energy(lx, ly, 1.0, na, nb)
+    assert abs((e0 + s.eref) - exact) < 1e-10
+    if (lx, ly) == (8, 1):
+        assert abs(exact - 2.0 * (-2.0 - 2.0 * math.sqrt(2.0))) < 1e-12
+
+
+@pytest.mark.parametrize("U", [0.5, 4.0, 10.0])
+def test_two_site_hubbard_closed_form(U):
+    s = oracle.System.hubbard(2, 1, 0, 0, 1.0, U, 1, 1, ref=[1, 2])
+    e0, _, _ = s.exact_ground_state()
+    assert abs((e0 + s.eref) - 0.5 * (U - math.sqrt(U * U + 16.0))) < 1e-12
+
+
+# ----------------------------------------------------------------- excitation generation
+def _word_for(k, m):
+    """smallest 64-bit word w with floor(w m / 2^64) == k"""
+    return -((-k << 64) // m)
+
+
+def _enumerate_generator(s, p_single, det, z=2):
+    """All discrete outcomes of one generation from ``det`` with their exact
+    probabilities; returns {target: probability}, P(fail)."""
+    n = s.na + s.nb
+    N = s.norb
+    ps = Fraction(p_single)
+    out = {}
+    pfail = Fraction(0)
+    def rec(words, prob):
+        nonlocal pfail
+        cls, tgt = s.generate(p_single, det, words)
+        if cls < 0:
+            pfail += prob
+        else:
+            out.setdefault(tgt, []).append((prob, cls))
+    if s.kind == "hubbard":
+        for e in range(n):
+            for k in range(z):
+                rec([0, _word_for(e, n), _word_for(k, z), 0], Fraction(1, n * z))
+        return out, pfail
+    ma, mb = N - s.na, N - s.nb
+    single_w0, double_w0 = 0, MASK
+    for e in range(n):
+        m = ma if e < s.na else mb
+        if m == 0:
+            rec([single_w0, _word_for(e, n), 0, 0], ps / n)
+            continue
+        for hh in range(m):
+            rec([single_w0, _word_for(e, n), _word_for(hh, m), 0], ps / (n * m))
+    if n >= 2:
+        for x in range(n * (n - 1)):
+            e1, r = divmod(x, n - 1)
+            e2 = r + (r >= e1)
+            s1, s2 = e1 >= s.na, e2 >= s.na
+            base = (1 - ps) / (n * (n - 1))
+            if s1 != s2:
+                M = ma * mb
+            else:
+                m = mb if s1 else ma
+                M = m * (m - 1)
+            if M == 0:
+                rec([double_w0, _word_for(x, n * (n - 1)), 0, 0], base)
+                continue
+            for y in range(M):
+                rec([double_w0, _word_for(x, n * (n - 1)), _word_for(y, M), 0], base / M)
+    return out, pfail
+
+
+@pytest.mark.parametrize("which", ["abinitio", "abinitio_asym", "hubbard2d", "hubbard1d"])
+def test_pgen_exact_enumeration(which):
+    p_single = 0.1
+    if which == "abinitio":
+        sysd = workloads.small_abinitio(6, 3, 3)
+    elif which == "abinitio_asym":
+        sysd = workloads.small_abinitio(6, 3, 1)
+    elif which == "hubbard2d":
+        sysd = workloads.hubbard_2d(3, 4, 4.0)
+    else:
+        sysd = workloads.hubbard_1d(6, 1.0, 4.0)
+    s = oracle.system_from_workload(sysd)
+    z = 4 if sysd.get("ly", 1) > 1 else 2
+    rng = np.random.default_rng(5)
+    dets = s.determinants()
+    for det in [s.ref] + [dets[i] for i in rng.choice(len(dets), 5, replace=False)]:
+        out, pfail = _enumerate_generator(s, p_single, det, z)
+        total = pfail
+        for tgt, lst in out.items():
+            ptot = sum(p for p, _ in lst)
+            cls = lst[0][1]
+            assert all(c == cls for _, c in lst)
+            # the probability the oracle reports for this class equals the exact one
+            assert abs(s.pgen(p_single, cls) - float(ptot)) <= 1e-15 * float(ptot), (tgt, cls)
+            total += ptot
+            assert tgt != det
+            assert bin(tgt[0]).count("1") == s.na and bin(tgt[1]).count("1") == s.nb  # S_z conserved
+        assert total == 1
+        # every determinant connected to det by a non-zero matrix element is reachable
+        for d in dets:
+            if d != det and s.hoff(det, d) != 0.0:
+                assert d in out, d
+
+
+def test_generator_frequencies_chi2():
+    s = oracle.system_from_workload(workloads.small_abinitio(5, 2, 2))
+    det = s.ref
+    rng = np.random.default_rng(17)
+    n = 40000
+    counts = {}
+    words = rng.integers(0, 2 ** 63, size=(n, 4), dtype=np.uint64) * np.uint64(2) + \
+        rng.integers(0, 2, size=(n, 4), dtype=np.uint64)
+    fails = 0
+    for w in words:
+        cls, tgt = s.generate(0.1, det, w)
+        if cls < 0:
+            fails += 1
+            continue
+        counts.setdefault((tgt, cls), 0)
+        counts[(tgt, cls)] += 1
+    chi2 = 0.0
+    for (tgt, cls), k in counts.items():
+        e = n * s.pgen(0.1, cls)
+        chi2 += (k - e) ** 2 / e
+    dof = len(counts)
+    assert fails == 0
+    assert chi2 < dof + 5 * math.sqrt(2 * dof), (chi2, dof)
+
+
+# ----------------------------------------------------------------- projected energy
+@pytest.mark.parametrize("which", ["hubbard", "abinitio"])
+def test_projected_energy_exact_for_eigenstate(which):
+    sysd = workloads.hubbard_1d(6, 1.0, 4.0) if which == "hubbard" else workloads.small_abinitio(6, 3, 2)
+    s = oracle.system_from_workload(sysd)
+    e0, v, dets = s.exact_ground_state()
+    r = oracle.Run(s)
+    k = dets.index(s.ref)
+    v = v * (1e4 / v[k])
+    r.import_state([d[0] for d in dets], [d[1] for d in dets], v, 0, 0.0)
+    num, den = r.proj_energy()
+    assert abs(num / den - e0) < 1e-10 * max(1.0, abs(e0))
+
+
+# ----------------------------------------------------------------- one projector step
+def _expected_step(s, dets, c, tau, S, n_a, Hrel):
+    """E[C(t+dt)] for one iteration from amplitudes c (Eq. (3) with the
+    initiator rule: a spawn from a non-initiator onto an unoccupied
+    determinant is removed)."""
+    ref = dets.index(s.ref)
+    init = (np.abs(c) > n_a) | (np.arange(len(c)) == ref)
+    occ = c != 0.0
+    out = c - tau * (np.diag(Hrel) - S) * c
+    off = Hrel - np.diag(np.diag(Hrel))
+    for j in range(len(c)):
+        allowed = init | occ[j]
+        out[j] += -tau * np.sum(off[j, :] * c * allowed)
+    return out
+
+
+@pytest.mark.parametrize("case", ["hubbard_plain", "abinitio_plain", "abinitio_initiator", "hubbard_semistoch"])
+def test_one_step_expectation(case):
+    """Averaged over independent seeds, one oracle iteration must reproduce
+    (1 - dtau (H - S)) C (plain FCIQMC, Eq. (1)), or its initiator-truncated
+    form.  A wrong sign, p_gen, weight, death factor, rounding or summation
+    shows up as a biased component."""
+    if case.startswith("hubbard"):
+        sysd = workloads.hubbard_1d(6, 1.0, 2.0)
+        tau = 0.02
+    else:
+        sysd = workloads.small_abinitio(5, 2, 2, seed=31)
+        tau = 0.002
+    s = oracle.system_from_workload(sysd)
+    e0, v, dets = s.exact_ground_state()
+    _, Hrel = s.hamiltonian(dets)
+    rng = np.random.default_rng(1)
+    n_a = 3.0 if "initiator" in case else 0.0
+    c = np.round(rng.normal(0, 1, len(dets)) * 4.0, 1)
+    c[np.abs(c) < 1.0] = 0.0 if "initiator" in case else 1.5
+    k = dets.index(s.ref)
+    c[k] = 20.0
+    S = -0.3
+    semi = "semistoch" in case
+    nseeds = 1500
+    acc = np.zeros(len(dets))
+    acc2 = np.zeros(len(dets))
+    index = {d: i for i, d in enumerate(dets)}
+    for seed in range(1, nseeds + 1):
+        r = oracle.Run(s, tau=tau, seed=seed, initiator_threshold=n_a, initial_shift=S,
+                       target_walkers=1e12, semistoch_size=40 if semi else 0, semistoch_start=1)
+        if semi:
+            r.import_state([d[0] for d in dets], [d[1] for d in dets], c, 5, S, vary=1, shift_start=4,
+                           cnt=0, nw_last=1 << 70)
+        else:
+            r.import_state([d[0] for d in dets], [d[1] for d in dets], c, 5, S)
+        r.step(1)
+        if semi:
+            assert r.semistoch_info()[0] == 40
+        ex = r.export()
+        cn = np.zeros(len(dets))
+        for a, b, cc in zip(ex["alpha"], ex["beta"], ex["c"]):
+            cn[index[(int(a), int(b))]] = cc
+        acc += cn
+        acc2 += cn * cn
+    mean = acc / nseeds
+    var = np.maximum(acc2 / nseeds - mean ** 2, 1e-300)
+    se = np.sqrt(var / nseeds)
+    exp = _expected_step(s, dets, c, tau, S, n_a, Hrel)
+    z = (mean - exp) / np.where(se > 0, se, 1.0)
+    det_comp = se == 0
+    # components with no randomness must be exact
+    np.testing.assert_allclose(mean[det_comp], exp[det_comp], rtol=1e-12, atol=1e-12)
+    zz = z[~det_comp]
+    assert np.max(np.abs(zz)) < 5.0, (np.argmax(np.abs(zz)), np.max(np.abs(zz)))
+    chi2 = float(np.sum(zz ** 2))
+    assert chi2 < zz.size + 5 * math.sqrt(2 * zz.size), (chi2, zz.size)
+
+
+# ----------------------------------------------------------------- semi-stochastic limit
+def test_semistochastic_whole_space_is_power_method():
+    """With D = the whole Hilbert space nothing is sampled: the iteration is the
+    deterministic power method with 1 - dtau (H - S), whose projected energy
+    converges to the exact E_0 (Sec. III)."""
+    s = oracle.system_from_workload(workloads.hubbard_1d(4, 1.0, 4.0))
+    e0, v, dets = s.exact_ground_state()
+    r = oracle.Run(s, tau=0.05, seed=3, target_walkers=1e12, semistoch_size=len(dets), semistoch_start=1)
+    c = np.full(len(dets), 7.0)
+    r.import_state([d[0] for d in dets], [d[1] for d in dets], c, 1, e0, vary=1, shift_start=0, cnt=0,
+                   nw_last=int(7.0 * len(dets)) << 32)
+    r.step(1500)
+    assert r.semistoch_info()[0] == len(dets)
+    num, den = r.proj_energy()
+    assert abs(num / den - e0) < 1e-9
+
+
+# ----------------------------------------------------------------- full runs
+@pytest.mark.parametrize("which", ["hubbard", "abinitio"])
+def test_fciqmc_energy_within_3sigma_of_exact(which):
+    if which == "hubbard":
+        sysd, tau = workloads.hubbard_1d(6, 1.0, 4.0), 0.02
+    else:
+        sysd, tau = workloads.small_abinitio(6, 3, 3, seed=9), 0.005
+    s = oracle.system_from_workload(sysd)
+    e0, _, dets = s.exact_ground_state()
+    # start the shift a little above E_0 so that the growth phase is short
+    r = oracle.Run(s, tau=tau, seed=12, target_walkers=2000, initiator_threshold=0.0, initial_walkers=200.0,
+                   initial_shift=e0 + 0.3)
+    r.step(3000)
+    st = r.stats()
+    start = int(np.argmax(st["vary"] > 0)) + 300
+    num, den = st["e_num"][start:], st["e_den"][start:]
+    e, sig = oracle.ratio_estimate(num, den)
+    assert sig > 0
+    assert abs(e - e0) < 3.0 * sig + 1e-9, (e, e0, sig)
+    ms, ss, _ = oracle.blocking(st["S"][start:])
+    assert abs(ms - e0) < 5.0 * ss + 0.05 * abs(e0) + 0.05
+    ex = r.export()
+    for a, b in zip(ex["alpha"], ex["beta"]):
+        assert bin(int(a)).count("1") == s.na and bin(int(b)).count("1") == s.nb
+
+
+def test_run_is_deterministic_and_keyed():
+    sysd, prm = workloads.config_hubbard_ring()
+    s = oracle.system_from_workload(sysd)
+    r1 = oracle.Run(s, **dict(prm, target_walkers=500))
+    r2 = oracle.Run(s, **dict(prm, target_walkers=500))
+    r1.step(150)
+    r2.step(150)
+    e1, e2 = r1.export(), r2.export()
+    for k in e1:
+        np.testing.assert_array_equal(e1[k], e2[k])
+    r3 = oracle.Run(s, **dict(prm, target_walkers=500, seed=2))
+    r3.step(150)
+    assert not np.array_equal(r3.export()["c"], e1["c"]) or len(r3.export()["c"]) != len(e1["c"])
