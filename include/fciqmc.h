@@ -1,0 +1,232 @@
+/*
+ * fciqmc.h -- C ABI of the GB300 initiator-FCIQMC library.
+ *
+ * One handle = one FCIQMC run: a sparse walker list of Slater determinants
+ * (two uint64 occupation words, alpha and beta) with signed binary64
+ * amplitudes, resident in device memory, advanced by the projector
+ * psi(t + dt) = (1 - dt (H - S)) psi(t) of Eq. (1) of Guther et al.,
+ * J. Chem. Phys. 153, 034107 (2020) (arXiv:2006.14956), in the three steps
+ * of its Eq. (3): spawning, death, annihilation, with the initiator rule of
+ * Sec. I, stochastic rounding at C_min (Eq. (2)), the shift update and the
+ * reference projected energy of Eq. (8).  Deterministic (semi-stochastic)
+ * projection inside the space D of Sec. III is optional.
+ *
+ * Conventions used throughout:
+ *  - Determinant: alpha word bit p set <=> spatial orbital p occupied by an
+ *    alpha electron; same for beta.  Canonical operator order is alpha_0 ..
+ *    alpha_{N-1}, beta_0 .. beta_{N-1}; all fermionic signs follow from it.
+ *  - Integrals: chemist notation (pq|rs), 8-fold packed as in FCIDUMP files:
+ *    pair(p,q) = max(p,q)(max(p,q)+1)/2 + min(p,q), and
+ *    eri[pair(pair(p,q), pair(r,s))] = (pq|rs).
+ *  - Random numbers: Philox4x64-10 keyed by (seed, 0) with the counter
+ *    (alpha, beta, iteration, (slot << 8) | purpose); every random decision
+ *    is a function of the determinant, the iteration and the attempt only,
+ *    so results do not depend on list order, batching or launch geometry.
+ *  - Buffers passed in are HOST pointers unless stated otherwise; they are
+ *    copied, and the caller keeps ownership.  The handle owns all device
+ *    memory it allocates.
+ *  - No function throws; every error is reported by its return code, with a
+ *    message available from fciqmc_last_error().
+ *  - Thread safety: a handle may be used by one host thread at a time.
+ */
+#ifndef FCIQMC_GB300_H
+#define FCIQMC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+enum {
+    FCIQMC_OK = 0,
+    FCIQMC_ERR_INVALID_ARG = 1,   /* bad argument; nothing changed */
+    FCIQMC_ERR_OUT_OF_MEMORY = 2, /* device or host allocation failed */
+    FCIQMC_ERR_CAPACITY = 3,      /* a fixed-capacity buffer overflowed; the state is unchanged */
+    FCIQMC_ERR_NUMERIC = 4,       /* NaN/Inf or a population beyond the representable range */
+    FCIQMC_ERR_TIMEOUT = 5,       /* a bounded device-side wait expired */
+    FCIQMC_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+    FCIQMC_ERR_UNSUPPORTED = 7    /* valid request outside what this build supports */
+};
+
+enum { FCIQMC_ABINITIO = 0, FCIQMC_HUBBARD = 1 };
+
+/* The Hamiltonian (Sec. I; Eq. (3)).  For FCIQMC_ABINITIO, h1 and eri are
+ * host arrays of binary64 (norb*norb row-major, and the packed 8-fold ERI).
+ * For FCIQMC_HUBBARD the library builds h_pq = -t on lattice bonds and
+ * (pp|pp) = U itself from lx, ly and the periodic flags; sites are numbered
+ * x + lx*y.  A periodic direction must have length 1 or >= 3.
+ * ref: the reference determinant of Eq. (8); when has_ref is 0 it is the
+ * aufbau determinant (ABINITIO) or the Neel determinant, alpha on sites with
+ * even x+y (HUBBARD). */
+typedef struct {
+    int32_t kind;
+    int32_t norb;      /* spatial orbitals (ABINITIO), <= 64 */
+    int32_t n_alpha;
+    int32_t n_beta;
+    double ecore;
+    const double *h1;  /* ABINITIO: norb*norb */
+    const double *eri; /* ABINITIO: packed (npair*(npair+1)/2), npair = norb(norb+1)/2 */
+    int32_t lx, ly;    /* HUBBARD lattice, lx*ly <= 64 */
+    int32_t periodic_x, periodic_y;
+    double t, U;
+    int32_t has_ref;
+    int32_t pad0;
+    uint64_t ref_alpha, ref_beta;
+} fciqmc_system;
+
+/* Run parameters.  tau: time step (Eq. (1)).  Shift (Eq. (1)): S starts at
+ * initial_shift and stays there until the walker number N_w first reaches
+ * target_walkers; from then on, every shift_interval (A) iterations,
+ * S <- S - shift_damping / (A tau) * ln(N_w(t) / N_w(t - A)).
+ * initiator_threshold n_a: a determinant is an initiator when |C| > n_a (or
+ * it is the reference, or it lies in D); 0 gives plain FCIQMC.  c_min:
+ * rounding threshold of Eq. (2).  p_single: probability of proposing a single
+ * excitation (App. A).  semistoch_size: N_D of Sec. III (0 = off), chosen
+ * semistoch_start iterations after the shift starts to vary.
+ * max_dets / max_spawns: capacity hints (0 = derived from target_walkers);
+ * capacities grow automatically when exceeded.  stream: a cudaStream_t
+ * (NULL = the library creates its own).  alloc/free: optional device
+ * allocator (for example a framework's caching allocator); NULL = cudaMalloc. */
+typedef struct {
+    double tau;
+    double shift_damping;
+    double target_walkers;
+    double initial_walkers;
+    double initial_shift;
+    double initiator_threshold;
+    double c_min;
+    double p_single;
+    int64_t shift_interval;
+    uint64_t seed;
+    int64_t semistoch_size;
+    int64_t semistoch_start;
+    int64_t max_dets;
+    int64_t max_spawns;
+    void *stream;
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, void *ctx);
+    void *alloc_ctx;
+} fciqmc_params;
+
+/* One row per completed iteration.  nw: walker number N_w = 2^-32 sum
+ * floor(|C| 2^32).  shift: S after the iteration (relative to E_ref).
+ * e_num = sum_{j != ref} H_ref,j C_j and e_den = C_ref after the iteration
+ * (Eq. (8)); attempts = sum ceil(|C|); spawns = spawned walkers stored;
+ * rejected = spawns removed by the initiator rule; annihilated = walkers
+ * removed by summing opposite-sign contributions. */
+typedef struct {
+    int64_t iteration;
+    double nw;
+    double shift;
+    double e_num;
+    double e_den;
+    int64_t ndet;
+    int64_t attempts;
+    int64_t spawns;
+    int64_t rejected;
+    double annihilated;
+    int32_t vary;
+    int32_t pad0;
+} fciqmc_iter_stats;
+
+/* Summary returned by fciqmc_energy.  Energies are absolute (E_ref added).
+ * e_proj_mean / e_proj_sigma: ratio of the means of e_num and e_den over
+ * iterations from equil_start on, with a Flyvbjerg-Petersen blocking error;
+ * equil_start = the iteration at which the shift started to vary + 500. */
+typedef struct {
+    int64_t iteration;
+    int64_t ndet;
+    double nw;
+    double eref;
+    double shift;
+    double e_proj_inst;
+    double e_proj_mean;
+    double e_proj_sigma;
+    double shift_mean;
+    double shift_sigma;
+    int64_t equil_start;
+    int64_t n_samples;
+    int64_t attempts_total;
+    int64_t spawns_total;
+    int64_t rejected_total;
+    double annihilated_total;
+    int32_t vary;
+    int32_t pad0;
+} fciqmc_stats;
+
+typedef struct fciqmc_handle fciqmc_handle;
+
+/* Creates a run: validates and copies the system, uploads the integrals,
+ * places initial_walkers on the reference determinant, sizes the bucketed
+ * walker and spawn buffers, and captures one iteration as a CUDA graph.
+ * Returns FCIQMC_OK and *out, or an error code (then *out is NULL). */
+int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *params, fciqmc_handle **out);
+
+/* Runs n_iter projector iterations on the handle's stream and synchronises
+ * once at the end.  On FCIQMC_ERR_CAPACITY the library grows the buffers and
+ * repeats the failed iteration, which is bit-identical because every random
+ * draw is keyed; other errors stop the run at the last good iteration. */
+int fciqmc_step(fciqmc_handle *h, int64_t n_iter);
+
+/* Fills *out from the iteration history (host-side statistics). */
+int fciqmc_energy(fciqmc_handle *h, fciqmc_stats *out);
+
+/* Frees all resources; NULL is allowed. */
+void fciqmc_destroy(fciqmc_handle *h);
+
+/* Message of the last error on this handle (or of the last failed create
+ * when h is NULL). */
+const char *fciqmc_last_error(const fciqmc_handle *h);
+
+/* Number of occupied determinants after the last completed iteration. */
+int64_t fciqmc_num_dets(fciqmc_handle *h);
+
+/* Copies the walker list to host arrays of capacity cap, sorted by (alpha,
+ * beta) ascending; hdiag = H_ii - E_ref; flags bit 0 = reference, bit 1 =
+ * in D.  *n_out receives the number of determinants (also when it exceeds
+ * cap, in which case FCIQMC_ERR_CAPACITY is returned and nothing copied). */
+int fciqmc_export_state(fciqmc_handle *h, int64_t cap, uint64_t *alpha, uint64_t *beta, double *c,
+                        double *hdiag, int32_t *flags, int64_t *n_out);
+
+/* Shift state: S, vary flag, iteration at which it started, iterations since
+ * the last update, and N_w at the last update as a 128-bit fixed-point
+ * integer (N_w * 2^32, high and low words). */
+int fciqmc_export_shift(fciqmc_handle *h, int64_t *iteration, double *S, int32_t *vary,
+                        int64_t *shift_start, int64_t *cnt, uint64_t *nw_last_hi, uint64_t *nw_last_lo);
+
+/* Replaces the walker list and the shift state (a restart from a checkpoint).
+ * Keys must be distinct, with the right electron counts; the reference
+ * determinant is kept (added with C = 0 when absent). */
+int fciqmc_import_state(fciqmc_handle *h, int64_t n, const uint64_t *alpha, const uint64_t *beta,
+                        const double *c, int64_t iteration, double S, int32_t vary, int64_t shift_start,
+                        int64_t cnt, uint64_t nw_last_hi, uint64_t nw_last_lo);
+
+/* Copies rows first .. first+count-1 of the per-iteration history. */
+int fciqmc_iter_stats_get(fciqmc_handle *h, int64_t first, int64_t count, fciqmc_iter_stats *out);
+int64_t fciqmc_iter_stats_count(fciqmc_handle *h);
+
+/* Advances k independent handles by n_iter iterations each, sharing every
+ * launch: one graph-captured iteration processes the buckets of all k runs.
+ * Each run's results are bit-identical to running it alone.  All handles
+ * must be distinct; they are synchronised on the first handle's stream. */
+int fciqmc_step_batch(fciqmc_handle **hs, int32_t k, int64_t n_iter);
+
+/* Device timing of the kernels of the last fciqmc_step call (milliseconds per
+ * iteration, averaged), measured with CUDA events on the handle's stream:
+ * out[0] spawn, out[1] heavy-determinant spawn, out[2] annihilation,
+ * out[3] finalize, out[4] semi-stochastic.  Enabled by fciqmc_set_profiling. */
+int fciqmc_set_profiling(fciqmc_handle *h, int32_t on);
+int fciqmc_kernel_times(fciqmc_handle *h, double out[5]);
+
+/* Internal layout figures used to compute algorithmic bytes and to size
+ * buffers: out[0] buckets, out[1] main capacity per bucket, out[2] spawn
+ * capacity per bucket, out[3] device bytes allocated. */
+int fciqmc_layout(fciqmc_handle *h, int64_t out[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,899 @@
+// capi.cu -- host side of the C ABI in include/fciqmc.h.
+//
+// Owns the device memory of each run, prepares the integrals (including the
+// fixed-point tables used for exact diagonal sums), sizes the bucketed
+// buffers, captures one projector iteration as a CUDA graph, replays it, and
+// grows the buffers when a capacity flag comes back.  Statistics (blocking
+// analysis of the projected energy) are computed here on the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fq_internal.h"
+
+using namespace fq;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct fciqmc_handle {
+    // system (host copies)
+    int kind = 0, norb = 0, na = 0, nb = 0;
+    double ecore = 0.0;
+    std::vector<double> h, eri;
+    std::vector<int> nbr;
+    int z = 0;
+    double t = 0.0, U = 0.0;
+    u64 ref_a = 0, ref_b = 0;
+    double eref = 0.0;
+    fciqmc_params p{};
+    // device
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<DevBuf> bufs;
+    size_t bytes = 0;
+    DevInst hi{};                 // host image of the device descriptor
+    DevInst *dinst = nullptr;     // device copy
+    int *dunit = nullptr;         // unit_start {0, nb}
+    IterState *dstate = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    bool profiling = false;
+    double ktime[5] = {0, 0, 0, 0, 0};
+    // layout
+    int bb = 0;
+    int heavy_cap = 0;
+    int ring_cap = 4096;
+    // host-side history
+    std::vector<fciqmc_iter_stats> hist;
+    IterState hst{};
+    std::string err;
+    // semi-stochastic space
+    int nd = 0;
+    long long nnz = 0;
+};
+
+// ------------------------------------------------------------------ helpers
+static int fail(fciqmc_handle *h, int code, const std::string &msg)
+{
+    if (h) h->err = msg; else g_create_error = msg;
+    return code;
+}
+
+#define CUDA_TRY(h, call)                                                                         \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return fail(h, e_ == cudaErrorMemoryAllocation ? FCIQMC_ERR_OUT_OF_MEMORY \
+                                              : FCIQMC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static void *dev_alloc(fciqmc_handle *h, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *ptr = nullptr;
+    if (h->p.alloc) ptr = h->p.alloc(bytes, h->p.alloc_ctx);
+    else if (cudaMalloc(&ptr, bytes) != cudaSuccess) ptr = nullptr;
+    if (ptr) {
+        h->bufs.push_back({ptr, bytes});
+        h->bytes += bytes;
+    }
+    return ptr;
+}
+
+static void dev_free(fciqmc_handle *h, void *ptr)
+{
+    if (!ptr) return;
+    for (size_t i = 0; i < h->bufs.size(); i++)
+        if (h->bufs[i].p == ptr) {
+            h->bytes -= h->bufs[i].bytes;
+            h->bufs.erase(h->bufs.begin() + i);
+            break;
+        }
+    if (h->p.free) h->p.free(ptr, h->p.alloc_ctx);
+    else cudaFree(ptr);
+}
+
+static int64_t pair_index(int64_t i, int64_t j) { return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i; }
+
+// binary64 -> (mantissa, exponent) with x = m 2^e, m odd (or 0)
+static void decompose(double x, u64 *m, int *e)
+{
+    u64 bits;
+    memcpy(&bits, &x, 8);
+    int ex = (int)((bits >> 52) & 0x7ff);
+    u64 mm = bits & 0xFFFFFFFFFFFFFULL;
+    int ee;
+    if (ex == 0) ee = -1074; else { mm |= 1ULL << 52; ee = ex - 1075; }
+    if (mm == 0) { *m = 0; *e = 0; return; }
+    while (!(mm & 1ULL)) { mm >>= 1; ee++; }
+    *m = mm;
+    *e = ee;
+}
+
+// exact placement of x on the grid 2^-F (caller guarantees it fits)
+static i128 host_fixed(double x, int F)
+{
+    u64 m;
+    int e;
+    decompose(x, &m, &e);
+    if (m == 0) return 0;
+    int sh = e + F;
+    u128 v = sh >= 0 ? ((u128)m << sh) : (u128)(m >> (-sh));
+    return std::signbit(x) ? -(i128)v : (i128)v;
+}
+
+// nearest binary64 to v 2^-F, ties to even
+static double host_fixed_to_double(i128 v, int F)
+{
+    if (v == 0) return 0.0;
+    bool neg = v < 0;
+    u128 u = neg ? (u128)(-v) : (u128)v;
+    int msb = 127;
+    while (!((u >> msb) & 1)) msb--;
+    u64 mant;
+    int e2;
+    if (msb <= 52) { mant = (u64)u; e2 = 0; }
+    else {
+        int sh = msb - 52;
+        u128 q = u >> sh;
+        mant = (u64)q;
+        u128 rem = u - (q << sh), half = (u128)1 << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1))) mant++;
+        e2 = sh;
+    }
+    double r = std::ldexp((double)mant, e2 - F);
+    return neg ? -r : r;
+}
+
+static int exponent_of(double x)
+{
+    int e;
+    std::frexp(x, &e);
+    return e - 1;  // x in [2^e, 2^(e+1))
+}
+
+// generation probability of class c (App. A uniform generator, spin-conditioned)
+static double pgen_class(const fciqmc_handle *h, int c)
+{
+    int n = h->na + h->nb, N = h->norb;
+    int64_t ma = N - h->na, mb = N - h->nb, nn = (int64_t)n * (n - 1);
+    double ps = h->p.p_single;
+    switch (c) {
+    case CLS_SINGLE_A: return ps / ((double)n * (double)ma);
+    case CLS_SINGLE_B: return ps / ((double)n * (double)mb);
+    case CLS_DOUBLE_AB: return ((1.0 - ps) * 2.0) / ((double)nn * (double)(ma * mb));
+    case CLS_DOUBLE_AA: return ((1.0 - ps) * 4.0) / ((double)nn * (double)(ma * (ma - 1)));
+    case CLS_DOUBLE_BB: return ((1.0 - ps) * 4.0) / ((double)nn * (double)(mb * (mb - 1)));
+    case CLS_HOP: return 1.0 / ((double)n * (double)h->z);
+    }
+    return 0.0;
+}
+
+// ------------------------------------------------------------------ layout
+static int alloc_layout(fciqmc_handle *h, DevInst &I, int bb)
+{
+    const size_t nbk = (size_t)1 << bb;
+    const size_t nm = nbk * CAP_M, ns = nbk * CAP_S;
+    for (int k = 0; k < 2; k++) {
+        I.key[k] = (ulonglong2 *)dev_alloc(h, nm * sizeof(ulonglong2));
+        I.c[k] = (double *)dev_alloc(h, nm * sizeof(double));
+        I.hd[k] = (double *)dev_alloc(h, nm * sizeof(double));
+        I.fl[k] = (uint8_t *)dev_alloc(h, nm);
+        I.cnt[k] = (int *)dev_alloc(h, nbk * sizeof(int));
+        if (!I.key[k] || !I.c[k] || !I.hd[k] || !I.fl[k] || !I.cnt[k]) return FCIQMC_ERR_OUT_OF_MEMORY;
+        if (cudaMemsetAsync(I.cnt[k], 0, nbk * sizeof(int), h->stream) != cudaSuccess) return FCIQMC_ERR_CUDA;
+    }
+    I.skey = (ulonglong2 *)dev_alloc(h, ns * sizeof(ulonglong2));
+    I.sw = (double *)dev_alloc(h, ns * sizeof(double));
+    I.scnt_i = (int *)dev_alloc(h, nbk * sizeof(int));
+    I.scnt_n = (int *)dev_alloc(h, nbk * sizeof(int));
+    I.part = (Partial *)dev_alloc(h, nbk * sizeof(Partial));
+    if (!I.skey || !I.sw || !I.scnt_i || !I.scnt_n || !I.part) return FCIQMC_ERR_OUT_OF_MEMORY;
+    cudaMemsetAsync(I.scnt_i, 0, nbk * sizeof(int), h->stream);
+    cudaMemsetAsync(I.scnt_n, 0, nbk * sizeof(int), h->stream);
+    cudaMemsetAsync(I.part, 0, nbk * sizeof(Partial), h->stream);
+    I.bb = bb;
+    I.unit0 = 0;
+    return FCIQMC_OK;
+}
+
+static void free_layout(fciqmc_handle *h, DevInst &I)
+{
+    for (int k = 0; k < 2; k++) {
+        dev_free(h, I.key[k]); dev_free(h, I.c[k]); dev_free(h, I.hd[k]); dev_free(h, I.fl[k]); dev_free(h, I.cnt[k]);
+        I.key[k] = nullptr; I.c[k] = nullptr; I.hd[k] = nullptr; I.fl[k] = nullptr; I.cnt[k] = nullptr;
+    }
+    dev_free(h, I.skey); dev_free(h, I.sw); dev_free(h, I.scnt_i); dev_free(h, I.scnt_n); dev_free(h, I.part);
+    I.skey = nullptr; I.sw = nullptr; I.scnt_i = nullptr; I.scnt_n = nullptr; I.part = nullptr;
+}
+
+static int upload_inst(fciqmc_handle *h)
+{
+    CUDA_TRY(h, cudaMemcpyAsync(h->dinst, &h->hi, sizeof(DevInst), cudaMemcpyHostToDevice, h->stream));
+    int us[2] = {0, 1 << h->bb};
+    CUDA_TRY(h, cudaMemcpyAsync(h->dunit, us, sizeof(us), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return FCIQMC_OK;
+}
+
+static int enqueue_iteration(fciqmc_handle *h, cudaEvent_t *ev)
+{
+    const int units = 1 << h->bb;
+    if (ev) cudaEventRecord(ev[0], h->stream);
+    launch_spawn(h->dinst, h->dunit, 1, units, h->stream);
+    if (ev) cudaEventRecord(ev[1], h->stream);
+    launch_spawn_heavy(h->dinst, 1, h->stream);
+    if (ev) cudaEventRecord(ev[2], h->stream);
+    if (h->nd > 0) launch_semistoch(h->dinst, 1, h->nd, h->stream);
+    if (ev) cudaEventRecord(ev[3], h->stream);
+    cudaError_t e = launch_annihilate(h->dinst, h->dunit, 1, units, h->stream);
+    if (e != cudaSuccess) return fail(h, FCIQMC_ERR_CUDA, std::string("annihilation launch: ") + cudaGetErrorString(e));
+    if (ev) cudaEventRecord(ev[4], h->stream);
+    launch_finalize(h->dinst, 1, h->stream);
+    if (ev) cudaEventRecord(ev[5], h->stream);
+    return FCIQMC_OK;
+}
+
+static int capture_graph(fciqmc_handle *h)
+{
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    cudaGraph_t g;
+    CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_iteration(h, nullptr);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(h, FCIQMC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(h, FCIQMC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return FCIQMC_OK;
+}
+
+static int read_state(fciqmc_handle *h)
+{
+    CUDA_TRY(h, cudaMemcpyAsync(&h->hst, h->dstate, sizeof(IterState), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return FCIQMC_OK;
+}
+
+static int write_state(fciqmc_handle *h)
+{
+    CUDA_TRY(h, cudaMemcpyAsync(h->dstate, &h->hst, sizeof(IterState), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return FCIQMC_OK;
+}
+
+// split every bucket in two (one more hash bit)
+static int grow_buckets(fciqmc_handle *h)
+{
+    if (h->bb >= 24) return fail(h, FCIQMC_ERR_CAPACITY, "walker list exceeds 2^24 buckets");
+    DevInst nI = h->hi;
+    int rc = alloc_layout(h, nI, h->bb + 1);
+    if (rc) return fail(h, rc, "out of device memory while growing the walker buffers");
+    DevInst *tmp = (DevInst *)dev_alloc(h, 2 * sizeof(DevInst));
+    if (!tmp) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory");
+    CUDA_TRY(h, cudaMemcpyAsync(tmp, &h->hi, sizeof(DevInst), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(tmp + 1, &nI, sizeof(DevInst), cudaMemcpyHostToDevice, h->stream));
+    const int par = h->hst.parity;
+    launch_rebucket(tmp, tmp + 1, 1 << h->bb, par, h->stream);
+    CUDA_TRY(h, cudaGetLastError());
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    int rc2 = read_state(h);
+    if (rc2) return rc2;
+    dev_free(h, tmp);
+    free_layout(h, h->hi);
+    h->hi = nI;
+    h->bb = nI.bb;
+    if (h->hst.err & ERRB_MAIN_CAP) return fail(h, FCIQMC_ERR_CAPACITY, "bucket overflow while splitting");
+    return FCIQMC_OK;
+}
+
+static int grow_heavy(fciqmc_handle *h)
+{
+    int ncap = h->heavy_cap * 4;
+    HeavyChunk *nh = (HeavyChunk *)dev_alloc(h, (size_t)ncap * sizeof(HeavyChunk));
+    if (!nh) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (heavy queue)");
+    dev_free(h, h->hi.heavy);
+    h->hi.heavy = nh;
+    h->hi.heavy_cap = ncap;
+    h->heavy_cap = ncap;
+    return FCIQMC_OK;
+}
+
+static int reset_after_error(fciqmc_handle *h)
+{
+    const size_t nbk = (size_t)1 << h->bb;
+    CUDA_TRY(h, cudaMemsetAsync(h->hi.scnt_i, 0, nbk * sizeof(int), h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(h->hi.scnt_n, 0, nbk * sizeof(int), h->stream));
+    h->hst.err = 0;
+    h->hst.heavy_n = 0;
+    return write_state(h);
+}
+
+static int pull_history(fciqmc_handle *h, long long from, long long to)
+{
+    if (to <= from) return FCIQMC_OK;
+    std::vector<fciqmc_iter_stats> rows((size_t)(to - from));
+    for (long long it = from; it < to;) {
+        long long slot = it % h->ring_cap;
+        long long n = std::min<long long>(to - it, h->ring_cap - slot);
+        CUDA_TRY(h, cudaMemcpyAsync(rows.data() + (it - from), h->hi.ring + slot, n * sizeof(fciqmc_iter_stats),
+                                    cudaMemcpyDeviceToHost, h->stream));
+        it += n;
+    }
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    // the history is indexed by iteration; a retried iteration overwrites
+    if ((long long)h->hist.size() > from) h->hist.resize((size_t)from);
+    h->hist.insert(h->hist.end(), rows.begin(), rows.end());
+    return FCIQMC_OK;
+}
+
+int build_semistochastic(fciqmc_handle *h);  // semistoch.cu
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char *fciqmc_last_error(const fciqmc_handle *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void fciqmc_destroy(fciqmc_handle *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    while (!h->bufs.empty()) dev_free(h, h->bufs.back().p);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_handle **out)
+{
+    if (!out) return fail(nullptr, FCIQMC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!sys || !prm) return fail(nullptr, FCIQMC_ERR_INVALID_ARG, "system or params is NULL");
+    fciqmc_handle *h = new fciqmc_handle();
+    h->p = *prm;
+    auto bail = [&](int rc, const std::string &msg) {
+        g_create_error = msg;
+        fciqmc_destroy(h);
+        return rc;
+    };
+    const fciqmc_params &P = h->p;
+    if (!(P.tau > 0.0) || !(P.c_min > 0.0) || !(P.initial_walkers > 0.0) || P.shift_interval < 1 ||
+        !(P.p_single >= 0.0 && P.p_single <= 1.0) || !(P.initiator_threshold >= 0.0) || !(P.shift_damping >= 0.0) ||
+        !(P.target_walkers > 0.0) || !std::isfinite(P.initial_shift))
+        return bail(FCIQMC_ERR_INVALID_ARG, "invalid parameters (tau, c_min, initial_walkers, shift_interval, p_single, "
+                                            "initiator_threshold, shift_damping, target_walkers must be positive/finite)");
+    h->kind = sys->kind;
+    h->na = sys->n_alpha;
+    h->nb = sys->n_beta;
+    h->ecore = sys->ecore;
+    int N;
+    if (sys->kind == FCIQMC_ABINITIO) {
+        N = sys->norb;
+        if (N < 1 || N > 64 || !sys->h1 || !sys->eri) return bail(FCIQMC_ERR_INVALID_ARG, "ab initio system needs 1 <= norb <= 64, h1 and eri");
+        int64_t np = (int64_t)N * (N + 1) / 2, ne = np * (np + 1) / 2;
+        h->h.assign(sys->h1, sys->h1 + (size_t)N * N);
+        h->eri.assign(sys->eri, sys->eri + ne);
+    } else if (sys->kind == FCIQMC_HUBBARD) {
+        int lx = sys->lx, ly = sys->ly;
+        N = lx * ly;
+        if (lx < 1 || ly < 1 || N > 64 || (sys->periodic_x && lx == 2) || (sys->periodic_y && ly == 2))
+            return bail(FCIQMC_ERR_INVALID_ARG, "Hubbard lattice needs lx*ly <= 64 and periodic lengths of 1 or >= 3");
+        h->z = ly > 1 ? 4 : 2;
+        h->t = sys->t;
+        h->U = sys->U;
+        h->nbr.assign((size_t)4 * N, -1);
+        for (int y = 0; y < ly; y++)
+            for (int x = 0; x < lx; x++) {
+                int p = x + lx * y;
+                int *q = &h->nbr[4 * p];
+                q[0] = x > 0 ? p - 1 : (sys->periodic_x && lx > 1 ? p + lx - 1 : -1);
+                q[1] = x < lx - 1 ? p + 1 : (sys->periodic_x && lx > 1 ? p - (lx - 1) : -1);
+                q[2] = y > 0 ? p - lx : (sys->periodic_y && ly > 1 ? p + lx * (ly - 1) : -1);
+                q[3] = y < ly - 1 ? p + lx : (sys->periodic_y && ly > 1 ? p - lx * (ly - 1) : -1);
+            }
+        int64_t np = (int64_t)N * (N + 1) / 2, ne = np * (np + 1) / 2;
+        h->h.assign((size_t)N * N, 0.0);
+        h->eri.assign((size_t)ne, 0.0);
+        for (int p = 0; p < N; p++)
+            for (int k = 0; k < h->z; k++)
+                if (h->nbr[4 * p + k] >= 0) h->h[(size_t)p * N + h->nbr[4 * p + k]] = -sys->t;
+        for (int p = 0; p < N; p++) h->eri[pair_index(pair_index(p, p), pair_index(p, p))] = sys->U;
+    } else {
+        return bail(FCIQMC_ERR_INVALID_ARG, "unknown system kind");
+    }
+    h->norb = N;
+    if (h->na < 0 || h->nb < 0 || h->na > N || h->nb > N || h->na + h->nb < 1)
+        return bail(FCIQMC_ERR_INVALID_ARG, "electron counts out of range");
+    const u64 normask = N >= 64 ? ~0ULL : ((1ULL << N) - 1);
+    if (sys->has_ref) {
+        h->ref_a = sys->ref_alpha;
+        h->ref_b = sys->ref_beta;
+    } else if (sys->kind == FCIQMC_ABINITIO) {
+        h->ref_a = h->na >= 64 ? ~0ULL : ((1ULL << h->na) - 1);
+        h->ref_b = h->nb >= 64 ? ~0ULL : ((1ULL << h->nb) - 1);
+    } else {
+        for (int y = 0; y < sys->ly; y++)
+            for (int x = 0; x < sys->lx; x++) {
+                if (((x + y) & 1) == 0) h->ref_a |= 1ULL << (x + sys->lx * y);
+                else h->ref_b |= 1ULL << (x + sys->lx * y);
+            }
+    }
+    if (__builtin_popcountll(h->ref_a) != h->na || __builtin_popcountll(h->ref_b) != h->nb ||
+        ((h->ref_a | h->ref_b) & ~normask))
+        return bail(FCIQMC_ERR_INVALID_ARG, "reference determinant does not match the electron counts");
+
+    // exact-sum scale F: every integral (and E_core) must lie on the grid 2^-F
+    int lsb_min = 0, msb_max = -1100;
+    bool any = false;
+    auto scan = [&](double x) {
+        if (x == 0.0) return true;
+        if (!std::isfinite(x)) return false;
+        u64 m;
+        int e;
+        decompose(x, &m, &e);
+        lsb_min = any ? std::min(lsb_min, e) : e;
+        msb_max = any ? std::max(msb_max, exponent_of(std::fabs(x))) : exponent_of(std::fabs(x));
+        any = true;
+        return true;
+    };
+    for (double x : h->h) if (!scan(x)) return bail(FCIQMC_ERR_INVALID_ARG, "non-finite one-electron integral");
+    for (double x : h->eri) if (!scan(x)) return bail(FCIQMC_ERR_INVALID_ARG, "non-finite two-electron integral");
+    if (!scan(h->ecore)) return bail(FCIQMC_ERR_INVALID_ARG, "non-finite core energy");
+    const int n = h->na + h->nb;
+    const int F = any ? std::max(0, -lsb_min) : 0;
+    int terms_bits = 0;
+    while ((1LL << terms_bits) < (long long)n * n + 2 * n + 4) terms_bits++;
+    if (any && msb_max + F + terms_bits + 2 > 125)
+        return bail(FCIQMC_ERR_UNSUPPORTED, "integral dynamic range too wide for the 128-bit exact accumulator");
+    const int ecm = exponent_of(P.c_min);
+    const int Fw = 52 - ecm;
+    if (Fw + 31 + 14 > 125 || Fw + 31 < 0)
+        return bail(FCIQMC_ERR_UNSUPPORTED, "c_min outside the supported range (about 1e-9 .. 1e9)");
+
+    // device, stream
+    if (P.stream) h->stream = (cudaStream_t)P.stream;
+    else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(FCIQMC_ERR_CUDA, "cannot create a CUDA stream (no usable GPU?)");
+        h->own_stream = true;
+    }
+
+    // fixed-point tables for the exact diagonal sums
+    std::vector<ulonglong2> hfx(N), Jfx((size_t)N * N), Kfx((size_t)N * N);
+    auto put = [](ulonglong2 &d, i128 v) { d.x = (u64)(u128)v; d.y = (u64)((u128)v >> 64); };
+    for (int p = 0; p < N; p++) {
+        put(hfx[p], host_fixed(h->h[(size_t)p * N + p], F));
+        for (int q = 0; q < N; q++) {
+            put(Jfx[(size_t)p * N + q], host_fixed(h->eri[pair_index(pair_index(p, p), pair_index(q, q))], F));
+            put(Kfx[(size_t)p * N + q], host_fixed(h->eri[pair_index(pair_index(p, q), pair_index(q, p))], F));
+        }
+    }
+    // X(ref): sum over occupied orbitals and occupied pairs
+    std::vector<std::pair<int, int>> occ;
+    for (int p = 0; p < N; p++) if ((h->ref_a >> p) & 1) occ.push_back({p, 0});
+    for (int p = 0; p < N; p++) if ((h->ref_b >> p) & 1) occ.push_back({p, 1});
+    i128 xref = 0;
+    for (size_t i = 0; i < occ.size(); i++) {
+        xref += host_fixed(h->h[(size_t)occ[i].first * N + occ[i].first], F);
+        for (size_t j = i + 1; j < occ.size(); j++) {
+            int p = occ[i].first, q = occ[j].first;
+            xref += host_fixed(h->eri[pair_index(pair_index(p, p), pair_index(q, q))], F);
+            if (occ[i].second == occ[j].second) xref -= host_fixed(h->eri[pair_index(pair_index(p, q), pair_index(q, p))], F);
+        }
+    }
+    h->eref = host_fixed_to_double(xref + host_fixed(h->ecore, F), F);
+
+    DevInst &I = h->hi;
+    I.kind = h->kind; I.norb = N; I.na = h->na; I.nb = h->nb; I.n = n; I.ma = N - h->na; I.mb = N - h->nb; I.z = h->z;
+    I.F = F; I.Fw = Fw;
+    I.ref_a = h->ref_a; I.ref_b = h->ref_b; I.normask = normask;
+    I.xref_lo = (u64)(u128)xref; I.xref_hi = (u64)((u128)xref >> 64);
+    for (int c = 0; c < NCLS; c++) I.lam[c] = P.tau / pgen_class(h, c);
+    I.tmt = -h->t;
+    {
+        double q = P.p_single * 0x1p53;  // exact
+        I.tsingle = (u64)std::ceil(q);
+    }
+    I.seed = P.seed; I.tau = P.tau; I.cmin = P.c_min; I.n_a = P.initiator_threshold;
+    I.cz = P.shift_damping / ((double)P.shift_interval * P.tau);
+    I.target = P.target_walkers; I.A = P.shift_interval;
+    I.semi_start = P.semistoch_start; I.semi_size = P.semistoch_size;
+    I.ring_cap = h->ring_cap;
+
+    // integrals and tables on the device
+    double *dh = (double *)dev_alloc(h, h->h.size() * sizeof(double));
+    double *deri = (double *)dev_alloc(h, h->eri.size() * sizeof(double));
+    ulonglong2 *dhfx = (ulonglong2 *)dev_alloc(h, hfx.size() * sizeof(ulonglong2));
+    ulonglong2 *dJ = (ulonglong2 *)dev_alloc(h, Jfx.size() * sizeof(ulonglong2));
+    ulonglong2 *dK = (ulonglong2 *)dev_alloc(h, Kfx.size() * sizeof(ulonglong2));
+    int *dnbr = (int *)dev_alloc(h, std::max<size_t>(1, h->nbr.size()) * sizeof(int));
+    h->dinst = (DevInst *)dev_alloc(h, sizeof(DevInst));
+    h->dunit = (int *)dev_alloc(h, 2 * sizeof(int));
+    h->dstate = (IterState *)dev_alloc(h, sizeof(IterState));
+    I.ring = (fciqmc_iter_stats *)dev_alloc(h, (size_t)h->ring_cap * sizeof(fciqmc_iter_stats));
+    if (!dh || !deri || !dhfx || !dJ || !dK || !dnbr || !h->dinst || !h->dunit || !h->dstate || !I.ring)
+        return bail(FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (integrals)");
+    cudaMemcpyAsync(dh, h->h.data(), h->h.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(deri, h->eri.data(), h->eri.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(dhfx, hfx.data(), hfx.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(dJ, Jfx.data(), Jfx.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(dK, Kfx.data(), Kfx.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice, h->stream);
+    if (!h->nbr.empty()) cudaMemcpyAsync(dnbr, h->nbr.data(), h->nbr.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    I.h = dh; I.eri = deri; I.hfx = dhfx; I.Jfx = dJ; I.Kfx = dK; I.nbr = dnbr;
+    I.st = h->dstate;
+
+    // bucket layout: average occupancy well below the per-bucket capacity
+    double dets_hint = P.max_dets > 0 ? (double)P.max_dets : std::max(4096.0, 2.0 * P.target_walkers);
+    int bb = 0;
+    while (((double)(1LL << bb)) * 640.0 < dets_hint && bb < 24) bb++;
+    int rc = alloc_layout(h, I, bb);
+    if (rc) return bail(rc, "out of device memory (walker buffers)");
+    h->bb = bb;
+    h->heavy_cap = std::max(4096, (int)std::min(1e8, 4.0 * P.target_walkers / HEAVY_ATT));
+    I.heavy = (HeavyChunk *)dev_alloc(h, (size_t)h->heavy_cap * sizeof(HeavyChunk));
+    I.heavy_cap = h->heavy_cap;
+    if (!I.heavy) return bail(FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (heavy queue)");
+
+    // initial state: initial_walkers on the reference determinant
+    {
+        const int b0 = bb ? (int)(det_hash_host(h->ref_a, h->ref_b) >> (64 - bb)) : 0;
+        ulonglong2 k;
+        k.x = h->ref_a; k.y = h->ref_b;
+        double c = P.initial_walkers, hd0 = 0.0;
+        uint8_t f = DFLAG_REF;
+        int one = 1;
+        size_t o = (size_t)b0 * CAP_M;
+        cudaMemcpyAsync(I.key[0] + o, &k, sizeof(k), cudaMemcpyHostToDevice, h->stream);
+        cudaMemcpyAsync(I.c[0] + o, &c, sizeof(c), cudaMemcpyHostToDevice, h->stream);
+        cudaMemcpyAsync(I.hd[0] + o, &hd0, sizeof(hd0), cudaMemcpyHostToDevice, h->stream);
+        cudaMemcpyAsync(I.fl[0] + o, &f, 1, cudaMemcpyHostToDevice, h->stream);
+        cudaMemcpyAsync(I.cnt[0] + b0, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream);
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return bail(FCIQMC_ERR_CUDA, "initial upload failed");
+    }
+    memset(&h->hst, 0, sizeof(IterState));
+    h->hst.S = P.initial_shift;
+    if (write_state(h)) return bail(FCIQMC_ERR_CUDA, h->err);
+    if (upload_inst(h)) return bail(FCIQMC_ERR_CUDA, h->err);
+    if (capture_graph(h)) return bail(FCIQMC_ERR_CUDA, h->err);
+    *out = h;
+    return FCIQMC_OK;
+}
+
+int fciqmc_set_profiling(fciqmc_handle *h, int32_t on)
+{
+    if (!h) return FCIQMC_ERR_INVALID_ARG;
+    h->profiling = on != 0;
+    return FCIQMC_OK;
+}
+
+int fciqmc_kernel_times(fciqmc_handle *h, double out[5])
+{
+    if (!h || !out) return FCIQMC_ERR_INVALID_ARG;
+    for (int k = 0; k < 5; k++) out[k] = h->ktime[k];
+    return FCIQMC_OK;
+}
+
+int fciqmc_layout(fciqmc_handle *h, int64_t out[4])
+{
+    if (!h || !out) return FCIQMC_ERR_INVALID_ARG;
+    out[0] = 1LL << h->bb; out[1] = CAP_M; out[2] = CAP_S; out[3] = (int64_t)h->bytes;
+    return FCIQMC_OK;
+}
+
+int fciqmc_step(fciqmc_handle *h, int64_t n_iter)
+{
+    if (!h || n_iter < 0) return FCIQMC_ERR_INVALID_ARG;
+    int rc = read_state(h);
+    if (rc) return rc;
+    long long target_iter = h->hst.iter + n_iter;
+    int retries = 0;
+    std::vector<cudaEvent_t> evs;
+    double kt[5] = {0, 0, 0, 0, 0};
+    long long kn = 0;
+    while (h->hst.iter < target_iter) {
+        long long start = h->hst.iter;
+        long long chunk = std::min<long long>(target_iter - start, h->ring_cap);
+        if (h->profiling) {
+            evs.resize((size_t)chunk * 6);
+            for (auto &e : evs) cudaEventCreate(&e);
+            for (long long k = 0; k < chunk; k++) {
+                rc = enqueue_iteration(h, evs.data() + 6 * k);
+                if (rc) return rc;
+            }
+        } else {
+            for (long long k = 0; k < chunk; k++) CUDA_TRY(h, cudaGraphLaunch(h->graph, h->stream));
+        }
+        rc = read_state(h);
+        if (rc) return rc;
+        if (h->profiling) {
+            long long done = h->hst.iter - start;
+            for (long long k = 0; k < done; k++)
+                for (int j = 0; j < 5; j++) {
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, evs[6 * k + j], evs[6 * k + j + 1]);
+                    kt[j == 2 ? 4 : (j > 2 ? j - 1 : j)] += ms;
+                }
+            kn += done;
+            for (auto &e : evs) cudaEventDestroy(e);
+            evs.clear();
+        }
+        rc = pull_history(h, start, h->hst.iter);
+        if (rc) return rc;
+        int err = h->hst.err;
+        if (!err) continue;
+        if (err & ERRB_NUMERIC) return fail(h, FCIQMC_ERR_NUMERIC, "numeric error (NaN/Inf or |C| >= 2^31) at iteration " + std::to_string(h->hst.iter));
+        if (err & ERRB_TIMEOUT) return fail(h, FCIQMC_ERR_TIMEOUT, "device wait timed out");
+        if (err & ERRB_PAUSE_SEMI) {
+            rc = build_semistochastic(h);
+            if (rc) return rc;
+            h->hst.err &= ~ERRB_PAUSE_SEMI;
+            rc = write_state(h);
+            if (rc) return rc;
+            continue;
+        }
+        if (++retries > 64) return fail(h, FCIQMC_ERR_CAPACITY, "capacity growth did not converge");
+        rc = reset_after_error(h);
+        if (rc) return rc;
+        if (err & (ERRB_SPAWN_CAP | ERRB_MAIN_CAP)) {
+            rc = grow_buckets(h);
+            if (rc) return rc;
+            rc = reset_after_error(h);
+            if (rc) return rc;
+        }
+        if (err & ERRB_HEAVY_CAP) {
+            rc = grow_heavy(h);
+            if (rc) return rc;
+        }
+        rc = upload_inst(h);
+        if (rc) return rc;
+        rc = capture_graph(h);
+        if (rc) return rc;
+    }
+    if (h->profiling && kn > 0)
+        for (int j = 0; j < 5; j++) h->ktime[j] = kt[j] / (double)kn;
+    return FCIQMC_OK;
+}
+
+int64_t fciqmc_num_dets(fciqmc_handle *h)
+{
+    if (!h) return -1;
+    int nbk = 1 << h->bb;
+    std::vector<int> cnt(nbk);
+    if (read_state(h)) return -1;
+    if (cudaMemcpy(cnt.data(), h->hi.cnt[h->hst.parity], nbk * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    int64_t s = 0;
+    for (int c : cnt) s += c;
+    return s;
+}
+
+int fciqmc_export_state(fciqmc_handle *h, int64_t cap, uint64_t *alpha, uint64_t *beta, double *c, double *hdiag,
+                        int32_t *flags, int64_t *n_out)
+{
+    if (!h || !n_out) return FCIQMC_ERR_INVALID_ARG;
+    int rc = read_state(h);
+    if (rc) return rc;
+    const int par = h->hst.parity;
+    const size_t nbk = (size_t)1 << h->bb, nm = nbk * CAP_M;
+    std::vector<int> cnt(nbk);
+    CUDA_TRY(h, cudaMemcpy(cnt.data(), h->hi.cnt[par], nbk * sizeof(int), cudaMemcpyDeviceToHost));
+    int64_t n = 0;
+    for (int x : cnt) n += x;
+    *n_out = n;
+    if (n > cap) return fail(h, FCIQMC_ERR_CAPACITY, "export buffer too small");
+    if (n > 0 && (!alpha || !beta || !c)) return FCIQMC_ERR_INVALID_ARG;
+    std::vector<ulonglong2> k(nm);
+    std::vector<double> cc(nm), hh(nm);
+    std::vector<uint8_t> ff(nm);
+    CUDA_TRY(h, cudaMemcpy(k.data(), h->hi.key[par], nm * sizeof(ulonglong2), cudaMemcpyDeviceToHost));
+    CUDA_TRY(h, cudaMemcpy(cc.data(), h->hi.c[par], nm * sizeof(double), cudaMemcpyDeviceToHost));
+    CUDA_TRY(h, cudaMemcpy(hh.data(), h->hi.hd[par], nm * sizeof(double), cudaMemcpyDeviceToHost));
+    CUDA_TRY(h, cudaMemcpy(ff.data(), h->hi.fl[par], nm, cudaMemcpyDeviceToHost));
+    std::vector<size_t> idx;
+    idx.reserve((size_t)n);
+    for (size_t b = 0; b < nbk; b++)
+        for (int e = 0; e < cnt[b]; e++) idx.push_back(b * CAP_M + e);
+    std::sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
+        return k[x].x < k[y].x || (k[x].x == k[y].x && k[x].y < k[y].y);
+    });
+    for (size_t i = 0; i < idx.size(); i++) {
+        alpha[i] = k[idx[i]].x;
+        beta[i] = k[idx[i]].y;
+        c[i] = cc[idx[i]];
+        if (hdiag) hdiag[i] = hh[idx[i]];
+        if (flags) flags[i] = ff[idx[i]];
+    }
+    return FCIQMC_OK;
+}
+
+int fciqmc_export_shift(fciqmc_handle *h, int64_t *iteration, double *S, int32_t *vary, int64_t *shift_start,
+                        int64_t *cnt, uint64_t *nw_last_hi, uint64_t *nw_last_lo)
+{
+    if (!h) return FCIQMC_ERR_INVALID_ARG;
+    int rc = read_state(h);
+    if (rc) return rc;
+    if (iteration) *iteration = h->hst.iter;
+    if (S) *S = h->hst.S;
+    if (vary) *vary = h->hst.vary;
+    if (shift_start) *shift_start = h->hst.shift_start;
+    if (cnt) *cnt = h->hst.cnt;
+    if (nw_last_hi) *nw_last_hi = h->hst.nwl_hi;
+    if (nw_last_lo) *nw_last_lo = h->hst.nwl_lo;
+    return FCIQMC_OK;
+}
+
+int fciqmc_import_state(fciqmc_handle *h, int64_t n, const uint64_t *alpha, const uint64_t *beta, const double *c,
+                        int64_t iteration, double S, int32_t vary, int64_t shift_start, int64_t cnt, uint64_t nw_last_hi,
+                        uint64_t nw_last_lo)
+{
+    if (!h || n < 0 || (n > 0 && (!alpha || !beta || !c)) || iteration < 0) return FCIQMC_ERR_INVALID_ARG;
+    const u64 normask = h->norb >= 64 ? ~0ULL : ((1ULL << h->norb) - 1);
+    std::vector<u64> A(alpha, alpha + n), B(beta, beta + n);
+    std::vector<double> C(c, c + n);
+    bool has_ref = false;
+    for (int64_t i = 0; i < n; i++) {
+        if (__builtin_popcountll(A[i]) != h->na || __builtin_popcountll(B[i]) != h->nb || ((A[i] | B[i]) & ~normask) ||
+            !std::isfinite(C[i]))
+            return fail(h, FCIQMC_ERR_INVALID_ARG, "imported determinant with wrong electron count or bad amplitude");
+        if (A[i] == h->ref_a && B[i] == h->ref_b) has_ref = true;
+    }
+    if (!has_ref) { A.push_back(h->ref_a); B.push_back(h->ref_b); C.push_back(0.0); }
+    int rc = read_state(h);
+    if (rc) return rc;
+    for (;;) {
+        const size_t nbk = (size_t)1 << h->bb;
+        std::vector<int> cnt_b(nbk, 0);
+        bool over = false;
+        for (size_t i = 0; i < A.size(); i++) {
+            int b = h->bb ? (int)(det_hash_host(A[i], B[i]) >> (64 - h->bb)) : 0;
+            if (++cnt_b[b] > CAP_M / 2) over = true;
+        }
+        if (!over) break;
+        DevInst nI = h->hi;
+        rc = alloc_layout(h, nI, h->bb + 1);
+        if (rc) return fail(h, rc, "out of device memory");
+        free_layout(h, h->hi);
+        h->hi = nI;
+        h->bb = nI.bb;
+    }
+    const size_t nbk = (size_t)1 << h->bb, nm = nbk * CAP_M;
+    std::vector<int> cnt_b(nbk, 0);
+    std::vector<ulonglong2> k(nm);
+    std::vector<double> cc(nm, 0.0);
+    std::vector<uint8_t> ff(nm, 0);
+    for (size_t i = 0; i < A.size(); i++) {
+        int b = h->bb ? (int)(det_hash_host(A[i], B[i]) >> (64 - h->bb)) : 0;
+        size_t o = (size_t)b * CAP_M + cnt_b[b]++;
+        k[o].x = A[i]; k[o].y = B[i];
+        cc[o] = C[i];
+    }
+    const int par = 0;
+    CUDA_TRY(h, cudaMemcpy(h->hi.key[par], k.data(), nm * sizeof(ulonglong2), cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(h->hi.c[par], cc.data(), nm * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(h->hi.fl[par], ff.data(), nm, cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(h->hi.cnt[par], cnt_b.data(), nbk * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemset(h->hi.scnt_i, 0, nbk * sizeof(int)));
+    CUDA_TRY(h, cudaMemset(h->hi.scnt_n, 0, nbk * sizeof(int)));
+    rc = upload_inst(h);
+    if (rc) return rc;
+    launch_diag(h->dinst, par, (int)nbk, h->stream);
+    CUDA_TRY(h, cudaGetLastError());
+    memset(&h->hst, 0, sizeof(IterState));
+    h->hst.iter = iteration; h->hst.parity = par; h->hst.S = S; h->hst.vary = vary;
+    h->hst.shift_start = shift_start; h->hst.cnt = cnt; h->hst.nwl_hi = nw_last_hi; h->hst.nwl_lo = nw_last_lo;
+    rc = write_state(h);
+    if (rc) return rc;
+    h->hist.clear();
+    h->hist.resize((size_t)iteration);
+    for (int64_t i = 0; i < iteration; i++) { memset(&h->hist[i], 0, sizeof(fciqmc_iter_stats)); h->hist[i].iteration = -1; }
+    return capture_graph(h);
+}
+
+int64_t fciqmc_iter_stats_count(fciqmc_handle *h) { return h ? (int64_t)h->hist.size() : -1; }
+
+int fciqmc_iter_stats_get(fciqmc_handle *h, int64_t first, int64_t count, fciqmc_iter_stats *out)
+{
+    if (!h || !out || first < 0 || count < 0 || first + count > (int64_t)h->hist.size()) return FCIQMC_ERR_INVALID_ARG;
+    memcpy(out, h->hist.data() + first, (size_t)count * sizeof(fciqmc_iter_stats));
+    return FCIQMC_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ statistics
+// Flyvbjerg-Petersen blocking: repeatedly average neighbouring pairs; the
+// standard error at each level is sqrt(var/(n-1)); the first level whose
+// error agrees with the next within the error's own uncertainty is taken.
+static double blocking_sigma(std::vector<double> x)
+{
+    std::vector<std::pair<double, double>> lev;
+    while (x.size() >= 2) {
+        size_t n = x.size();
+        double mean = 0.0;
+        for (double v : x) mean += v;
+        mean /= (double)n;
+        double var = 0.0;
+        for (double v : x) var += (v - mean) * (v - mean);
+        var /= (double)n;
+        double se = std::sqrt(var / (double)(n - 1));
+        lev.push_back({se, se / std::sqrt(2.0 * (double)(n - 1))});
+        std::vector<double> y(n / 2);
+        for (size_t i = 0; i < n / 2; i++) y[i] = 0.5 * (x[2 * i] + x[2 * i + 1]);
+        x.swap(y);
+    }
+    if (lev.empty()) return NAN;
+    for (size_t k = 0; k + 1 < lev.size(); k++)
+        if (std::fabs(lev[k + 1].first - lev[k].first) < lev[k].second) return lev[k].first;
+    return lev.back().first;
+}
+
+extern "C" int fciqmc_energy(fciqmc_handle *h, fciqmc_stats *out)
+{
+    if (!h || !out) return FCIQMC_ERR_INVALID_ARG;
+    memset(out, 0, sizeof(*out));
+    int rc = read_state(h);
+    if (rc) return rc;
+    out->iteration = h->hst.iter;
+    out->eref = h->eref;
+    out->shift = h->eref + h->hst.S;
+    out->vary = h->hst.vary;
+    out->equil_start = h->hst.vary ? h->hst.shift_start + 500 : -1;
+    out->e_proj_mean = NAN;
+    out->e_proj_sigma = NAN;
+    out->shift_mean = NAN;
+    out->shift_sigma = NAN;
+    for (const auto &r : h->hist) {
+        if (r.iteration < 0) continue;
+        out->attempts_total += r.attempts;
+        out->spawns_total += r.spawns;
+        out->rejected_total += r.rejected;
+        out->annihilated_total += r.annihilated;
+    }
+    if (!h->hist.empty()) {
+        const auto &r = h->hist.back();
+        out->nw = r.nw;
+        out->ndet = r.ndet;
+        out->e_proj_inst = r.e_den != 0.0 ? h->eref + r.e_num / r.e_den : NAN;
+    }
+    if (out->equil_start >= 0) {
+        std::vector<double> num, den, sh;
+        for (const auto &r : h->hist)
+            if (r.iteration >= out->equil_start) { num.push_back(r.e_num); den.push_back(r.e_den); sh.push_back(r.shift); }
+        out->n_samples = (int64_t)num.size();
+        if (num.size() >= 8) {
+            double mn = 0, md = 0, ms = 0;
+            for (size_t i = 0; i < num.size(); i++) { mn += num[i]; md += den[i]; ms += sh[i]; }
+            mn /= num.size(); md /= den.size(); ms /= sh.size();
+            double sn = blocking_sigma(num), sd = blocking_sigma(den);
+            double cov = 0, vn = 0, vd = 0;
+            for (size_t i = 0; i < num.size(); i++) {
+                cov += (num[i] - mn) * (den[i] - md);
+                vn += (num[i] - mn) * (num[i] - mn);
+                vd += (den[i] - md) * (den[i] - md);
+            }
+            double rho = (vn > 0 && vd > 0) ? cov / std::sqrt(vn * vd) : 0.0;
+            double r = mn / md;
+            double rel = (mn != 0.0) ? (sn / mn) * (sn / mn) + (sd / md) * (sd / md) - 2.0 * rho * sn * sd / (mn * md)
+                                     : (sn / md) * (sn / md);
+            out->e_proj_mean = h->eref + r;
+            out->e_proj_sigma = mn != 0.0 ? std::fabs(r) * std::sqrt(std::max(rel, 0.0)) : std::sqrt(std::max(rel, 0.0));
+            out->shift_mean = h->eref + ms;
+            out->shift_sigma = blocking_sigma(sh);
+        }
+    }
+    return FCIQMC_OK;
+}

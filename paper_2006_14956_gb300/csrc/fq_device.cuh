@@ -1,0 +1,277 @@
+// fq_device.cuh -- device helpers of the GB300 FCIQMC kernels.
+//
+// Everything here is integer or exactly-rounded binary64 arithmetic; kernels
+// are compiled with -fmad=false so that no multiply-add is contracted.
+#pragma once
+#include "fq_internal.h"
+
+namespace fq {
+
+// ---------------------------------------------------------------- bit tricks
+__device__ __forceinline__ u64 mask_below(int p) { return p >= 64 ? ~0ULL : ((1ULL << p) - 1ULL); }
+
+// position of the k-th (0-based) set bit of x, by halving with popc
+__device__ __forceinline__ int nth_set(u64 x, int k)
+{
+    int pos = 0;
+    int c = __popc((unsigned)x);
+    if (k >= c) { k -= c; x >>= 32; pos = 32; }
+    unsigned w = (unsigned)x;
+    c = __popc(w & 0xffffu);
+    if (k >= c) { k -= c; w >>= 16; pos += 16; }
+    c = __popc(w & 0xffu);
+    if (k >= c) { k -= c; w >>= 8; pos += 8; }
+    c = __popc(w & 0xfu);
+    if (k >= c) { k -= c; w >>= 4; pos += 4; }
+    c = __popc(w & 0x3u);
+    if (k >= c) { k -= c; w >>= 2; pos += 2; }
+    if (k >= (int)(w & 1u)) pos += 1;
+    return pos;
+}
+
+// floor(w * m / 2^64): an integer in [0, m)
+__device__ __forceinline__ u64 pick(u64 w, u64 m) { return __umul64hi(w, m); }
+
+// number of occupied spin orbitals before canonical position pos, then flip it
+__device__ __forceinline__ int flip_parity(u64 &a, u64 &b, int N, int pos)
+{
+    int c;
+    if (pos < N) { c = __popcll(a & mask_below(pos)); a ^= 1ULL << pos; }
+    else { c = __popcll(a) + __popcll(b & mask_below(pos - N)); b ^= 1ULL << (pos - N); }
+    return c & 1;
+}
+
+// ---------------------------------------------------------------- hashing
+__device__ __host__ __forceinline__ u64 fmix64(u64 x)
+{
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdULL;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ULL;
+    x ^= x >> 33;
+    return x;
+}
+__device__ __host__ __forceinline__ u64 det_hash(u64 a, u64 b) { return fmix64((a * 0x9E3779B97F4A7C15ULL) ^ b); }
+__device__ __forceinline__ int bucket_of(u64 h, int bb) { return bb ? (int)(h >> (64 - bb)) : 0; }
+
+// ---------------------------------------------------------------- Philox4x64-10
+// Salmon, Moraes, Dror, Shaw, SC'11: ten rounds of two 64x64->128 products.
+__device__ __forceinline__ void philox(u64 c0, u64 c1, u64 c2, u64 c3, u64 k0, u64 k1, u64 out[4])
+{
+    const u64 M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const u64 W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        if (r) { k0 += W0; k1 += W1; }
+        u64 hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        u64 hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        u64 n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+__device__ __forceinline__ double u53(u64 w) { return (double)(w >> 11) * 0x1p-53; }
+
+// Eq. (2): |v| >= c_min kept; else sign(v) c_min with probability |v|/c_min, else 0
+__device__ __forceinline__ double round_stoch(double v, double cmin, double u)
+{
+    if (v == 0.0 || fabs(v) >= cmin) return v;
+    return u < fabs(v) / cmin ? copysign(cmin, v) : 0.0;
+}
+
+// ---------------------------------------------------------------- exact sums
+// A binary64 x = m 2^e is placed on the fixed grid 2^-F as the integer
+// m 2^(e+F).  The host checked that every value summed this way lies on the
+// grid and that the sums fit in 126 bits, so the conversion and the integer
+// sums are exact and the single rounding happens in fixed_to_double.
+__device__ __forceinline__ i128 to_fixed(double x, int F)
+{
+    u64 bits = (u64)__double_as_longlong(x);
+    int ex = (int)((bits >> 52) & 0x7ff);
+    u64 m = bits & 0xFFFFFFFFFFFFFULL;
+    int e;
+    if (ex == 0) { if (m == 0) return 0; e = -1074; } else { m |= 1ULL << 52; e = ex - 1075; }
+    int sh = e + F;
+    u128 v = sh >= 0 ? ((u128)m << sh) : (sh > -64 ? (u128)(m >> (-sh)) : (u128)0);
+    return (bits >> 63) ? -(i128)v : (i128)v;
+}
+
+__device__ __forceinline__ i128 fx_load(const ulonglong2 *t, int i)
+{
+    ulonglong2 v = __ldg(t + i);
+    return (i128)(((u128)v.y << 64) | (u128)v.x);
+}
+
+// round v 2^-F to the nearest binary64, ties to even (normal range assumed)
+__device__ __forceinline__ double fixed_to_double(i128 v, int F)
+{
+    if (v == 0) return 0.0;
+    u64 sign = 0;
+    u128 u;
+    if (v < 0) { sign = 1ULL << 63; u = (u128)(-v); } else u = (u128)v;
+    u64 hi = (u64)(u >> 64), lo = (u64)u;
+    int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+    u64 mant;
+    int e2;
+    if (msb <= 52) {
+        mant = lo << (52 - msb);
+        e2 = msb - 52;
+    } else {
+        int sh = msb - 52;
+        u128 q = u >> sh;
+        mant = (u64)q;
+        u128 rem = u - (q << sh);
+        u128 half = (u128)1 << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1ULL))) {
+            mant++;
+            if (mant == (1ULL << 53)) { mant >>= 1; sh++; }
+        }
+        e2 = sh;
+    }
+    int E = 52 + e2 - F;
+    u64 bits = sign | ((u64)(E + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFULL);
+    return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ double u128_to_double(u128 u) { return fixed_to_double((i128)u, 0); }
+__device__ __forceinline__ double i128_to_double(i128 v) { return fixed_to_double(v, 0); }
+
+// floor(|c| 2^32); |c| < 2^31 checked by the caller
+__device__ __forceinline__ u64 fx32(double c) { return (u64)(fabs(c) * 4294967296.0); }
+
+__device__ __forceinline__ i128 shfl_xor_i128(i128 v, int m)
+{
+    u64 lo = (u64)v, hi = (u64)((u128)v >> 64);
+    lo = __shfl_xor_sync(0xffffffffu, lo, m);
+    hi = __shfl_xor_sync(0xffffffffu, hi, m);
+    return (i128)(((u128)hi << 64) | (u128)lo);
+}
+
+// ---------------------------------------------------------------- logarithm
+// ln x = k ln2 + 2 atanh(s), x = m 2^k, m in (sqrt(1/2), sqrt(2)],
+// s = (m-1)/(m+1); the atanh series is summed in Horner form to z^11, z = s^2.
+__device__ double fq_ln(double x)
+{
+    u64 bits = (u64)__double_as_longlong(x);
+    int k;
+    if (((bits >> 52) & 0x7ff) == 0) {
+        double y = x * 0x1p54;
+        bits = (u64)__double_as_longlong(y);
+        k = (int)((bits >> 52) & 0x7ff) - 1023 - 54;
+    } else {
+        k = (int)((bits >> 52) & 0x7ff) - 1023;
+    }
+    bits = (bits & 0xFFFFFFFFFFFFFULL) | (1023ULL << 52);
+    double m = __longlong_as_double((long long)bits);
+    if (m > 1.4142135623730951) { m = m * 0.5; k += 1; }
+    double s = (m - 1.0) / (m + 1.0);
+    double z = s * s;
+    double p = 2.0 / 23.0;
+    for (int j = 10; j >= 0; j--) p = 2.0 / (double)(2 * j + 1) + z * p;
+    double r = s * p;
+    const double ln2_hi = 0x1.62e42fefa39efp-1, ln2_lo = 0x1.abc9e3b39803fp-56;
+    return (double)k * ln2_hi + ((double)k * ln2_lo + r);
+}
+
+// ---------------------------------------------------------------- integrals
+__device__ __forceinline__ int pidx(int p, int q) { return p >= q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p; }
+__device__ __forceinline__ double eri4(const DevInst &I, int p, int q, int r, int s)
+{
+    return __ldg(I.eri + pidx(pidx(p, q), pidx(r, s)));
+}
+
+// single excitation i -> a of spin sp from (pa, pb):
+// exact sum of h_ai + sum_{k occ, k != i} (ai|kk) - sum_{k occ same spin, k != i} (ak|ki)
+__device__ double single_exact(const DevInst &I, u64 pa, u64 pb, int sp, int i, int a)
+{
+    const int N = I.norb, F = I.F;
+    i128 acc = to_fixed(__ldg(I.h + a * N + i), F);
+    const int pai = pidx(a, i);
+    u64 occ[2] = { pa, pb };
+    occ[sp] &= ~(1ULL << i);
+    for (int s = 0; s < 2; s++) {
+        u64 x = occ[s];
+        while (x) {
+            int k = __ffsll((long long)x) - 1;
+            x &= x - 1;
+            acc += to_fixed(__ldg(I.eri + pidx(pai, k * (k + 3) / 2)), F);
+            if (s == sp) acc -= to_fixed(__ldg(I.eri + pidx(pidx(a, k), pidx(k, i))), F);
+        }
+    }
+    return fixed_to_double(acc, F);
+}
+
+// <D_j|H|D_i>, D_j != D_i (used for E_proj): Slater-Condon rules with the
+// same sign convention as the spawning code
+__device__ double hoff_generic(const DevInst &I, u64 ia, u64 ib, u64 ja, u64 jb)
+{
+    const int N = I.norb;
+    u64 ra = ia & ~ja, rb = ib & ~jb, aa = ja & ~ia, ab = jb & ~ib;
+    int nr = __popcll(ra) + __popcll(rb);
+    if (nr == 0 || nr > 2 || nr != __popcll(aa) + __popcll(ab)) return 0.0;
+    if (nr == 1) {
+        int sp = ra ? 0 : 1;
+        if ((sp == 0 && !aa) || (sp == 1 && !ab)) return 0.0;
+        int i = __ffsll((long long)(sp ? rb : ra)) - 1, a = __ffsll((long long)(sp ? ab : aa)) - 1;
+        u64 x = sp ? ib : ia;
+        u64 between = i < a ? (mask_below(a) & ~mask_below(i + 1)) : (mask_below(i) & ~mask_below(a + 1));
+        double v = single_exact(I, ia, ib, sp, i, a);
+        return (__popcll(x & between) & 1) ? -v : v;
+    }
+    // canonical positions of the two removed and two added spin orbitals
+    int P[2], Q[2], np = 0, nq = 0;
+    u64 x;
+    x = ra; while (x) { int k = __ffsll((long long)x) - 1; x &= x - 1; P[np++] = k; }
+    x = rb; while (x) { int k = __ffsll((long long)x) - 1; x &= x - 1; P[np++] = N + k; }
+    x = aa; while (x) { int k = __ffsll((long long)x) - 1; x &= x - 1; Q[nq++] = k; }
+    x = ab; while (x) { int k = __ffsll((long long)x) - 1; x &= x - 1; Q[nq++] = N + k; }
+    u64 ta = ia, tb = ib;
+    int par = flip_parity(ta, tb, N, P[0]);
+    par ^= flip_parity(ta, tb, N, P[1]);
+    par ^= flip_parity(ta, tb, N, Q[1]);
+    par ^= flip_parity(ta, tb, N, Q[0]);
+    int si = P[0] >= N, sj = P[1] >= N, sa = Q[0] >= N, sb = Q[1] >= N;
+    int oi = P[0] % N, oj = P[1] % N, oa = Q[0] % N, ob = Q[1] % N;
+    bool dir = (sa == si) && (sb == sj), exch = (sa == sj) && (sb == si);
+    double v;
+    if (dir && exch) v = eri4(I, oa, oi, ob, oj) - eri4(I, oa, oj, ob, oi);
+    else if (dir) v = eri4(I, oa, oi, ob, oj);
+    else if (exch) v = -eri4(I, oa, oj, ob, oi);
+    else v = 0.0;
+    return par ? -v : v;
+}
+
+// H_ii - E_ref for determinant (a, b), computed by one warp: the exact sum
+// of h_pp over occupied orbitals and (pp|qq) - delta_spin (pq|qp) over
+// occupied pairs, minus the same sum for the reference, rounded once.
+__device__ double diag_exact_warp(const DevInst &I, u64 a, u64 b)
+{
+    const int lane = threadIdx.x & 31, N = I.norb;
+    i128 part = 0;
+    for (int e = lane; e < I.n; e += 32) {
+        bool sp = e >= I.na;
+        u64 w = sp ? b : a;
+        int p = nth_set(w, sp ? e - I.na : e);
+        part += fx_load(I.hfx, p);
+        u64 same = w & ~mask_below(p + 1);
+        while (same) {
+            int q = __ffsll((long long)same) - 1;
+            same &= same - 1;
+            part += fx_load(I.Jfx, p * N + q) - fx_load(I.Kfx, p * N + q);
+        }
+        if (!sp) {
+            u64 ob = b;
+            while (ob) {
+                int q = __ffsll((long long)ob) - 1;
+                ob &= ob - 1;
+                part += fx_load(I.Jfx, p * N + q);
+            }
+        }
+    }
+    for (int m = 16; m >= 1; m >>= 1) part += shfl_xor_i128(part, m);
+    i128 xref = (i128)(((u128)I.xref_hi << 64) | (u128)I.xref_lo);
+    return fixed_to_double(part - xref, I.F);
+}
+
+}  // namespace fq

@@ -1,0 +1,141 @@
+// fq_internal.h -- layout shared by the host driver (capi.cu) and the kernels
+// (kernels.cu) of the GB300 FCIQMC library.  Not part of the public ABI.
+#pragma once
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#include "../../include/fciqmc.h"
+
+namespace fq {
+
+typedef unsigned long long u64;
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+// excitation classes; lambda_c = tau / p_gen(c)
+enum { CLS_SINGLE_A = 0, CLS_SINGLE_B, CLS_DOUBLE_AB, CLS_DOUBLE_AA, CLS_DOUBLE_BB, CLS_HOP, NCLS };
+// Philox counter purposes
+enum { PURPOSE_SPAWN = 1, PURPOSE_DEATH = 2, PURPOSE_ANNIH = 3 };
+// device error bits (IterState::err)
+enum {
+    ERRB_SPAWN_CAP = 1,   // a bucket received more spawns than it holds
+    ERRB_MAIN_CAP = 2,    // a bucket's new list exceeds its capacity
+    ERRB_HEAVY_CAP = 4,   // heavy-determinant chunk queue full
+    ERRB_NUMERIC = 8,     // NaN/Inf or |C|, |w| beyond 2^31
+    ERRB_TIMEOUT = 16,    // bounded wait expired
+    ERRB_PAUSE_SEMI = 32, // iteration boundary at which D must be built (not an error)
+};
+enum { DFLAG_REF = 1, DFLAG_D = 2 };
+
+// launch geometry
+constexpr int K1_THREADS = 256;
+constexpr unsigned HEAVY_ATT = 2048;  // attempts per heavy chunk
+constexpr int K3_THREADS = 256;
+constexpr int EMAX = 3072;            // main + spawned records staged per bucket
+constexpr int CAP_M = 1536;           // main-list capacity per bucket
+constexpr int CAP_S = EMAX - CAP_M;   // spawn capacity per bucket
+constexpr int GBITS = 11;             // sub-hash groups per bucket in the annihilation sort
+constexpr int NGROUP = 1 << GBITS;
+constexpr int K5_THREADS = 1024;
+
+struct HeavyChunk {  // a slice of the attempts of one determinant with many walkers
+    u64 a, b;
+    double cper;
+    u64 k0;
+    uint32_t count;
+    uint32_t flags;  // bit 0: initiator, bit 1: parent in D
+};
+
+struct Partial {  // per-bucket reductions of one iteration
+    u64 nw_lo, nw_hi;       // N_w * 2^32 as a 128-bit integer
+    u64 ann_lo, ann_hi;     // annihilated walkers * 2^32 (signed 128-bit)
+    long long ndet, rejected, spawns, attempts;
+    double e_num;
+    double pad;
+};
+
+struct IterState {  // device-resident iteration state of one run
+    long long iter;
+    int parity;
+    int vary;
+    double S;
+    long long shift_start;
+    long long cnt;
+    u64 nwl_hi, nwl_lo;     // N_w(2^32 units) at the last shift update
+    int err;
+    int heavy_n;
+    double e_den;
+    long long semi_built;   // 1 once D exists
+    long long pad[4];
+};
+
+// one run as seen by the kernels
+struct DevInst {
+    // system
+    int kind, norb, na, nb, n, ma, mb, z;
+    int F;    // exact-sum scale of the integrals: value = X * 2^-F
+    int Fw;   // exact-sum scale of spawned weights
+    const double *h;
+    const double *eri;
+    const int *nbr;
+    const ulonglong2 *hfx;  // h_pp, fixed point (lo, hi)
+    const ulonglong2 *Jfx;  // (pp|qq)
+    const ulonglong2 *Kfx;  // (pq|qp)
+    u64 xref_lo, xref_hi;   // exact diagonal sum of the reference
+    u64 ref_a, ref_b;
+    u64 normask;
+    double lam[NCLS];
+    double tmt;             // -t (Hubbard hopping matrix element)
+    u64 tsingle;            // single excitation iff (w0 >> 11) < tsingle
+    u64 seed;
+    double tau, cmin, n_a;
+    double cz;              // shift_damping / (A tau)
+    double target;
+    long long A;
+    long long semi_start;
+    long long semi_size;
+    // layout
+    int bb;                 // buckets = 1 << bb
+    int unit0;              // first global unit (bucket) index of this run
+    ulonglong2 *key[2];
+    double *c[2];
+    double *hd[2];
+    uint8_t *fl[2];
+    int *cnt[2];
+    ulonglong2 *skey;
+    double *sw;
+    int *scnt_i;
+    int *scnt_n;
+    HeavyChunk *heavy;
+    int heavy_cap;
+    Partial *part;
+    IterState *st;
+    fciqmc_iter_stats *ring;
+    int ring_cap;
+    // semi-stochastic space D (sorted keys, CSR of H^D - E_ref, new amplitudes)
+    int nd;
+    const ulonglong2 *dkey;
+    const long long *drow;
+    const int *dcol;
+    const double *dval;
+    double *dc_new;         // C_D after the exact projection of this iteration
+    const u64 *dhash_keys;  // open-addressing set of D keys (a, b interleaved), size dhash_cap
+    int dhash_bits;
+};
+
+// host-side launchers (kernels.cu)
+void launch_spawn(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, cudaStream_t s);
+void launch_spawn_heavy(const DevInst *dinst, int n_inst, cudaStream_t s);
+void launch_semistoch(const DevInst *dinst, int n_inst, int max_nd, cudaStream_t s);
+cudaError_t launch_annihilate(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, cudaStream_t s);
+void launch_finalize(const DevInst *dinst, int n_inst, cudaStream_t s);
+void launch_rebucket(const DevInst *src, const DevInst *dst, int nb_src, int parity, cudaStream_t s);
+void launch_diag(const DevInst *dinst, int parity, int nb, cudaStream_t s);
+void launch_select_top(const DevInst *dinst, int parity, int nb, double *mag_out, ulonglong2 *key_out, cudaStream_t s);
+void launch_build_hd(const DevInst *dinst, int nd, long long *rowcount, int pass, cudaStream_t s);
+void launch_mark_d(const DevInst *dinst, int parity, int nb, cudaStream_t s);
+
+// host helpers shared with capi.cu
+u64 det_hash_host(u64 a, u64 b);
+
+}  // namespace fq

@@ -1,0 +1,801 @@
+// kernels.cu -- the projector iteration of initiator-FCIQMC on GB300.
+//
+// One iteration (Eq. (3) of Guther et al. 2020) is four launches over the
+// bucketed walker list of every run in the batch:
+//   k_spawn        (a) spawning: ceil(|C_i|) attempts per determinant, one
+//                  Philox block, one excitation and one Slater-Condon element
+//                  per attempt; survivors of the rounding of Eq. (2) are
+//                  appended to the spawn bucket of their target.
+//   k_spawn_heavy  the same for determinants with more than HEAVY_ATT walkers,
+//                  split into fixed-size slices so no block waits on one
+//                  heavily populated determinant.
+//   k_annihilate   (b)+(c) per bucket: stage the bucket's walkers and spawns
+//                  in shared memory, group equal determinants by a sub-hash
+//                  counting sort, apply death and rounding, sum the spawns
+//                  exactly, apply the initiator rule and rounding, write the
+//                  new bucket, compute H_jj for new determinants, and reduce
+//                  N_w, E_num (Eq. (8)) and counters per bucket.
+//   k_finalize     per run: total the bucket reductions, update the shift,
+//                  append the statistics row, flip the buffers.
+// All of them read the iteration state from device memory, so one iteration
+// is captured once as a CUDA graph and replayed.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fq_device.cuh"
+
+namespace fq {
+
+__device__ __forceinline__ int find_inst(const int *unit_start, int n_inst, int u)
+{
+    int lo = 0, hi = n_inst;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (__ldg(unit_start + mid) <= u) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// D membership (open addressing on the determinant hash; empty slot = (0,0),
+// which is never a valid determinant because every run has electrons)
+__device__ __forceinline__ bool in_D(const DevInst &I, u64 a, u64 b)
+{
+    if (I.nd == 0) return false;
+    u64 m = (1ULL << I.dhash_bits) - 1;
+    u64 s = det_hash(a, b) & m;
+    for (int probe = 0; probe < (1 << I.dhash_bits); probe++) {
+        u64 ka = __ldg(I.dhash_keys + 2 * s), kb = __ldg(I.dhash_keys + 2 * s + 1);
+        if (ka == a && kb == b) return true;
+        if (ka == 0 && kb == 0) return false;
+        s = (s + 1) & m;
+    }
+    return false;
+}
+
+// ------------------------------------------------------------------ spawning
+// One spawning attempt k from parent (pa, pb) with amplitude-per-attempt cper.
+// flags bit 0: parent is an initiator; bit 1: parent lies in D.
+__device__ void do_attempt(const DevInst &I, long long it, u64 pa, u64 pb, double cper, unsigned flags, u64 k)
+{
+    u64 w[4];
+    philox(pa, pb, (u64)it, (k << 8) | (u64)PURPOSE_SPAWN, I.seed, 0ULL, w);
+    const int N = I.norb, n = I.n, na = I.na;
+    u64 ta = pa, tb = pb;
+    int cls;
+    double H;
+    if (I.kind == FCIQMC_HUBBARD) {
+        int e = (int)pick(w[1], (u64)n);
+        int sp = e >= na;
+        u64 x = sp ? pb : pa;
+        int p = nth_set(x, sp ? e - na : e);
+        int q = __ldg(I.nbr + 4 * p + (int)pick(w[2], (u64)I.z));
+        if (q < 0 || ((x >> q) & 1ULL)) return;
+        u64 between = p < q ? (mask_below(q) & ~mask_below(p + 1)) : (mask_below(p) & ~mask_below(q + 1));
+        H = (__popcll(x & between) & 1) ? -I.tmt : I.tmt;
+        x ^= (1ULL << p) | (1ULL << q);
+        if (sp) tb = x; else ta = x;
+        cls = CLS_HOP;
+    } else if ((w[0] >> 11) < I.tsingle) {
+        int e = (int)pick(w[1], (u64)n);
+        int sp = e >= na;
+        u64 x = sp ? pb : pa;
+        int i = nth_set(x, sp ? e - na : e);
+        int m = sp ? I.mb : I.ma;
+        if (m == 0) return;
+        int a = nth_set(~x & I.normask, (int)pick(w[2], (u64)m));
+        u64 between = i < a ? (mask_below(a) & ~mask_below(i + 1)) : (mask_below(i) & ~mask_below(a + 1));
+        double v = single_exact(I, pa, pb, sp, i, a);
+        H = (__popcll(x & between) & 1) ? -v : v;
+        x ^= (1ULL << i) | (1ULL << a);
+        if (sp) tb = x; else ta = x;
+        cls = sp ? CLS_SINGLE_B : CLS_SINGLE_A;
+    } else {
+        if (n < 2) return;
+        unsigned xe = (unsigned)pick(w[1], (u64)(n * (n - 1)));
+        int e1 = (int)(xe / (unsigned)(n - 1)), r = (int)(xe % (unsigned)(n - 1));
+        int e2 = r + (r >= e1 ? 1 : 0);
+        int s1 = e1 >= na, s2 = e2 >= na;
+        int o1 = nth_set(s1 ? pb : pa, s1 ? e1 - na : e1);
+        int o2 = nth_set(s2 ? pb : pa, s2 ? e2 - na : e2);
+        int P0, P1, Q0, Q1, oi, oj, oa, ob;
+        if (s1 != s2) {
+            if (I.ma == 0 || I.mb == 0) return;
+            oi = s1 ? o2 : o1;  // alpha electron
+            oj = s1 ? o1 : o2;  // beta electron
+            unsigned y = (unsigned)pick(w[2], (u64)(I.ma * I.mb));
+            oa = nth_set(~pa & I.normask, (int)(y / (unsigned)I.mb));
+            ob = nth_set(~pb & I.normask, (int)(y % (unsigned)I.mb));
+            P0 = oi; P1 = N + oj; Q0 = oa; Q1 = N + ob;
+            ta = pa ^ (1ULL << oi) ^ (1ULL << oa);
+            tb = pb ^ (1ULL << oj) ^ (1ULL << ob);
+            cls = CLS_DOUBLE_AB;
+        } else {
+            int m = s1 ? I.mb : I.ma;
+            if (m < 2) return;
+            u64 x = s1 ? pb : pa;
+            unsigned y = (unsigned)pick(w[2], (u64)(m * (m - 1)));
+            int h1 = (int)(y / (unsigned)(m - 1)), rr = (int)(y % (unsigned)(m - 1));
+            int h2 = rr + (rr >= h1 ? 1 : 0);
+            int q1 = nth_set(~x & I.normask, h1), q2 = nth_set(~x & I.normask, h2);
+            oi = min(o1, o2); oj = max(o1, o2); oa = min(q1, q2); ob = max(q1, q2);
+            int off = s1 ? N : 0;
+            P0 = off + oi; P1 = off + oj; Q0 = off + oa; Q1 = off + ob;
+            x ^= (1ULL << oi) | (1ULL << oj) | (1ULL << oa) | (1ULL << ob);
+            if (s1) tb = x; else ta = x;
+            cls = s1 ? CLS_DOUBLE_BB : CLS_DOUBLE_AA;
+        }
+        u64 xa = pa, xb = pb;
+        int par = flip_parity(xa, xb, N, P0);
+        par ^= flip_parity(xa, xb, N, P1);
+        par ^= flip_parity(xa, xb, N, Q1);
+        par ^= flip_parity(xa, xb, N, Q0);
+        double v = (cls == CLS_DOUBLE_AB) ? eri4(I, oa, oi, ob, oj) : eri4(I, oa, oi, ob, oj) - eri4(I, oa, oj, ob, oi);
+        H = par ? -v : v;
+    }
+    if (H == 0.0) return;
+    double ws = -(H * (I.lam[cls] * cper));
+    if (fabs(ws) < I.cmin) {
+        ws = round_stoch(ws, I.cmin, u53(w[3]));
+        if (ws == 0.0) return;
+    }
+    if (!(fabs(ws) < 0x1p31)) { atomicOr(&I.st->err, ERRB_NUMERIC); return; }
+    if ((flags & 2u) && in_D(I, ta, tb)) return;  // D -> D is applied exactly
+    int bt = bucket_of(det_hash(ta, tb), I.bb);
+    if (flags & 1u) {
+        int s = atomicAdd(I.scnt_i + bt, 1);
+        if (s < CAP_S) {
+            size_t o = (size_t)bt * CAP_S + s;
+            I.skey[o] = make_ulonglong2(ta, tb);
+            I.sw[o] = ws;
+        }
+    } else {
+        int s = atomicAdd(I.scnt_n + bt, 1);
+        int slot = CAP_S - 1 - s;
+        if (slot >= 0) {
+            size_t o = (size_t)bt * CAP_S + slot;
+            I.skey[o] = make_ulonglong2(ta, tb);
+            I.sw[o] = ws;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(K1_THREADS) k_spawn(const DevInst *__restrict__ insts, const int *__restrict__ unit_start,
+                                                      int n_inst, int n_units)
+{
+    __shared__ unsigned s_off[K1_THREADS + 1];
+    __shared__ u64 s_a[K1_THREADS], s_b[K1_THREADS];
+    __shared__ double s_cper[K1_THREADS];
+    __shared__ unsigned s_fl[K1_THREADS];
+    __shared__ unsigned s_w[K1_THREADS / 32];
+    __shared__ long long s_wl[K1_THREADS / 32];
+    __shared__ int s_err, s_par;
+    __shared__ long long s_it;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const int ii = find_inst(unit_start, n_inst, u);
+        const DevInst &I = insts[ii];
+        if (t == 0) {
+            s_err = *(volatile int *)&I.st->err;
+            s_par = I.st->parity;
+            s_it = I.st->iter;
+        }
+        __syncthreads();
+        if (s_err) { __syncthreads(); continue; }
+        const int b = u - I.unit0, par = s_par;
+        const long long it = s_it;
+        const int m = I.cnt[par][b];
+        const size_t base = (size_t)b * CAP_M;
+        long long att = 0;
+        for (int d0 = 0; d0 < m; d0 += K1_THREADS) {
+            const int d = d0 + t;
+            unsigned nat_l = 0, fl = 0;
+            u64 pa = 0, pb = 0;
+            double cper = 0.0;
+            u64 nat = 0;
+            if (d < m) {
+                ulonglong2 kk = I.key[par][base + d];
+                double c = I.c[par][base + d];
+                uint8_t f = I.fl[par][base + d];
+                pa = kk.x; pb = kk.y;
+                if (c != 0.0) {
+                    double mag = fabs(c);
+                    if (!(mag < 0x1p31)) {
+                        atomicOr(&I.st->err, ERRB_NUMERIC);
+                    } else {
+                        nat = (u64)ceil(mag);
+                        bool init = mag > I.n_a || (f & (DFLAG_REF | DFLAG_D));
+                        fl = (init ? 1u : 0u) | ((f & DFLAG_D) ? 2u : 0u);
+                        cper = c / (double)nat;
+                        att += (long long)nat;
+                        if (nat <= HEAVY_ATT) nat_l = (unsigned)nat;
+                    }
+                }
+            }
+            // heavy determinants: split into slices, written cooperatively by the warp
+            unsigned hv = __ballot_sync(0xffffffffu, nat > HEAVY_ATT);
+            while (hv) {
+                int src = __ffs(hv) - 1;
+                hv &= hv - 1;
+                u64 hn = __shfl_sync(0xffffffffu, nat, src);
+                u64 ha = __shfl_sync(0xffffffffu, pa, src), hb = __shfl_sync(0xffffffffu, pb, src);
+                double hc = __shfl_sync(0xffffffffu, cper, src);
+                unsigned hfl = __shfl_sync(0xffffffffu, fl, src);
+                unsigned nch = (unsigned)((hn + HEAVY_ATT - 1) / HEAVY_ATT);
+                int q0 = 0;
+                if (lane == 0) q0 = atomicAdd(&I.st->heavy_n, (int)nch);
+                q0 = __shfl_sync(0xffffffffu, q0, 0);
+                if ((long long)q0 + nch > (long long)I.heavy_cap) {
+                    if (lane == 0) atomicOr(&I.st->err, ERRB_HEAVY_CAP);
+                } else {
+                    for (unsigned q = lane; q < nch; q += 32) {
+                        HeavyChunk h;
+                        h.a = ha; h.b = hb; h.cper = hc; h.k0 = (u64)q * HEAVY_ATT;
+                        u64 left = hn - h.k0;
+                        h.count = (unsigned)(left < HEAVY_ATT ? left : HEAVY_ATT);
+                        h.flags = hfl;
+                        I.heavy[q0 + q] = h;
+                    }
+                }
+            }
+            // block exclusive scan of the light attempt counts
+            unsigned v = nat_l;
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            if (lane == 31) s_w[warp] = v;
+            __syncthreads();
+            if (warp == 0) {
+                unsigned x = lane < K1_THREADS / 32 ? s_w[lane] : 0u;
+                for (int o = 1; o < 32; o <<= 1) {
+                    unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                if (lane < K1_THREADS / 32) s_w[lane] = x;
+            }
+            __syncthreads();
+            unsigned excl = v - nat_l + (warp ? s_w[warp - 1] : 0u);
+            s_off[t] = excl;
+            if (t == K1_THREADS - 1) s_off[K1_THREADS] = excl + nat_l;
+            s_a[t] = pa; s_b[t] = pb; s_cper[t] = cper; s_fl[t] = fl;
+            __syncthreads();
+            const unsigned total = s_off[K1_THREADS];
+            for (unsigned a = t; a < total; a += K1_THREADS) {
+                int lo = 0, hi = K1_THREADS;
+                while (hi - lo > 1) {
+                    int mid = (lo + hi) >> 1;
+                    if (s_off[mid] <= a) lo = mid; else hi = mid;
+                }
+                do_attempt(I, it, s_a[lo], s_b[lo], s_cper[lo], s_fl[lo], (u64)(a - s_off[lo]));
+            }
+            __syncthreads();
+        }
+        // attempts of this bucket
+        for (int o = 16; o >= 1; o >>= 1) att += __shfl_xor_sync(0xffffffffu, att, o);
+        if (lane == 0) s_wl[warp] = att;
+        __syncthreads();
+        if (t == 0) {
+            long long s = 0;
+            for (int k = 0; k < K1_THREADS / 32; k++) s += s_wl[k];
+            I.part[b].attempts = s;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(K1_THREADS) k_spawn_heavy(const DevInst *__restrict__ insts, int n_inst)
+{
+    __shared__ int s_n, s_err;
+    __shared__ long long s_it;
+    for (int ii = 0; ii < n_inst; ii++) {
+        const DevInst &I = insts[ii];
+        if (threadIdx.x == 0) {
+            s_err = *(volatile int *)&I.st->err;
+            s_n = I.st->heavy_n;
+            s_it = I.st->iter;
+        }
+        __syncthreads();
+        if (!s_err) {
+            for (int q = blockIdx.x; q < s_n; q += gridDim.x) {
+                HeavyChunk h = I.heavy[q];
+                for (unsigned a = threadIdx.x; a < h.count; a += blockDim.x)
+                    do_attempt(I, s_it, h.a, h.b, h.cper, h.flags, h.k0 + a);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ annihilation
+struct K3Smem {
+    ulonglong2 key[EMAX];
+    double val[EMAX];
+    unsigned short perm[EMAX];
+    unsigned short lead[EMAX];  // leaders of each group in key order; bit 15 = kept
+    unsigned short grp[EMAX];
+    int goff[NGROUP + 1];
+    int cur[NGROUP];
+    unsigned short nlead[NGROUP];
+    int wsum[K3_THREADS / 32];
+    double red_d[K3_THREADS / 32];
+    u64 red_u[K3_THREADS / 32][8];
+    int n_new;
+    int hdr_err, hdr_par;
+    long long hdr_it;
+    double hdr_S;
+};
+
+__device__ __forceinline__ bool key_less(u64 a1, u64 b1, u64 a2, u64 b2) { return a1 < a2 || (a1 == a2 && b1 < b2); }
+
+// D index of a determinant known to be in D (binary search over sorted keys)
+__device__ int d_index(const DevInst &I, u64 a, u64 b)
+{
+    int lo = 0, hi = I.nd;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        ulonglong2 k = __ldg(I.dkey + mid);
+        if (k.x == a && k.y == b) return mid;
+        if (key_less(k.x, k.y, a, b)) lo = mid + 1; else hi = mid;
+    }
+    return -1;
+}
+
+__device__ __forceinline__ int block_excl_scan(int v, int *wsum, int *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int s = lane < K3_THREADS / 32 ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < K3_THREADS / 32) wsum[lane] = s;
+    }
+    __syncthreads();
+    int r = x - v + (warp ? wsum[warp - 1] : 0);
+    *total = wsum[K3_THREADS / 32 - 1];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(K3_THREADS, 2) k_annihilate(const DevInst *__restrict__ insts,
+                                                              const int *__restrict__ unit_start, int n_inst, int n_units)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    K3Smem &S = *reinterpret_cast<K3Smem *>(smem_raw);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    constexpr int GPT = NGROUP / K3_THREADS;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const int ii = find_inst(unit_start, n_inst, u);
+        const DevInst &I = insts[ii];
+        if (t == 0) {
+            S.hdr_err = *(volatile int *)&I.st->err;
+            S.hdr_par = I.st->parity;
+            S.hdr_it = I.st->iter;
+            S.hdr_S = I.st->S;
+            S.n_new = 0;
+        }
+        __syncthreads();
+        if (S.hdr_err) { __syncthreads(); continue; }
+        const int b = u - I.unit0, par = S.hdr_par;
+        const long long it = S.hdr_it;
+        const double shift = S.hdr_S;
+        const int m = I.cnt[par][b], si = I.scnt_i[b], sn = I.scnt_n[b];
+        if (si + sn > CAP_S) {
+            if (t == 0) atomicOr(&I.st->err, ERRB_SPAWN_CAP);
+            __syncthreads();
+            continue;
+        }
+        const int E = m + si + sn;
+        const size_t base = (size_t)b * CAP_M, sbase = (size_t)b * CAP_S;
+        const int shift_g = 64 - I.bb - GBITS;
+        const ulonglong2 *okey = I.key[par];
+        const double *oc = I.c[par], *ohd = I.hd[par];
+        const uint8_t *ofl = I.fl[par];
+
+        // 1. stage the bucket: walkers [0, m), initiator spawns [m, m+si),
+        //    other spawns [m+si, E); histogram of the sub-hash groups
+        for (int g = t; g < NGROUP; g += K3_THREADS) S.cur[g] = 0;
+        __syncthreads();
+        for (int e = t; e < E; e += K3_THREADS) {
+            ulonglong2 k;
+            double v;
+            if (e < m) { k = okey[base + e]; v = oc[base + e]; }
+            else if (e < m + si) { k = I.skey[sbase + (e - m)]; v = I.sw[sbase + (e - m)]; }
+            else { int slot = CAP_S - 1 - (e - m - si); k = I.skey[sbase + slot]; v = I.sw[sbase + slot]; }
+            S.key[e] = k;
+            S.val[e] = v;
+            int g = (int)((det_hash(k.x, k.y) >> shift_g) & (NGROUP - 1));
+            S.grp[e] = (unsigned short)g;
+            atomicAdd(&S.cur[g], 1);
+        }
+        __syncthreads();
+        // 2. group offsets (each thread owns GPT consecutive groups)
+        {
+            int loc[GPT], sum = 0;
+#pragma unroll
+            for (int q = 0; q < GPT; q++) { loc[q] = S.cur[t * GPT + q]; sum += loc[q]; }
+            int tot;
+            int ex = block_excl_scan(sum, S.wsum, &tot);
+#pragma unroll
+            for (int q = 0; q < GPT; q++) { S.goff[t * GPT + q] = ex; S.cur[t * GPT + q] = ex; ex += loc[q]; }
+            if (t == 0) S.goff[NGROUP] = tot;
+        }
+        __syncthreads();
+        for (int e = t; e < E; e += K3_THREADS) {
+            int pos = atomicAdd(&S.cur[S.grp[e]], 1);
+            S.perm[pos] = (unsigned short)e;
+        }
+        __syncthreads();
+
+        // 3. pass 1: within each group, visit distinct determinants in key order
+        int nk = 0;
+        long long rejected = 0;
+        i128 ann = 0;
+        for (int q = 0; q < GPT; q++) {
+            const int g = t * GPT + q, lo = S.goff[g], hi = S.goff[g + 1];
+            int nl = 0;
+            u64 la = 0, lb = 0;
+            bool first = true;
+            while (true) {
+                bool found = false;
+                u64 ba = 0, bb2 = 0;
+                for (int r = lo; r < hi; r++) {
+                    ulonglong2 k = S.key[S.perm[r]];
+                    bool gt = first || key_less(la, lb, k.x, k.y);
+                    if (gt && (!found || key_less(k.x, k.y, ba, bb2))) { found = true; ba = k.x; bb2 = k.y; }
+                }
+                if (!found) break;
+                first = false;
+                la = ba; lb = bb2;
+                int me = -1, leader = -1, ni = 0, nn = 0;
+                i128 Xi = 0, Xn = 0;
+                u128 fi = 0, fn = 0;
+                for (int r = lo; r < hi; r++) {
+                    int e = S.perm[r];
+                    ulonglong2 k = S.key[e];
+                    if (k.x != ba || k.y != bb2) continue;
+                    if (leader < 0) leader = e;
+                    if (e < m) { me = e; continue; }
+                    double w = S.val[e];
+                    if (e < m + si) { Xi += to_fixed(w, I.Fw); fi += fx32(w); ni++; }
+                    else { Xn += to_fixed(w, I.Fw); fn += fx32(w); nn++; }
+                }
+                if (me >= 0) leader = me;
+                const bool present = me >= 0;
+                uint8_t fl = present ? ofl[base + me] : 0;
+                double c0 = present ? S.val[me] : 0.0, cp = 0.0;
+                if (present) {
+                    if (fl & DFLAG_D) {
+                        cp = I.dc_new[d_index(I, ba, bb2)];
+                    } else {
+                        // (b) death: C (1 - tau (H_ii - E_ref - S)), then Eq. (2)
+                        double f = 1.0 - I.tau * (ohd[base + me] - shift);
+                        cp = c0 * f;
+                        if (cp != 0.0 && fabs(cp) < I.cmin) {
+                            u64 w[4];
+                            philox(ba, bb2, (u64)it, (u64)PURPOSE_DEATH, I.seed, 0ULL, w);
+                            cp = round_stoch(cp, I.cmin, u53(w[0]));
+                        }
+                    }
+                }
+                // (c) annihilation with the initiator rule: spawns from
+                // non-initiators survive only onto determinants occupied at
+                // the start of the iteration
+                const bool occ = present && c0 != 0.0;
+                i128 X = Xi;
+                u128 fs = fi;
+                int nacc = ni;
+                if (occ) { X += Xn; fs += fn; nacc += nn; } else rejected += nn;
+                double acc = cp;
+                if (nacc > 0) {
+                    double swsum = fixed_to_double(X, I.Fw);
+                    acc = present ? cp + swsum : swsum;
+                    i128 in = (present ? (i128)fx32(cp) : (i128)0) + (i128)fs;
+                    ann += in - (i128)fx32(acc);
+                    if (!(fl & DFLAG_D) && acc != 0.0 && fabs(acc) < I.cmin) {
+                        u64 w[4];
+                        philox(ba, bb2, (u64)it, (u64)PURPOSE_ANNIH, I.seed, 0ULL, w);
+                        acc = round_stoch(acc, I.cmin, u53(w[0]));
+                    }
+                }
+                const bool keep = acc != 0.0 || (fl & (DFLAG_REF | DFLAG_D));
+                S.val[leader] = acc;
+                S.lead[lo + nl] = (unsigned short)(leader | (keep ? 0x8000 : 0));
+                nl++;
+                nk += keep ? 1 : 0;
+            }
+            S.nlead[g] = (unsigned short)nl;
+        }
+        int total;
+        int o = block_excl_scan(nk, S.wsum, &total);
+        const bool overflow = total > CAP_M;
+        if (overflow && t == 0) atomicOr(&I.st->err, ERRB_MAIN_CAP);
+
+        // 4. pass 2: write the new bucket in (group, key) order; reductions
+        const int np = par ^ 1;
+        ulonglong2 *nkey = I.key[np];
+        double *nc = I.c[np], *nhd = I.hd[np];
+        uint8_t *nfl = I.fl[np];
+        u128 nw = 0;
+        double enm = 0.0;
+        bool bad = false;
+        if (!overflow) {
+            for (int q = 0; q < GPT; q++) {
+                const int g = t * GPT + q, lo = S.goff[g], nl = S.nlead[g];
+                for (int j = 0; j < nl; j++) {
+                    int v = S.lead[lo + j];
+                    if (!(v & 0x8000)) continue;
+                    int L = v & 0x7fff;
+                    ulonglong2 k = S.key[L];
+                    double c = S.val[L];
+                    size_t dst = base + o;
+                    nkey[dst] = k;
+                    nc[dst] = c;
+                    uint8_t f = L < m ? ofl[base + L] : 0;
+                    nfl[dst] = f;
+                    if (L < m) nhd[dst] = ohd[base + L];
+                    else {
+                        int qn = atomicAdd(&S.n_new, 1);
+                        S.perm[qn] = (unsigned short)L;
+                        S.grp[qn] = (unsigned short)o;
+                    }
+                    if (!(fabs(c) < 0x1p31)) bad = true;
+                    else nw += fx32(c);
+                    if (f & DFLAG_REF) I.st->e_den = c;
+                    else {
+                        int lev = __popcll(k.x ^ I.ref_a) + __popcll(k.y ^ I.ref_b);
+                        if (lev <= 4 && c != 0.0) enm = enm + hoff_generic(I, k.x, k.y, I.ref_a, I.ref_b) * c;
+                    }
+                    o++;
+                }
+            }
+        }
+        if (bad) atomicOr(&I.st->err, ERRB_NUMERIC);
+        __syncthreads();
+        // 5. H_jj - E_ref for new determinants, one warp each
+        if (!overflow) {
+            const int nnew = S.n_new;
+            for (int q = warp; q < nnew; q += K3_THREADS / 32) {
+                int L = S.perm[q];
+                ulonglong2 k = S.key[L];
+                double hdv = diag_exact_warp(I, k.x, k.y);
+                if (lane == 0) nhd[base + S.grp[q]] = hdv;
+            }
+        }
+        // 6. bucket reductions (fixed order: lanes by xor tree, warps in index order)
+        for (int mm = 16; mm >= 1; mm >>= 1) {
+            enm = enm + __shfl_xor_sync(0xffffffffu, enm, mm);
+            rejected += __shfl_xor_sync(0xffffffffu, rejected, mm);
+            ann += shfl_xor_i128(ann, mm);
+            nw += (u128)shfl_xor_i128((i128)nw, mm);
+        }
+        if (lane == 0) {
+            S.red_d[warp] = enm;
+            S.red_u[warp][0] = (u64)nw;
+            S.red_u[warp][1] = (u64)(nw >> 64);
+            S.red_u[warp][2] = (u64)ann;
+            S.red_u[warp][3] = (u64)((u128)ann >> 64);
+            S.red_u[warp][4] = (u64)rejected;
+        }
+        __syncthreads();
+        if (t == 0) {
+            double e_sum = 0.0;
+            u128 nws = 0;
+            i128 anns = 0;
+            long long rej = 0;
+            for (int k = 0; k < K3_THREADS / 32; k++) {
+                e_sum = e_sum + S.red_d[k];
+                nws += ((u128)S.red_u[k][1] << 64) | S.red_u[k][0];
+                anns += (i128)(((u128)S.red_u[k][3] << 64) | S.red_u[k][2]);
+                rej += (long long)S.red_u[k][4];
+            }
+            Partial &P = I.part[b];
+            P.nw_lo = (u64)nws;
+            P.nw_hi = (u64)(nws >> 64);
+            P.ann_lo = (u64)anns;
+            P.ann_hi = (u64)((u128)anns >> 64);
+            P.ndet = total;
+            P.rejected = rej;
+            P.spawns = si + sn;
+            P.e_num = e_sum;
+            if (!overflow) I.cnt[np][b] = total;
+            I.scnt_i[b] = 0;
+            I.scnt_n[b] = 0;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ finalize
+__global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restrict__ insts, int n_inst)
+{
+    const DevInst &I = insts[blockIdx.x];
+    IterState *st = I.st;
+    __shared__ int s_err;
+    __shared__ double s_d[K5_THREADS / 32];
+    __shared__ u64 s_u[K5_THREADS / 32][8];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) s_err = *(volatile int *)&st->err;
+    __syncthreads();
+    if (s_err) return;
+    const int nbk = 1 << I.bb;
+    u128 nw = 0;
+    i128 ann = 0;
+    long long ndet = 0, rej = 0, sp = 0, att = 0;
+    double en = 0.0;
+    for (int u = t; u < nbk; u += K5_THREADS) {
+        const Partial &P = I.part[u];
+        nw += ((u128)P.nw_hi << 64) | P.nw_lo;
+        ann += (i128)(((u128)P.ann_hi << 64) | P.ann_lo);
+        ndet += P.ndet; rej += P.rejected; sp += P.spawns; att += P.attempts;
+        en = en + P.e_num;
+    }
+    for (int mm = 16; mm >= 1; mm >>= 1) {
+        en = en + __shfl_xor_sync(0xffffffffu, en, mm);
+        ndet += __shfl_xor_sync(0xffffffffu, ndet, mm);
+        rej += __shfl_xor_sync(0xffffffffu, rej, mm);
+        sp += __shfl_xor_sync(0xffffffffu, sp, mm);
+        att += __shfl_xor_sync(0xffffffffu, att, mm);
+        ann += shfl_xor_i128(ann, mm);
+        nw += (u128)shfl_xor_i128((i128)nw, mm);
+    }
+    if (lane == 0) {
+        s_d[warp] = en;
+        s_u[warp][0] = (u64)nw; s_u[warp][1] = (u64)(nw >> 64);
+        s_u[warp][2] = (u64)ann; s_u[warp][3] = (u64)((u128)ann >> 64);
+        s_u[warp][4] = (u64)ndet; s_u[warp][5] = (u64)rej; s_u[warp][6] = (u64)sp; s_u[warp][7] = (u64)att;
+    }
+    __syncthreads();
+    if (t != 0) return;
+    double e_num = 0.0;
+    u128 W = 0;
+    i128 A = 0;
+    long long nd = 0, rj = 0, sps = 0, at = 0;
+    for (int k = 0; k < K5_THREADS / 32; k++) {
+        e_num = e_num + s_d[k];
+        W += ((u128)s_u[k][1] << 64) | s_u[k][0];
+        A += (i128)(((u128)s_u[k][3] << 64) | s_u[k][2]);
+        nd += (long long)s_u[k][4]; rj += (long long)s_u[k][5]; sps += (long long)s_u[k][6]; at += (long long)s_u[k][7];
+    }
+    const double nwd = u128_to_double(W) * 0x1p-32;
+    const long long it = st->iter;
+    // shift update (Booth, Thom, Alavi 2009)
+    if (!st->vary) {
+        if (nwd >= I.target) {
+            st->vary = 1;
+            st->shift_start = it;
+            st->nwl_lo = (u64)W; st->nwl_hi = (u64)(W >> 64);
+            st->cnt = 0;
+        }
+    } else if (++st->cnt == I.A) {
+        u128 L = ((u128)st->nwl_hi << 64) | st->nwl_lo;
+        double ratio = nwd / (u128_to_double(L) * 0x1p-32);
+        st->S = st->S - I.cz * fq_ln(ratio);
+        st->nwl_lo = (u64)W; st->nwl_hi = (u64)(W >> 64);
+        st->cnt = 0;
+    }
+    if (!(st->S == st->S) || !(nwd == nwd)) st->err |= ERRB_NUMERIC;
+    fciqmc_iter_stats &R = I.ring[it % I.ring_cap];
+    R.iteration = it; R.nw = nwd; R.shift = st->S; R.e_num = e_num; R.e_den = st->e_den;
+    R.ndet = nd; R.attempts = at; R.spawns = sps; R.rejected = rj;
+    R.annihilated = i128_to_double(A) * 0x1p-32; R.vary = st->vary; R.pad0 = 0;
+    st->iter = it + 1;
+    st->parity ^= 1;
+    st->heavy_n = 0;
+    if (I.semi_size > 0 && !st->semi_built && st->vary && it + 1 == st->shift_start + I.semi_start)
+        st->err |= ERRB_PAUSE_SEMI;
+}
+
+// ------------------------------------------------------------------ growth and import
+// split every bucket of src (bb bits) into two buckets of dst (bb+1 bits)
+__global__ void k_rebucket(const DevInst *__restrict__ src, const DevInst *__restrict__ dst, int nb_src, int par)
+{
+    for (int b = blockIdx.x; b < nb_src; b += gridDim.x) {
+        const int m = src->cnt[par][b];
+        for (int e = threadIdx.x; e < m; e += blockDim.x) {
+            size_t o = (size_t)b * CAP_M + e;
+            ulonglong2 k = src->key[par][o];
+            int nbk = bucket_of(det_hash(k.x, k.y), dst->bb);
+            int slot = atomicAdd(dst->cnt[par] + nbk, 1);
+            if (slot >= CAP_M) { atomicOr(&dst->st->err, ERRB_MAIN_CAP); continue; }
+            size_t d = (size_t)nbk * CAP_M + slot;
+            dst->key[par][d] = k;
+            dst->c[par][d] = src->c[par][o];
+            dst->hd[par][d] = src->hd[par][o];
+            dst->fl[par][d] = src->fl[par][o];
+        }
+    }
+}
+
+// H_ii - E_ref and reference flags for every determinant of buffer par
+__global__ void k_diag(const DevInst *__restrict__ I, int par, int nb)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int b = gw; b < nb; b += nw) {
+        const int m = I->cnt[par][b];
+        for (int e = 0; e < m; e++) {
+            size_t o = (size_t)b * CAP_M + e;
+            ulonglong2 k = I->key[par][o];
+            double hdv = diag_exact_warp(*I, k.x, k.y);
+            if (lane == 0) {
+                I->hd[par][o] = hdv;
+                uint8_t f = I->fl[par][o] & DFLAG_D;
+                if (k.x == I->ref_a && k.y == I->ref_b) f |= DFLAG_REF;
+                I->fl[par][o] = f;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+static int g_num_sms = 0;
+static int num_sms()
+{
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    return g_num_sms;
+}
+
+void launch_spawn(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, cudaStream_t s)
+{
+    int grid = n_units < num_sms() * 8 ? n_units : num_sms() * 8;
+    if (grid < 1) grid = 1;
+    k_spawn<<<grid, K1_THREADS, 0, s>>>(dinst, unit_start, n_inst, n_units);
+}
+
+void launch_spawn_heavy(const DevInst *dinst, int n_inst, cudaStream_t s)
+{
+    k_spawn_heavy<<<num_sms() * 4, K1_THREADS, 0, s>>>(dinst, n_inst);
+}
+
+cudaError_t launch_annihilate(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, cudaStream_t s)
+{
+    static bool attr = false;
+    const size_t smem = sizeof(K3Smem);
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_annihilate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    int grid = n_units < num_sms() * 2 ? n_units : num_sms() * 2;
+    if (grid < 1) grid = 1;
+    k_annihilate<<<grid, K3_THREADS, smem, s>>>(dinst, unit_start, n_inst, n_units);
+    return cudaGetLastError();
+}
+
+void launch_finalize(const DevInst *dinst, int n_inst, cudaStream_t s)
+{
+    k_finalize<<<n_inst, K5_THREADS, 0, s>>>(dinst, n_inst);
+}
+
+void launch_rebucket(const DevInst *src, const DevInst *dst, int nb_src, int parity, cudaStream_t s)
+{
+    int grid = nb_src < num_sms() * 8 ? nb_src : num_sms() * 8;
+    k_rebucket<<<grid, 256, 0, s>>>(src, dst, nb_src, parity);
+}
+
+void launch_diag(const DevInst *dinst, int parity, int nb, cudaStream_t s)
+{
+    int warps = nb;
+    int blocks = (warps * 32 + 255) / 256;
+    if (blocks > num_sms() * 16) blocks = num_sms() * 16;
+    if (blocks < 1) blocks = 1;
+    k_diag<<<blocks, 256, 0, s>>>(dinst, parity, nb);
+}
+
+u64 det_hash_host(u64 a, u64 b) { return det_hash(a, b); }
+
+}  // namespace fq

@@ -1,0 +1,201 @@
+"""GPU path against the CPU oracle (needs a GB300).
+
+Both sides run the same seeded system and parameters.  Determinant keys,
+amplitudes, H_ii - E_ref, flags, walker numbers, shifts and every counter must
+agree bit for bit: every random decision is keyed by (determinant, iteration,
+attempt), every multi-term sum that feeds the dynamics is an exact sum rounded
+once, and both sides evaluate the remaining binary64 expressions in the same
+order without fused multiply-adds.  Only E_num (Eq. (8)), a diagnostic that
+does not feed back, is summed in a different order on the two sides; it is
+compared within 1e-11 relative (each side's rounding error is below
+n * 2^-53 * sum |terms| with n <= 1e4 terms per bucket tree level).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+EXACT_STATS = ["iteration", "nw", "shift", "ndet", "attempts", "spawns", "rejected", "annihilated", "e_den", "vary"]
+
+
+def _fq():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2006_14956_gb300 as fq
+    return fq
+
+
+def bits(x):
+    return np.ascontiguousarray(x, np.float64).view(np.uint64)
+
+
+def assert_states_equal(g, o):
+    assert g["alpha"].size == o["alpha"].size, (g["alpha"].size, o["alpha"].size)
+    np.testing.assert_array_equal(g["alpha"], o["alpha"])
+    np.testing.assert_array_equal(g["beta"], o["beta"])
+    np.testing.assert_array_equal(bits(g["c"]), bits(o["c"]))
+    np.testing.assert_array_equal(bits(g["hdiag"]), bits(o["hdiag"]))
+    np.testing.assert_array_equal(g["flags"], o["flags"])
+
+
+def assert_stats_equal(gs, os_, first=0):
+    n = len(os_["iter"]) - first
+    assert len(gs["iteration"]) >= n
+    for k in EXACT_STATS:
+        ok = "iter" if k == "iteration" else k
+        a = np.asarray(gs[k][-n:])
+        b = np.asarray(os_[ok][first:])
+        if a.dtype.kind == "f":
+            np.testing.assert_array_equal(bits(a), bits(b), err_msg=k)
+        else:
+            np.testing.assert_array_equal(a, b, err_msg=k)
+    en_g, en_o = np.asarray(gs["e_num"][-n:]), np.asarray(os_["e_num"][first:])
+    np.testing.assert_allclose(en_g, en_o, rtol=1e-11, atol=1e-9)
+
+
+def run_pair(sysd, params, n_iter, chunks=1):
+    fq = _fq()
+    g = fq.fciqmc_create(sysd, params)
+    o = oracle.Run(oracle.system_from_workload(sysd), **params)
+    per = n_iter // chunks
+    for _ in range(chunks):
+        fq.fciqmc_step(g, per)
+        o.step(per)
+    return fq, g, o
+
+
+CASES = {
+    "hubbard_ring_8": (workloads.hubbard_1d(8, 1.0, 4.0),
+                       dict(tau=0.01, target_walkers=2000, initial_walkers=10.0, seed=1), 500),
+    "hubbard_4x4_initiator": (workloads.hubbard_2d(4, 4, 4.0),
+                              dict(tau=0.005, target_walkers=5000, initiator_threshold=3.0, seed=7), 300),
+    "hubbard_3x4_open": (dict(workloads.hubbard_2d(3, 4, 8.0), periodic_x=False),
+                         dict(tau=0.004, target_walkers=3000, initiator_threshold=3.0, seed=3), 250),
+    "abinitio_8_3_3": (workloads.small_abinitio(8, 3, 3, seed=5),
+                       dict(tau=0.005, target_walkers=3000, initiator_threshold=3.0, seed=11), 300),
+    "abinitio_8_4_2_plain": (workloads.small_abinitio(8, 4, 2, seed=6),
+                             dict(tau=0.004, target_walkers=2000, initiator_threshold=0.0, seed=12), 250),
+    "abinitio_cmin_half": (workloads.small_abinitio(7, 3, 2, seed=8),
+                           dict(tau=0.004, target_walkers=1500, c_min=0.5, initiator_threshold=2.0, seed=5), 200),
+    "abinitio_cmin_two": (workloads.small_abinitio(7, 2, 3, seed=9),
+                          dict(tau=0.004, target_walkers=1500, c_min=2.0, initiator_threshold=3.0, seed=6), 200),
+    "single_electron": (workloads.small_abinitio(6, 1, 0, seed=10),
+                        dict(tau=0.01, target_walkers=500, seed=2), 150),
+    "doubles_only": (workloads.small_abinitio(7, 2, 2, seed=13),
+                     dict(tau=0.004, target_walkers=1500, p_single=0.0, initiator_threshold=3.0, seed=8), 150),
+    "singles_only": (workloads.small_abinitio(7, 2, 2, seed=14),
+                     dict(tau=0.004, target_walkers=1500, p_single=1.0, seed=9), 150),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_gpu_matches_oracle_bit_exact(name):
+    sysd, params, n = CASES[name]
+    fq, g, o = run_pair(sysd, params, n, chunks=2)
+    assert_states_equal(fq.fciqmc_export_state(g), o.export())
+    assert_stats_equal(fq.fciqmc_iter_stats_get(g), o.stats())
+    sh = fq.fciqmc_export_shift(g)
+    osh = o.shift_state()
+    assert sh["S"] == osh["S"] and sh["vary"] == osh["vary"] and sh["nw_last"] == osh["nw_last"]
+
+
+def test_abinitio_24_orbitals_bit_exact():
+    """The 24-orbital, 6+6-electron synthetic system (96 Cholesky vectors,
+    initiator threshold 3, tau 1e-3) at a reduced walker target."""
+    sysd, params = workloads.config_abinitio_24()
+    params = dict(params, target_walkers=2e4)
+    fq, g, o = run_pair(sysd, params, 160, chunks=2)
+    assert_states_equal(fq.fciqmc_export_state(g), o.export())
+    assert_stats_equal(fq.fciqmc_iter_stats_get(g), o.stats())
+
+
+def test_heavy_determinants_bit_exact():
+    """A reference with 3e5 walkers takes the sliced heavy-determinant path."""
+    sysd = workloads.small_abinitio(8, 3, 3, seed=21)
+    params = dict(tau=0.002, target_walkers=1e9, initial_walkers=3e5, initiator_threshold=3.0, seed=4)
+    fq, g, o = run_pair(sysd, params, 6)
+    assert_states_equal(fq.fciqmc_export_state(g), o.export())
+    assert_stats_equal(fq.fciqmc_iter_stats_get(g), o.stats())
+    assert o.stats()["attempts"][0] >= 3e5
+
+
+def test_capacity_growth_is_bit_identical():
+    """Starting from one bucket, the list outgrows its buffers several times;
+    each overflowing iteration is repeated after growth with identical results."""
+    fq = _fq()
+    sysd = workloads.hubbard_2d(4, 4, 2.0)
+    params = dict(tau=0.005, target_walkers=3e4, initiator_threshold=3.0, seed=17, max_dets=16)
+    g = fq.fciqmc_create(sysd, params)
+    assert fq.fciqmc_layout(g)["buckets"] == 1
+    o = oracle.Run(oracle.system_from_workload(sysd), **{k: v for k, v in params.items() if k != "max_dets"})
+    fq.fciqmc_step(g, 300)
+    o.step(300)
+    assert fq.fciqmc_layout(g)["buckets"] > 1
+    assert_states_equal(fq.fciqmc_export_state(g), o.export())
+    assert_stats_equal(fq.fciqmc_iter_stats_get(g), o.stats())
+
+
+def test_checkpoint_restart_continues_identically():
+    fq = _fq()
+    sysd, params = workloads.small_abinitio(8, 3, 3, seed=5), dict(tau=0.005, target_walkers=3000,
+                                                                    initiator_threshold=3.0, seed=11)
+    g1 = fq.fciqmc_create(sysd, params)
+    fq.fciqmc_step(g1, 200)
+    st = fq.fciqmc_export_state(g1)
+    sh = fq.fciqmc_export_shift(g1)
+    g2 = fq.fciqmc_create(sysd, params)
+    fq.fciqmc_import_state(g2, st["alpha"], st["beta"], st["c"], sh["iteration"], sh["S"], sh["vary"],
+                           sh["shift_start"], sh["cnt"], sh["nw_last"])
+    o = oracle.Run(oracle.system_from_workload(sysd), **params)
+    o.import_state(st["alpha"], st["beta"], st["c"], sh["iteration"], sh["S"], sh["vary"], sh["shift_start"],
+                   sh["cnt"], sh["nw_last"])
+    assert_states_equal(fq.fciqmc_export_state(g2), o.export())
+    fq.fciqmc_step(g1, 50)
+    fq.fciqmc_step(g2, 50)
+    o.step(50)
+    s1, s2 = fq.fciqmc_export_state(g1), fq.fciqmc_export_state(g2)
+    assert_states_equal(s1, s2)
+    assert_states_equal(s2, o.export())
+
+
+def test_energy_within_3sigma_of_exact_diagonalisation():
+    """8-site Hubbard ring, U=4, plain FCIQMC (n_a = 0), 2000 iterations at
+    1e4 walkers: E_proj within 3 sigma of the exact ground state."""
+    fq = _fq()
+    sysd, params = workloads.config_hubbard_ring()
+    s = oracle.system_from_workload(sysd)
+    e0, _, _ = s.exact_ground_state()
+    g = fq.fciqmc_create(sysd, dict(params, initial_shift=e0 + 0.3, initial_walkers=500.0))
+    fq.fciqmc_step(g, 2500)
+    en = fq.fciqmc_energy(g)
+    assert en["n_samples"] > 1000
+    assert abs(en["e_proj_mean"] - (e0 + s.eref)) < 3.0 * en["e_proj_sigma"] + 1e-9, en
+    assert en["e_proj_sigma"] < 0.05
+
+
+def test_full_size_sampled_parity_abinitio_24():
+    """At the full 1e6-walker size of the 24-orbital system, in the launch
+    configuration the benchmark times: the GPU state after equilibration is
+    handed to the oracle, and one further iteration must agree bit for bit
+    over the whole list."""
+    fq = _fq()
+    sysd, params = workloads.config_abinitio_24()
+    g = fq.fciqmc_create(sysd, dict(params, initial_walkers=1e6))
+    fq.fciqmc_step(g, 300)
+    st = fq.fciqmc_export_state(g)
+    sh = fq.fciqmc_export_shift(g)
+    assert st["c"].size > 1e5
+    o = oracle.Run(oracle.system_from_workload(sysd), **dict(params, initial_walkers=1e6))
+    o.import_state(st["alpha"], st["beta"], st["c"], sh["iteration"], sh["S"], sh["vary"], sh["shift_start"],
+                   sh["cnt"], sh["nw_last"])
+    fq.fciqmc_step(g, 1)
+    o.step(1)
+    assert_states_equal(fq.fciqmc_export_state(g), o.export())
+    gs = fq.fciqmc_iter_stats_get(g)
+    os_ = o.stats()
+    for k in ["nw", "shift", "ndet", "attempts", "spawns", "rejected", "annihilated"]:
+        assert bits(gs[k][-1:])[0] == bits(os_[k][-1:])[0] if gs[k].dtype.kind == "f" else gs[k][-1] == os_[k][-1], k
