@@ -187,7 +187,7 @@ static double pgen_class(const fciqmc_handle *h, int c)
 static int alloc_layout(fciqmc_handle *h, DevInst &I, int bb)
 {
     const size_t nbk = (size_t)1 << bb;
-    const size_t nm = nbk * CAP_M, ns = nbk * CAP_S;
+    const size_t nm = nbk * CAP_M, ns = nbk * (size_t)I.cap_s;
     for (int k = 0; k < 2; k++) {
         I.key[k] = (ulonglong2 *)dev_alloc(h, nm * sizeof(ulonglong2));
         I.c[k] = (double *)dev_alloc(h, nm * sizeof(double));
@@ -202,7 +202,8 @@ static int alloc_layout(fciqmc_handle *h, DevInst &I, int bb)
     I.scnt_i = (int *)dev_alloc(h, nbk * sizeof(int));
     I.scnt_n = (int *)dev_alloc(h, nbk * sizeof(int));
     I.part = (Partial *)dev_alloc(h, nbk * sizeof(Partial));
-    if (!I.skey || !I.sw || !I.scnt_i || !I.scnt_n || !I.part) return FCIQMC_ERR_OUT_OF_MEMORY;
+    I.big_list = (int *)dev_alloc(h, nbk * sizeof(int));
+    if (!I.skey || !I.sw || !I.scnt_i || !I.scnt_n || !I.part || !I.big_list) return FCIQMC_ERR_OUT_OF_MEMORY;
     cudaMemsetAsync(I.scnt_i, 0, nbk * sizeof(int), h->stream);
     cudaMemsetAsync(I.scnt_n, 0, nbk * sizeof(int), h->stream);
     cudaMemsetAsync(I.part, 0, nbk * sizeof(Partial), h->stream);
@@ -218,7 +219,8 @@ static void free_layout(fciqmc_handle *h, DevInst &I)
         I.key[k] = nullptr; I.c[k] = nullptr; I.hd[k] = nullptr; I.fl[k] = nullptr; I.cnt[k] = nullptr;
     }
     dev_free(h, I.skey); dev_free(h, I.sw); dev_free(h, I.scnt_i); dev_free(h, I.scnt_n); dev_free(h, I.part);
-    I.skey = nullptr; I.sw = nullptr; I.scnt_i = nullptr; I.scnt_n = nullptr; I.part = nullptr;
+    dev_free(h, I.big_list);
+    I.skey = nullptr; I.sw = nullptr; I.scnt_i = nullptr; I.scnt_n = nullptr; I.part = nullptr; I.big_list = nullptr;
 }
 
 static int upload_inst(fciqmc_handle *h)
@@ -242,6 +244,7 @@ static int enqueue_iteration(fciqmc_handle *h, cudaEvent_t *ev)
     if (ev) cudaEventRecord(ev[3], h->stream);
     cudaError_t e = launch_annihilate(h->dinst, h->dunit, 1, units, h->stream);
     if (e != cudaSuccess) return fail(h, FCIQMC_ERR_CUDA, std::string("annihilation launch: ") + cudaGetErrorString(e));
+    launch_annihilate_big(h->dinst, 1, h->stream);
     if (ev) cudaEventRecord(ev[4], h->stream);
     launch_finalize(h->dinst, 1, h->stream);
     if (ev) cudaEventRecord(ev[5], h->stream);
@@ -302,6 +305,30 @@ static int grow_buckets(fciqmc_handle *h)
     return FCIQMC_OK;
 }
 
+// larger spawn regions per bucket; buckets that no longer fit in shared
+// memory are annihilated from a global scratch slice per block
+static int grow_spawn_capacity(fciqmc_handle *h)
+{
+    DevInst &I = h->hi;
+    const size_t nbk = (size_t)1 << h->bb;
+    const int ncap = I.cap_s * 2;
+    if ((size_t)ncap * nbk > ((size_t)1 << 33)) return fail(h, FCIQMC_ERR_CAPACITY, "spawn buffer limit reached");
+    ulonglong2 *nk = (ulonglong2 *)dev_alloc(h, nbk * (size_t)ncap * sizeof(ulonglong2));
+    double *nw = (double *)dev_alloc(h, nbk * (size_t)ncap * sizeof(double));
+    const int Ecap = CAP_M + ncap;
+    int gbits = GBITS;
+    while ((1 << gbits) < Ecap) gbits++;
+    const int G = 1 << gbits;
+    size_t stride = (size_t)Ecap * (sizeof(ulonglong2) + sizeof(double) + 12) + (size_t)(3 * G + 1) * 4;
+    stride = (stride + 255) & ~(size_t)255;
+    unsigned char *scr = (unsigned char *)dev_alloc(h, stride * BIG_BLOCKS);
+    if (!nk || !nw || !scr) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (spawn buffers)");
+    dev_free(h, I.skey); dev_free(h, I.sw); dev_free(h, I.big_scratch);
+    I.skey = nk; I.sw = nw; I.cap_s = ncap;
+    I.big_scratch = scr; I.big_stride = stride; I.big_gbits = gbits;
+    return FCIQMC_OK;
+}
+
 static int grow_heavy(fciqmc_handle *h)
 {
     int ncap = h->heavy_cap * 4;
@@ -321,6 +348,7 @@ static int reset_after_error(fciqmc_handle *h)
     CUDA_TRY(h, cudaMemsetAsync(h->hi.scnt_n, 0, nbk * sizeof(int), h->stream));
     h->hst.err = 0;
     h->hst.heavy_n = 0;
+    h->hst.big_n = 0;
     return write_state(h);
 }
 
@@ -466,6 +494,10 @@ int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_han
         return bail(FCIQMC_ERR_UNSUPPORTED, "c_min outside the supported range (about 1e-9 .. 1e9)");
 
     // device, stream
+    if (init_kernels() != cudaSuccess) {
+        cudaGetLastError();
+        return bail(FCIQMC_ERR_CUDA, "no usable CUDA device (kernel attribute setup failed)");
+    }
     if (P.stream) h->stream = (cudaStream_t)P.stream;
     else {
         if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -541,6 +573,7 @@ int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_han
     double dets_hint = P.max_dets > 0 ? (double)P.max_dets : std::max(4096.0, 2.0 * P.target_walkers);
     int bb = 0;
     while (((double)(1LL << bb)) * 640.0 < dets_hint && bb < 24) bb++;
+    I.cap_s = CAP_S0;
     int rc = alloc_layout(h, I, bb);
     if (rc) return bail(rc, "out of device memory (walker buffers)");
     h->bb = bb;
@@ -591,7 +624,7 @@ int fciqmc_kernel_times(fciqmc_handle *h, double out[5])
 int fciqmc_layout(fciqmc_handle *h, int64_t out[4])
 {
     if (!h || !out) return FCIQMC_ERR_INVALID_ARG;
-    out[0] = 1LL << h->bb; out[1] = CAP_M; out[2] = CAP_S; out[3] = (int64_t)h->bytes;
+    out[0] = 1LL << h->bb; out[1] = CAP_M; out[2] = h->hi.cap_s; out[3] = (int64_t)h->bytes;
     return FCIQMC_OK;
 }
 
@@ -650,7 +683,11 @@ int fciqmc_step(fciqmc_handle *h, int64_t n_iter)
         rc = reset_after_error(h);
         if (rc) return rc;
         if (err & (ERRB_SPAWN_CAP | ERRB_MAIN_CAP)) {
-            rc = grow_buckets(h);
+            // split buckets when the list itself is crowded; otherwise a few
+            // determinants receive many spawns and the spawn regions grow
+            long long ndet = h->hist.empty() ? 1 : h->hist.back().ndet;
+            bool crowded = (err & ERRB_MAIN_CAP) || ndet > (long long)(1LL << h->bb) * (CAP_M / 2);
+            rc = crowded ? grow_buckets(h) : grow_spawn_capacity(h);
             if (rc) return rc;
             rc = reset_after_error(h);
             if (rc) return rc;

@@ -153,6 +153,7 @@ __device__ __forceinline__ i128 shfl_xor_i128(i128 v, int m)
 // s = (m-1)/(m+1); the atanh series is summed in Horner form to z^11, z = s^2.
 __device__ double fq_ln(double x)
 {
+    if (!(x > 0.0) || isinf(x)) return __longlong_as_double(0x7ff8000000000000LL);
     u64 bits = (u64)__double_as_longlong(x);
     int k;
     if (((bits >> 52) & 0x7ff) == 0) {

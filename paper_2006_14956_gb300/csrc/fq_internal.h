@@ -33,7 +33,8 @@ constexpr unsigned HEAVY_ATT = 2048;  // attempts per heavy chunk
 constexpr int K3_THREADS = 256;
 constexpr int EMAX = 3072;            // main + spawned records staged per bucket
 constexpr int CAP_M = 1536;           // main-list capacity per bucket
-constexpr int CAP_S = EMAX - CAP_M;   // spawn capacity per bucket
+constexpr int CAP_S0 = EMAX - CAP_M;  // initial spawn capacity per bucket (grows at run time)
+constexpr int BIG_BLOCKS = 64;        // blocks of the large-bucket annihilation kernel
 constexpr int GBITS = 11;             // sub-hash groups per bucket in the annihilation sort
 constexpr int NGROUP = 1 << GBITS;
 constexpr int K5_THREADS = 1024;
@@ -66,7 +67,9 @@ struct IterState {  // device-resident iteration state of one run
     int heavy_n;
     double e_den;
     long long semi_built;   // 1 once D exists
-    long long pad[4];
+    int big_n;              // buckets deferred to the large-bucket kernel
+    int pad0;
+    long long pad[3];
 };
 
 // one run as seen by the kernels
@@ -106,6 +109,11 @@ struct DevInst {
     double *sw;
     int *scnt_i;
     int *scnt_n;
+    int cap_s;              // spawn capacity per bucket
+    int big_gbits;          // sub-hash bits of the large-bucket path
+    int *big_list;          // deferred bucket ids (capacity = buckets)
+    unsigned char *big_scratch;  // BIG_BLOCKS slices of big_stride bytes
+    size_t big_stride;
     HeavyChunk *heavy;
     int heavy_cap;
     Partial *part;
@@ -119,6 +127,7 @@ struct DevInst {
     const int *dcol;
     const double *dval;
     double *dc_new;         // C_D after the exact projection of this iteration
+    double *dc_cur;         // C_D after the last completed iteration
     const u64 *dhash_keys;  // open-addressing set of D keys (a, b interleaved), size dhash_cap
     int dhash_bits;
 };
@@ -128,6 +137,9 @@ void launch_spawn(const DevInst *dinst, const int *unit_start, int n_inst, int n
 void launch_spawn_heavy(const DevInst *dinst, int n_inst, cudaStream_t s);
 void launch_semistoch(const DevInst *dinst, int n_inst, int max_nd, cudaStream_t s);
 cudaError_t launch_annihilate(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, cudaStream_t s);
+cudaError_t init_kernels();
+size_t annihilate_smem_bytes();
+void launch_annihilate_big(const DevInst *dinst, int n_inst, cudaStream_t s);
 void launch_finalize(const DevInst *dinst, int n_inst, cudaStream_t s);
 void launch_rebucket(const DevInst *src, const DevInst *dst, int nb_src, int parity, cudaStream_t s);
 void launch_diag(const DevInst *dinst, int parity, int nb, cudaStream_t s);

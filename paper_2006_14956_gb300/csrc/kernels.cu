@@ -141,18 +141,19 @@ __device__ void do_attempt(const DevInst &I, long long it, u64 pa, u64 pb, doubl
     if (!(fabs(ws) < 0x1p31)) { atomicOr(&I.st->err, ERRB_NUMERIC); return; }
     if ((flags & 2u) && in_D(I, ta, tb)) return;  // D -> D is applied exactly
     int bt = bucket_of(det_hash(ta, tb), I.bb);
+    const int cap_s = I.cap_s;
     if (flags & 1u) {
         int s = atomicAdd(I.scnt_i + bt, 1);
-        if (s < CAP_S) {
-            size_t o = (size_t)bt * CAP_S + s;
+        if (s < cap_s) {
+            size_t o = (size_t)bt * cap_s + s;
             I.skey[o] = make_ulonglong2(ta, tb);
             I.sw[o] = ws;
         }
     } else {
         int s = atomicAdd(I.scnt_n + bt, 1);
-        int slot = CAP_S - 1 - s;
+        int slot = cap_s - 1 - s;
         if (slot >= 0) {
-            size_t o = (size_t)bt * CAP_S + slot;
+            size_t o = (size_t)bt * cap_s + slot;
             I.skey[o] = make_ulonglong2(ta, tb);
             I.sw[o] = ws;
         }
@@ -307,15 +308,22 @@ __global__ void __launch_bounds__(K1_THREADS) k_spawn_heavy(const DevInst *__res
 }
 
 // ------------------------------------------------------------------ annihilation
-struct K3Smem {
-    ulonglong2 key[EMAX];
-    double val[EMAX];
-    unsigned short perm[EMAX];
-    unsigned short lead[EMAX];  // leaders of each group in key order; bit 15 = kept
-    unsigned short grp[EMAX];
-    int goff[NGROUP + 1];
-    int cur[NGROUP];
-    unsigned short nlead[NGROUP];
+// Staging arrays of one bucket: in shared memory (IDX = 16-bit) for buckets
+// of at most EMAX records, in a global scratch slice (IDX = 32-bit) for the
+// rare larger ones (a determinant that receives thousands of spawns).
+template <typename IDX>
+struct Stage {
+    ulonglong2 *key;
+    double *val;
+    IDX *perm;
+    IDX *lead;   // leaders of each group in key order; top bit = kept
+    IDX *grp;
+    IDX *goff;
+    int *cur;
+    IDX *nlead;
+};
+
+struct K3Shared {
     int wsum[K3_THREADS / 32];
     double red_d[K3_THREADS / 32];
     u64 red_u[K3_THREADS / 32][8];
@@ -323,6 +331,18 @@ struct K3Smem {
     int hdr_err, hdr_par;
     long long hdr_it;
     double hdr_S;
+};
+
+struct K3Smem {
+    K3Shared sh;
+    ulonglong2 key[EMAX];
+    double val[EMAX];
+    unsigned short perm[EMAX];
+    unsigned short lead[EMAX];
+    unsigned short grp[EMAX];
+    unsigned short goff[NGROUP + 1];
+    int cur[NGROUP];
+    unsigned short nlead[NGROUP];
 };
 
 __device__ __forceinline__ bool key_less(u64 a1, u64 b1, u64 a2, u64 b2) { return a1 < a2 || (a1 == a2 && b1 < b2); }
@@ -365,13 +385,248 @@ __device__ __forceinline__ int block_excl_scan(int v, int *wsum, int *total)
     return r;
 }
 
+// Death, annihilation and the reductions of one bucket b (steps (b) and (c)
+// of Eq. (3)).  All threads of the block call this together.
+template <typename IDX>
+__device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int gbits, int b, int par, long long it,
+                            double shift, int m, int si, int sn)
+{
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const IDX KEEP = (IDX)1 << (8 * sizeof(IDX) - 1);
+    const int G = 1 << gbits, GPT = G / K3_THREADS;
+    const int E = m + si + sn, cap_s = I.cap_s;
+    const size_t base = (size_t)b * CAP_M, sbase = (size_t)b * cap_s;
+    const int shift_g = 64 - I.bb - gbits;
+    const ulonglong2 *okey = I.key[par];
+    const double *oc = I.c[par], *ohd = I.hd[par];
+    const uint8_t *ofl = I.fl[par];
+
+    // 1. stage the bucket: walkers [0, m), initiator spawns [m, m+si),
+    //    other spawns [m+si, E); histogram of the sub-hash groups
+    for (int g = t; g < G; g += K3_THREADS) W.cur[g] = 0;
+    if (t == 0) S.n_new = 0;
+    __syncthreads();
+    for (int e = t; e < E; e += K3_THREADS) {
+        ulonglong2 k;
+        double v;
+        if (e < m) { k = okey[base + e]; v = oc[base + e]; }
+        else if (e < m + si) { k = I.skey[sbase + (e - m)]; v = I.sw[sbase + (e - m)]; }
+        else { int slot = cap_s - 1 - (e - m - si); k = I.skey[sbase + slot]; v = I.sw[sbase + slot]; }
+        W.key[e] = k;
+        W.val[e] = v;
+        int g = (int)((det_hash(k.x, k.y) >> shift_g) & (u64)(G - 1));
+        W.grp[e] = (IDX)g;
+        atomicAdd(&W.cur[g], 1);
+    }
+    __syncthreads();
+    // 2. group offsets (each thread owns GPT consecutive groups)
+    {
+        int sum = 0;
+        for (int q = 0; q < GPT; q++) sum += W.cur[t * GPT + q];
+        int tot;
+        int ex = block_excl_scan(sum, S.wsum, &tot);
+        for (int q = 0; q < GPT; q++) {
+            int c = W.cur[t * GPT + q];
+            W.goff[t * GPT + q] = (IDX)ex;
+            W.cur[t * GPT + q] = ex;
+            ex += c;
+        }
+        if (t == 0) W.goff[G] = (IDX)tot;
+    }
+    __syncthreads();
+    for (int e = t; e < E; e += K3_THREADS) {
+        int pos = atomicAdd(&W.cur[W.grp[e]], 1);
+        W.perm[pos] = (IDX)e;
+    }
+    __syncthreads();
+
+    // 3. pass 1: within each group, visit distinct determinants in key order
+    int nk = 0;
+    long long rejected = 0;
+    i128 ann = 0;
+    for (int q = 0; q < GPT; q++) {
+        const int g = t * GPT + q, lo = W.goff[g], hi = W.goff[g + 1];
+        int nl = 0;
+        u64 la = 0, lb = 0;
+        bool first = true;
+        while (true) {
+            bool found = false;
+            u64 ba = 0, bb2 = 0;
+            for (int r = lo; r < hi; r++) {
+                ulonglong2 k = W.key[W.perm[r]];
+                bool gt = first || key_less(la, lb, k.x, k.y);
+                if (gt && (!found || key_less(k.x, k.y, ba, bb2))) { found = true; ba = k.x; bb2 = k.y; }
+            }
+            if (!found) break;
+            first = false;
+            la = ba; lb = bb2;
+            int me = -1, leader = -1, ni = 0, nn = 0;
+            i128 Xi = 0, Xn = 0;
+            u128 fi = 0, fn = 0;
+            for (int r = lo; r < hi; r++) {
+                int e = W.perm[r];
+                ulonglong2 k = W.key[e];
+                if (k.x != ba || k.y != bb2) continue;
+                if (leader < 0) leader = e;
+                if (e < m) { me = e; continue; }
+                double w = W.val[e];
+                if (e < m + si) { Xi += to_fixed(w, I.Fw); fi += fx32(w); ni++; }
+                else { Xn += to_fixed(w, I.Fw); fn += fx32(w); nn++; }
+            }
+            if (me >= 0) leader = me;
+            const bool present = me >= 0;
+            uint8_t fl = present ? ofl[base + me] : 0;
+            double c0 = present ? W.val[me] : 0.0, cp = 0.0;
+            if (present) {
+                if (fl & DFLAG_D) {
+                    cp = I.dc_new[d_index(I, ba, bb2)];
+                } else {
+                    // (b) death: C (1 - tau (H_ii - E_ref - S)), then Eq. (2)
+                    double f = 1.0 - I.tau * (ohd[base + me] - shift);
+                    cp = c0 * f;
+                    if (cp != 0.0 && fabs(cp) < I.cmin) {
+                        u64 w[4];
+                        philox(ba, bb2, (u64)it, (u64)PURPOSE_DEATH, I.seed, 0ULL, w);
+                        cp = round_stoch(cp, I.cmin, u53(w[0]));
+                    }
+                }
+            }
+            // (c) annihilation with the initiator rule: spawns from
+            // non-initiators survive only onto determinants occupied at the
+            // start of the iteration
+            const bool occ = present && c0 != 0.0;
+            i128 X = Xi;
+            u128 fs = fi;
+            int nacc = ni;
+            if (occ) { X += Xn; fs += fn; nacc += nn; } else rejected += nn;
+            double acc = cp;
+            if (nacc > 0) {
+                double swsum = fixed_to_double(X, I.Fw);
+                acc = present ? cp + swsum : swsum;
+                i128 in = (present ? (i128)fx32(cp) : (i128)0) + (i128)fs;
+                ann += in - (i128)fx32(acc);
+                if (!(fl & DFLAG_D) && acc != 0.0 && fabs(acc) < I.cmin) {
+                    u64 w[4];
+                    philox(ba, bb2, (u64)it, (u64)PURPOSE_ANNIH, I.seed, 0ULL, w);
+                    acc = round_stoch(acc, I.cmin, u53(w[0]));
+                }
+            }
+            const bool keep = acc != 0.0 || (fl & (DFLAG_REF | DFLAG_D));
+            W.val[leader] = acc;
+            W.lead[lo + nl] = (IDX)leader | (keep ? KEEP : (IDX)0);
+            nl++;
+            nk += keep ? 1 : 0;
+        }
+        W.nlead[g] = (IDX)nl;
+    }
+    int total;
+    int o = block_excl_scan(nk, S.wsum, &total);
+    const bool overflow = total > CAP_M;
+    if (overflow && t == 0) atomicOr(&I.st->err, ERRB_MAIN_CAP);
+
+    // 4. pass 2: write the new bucket in (group, key) order; reductions
+    const int np = par ^ 1;
+    ulonglong2 *nkey = I.key[np];
+    double *nc = I.c[np], *nhd = I.hd[np];
+    uint8_t *nfl = I.fl[np];
+    u128 nw = 0;
+    double enm = 0.0;
+    bool bad = false;
+    if (!overflow) {
+        for (int q = 0; q < GPT; q++) {
+            const int g = t * GPT + q, lo = W.goff[g], nl = W.nlead[g];
+            for (int j = 0; j < nl; j++) {
+                IDX v = W.lead[lo + j];
+                if (!(v & KEEP)) continue;
+                int L = (int)(v & (KEEP - 1));
+                ulonglong2 k = W.key[L];
+                double c = W.val[L];
+                size_t dst = base + o;
+                nkey[dst] = k;
+                nc[dst] = c;
+                uint8_t f = L < m ? ofl[base + L] : 0;
+                nfl[dst] = f;
+                if (L < m) nhd[dst] = ohd[base + L];
+                else {
+                    int qn = atomicAdd(&S.n_new, 1);
+                    W.perm[qn] = (IDX)L;
+                    W.grp[qn] = (IDX)o;
+                }
+                if (!(fabs(c) < 0x1p31)) bad = true;
+                else nw += fx32(c);
+                if (f & DFLAG_REF) I.st->e_den = c;
+                else {
+                    int lev = __popcll(k.x ^ I.ref_a) + __popcll(k.y ^ I.ref_b);
+                    if (lev <= 4 && c != 0.0) enm = enm + hoff_generic(I, k.x, k.y, I.ref_a, I.ref_b) * c;
+                }
+                if (f & DFLAG_D) I.dc_cur[d_index(I, k.x, k.y)] = c;
+                o++;
+            }
+        }
+    }
+    if (bad) atomicOr(&I.st->err, ERRB_NUMERIC);
+    __syncthreads();
+    // 5. H_jj - E_ref for new determinants, one warp each
+    if (!overflow) {
+        const int nnew = S.n_new;
+        for (int q = warp; q < nnew; q += K3_THREADS / 32) {
+            int L = (int)W.perm[q];
+            ulonglong2 k = W.key[L];
+            double hdv = diag_exact_warp(I, k.x, k.y);
+            if (lane == 0) nhd[base + (int)W.grp[q]] = hdv;
+        }
+    }
+    // 6. bucket reductions (fixed order: lanes by xor tree, warps in index order)
+    for (int mm = 16; mm >= 1; mm >>= 1) {
+        enm = enm + __shfl_xor_sync(0xffffffffu, enm, mm);
+        rejected += __shfl_xor_sync(0xffffffffu, rejected, mm);
+        ann += shfl_xor_i128(ann, mm);
+        nw += (u128)shfl_xor_i128((i128)nw, mm);
+    }
+    if (lane == 0) {
+        S.red_d[warp] = enm;
+        S.red_u[warp][0] = (u64)nw;
+        S.red_u[warp][1] = (u64)(nw >> 64);
+        S.red_u[warp][2] = (u64)ann;
+        S.red_u[warp][3] = (u64)((u128)ann >> 64);
+        S.red_u[warp][4] = (u64)rejected;
+    }
+    __syncthreads();
+    if (t == 0) {
+        double e_sum = 0.0;
+        u128 nws = 0;
+        i128 anns = 0;
+        long long rej = 0;
+        for (int k = 0; k < K3_THREADS / 32; k++) {
+            e_sum = e_sum + S.red_d[k];
+            nws += ((u128)S.red_u[k][1] << 64) | S.red_u[k][0];
+            anns += (i128)(((u128)S.red_u[k][3] << 64) | S.red_u[k][2]);
+            rej += (long long)S.red_u[k][4];
+        }
+        Partial &P = I.part[b];
+        P.nw_lo = (u64)nws;
+        P.nw_hi = (u64)(nws >> 64);
+        P.ann_lo = (u64)anns;
+        P.ann_hi = (u64)((u128)anns >> 64);
+        P.ndet = total;
+        P.rejected = rej;
+        P.spawns = si + sn;
+        P.e_num = e_sum;
+        if (!overflow) I.cnt[np][b] = total;
+        I.scnt_i[b] = 0;
+        I.scnt_n[b] = 0;
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(K3_THREADS, 2) k_annihilate(const DevInst *__restrict__ insts,
                                                               const int *__restrict__ unit_start, int n_inst, int n_units)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    K3Smem &S = *reinterpret_cast<K3Smem *>(smem_raw);
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    constexpr int GPT = NGROUP / K3_THREADS;
+    K3Smem &Sm = *reinterpret_cast<K3Smem *>(smem_raw);
+    K3Shared &S = Sm.sh;
+    Stage<unsigned short> W{Sm.key, Sm.val, Sm.perm, Sm.lead, Sm.grp, Sm.goff, Sm.cur, Sm.nlead};
+    const int t = threadIdx.x;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
         const int ii = find_inst(unit_start, n_inst, u);
         const DevInst &I = insts[ii];
@@ -380,237 +635,67 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k_annihilate(const DevInst *__r
             S.hdr_par = I.st->parity;
             S.hdr_it = I.st->iter;
             S.hdr_S = I.st->S;
-            S.n_new = 0;
         }
         __syncthreads();
-        if (S.hdr_err) { __syncthreads(); continue; }
-        const int b = u - I.unit0, par = S.hdr_par;
+        const int err = S.hdr_err, par = S.hdr_par;
         const long long it = S.hdr_it;
         const double shift = S.hdr_S;
+        __syncthreads();
+        if (err) continue;
+        const int b = u - I.unit0;
         const int m = I.cnt[par][b], si = I.scnt_i[b], sn = I.scnt_n[b];
-        if (si + sn > CAP_S) {
+        if (si + sn > I.cap_s) {
             if (t == 0) atomicOr(&I.st->err, ERRB_SPAWN_CAP);
-            __syncthreads();
             continue;
         }
-        const int E = m + si + sn;
-        const size_t base = (size_t)b * CAP_M, sbase = (size_t)b * CAP_S;
-        const int shift_g = 64 - I.bb - GBITS;
-        const ulonglong2 *okey = I.key[par];
-        const double *oc = I.c[par], *ohd = I.hd[par];
-        const uint8_t *ofl = I.fl[par];
+        if (m + si + sn > EMAX) {  // too large for shared memory: deferred to k_annihilate_big
+            if (t == 0) I.big_list[atomicAdd(&I.st->big_n, 1)] = b;
+            continue;
+        }
+        anni_bucket<unsigned short>(I, S, W, GBITS, b, par, it, shift, m, si, sn);
+    }
+}
 
-        // 1. stage the bucket: walkers [0, m), initiator spawns [m, m+si),
-        //    other spawns [m+si, E); histogram of the sub-hash groups
-        for (int g = t; g < NGROUP; g += K3_THREADS) S.cur[g] = 0;
-        __syncthreads();
-        for (int e = t; e < E; e += K3_THREADS) {
-            ulonglong2 k;
-            double v;
-            if (e < m) { k = okey[base + e]; v = oc[base + e]; }
-            else if (e < m + si) { k = I.skey[sbase + (e - m)]; v = I.sw[sbase + (e - m)]; }
-            else { int slot = CAP_S - 1 - (e - m - si); k = I.skey[sbase + slot]; v = I.sw[sbase + slot]; }
-            S.key[e] = k;
-            S.val[e] = v;
-            int g = (int)((det_hash(k.x, k.y) >> shift_g) & (NGROUP - 1));
-            S.grp[e] = (unsigned short)g;
-            atomicAdd(&S.cur[g], 1);
-        }
-        __syncthreads();
-        // 2. group offsets (each thread owns GPT consecutive groups)
-        {
-            int loc[GPT], sum = 0;
-#pragma unroll
-            for (int q = 0; q < GPT; q++) { loc[q] = S.cur[t * GPT + q]; sum += loc[q]; }
-            int tot;
-            int ex = block_excl_scan(sum, S.wsum, &tot);
-#pragma unroll
-            for (int q = 0; q < GPT; q++) { S.goff[t * GPT + q] = ex; S.cur[t * GPT + q] = ex; ex += loc[q]; }
-            if (t == 0) S.goff[NGROUP] = tot;
-        }
-        __syncthreads();
-        for (int e = t; e < E; e += K3_THREADS) {
-            int pos = atomicAdd(&S.cur[S.grp[e]], 1);
-            S.perm[pos] = (unsigned short)e;
-        }
-        __syncthreads();
-
-        // 3. pass 1: within each group, visit distinct determinants in key order
-        int nk = 0;
-        long long rejected = 0;
-        i128 ann = 0;
-        for (int q = 0; q < GPT; q++) {
-            const int g = t * GPT + q, lo = S.goff[g], hi = S.goff[g + 1];
-            int nl = 0;
-            u64 la = 0, lb = 0;
-            bool first = true;
-            while (true) {
-                bool found = false;
-                u64 ba = 0, bb2 = 0;
-                for (int r = lo; r < hi; r++) {
-                    ulonglong2 k = S.key[S.perm[r]];
-                    bool gt = first || key_less(la, lb, k.x, k.y);
-                    if (gt && (!found || key_less(k.x, k.y, ba, bb2))) { found = true; ba = k.x; bb2 = k.y; }
-                }
-                if (!found) break;
-                first = false;
-                la = ba; lb = bb2;
-                int me = -1, leader = -1, ni = 0, nn = 0;
-                i128 Xi = 0, Xn = 0;
-                u128 fi = 0, fn = 0;
-                for (int r = lo; r < hi; r++) {
-                    int e = S.perm[r];
-                    ulonglong2 k = S.key[e];
-                    if (k.x != ba || k.y != bb2) continue;
-                    if (leader < 0) leader = e;
-                    if (e < m) { me = e; continue; }
-                    double w = S.val[e];
-                    if (e < m + si) { Xi += to_fixed(w, I.Fw); fi += fx32(w); ni++; }
-                    else { Xn += to_fixed(w, I.Fw); fn += fx32(w); nn++; }
-                }
-                if (me >= 0) leader = me;
-                const bool present = me >= 0;
-                uint8_t fl = present ? ofl[base + me] : 0;
-                double c0 = present ? S.val[me] : 0.0, cp = 0.0;
-                if (present) {
-                    if (fl & DFLAG_D) {
-                        cp = I.dc_new[d_index(I, ba, bb2)];
-                    } else {
-                        // (b) death: C (1 - tau (H_ii - E_ref - S)), then Eq. (2)
-                        double f = 1.0 - I.tau * (ohd[base + me] - shift);
-                        cp = c0 * f;
-                        if (cp != 0.0 && fabs(cp) < I.cmin) {
-                            u64 w[4];
-                            philox(ba, bb2, (u64)it, (u64)PURPOSE_DEATH, I.seed, 0ULL, w);
-                            cp = round_stoch(cp, I.cmin, u53(w[0]));
-                        }
-                    }
-                }
-                // (c) annihilation with the initiator rule: spawns from
-                // non-initiators survive only onto determinants occupied at
-                // the start of the iteration
-                const bool occ = present && c0 != 0.0;
-                i128 X = Xi;
-                u128 fs = fi;
-                int nacc = ni;
-                if (occ) { X += Xn; fs += fn; nacc += nn; } else rejected += nn;
-                double acc = cp;
-                if (nacc > 0) {
-                    double swsum = fixed_to_double(X, I.Fw);
-                    acc = present ? cp + swsum : swsum;
-                    i128 in = (present ? (i128)fx32(cp) : (i128)0) + (i128)fs;
-                    ann += in - (i128)fx32(acc);
-                    if (!(fl & DFLAG_D) && acc != 0.0 && fabs(acc) < I.cmin) {
-                        u64 w[4];
-                        philox(ba, bb2, (u64)it, (u64)PURPOSE_ANNIH, I.seed, 0ULL, w);
-                        acc = round_stoch(acc, I.cmin, u53(w[0]));
-                    }
-                }
-                const bool keep = acc != 0.0 || (fl & (DFLAG_REF | DFLAG_D));
-                S.val[leader] = acc;
-                S.lead[lo + nl] = (unsigned short)(leader | (keep ? 0x8000 : 0));
-                nl++;
-                nk += keep ? 1 : 0;
-            }
-            S.nlead[g] = (unsigned short)nl;
-        }
-        int total;
-        int o = block_excl_scan(nk, S.wsum, &total);
-        const bool overflow = total > CAP_M;
-        if (overflow && t == 0) atomicOr(&I.st->err, ERRB_MAIN_CAP);
-
-        // 4. pass 2: write the new bucket in (group, key) order; reductions
-        const int np = par ^ 1;
-        ulonglong2 *nkey = I.key[np];
-        double *nc = I.c[np], *nhd = I.hd[np];
-        uint8_t *nfl = I.fl[np];
-        u128 nw = 0;
-        double enm = 0.0;
-        bool bad = false;
-        if (!overflow) {
-            for (int q = 0; q < GPT; q++) {
-                const int g = t * GPT + q, lo = S.goff[g], nl = S.nlead[g];
-                for (int j = 0; j < nl; j++) {
-                    int v = S.lead[lo + j];
-                    if (!(v & 0x8000)) continue;
-                    int L = v & 0x7fff;
-                    ulonglong2 k = S.key[L];
-                    double c = S.val[L];
-                    size_t dst = base + o;
-                    nkey[dst] = k;
-                    nc[dst] = c;
-                    uint8_t f = L < m ? ofl[base + L] : 0;
-                    nfl[dst] = f;
-                    if (L < m) nhd[dst] = ohd[base + L];
-                    else {
-                        int qn = atomicAdd(&S.n_new, 1);
-                        S.perm[qn] = (unsigned short)L;
-                        S.grp[qn] = (unsigned short)o;
-                    }
-                    if (!(fabs(c) < 0x1p31)) bad = true;
-                    else nw += fx32(c);
-                    if (f & DFLAG_REF) I.st->e_den = c;
-                    else {
-                        int lev = __popcll(k.x ^ I.ref_a) + __popcll(k.y ^ I.ref_b);
-                        if (lev <= 4 && c != 0.0) enm = enm + hoff_generic(I, k.x, k.y, I.ref_a, I.ref_b) * c;
-                    }
-                    o++;
-                }
-            }
-        }
-        if (bad) atomicOr(&I.st->err, ERRB_NUMERIC);
-        __syncthreads();
-        // 5. H_jj - E_ref for new determinants, one warp each
-        if (!overflow) {
-            const int nnew = S.n_new;
-            for (int q = warp; q < nnew; q += K3_THREADS / 32) {
-                int L = S.perm[q];
-                ulonglong2 k = S.key[L];
-                double hdv = diag_exact_warp(I, k.x, k.y);
-                if (lane == 0) nhd[base + S.grp[q]] = hdv;
-            }
-        }
-        // 6. bucket reductions (fixed order: lanes by xor tree, warps in index order)
-        for (int mm = 16; mm >= 1; mm >>= 1) {
-            enm = enm + __shfl_xor_sync(0xffffffffu, enm, mm);
-            rejected += __shfl_xor_sync(0xffffffffu, rejected, mm);
-            ann += shfl_xor_i128(ann, mm);
-            nw += (u128)shfl_xor_i128((i128)nw, mm);
-        }
-        if (lane == 0) {
-            S.red_d[warp] = enm;
-            S.red_u[warp][0] = (u64)nw;
-            S.red_u[warp][1] = (u64)(nw >> 64);
-            S.red_u[warp][2] = (u64)ann;
-            S.red_u[warp][3] = (u64)((u128)ann >> 64);
-            S.red_u[warp][4] = (u64)rejected;
-        }
-        __syncthreads();
+__global__ void __launch_bounds__(K3_THREADS) k_annihilate_big(const DevInst *__restrict__ insts, int n_inst)
+{
+    __shared__ K3Shared S;
+    const int t = threadIdx.x;
+    for (int ii = 0; ii < n_inst; ii++) {
+        const DevInst &I = insts[ii];
         if (t == 0) {
-            double e_sum = 0.0;
-            u128 nws = 0;
-            i128 anns = 0;
-            long long rej = 0;
-            for (int k = 0; k < K3_THREADS / 32; k++) {
-                e_sum = e_sum + S.red_d[k];
-                nws += ((u128)S.red_u[k][1] << 64) | S.red_u[k][0];
-                anns += (i128)(((u128)S.red_u[k][3] << 64) | S.red_u[k][2]);
-                rej += (long long)S.red_u[k][4];
-            }
-            Partial &P = I.part[b];
-            P.nw_lo = (u64)nws;
-            P.nw_hi = (u64)(nws >> 64);
-            P.ann_lo = (u64)anns;
-            P.ann_hi = (u64)((u128)anns >> 64);
-            P.ndet = total;
-            P.rejected = rej;
-            P.spawns = si + sn;
-            P.e_num = e_sum;
-            if (!overflow) I.cnt[np][b] = total;
-            I.scnt_i[b] = 0;
-            I.scnt_n[b] = 0;
+            S.hdr_err = *(volatile int *)&I.st->err;
+            S.hdr_par = I.st->parity;
+            S.hdr_it = I.st->iter;
+            S.hdr_S = I.st->S;
+            S.n_new = I.st->big_n;
         }
         __syncthreads();
+        const int err = S.hdr_err, par = S.hdr_par, nbig = S.n_new;
+        const long long it = S.hdr_it;
+        const double shift = S.hdr_S;
+        __syncthreads();
+        if (err || nbig == 0) continue;
+        if (!I.big_scratch) {  // no scratch yet: report, the host allocates it and repeats the iteration
+            if (t == 0) atomicOr(&I.st->err, ERRB_SPAWN_CAP);
+            continue;
+        }
+        // this block's scratch slice
+        const int Ecap = CAP_M + I.cap_s, gbits = I.big_gbits, G = 1 << gbits;
+        unsigned char *p = I.big_scratch + (size_t)blockIdx.x * I.big_stride;
+        Stage<unsigned> W;
+        W.key = (ulonglong2 *)p; p += (size_t)Ecap * sizeof(ulonglong2);
+        W.val = (double *)p; p += (size_t)Ecap * sizeof(double);
+        W.perm = (unsigned *)p; p += (size_t)Ecap * 4;
+        W.lead = (unsigned *)p; p += (size_t)Ecap * 4;
+        W.grp = (unsigned *)p; p += (size_t)Ecap * 4;
+        W.goff = (unsigned *)p; p += (size_t)(G + 1) * 4;
+        W.cur = (int *)p; p += (size_t)G * 4;
+        W.nlead = (unsigned *)p;
+        for (int q = blockIdx.x; q < nbig; q += gridDim.x) {
+            const int b = I.big_list[q];
+            const int m = I.cnt[par][b], si = I.scnt_i[b], sn = I.scnt_n[b];
+            anni_bucket<unsigned>(I, S, W, gbits, b, par, it, shift, m, si, sn);
+        }
     }
 }
 
@@ -690,6 +775,7 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
     st->iter = it + 1;
     st->parity ^= 1;
     st->heavy_n = 0;
+    st->big_n = 0;
     if (I.semi_size > 0 && !st->semi_built && st->vary && it + 1 == st->shift_start + I.semi_start)
         st->err |= ERRB_PAUSE_SEMI;
 }
@@ -761,19 +847,25 @@ void launch_spawn_heavy(const DevInst *dinst, int n_inst, cudaStream_t s)
     k_spawn_heavy<<<num_sms() * 4, K1_THREADS, 0, s>>>(dinst, n_inst);
 }
 
+cudaError_t init_kernels()
+{
+    return cudaFuncSetAttribute(k_annihilate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K3Smem));
+}
+
+size_t annihilate_smem_bytes() { return sizeof(K3Smem); }
+
 cudaError_t launch_annihilate(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, cudaStream_t s)
 {
-    static bool attr = false;
     const size_t smem = sizeof(K3Smem);
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_annihilate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
     int grid = n_units < num_sms() * 2 ? n_units : num_sms() * 2;
     if (grid < 1) grid = 1;
     k_annihilate<<<grid, K3_THREADS, smem, s>>>(dinst, unit_start, n_inst, n_units);
     return cudaGetLastError();
+}
+
+void launch_annihilate_big(const DevInst *dinst, int n_inst, cudaStream_t s)
+{
+    k_annihilate_big<<<BIG_BLOCKS, K3_THREADS, 0, s>>>(dinst, n_inst);
 }
 
 void launch_finalize(const DevInst *dinst, int n_inst, cudaStream_t s)
