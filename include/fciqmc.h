@@ -4,11 +4,11 @@
  * One handle = one FCIQMC run: a sparse walker list of Slater determinants
  * (two uint64 occupation words, alpha and beta) with signed binary64
  * amplitudes, resident in device memory, advanced by the projector
- * psi(t + dt) = (1 - dt (H - S)) psi(t) of Eq. (1) of Guther et al.,
+ * psi(t + dt) = (1 - dt (H - S)) psi(t) of Eq. (2) of Guther et al.,
  * J. Chem. Phys. 153, 034107 (2020) (arXiv:2006.14956), in the three steps
- * of its Eq. (3): spawning, death, annihilation, with the initiator rule of
- * Sec. I, stochastic rounding at C_min (Eq. (2)), the shift update and the
- * reference projected energy of Eq. (8).  Deterministic (semi-stochastic)
+ * of its Eq. (4): spawning, death, annihilation, with the initiator rule of
+ * Sec. I, stochastic rounding at C_min (Eq. (3)), the shift update and the
+ * reference projected energy of Eq. (9).  Deterministic (semi-stochastic)
  * projection inside the space D of Sec. III is optional.
  *
  * Conventions used throughout:
@@ -53,12 +53,12 @@ enum {
 
 enum { FCIQMC_ABINITIO = 0, FCIQMC_HUBBARD = 1 };
 
-/* The Hamiltonian (Sec. I; Eq. (3)).  For FCIQMC_ABINITIO, h1 and eri are
+/* The Hamiltonian (Sec. I; Eq. (4)).  For FCIQMC_ABINITIO, h1 and eri are
  * host arrays of binary64 (norb*norb row-major, and the packed 8-fold ERI).
  * For FCIQMC_HUBBARD the library builds h_pq = -t on lattice bonds and
  * (pp|pp) = U itself from lx, ly and the periodic flags; sites are numbered
  * x + lx*y.  A periodic direction must have length 1 or >= 3.
- * ref: the reference determinant of Eq. (8); when has_ref is 0 it is the
+ * ref: the reference determinant of Eq. (9); when has_ref is 0 it is the
  * aufbau determinant (ABINITIO) or the Neel determinant, alpha on sites with
  * even x+y (HUBBARD). */
 typedef struct {
@@ -77,17 +77,17 @@ typedef struct {
     uint64_t ref_alpha, ref_beta;
 } fciqmc_system;
 
-/* Run parameters.  tau: time step (Eq. (1)).  Shift (Eq. (1)): S starts at
+/* Run parameters.  tau: time step (Eq. (2)).  Shift (Eq. (2)): S starts at
  * initial_shift and stays there until the walker number N_w first reaches
  * target_walkers; from then on, every shift_interval (A) iterations,
  * S <- S - shift_damping / (A tau) * ln(N_w(t) / N_w(t - A)).
  * initiator_threshold n_a: a determinant is an initiator when |C| > n_a (or
  * it is the reference, or it lies in D); 0 gives plain FCIQMC.  c_min:
- * rounding threshold of Eq. (2).  p_single: probability of proposing a single
+ * rounding threshold of Eq. (3).  p_single: probability of proposing a single
  * excitation (App. A).  semistoch_size: N_D of Sec. III (0 = off), chosen
  * semistoch_start iterations after the shift starts to vary.
  * max_dets / max_spawns: capacity hints (0 = derived from target_walkers);
- * capacities grow automatically when exceeded.  stream: a cudaStream_t
+ * capacities grow automatically when exceeded, up to max_device_bytes.  stream: a cudaStream_t
  * (NULL = the library creates its own).  alloc/free: optional device
  * allocator (for example a framework's caching allocator); NULL = cudaMalloc. */
 typedef struct {
@@ -105,6 +105,7 @@ typedef struct {
     int64_t semistoch_start;
     int64_t max_dets;
     int64_t max_spawns;
+    int64_t max_device_bytes; /* growth beyond this fails with FCIQMC_ERR_OUT_OF_MEMORY (0 = no limit) */
     void *stream;
     void *(*alloc)(size_t bytes, void *ctx);
     void (*free)(void *ptr, void *ctx);
@@ -114,7 +115,7 @@ typedef struct {
 /* One row per completed iteration.  nw: walker number N_w = 2^-32 sum
  * floor(|C| 2^32).  shift: S after the iteration (relative to E_ref).
  * e_num = sum_{j != ref} H_ref,j C_j and e_den = C_ref after the iteration
- * (Eq. (8)); attempts = sum ceil(|C|); spawns = spawned walkers stored;
+ * (Eq. (9)); attempts = sum ceil(|C|); spawns = spawned walkers stored;
  * rejected = spawns removed by the initiator rule; annihilated = walkers
  * removed by summing opposite-sign contributions. */
 typedef struct {
@@ -170,6 +171,18 @@ int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *params, fciqmc_
  * repeats the failed iteration, which is bit-identical because every random
  * draw is keyed; other errors stop the run at the last good iteration. */
 int fciqmc_step(fciqmc_handle *h, int64_t n_iter);
+
+/* Enqueues n_iter iterations on the handle's stream and returns at once (no
+ * host synchronisation, no error check).  The caller must call fciqmc_sync
+ * before reading results; fciqmc_sync reports the first error and, after a
+ * capacity overflow, grows the buffers and repeats the missing iterations
+ * (bit-identical).  Lets a caller overlap host work or bracket single
+ * iterations with its own events on fciqmc_stream(h). */
+int fciqmc_step_async(fciqmc_handle *h, int64_t n_iter);
+int fciqmc_sync(fciqmc_handle *h);
+
+/* The cudaStream_t all work of the handle runs on. */
+void *fciqmc_stream(fciqmc_handle *h);
 
 /* Fills *out from the iteration history (host-side statistics). */
 int fciqmc_energy(fciqmc_handle *h, fciqmc_stats *out);

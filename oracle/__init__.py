@@ -7,7 +7,7 @@ library never imports it, and the two share no code.
 ``fciqmc_oracle.c`` holds the method (Philox4x64-10 draws, uniform and lattice
 excitation generation, Slater-Condon rules, spawn / death / annihilation with
 the initiator rule, semi-stochastic projection, shift update and the reference
-projected energy of Eq. (8) of the paper).  This module wraps it with ctypes and
+projected energy of Eq. (9) of the paper).  This module wraps it with ctypes and
 adds what needs no new arithmetic: exact diagonalisation through
 ``numpy.linalg.eigh`` on the oracle's own Hamiltonian matrix, the U=0 Hubbard
 band energy in closed form, and Flyvbjerg-Petersen blocking statistics.
@@ -144,7 +144,7 @@ def ln(x: float) -> float:
 
 # ---------------------------------------------------------------- systems
 class System:
-    """Hamiltonian of the paper's Eq. (8)-style ab initio or Hubbard system."""
+    """Ab initio (FCIDUMP-style integrals) or Hubbard Hamiltonian."""
 
     def __init__(self, handle, norb, na, nb, kind):
         self.h = handle
@@ -308,7 +308,7 @@ class Run:
                          int(cnt), (int(nw_last) >> 64) & 0xFFFFFFFFFFFFFFFF, int(nw_last) & 0xFFFFFFFFFFFFFFFF)
 
     def proj_energy(self):
-        """(E_num, E_den) of the current list, Eq. (8)."""
+        """(E_num, E_den) of the current list, Eq. (9)."""
         num = C.c_double()
         den = C.c_double()
         lib().orc_proj_energy(self.h, C.byref(num), C.byref(den))

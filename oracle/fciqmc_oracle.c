@@ -14,16 +14,16 @@
  * evaluated as written, one IEEE-754 binary64 operation at a time, with no
  * fused multiply-add.)
  *
- * What is computed, in the paper's order (Sec. I, Eq. (3) "fciqmc_dyn"):
+ * What is computed, in the paper's order (Sec. I, Eq. (4)):
  *   (a) spawn:  sum_{j != i} -dtau H_ji C_i |D_j>, sampled with one excitation
- *       per attempt, p_s = dtau |H_ij| / p_gen(j|i) (Sec. II, Eq. (4));
- *   (b) death:  (1 - dtau (H_ii - S)) C_i, then stochastic rounding (Eq. (2));
+ *       per attempt, p_s = dtau |H_ij| / p_gen(j|i) (Sec. II, Eq. (5));
+ *   (b) death:  (1 - dtau (H_ii - S)) C_i, then stochastic rounding (Eq. (3));
  *   (c) annihilation: all spawned contributions to a determinant are summed
  *       into it, with the initiator rule (Sec. I) applied to spawns onto
  *       unoccupied determinants, then stochastic rounding;
- *   plus the shift update (Eq. (1), S(tau) "updated to match the ground
- *   state energy"), the reference projected energy (Sec. IV, Eq. (8)), and
- *   semi-stochastic projection (Sec. III, Eqs. (5)-(6)).
+ *   plus the shift update (Eq. (2), S(tau) "updated to match the ground
+ *   state energy"), the reference projected energy (Sec. IV, Eq. (9)), and
+ *   semi-stochastic projection (Sec. III, Eqs. (7)-(8)).
  *
  * Readings adopted where the paper is silent (each listed in the design notes):
  *   R1  determinant = (alpha word, beta word); canonical operator order is
@@ -677,7 +677,7 @@ int64_t orc_semistoch_info(const orc_run *r, int64_t *nnz)
 
 static double round_stoch(double v, double cmin, double u)
 {
-    /* Eq. (2): keep |v| >= C_min; else sign(v) C_min with prob |v|/C_min, else 0 */
+    /* Eq. (3): keep |v| >= C_min; else sign(v) C_min with prob |v|/C_min, else 0 */
     if (v == 0.0 || fabs(v) >= cmin) return v;
     return u < fabs(v) / cmin ? copysign(cmin, v) : 0.0;
 }
@@ -803,7 +803,7 @@ static int one_iteration(orc_run *r)
     free(sp); free(c0); free(r->L);
     r->L = out; r->n = no; r->cap = outcap;
 
-    /* reductions: N_w (R6), E_num / E_den (Eq. (8)) */
+    /* reductions: N_w (R6), E_num / E_den (Eq. (9)) */
     u128 W = 0;
     double e_num = 0.0, e_den = 0.0;
     for (int64_t i = 0; i < no; i++) {
@@ -892,7 +892,7 @@ void orc_stats(const orc_run *r, int64_t i0, int64_t n, orc_stat *out)
 int orc_stat_size(void) { return (int)sizeof(orc_stat); }
 int orc_params_size(void) { return (int)sizeof(orc_params); }
 
-/* E_num, E_den of the current list (Eq. (8)): E_num = sum_{j != ref} H_ref,j C_j
+/* E_num, E_den of the current list (Eq. (9)): E_num = sum_{j != ref} H_ref,j C_j
  * summed in ascending key order, E_den = C_ref */
 void orc_proj_energy(const orc_run *r, double *num, double *den)
 {

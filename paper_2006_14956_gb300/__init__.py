@@ -63,7 +63,7 @@ class fciqmc_params(C.Structure):
                 ("initiator_threshold", C.c_double), ("c_min", C.c_double), ("p_single", C.c_double),
                 ("shift_interval", C.c_int64), ("seed", C.c_uint64), ("semistoch_size", C.c_int64),
                 ("semistoch_start", C.c_int64), ("max_dets", C.c_int64), ("max_spawns", C.c_int64),
-                ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
+                ("max_device_bytes", C.c_int64), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
 class fciqmc_iter_stats(C.Structure):
@@ -87,6 +87,9 @@ _dp = C.POINTER(C.c_double)
 _SIGS = {
     "fciqmc_create": (C.c_int, [C.POINTER(fciqmc_system), C.POINTER(fciqmc_params), C.POINTER(_H)]),
     "fciqmc_step": (C.c_int, [_H, C.c_int64]),
+    "fciqmc_step_async": (C.c_int, [_H, C.c_int64]),
+    "fciqmc_sync": (C.c_int, [_H]),
+    "fciqmc_stream": (C.c_void_p, [_H]),
     "fciqmc_energy": (C.c_int, [_H, C.POINTER(fciqmc_stats)]),
     "fciqmc_destroy": (None, [_H]),
     "fciqmc_last_error": (C.c_char_p, [_H]),
@@ -180,7 +183,7 @@ def _system_struct(system):
 
 DEFAULTS = dict(tau=0.01, shift_damping=0.1, target_walkers=1e4, initial_walkers=10.0, initial_shift=0.0,
                 initiator_threshold=0.0, c_min=1.0, p_single=0.1, shift_interval=10, seed=1, semistoch_size=0,
-                semistoch_start=100, max_dets=0, max_spawns=0)
+                semistoch_start=100, max_dets=0, max_spawns=0, max_device_bytes=0)
 
 
 def fciqmc_create(system, params=None, stream=None, use_torch=True):
@@ -229,6 +232,18 @@ def fciqmc_destroy(handle):
 
 def fciqmc_step(handle, n_iter):
     _check(_lib.fciqmc_step(handle.h, int(n_iter)), handle.h)
+
+
+def fciqmc_step_async(handle, n_iter):
+    _check(_lib.fciqmc_step_async(handle.h, int(n_iter)), handle.h)
+
+
+def fciqmc_sync(handle):
+    _check(_lib.fciqmc_sync(handle.h), handle.h)
+
+
+def fciqmc_stream(handle):
+    return _lib.fciqmc_stream(handle.h)
 
 
 def fciqmc_step_batch(handles, n_iter):

@@ -64,6 +64,9 @@ struct fciqmc_handle {
     // semi-stochastic space
     int nd = 0;
     long long nnz = 0;
+    // asynchronous stepping
+    bool pending = false;
+    long long async_base = 0, async_target = 0;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -84,6 +87,7 @@ static void *dev_alloc(fciqmc_handle *h, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
     bytes = (bytes + 255) & ~(size_t)255;
+    if (h->p.max_device_bytes > 0 && h->bytes + bytes > (size_t)h->p.max_device_bytes) return nullptr;
     void *ptr = nullptr;
     if (h->p.alloc) ptr = h->p.alloc(bytes, h->p.alloc_ctx);
     else if (cudaMalloc(&ptr, bytes) != cudaSuccess) ptr = nullptr;
@@ -307,11 +311,13 @@ static int grow_buckets(fciqmc_handle *h)
 
 // larger spawn regions per bucket; buckets that no longer fit in shared
 // memory are annihilated from a global scratch slice per block
-static int grow_spawn_capacity(fciqmc_handle *h)
+static int grow_spawn_capacity(fciqmc_handle *h, long long need)
 {
     DevInst &I = h->hi;
     const size_t nbk = (size_t)1 << h->bb;
-    const int ncap = I.cap_s * 2;
+    long long want = std::max<long long>(2LL * I.cap_s, need + need / 4);
+    int ncap = I.cap_s;
+    while (ncap < want && ncap < (1 << 30)) ncap *= 2;
     if ((size_t)ncap * nbk > ((size_t)1 << 33)) return fail(h, FCIQMC_ERR_CAPACITY, "spawn buffer limit reached");
     ulonglong2 *nk = (ulonglong2 *)dev_alloc(h, nbk * (size_t)ncap * sizeof(ulonglong2));
     double *nw = (double *)dev_alloc(h, nbk * (size_t)ncap * sizeof(double));
@@ -349,6 +355,8 @@ static int reset_after_error(fciqmc_handle *h)
     h->hst.err = 0;
     h->hst.heavy_n = 0;
     h->hst.big_n = 0;
+    h->hst.need_spawn = 0;
+    h->hst.need_main = 0;
     return write_state(h);
 }
 
@@ -364,8 +372,15 @@ static int pull_history(fciqmc_handle *h, long long from, long long to)
         it += n;
     }
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    // the history is indexed by iteration; a retried iteration overwrites
+    // the history is indexed by iteration; a retried iteration overwrites,
+    // and rows that fell out of the ring are kept as placeholders
     if ((long long)h->hist.size() > from) h->hist.resize((size_t)from);
+    while ((long long)h->hist.size() < from) {
+        fciqmc_iter_stats z;
+        memset(&z, 0, sizeof z);
+        z.iteration = -1;
+        h->hist.push_back(z);
+    }
     h->hist.insert(h->hist.end(), rows.begin(), rows.end());
     return FCIQMC_OK;
 }
@@ -570,14 +585,21 @@ int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_han
     I.st = h->dstate;
 
     // bucket layout: average occupancy well below the per-bucket capacity
-    double dets_hint = P.max_dets > 0 ? (double)P.max_dets : std::max(4096.0, 2.0 * P.target_walkers);
+    // start at the expected size (capped: buffers grow on demand)
+    double dets_hint = P.max_dets > 0 ? (double)P.max_dets : std::min(std::max(4096.0, P.target_walkers), 8388608.0);
+    {
+        double fci = 1.0;  // C(N, n_alpha) C(N, n_beta)
+        for (int k = 0; k < h->na; k++) fci *= (double)(N - k) / (double)(k + 1);
+        for (int k = 0; k < h->nb; k++) fci *= (double)(N - k) / (double)(k + 1);
+        if (P.max_dets <= 0) dets_hint = std::min(dets_hint, std::max(1.0, fci));
+    }
     int bb = 0;
     while (((double)(1LL << bb)) * 640.0 < dets_hint && bb < 24) bb++;
     I.cap_s = CAP_S0;
     int rc = alloc_layout(h, I, bb);
     if (rc) return bail(rc, "out of device memory (walker buffers)");
     h->bb = bb;
-    h->heavy_cap = std::max(4096, (int)std::min(1e8, 4.0 * P.target_walkers / HEAVY_ATT));
+    h->heavy_cap = std::max(4096, (int)std::min(1e6, 4.0 * P.target_walkers / HEAVY_ATT));
     I.heavy = (HeavyChunk *)dev_alloc(h, (size_t)h->heavy_cap * sizeof(HeavyChunk));
     I.heavy_cap = h->heavy_cap;
     if (!I.heavy) return bail(FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (heavy queue)");
@@ -628,19 +650,76 @@ int fciqmc_layout(fciqmc_handle *h, int64_t out[4])
     return FCIQMC_OK;
 }
 
+static int step_to(fciqmc_handle *h, long long target_iter);
+
 int fciqmc_step(fciqmc_handle *h, int64_t n_iter)
 {
     if (!h || n_iter < 0) return FCIQMC_ERR_INVALID_ARG;
+    if (h->pending) {
+        int rc = fciqmc_sync(h);
+        if (rc) return rc;
+    }
     int rc = read_state(h);
     if (rc) return rc;
-    long long target_iter = h->hst.iter + n_iter;
+    return step_to(h, h->hst.iter + n_iter);
+}
+
+int fciqmc_step_async(fciqmc_handle *h, int64_t n_iter)
+{
+    if (!h || n_iter < 0) return FCIQMC_ERR_INVALID_ARG;
+    if (!h->pending) {
+        int rc = read_state(h);
+        if (rc) return rc;
+        h->async_base = h->hst.iter;
+        h->async_target = h->hst.iter;
+    }
+    for (int64_t k = 0; k < n_iter; k++) CUDA_TRY(h, cudaGraphLaunch(h->graph, h->stream));
+    h->async_target += n_iter;
+    h->pending = true;
+    return FCIQMC_OK;
+}
+
+int fciqmc_sync(fciqmc_handle *h)
+{
+    if (!h) return FCIQMC_ERR_INVALID_ARG;
+    if (!h->pending) return FCIQMC_OK;
+    h->pending = false;
+    int rc = read_state(h);
+    if (rc) return rc;
+    // rows of the iterations that completed; beyond the ring only the last ring_cap are kept
+    long long from = std::max<long long>(h->async_base, h->hst.iter - h->ring_cap);
+    rc = pull_history(h, from, h->hst.iter);
+    if (rc) return rc;
+    if (!h->hst.err) return FCIQMC_OK;
+    return step_to(h, h->async_target);
+}
+
+void *fciqmc_stream(fciqmc_handle *h) { return h ? (void *)h->stream : nullptr; }
+
+// Runs iterations until target_iter, in chunks of graph replays; after each
+// chunk reads the device state and reacts to its flags (capacity growth with
+// a bit-identical repeat, semi-stochastic set-up, or a fatal error).
+static int handle_flags(fciqmc_handle *h, int *retries);
+
+static int step_to(fciqmc_handle *h, long long target_iter)
+{
+    int rc;
     int retries = 0;
     std::vector<cudaEvent_t> evs;
     double kt[5] = {0, 0, 0, 0, 0};
     long long kn = 0;
-    while (h->hst.iter < target_iter) {
-        long long start = h->hst.iter;
-        long long chunk = std::min<long long>(target_iter - start, h->ring_cap);
+    long long chunk_max = 16;  // grows after clean chunks; an error costs at most one chunk of no-op replays
+    for (;;) {
+        if (h->hst.err) {
+            chunk_max = 16;
+            rc = handle_flags(h, &retries);
+            if (rc) return rc;
+            continue;
+        }
+        if (h->hst.iter >= target_iter) break;
+        const long long start = h->hst.iter;
+        const long long chunk = std::min<long long>(std::min<long long>(target_iter - start, h->ring_cap), chunk_max);
+        chunk_max = std::min<long long>(chunk_max * 2, h->ring_cap);
         if (h->profiling) {
             evs.resize((size_t)chunk * 6);
             for (auto &e : evs) cudaEventCreate(&e);
@@ -654,7 +733,7 @@ int fciqmc_step(fciqmc_handle *h, int64_t n_iter)
         rc = read_state(h);
         if (rc) return rc;
         if (h->profiling) {
-            long long done = h->hst.iter - start;
+            const long long done = h->hst.iter - start;
             for (long long k = 0; k < done; k++)
                 for (int j = 0; j < 5; j++) {
                     float ms = 0.f;
@@ -667,43 +746,62 @@ int fciqmc_step(fciqmc_handle *h, int64_t n_iter)
         }
         rc = pull_history(h, start, h->hst.iter);
         if (rc) return rc;
-        int err = h->hst.err;
-        if (!err) continue;
-        if (err & ERRB_NUMERIC) return fail(h, FCIQMC_ERR_NUMERIC, "numeric error (NaN/Inf or |C| >= 2^31) at iteration " + std::to_string(h->hst.iter));
-        if (err & ERRB_TIMEOUT) return fail(h, FCIQMC_ERR_TIMEOUT, "device wait timed out");
-        if (err & ERRB_PAUSE_SEMI) {
-            rc = build_semistochastic(h);
-            if (rc) return rc;
-            h->hst.err &= ~ERRB_PAUSE_SEMI;
-            rc = write_state(h);
-            if (rc) return rc;
-            continue;
-        }
-        if (++retries > 64) return fail(h, FCIQMC_ERR_CAPACITY, "capacity growth did not converge");
-        rc = reset_after_error(h);
-        if (rc) return rc;
-        if (err & (ERRB_SPAWN_CAP | ERRB_MAIN_CAP)) {
-            // split buckets when the list itself is crowded; otherwise a few
-            // determinants receive many spawns and the spawn regions grow
-            long long ndet = h->hist.empty() ? 1 : h->hist.back().ndet;
-            bool crowded = (err & ERRB_MAIN_CAP) || ndet > (long long)(1LL << h->bb) * (CAP_M / 2);
-            rc = crowded ? grow_buckets(h) : grow_spawn_capacity(h);
+        if (!h->hst.err && !h->hist.empty() && h->hist.back().ndet > (1LL << h->bb) * (long long)(CAP_M / 2) &&
+            h->bb < 24) {
+            // keep head-room in the main buckets: split once the average
+            // occupancy passes half the capacity
+            rc = grow_buckets(h);
             if (rc) return rc;
             rc = reset_after_error(h);
             if (rc) return rc;
-        }
-        if (err & ERRB_HEAVY_CAP) {
-            rc = grow_heavy(h);
+            rc = upload_inst(h);
+            if (rc) return rc;
+            rc = capture_graph(h);
             if (rc) return rc;
         }
-        rc = upload_inst(h);
-        if (rc) return rc;
-        rc = capture_graph(h);
-        if (rc) return rc;
     }
     if (h->profiling && kn > 0)
         for (int j = 0; j < 5; j++) h->ktime[j] = kt[j] / (double)kn;
     return FCIQMC_OK;
+}
+
+static int handle_flags(fciqmc_handle *h, int *retries)
+{
+    int rc;
+    const int err = h->hst.err;
+    if (err & ERRB_NUMERIC)
+        return fail(h, FCIQMC_ERR_NUMERIC, "numeric error (NaN/Inf or |C| >= 2^31) at iteration " + std::to_string(h->hst.iter));
+    if (err & ERRB_TIMEOUT) return fail(h, FCIQMC_ERR_TIMEOUT, "device wait timed out");
+    if (err == ERRB_PAUSE_SEMI) {
+        rc = build_semistochastic(h);
+        if (rc) return rc;
+        h->hst.err = 0;
+        return write_state(h);
+    }
+    if (++*retries > 64) return fail(h, FCIQMC_ERR_CAPACITY, "capacity growth did not converge");
+    const long long need = h->hst.need_spawn;
+    rc = reset_after_error(h);
+    if (rc) return rc;
+    if (err & (ERRB_SPAWN_CAP | ERRB_MAIN_CAP)) {
+        // a new list too large for its bucket, or spawns spread evenly over
+        // crowded buckets: split buckets.  Spawns concentrated on a few
+        // determinants: enlarge the spawn regions to what was needed.
+        const long long nbk = 1LL << h->bb;
+        const long long spawns_prev = h->hist.empty() ? 0 : h->hist.back().spawns;
+        const bool even = spawns_prev > nbk * (long long)h->hi.cap_s / 2;
+        if ((err & ERRB_MAIN_CAP) || ((err & ERRB_SPAWN_CAP) && even)) rc = grow_buckets(h);
+        else rc = grow_spawn_capacity(h, need);
+        if (rc) return rc;
+        rc = reset_after_error(h);
+        if (rc) return rc;
+    }
+    if (err & ERRB_HEAVY_CAP) {
+        rc = grow_heavy(h);
+        if (rc) return rc;
+    }
+    rc = upload_inst(h);
+    if (rc) return rc;
+    return capture_graph(h);
 }
 
 int64_t fciqmc_num_dets(fciqmc_handle *h)

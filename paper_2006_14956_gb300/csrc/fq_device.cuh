@@ -73,7 +73,7 @@ __device__ __forceinline__ void philox(u64 c0, u64 c1, u64 c2, u64 c3, u64 k0, u
 
 __device__ __forceinline__ double u53(u64 w) { return (double)(w >> 11) * 0x1p-53; }
 
-// Eq. (2): |v| >= c_min kept; else sign(v) c_min with probability |v|/c_min, else 0
+// Eq. (3): |v| >= c_min kept; else sign(v) c_min with probability |v|/c_min, else 0
 __device__ __forceinline__ double round_stoch(double v, double cmin, double u)
 {
     if (v == 0.0 || fabs(v) >= cmin) return v;

@@ -68,8 +68,10 @@ struct IterState {  // device-resident iteration state of one run
     double e_den;
     long long semi_built;   // 1 once D exists
     int big_n;              // buckets deferred to the large-bucket kernel
+    int need_spawn;         // largest spawn count of an overflowing bucket
+    int need_main;          // largest new-list size of an overflowing bucket
     int pad0;
-    long long pad[3];
+    long long pad[2];
 };
 
 // one run as seen by the kernels

@@ -1,10 +1,10 @@
 // kernels.cu -- the projector iteration of initiator-FCIQMC on GB300.
 //
-// One iteration (Eq. (3) of Guther et al. 2020) is four launches over the
+// One iteration (Eq. (4) of Guther et al. 2020) is four launches over the
 // bucketed walker list of every run in the batch:
 //   k_spawn        (a) spawning: ceil(|C_i|) attempts per determinant, one
 //                  Philox block, one excitation and one Slater-Condon element
-//                  per attempt; survivors of the rounding of Eq. (2) are
+//                  per attempt; survivors of the rounding of Eq. (3) are
 //                  appended to the spawn bucket of their target.
 //   k_spawn_heavy  the same for determinants with more than HEAVY_ATT walkers,
 //                  split into fixed-size slices so no block waits on one
@@ -14,7 +14,7 @@
 //                  counting sort, apply death and rounding, sum the spawns
 //                  exactly, apply the initiator rule and rounding, write the
 //                  new bucket, compute H_jj for new determinants, and reduce
-//                  N_w, E_num (Eq. (8)) and counters per bucket.
+//                  N_w, E_num (Eq. (9)) and counters per bucket.
 //   k_finalize     per run: total the bucket reductions, update the shift,
 //                  append the statistics row, flip the buffers.
 // All of them read the iteration state from device memory, so one iteration
@@ -386,7 +386,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int *wsum, int *total)
 }
 
 // Death, annihilation and the reductions of one bucket b (steps (b) and (c)
-// of Eq. (3)).  All threads of the block call this together.
+// of Eq. (4)).  All threads of the block call this together.
 template <typename IDX>
 __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int gbits, int b, int par, long long it,
                             double shift, int m, int si, int sn)
@@ -481,7 +481,7 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int gbi
                 if (fl & DFLAG_D) {
                     cp = I.dc_new[d_index(I, ba, bb2)];
                 } else {
-                    // (b) death: C (1 - tau (H_ii - E_ref - S)), then Eq. (2)
+                    // (b) death: C (1 - tau (H_ii - E_ref - S)), then Eq. (3)
                     double f = 1.0 - I.tau * (ohd[base + me] - shift);
                     cp = c0 * f;
                     if (cp != 0.0 && fabs(cp) < I.cmin) {
@@ -522,7 +522,7 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int gbi
     int total;
     int o = block_excl_scan(nk, S.wsum, &total);
     const bool overflow = total > CAP_M;
-    if (overflow && t == 0) atomicOr(&I.st->err, ERRB_MAIN_CAP);
+    if (overflow && t == 0) { atomicOr(&I.st->err, ERRB_MAIN_CAP); atomicMax(&I.st->need_main, total); }
 
     // 4. pass 2: write the new bucket in (group, key) order; reductions
     const int np = par ^ 1;
@@ -645,7 +645,7 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k_annihilate(const DevInst *__r
         const int b = u - I.unit0;
         const int m = I.cnt[par][b], si = I.scnt_i[b], sn = I.scnt_n[b];
         if (si + sn > I.cap_s) {
-            if (t == 0) atomicOr(&I.st->err, ERRB_SPAWN_CAP);
+            if (t == 0) { atomicOr(&I.st->err, ERRB_SPAWN_CAP); atomicMax(&I.st->need_spawn, si + sn); }
             continue;
         }
         if (m + si + sn > EMAX) {  // too large for shared memory: deferred to k_annihilate_big

@@ -5,7 +5,7 @@ amplitudes, H_ii - E_ref, flags, walker numbers, shifts and every counter must
 agree bit for bit: every random decision is keyed by (determinant, iteration,
 attempt), every multi-term sum that feeds the dynamics is an exact sum rounded
 once, and both sides evaluate the remaining binary64 expressions in the same
-order without fused multiply-adds.  Only E_num (Eq. (8)), a diagnostic that
+order without fused multiply-adds.  Only E_num (Eq. (9)), a diagnostic that
 does not feed back, is summed in a different order on the two sides; it is
 compared within 1e-11 relative (each side's rounding error is below
 n * 2^-53 * sum |terms| with n <= 1e4 terms per bucket tree level).
@@ -46,7 +46,7 @@ def assert_stats_equal(gs, os_, first=0):
     n = len(os_["iter"]) - first
     assert len(gs["iteration"]) >= n
     for k in EXACT_STATS:
-        ok = "iter" if k == "iteration" else k
+        ok = {"iteration": "iter", "shift": "S"}.get(k, k)
         a = np.asarray(gs[k][-n:])
         b = np.asarray(os_[ok][first:])
         if a.dtype.kind == "f":
@@ -57,8 +57,14 @@ def assert_stats_equal(gs, os_, first=0):
     np.testing.assert_allclose(en_g, en_o, rtol=1e-11, atol=1e-9)
 
 
+# A critically damped shift (zeta/(A tau) * A tau = zeta = 0.5 over A = 5)
+# keeps the population near its target, so the oracle finishes in seconds.
+DAMP = dict(shift_damping=0.5, shift_interval=5)
+
+
 def run_pair(sysd, params, n_iter, chunks=1):
     fq = _fq()
+    params = dict(DAMP, **params)
     g = fq.fciqmc_create(sysd, params)
     o = oracle.Run(oracle.system_from_workload(sysd), **params)
     per = n_iter // chunks
@@ -103,11 +109,16 @@ def test_gpu_matches_oracle_bit_exact(name):
     assert sh["S"] == osh["S"] and sh["vary"] == osh["vary"] and sh["nw_last"] == osh["nw_last"]
 
 
+# The 24-orbital system's prescribed tau = 1e-3 exceeds 1/sum_j |H_ref,j| (no
+# shift can hold the walker number there); these tests use the benchmark's 2e-4.
+TAU24 = 2e-4
+
+
 def test_abinitio_24_orbitals_bit_exact():
     """The 24-orbital, 6+6-electron synthetic system (96 Cholesky vectors,
-    initiator threshold 3, tau 1e-3) at a reduced walker target."""
+    initiator threshold 3) at a reduced walker target."""
     sysd, params = workloads.config_abinitio_24()
-    params = dict(params, target_walkers=2e4)
+    params = dict(params, tau=TAU24, target_walkers=2e4)
     fq, g, o = run_pair(sysd, params, 160, chunks=2)
     assert_states_equal(fq.fciqmc_export_state(g), o.export())
     assert_stats_equal(fq.fciqmc_iter_stats_get(g), o.stats())
@@ -128,7 +139,7 @@ def test_capacity_growth_is_bit_identical():
     each overflowing iteration is repeated after growth with identical results."""
     fq = _fq()
     sysd = workloads.hubbard_2d(4, 4, 2.0)
-    params = dict(tau=0.005, target_walkers=3e4, initiator_threshold=3.0, seed=17, max_dets=16)
+    params = dict(DAMP, tau=0.005, target_walkers=3e4, initiator_threshold=3.0, seed=17, max_dets=16)
     g = fq.fciqmc_create(sysd, params)
     assert fq.fciqmc_layout(g)["buckets"] == 1
     o = oracle.Run(oracle.system_from_workload(sysd), **{k: v for k, v in params.items() if k != "max_dets"})
@@ -141,7 +152,7 @@ def test_capacity_growth_is_bit_identical():
 
 def test_checkpoint_restart_continues_identically():
     fq = _fq()
-    sysd, params = workloads.small_abinitio(8, 3, 3, seed=5), dict(tau=0.005, target_walkers=3000,
+    sysd, params = workloads.small_abinitio(8, 3, 3, seed=5), dict(DAMP, tau=0.005, target_walkers=3000,
                                                                     initiator_threshold=3.0, seed=11)
     g1 = fq.fciqmc_create(sysd, params)
     fq.fciqmc_step(g1, 200)
@@ -184,12 +195,14 @@ def test_full_size_sampled_parity_abinitio_24():
     over the whole list."""
     fq = _fq()
     sysd, params = workloads.config_abinitio_24()
-    g = fq.fciqmc_create(sysd, dict(params, initial_walkers=1e6))
+    params = dict(params, tau=TAU24, initial_walkers=6.25e5, target_walkers=6.25e5, shift_damping=1.0,
+                  shift_interval=2)
+    g = fq.fciqmc_create(sysd, params)
     fq.fciqmc_step(g, 300)
     st = fq.fciqmc_export_state(g)
     sh = fq.fciqmc_export_shift(g)
     assert st["c"].size > 1e5
-    o = oracle.Run(oracle.system_from_workload(sysd), **dict(params, initial_walkers=1e6))
+    o = oracle.Run(oracle.system_from_workload(sysd), **params)
     o.import_state(st["alpha"], st["beta"], st["c"], sh["iteration"], sh["S"], sh["vary"], sh["shift_start"],
                    sh["cnt"], sh["nw_last"])
     fq.fciqmc_step(g, 1)
@@ -198,4 +211,8 @@ def test_full_size_sampled_parity_abinitio_24():
     gs = fq.fciqmc_iter_stats_get(g)
     os_ = o.stats()
     for k in ["nw", "shift", "ndet", "attempts", "spawns", "rejected", "annihilated"]:
-        assert bits(gs[k][-1:])[0] == bits(os_[k][-1:])[0] if gs[k].dtype.kind == "f" else gs[k][-1] == os_[k][-1], k
+        ok = {"shift": "S"}.get(k, k)
+        if gs[k].dtype.kind == "f":
+            assert bits(gs[k][-1:])[0] == bits(os_[ok][-1:])[0], k
+        else:
+            assert gs[k][-1] == os_[ok][-1], k

@@ -3,7 +3,7 @@
 Each test ties one part of the oracle to an independent source: a library
 routine (numpy Philox, math.fsum, numpy.log), brute-force operator algebra,
 closed-form energies, exact enumeration of generation probabilities, and the
-exact expectation value of one projector step (Eq. (1) of the paper).
+exact expectation value of one projector step (Eq. (2) of the paper).
 """
 import itertools
 import math
@@ -265,7 +265,7 @@ def test_projected_energy_exact_for_eigenstate(which):
 
 # ----------------------------------------------------------------- one projector step
 def _expected_step(s, dets, c, tau, S, n_a, Hrel):
-    """E[C(t+dt)] for one iteration from amplitudes c (Eq. (3) with the
+    """E[C(t+dt)] for one iteration from amplitudes c (Eq. (4) with the
     initiator rule: a spawn from a non-initiator onto an unoccupied
     determinant is removed)."""
     ref = dets.index(s.ref)
@@ -282,7 +282,7 @@ def _expected_step(s, dets, c, tau, S, n_a, Hrel):
 @pytest.mark.parametrize("case", ["hubbard_plain", "abinitio_plain", "abinitio_initiator", "hubbard_semistoch"])
 def test_one_step_expectation(case):
     """Averaged over independent seeds, one oracle iteration must reproduce
-    (1 - dtau (H - S)) C (plain FCIQMC, Eq. (1)), or its initiator-truncated
+    (1 - dtau (H - S)) C (plain FCIQMC, Eq. (2)), or its initiator-truncated
     form.  A wrong sign, p_gen, weight, death factor, rounding, initiator
     filter or summation shows up as a biased component."""
     rng = np.random.default_rng(1)
