@@ -83,7 +83,8 @@ typedef struct {
  * S <- S - shift_damping / (A tau) * ln(N_w(t) / N_w(t - A)).
  * initiator_threshold n_a: a determinant is an initiator when |C| > n_a (or
  * it is the reference, or it lies in D); 0 gives plain FCIQMC.  c_min:
- * rounding threshold of Eq. (3).  p_single: probability of proposing a single
+ * rounding threshold of Eq. (3); tau <= 0 selects tau = 0.5 / sum_j |H_ref,j|
+ * (see fciqmc_ref_offdiag_sum).  p_single: probability of proposing a single
  * excitation (App. A).  semistoch_size: N_D of Sec. III (0 = off), chosen
  * semistoch_start iterations after the shift starts to vary.
  * max_dets / max_spawns: capacity hints (0 = derived from target_walkers);
@@ -226,6 +227,50 @@ int64_t fciqmc_iter_stats_count(fciqmc_handle *h);
  * Each run's results are bit-identical to running it alone.  All handles
  * must be distinct; they are synchronised on the first handle's stream. */
 int fciqmc_step_batch(fciqmc_handle **hs, int32_t k, int64_t n_iter);
+
+/* sum_j |<D_j|H|D_ref>| over all single and double excitations of the
+ * reference, computed on the device in a fixed order (deterministic).  A run
+ * created with tau <= 0 uses tau = 0.5 / this sum: a walker spawns
+ * tau sum_j |H_ij| walkers per iteration in expectation, and only when that is
+ * below 1 can the shift hold the walker number. */
+int fciqmc_ref_offdiag_sum(fciqmc_handle *h, double *out);
+double fciqmc_tau(fciqmc_handle *h);
+
+/* ---- serving: runs admitted by device memory and stepped together ----
+ * A request is a system + parameters + a target error; the server admits
+ * queued requests (first come, first served) while the sum of the device
+ * memory of running requests stays within mem_budget_bytes and at most
+ * max_active run, advances all running requests together (one batched launch
+ * per iteration, fciqmc_step_batch), and retires a request when the blocking
+ * error of its projected energy is below target_sigma with at least 200
+ * samples after equilibration, or after max_iters iterations.  Each result is
+ * identical to running the request alone. */
+typedef struct fciqmc_server fciqmc_server;
+typedef struct {
+    int32_t state;        /* 0 queued, 1 running, 2 converged, 3 stopped at max_iters, 4 failed */
+    int32_t error;        /* status code of a failed request */
+    int64_t iterations;
+    double energy;        /* E_proj mean (absolute) */
+    double sigma;         /* its blocking error */
+    double shift;
+    double t_submit;      /* seconds on the server's clock */
+    double t_start;
+    double t_done;
+    int64_t attempts;
+    int64_t device_bytes; /* peak device memory of the run */
+    double tau;
+} fciqmc_request_status;
+
+int fciqmc_server_create(int64_t mem_budget_bytes, int32_t max_active, void *stream, fciqmc_server **out);
+/* copies sys (including the integral arrays) and params; returns the request id */
+int fciqmc_server_submit(fciqmc_server *srv, const fciqmc_system *sys, const fciqmc_params *params,
+                         double target_sigma, int64_t max_iters, int64_t *id);
+/* one scheduling round: admit, advance every running request by n_iter
+ * iterations, retire finished ones; *n_active = running + queued afterwards */
+int fciqmc_server_tick(fciqmc_server *srv, int64_t n_iter, int32_t *n_active);
+int fciqmc_server_poll(fciqmc_server *srv, int64_t id, fciqmc_request_status *out);
+double fciqmc_server_clock(fciqmc_server *srv);
+void fciqmc_server_destroy(fciqmc_server *srv);
 
 /* Device timing of the kernels of the last fciqmc_step call (milliseconds per
  * iteration, averaged), measured with CUDA events on the handle's stream:

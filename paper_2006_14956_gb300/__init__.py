@@ -81,6 +81,14 @@ class fciqmc_stats(C.Structure):
                 ("vary", C.c_int32), ("pad0", C.c_int32)]
 
 
+class fciqmc_request_status(C.Structure):
+    _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("iterations", C.c_int64), ("energy", C.c_double),
+                ("sigma", C.c_double), ("shift", C.c_double), ("t_submit", C.c_double), ("t_start", C.c_double),
+                ("t_done", C.c_double), ("attempts", C.c_int64), ("device_bytes", C.c_int64), ("tau", C.c_double)]
+
+
+REQUEST_STATES = {0: "queued", 1: "running", 2: "converged", 3: "max_iters", 4: "failed"}
+
 _H = C.c_void_p
 _u64p = C.POINTER(C.c_uint64)
 _dp = C.POINTER(C.c_double)
@@ -106,6 +114,15 @@ _SIGS = {
     "fciqmc_set_profiling": (C.c_int, [_H, C.c_int32]),
     "fciqmc_kernel_times": (C.c_int, [_H, _dp]),
     "fciqmc_layout": (C.c_int, [_H, C.POINTER(C.c_int64)]),
+    "fciqmc_ref_offdiag_sum": (C.c_int, [_H, _dp]),
+    "fciqmc_tau": (C.c_double, [_H]),
+    "fciqmc_server_create": (C.c_int, [C.c_int64, C.c_int32, C.c_void_p, C.POINTER(_H)]),
+    "fciqmc_server_submit": (C.c_int, [_H, C.POINTER(fciqmc_system), C.POINTER(fciqmc_params), C.c_double,
+                                       C.c_int64, C.POINTER(C.c_int64)]),
+    "fciqmc_server_tick": (C.c_int, [_H, C.c_int64, C.POINTER(C.c_int32)]),
+    "fciqmc_server_poll": (C.c_int, [_H, C.c_int64, C.POINTER(fciqmc_request_status)]),
+    "fciqmc_server_clock": (C.c_double, [_H]),
+    "fciqmc_server_destroy": (None, [_H]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -186,15 +203,20 @@ DEFAULTS = dict(tau=0.01, shift_damping=0.1, target_walkers=1e4, initial_walkers
                 semistoch_start=100, max_dets=0, max_spawns=0, max_device_bytes=0)
 
 
-def fciqmc_create(system, params=None, stream=None, use_torch=True):
-    """Create a run; returns an opaque handle (keep the returned object alive)."""
+def _params_struct(params):
     p = dict(DEFAULTS)
     p.update(params or {})
-    s, keep = _system_struct(system)
     prm = fciqmc_params()
     ftypes = dict(fciqmc_params._fields_)
     for k in DEFAULTS:
         setattr(prm, k, float(p[k]) if ftypes[k] is C.c_double else int(p[k]))
+    return prm
+
+
+def fciqmc_create(system, params=None, stream=None, use_torch=True):
+    """Create a run; returns an opaque handle (keep the returned object alive)."""
+    s, keep = _system_struct(system)
+    prm = _params_struct(params)
     allocator = None
     if stream is None and use_torch:
         try:
@@ -320,3 +342,65 @@ def fciqmc_layout(handle):
     out = (C.c_int64 * 4)()
     _check(_lib.fciqmc_layout(handle.h, out), handle.h)
     return dict(buckets=out[0], cap_main=out[1], cap_spawn=out[2], device_bytes=out[3])
+
+
+def fciqmc_ref_offdiag_sum(handle):
+    out = C.c_double()
+    _check(_lib.fciqmc_ref_offdiag_sum(handle.h, C.byref(out)), handle.h)
+    return out.value
+
+
+def fciqmc_tau(handle):
+    return _lib.fciqmc_tau(handle.h)
+
+
+class Server:
+    """Owner of a fciqmc_server (device memory is allocated with cudaMalloc)."""
+
+    def __init__(self, h):
+        self.h = h
+        self._keep = []
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.fciqmc_server_destroy(self.h)
+            self.h = None
+
+
+def fciqmc_server_create(mem_budget_bytes, max_active=64, stream=None):
+    h = _H()
+    _check(_lib.fciqmc_server_create(int(mem_budget_bytes), int(max_active), stream, C.byref(h)))
+    return Server(h)
+
+
+def fciqmc_server_submit(server, system, params, target_sigma, max_iters):
+    s, keep = _system_struct(system)
+    prm = _params_struct(params)
+    rid = C.c_int64()
+    _check(_lib.fciqmc_server_submit(server.h, C.byref(s), C.byref(prm), float(target_sigma), int(max_iters),
+                                     C.byref(rid)))
+    return rid.value
+
+
+def fciqmc_server_tick(server, n_iter):
+    n = C.c_int32()
+    _check(_lib.fciqmc_server_tick(server.h, int(n_iter), C.byref(n)))
+    return n.value
+
+
+def fciqmc_server_poll(server, rid):
+    st = fciqmc_request_status()
+    _check(_lib.fciqmc_server_poll(server.h, int(rid), C.byref(st)))
+    d = {f: getattr(st, f) for f, _ in fciqmc_request_status._fields_}
+    d["state_name"] = REQUEST_STATES.get(d["state"], "?")
+    return d
+
+
+def fciqmc_server_clock(server):
+    return _lib.fciqmc_server_clock(server.h)
+
+
+def fciqmc_server_destroy(server):
+    if server.h:
+        _lib.fciqmc_server_destroy(server.h)
+        server.h = None

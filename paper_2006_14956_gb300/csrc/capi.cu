@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -64,6 +65,7 @@ struct fciqmc_handle {
     // semi-stochastic space
     int nd = 0;
     long long nnz = 0;
+    double ref_sum = 0.0;
     // asynchronous stepping
     bool pending = false;
     long long async_base = 0, async_target = 0;
@@ -322,16 +324,15 @@ static int grow_spawn_capacity(fciqmc_handle *h, long long need)
     ulonglong2 *nk = (ulonglong2 *)dev_alloc(h, nbk * (size_t)ncap * sizeof(ulonglong2));
     double *nw = (double *)dev_alloc(h, nbk * (size_t)ncap * sizeof(double));
     const int Ecap = CAP_M + ncap;
-    int gbits = GBITS;
-    while ((1 << gbits) < Ecap) gbits++;
-    const int G = 1 << gbits;
-    size_t stride = (size_t)Ecap * (sizeof(ulonglong2) + sizeof(double) + 12) + (size_t)(3 * G + 1) * 4;
+    int tabbits = TABBITS;
+    while ((1 << tabbits) < 2 * Ecap) tabbits++;
+    size_t stride = (size_t)Ecap * (sizeof(ulonglong2) + sizeof(double) + 8 + 8 + 4 + 4 + 4) + ((size_t)4 << tabbits);
     stride = (stride + 255) & ~(size_t)255;
     unsigned char *scr = (unsigned char *)dev_alloc(h, stride * BIG_BLOCKS);
     if (!nk || !nw || !scr) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (spawn buffers)");
     dev_free(h, I.skey); dev_free(h, I.sw); dev_free(h, I.big_scratch);
     I.skey = nk; I.sw = nw; I.cap_s = ncap;
-    I.big_scratch = scr; I.big_stride = stride; I.big_gbits = gbits;
+    I.big_scratch = scr; I.big_stride = stride; I.big_tabbits = tabbits;
     return FCIQMC_OK;
 }
 
@@ -385,7 +386,106 @@ static int pull_history(fciqmc_handle *h, long long from, long long to)
     return FCIQMC_OK;
 }
 
-int build_semistochastic(fciqmc_handle *h);  // semistoch.cu
+// ------------------------------------------------------------------ semi-stochastic set-up (Sec. III)
+// D = the N_D determinants of largest |C| (ties: ascending key), found by a
+// 16-bit-digit radix selection over the bit patterns of |C| on the device;
+// H^D in CSR built on the device; the main list flags D and pins it.
+static int build_semistochastic(fciqmc_handle *h)
+{
+    DevInst &I = h->hi;
+    const int par = h->hst.parity, nbk = 1 << h->bb;
+    std::vector<int> cnt(nbk);
+    CUDA_TRY(h, cudaMemcpy(cnt.data(), I.cnt[par], nbk * sizeof(int), cudaMemcpyDeviceToHost));
+    long long ndet = 0;
+    for (int c : cnt) ndet += c;
+    const long long nd = std::min<long long>(h->p.semistoch_size, ndet);
+    h->hst.semi_built = 1;
+    if (nd <= 0) return FCIQMC_OK;
+    unsigned *dhist = (unsigned *)dev_alloc(h, 65536 * sizeof(unsigned));
+    if (!dhist) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (semi-stochastic selection)");
+    std::vector<unsigned> hist(65536);
+    u64 prefix = 0;
+    long long need = nd, ties = 0;
+    for (int shift = 0; shift < 64; shift += 16) {
+        CUDA_TRY(h, cudaMemsetAsync(dhist, 0, 65536 * sizeof(unsigned), h->stream));
+        launch_abs_hist(h->dinst, par, nbk, shift, prefix, dhist, h->stream);
+        CUDA_TRY(h, cudaMemcpyAsync(hist.data(), dhist, 65536 * sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        long long acc = 0;
+        int d = 65535;
+        for (; d > 0; d--) {
+            if (acc + hist[d] >= need) break;
+            acc += hist[d];
+        }
+        need -= acc;
+        ties = hist[d];
+        prefix = (prefix << 16) | (u64)d;
+    }
+    const u64 thr = prefix;  // bit pattern of the N_D-th largest |C|
+    const int cap = (int)(nd - need + ties);
+    ulonglong2 *ckeys = (ulonglong2 *)dev_alloc(h, (size_t)cap * sizeof(ulonglong2));
+    u64 *cmags = (u64 *)dev_alloc(h, (size_t)cap * sizeof(u64));
+    int *dn = (int *)dev_alloc(h, sizeof(int));
+    if (!ckeys || !cmags || !dn) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (semi-stochastic selection)");
+    CUDA_TRY(h, cudaMemsetAsync(dn, 0, sizeof(int), h->stream));
+    launch_abs_collect(h->dinst, par, nbk, thr, ckeys, cmags, dn, cap, h->stream);
+    std::vector<ulonglong2> keys(cap);
+    std::vector<u64> mags(cap);
+    int ncol = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&ncol, dn, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(keys.data(), ckeys, (size_t)cap * sizeof(ulonglong2), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(mags.data(), cmags, (size_t)cap * sizeof(u64), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (ncol != cap) return fail(h, FCIQMC_ERR_CUDA, "semi-stochastic selection count mismatch");
+    std::vector<ulonglong2> sel, tie;
+    for (int i = 0; i < cap; i++) (mags[i] > thr ? sel : tie).push_back(keys[i]);
+    auto kless = [](const ulonglong2 &x, const ulonglong2 &y) { return x.x < y.x || (x.x == y.x && x.y < y.y); };
+    std::sort(tie.begin(), tie.end(), kless);
+    for (long long i = 0; i < need; i++) sel.push_back(tie[(size_t)i]);
+    std::sort(sel.begin(), sel.end(), kless);
+    dev_free(h, dhist); dev_free(h, ckeys); dev_free(h, cmags); dev_free(h, dn);
+    // open-addressing set of D keys
+    int hb = 1;
+    while ((1LL << hb) < 2 * nd) hb++;
+    std::vector<u64> tabk((size_t)2 << hb, 0ULL);
+    for (const auto &k : sel) {
+        u64 sl = det_hash_host(k.x, k.y) & (((u64)1 << hb) - 1);
+        while (tabk[2 * sl] || tabk[2 * sl + 1]) sl = (sl + 1) & (((u64)1 << hb) - 1);
+        tabk[2 * sl] = k.x;
+        tabk[2 * sl + 1] = k.y;
+    }
+    ulonglong2 *dkey = (ulonglong2 *)dev_alloc(h, (size_t)nd * sizeof(ulonglong2));
+    u64 *dtab = (u64 *)dev_alloc(h, tabk.size() * sizeof(u64));
+    long long *rowcnt = (long long *)dev_alloc(h, (size_t)nd * sizeof(long long));
+    long long *rowptr = (long long *)dev_alloc(h, (size_t)(nd + 1) * sizeof(long long));
+    double *dcn = (double *)dev_alloc(h, (size_t)nd * sizeof(double));
+    double *dcc = (double *)dev_alloc(h, (size_t)nd * sizeof(double));
+    if (!dkey || !dtab || !rowcnt || !rowptr || !dcn || !dcc) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (D)");
+    CUDA_TRY(h, cudaMemcpy(dkey, sel.data(), (size_t)nd * sizeof(ulonglong2), cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(dtab, tabk.data(), tabk.size() * sizeof(u64), cudaMemcpyHostToDevice));
+    launch_build_hd(h->dinst, (int)nd, dkey, rowcnt, nullptr, nullptr, nullptr, 0, h->stream);
+    std::vector<long long> rc((size_t)nd), rp((size_t)nd + 1, 0);
+    CUDA_TRY(h, cudaMemcpyAsync(rc.data(), rowcnt, (size_t)nd * sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    for (long long r = 0; r < nd; r++) rp[r + 1] = rp[r] + rc[r];
+    const long long nnz = rp[nd];
+    int *dcol = (int *)dev_alloc(h, (size_t)nnz * sizeof(int));
+    double *dval = (double *)dev_alloc(h, (size_t)nnz * sizeof(double));
+    if (!dcol || !dval) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (H^D)");
+    CUDA_TRY(h, cudaMemcpy(rowptr, rp.data(), (size_t)(nd + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+    launch_build_hd(h->dinst, (int)nd, dkey, rowcnt, rowptr, dcol, dval, 1, h->stream);
+    dev_free(h, rowcnt);
+    I.nd = (int)nd; I.dkey = dkey; I.drow = rowptr; I.dcol = dcol; I.dval = dval; I.dc_new = dcn; I.dc_cur = dcc;
+    I.dhash_keys = dtab; I.dhash_bits = hb;
+    int rc2 = upload_inst(h);
+    if (rc2) return rc2;
+    launch_mark_d(h->dinst, par, nbk, h->stream);
+    CUDA_TRY(h, cudaGetLastError());
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->nd = (int)nd;
+    h->nnz = nnz;
+    return capture_graph(h);
+}
 
 // ------------------------------------------------------------------ C ABI
 extern "C" {
@@ -415,7 +515,7 @@ int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_han
         return rc;
     };
     const fciqmc_params &P = h->p;
-    if (!(P.tau > 0.0) || !(P.c_min > 0.0) || !(P.initial_walkers > 0.0) || P.shift_interval < 1 ||
+    if (!(P.tau == P.tau) || !(P.c_min > 0.0) || !(P.initial_walkers > 0.0) || P.shift_interval < 1 ||
         !(P.p_single >= 0.0 && P.p_single <= 1.0) || !(P.initiator_threshold >= 0.0) || !(P.shift_damping >= 0.0) ||
         !(P.target_walkers > 0.0) || !std::isfinite(P.initial_shift))
         return bail(FCIQMC_ERR_INVALID_ARG, "invalid parameters (tau, c_min, initial_walkers, shift_interval, p_single, "
@@ -550,14 +650,20 @@ int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_han
     I.F = F; I.Fw = Fw;
     I.ref_a = h->ref_a; I.ref_b = h->ref_b; I.normask = normask;
     I.xref_lo = (u64)(u128)xref; I.xref_hi = (u64)((u128)xref >> 64);
-    for (int c = 0; c < NCLS; c++) I.lam[c] = P.tau / pgen_class(h, c);
+    const bool auto_tau = !(P.tau > 0.0);
     I.tmt = -h->t;
     {
         double q = P.p_single * 0x1p53;  // exact
         I.tsingle = (u64)std::ceil(q);
     }
-    I.seed = P.seed; I.tau = P.tau; I.cmin = P.c_min; I.n_a = P.initiator_threshold;
-    I.cz = P.shift_damping / ((double)P.shift_interval * P.tau);
+    I.seed = P.seed; I.cmin = P.c_min; I.n_a = P.initiator_threshold;
+    {
+        int e2;
+        double fr = std::frexp(P.c_min, &e2);
+        I.cmin_pow2 = fr == 0.5;  // c_min = 2^(e2-1)
+        I.cmin_log2 = e2 - 1;
+    }
+
     I.target = P.target_walkers; I.A = P.shift_interval;
     I.semi_start = P.semistoch_start; I.semi_size = P.semistoch_size;
     I.ring_cap = h->ring_cap;
@@ -583,6 +689,22 @@ int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_han
     if (!h->nbr.empty()) cudaMemcpyAsync(dnbr, h->nbr.data(), h->nbr.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream);
     I.h = dh; I.eri = deri; I.hfx = dhfx; I.Jfx = dJ; I.Kfx = dK; I.nbr = dnbr;
     I.st = h->dstate;
+    // time step: given, or 0.5 / sum_j |H_ref,j| (computed on the device)
+    {
+        double *dpart = (double *)dev_alloc(h, 64 * sizeof(double));
+        if (!dpart) return bail(FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory");
+        if (cudaMemcpyAsync(h->dinst, &I, sizeof(DevInst), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+            ref_abs_sum(h->dinst, dpart, &h->ref_sum, h->stream) != cudaSuccess)
+            return bail(FCIQMC_ERR_CUDA, "reference coupling sum failed");
+        dev_free(h, dpart);
+        if (auto_tau) {
+            if (!(h->ref_sum > 0.0)) return bail(FCIQMC_ERR_INVALID_ARG, "tau <= 0 needs a reference with couplings");
+            h->p.tau = 0.5 / h->ref_sum;
+        }
+        I.tau = h->p.tau;
+        for (int c = 0; c < NCLS; c++) I.lam[c] = h->p.tau / pgen_class(h, c);
+        I.cz = P.shift_damping / ((double)P.shift_interval * h->p.tau);
+    }
 
     // bucket layout: average occupancy well below the per-bucket capacity
     // start at the expected size (capped: buffers grow on demand)
@@ -622,6 +744,7 @@ int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_han
     }
     memset(&h->hst, 0, sizeof(IterState));
     h->hst.S = P.initial_shift;
+    h->hst.stop_iter = LLONG_MAX;
     if (write_state(h)) return bail(FCIQMC_ERR_CUDA, h->err);
     if (upload_inst(h)) return bail(FCIQMC_ERR_CUDA, h->err);
     if (capture_graph(h)) return bail(FCIQMC_ERR_CUDA, h->err);
@@ -768,6 +891,13 @@ static int step_to(fciqmc_handle *h, long long target_iter)
 static int handle_flags(fciqmc_handle *h, int *retries)
 {
     int rc;
+    if (h->hst.err & ERRB_STOP) {  // left by a batch: clear and continue
+        h->hst.err &= ~ERRB_STOP;
+        h->hst.stop_iter = LLONG_MAX;
+        rc = write_state(h);
+        if (rc) return rc;
+        if (!h->hst.err) return FCIQMC_OK;
+    }
     const int err = h->hst.err;
     if (err & ERRB_NUMERIC)
         return fail(h, FCIQMC_ERR_NUMERIC, "numeric error (NaN/Inf or |C| >= 2^31) at iteration " + std::to_string(h->hst.iter));
@@ -928,6 +1058,7 @@ int fciqmc_import_state(fciqmc_handle *h, int64_t n, const uint64_t *alpha, cons
     launch_diag(h->dinst, par, (int)nbk, h->stream);
     CUDA_TRY(h, cudaGetLastError());
     memset(&h->hst, 0, sizeof(IterState));
+    h->hst.stop_iter = LLONG_MAX;
     h->hst.iter = iteration; h->hst.parity = par; h->hst.S = S; h->hst.vary = vary;
     h->hst.shift_start = shift_start; h->hst.cnt = cnt; h->hst.nwl_hi = nw_last_hi; h->hst.nwl_lo = nw_last_lo;
     rc = write_state(h);
@@ -939,6 +1070,135 @@ int fciqmc_import_state(fciqmc_handle *h, int64_t n, const uint64_t *alpha, cons
 }
 
 int64_t fciqmc_iter_stats_count(fciqmc_handle *h) { return h ? (int64_t)h->hist.size() : -1; }
+
+// Many runs per launch: one descriptor table covering the buckets of all
+// runs, one captured iteration graph; each run stops at its own target via
+// the stop iteration, and capacity flags are handled run by run.
+int fciqmc_step_batch(fciqmc_handle **hs, int32_t k, int64_t n_iter)
+{
+    if (!hs || k < 1 || n_iter < 0) return FCIQMC_ERR_INVALID_ARG;
+    for (int i = 0; i < k; i++) {
+        if (!hs[i]) return FCIQMC_ERR_INVALID_ARG;
+        for (int j = 0; j < i; j++)
+            if (hs[j] == hs[i]) return fail(hs[0], FCIQMC_ERR_INVALID_ARG, "a handle appears twice in the batch");
+    }
+    fciqmc_handle *h0 = hs[0];
+    std::vector<long long> target(k);
+    for (int i = 0; i < k; i++) {
+        fciqmc_handle *h = hs[i];
+        int rc = h->pending ? fciqmc_sync(h) : FCIQMC_OK;
+        if (rc) return rc;
+        rc = read_state(h);
+        if (rc) return rc;
+        if (h->hst.err) {  // leftover flags (e.g. a pending semi-stochastic set-up)
+            int retries = 0;
+            rc = handle_flags(h, &retries);
+            if (rc) return rc;
+        }
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        target[i] = h->hst.iter + n_iter;
+    }
+    DevInst *dinst = (DevInst *)dev_alloc(h0, (size_t)k * sizeof(DevInst));
+    int *dunit = (int *)dev_alloc(h0, (size_t)(k + 1) * sizeof(int));
+    if (!dinst || !dunit) return fail(h0, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (batch table)");
+    cudaGraphExec_t gexec = nullptr;
+    int units = 0, max_nd = 0;
+    auto cleanup = [&]() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+    };
+    auto rebuild = [&]() -> int {
+        std::vector<DevInst> tab(k);
+        std::vector<int> us(k + 1);
+        units = 0;
+        max_nd = 0;
+        for (int i = 0; i < k; i++) {
+            tab[i] = hs[i]->hi;
+            tab[i].unit0 = units;
+            us[i] = units;
+            units += 1 << hs[i]->bb;
+            max_nd = std::max(max_nd, hs[i]->nd);
+        }
+        us[k] = units;
+        CUDA_TRY(h0, cudaMemcpy(dinst, tab.data(), (size_t)k * sizeof(DevInst), cudaMemcpyHostToDevice));
+        CUDA_TRY(h0, cudaMemcpy(dunit, us.data(), (size_t)(k + 1) * sizeof(int), cudaMemcpyHostToDevice));
+        cleanup();
+        cudaGraph_t g;
+        CUDA_TRY(h0, cudaStreamBeginCapture(h0->stream, cudaStreamCaptureModeThreadLocal));
+        launch_spawn(dinst, dunit, k, units, h0->stream);
+        launch_spawn_heavy(dinst, k, h0->stream);
+        if (max_nd > 0) launch_semistoch(dinst, k, max_nd, h0->stream);
+        cudaError_t le = launch_annihilate(dinst, dunit, k, units, h0->stream);
+        launch_annihilate_big(dinst, k, h0->stream);
+        launch_finalize(dinst, k, h0->stream);
+        cudaError_t e = cudaStreamEndCapture(h0->stream, &g);
+        if (le != cudaSuccess || e != cudaSuccess) return fail(h0, FCIQMC_ERR_CUDA, "batch graph capture failed");
+        e = cudaGraphInstantiate(&gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(h0, FCIQMC_ERR_CUDA, "batch graph instantiate failed");
+        return FCIQMC_OK;
+    };
+    int rc = FCIQMC_OK;
+    for (int i = 0; i < k && !rc; i++) {
+        hs[i]->hst.stop_iter = target[i];
+        if (hs[i]->hst.iter >= target[i]) hs[i]->hst.err |= ERRB_STOP;
+        rc = write_state(hs[i]);
+    }
+    if (!rc) rc = rebuild();
+    long long chunk_max = 16;
+    std::vector<int> retries(k, 0);
+    while (!rc) {
+        long long remaining = 0;
+        for (int i = 0; i < k; i++) remaining = std::max(remaining, target[i] - hs[i]->hst.iter);
+        if (remaining <= 0) break;
+        const long long chunk = std::min<long long>(std::min<long long>(remaining, chunk_max), h0->ring_cap);
+        chunk_max = std::min<long long>(chunk_max * 2, h0->ring_cap);
+        std::vector<long long> start(k);
+        for (int i = 0; i < k; i++) start[i] = hs[i]->hst.iter;
+        for (long long c = 0; c < chunk && !rc; c++)
+            if (cudaGraphLaunch(gexec, h0->stream) != cudaSuccess) rc = fail(h0, FCIQMC_ERR_CUDA, "batch graph launch failed");
+        if (rc) break;
+        if (cudaStreamSynchronize(h0->stream) != cudaSuccess) { rc = fail(h0, FCIQMC_ERR_CUDA, "batch synchronisation failed"); break; }
+        bool changed = false;
+        for (int i = 0; i < k && !rc; i++) {
+            fciqmc_handle *h = hs[i];
+            rc = read_state(h);
+            if (rc) break;
+            rc = pull_history(h, start[i], h->hst.iter);
+            if (rc) break;
+            const int err = h->hst.err & ~ERRB_STOP;
+            if (err) {
+                chunk_max = 16;
+                const int bb0 = h->bb, nd0 = h->nd, cap0 = h->hi.cap_s, hc0 = h->heavy_cap;
+                h->hst.err = err;  // keep the stop flag off while handling
+                rc = handle_flags(h, &retries[i]);
+                if (rc) break;
+                if (h->bb != bb0 || h->nd != nd0 || h->hi.cap_s != cap0 || h->heavy_cap != hc0) changed = true;
+                h->hst.stop_iter = target[i];
+                if (h->hst.iter >= target[i]) h->hst.err |= ERRB_STOP;
+                rc = write_state(h);
+                changed = true;
+            } else if (!(h->hst.err & ERRB_STOP) && h->hst.iter >= target[i]) {
+                h->hst.err |= ERRB_STOP;
+                rc = write_state(h);
+            }
+        }
+        if (!rc && changed) rc = rebuild();
+    }
+    // restore the single-run state: no stop flag, own graph
+    for (int i = 0; i < k; i++) {
+        fciqmc_handle *h = hs[i];
+        if (read_state(h)) continue;
+        h->hst.err &= ~ERRB_STOP;
+        h->hst.stop_iter = LLONG_MAX;
+        write_state(h);
+        capture_graph(h);
+    }
+    cleanup();
+    dev_free(h0, dinst);
+    dev_free(h0, dunit);
+    return rc;
+}
 
 int fciqmc_iter_stats_get(fciqmc_handle *h, int64_t first, int64_t count, fciqmc_iter_stats *out)
 {
@@ -1032,3 +1292,206 @@ extern "C" int fciqmc_energy(fciqmc_handle *h, fciqmc_stats *out)
     }
     return FCIQMC_OK;
 }
+
+// ------------------------------------------------------------------ time step
+extern "C" int fciqmc_ref_offdiag_sum(fciqmc_handle *h, double *out)
+{
+    if (!h || !out) return FCIQMC_ERR_INVALID_ARG;
+    *out = h->ref_sum;
+    return FCIQMC_OK;
+}
+
+extern "C" double fciqmc_tau(fciqmc_handle *h) { return h ? h->p.tau : NAN; }
+
+// ------------------------------------------------------------------ serving
+#include <chrono>
+#include <deque>
+#include <map>
+
+namespace {
+
+struct Request {
+    int64_t id = 0;
+    fciqmc_system sys{};
+    std::vector<double> h1, eri;
+    fciqmc_params p{};
+    double target_sigma = 1e-3;
+    int64_t max_iters = 0;
+    fciqmc_request_status st{};
+    fciqmc_handle *h = nullptr;
+    int64_t est_bytes = 0;
+};
+
+}  // namespace
+
+struct fciqmc_server {
+    int64_t budget = 0;
+    int max_active = 0;
+    void *stream = nullptr;
+    std::chrono::steady_clock::time_point t0;
+    int64_t next_id = 1;
+    std::deque<int64_t> queue;
+    std::vector<int64_t> running;
+    std::map<int64_t, Request> req;
+    std::string err;
+    double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+};
+
+// device memory a request needs when admitted (its initial layout and integrals)
+static int64_t estimate_bytes(const Request &r)
+{
+    const int N = r.sys.kind == FCIQMC_HUBBARD ? r.sys.lx * r.sys.ly : r.sys.norb;
+    const double np = (double)N * (N + 1) / 2, ne = np * (np + 1) / 2;
+    double dets = r.p.max_dets > 0 ? (double)r.p.max_dets : std::min(std::max(4096.0, r.p.target_walkers), 8388608.0);
+    int bb = 0;
+    while (((double)(1LL << bb)) * (CAP_M / 2.5) < dets && bb < 24) bb++;
+    const double per_bucket = 2.0 * CAP_M * (16 + 8 + 8 + 1) + CAP_S0 * 24.0 + 2 * 8 + sizeof(Partial) + 3 * 4;
+    return (int64_t)((double)(1LL << bb) * per_bucket + 8.0 * (N * N + ne) + 48.0 * N * N + 4096.0 * 88 + 1.0e6);
+}
+
+extern "C" {
+
+int fciqmc_server_create(int64_t mem_budget_bytes, int32_t max_active, void *stream, fciqmc_server **out)
+{
+    if (!out || mem_budget_bytes <= 0 || max_active < 1) return FCIQMC_ERR_INVALID_ARG;
+    fciqmc_server *s = new fciqmc_server();
+    s->budget = mem_budget_bytes;
+    s->max_active = max_active;
+    s->stream = stream;
+    s->t0 = std::chrono::steady_clock::now();
+    *out = s;
+    return FCIQMC_OK;
+}
+
+double fciqmc_server_clock(fciqmc_server *srv) { return srv ? srv->now() : NAN; }
+
+int fciqmc_server_submit(fciqmc_server *srv, const fciqmc_system *sys, const fciqmc_params *params, double target_sigma,
+                         int64_t max_iters, int64_t *id)
+{
+    if (!srv || !sys || !params || !id || !(target_sigma > 0.0) || max_iters < 1) return FCIQMC_ERR_INVALID_ARG;
+    Request r;
+    r.id = srv->next_id++;
+    r.sys = *sys;
+    if (sys->kind == FCIQMC_ABINITIO) {
+        if (sys->norb < 1 || sys->norb > 64 || !sys->h1 || !sys->eri) return FCIQMC_ERR_INVALID_ARG;
+        const int64_t N = sys->norb, np = N * (N + 1) / 2, ne = np * (np + 1) / 2;
+        r.h1.assign(sys->h1, sys->h1 + N * N);
+        r.eri.assign(sys->eri, sys->eri + ne);
+    }
+    r.p = *params;
+    r.p.stream = srv->stream;
+    r.target_sigma = target_sigma;
+    r.max_iters = max_iters;
+    r.est_bytes = estimate_bytes(r);
+    r.st.state = 0;
+    r.st.t_submit = srv->now();
+    r.st.energy = NAN;
+    r.st.sigma = NAN;
+    *id = r.id;
+    srv->req[r.id] = std::move(r);
+    srv->queue.push_back(*id);
+    return FCIQMC_OK;
+}
+
+static void retire(fciqmc_server *srv, Request &r, int state)
+{
+    fciqmc_stats st;
+    if (r.h && fciqmc_energy(r.h, &st) == FCIQMC_OK) {
+        r.st.iterations = st.iteration;
+        r.st.energy = st.e_proj_mean;
+        r.st.sigma = st.e_proj_sigma;
+        r.st.shift = st.shift;
+        r.st.attempts = st.attempts_total;
+    }
+    if (r.h) {
+        r.st.device_bytes = std::max<int64_t>(r.st.device_bytes, (int64_t)r.h->bytes);
+        fciqmc_destroy(r.h);
+    }
+    r.h = nullptr;
+    r.st.state = state;
+    r.st.t_done = srv->now();
+}
+
+int fciqmc_server_tick(fciqmc_server *srv, int64_t n_iter, int32_t *n_active)
+{
+    if (!srv || n_iter < 1) return FCIQMC_ERR_INVALID_ARG;
+    // 1. admission: first come, first served, by device memory
+    int64_t used = 0;
+    for (int64_t id : srv->running) used += (int64_t)srv->req[id].h->bytes;
+    while (!srv->queue.empty() && (int)srv->running.size() < srv->max_active) {
+        Request &r = srv->req[srv->queue.front()];
+        if (!srv->running.empty() && used + r.est_bytes > srv->budget) break;
+        srv->queue.pop_front();
+        fciqmc_system sys = r.sys;
+        if (sys.kind == FCIQMC_ABINITIO) { sys.h1 = r.h1.data(); sys.eri = r.eri.data(); }
+        fciqmc_params p = r.p;
+        if (p.max_device_bytes <= 0) p.max_device_bytes = std::max<int64_t>(srv->budget - used, r.est_bytes);
+        int rc = fciqmc_create(&sys, &p, &r.h);
+        r.st.t_start = srv->now();
+        if (rc) {
+            r.st.state = 4;
+            r.st.error = rc;
+            r.st.t_done = r.st.t_start;
+            continue;
+        }
+        r.st.state = 1;
+        r.st.tau = r.h->p.tau;
+        used += (int64_t)r.h->bytes;
+        srv->running.push_back(r.id);
+    }
+    // 2. advance every running request together
+    if (!srv->running.empty()) {
+        std::vector<fciqmc_handle *> hs;
+        for (int64_t id : srv->running) hs.push_back(srv->req[id].h);
+        int rc = fciqmc_step_batch(hs.data(), (int32_t)hs.size(), n_iter);
+        if (rc) {
+            // find the failing run(s): step each alone to isolate the error
+            for (int64_t id : srv->running) {
+                Request &r = srv->req[id];
+                fciqmc_stats st;
+                if (fciqmc_energy(r.h, &st) != FCIQMC_OK || r.h->hst.err & ~(ERRB_STOP | ERRB_PAUSE_SEMI)) {
+                    r.st.error = rc;
+                    retire(srv, r, 4);
+                }
+            }
+        }
+    }
+    // 3. retire converged or exhausted requests
+    std::vector<int64_t> still;
+    for (int64_t id : srv->running) {
+        Request &r = srv->req[id];
+        if (!r.h) continue;
+        r.st.device_bytes = std::max<int64_t>(r.st.device_bytes, (int64_t)r.h->bytes);
+        fciqmc_stats st;
+        if (fciqmc_energy(r.h, &st) != FCIQMC_OK) { retire(srv, r, 4); continue; }
+        r.st.iterations = st.iteration;
+        r.st.energy = st.e_proj_mean;
+        r.st.sigma = st.e_proj_sigma;
+        r.st.attempts = st.attempts_total;
+        if (st.n_samples >= 200 && st.e_proj_sigma < r.target_sigma) retire(srv, r, 2);
+        else if (st.iteration >= r.max_iters) retire(srv, r, 3);
+        else still.push_back(id);
+    }
+    srv->running.swap(still);
+    if (n_active) *n_active = (int32_t)(srv->running.size() + srv->queue.size());
+    return FCIQMC_OK;
+}
+
+int fciqmc_server_poll(fciqmc_server *srv, int64_t id, fciqmc_request_status *out)
+{
+    if (!srv || !out) return FCIQMC_ERR_INVALID_ARG;
+    auto it = srv->req.find(id);
+    if (it == srv->req.end()) return FCIQMC_ERR_INVALID_ARG;
+    *out = it->second.st;
+    return FCIQMC_OK;
+}
+
+void fciqmc_server_destroy(fciqmc_server *srv)
+{
+    if (!srv) return;
+    for (auto &kv : srv->req)
+        if (kv.second.h) fciqmc_destroy(kv.second.h);
+    delete srv;
+}
+
+}  // extern "C"

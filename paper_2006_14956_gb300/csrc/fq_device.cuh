@@ -73,11 +73,72 @@ __device__ __forceinline__ void philox(u64 c0, u64 c1, u64 c2, u64 c3, u64 k0, u
 
 __device__ __forceinline__ double u53(u64 w) { return (double)(w >> 11) * 0x1p-53; }
 
-// Eq. (3): |v| >= c_min kept; else sign(v) c_min with probability |v|/c_min, else 0
-__device__ __forceinline__ double round_stoch(double v, double cmin, double u)
+// ---------------------------------------------------------------- binary64 by its bits
+// Exact integer forms of comparisons and conversions: on GB300 the FP64 pipe
+// issues at a small fraction of the integer rate, and these are exact.
+constexpr u64 SIGN64 = 0x8000000000000000ULL;
+__device__ __forceinline__ u64 dbits(double x) { return (u64)__double_as_longlong(x); }
+__device__ __forceinline__ double bitsd(u64 b) { return __longlong_as_double((long long)b); }
+__device__ __forceinline__ bool is_zero(double x) { return (dbits(x) << 1) == 0; }
+// |x| < y for y positive and finite (false for NaN x)
+__device__ __forceinline__ bool abs_lt(double x, double y) { return (dbits(x) & ~SIGN64) < dbits(y); }
+__device__ __forceinline__ double with_sign_of(double mag, double s) { return bitsd(dbits(mag) | (dbits(s) & SIGN64)); }
+
+// |x| = M 2^E with M the integer significand
+__device__ __forceinline__ void split_abs(double x, u64 &M, int &E)
 {
-    if (v == 0.0 || fabs(v) >= cmin) return v;
-    return u < fabs(v) / cmin ? copysign(cmin, v) : 0.0;
+    u64 b = dbits(x);
+    int ex = (int)((b >> 52) & 0x7ff);
+    M = b & 0xFFFFFFFFFFFFFULL;
+    if (ex) { M |= 1ULL << 52; E = ex - 1075; } else E = -1074;
+}
+
+// floor(|c| 2^32) for |c| < 2^31
+__device__ __forceinline__ u64 fx32(double c)
+{
+    u64 M;
+    int E;
+    split_abs(c, M, E);
+    int sh = E + 32;
+    if (sh >= 0) return M << sh;
+    return -sh >= 64 ? 0ULL : (M >> (-sh));
+}
+
+// ceil(|c|) for 0 < |c| < 2^31
+__device__ __forceinline__ u64 ceil_abs(double c)
+{
+    u64 M;
+    int E;
+    split_abs(c, M, E);
+    if (E >= 0) return M << E;
+    int s = -E;
+    return s >= 64 ? 1ULL : ((M + ((1ULL << s) - 1ULL)) >> s);
+}
+
+// Eq. (3) decision "u < |v| / c_min" with u = (w >> 11) 2^-53, for 0 < |v| < c_min.
+// When c_min = 2^k the quotient is exact and the test is the integer
+// comparison (w >> 11) < ceil(|v| 2^(53-k)); otherwise binary64 as written.
+__device__ __forceinline__ bool draw_keeps(u64 w, double v, double cmin, int cmin_log2, bool pow2)
+{
+    if (!pow2) return u53(w) < fabs(v) / cmin;
+    u64 M;
+    int E;
+    split_abs(v, M, E);
+    int sh = E + 53 - cmin_log2;
+    u64 T;
+    if (sh >= 0) T = M << sh;
+    else {
+        int s = -sh;
+        T = s >= 64 ? 1ULL : ((M + ((1ULL << s) - 1ULL)) >> s);
+    }
+    return (w >> 11) < T;
+}
+
+// Eq. (3): |v| >= c_min kept; else sign(v) c_min with probability |v|/c_min, else 0
+__device__ __forceinline__ double round_stoch(double v, double cmin, int cmin_log2, bool pow2, u64 w)
+{
+    if (is_zero(v) || !abs_lt(v, cmin)) return v;
+    return draw_keeps(w, v, cmin, cmin_log2, pow2) ? with_sign_of(cmin, v) : 0.0;
 }
 
 // ---------------------------------------------------------------- exact sums
@@ -137,8 +198,6 @@ __device__ __forceinline__ double fixed_to_double(i128 v, int F)
 __device__ __forceinline__ double u128_to_double(u128 u) { return fixed_to_double((i128)u, 0); }
 __device__ __forceinline__ double i128_to_double(i128 v) { return fixed_to_double(v, 0); }
 
-// floor(|c| 2^32); |c| < 2^31 checked by the caller
-__device__ __forceinline__ u64 fx32(double c) { return (u64)(fabs(c) * 4294967296.0); }
 
 __device__ __forceinline__ i128 shfl_xor_i128(i128 v, int m)
 {
@@ -151,7 +210,7 @@ __device__ __forceinline__ i128 shfl_xor_i128(i128 v, int m)
 // ---------------------------------------------------------------- logarithm
 // ln x = k ln2 + 2 atanh(s), x = m 2^k, m in (sqrt(1/2), sqrt(2)],
 // s = (m-1)/(m+1); the atanh series is summed in Horner form to z^11, z = s^2.
-__device__ double fq_ln(double x)
+static __device__ double fq_ln(double x)
 {
     if (!(x > 0.0) || isinf(x)) return __longlong_as_double(0x7ff8000000000000LL);
     u64 bits = (u64)__double_as_longlong(x);
@@ -184,7 +243,7 @@ __device__ __forceinline__ double eri4(const DevInst &I, int p, int q, int r, in
 
 // single excitation i -> a of spin sp from (pa, pb):
 // exact sum of h_ai + sum_{k occ, k != i} (ai|kk) - sum_{k occ same spin, k != i} (ak|ki)
-__device__ double single_exact(const DevInst &I, u64 pa, u64 pb, int sp, int i, int a)
+static __device__ double single_exact(const DevInst &I, u64 pa, u64 pb, int sp, int i, int a)
 {
     const int N = I.norb, F = I.F;
     i128 acc = to_fixed(__ldg(I.h + a * N + i), F);
@@ -205,7 +264,7 @@ __device__ double single_exact(const DevInst &I, u64 pa, u64 pb, int sp, int i, 
 
 // <D_j|H|D_i>, D_j != D_i (used for E_proj): Slater-Condon rules with the
 // same sign convention as the spawning code
-__device__ double hoff_generic(const DevInst &I, u64 ia, u64 ib, u64 ja, u64 jb)
+static __device__ double hoff_generic(const DevInst &I, u64 ia, u64 ib, u64 ja, u64 jb)
 {
     const int N = I.norb;
     u64 ra = ia & ~ja, rb = ib & ~jb, aa = ja & ~ia, ab = jb & ~ib;
@@ -243,10 +302,23 @@ __device__ double hoff_generic(const DevInst &I, u64 ia, u64 ib, u64 ja, u64 jb)
     return par ? -v : v;
 }
 
+// index of a determinant in the sorted key list of D, or -1
+__device__ __forceinline__ int d_index_of(const DevInst &I, u64 a, u64 b)
+{
+    int lo = 0, hi = I.nd;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const ulonglong2 k = I.dkey[mid];
+        if (k.x == a && k.y == b) return mid;
+        if (k.x < a || (k.x == a && k.y < b)) lo = mid + 1; else hi = mid;
+    }
+    return -1;
+}
+
 // H_ii - E_ref for determinant (a, b), computed by one warp: the exact sum
 // of h_pp over occupied orbitals and (pp|qq) - delta_spin (pq|qp) over
 // occupied pairs, minus the same sum for the reference, rounded once.
-__device__ double diag_exact_warp(const DevInst &I, u64 a, u64 b)
+static __device__ double diag_exact_warp(const DevInst &I, u64 a, u64 b)
 {
     const int lane = threadIdx.x & 31, N = I.norb;
     i128 part = 0;

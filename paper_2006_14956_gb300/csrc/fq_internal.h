@@ -24,6 +24,7 @@ enum {
     ERRB_NUMERIC = 8,     // NaN/Inf or |C|, |w| beyond 2^31
     ERRB_TIMEOUT = 16,    // bounded wait expired
     ERRB_PAUSE_SEMI = 32, // iteration boundary at which D must be built (not an error)
+    ERRB_STOP = 64,       // the run reached its stop iteration inside a batch (not an error)
 };
 enum { DFLAG_REF = 1, DFLAG_D = 2 };
 
@@ -31,9 +32,10 @@ enum { DFLAG_REF = 1, DFLAG_D = 2 };
 constexpr int K1_THREADS = 256;
 constexpr unsigned HEAVY_ATT = 2048;  // attempts per heavy chunk
 constexpr int K3_THREADS = 256;
-constexpr int EMAX = 3072;            // main + spawned records staged per bucket
-constexpr int CAP_M = 1536;           // main-list capacity per bucket
+constexpr int EMAX = 2048;            // main + spawned records staged per bucket in shared memory
+constexpr int CAP_M = 1024;           // main-list capacity per bucket
 constexpr int CAP_S0 = EMAX - CAP_M;  // initial spawn capacity per bucket (grows at run time)
+constexpr int TABBITS = 12;           // shared-memory hash table of the annihilation (2 x EMAX slots)
 constexpr int BIG_BLOCKS = 64;        // blocks of the large-bucket annihilation kernel
 constexpr int GBITS = 11;             // sub-hash groups per bucket in the annihilation sort
 constexpr int NGROUP = 1 << GBITS;
@@ -71,7 +73,8 @@ struct IterState {  // device-resident iteration state of one run
     int need_spawn;         // largest spawn count of an overflowing bucket
     int need_main;          // largest new-list size of an overflowing bucket
     int pad0;
-    long long pad[2];
+    long long stop_iter;    // K5 raises ERRB_STOP when iter reaches it
+    long long pad1;
 };
 
 // one run as seen by the kernels
@@ -94,6 +97,8 @@ struct DevInst {
     u64 tsingle;            // single excitation iff (w0 >> 11) < tsingle
     u64 seed;
     double tau, cmin, n_a;
+    int cmin_log2;          // c_min = 2^cmin_log2 when cmin_pow2
+    int cmin_pow2;
     double cz;              // shift_damping / (A tau)
     double target;
     long long A;
@@ -112,7 +117,7 @@ struct DevInst {
     int *scnt_i;
     int *scnt_n;
     int cap_s;              // spawn capacity per bucket
-    int big_gbits;          // sub-hash bits of the large-bucket path
+    int big_tabbits;        // hash-table bits of the large-bucket path
     int *big_list;          // deferred bucket ids (capacity = buckets)
     unsigned char *big_scratch;  // BIG_BLOCKS slices of big_stride bytes
     size_t big_stride;
@@ -127,7 +132,7 @@ struct DevInst {
     const ulonglong2 *dkey;
     const long long *drow;
     const int *dcol;
-    const double *dval;
+    const double *dval;     // H^D - E_ref on the diagonal
     double *dc_new;         // C_D after the exact projection of this iteration
     double *dc_cur;         // C_D after the last completed iteration
     const u64 *dhash_keys;  // open-addressing set of D keys (a, b interleaved), size dhash_cap
@@ -145,9 +150,14 @@ void launch_annihilate_big(const DevInst *dinst, int n_inst, cudaStream_t s);
 void launch_finalize(const DevInst *dinst, int n_inst, cudaStream_t s);
 void launch_rebucket(const DevInst *src, const DevInst *dst, int nb_src, int parity, cudaStream_t s);
 void launch_diag(const DevInst *dinst, int parity, int nb, cudaStream_t s);
-void launch_select_top(const DevInst *dinst, int parity, int nb, double *mag_out, ulonglong2 *key_out, cudaStream_t s);
-void launch_build_hd(const DevInst *dinst, int nd, long long *rowcount, int pass, cudaStream_t s);
+void launch_abs_hist(const DevInst *dinst, int par, int nb, int shift, u64 prefix, unsigned *hist, cudaStream_t s);
+void launch_abs_collect(const DevInst *dinst, int par, int nb, u64 thr, ulonglong2 *keys, u64 *mags, int *n, int cap,
+                        cudaStream_t s);
+void launch_build_hd(const DevInst *dinst, int nd, const ulonglong2 *dkey, long long *rowcnt, const long long *rowptr,
+                     int *col, double *val, int pass, cudaStream_t s);
 void launch_mark_d(const DevInst *dinst, int parity, int nb, cudaStream_t s);
+
+cudaError_t ref_abs_sum(const DevInst *dinst, double *dpartial, double *out, cudaStream_t s);
 
 // host helpers shared with capi.cu
 u64 det_hash_host(u64 a, u64 b);

@@ -132,13 +132,13 @@ __device__ void do_attempt(const DevInst &I, long long it, u64 pa, u64 pb, doubl
         double v = (cls == CLS_DOUBLE_AB) ? eri4(I, oa, oi, ob, oj) : eri4(I, oa, oi, ob, oj) - eri4(I, oa, oj, ob, oi);
         H = par ? -v : v;
     }
-    if (H == 0.0) return;
+    if (is_zero(H)) return;
     double ws = -(H * (I.lam[cls] * cper));
-    if (fabs(ws) < I.cmin) {
-        ws = round_stoch(ws, I.cmin, u53(w[3]));
-        if (ws == 0.0) return;
+    if (abs_lt(ws, I.cmin)) {
+        ws = round_stoch(ws, I.cmin, I.cmin_log2, I.cmin_pow2, w[3]);
+        if (is_zero(ws)) return;
     }
-    if (!(fabs(ws) < 0x1p31)) { atomicOr(&I.st->err, ERRB_NUMERIC); return; }
+    if (!abs_lt(ws, 0x1p31)) { atomicOr(&I.st->err, ERRB_NUMERIC); return; }
     if ((flags & 2u) && in_D(I, ta, tb)) return;  // D -> D is applied exactly
     int bt = bucket_of(det_hash(ta, tb), I.bb);
     const int cap_s = I.cap_s;
@@ -198,13 +198,12 @@ __global__ void __launch_bounds__(K1_THREADS) k_spawn(const DevInst *__restrict_
                 double c = I.c[par][base + d];
                 uint8_t f = I.fl[par][base + d];
                 pa = kk.x; pb = kk.y;
-                if (c != 0.0) {
-                    double mag = fabs(c);
-                    if (!(mag < 0x1p31)) {
+                if (!is_zero(c)) {
+                    if (!abs_lt(c, 0x1p31)) {
                         atomicOr(&I.st->err, ERRB_NUMERIC);
                     } else {
-                        nat = (u64)ceil(mag);
-                        bool init = mag > I.n_a || (f & (DFLAG_REF | DFLAG_D));
+                        nat = ceil_abs(c);
+                        bool init = (dbits(c) & ~SIGN64) > dbits(I.n_a) || (f & (DFLAG_REF | DFLAG_D));
                         fl = (init ? 1u : 0u) | ((f & DFLAG_D) ? 2u : 0u);
                         cper = c / (double)nat;
                         att += (long long)nat;
@@ -308,20 +307,26 @@ __global__ void __launch_bounds__(K1_THREADS) k_spawn_heavy(const DevInst *__res
 }
 
 // ------------------------------------------------------------------ annihilation
-// Staging arrays of one bucket: in shared memory (IDX = 16-bit) for buckets
-// of at most EMAX records, in a global scratch slice (IDX = 32-bit) for the
-// rare larger ones (a determinant that receives thousands of spawns).
+// Per bucket, one block: the bucket's walkers and spawns are staged (shared
+// memory for up to EMAX records, a global scratch slice for larger buckets)
+// and every distinct determinant gets one owner record through an
+// open-addressing table: walkers are inserted first, then every spawn finds
+// its target or inserts itself as the owner of a new determinant.  Accepted
+// weights are added to the owner's exact 128-bit accumulator with two 64-bit
+// atomics (the low word's carry goes to the high word), so the sum does not
+// depend on the order of arrival.
 template <typename IDX>
 struct Stage {
     ulonglong2 *key;
-    double *val;
-    IDX *perm;
-    IDX *lead;   // leaders of each group in key order; top bit = kept
-    IDX *grp;
-    IDX *goff;
-    int *cur;
-    IDX *nlead;
+    double *val;      // C (walkers) or w (spawns); after death C', after annihilation the result
+    u64 *acc_lo;
+    u64 *acc_hi;
+    int *nacc;        // accepted spawns per owner
+    int *eflag;       // EF_* bits
+    IDX *tab;         // hash table: element index + 1, 0 = empty
+    IDX *opos;        // output position of kept owners
 };
+enum { EF_OWNER = 1, EF_OCC = 2, EF_KEEP = 4, EF_REF = 16, EF_D = 32 };
 
 struct K3Shared {
     int wsum[K3_THREADS / 32];
@@ -337,28 +342,15 @@ struct K3Smem {
     K3Shared sh;
     ulonglong2 key[EMAX];
     double val[EMAX];
-    unsigned short perm[EMAX];
-    unsigned short lead[EMAX];
-    unsigned short grp[EMAX];
-    unsigned short goff[NGROUP + 1];
-    int cur[NGROUP];
-    unsigned short nlead[NGROUP];
+    u64 acc_lo[EMAX];
+    u64 acc_hi[EMAX];
+    int nacc[EMAX];
+    int eflag[EMAX];
+    unsigned short tab[1 << TABBITS];
+    unsigned short opos[EMAX];
 };
 
 __device__ __forceinline__ bool key_less(u64 a1, u64 b1, u64 a2, u64 b2) { return a1 < a2 || (a1 == a2 && b1 < b2); }
-
-// D index of a determinant known to be in D (binary search over sorted keys)
-__device__ int d_index(const DevInst &I, u64 a, u64 b)
-{
-    int lo = 0, hi = I.nd;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        ulonglong2 k = __ldg(I.dkey + mid);
-        if (k.x == a && k.y == b) return mid;
-        if (key_less(k.x, k.y, a, b)) lo = mid + 1; else hi = mid;
-    }
-    return -1;
-}
 
 __device__ __forceinline__ int block_excl_scan(int v, int *wsum, int *total)
 {
@@ -388,143 +380,144 @@ __device__ __forceinline__ int block_excl_scan(int v, int *wsum, int *total)
 // Death, annihilation and the reductions of one bucket b (steps (b) and (c)
 // of Eq. (4)).  All threads of the block call this together.
 template <typename IDX>
-__device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int gbits, int b, int par, long long it,
+__device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tabbits, int b, int par, long long it,
                             double shift, int m, int si, int sn)
 {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const IDX KEEP = (IDX)1 << (8 * sizeof(IDX) - 1);
-    const int G = 1 << gbits, GPT = G / K3_THREADS;
-    const int E = m + si + sn, cap_s = I.cap_s;
+    const int E = m + si + sn, cap_s = I.cap_s, TAB = 1 << tabbits;
+    const u64 tmask = (u64)(TAB - 1);
     const size_t base = (size_t)b * CAP_M, sbase = (size_t)b * cap_s;
-    const int shift_g = 64 - I.bb - gbits;
     const ulonglong2 *okey = I.key[par];
     const double *oc = I.c[par], *ohd = I.hd[par];
     const uint8_t *ofl = I.fl[par];
 
-    // 1. stage the bucket: walkers [0, m), initiator spawns [m, m+si),
-    //    other spawns [m+si, E); histogram of the sub-hash groups
-    for (int g = t; g < G; g += K3_THREADS) W.cur[g] = 0;
+    // 1. stage: walkers [0, m), initiator spawns [m, m+si), other spawns [m+si, E)
+    for (int q = t; q < TAB; q += K3_THREADS) W.tab[q] = 0;
     if (t == 0) S.n_new = 0;
-    __syncthreads();
     for (int e = t; e < E; e += K3_THREADS) {
         ulonglong2 k;
         double v;
-        if (e < m) { k = okey[base + e]; v = oc[base + e]; }
-        else if (e < m + si) { k = I.skey[sbase + (e - m)]; v = I.sw[sbase + (e - m)]; }
-        else { int slot = cap_s - 1 - (e - m - si); k = I.skey[sbase + slot]; v = I.sw[sbase + slot]; }
+        int f = 0;
+        if (e < m) {
+            k = okey[base + e];
+            v = oc[base + e];
+            uint8_t fl = ofl[base + e];
+            f = EF_OWNER | (is_zero(v) ? 0 : EF_OCC) | ((fl & DFLAG_REF) ? EF_REF : 0) | ((fl & DFLAG_D) ? EF_D : 0);
+        } else if (e < m + si) {
+            k = I.skey[sbase + (e - m)];
+            v = I.sw[sbase + (e - m)];
+        } else {
+            int slot = cap_s - 1 - (e - m - si);
+            k = I.skey[sbase + slot];
+            v = I.sw[sbase + slot];
+        }
         W.key[e] = k;
         W.val[e] = v;
-        int g = (int)((det_hash(k.x, k.y) >> shift_g) & (u64)(G - 1));
-        W.grp[e] = (IDX)g;
-        atomicAdd(&W.cur[g], 1);
+        W.acc_lo[e] = 0;
+        W.acc_hi[e] = 0;
+        W.nacc[e] = 0;
+        W.eflag[e] = f;
     }
     __syncthreads();
-    // 2. group offsets (each thread owns GPT consecutive groups)
-    {
-        int sum = 0;
-        for (int q = 0; q < GPT; q++) sum += W.cur[t * GPT + q];
-        int tot;
-        int ex = block_excl_scan(sum, S.wsum, &tot);
-        for (int q = 0; q < GPT; q++) {
-            int c = W.cur[t * GPT + q];
-            W.goff[t * GPT + q] = (IDX)ex;
-            W.cur[t * GPT + q] = ex;
-            ex += c;
+    // 2. walkers: insert into the table (keys are distinct); death (b) and Eq. (3)
+    for (int e = t; e < m; e += K3_THREADS) {
+        ulonglong2 k = W.key[e];
+        u64 s = det_hash(k.x, k.y) & tmask;
+        while (atomicCAS(&W.tab[s], (IDX)0, (IDX)(e + 1)) != (IDX)0) s = (s + 1) & tmask;
+        const int f = W.eflag[e];
+        double cp;
+        if (f & EF_D) {
+            cp = I.dc_new[d_index_of(I, k.x, k.y)];
+        } else {
+            // C (1 - tau (H_ii - E_ref - S)), then rounding with the death draw
+            double c0 = W.val[e];
+            double fct = 1.0 - I.tau * (ohd[base + e] - shift);
+            cp = c0 * fct;
+            if (!is_zero(cp) && abs_lt(cp, I.cmin)) {
+                u64 w[4];
+                philox(k.x, k.y, (u64)it, (u64)PURPOSE_DEATH, I.seed, 0ULL, w);
+                cp = round_stoch(cp, I.cmin, I.cmin_log2, I.cmin_pow2, w[0]);
+            }
         }
-        if (t == 0) W.goff[G] = (IDX)tot;
+        W.val[e] = cp;
     }
     __syncthreads();
-    for (int e = t; e < E; e += K3_THREADS) {
-        int pos = atomicAdd(&W.cur[W.grp[e]], 1);
-        W.perm[pos] = (IDX)e;
-    }
-    __syncthreads();
-
-    // 3. pass 1: within each group, visit distinct determinants in key order
-    int nk = 0;
+    // 3. spawns: find the target or become the owner of a new determinant;
+    //    initiator rule (Sec. I): a non-initiator spawn survives only onto a
+    //    determinant occupied at the start of the iteration
     long long rejected = 0;
     i128 ann = 0;
-    for (int q = 0; q < GPT; q++) {
-        const int g = t * GPT + q, lo = W.goff[g], hi = W.goff[g + 1];
-        int nl = 0;
-        u64 la = 0, lb = 0;
-        bool first = true;
+    for (int e = m + t; e < E; e += K3_THREADS) {
+        const ulonglong2 k = W.key[e];
+        u64 s = det_hash(k.x, k.y) & tmask;
+        int target = -1;
         while (true) {
-            bool found = false;
-            u64 ba = 0, bb2 = 0;
-            for (int r = lo; r < hi; r++) {
-                ulonglong2 k = W.key[W.perm[r]];
-                bool gt = first || key_less(la, lb, k.x, k.y);
-                if (gt && (!found || key_less(k.x, k.y, ba, bb2))) { found = true; ba = k.x; bb2 = k.y; }
+            IDX v = ((volatile IDX *)W.tab)[s];
+            if (v == 0) {
+                IDX old = atomicCAS(&W.tab[s], (IDX)0, (IDX)(e + 1));
+                if (old == 0) { target = e; break; }
+                v = old;
             }
-            if (!found) break;
-            first = false;
-            la = ba; lb = bb2;
-            int me = -1, leader = -1, ni = 0, nn = 0;
-            i128 Xi = 0, Xn = 0;
-            u128 fi = 0, fn = 0;
-            for (int r = lo; r < hi; r++) {
-                int e = W.perm[r];
-                ulonglong2 k = W.key[e];
-                if (k.x != ba || k.y != bb2) continue;
-                if (leader < 0) leader = e;
-                if (e < m) { me = e; continue; }
-                double w = W.val[e];
-                if (e < m + si) { Xi += to_fixed(w, I.Fw); fi += fx32(w); ni++; }
-                else { Xn += to_fixed(w, I.Fw); fn += fx32(w); nn++; }
-            }
-            if (me >= 0) leader = me;
-            const bool present = me >= 0;
-            uint8_t fl = present ? ofl[base + me] : 0;
-            double c0 = present ? W.val[me] : 0.0, cp = 0.0;
-            if (present) {
-                if (fl & DFLAG_D) {
-                    cp = I.dc_new[d_index(I, ba, bb2)];
-                } else {
-                    // (b) death: C (1 - tau (H_ii - E_ref - S)), then Eq. (3)
-                    double f = 1.0 - I.tau * (ohd[base + me] - shift);
-                    cp = c0 * f;
-                    if (cp != 0.0 && fabs(cp) < I.cmin) {
-                        u64 w[4];
-                        philox(ba, bb2, (u64)it, (u64)PURPOSE_DEATH, I.seed, 0ULL, w);
-                        cp = round_stoch(cp, I.cmin, u53(w[0]));
-                    }
-                }
-            }
-            // (c) annihilation with the initiator rule: spawns from
-            // non-initiators survive only onto determinants occupied at the
-            // start of the iteration
-            const bool occ = present && c0 != 0.0;
-            i128 X = Xi;
-            u128 fs = fi;
-            int nacc = ni;
-            if (occ) { X += Xn; fs += fn; nacc += nn; } else rejected += nn;
-            double acc = cp;
-            if (nacc > 0) {
-                double swsum = fixed_to_double(X, I.Fw);
-                acc = present ? cp + swsum : swsum;
-                i128 in = (present ? (i128)fx32(cp) : (i128)0) + (i128)fs;
-                ann += in - (i128)fx32(acc);
-                if (!(fl & DFLAG_D) && acc != 0.0 && fabs(acc) < I.cmin) {
-                    u64 w[4];
-                    philox(ba, bb2, (u64)it, (u64)PURPOSE_ANNIH, I.seed, 0ULL, w);
-                    acc = round_stoch(acc, I.cmin, u53(w[0]));
-                }
-            }
-            const bool keep = acc != 0.0 || (fl & (DFLAG_REF | DFLAG_D));
-            W.val[leader] = acc;
-            W.lead[lo + nl] = (IDX)leader | (keep ? KEEP : (IDX)0);
-            nl++;
-            nk += keep ? 1 : 0;
+            const int tt = (int)v - 1;
+            const ulonglong2 kk = W.key[tt];
+            if (kk.x == k.x && kk.y == k.y) { target = tt; break; }
+            s = (s + 1) & tmask;
         }
-        W.nlead[g] = (IDX)nl;
+        if (target == e) atomicOr(&W.eflag[e], EF_OWNER);
+        const bool init = e < m + si;
+        const bool accepted = init || (target < m && (W.eflag[target] & EF_OCC));
+        if (!accepted) { rejected++; continue; }
+        const double w = W.val[e];
+        const i128 x = to_fixed(w, I.Fw);
+        const u64 lo = (u64)x, hi = (u64)((u128)x >> 64);
+        const u64 old = atomicAdd((unsigned long long *)&W.acc_lo[target], (unsigned long long)lo);
+        atomicAdd((unsigned long long *)&W.acc_hi[target], (unsigned long long)(hi + (old + lo < old ? 1ULL : 0ULL)));
+        atomicAdd(&W.nacc[target], 1);
+        ann += (i128)fx32(w);
     }
+    __syncthreads();
+    // 4. owners: sum = C' + exact spawn sum, then Eq. (3) with the annihilation draw
+    int nk = 0;
+    for (int e = t; e < E; e += K3_THREADS) {
+        const int f = W.eflag[e];
+        if (!(f & EF_OWNER)) continue;
+        const bool present = e < m;
+        const double cp = present ? W.val[e] : 0.0;
+        double accv = cp;
+        if (W.nacc[e] > 0) {
+            const i128 X = (i128)(((u128)W.acc_hi[e] << 64) | (u128)W.acc_lo[e]);
+            const double sw = fixed_to_double(X, I.Fw);
+            accv = present ? cp + sw : sw;
+            ann += (present ? (i128)fx32(cp) : (i128)0) - (i128)fx32(accv);
+            if (!(f & EF_D) && !is_zero(accv) && abs_lt(accv, I.cmin)) {
+                const ulonglong2 k = W.key[e];
+                u64 w[4];
+                philox(k.x, k.y, (u64)it, (u64)PURPOSE_ANNIH, I.seed, 0ULL, w);
+                accv = round_stoch(accv, I.cmin, I.cmin_log2, I.cmin_pow2, w[0]);
+            }
+        }
+        W.val[e] = accv;
+        if (!is_zero(accv) || (f & (EF_REF | EF_D))) {
+            W.eflag[e] = f | EF_KEEP;
+            nk++;
+        }
+    }
+    // 5. output positions in element order
     int total;
-    int o = block_excl_scan(nk, S.wsum, &total);
+    const int per = (E + K3_THREADS - 1) / K3_THREADS;
+    const int e0 = t * per, e1 = min(E, e0 + per);
+    int cnt = 0;
+    __syncthreads();
+    for (int e = e0; e < e1; e++) cnt += (W.eflag[e] & EF_KEEP) ? 1 : 0;
+    int o = block_excl_scan(cnt, S.wsum, &total);
     const bool overflow = total > CAP_M;
     if (overflow && t == 0) { atomicOr(&I.st->err, ERRB_MAIN_CAP); atomicMax(&I.st->need_main, total); }
+    for (int e = e0; e < e1; e++)
+        if (W.eflag[e] & EF_KEEP) W.opos[e] = (IDX)(o++);
+    (void)nk;
+    __syncthreads();
 
-    // 4. pass 2: write the new bucket in (group, key) order; reductions
+    // 6. write the new bucket; reductions
     const int np = par ^ 1;
     ulonglong2 *nkey = I.key[np];
     double *nc = I.c[np], *nhd = I.hd[np];
@@ -533,50 +526,43 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int gbi
     double enm = 0.0;
     bool bad = false;
     if (!overflow) {
-        for (int q = 0; q < GPT; q++) {
-            const int g = t * GPT + q, lo = W.goff[g], nl = W.nlead[g];
-            for (int j = 0; j < nl; j++) {
-                IDX v = W.lead[lo + j];
-                if (!(v & KEEP)) continue;
-                int L = (int)(v & (KEEP - 1));
-                ulonglong2 k = W.key[L];
-                double c = W.val[L];
-                size_t dst = base + o;
-                nkey[dst] = k;
-                nc[dst] = c;
-                uint8_t f = L < m ? ofl[base + L] : 0;
-                nfl[dst] = f;
-                if (L < m) nhd[dst] = ohd[base + L];
-                else {
-                    int qn = atomicAdd(&S.n_new, 1);
-                    W.perm[qn] = (IDX)L;
-                    W.grp[qn] = (IDX)o;
-                }
-                if (!(fabs(c) < 0x1p31)) bad = true;
-                else nw += fx32(c);
-                if (f & DFLAG_REF) I.st->e_den = c;
-                else {
-                    int lev = __popcll(k.x ^ I.ref_a) + __popcll(k.y ^ I.ref_b);
-                    if (lev <= 4 && c != 0.0) enm = enm + hoff_generic(I, k.x, k.y, I.ref_a, I.ref_b) * c;
-                }
-                if (f & DFLAG_D) I.dc_cur[d_index(I, k.x, k.y)] = c;
-                o++;
+        for (int e = t; e < E; e += K3_THREADS) {
+            const int f = W.eflag[e];
+            if (!(f & EF_KEEP)) continue;
+            const ulonglong2 k = W.key[e];
+            const double c = W.val[e];
+            const size_t dst = base + W.opos[e];
+            nkey[dst] = k;
+            nc[dst] = c;
+            nfl[dst] = (uint8_t)(((f & EF_REF) ? DFLAG_REF : 0) | ((f & EF_D) ? DFLAG_D : 0));
+            if (e < m) nhd[dst] = ohd[base + e];
+            else {
+                const int qn = atomicAdd(&S.n_new, 1);
+                W.nacc[qn] = e;  // accumulators are free now: reuse as the list of new determinants
             }
+            if (!abs_lt(c, 0x1p31)) bad = true;
+            else nw += fx32(c);
+            if (f & EF_REF) I.st->e_den = c;
+            else {
+                const int lev = __popcll(k.x ^ I.ref_a) + __popcll(k.y ^ I.ref_b);
+                if (lev <= 4 && !is_zero(c)) enm = enm + hoff_generic(I, k.x, k.y, I.ref_a, I.ref_b) * c;
+            }
+            if (f & EF_D) I.dc_cur[d_index_of(I, k.x, k.y)] = c;
         }
     }
     if (bad) atomicOr(&I.st->err, ERRB_NUMERIC);
     __syncthreads();
-    // 5. H_jj - E_ref for new determinants, one warp each
+    // 7. H_jj - E_ref for new determinants, one warp each
     if (!overflow) {
         const int nnew = S.n_new;
         for (int q = warp; q < nnew; q += K3_THREADS / 32) {
-            int L = (int)W.perm[q];
-            ulonglong2 k = W.key[L];
-            double hdv = diag_exact_warp(I, k.x, k.y);
-            if (lane == 0) nhd[base + (int)W.grp[q]] = hdv;
+            const int e = W.nacc[q];
+            const ulonglong2 k = W.key[e];
+            const double hdv = diag_exact_warp(I, k.x, k.y);
+            if (lane == 0) nhd[base + W.opos[e]] = hdv;
         }
     }
-    // 6. bucket reductions (fixed order: lanes by xor tree, warps in index order)
+    // 8. bucket reductions (fixed order: lanes by xor tree, warps in index order)
     for (int mm = 16; mm >= 1; mm >>= 1) {
         enm = enm + __shfl_xor_sync(0xffffffffu, enm, mm);
         rejected += __shfl_xor_sync(0xffffffffu, rejected, mm);
@@ -625,7 +611,7 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k_annihilate(const DevInst *__r
     extern __shared__ __align__(16) unsigned char smem_raw[];
     K3Smem &Sm = *reinterpret_cast<K3Smem *>(smem_raw);
     K3Shared &S = Sm.sh;
-    Stage<unsigned short> W{Sm.key, Sm.val, Sm.perm, Sm.lead, Sm.grp, Sm.goff, Sm.cur, Sm.nlead};
+    Stage<unsigned short> W{Sm.key, Sm.val, Sm.acc_lo, Sm.acc_hi, Sm.nacc, Sm.eflag, Sm.tab, Sm.opos};
     const int t = threadIdx.x;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
         const int ii = find_inst(unit_start, n_inst, u);
@@ -652,7 +638,7 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k_annihilate(const DevInst *__r
             if (t == 0) I.big_list[atomicAdd(&I.st->big_n, 1)] = b;
             continue;
         }
-        anni_bucket<unsigned short>(I, S, W, GBITS, b, par, it, shift, m, si, sn);
+        anni_bucket<unsigned short>(I, S, W, TABBITS, b, par, it, shift, m, si, sn);
     }
 }
 
@@ -680,21 +666,21 @@ __global__ void __launch_bounds__(K3_THREADS) k_annihilate_big(const DevInst *__
             continue;
         }
         // this block's scratch slice
-        const int Ecap = CAP_M + I.cap_s, gbits = I.big_gbits, G = 1 << gbits;
+        const int Ecap = CAP_M + I.cap_s, tabbits = I.big_tabbits;
         unsigned char *p = I.big_scratch + (size_t)blockIdx.x * I.big_stride;
         Stage<unsigned> W;
         W.key = (ulonglong2 *)p; p += (size_t)Ecap * sizeof(ulonglong2);
         W.val = (double *)p; p += (size_t)Ecap * sizeof(double);
-        W.perm = (unsigned *)p; p += (size_t)Ecap * 4;
-        W.lead = (unsigned *)p; p += (size_t)Ecap * 4;
-        W.grp = (unsigned *)p; p += (size_t)Ecap * 4;
-        W.goff = (unsigned *)p; p += (size_t)(G + 1) * 4;
-        W.cur = (int *)p; p += (size_t)G * 4;
-        W.nlead = (unsigned *)p;
+        W.acc_lo = (u64 *)p; p += (size_t)Ecap * 8;
+        W.acc_hi = (u64 *)p; p += (size_t)Ecap * 8;
+        W.nacc = (int *)p; p += (size_t)Ecap * 4;
+        W.eflag = (int *)p; p += (size_t)Ecap * 4;
+        W.opos = (unsigned *)p; p += (size_t)Ecap * 4;
+        W.tab = (unsigned *)p;
         for (int q = blockIdx.x; q < nbig; q += gridDim.x) {
             const int b = I.big_list[q];
             const int m = I.cnt[par][b], si = I.scnt_i[b], sn = I.scnt_n[b];
-            anni_bucket<unsigned>(I, S, W, gbits, b, par, it, shift, m, si, sn);
+            anni_bucket<unsigned>(I, S, W, tabbits, b, par, it, shift, m, si, sn);
         }
     }
 }
@@ -778,6 +764,7 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
     st->big_n = 0;
     if (I.semi_size > 0 && !st->semi_built && st->vary && it + 1 == st->shift_start + I.semi_start)
         st->err |= ERRB_PAUSE_SEMI;
+    if (it + 1 >= st->stop_iter) st->err |= ERRB_STOP;
 }
 
 // ------------------------------------------------------------------ growth and import
@@ -820,6 +807,73 @@ __global__ void k_diag(const DevInst *__restrict__ I, int par, int nb)
             }
         }
     }
+}
+
+// ------------------------------------------------------------------ time-step bound
+// sum_j |<D_j|H|D_ref>| over every single and double excitation of the
+// reference; fixed grid, fixed per-thread order and fixed reduction tree, so
+// the result is deterministic.
+constexpr int REFSUM_BLOCKS = 64;
+__global__ void __launch_bounds__(256) k_ref_abs_sum(const DevInst *__restrict__ Ip, double *partial)
+{
+    const DevInst &I = *Ip;
+    const u64 ra = I.ref_a, rb = I.ref_b, va = ~ra & I.normask, vb = ~rb & I.normask;
+    const long long na = I.na, nb = I.nb, ma = I.ma, mb = I.mb;
+    const long long s1 = na * ma, s2 = nb * mb, s3 = na * nb * ma * mb, s4 = na * na * ma * ma, s5 = nb * nb * mb * mb;
+    const long long total = s1 + s2 + s3 + s4 + s5;
+    double acc = 0.0;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        long long q = idx;
+        u64 ta = ra, tb = rb;
+        if (q < s1) {
+            ta ^= (1ULL << nth_set(ra, (int)(q / ma))) | (1ULL << nth_set(va, (int)(q % ma)));
+        } else if ((q -= s1) < s2) {
+            tb ^= (1ULL << nth_set(rb, (int)(q / mb))) | (1ULL << nth_set(vb, (int)(q % mb)));
+        } else if ((q -= s2) < s3) {
+            const int b = (int)(q % mb); q /= mb;
+            const int a = (int)(q % ma); q /= ma;
+            const int j = (int)(q % nb), i = (int)(q / nb);
+            ta ^= (1ULL << nth_set(ra, i)) | (1ULL << nth_set(va, a));
+            tb ^= (1ULL << nth_set(rb, j)) | (1ULL << nth_set(vb, b));
+        } else if ((q -= s3) < s4) {
+            const int b = (int)(q % ma); q /= ma;
+            const int a = (int)(q % ma); q /= ma;
+            const int j = (int)(q % na), i = (int)(q / na);
+            if (!(i < j && a < b)) continue;
+            ta ^= (1ULL << nth_set(ra, i)) | (1ULL << nth_set(ra, j)) | (1ULL << nth_set(va, a)) | (1ULL << nth_set(va, b));
+        } else {
+            q -= s4;
+            const int b = (int)(q % mb); q /= mb;
+            const int a = (int)(q % mb); q /= mb;
+            const int j = (int)(q % nb), i = (int)(q / nb);
+            if (!(i < j && a < b)) continue;
+            tb ^= (1ULL << nth_set(rb, i)) | (1ULL << nth_set(rb, j)) | (1ULL << nth_set(vb, a)) | (1ULL << nth_set(vb, b));
+        }
+        acc = acc + fabs(hoff_generic(I, ra, rb, ta, tb));
+    }
+    __shared__ double sm[8];
+    for (int m = 16; m >= 1; m >>= 1) acc = acc + __shfl_xor_sync(0xffffffffu, acc, m);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < 8; k++) s = s + sm[k];
+        partial[blockIdx.x] = s;
+    }
+}
+
+cudaError_t ref_abs_sum(const DevInst *dinst, double *dpartial, double *out, cudaStream_t s)
+{
+    k_ref_abs_sum<<<REFSUM_BLOCKS, 256, 0, s>>>(dinst, dpartial);
+    double hp[REFSUM_BLOCKS];
+    cudaError_t e = cudaMemcpyAsync(hp, dpartial, sizeof(hp), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    double acc = 0.0;
+    for (int k = 0; k < REFSUM_BLOCKS; k++) acc = acc + hp[k];
+    *out = acc;
+    return cudaSuccess;
 }
 
 // ------------------------------------------------------------------ launchers

@@ -55,7 +55,7 @@ def test_create_without_gpu_fails_cleanly():
 def test_invalid_arguments_rejected_before_any_device_work():
     import paper_2006_14956_gb300 as fq
     import workloads
-    for bad in [dict(tau=-1.0), dict(c_min=0.0), dict(p_single=1.5), dict(shift_interval=0)]:
+    for bad in [dict(tau=float('nan')), dict(c_min=0.0), dict(p_single=1.5), dict(shift_interval=0)]:
         try:
             fq.fciqmc_create(workloads.hubbard_1d(4), bad, use_torch=False)
         except fq.FciqmcError as e:

@@ -216,3 +216,40 @@ def test_full_size_sampled_parity_abinitio_24():
             assert bits(gs[k][-1:])[0] == bits(os_[ok][-1:])[0], k
         else:
             assert gs[k][-1] == os_[ok][-1], k
+
+
+@pytest.mark.parametrize("name,sysd,params,n", [
+    ("abinitio_8_D60", workloads.small_abinitio(8, 3, 3, seed=5),
+     dict(tau=0.005, target_walkers=3000, initiator_threshold=3.0, seed=11, semistoch_size=60, semistoch_start=5), 200),
+    ("hubbard_4x4_D200", workloads.hubbard_2d(4, 4, 4.0),
+     dict(tau=0.005, target_walkers=5000, initiator_threshold=3.0, seed=7, semistoch_size=200, semistoch_start=3), 200),
+    ("abinitio_7_D_ties", workloads.small_abinitio(7, 2, 2, seed=13),
+     dict(tau=0.004, target_walkers=800, initiator_threshold=0.0, seed=8, semistoch_size=150, semistoch_start=1), 150),
+])
+def test_semistochastic_bit_exact(name, sysd, params, n):
+    """Deterministic projection inside D (Sec. III): selection of the N_D most
+    populated determinants (ties by key), H^D in CSR, exact update, D -> D
+    spawns removed.  Keys, amplitudes, D flags and counters match the oracle."""
+    fq, g, o = run_pair(sysd, params, n, chunks=2)
+    gs, os_ = fq.fciqmc_export_state(g), o.export()
+    assert_states_equal(gs, os_)
+    assert int(np.sum((gs["flags"] & 2) > 0)) == o.semistoch_info()[0] > 0
+    assert_stats_equal(fq.fciqmc_iter_stats_get(g), o.stats())
+
+
+def test_semistochastic_whole_space_converges_to_exact_energy():
+    """D = the whole space: the GPU iteration is the power method with
+    1 - dt (H - S) and E_proj reaches the exact E_0 (Sec. III)."""
+    fq = _fq()
+    sysd = workloads.hubbard_1d(6, 1.0, 4.0)
+    s = oracle.system_from_workload(sysd)
+    e0, _, dets = s.exact_ground_state()
+    g = fq.fciqmc_create(sysd, dict(tau=0.02, target_walkers=2000, initial_walkers=100.0, seed=3,
+                                    semistoch_size=len(dets), semistoch_start=200, shift_damping=0.5,
+                                    shift_interval=5, initial_shift=e0 + 0.2))
+    fq.fciqmc_step(g, 2500)
+    st = fq.fciqmc_iter_stats_get(g)
+    st_state = fq.fciqmc_export_state(g)
+    assert st_state["c"].size == len(dets) and np.all((st_state["flags"] & 2) > 0)
+    e = st["e_num"][-1] / st["e_den"][-1]
+    assert abs(e - e0) < 1e-8, (e, e0)

@@ -1,0 +1,68 @@
+"""Serving: requests admitted by device memory and stepped together give the
+same result as the same request run alone."""
+import numpy as np
+import pytest
+
+import workloads
+from tests.test_gpu_parity import _fq
+
+pytestmark = pytest.mark.gpu
+
+
+def _mix():
+    h, eri = workloads.synthetic_abinitio(8, 24, 77)
+    ab = dict(kind="abinitio", norb=8, n_alpha=3, n_beta=3, h1=h, eri=eri, ecore=0.0)
+    return [
+        (workloads.hubbard_1d(8, 1.0, 4.0), dict(tau=0.01, target_walkers=2000, seed=11, shift_damping=0.5,
+                                                 shift_interval=5)),
+        (workloads.hubbard_2d(3, 4, 2.0), dict(tau=0.0, target_walkers=5000, seed=12, initiator_threshold=3.0,
+                                               shift_damping=0.5, shift_interval=5)),
+        (ab, dict(tau=0.0, target_walkers=3000, seed=13, initiator_threshold=3.0, shift_damping=0.5,
+                  shift_interval=5)),
+        (workloads.hubbard_1d(10, 1.0, 2.0), dict(tau=0.0, target_walkers=4000, seed=14, shift_damping=0.5,
+                                                  shift_interval=5)),
+    ]
+
+
+def test_requests_in_the_mix_equal_alone():
+    fq = _fq()
+    mix = _mix()
+    srv = fq.fciqmc_server_create(8 << 30, max_active=3)
+    ids = [fq.fciqmc_server_submit(srv, s, p, target_sigma=1e-12, max_iters=300) for s, p in mix]
+    while fq.fciqmc_server_tick(srv, 50) > 0:
+        pass
+    for (s, p), rid in zip(mix, ids):
+        st = fq.fciqmc_server_poll(srv, rid)
+        assert st["state_name"] == "max_iters", st
+        assert st["iterations"] == 300
+        alone = fq.fciqmc_create(s, p)
+        fq.fciqmc_step(alone, 300)
+        en = fq.fciqmc_energy(alone)
+        assert st["tau"] == fq.fciqmc_tau(alone)
+        for k_srv, k_alone in [("energy", "e_proj_mean"), ("sigma", "e_proj_sigma"), ("shift", "shift")]:
+            a, b = st[k_srv], en[k_alone]
+            assert (np.isnan(a) and np.isnan(b)) or a == b, (k_srv, a, b)
+        assert st["attempts"] == en["attempts_total"]
+        assert st["t_done"] >= st["t_start"] >= st["t_submit"]
+
+
+def test_admission_respects_the_memory_budget():
+    fq = _fq()
+    mix = _mix()
+    # a budget that fits roughly one request at a time
+    srv = fq.fciqmc_server_create(1, max_active=8)
+    ids = [fq.fciqmc_server_submit(srv, s, p, target_sigma=1e-12, max_iters=50) for s, p in mix[:3]]
+    fq.fciqmc_server_tick(srv, 50)
+    states = [fq.fciqmc_server_poll(srv, i)["state_name"] for i in ids]
+    assert states.count("queued") == 2
+    while fq.fciqmc_server_tick(srv, 50) > 0:
+        pass
+    assert all(fq.fciqmc_server_poll(srv, i)["state_name"] == "max_iters" for i in ids)
+
+
+def test_auto_time_step_bounds_spawning():
+    fq = _fq()
+    s, p = _mix()[2]
+    h = fq.fciqmc_create(s, p)
+    sm = fq.fciqmc_ref_offdiag_sum(h)
+    assert sm > 0 and fq.fciqmc_tau(h) == 0.5 / sm
