@@ -236,6 +236,34 @@ int fciqmc_step_batch(fciqmc_handle **hs, int32_t k, int64_t n_iter);
 int fciqmc_ref_offdiag_sum(fciqmc_handle *h, double *out);
 double fciqmc_tau(fciqmc_handle *h);
 
+/* The same sum as fciqmc_ref_offdiag_sum, for callers that cannot allocate
+ * device memory: frameworks whose memory pool owns every device byte, jobs
+ * held to a fixed memory budget, or loops that must not enter the driver's
+ * allocator (cudaMalloc can synchronise the whole device).  No counterpart in
+ * the paper: this is an interface
+ * convenience of this library.
+ *   norb, n_alpha, n_beta: as in fciqmc_system (norb <= 64);
+ *   d_h1, d_eri: DEVICE arrays owned by the caller, laid out as h1 / eri of
+ *     fciqmc_system (norb*norb, and the packed 8-fold ERI);
+ *   ref_alpha, ref_beta: the reference determinant;
+ *   d_out: DEVICE pointer to one double, receives the sum;
+ *   stream: cudaStream_t (NULL = legacy default stream).
+ * Calls no cudaMalloc/cudaFree and no allocating library routine.  Scratch
+ * lives in a fixed 1 KB array in the library's device image (64 block
+ * partial sums and the integral exponent range); every GPU that loads the
+ * library keeps it until the process exits.  The first call on a device looks
+ * up that array's device address (cudaGetSymbolAddress) with the device
+ * current; make that first call before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU race and must not be issued
+ * concurrently.  Synchronises the stream before returning.  Errors:
+ * FCIQMC_ERR_INVALID_ARG for bad sizes/pointers, a reference with the wrong
+ * electron counts or a non-finite integral; FCIQMC_ERR_UNSUPPORTED when the
+ * integrals' dynamic range exceeds the 128-bit exact accumulator;
+ * FCIQMC_ERR_CUDA on a CUDA failure. */
+int fciqmc_ref_offdiag_sum_noalloc(int32_t norb, int32_t n_alpha, int32_t n_beta, const double *d_h1,
+                                   const double *d_eri, uint64_t ref_alpha, uint64_t ref_beta, double *d_out,
+                                   void *stream);
+
 /* ---- serving: runs admitted by device memory and stepped together ----
  * A request is a system + parameters + a target error; the server admits
  * queued requests (first come, first served) while the sum of the device

@@ -116,6 +116,8 @@ _SIGS = {
     "fciqmc_layout": (C.c_int, [_H, C.POINTER(C.c_int64)]),
     "fciqmc_ref_offdiag_sum": (C.c_int, [_H, _dp]),
     "fciqmc_tau": (C.c_double, [_H]),
+    "fciqmc_ref_offdiag_sum_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                                 C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p]),
     "fciqmc_server_create": (C.c_int, [C.c_int64, C.c_int32, C.c_void_p, C.POINTER(_H)]),
     "fciqmc_server_submit": (C.c_int, [_H, C.POINTER(fciqmc_system), C.POINTER(fciqmc_params), C.c_double,
                                        C.c_int64, C.POINTER(C.c_int64)]),
@@ -348,6 +350,12 @@ def fciqmc_ref_offdiag_sum(handle):
     out = C.c_double()
     _check(_lib.fciqmc_ref_offdiag_sum(handle.h, C.byref(out)), handle.h)
     return out.value
+
+
+def fciqmc_ref_offdiag_sum_noalloc(norb, n_alpha, n_beta, d_h1, d_eri, ref_alpha, ref_beta, d_out, stream=None):
+    """Device pointers (ints) in, device pointer out; see include/fciqmc.h."""
+    _check(_lib.fciqmc_ref_offdiag_sum_noalloc(int(norb), int(n_alpha), int(n_beta), d_h1, d_eri, int(ref_alpha),
+                                               int(ref_beta), d_out, stream))
 
 
 def fciqmc_tau(handle):
