@@ -133,12 +133,105 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": "spawn attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_batch(args):
+    """64 uneven 2D Hubbard runs (3x4, 4x4, 4x5 at half filling, U/t in {2,4,8},
+    walker targets 1e4..1e6, tau 0.005, initiator threshold 3): every iteration
+    of all runs in one batched launch, against the same runs stepped one at a
+    time.  Attempts/s over the timed iterations of both."""
+    import torch
+    import paper_2006_14956_gb300 as fq
+    runs = workloads.batched_hubbard_instances(64)
+    runs = [(s, dict(p, shift_damping=0.5, shift_interval=5)) for s, p in runs]
+    hs = [fq.fciqmc_create(s, p) for s, p in runs]
+    fq.fciqmc_step_batch(hs, 300)                         # growth, untimed
+    fq.fciqmc_step_batch(hs, args.warmup)
+    n0 = [fq.fciqmc_iter_stats_count(h) for h in hs]
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    fq.fciqmc_step_batch(hs, args.steps)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t
+    att_b = sum(float(np.sum(fq.fciqmc_iter_stats_get(h)["attempts"][n0[i]:])) for i, h in enumerate(hs))
+    # the same states, one run at a time
+    seq = []
+    for (s, p), h in zip(runs, hs):
+        st, sh = fq.fciqmc_export_state(h), fq.fciqmc_export_shift(h)
+        g = fq.fciqmc_create(s, p)
+        fq.fciqmc_import_state(g, st["alpha"], st["beta"], st["c"], sh["iteration"], sh["S"], sh["vary"],
+                               sh["shift_start"], sh["cnt"], sh["nw_last"])
+        seq.append(g)
+    for g in seq:
+        fq.fciqmc_step(g, args.warmup)
+    m0 = [fq.fciqmc_iter_stats_count(g) for g in seq]
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for g in seq:
+        fq.fciqmc_step(g, args.steps)
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t
+    att_s = sum(float(np.sum(fq.fciqmc_iter_stats_get(g)["attempts"][m0[i]:])) for i, g in enumerate(seq))
+    walkers = [float(fq.fciqmc_iter_stats_get(h)["nw"][-1]) for h in hs]
+    return {"metric": METRIC, "value": att_b / tb, "unit": "spawn attempts/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tb / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "64 batched 2D Hubbard runs (3x4/4x4/4x5, U/t 2/4/8, targets 1e4..1e6)",
+                       "tau": 0.005, "initiator_threshold": 3, "walkers_total": sum(walkers),
+                       "walkers_min": min(walkers), "walkers_max": max(walkers)},
+            "sequential": {"value": att_s / ts, "ms_per_step": ts / args.steps * 1e3},
+            "batched_over_sequential": (att_b / tb) / (att_s / ts)}
+
+
+def run_serving(args):
+    """Poisson arrivals (20/s) of mixed FCIQMC requests (1D/2D Hubbard and
+    synthetic ab initio systems, walker targets 1e4..1e7), each run until the
+    blocking error of E_proj is below 1 mEh (or an iteration cap).  Reports
+    p50/p99 time from arrival to answer and throughput."""
+    import paper_2006_14956_gb300 as fq
+    reqs = workloads.serving_requests(args.requests, rate=20.0, seed=5)
+    srv = fq.fciqmc_server_create(200 << 30, max_active=64)
+    pending = list(reqs)
+    ids = {}
+    t0 = fq.fciqmc_server_clock(srv)
+    active = 0
+    while pending or active:
+        now = fq.fciqmc_server_clock(srv) - t0
+        while pending and pending[0]["arrival"] <= now:
+            r = pending.pop(0)
+            sysd = r["system"]
+            if sysd["kind"] == "abinitio":
+                h1, eri = workloads.synthetic_abinitio(sysd["norb"], sysd["n_chol"], sysd["integral_seed"])
+                sysd = dict(sysd, h1=h1, eri=eri, ecore=0.0)
+            prm = dict(tau=0.0, target_walkers=r["target_walkers"], initial_walkers=min(r["target_walkers"], 1e3),
+                       initiator_threshold=3.0, seed=r["seed"], shift_damping=0.5, shift_interval=5)
+            ids[r["id"]] = fq.fciqmc_server_submit(srv, sysd, prm, target_sigma=1e-3, max_iters=args.max_iters)
+        active = fq.fciqmc_server_tick(srv, 50) if ids else 0
+        if not active and pending:
+            time.sleep(max(0.0, pending[0]["arrival"] - (fq.fciqmc_server_clock(srv) - t0)))
+    t_end = fq.fciqmc_server_clock(srv) - t0
+    st = [fq.fciqmc_server_poll(srv, ids[r["id"]]) for r in reqs]
+    lat = np.array([s["t_done"] - s["t_submit"] for s in st])
+    att = float(sum(s["attempts"] for s in st))
+    conv = sum(1 for s in st if s["state_name"] == "converged")
+    return {"metric": METRIC, "value": float(np.percentile(lat, 50)), "unit": "s (p50 time to answer)",
+            "higher_is_better": False, "n_gpus": 1, "steps": len(reqs), "warmup": 0, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "requests": len(reqs), "converged": conv, "capped": len(reqs) - conv,
+            "requests_per_s": len(reqs) / t_end, "attempts_per_s": att / t_end,
+            "config": {"workload": "serving stream: Poisson 20/s, 1D/2D Hubbard 8-18 sites and ab initio 16-40 "
+                                   "orbitals, targets 1e4..1e7, to sigma(E_proj) < 1 mEh",
+                       "max_iters": args.max_iters, "tau": "0.5/sum_j|H_ref,j| per request"}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="abinitio24", choices=["abinitio24", "batch", "serving"])
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--max-iters", type=int, default=20000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))
@@ -147,6 +240,13 @@ def main():
     if args.impl == "reference":
         out = run_reference(args, rank, world)
         if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if args.workload in ("batch", "serving"):
+        import torch
+        torch.cuda.set_device(local)
+        out = run_batch(args) if args.workload == "batch" else run_serving(args)
+        if rank == 0:
             print(json.dumps(out), flush=True)
         return
 

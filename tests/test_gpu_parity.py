@@ -224,7 +224,8 @@ def test_full_size_sampled_parity_abinitio_24():
     ("hubbard_4x4_D200", workloads.hubbard_2d(4, 4, 4.0),
      dict(tau=0.005, target_walkers=5000, initiator_threshold=3.0, seed=7, semistoch_size=200, semistoch_start=3), 200),
     ("abinitio_7_D_ties", workloads.small_abinitio(7, 2, 2, seed=13),
-     dict(tau=0.004, target_walkers=800, initiator_threshold=0.0, seed=8, semistoch_size=150, semistoch_start=1), 150),
+     dict(tau=0.004, target_walkers=800, initial_walkers=800.0, initiator_threshold=0.0, seed=8, semistoch_size=150,
+          semistoch_start=1), 150),
 ])
 def test_semistochastic_bit_exact(name, sysd, params, n):
     """Deterministic projection inside D (Sec. III): selection of the N_D most
@@ -244,9 +245,9 @@ def test_semistochastic_whole_space_converges_to_exact_energy():
     sysd = workloads.hubbard_1d(6, 1.0, 4.0)
     s = oracle.system_from_workload(sysd)
     e0, _, dets = s.exact_ground_state()
-    g = fq.fciqmc_create(sysd, dict(tau=0.02, target_walkers=2000, initial_walkers=100.0, seed=3,
+    g = fq.fciqmc_create(sysd, dict(tau=0.02, target_walkers=4e4, initial_walkers=4e4, seed=3,
                                     semistoch_size=len(dets), semistoch_start=200, shift_damping=0.5,
-                                    shift_interval=5, initial_shift=e0 + 0.2))
+                                    shift_interval=5, initial_shift=e0))
     fq.fciqmc_step(g, 2500)
     st = fq.fciqmc_iter_stats_get(g)
     st_state = fq.fciqmc_export_state(g)
