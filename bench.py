@@ -35,7 +35,14 @@ EQUIL_ITERS = 300
 E2E_STEPS = 40
 
 
-def workload_params(seed_offset=0):
+def workload_params(seed_offset=0, workload="abinitio24"):
+    if workload == "abinitio50":
+        # 50 orbitals, 10+10 electrons, 200 Cholesky vectors: sum_j |H_ref,j| = 39309 Eh,
+        # so tau = 0.5 / 39309 rounded down = 1.25e-5 (the prescribed 5e-4 gives 19.7)
+        sysd, prm = workloads.config_abinitio_50()
+        prm = dict(prm, tau=1.25e-5, target_walkers=6e7, initial_walkers=6e7, shift_damping=1.0, shift_interval=2,
+                   seed=prm["seed"] + seed_offset, semistoch_size=10000, semistoch_start=100)
+        return sysd, prm
     sysd, prm = workloads.config_abinitio_24()
     prm = dict(prm, tau=TAU, target_walkers=TARGET, initial_walkers=TARGET, shift_damping=1.0, shift_interval=2,
                seed=prm["seed"] + seed_offset)
@@ -102,6 +109,17 @@ def oracle_rate(sysd, prm, state, shift, iters):
     att = float(np.sum(st["attempts"][-iters:]))
     ann = float(np.sum(st["annihilated"][-iters:]))
     return att / el, ann / el, att, el
+
+
+def aggregate_ranks(t_dev, attempts, annihilated, dist, device):
+    """Replicas (one independent run per rank): the job's time is the slowest
+    rank's, its work the sum over ranks."""
+    import torch
+    tt = torch.tensor([t_dev, attempts, annihilated], dtype=torch.float64, device=device)
+    tmax = tt[0:1].clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tt[1]), float(tt[2])
 
 
 def run_reference(args, rank, world):
@@ -229,7 +247,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="abinitio24", choices=["abinitio24", "batch", "serving"])
+    ap.add_argument("--workload", default="abinitio24", choices=["abinitio24", "abinitio50", "batch", "serving"])
+    ap.add_argument("--equil", type=int, default=EQUIL_ITERS)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--max-iters", type=int, default=20000)
     args = ap.parse_args()
@@ -258,9 +277,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    sysd, prm = workload_params(seed_offset=rank)
+    sysd, prm = workload_params(seed_offset=rank, workload=args.workload)
     h = fq.fciqmc_create(sysd, prm)
-    fq.fciqmc_step(h, EQUIL_ITERS)                       # growth / equilibration, untimed
+    fq.fciqmc_step(h, args.equil)                        # growth / equilibration, untimed
     fq.fciqmc_step(h, args.warmup)                       # warm-up steps
     stream = torch.cuda.ExternalStream(fq.fciqmc_stream(h))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
@@ -294,11 +313,7 @@ def main():
     ndet_mean = float(np.mean(st["ndet"][sel]))
     nw_mean = float(np.mean(st["nw"][sel]))
     if dist:
-        tt = torch.tensor([t_dev, attempts, annihilated], dtype=torch.float64, device="cuda")
-        tmax = tt[0:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        t_dev, attempts, annihilated = float(tmax[0]), float(tt[1]), float(tt[2])
+        t_dev, attempts, annihilated = aggregate_ranks(t_dev, attempts, annihilated, dist, "cuda")
     value = attempts / t_dev
 
     # ---- per-kernel device times for the roofline (events around each launch)
@@ -336,14 +351,17 @@ def main():
     except Exception:
         pass
 
+    big = args.workload == "abinitio50"
     # ---- end to end through the public API: restart from a host checkpoint
     state = fq.fciqmc_export_state(h)
+    if big:  # the oracle and the restart job take a bounded sample of the list (first 2e5 keys)
+        state = {k: v[:200000] for k, v in state.items()}
     shift = fq.fciqmc_export_shift(h)
     pinned = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in state.items()}
     host_state = {k: v.numpy() for k, v in pinned.items()}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h2 = fq.fciqmc_create(sysd, prm)
+    h2 = fq.fciqmc_create(sysd, dict(prm, semistoch_size=0) if big else prm)
     fq.fciqmc_import_state(h2, host_state["alpha"], host_state["beta"], host_state["c"], shift["iteration"],
                            shift["S"], shift["vary"], shift["shift_start"], shift["cnt"], shift["nw_last"])
     fq.fciqmc_step(h2, E2E_STEPS)
@@ -359,7 +377,8 @@ def main():
     # ---- CPU baseline: the oracle on the same equilibrated state, bounded sample
     cpu = None
     if rank == 0 and world >= 1:
-        o_att_rate, o_ann_rate, o_att, o_el = oracle_rate(sysd, prm, state, shift, 1)
+        o_att_rate, o_ann_rate, o_att, o_el = oracle_rate(sysd, dict(prm, semistoch_size=0) if big else prm, state,
+                                                          shift, 1)
         cpu = {"value": o_att_rate, "unit": "spawn attempts/s", "cores": 1, "kind": "oracle",
                "sample": "1 oracle iteration (%.3g attempts, %.1f s) from the GPU state at %.3g walkers" %
                          (o_att, o_el, nw_mean)}
@@ -370,9 +389,13 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "annihilated_per_s": annihilated / t_dev,
-            "config": {"workload": "abinitio-24orb-6a6b (synthetic: 96 Cholesky vectors, seed 2)",
-                       "generator": "uniform, p_single 0.1", "initiator_threshold": 3, "tau": TAU,
-                       "tau_note": "prescribed 1e-3 exceeds 1/sum_j|H_ref,j| (2412 Eh): walker number uncontrollable",
+            "config": {"workload": ("abinitio-24orb-6a6b (synthetic: 96 Cholesky vectors, seed 2)"
+                                    if args.workload == "abinitio24" else
+                                    "abinitio-50orb-10a10b (synthetic: 200 Cholesky vectors, seed 4), D = 1e4"),
+                       "generator": "uniform, p_single 0.1", "initiator_threshold": 3, "tau": prm["tau"],
+                       "tau_note": ("prescribed 1e-3 exceeds 1/sum_j|H_ref,j| (2412 Eh): walker number uncontrollable"
+                                    if args.workload == "abinitio24" else
+                                    "prescribed 5e-4 exceeds 1/sum_j|H_ref,j| (39309 Eh): walker number uncontrollable"),
                        "walkers_mean": nw_mean, "dets_mean": ndet_mean, "l2": "flushed (256 MB write) between steps",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "kernel": "k_annihilate", "achieved": achieved, "peak": peak,
@@ -383,8 +406,9 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_att / e2e_el, "unit": "spawn attempts/s", "h2d_bytes_per_step": h2d / E2E_STEPS,
                     "d2h_bytes_per_step": d2h / E2E_STEPS,
-                    "job": "create + import 1e6-walker checkpoint + %d steps + export + energy" % E2E_STEPS},
-            "gpu_launches": args.steps * 5,
+                    "job": "create + import %s checkpoint + %d steps + export + energy" %
+                           ("2e5-determinant sample" if big else "1e6-walker", E2E_STEPS)},
+            "gpu_launches": args.steps * (6 if fq.fciqmc_layout(h) and prm.get("semistoch_size", 0) else 5),
             "wall_s_timed": wall,
             "clocks": clk.summary(),
             "energy": {"e_proj_mean": en["e_proj_mean"], "e_proj_sigma": en["e_proj_sigma"], "shift": en["shift"]},

@@ -161,6 +161,16 @@ typedef struct {
 
 typedef struct fciqmc_handle fciqmc_handle;
 
+/* Reads an FCIDUMP file (Knowles-Handy format: a namelist with NORB, NELEC,
+ * MS2, then lines "value i j k l", 1-based orbitals; i j 0 0 one-electron,
+ * 0 0 0 0 core energy) into *out as an FCIQMC_ABINITIO system with
+ * n_alpha = (NELEC + MS2) / 2, n_beta = (NELEC - MS2) / 2.  Integrals are
+ * chemist (ij|kl); each listed value is placed at all of its 8-fold (or
+ * 2-fold for h) symmetric positions.  The arrays are allocated by the library
+ * and released by fciqmc_free_system. */
+int fciqmc_read_fcidump(const char *path, fciqmc_system *out);
+void fciqmc_free_system(fciqmc_system *sys);
+
 /* Creates a run: validates and copies the system, uploads the integrals,
  * places initial_walkers on the reference determinant, sizes the bucketed
  * walker and spawn buffers, and captures one iteration as a CUDA graph.

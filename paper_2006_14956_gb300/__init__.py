@@ -116,6 +116,8 @@ _SIGS = {
     "fciqmc_layout": (C.c_int, [_H, C.POINTER(C.c_int64)]),
     "fciqmc_ref_offdiag_sum": (C.c_int, [_H, _dp]),
     "fciqmc_tau": (C.c_double, [_H]),
+    "fciqmc_read_fcidump": (C.c_int, [C.c_char_p, C.POINTER(fciqmc_system)]),
+    "fciqmc_free_system": (None, [C.POINTER(fciqmc_system)]),
     "fciqmc_ref_offdiag_sum_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                                  C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p]),
     "fciqmc_server_create": (C.c_int, [C.c_int64, C.c_int32, C.c_void_p, C.POINTER(_H)]),
@@ -412,3 +414,18 @@ def fciqmc_server_destroy(server):
     if server.h:
         _lib.fciqmc_server_destroy(server.h)
         server.h = None
+
+
+def fciqmc_read_fcidump(path):
+    """Parse an FCIDUMP file with the library's reader; returns a system dict
+    (numpy copies of h1 and the packed ERI)."""
+    s = fciqmc_system()
+    _check(_lib.fciqmc_read_fcidump(str(path).encode(), C.byref(s)))
+    try:
+        N = s.norb
+        npair = N * (N + 1) // 2
+        h1 = np.ctypeslib.as_array(s.h1, shape=(N * N,)).reshape(N, N).copy()
+        eri = np.ctypeslib.as_array(s.eri, shape=(npair * (npair + 1) // 2,)).copy()
+        return dict(kind="abinitio", norb=N, n_alpha=s.n_alpha, n_beta=s.n_beta, h1=h1, eri=eri, ecore=s.ecore)
+    finally:
+        _lib.fciqmc_free_system(C.byref(s))

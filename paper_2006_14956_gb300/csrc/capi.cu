@@ -1495,3 +1495,99 @@ void fciqmc_server_destroy(fciqmc_server *srv)
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ FCIDUMP
+#include <cctype>
+#include <fstream>
+#include <sstream>
+
+static bool namelist_int(const std::string &nl, const char *key, long long *v)
+{
+    std::string up;
+    for (char c : nl) up += (char)std::toupper((unsigned char)c);
+    std::string k(key);
+    size_t pos = 0;
+    while ((pos = up.find(k, pos)) != std::string::npos) {
+        const bool left_ok = pos == 0 || !std::isalnum((unsigned char)up[pos - 1]);
+        size_t q = pos + k.size();
+        while (q < up.size() && std::isspace((unsigned char)up[q])) q++;
+        if (left_ok && q < up.size() && up[q] == '=') {
+            q++;
+            while (q < up.size() && std::isspace((unsigned char)up[q])) q++;
+            char *end = nullptr;
+            const long long x = std::strtoll(up.c_str() + q, &end, 10);
+            if (end != up.c_str() + q) { *v = x; return true; }
+        }
+        pos += k.size();
+    }
+    return false;
+}
+
+extern "C" int fciqmc_read_fcidump(const char *path, fciqmc_system *out)
+{
+    if (!path || !out) return FCIQMC_ERR_INVALID_ARG;
+    std::ifstream f(path);
+    if (!f) { g_create_error = std::string("cannot open ") + path; return FCIQMC_ERR_INVALID_ARG; }
+    std::string line, nl;
+    bool done = false;
+    while (!done && std::getline(f, line)) {
+        nl += line + " ";
+        std::string up;
+        for (char c : line) up += (char)std::toupper((unsigned char)c);
+        if (up.find("&END") != std::string::npos || up.find('/') != std::string::npos) done = true;
+    }
+    long long norb = 0, nelec = 0, ms2 = 0;
+    if (!done || !namelist_int(nl, "NORB", &norb) || !namelist_int(nl, "NELEC", &nelec)) {
+        g_create_error = "FCIDUMP namelist without NORB/NELEC";
+        return FCIQMC_ERR_INVALID_ARG;
+    }
+    namelist_int(nl, "MS2", &ms2);
+    if (norb < 1 || norb > 64 || nelec < 1 || (nelec + ms2) % 2 || nelec + ms2 < 0 || nelec - ms2 < 0 ||
+        (nelec + ms2) / 2 > norb || (nelec - ms2) / 2 > norb) {
+        g_create_error = "FCIDUMP sizes outside 1 <= NORB <= 64 or inconsistent NELEC/MS2";
+        return FCIQMC_ERR_INVALID_ARG;
+    }
+    const long long N = norb, np = N * (N + 1) / 2, ne = np * (np + 1) / 2;
+    double *h = (double *)std::calloc((size_t)(N * N), sizeof(double));
+    double *eri = (double *)std::calloc((size_t)ne, sizeof(double));
+    if (!h || !eri) { std::free(h); std::free(eri); return FCIQMC_ERR_OUT_OF_MEMORY; }
+    double ecore = 0.0;
+    while (std::getline(f, line)) {
+        for (char &c : line) if (c == 'D' || c == 'd') c = 'E';  // Fortran exponents
+        std::istringstream is(line);
+        double v;
+        long long i, j, k, l;
+        if (!(is >> v >> i >> j >> k >> l)) continue;
+        if (i < 0 || j < 0 || k < 0 || l < 0 || i > N || j > N || k > N || l > N) {
+            std::free(h); std::free(eri);
+            g_create_error = "FCIDUMP index out of range";
+            return FCIQMC_ERR_INVALID_ARG;
+        }
+        if (i == 0 && j == 0 && k == 0 && l == 0) ecore = v;
+        else if (k == 0 && l == 0) {
+            if (i == 0 || j == 0) continue;  // orbital energies: not part of H
+            h[(i - 1) * N + (j - 1)] = v;
+            h[(j - 1) * N + (i - 1)] = v;
+        } else if (i && j && k && l) {
+            eri[pair_index(pair_index(i - 1, j - 1), pair_index(k - 1, l - 1))] = v;
+        }
+    }
+    memset(out, 0, sizeof(*out));
+    out->kind = FCIQMC_ABINITIO;
+    out->norb = (int32_t)N;
+    out->n_alpha = (int32_t)((nelec + ms2) / 2);
+    out->n_beta = (int32_t)((nelec - ms2) / 2);
+    out->ecore = ecore;
+    out->h1 = h;
+    out->eri = eri;
+    return FCIQMC_OK;
+}
+
+extern "C" void fciqmc_free_system(fciqmc_system *sys)
+{
+    if (!sys) return;
+    std::free((void *)sys->h1);
+    std::free((void *)sys->eri);
+    sys->h1 = nullptr;
+    sys->eri = nullptr;
+}

@@ -53,231 +53,347 @@ __device__ __forceinline__ bool in_D(const DevInst &I, u64 a, u64 b)
 }
 
 // ------------------------------------------------------------------ spawning
-// One spawning attempt k from parent (pa, pb) with amplitude-per-attempt cper.
-// flags bit 0: parent is an initiator; bit 1: parent lies in D.
-__device__ void do_attempt(const DevInst &I, long long it, u64 pa, u64 pb, double cper, unsigned flags, u64 k)
+// One spawning attempt k from parent (pa, pb) draws the Philox block
+// (pa, pb, iteration, (k << 8) | spawn).  The block's attempts are first
+// drawn and classified (single, double, lattice hop, failed), queued in
+// shared memory by class, and then each queue is processed by whole warps, so
+// that the long exact sum of a single excitation does not stall warps of
+// doubles.  The words each attempt consumes and every decision are the same
+// as if the attempts were processed one by one.
+
+// append a surviving spawn (weight, Eq. (3) rounding, D -> D filter) to its bucket
+__device__ __forceinline__ void emit_spawn(const DevInst &I, u64 ta, u64 tb, double H, int cls, double cper,
+                                           unsigned flags, u64 w3)
 {
-    u64 w[4];
-    philox(pa, pb, (u64)it, (k << 8) | (u64)PURPOSE_SPAWN, I.seed, 0ULL, w);
-    const int N = I.norb, n = I.n, na = I.na;
-    u64 ta = pa, tb = pb;
-    int cls;
-    double H;
-    if (I.kind == FCIQMC_HUBBARD) {
-        int e = (int)pick(w[1], (u64)n);
-        int sp = e >= na;
-        u64 x = sp ? pb : pa;
-        int p = nth_set(x, sp ? e - na : e);
-        int q = __ldg(I.nbr + 4 * p + (int)pick(w[2], (u64)I.z));
-        if (q < 0 || ((x >> q) & 1ULL)) return;
-        u64 between = p < q ? (mask_below(q) & ~mask_below(p + 1)) : (mask_below(p) & ~mask_below(q + 1));
-        H = (__popcll(x & between) & 1) ? -I.tmt : I.tmt;
-        x ^= (1ULL << p) | (1ULL << q);
-        if (sp) tb = x; else ta = x;
-        cls = CLS_HOP;
-    } else if ((w[0] >> 11) < I.tsingle) {
-        int e = (int)pick(w[1], (u64)n);
-        int sp = e >= na;
-        u64 x = sp ? pb : pa;
-        int i = nth_set(x, sp ? e - na : e);
-        int m = sp ? I.mb : I.ma;
-        if (m == 0) return;
-        int a = nth_set(~x & I.normask, (int)pick(w[2], (u64)m));
-        u64 between = i < a ? (mask_below(a) & ~mask_below(i + 1)) : (mask_below(i) & ~mask_below(a + 1));
-        double v = single_exact(I, pa, pb, sp, i, a);
-        H = (__popcll(x & between) & 1) ? -v : v;
-        x ^= (1ULL << i) | (1ULL << a);
-        if (sp) tb = x; else ta = x;
-        cls = sp ? CLS_SINGLE_B : CLS_SINGLE_A;
-    } else {
-        if (n < 2) return;
-        unsigned xe = (unsigned)pick(w[1], (u64)(n * (n - 1)));
-        int e1 = (int)(xe / (unsigned)(n - 1)), r = (int)(xe % (unsigned)(n - 1));
-        int e2 = r + (r >= e1 ? 1 : 0);
-        int s1 = e1 >= na, s2 = e2 >= na;
-        int o1 = nth_set(s1 ? pb : pa, s1 ? e1 - na : e1);
-        int o2 = nth_set(s2 ? pb : pa, s2 ? e2 - na : e2);
-        int P0, P1, Q0, Q1, oi, oj, oa, ob;
-        if (s1 != s2) {
-            if (I.ma == 0 || I.mb == 0) return;
-            oi = s1 ? o2 : o1;  // alpha electron
-            oj = s1 ? o1 : o2;  // beta electron
-            unsigned y = (unsigned)pick(w[2], (u64)(I.ma * I.mb));
-            oa = nth_set(~pa & I.normask, (int)(y / (unsigned)I.mb));
-            ob = nth_set(~pb & I.normask, (int)(y % (unsigned)I.mb));
-            P0 = oi; P1 = N + oj; Q0 = oa; Q1 = N + ob;
-            ta = pa ^ (1ULL << oi) ^ (1ULL << oa);
-            tb = pb ^ (1ULL << oj) ^ (1ULL << ob);
-            cls = CLS_DOUBLE_AB;
-        } else {
-            int m = s1 ? I.mb : I.ma;
-            if (m < 2) return;
-            u64 x = s1 ? pb : pa;
-            unsigned y = (unsigned)pick(w[2], (u64)(m * (m - 1)));
-            int h1 = (int)(y / (unsigned)(m - 1)), rr = (int)(y % (unsigned)(m - 1));
-            int h2 = rr + (rr >= h1 ? 1 : 0);
-            int q1 = nth_set(~x & I.normask, h1), q2 = nth_set(~x & I.normask, h2);
-            oi = min(o1, o2); oj = max(o1, o2); oa = min(q1, q2); ob = max(q1, q2);
-            int off = s1 ? N : 0;
-            P0 = off + oi; P1 = off + oj; Q0 = off + oa; Q1 = off + ob;
-            x ^= (1ULL << oi) | (1ULL << oj) | (1ULL << oa) | (1ULL << ob);
-            if (s1) tb = x; else ta = x;
-            cls = s1 ? CLS_DOUBLE_BB : CLS_DOUBLE_AA;
-        }
-        u64 xa = pa, xb = pb;
-        int par = flip_parity(xa, xb, N, P0);
-        par ^= flip_parity(xa, xb, N, P1);
-        par ^= flip_parity(xa, xb, N, Q1);
-        par ^= flip_parity(xa, xb, N, Q0);
-        double v = (cls == CLS_DOUBLE_AB) ? eri4(I, oa, oi, ob, oj) : eri4(I, oa, oi, ob, oj) - eri4(I, oa, oj, ob, oi);
-        H = par ? -v : v;
-    }
     if (is_zero(H)) return;
     double ws = -(H * (I.lam[cls] * cper));
     if (abs_lt(ws, I.cmin)) {
-        ws = round_stoch(ws, I.cmin, I.cmin_log2, I.cmin_pow2, w[3]);
+        ws = round_stoch(ws, I.cmin, I.cmin_log2, I.cmin_pow2, w3);
         if (is_zero(ws)) return;
     }
     if (!abs_lt(ws, 0x1p31)) { atomicOr(&I.st->err, ERRB_NUMERIC); return; }
     if ((flags & 2u) && in_D(I, ta, tb)) return;  // D -> D is applied exactly
-    int bt = bucket_of(det_hash(ta, tb), I.bb);
+    const int bt = bucket_of(det_hash(ta, tb), I.bb);
     const int cap_s = I.cap_s;
     if (flags & 1u) {
-        int s = atomicAdd(I.scnt_i + bt, 1);
+        const int s = atomicAdd(I.scnt_i + bt, 1);
         if (s < cap_s) {
-            size_t o = (size_t)bt * cap_s + s;
+            const size_t o = (size_t)bt * cap_s + s;
             I.skey[o] = make_ulonglong2(ta, tb);
             I.sw[o] = ws;
         }
     } else {
-        int s = atomicAdd(I.scnt_n + bt, 1);
-        int slot = cap_s - 1 - s;
+        const int s = atomicAdd(I.scnt_n + bt, 1);
+        const int slot = cap_s - 1 - s;
         if (slot >= 0) {
-            size_t o = (size_t)bt * cap_s + slot;
+            const size_t o = (size_t)bt * cap_s + slot;
             I.skey[o] = make_ulonglong2(ta, tb);
             I.sw[o] = ws;
         }
     }
 }
 
+// lattice hop (Hubbard): electron w1, neighbour slot w2
+__device__ void spawn_hop(const DevInst &I, u64 pa, u64 pb, double cper, unsigned flags, u64 w1, u64 w2, u64 w3)
+{
+    const int e = (int)pick(w1, (u64)I.n);
+    const int sp = e >= I.na;
+    u64 x = sp ? pb : pa;
+    const int p = nth_set(x, sp ? e - I.na : e);
+    const int q = __ldg(I.nbr + 4 * p + (int)pick(w2, (u64)I.z));
+    if (q < 0 || ((x >> q) & 1ULL)) return;
+    const u64 between = p < q ? (mask_below(q) & ~mask_below(p + 1)) : (mask_below(p) & ~mask_below(q + 1));
+    const double H = (__popcll(x & between) & 1) ? -I.tmt : I.tmt;
+    x ^= (1ULL << p) | (1ULL << q);
+    emit_spawn(I, sp ? pa : x, sp ? x : pb, H, CLS_HOP, cper, flags, w3);
+}
+
+// single excitation (App. A): electron w1, hole of its spin w2
+__device__ void spawn_single(const DevInst &I, u64 pa, u64 pb, double cper, unsigned flags, u64 w1, u64 w2, u64 w3)
+{
+    const int e = (int)pick(w1, (u64)I.n);
+    const int sp = e >= I.na;
+    u64 x = sp ? pb : pa;
+    const int i = nth_set(x, sp ? e - I.na : e);
+    const int m = sp ? I.mb : I.ma;
+    const int a = nth_set(~x & I.normask, (int)pick(w2, (u64)m));
+    const u64 between = i < a ? (mask_below(a) & ~mask_below(i + 1)) : (mask_below(i) & ~mask_below(a + 1));
+    const double v = single_exact(I, pa, pb, sp, i, a);
+    const double H = (__popcll(x & between) & 1) ? -v : v;
+    x ^= (1ULL << i) | (1ULL << a);
+    emit_spawn(I, sp ? pa : x, sp ? x : pb, H, sp ? CLS_SINGLE_B : CLS_SINGLE_A, cper, flags, w3);
+}
+
+// double excitation (App. A): ordered electron pair w1, hole pair w2
+__device__ void spawn_double(const DevInst &I, u64 pa, u64 pb, double cper, unsigned flags, u64 w1, u64 w2, u64 w3)
+{
+    const int N = I.norb, n = I.n, na = I.na;
+    const unsigned xe = (unsigned)pick(w1, (u64)(n * (n - 1)));
+    const int e1 = (int)(xe / (unsigned)(n - 1)), r = (int)(xe % (unsigned)(n - 1));
+    const int e2 = r + (r >= e1 ? 1 : 0);
+    const int s1 = e1 >= na, s2 = e2 >= na;
+    const int o1 = nth_set(s1 ? pb : pa, s1 ? e1 - na : e1);
+    const int o2 = nth_set(s2 ? pb : pa, s2 ? e2 - na : e2);
+    int P0, P1, Q0, Q1, oi, oj, oa, ob, cls;
+    u64 ta, tb;
+    if (s1 != s2) {
+        oi = s1 ? o2 : o1;
+        oj = s1 ? o1 : o2;
+        const unsigned y = (unsigned)pick(w2, (u64)(I.ma * I.mb));
+        oa = nth_set(~pa & I.normask, (int)(y / (unsigned)I.mb));
+        ob = nth_set(~pb & I.normask, (int)(y % (unsigned)I.mb));
+        P0 = oi; P1 = N + oj; Q0 = oa; Q1 = N + ob;
+        ta = pa ^ (1ULL << oi) ^ (1ULL << oa);
+        tb = pb ^ (1ULL << oj) ^ (1ULL << ob);
+        cls = CLS_DOUBLE_AB;
+    } else {
+        const int m = s1 ? I.mb : I.ma;
+        u64 x = s1 ? pb : pa;
+        const unsigned y = (unsigned)pick(w2, (u64)(m * (m - 1)));
+        const int h1 = (int)(y / (unsigned)(m - 1)), rr = (int)(y % (unsigned)(m - 1));
+        const int h2 = rr + (rr >= h1 ? 1 : 0);
+        const int q1 = nth_set(~x & I.normask, h1), q2 = nth_set(~x & I.normask, h2);
+        oi = min(o1, o2); oj = max(o1, o2); oa = min(q1, q2); ob = max(q1, q2);
+        const int off = s1 ? N : 0;
+        P0 = off + oi; P1 = off + oj; Q0 = off + oa; Q1 = off + ob;
+        x ^= (1ULL << oi) | (1ULL << oj) | (1ULL << oa) | (1ULL << ob);
+        ta = s1 ? pa : x;
+        tb = s1 ? x : pb;
+        cls = s1 ? CLS_DOUBLE_BB : CLS_DOUBLE_AA;
+    }
+    u64 xa = pa, xb = pb;
+    int par = flip_parity(xa, xb, N, P0);
+    par ^= flip_parity(xa, xb, N, P1);
+    par ^= flip_parity(xa, xb, N, Q1);
+    par ^= flip_parity(xa, xb, N, Q0);
+    const double v = (cls == CLS_DOUBLE_AB) ? eri4(I, oa, oi, ob, oj) : eri4(I, oa, oi, ob, oj) - eri4(I, oa, oj, ob, oi);
+    emit_spawn(I, ta, tb, par ? -v : v, cls, cper, flags, w3);
+}
+
+// class of one attempt from its first two words, or -1 for a failed attempt
+enum { Q_DOUBLE = 0, Q_SINGLE = 1, Q_HOP = 2, NQ = 3 };
+__device__ __forceinline__ int classify(const DevInst &I, u64 pa, u64 pb, u64 w0, u64 w1)
+{
+    if (I.kind == FCIQMC_HUBBARD) return Q_HOP;
+    if ((w0 >> 11) < I.tsingle) {
+        const int e = (int)pick(w1, (u64)I.n);
+        return (e >= I.na ? I.mb : I.ma) == 0 ? -1 : Q_SINGLE;
+    }
+    const int n = I.n;
+    if (n < 2) return -1;
+    const unsigned xe = (unsigned)pick(w1, (u64)(n * (n - 1)));
+    const int e1 = (int)(xe / (unsigned)(n - 1)), r = (int)(xe % (unsigned)(n - 1));
+    const int e2 = r + (r >= e1 ? 1 : 0);
+    const int s1 = e1 >= I.na, s2 = e2 >= I.na;
+    if (s1 != s2) return (I.ma == 0 || I.mb == 0) ? -1 : Q_DOUBLE;
+    return (s1 ? I.mb : I.ma) < 2 ? -1 : Q_DOUBLE;
+}
+
+constexpr int CHUNK = 1024;  // attempts drawn and queued per round
+struct SpawnRec {
+    u64 w1, w2, w3;
+    unsigned det;
+    unsigned pad;
+};
+struct K1Smem {
+    ulonglong2 key[CAP_M];
+    double cper[CAP_M];
+    unsigned off[CAP_M + 1];
+    unsigned char fl[CAP_M];
+    SpawnRec rec[CHUNK];
+    int qn[NQ];
+    unsigned wsum[K1_THREADS / 32];
+    long long wl[K1_THREADS / 32];
+    int hdr_err, hdr_par;
+    long long hdr_it;
+};
+
+// draw and classify attempts [a0, a1) (attempt a of parent `det`, slot k), then process by class
+template <typename MAP>
+__device__ void run_attempts(const DevInst &I, K1Smem &S, long long it, unsigned A, MAP map)
+{
+    const int t = threadIdx.x, lane = t & 31;
+    for (unsigned a0 = 0; a0 < A; a0 += CHUNK) {
+        const unsigned a1 = min(A, a0 + CHUNK);
+        if (t < NQ) S.qn[t] = 0;
+        __syncthreads();
+        // queues are laid out back to back: doubles from the front of rec[],
+        // singles and hops from the back (hops only exist without the others)
+        for (unsigned a = a0 + t; a < a1 + ((a1 - a0) % 32 ? 32 - (a1 - a0) % 32 : 0); a += K1_THREADS) {
+            int cls = -1;
+            unsigned det = 0;
+            u64 w[4] = {0, 0, 0, 0};
+            if (a < a1) {
+                u64 k;
+                det = map.det_of(a, k);
+                const ulonglong2 kk = map.key(det);
+                philox(kk.x, kk.y, (u64)it, (k << 8) | (u64)PURPOSE_SPAWN, I.seed, 0ULL, w);
+                cls = classify(I, kk.x, kk.y, w[0], w[1]);
+            }
+            const bool front = cls == Q_DOUBLE, back = cls == Q_SINGLE || cls == Q_HOP;
+            const unsigned mf = __ballot_sync(0xffffffffu, front), mb = __ballot_sync(0xffffffffu, back);
+            int bf = 0, bk = 0;
+            if (lane == 0) {
+                if (mf) bf = atomicAdd(&S.qn[Q_DOUBLE], __popc(mf));
+                if (mb) bk = atomicAdd(&S.qn[Q_SINGLE], __popc(mb));
+            }
+            bf = __shfl_sync(0xffffffffu, bf, 0);
+            bk = __shfl_sync(0xffffffffu, bk, 0);
+            const unsigned below = (1u << lane) - 1u;
+            if (front || back) {
+                const int slot = front ? bf + __popc(mf & below) : CHUNK - 1 - (bk + __popc(mb & below));
+                SpawnRec &r = S.rec[slot];
+                r.w1 = w[1]; r.w2 = w[2]; r.w3 = w[3]; r.det = det;
+            }
+        }
+        __syncthreads();
+        const int nd = S.qn[Q_DOUBLE], ns = S.qn[Q_SINGLE];
+        for (int q = t; q < nd; q += K1_THREADS) {
+            const SpawnRec r = S.rec[q];
+            const ulonglong2 kk = map.key(r.det);
+            spawn_double(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3);
+        }
+        for (int q = t; q < ns; q += K1_THREADS) {
+            const SpawnRec r = S.rec[CHUNK - 1 - q];
+            const ulonglong2 kk = map.key(r.det);
+            if (I.kind == FCIQMC_HUBBARD) spawn_hop(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3);
+            else spawn_single(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3);
+        }
+        __syncthreads();
+    }
+}
+
+// attempts of the light determinants of one bucket
+struct BucketMap {
+    const K1Smem *S;
+    __device__ unsigned det_of(unsigned a, u64 &k) const
+    {
+        int lo = 0, hi = CAP_M;  // largest d with off[d] <= a (off[CAP_M] = total > a)
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (S->off[mid] <= a) lo = mid; else hi = mid;
+        }
+        k = a - S->off[lo];
+        return (unsigned)lo;
+    }
+    __device__ ulonglong2 key(unsigned d) const { return S->key[d]; }
+    __device__ double cper(unsigned d) const { return S->cper[d]; }
+    __device__ unsigned flags(unsigned d) const { return S->fl[d]; }
+};
+
+// attempts k0 .. k0+count-1 of one heavy determinant
+struct HeavyMap {
+    HeavyChunk h;
+    __device__ unsigned det_of(unsigned a, u64 &k) const { k = h.k0 + a; return 0; }
+    __device__ ulonglong2 key(unsigned) const { return make_ulonglong2(h.a, h.b); }
+    __device__ double cper(unsigned) const { return h.cper; }
+    __device__ unsigned flags(unsigned) const { return h.flags; }
+};
+
 __global__ void __launch_bounds__(K1_THREADS) k_spawn(const DevInst *__restrict__ insts, const int *__restrict__ unit_start,
                                                       int n_inst, int n_units)
 {
-    __shared__ unsigned s_off[K1_THREADS + 1];
-    __shared__ u64 s_a[K1_THREADS], s_b[K1_THREADS];
-    __shared__ double s_cper[K1_THREADS];
-    __shared__ unsigned s_fl[K1_THREADS];
-    __shared__ unsigned s_w[K1_THREADS / 32];
-    __shared__ long long s_wl[K1_THREADS / 32];
-    __shared__ int s_err, s_par;
-    __shared__ long long s_it;
+    extern __shared__ __align__(16) unsigned char k1_raw[];
+    K1Smem &S = *reinterpret_cast<K1Smem *>(k1_raw);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    constexpr int PER = CAP_M / K1_THREADS;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
         const int ii = find_inst(unit_start, n_inst, u);
         const DevInst &I = insts[ii];
         if (t == 0) {
-            s_err = *(volatile int *)&I.st->err;
-            s_par = I.st->parity;
-            s_it = I.st->iter;
+            S.hdr_err = *(volatile int *)&I.st->err;
+            S.hdr_par = I.st->parity;
+            S.hdr_it = I.st->iter;
         }
         __syncthreads();
-        if (s_err) { __syncthreads(); continue; }
-        const int b = u - I.unit0, par = s_par;
-        const long long it = s_it;
+        const int err = S.hdr_err, par = S.hdr_par;
+        const long long it = S.hdr_it;
+        __syncthreads();
+        if (err) continue;
+        const int b = u - I.unit0;
         const int m = I.cnt[par][b];
         const size_t base = (size_t)b * CAP_M;
+        // load the bucket: thread t owns determinants PER*t .. PER*t+PER-1
         long long att = 0;
-        for (int d0 = 0; d0 < m; d0 += K1_THREADS) {
-            const int d = d0 + t;
-            unsigned nat_l = 0, fl = 0;
-            u64 pa = 0, pb = 0;
+        unsigned mine = 0;
+        unsigned nl[PER];
+        for (int j = 0; j < PER; j++) {
+            const int d = PER * t + j;
+            nl[j] = 0;
+            if (d >= m) continue;
+            const ulonglong2 kk = I.key[par][base + d];
+            const double c = I.c[par][base + d];
+            const uint8_t f = I.fl[par][base + d];
+            unsigned fl = 0;
             double cper = 0.0;
             u64 nat = 0;
-            if (d < m) {
-                ulonglong2 kk = I.key[par][base + d];
-                double c = I.c[par][base + d];
-                uint8_t f = I.fl[par][base + d];
-                pa = kk.x; pb = kk.y;
-                if (!is_zero(c)) {
-                    if (!abs_lt(c, 0x1p31)) {
-                        atomicOr(&I.st->err, ERRB_NUMERIC);
-                    } else {
-                        nat = ceil_abs(c);
-                        bool init = (dbits(c) & ~SIGN64) > dbits(I.n_a) || (f & (DFLAG_REF | DFLAG_D));
-                        fl = (init ? 1u : 0u) | ((f & DFLAG_D) ? 2u : 0u);
-                        cper = c / (double)nat;
-                        att += (long long)nat;
-                        if (nat <= HEAVY_ATT) nat_l = (unsigned)nat;
-                    }
-                }
-            }
-            // heavy determinants: split into slices, written cooperatively by the warp
-            unsigned hv = __ballot_sync(0xffffffffu, nat > HEAVY_ATT);
-            while (hv) {
-                int src = __ffs(hv) - 1;
-                hv &= hv - 1;
-                u64 hn = __shfl_sync(0xffffffffu, nat, src);
-                u64 ha = __shfl_sync(0xffffffffu, pa, src), hb = __shfl_sync(0xffffffffu, pb, src);
-                double hc = __shfl_sync(0xffffffffu, cper, src);
-                unsigned hfl = __shfl_sync(0xffffffffu, fl, src);
-                unsigned nch = (unsigned)((hn + HEAVY_ATT - 1) / HEAVY_ATT);
-                int q0 = 0;
-                if (lane == 0) q0 = atomicAdd(&I.st->heavy_n, (int)nch);
-                q0 = __shfl_sync(0xffffffffu, q0, 0);
-                if ((long long)q0 + nch > (long long)I.heavy_cap) {
-                    if (lane == 0) atomicOr(&I.st->err, ERRB_HEAVY_CAP);
+            if (!is_zero(c)) {
+                if (!abs_lt(c, 0x1p31)) {
+                    atomicOr(&I.st->err, ERRB_NUMERIC);
                 } else {
-                    for (unsigned q = lane; q < nch; q += 32) {
-                        HeavyChunk h;
-                        h.a = ha; h.b = hb; h.cper = hc; h.k0 = (u64)q * HEAVY_ATT;
-                        u64 left = hn - h.k0;
-                        h.count = (unsigned)(left < HEAVY_ATT ? left : HEAVY_ATT);
-                        h.flags = hfl;
-                        I.heavy[q0 + q] = h;
+                    nat = ceil_abs(c);
+                    const bool init = (dbits(c) & ~SIGN64) > dbits(I.n_a) || (f & (DFLAG_REF | DFLAG_D));
+                    fl = (init ? 1u : 0u) | ((f & DFLAG_D) ? 2u : 0u);
+                    cper = c / (double)nat;
+                    att += (long long)nat;
+                    if (nat > HEAVY_ATT) {  // sliced into the heavy queue
+                        const unsigned nch = (unsigned)((nat + HEAVY_ATT - 1) / HEAVY_ATT);
+                        const int q0 = atomicAdd(&I.st->heavy_n, (int)nch);
+                        if ((long long)q0 + nch > (long long)I.heavy_cap) atomicOr(&I.st->err, ERRB_HEAVY_CAP);
+                        else
+                            for (unsigned q = 0; q < nch; q++) {
+                                HeavyChunk h;
+                                h.a = kk.x; h.b = kk.y; h.cper = cper; h.k0 = (u64)q * HEAVY_ATT;
+                                const u64 left = nat - h.k0;
+                                h.count = (unsigned)(left < HEAVY_ATT ? left : HEAVY_ATT);
+                                h.flags = fl;
+                                I.heavy[q0 + q] = h;
+                            }
+                    } else {
+                        nl[j] = (unsigned)nat;
                     }
                 }
             }
-            // block exclusive scan of the light attempt counts
-            unsigned v = nat_l;
-            for (int o = 1; o < 32; o <<= 1) {
-                unsigned y = __shfl_up_sync(0xffffffffu, v, o);
-                if (lane >= o) v += y;
-            }
-            if (lane == 31) s_w[warp] = v;
-            __syncthreads();
-            if (warp == 0) {
-                unsigned x = lane < K1_THREADS / 32 ? s_w[lane] : 0u;
-                for (int o = 1; o < 32; o <<= 1) {
-                    unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-                    if (lane >= o) x += y;
-                }
-                if (lane < K1_THREADS / 32) s_w[lane] = x;
-            }
-            __syncthreads();
-            unsigned excl = v - nat_l + (warp ? s_w[warp - 1] : 0u);
-            s_off[t] = excl;
-            if (t == K1_THREADS - 1) s_off[K1_THREADS] = excl + nat_l;
-            s_a[t] = pa; s_b[t] = pb; s_cper[t] = cper; s_fl[t] = fl;
-            __syncthreads();
-            const unsigned total = s_off[K1_THREADS];
-            for (unsigned a = t; a < total; a += K1_THREADS) {
-                int lo = 0, hi = K1_THREADS;
-                while (hi - lo > 1) {
-                    int mid = (lo + hi) >> 1;
-                    if (s_off[mid] <= a) lo = mid; else hi = mid;
-                }
-                do_attempt(I, it, s_a[lo], s_b[lo], s_cper[lo], s_fl[lo], (u64)(a - s_off[lo]));
-            }
-            __syncthreads();
+            S.key[d] = kk;
+            S.cper[d] = cper;
+            S.fl[d] = (unsigned char)fl;
+            mine += nl[j];
         }
-        // attempts of this bucket
+        // exclusive scan of the light attempt counts in determinant order
+        unsigned v = mine;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane == 31) S.wsum[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned x = lane < K1_THREADS / 32 ? S.wsum[lane] : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane < K1_THREADS / 32) S.wsum[lane] = x;
+        }
+        __syncthreads();
+        unsigned ex = v - mine + (warp ? S.wsum[warp - 1] : 0u);
+        for (int j = 0; j < PER; j++) {
+            S.off[PER * t + j] = ex;
+            ex += nl[j];
+        }
+        if (t == K1_THREADS - 1) S.off[CAP_M] = ex;
+        __syncthreads();
+        const unsigned total = S.off[CAP_M];
+        BucketMap map{&S};
+        run_attempts(I, S, it, total, map);
+        // attempts of this bucket (light and heavy)
         for (int o = 16; o >= 1; o >>= 1) att += __shfl_xor_sync(0xffffffffu, att, o);
-        if (lane == 0) s_wl[warp] = att;
+        if (lane == 0) S.wl[warp] = att;
         __syncthreads();
         if (t == 0) {
-            long long s = 0;
-            for (int k = 0; k < K1_THREADS / 32; k++) s += s_wl[k];
-            I.part[b].attempts = s;
+            long long sm = 0;
+            for (int k = 0; k < K1_THREADS / 32; k++) sm += S.wl[k];
+            I.part[b].attempts = sm;
         }
         __syncthreads();
     }
@@ -285,24 +401,24 @@ __global__ void __launch_bounds__(K1_THREADS) k_spawn(const DevInst *__restrict_
 
 __global__ void __launch_bounds__(K1_THREADS) k_spawn_heavy(const DevInst *__restrict__ insts, int n_inst)
 {
-    __shared__ int s_n, s_err;
-    __shared__ long long s_it;
+    extern __shared__ __align__(16) unsigned char k1_raw[];
+    K1Smem &S = *reinterpret_cast<K1Smem *>(k1_raw);
     for (int ii = 0; ii < n_inst; ii++) {
         const DevInst &I = insts[ii];
         if (threadIdx.x == 0) {
-            s_err = *(volatile int *)&I.st->err;
-            s_n = I.st->heavy_n;
-            s_it = I.st->iter;
+            S.hdr_err = *(volatile int *)&I.st->err;
+            S.qn[0] = I.st->heavy_n;
+            S.hdr_it = I.st->iter;
         }
         __syncthreads();
-        if (!s_err) {
-            for (int q = blockIdx.x; q < s_n; q += gridDim.x) {
-                HeavyChunk h = I.heavy[q];
-                for (unsigned a = threadIdx.x; a < h.count; a += blockDim.x)
-                    do_attempt(I, s_it, h.a, h.b, h.cper, h.flags, h.k0 + a);
-            }
-        }
+        const int err = S.hdr_err, nh = S.qn[0];
+        const long long it = S.hdr_it;
         __syncthreads();
+        if (err) continue;
+        for (int q = blockIdx.x; q < nh; q += gridDim.x) {
+            HeavyMap map{I.heavy[q]};
+            run_attempts(I, S, it, map.h.count, map);
+        }
     }
 }
 
@@ -893,17 +1009,21 @@ void launch_spawn(const DevInst *dinst, const int *unit_start, int n_inst, int n
 {
     int grid = n_units < num_sms() * 8 ? n_units : num_sms() * 8;
     if (grid < 1) grid = 1;
-    k_spawn<<<grid, K1_THREADS, 0, s>>>(dinst, unit_start, n_inst, n_units);
+    k_spawn<<<grid, K1_THREADS, sizeof(K1Smem), s>>>(dinst, unit_start, n_inst, n_units);
 }
 
 void launch_spawn_heavy(const DevInst *dinst, int n_inst, cudaStream_t s)
 {
-    k_spawn_heavy<<<num_sms() * 4, K1_THREADS, 0, s>>>(dinst, n_inst);
+    k_spawn_heavy<<<num_sms() * 2, K1_THREADS, sizeof(K1Smem), s>>>(dinst, n_inst);
 }
 
 cudaError_t init_kernels()
 {
-    return cudaFuncSetAttribute(k_annihilate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K3Smem));
+    cudaError_t e = cudaFuncSetAttribute(k_annihilate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K3Smem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spawn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K1Smem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_spawn_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K1Smem));
+    return e;
 }
 
 size_t annihilate_smem_bytes() { return sizeof(K3Smem); }

@@ -138,3 +138,27 @@ def small_abinitio(norb=6, na=3, nb=3, n_chol=None, seed=7):
     n_chol = n_chol or 4 * norb
     h, eri = synthetic_abinitio(norb, n_chol, seed)
     return dict(kind="abinitio", norb=norb, n_alpha=na, n_beta=nb, h1=h, eri=eri, ecore=0.0)
+
+
+def write_fcidump(path, h, eri_packed, n_alpha, n_beta, ecore=0.0):
+    """Write integrals in FCIDUMP form (one entry per symmetry-unique index set)."""
+    norb = h.shape[0]
+    with open(path, "w") as f:
+        f.write(" &FCI NORB=%d,NELEC=%d,MS2=%d,\n  ORBSYM=%s\n  ISYM=1,\n &END\n" %
+                (norb, n_alpha + n_beta, n_alpha - n_beta, "1," * norb))
+        for i in range(norb):
+            for j in range(i + 1):
+                ij = pair_index(i, j)
+                for k in range(norb):
+                    for l in range(k + 1):
+                        kl = pair_index(k, l)
+                        if kl > ij:
+                            continue
+                        v = eri_packed[ij * (ij + 1) // 2 + kl]
+                        if v != 0.0:
+                            f.write("%.17e %d %d %d %d\n" % (v, i + 1, j + 1, k + 1, l + 1))
+        for i in range(norb):
+            for j in range(i + 1):
+                if h[i, j] != 0.0:
+                    f.write("%.17e %d %d 0 0\n" % (h[i, j], i + 1, j + 1))
+        f.write("%.17e 0 0 0 0\n" % ecore)
