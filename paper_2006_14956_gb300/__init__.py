@@ -116,6 +116,7 @@ _SIGS = {
     "fciqmc_layout": (C.c_int, [_H, C.POINTER(C.c_int64)]),
     "fciqmc_ref_offdiag_sum": (C.c_int, [_H, _dp]),
     "fciqmc_tau": (C.c_double, [_H]),
+    "fciqmc_autotune": (C.c_int, [C.POINTER(_H), C.c_int32, C.c_int64, C.POINTER(C.c_int32)]),
     "fciqmc_read_fcidump": (C.c_int, [C.c_char_p, C.POINTER(fciqmc_system)]),
     "fciqmc_free_system": (None, [C.POINTER(fciqmc_system)]),
     "fciqmc_ref_offdiag_sum_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
@@ -332,6 +333,10 @@ def fciqmc_iter_stats_get(handle, first=0, count=None):
     return {f: np.array([getattr(arr[i], f) for i in range(count)]) for f in names}
 
 
+def fciqmc_iter_stats_count(handle):
+    return _lib.fciqmc_iter_stats_count(handle.h)
+
+
 def fciqmc_set_profiling(handle, on=True):
     _check(_lib.fciqmc_set_profiling(handle.h, int(bool(on))), handle.h)
 
@@ -429,3 +434,10 @@ def fciqmc_read_fcidump(path):
         return dict(kind="abinitio", norb=N, n_alpha=s.n_alpha, n_beta=s.n_beta, h1=h1, eri=eri, ecore=s.ecore)
     finally:
         _lib.fciqmc_free_system(C.byref(s))
+
+
+def fciqmc_autotune(handles, n_iter):
+    arr = (_H * len(handles))(*[x.h for x in handles])
+    out = (C.c_int32 * 3)()
+    _check(_lib.fciqmc_autotune(arr, len(handles), int(n_iter), out), handles[0].h)
+    return dict(spawn_blocks_per_sm=out[0], heavy_blocks_per_sm=out[1], annihilate_blocks_per_sm=out[2])

@@ -291,6 +291,7 @@ static int grow_buckets(fciqmc_handle *h)
 {
     if (h->bb >= 24) return fail(h, FCIQMC_ERR_CAPACITY, "walker list exceeds 2^24 buckets");
     DevInst nI = h->hi;
+    if (nI.cap_s > CAP_S0) nI.cap_s /= 2;  // each new bucket receives about half the spawns
     int rc = alloc_layout(h, nI, h->bb + 1);
     if (rc) return fail(h, rc, "out of device memory while growing the walker buffers");
     DevInst *tmp = (DevInst *)dev_alloc(h, 2 * sizeof(DevInst));
@@ -358,6 +359,7 @@ static int reset_after_error(fciqmc_handle *h)
     h->hst.big_n = 0;
     h->hst.need_spawn = 0;
     h->hst.need_main = 0;
+    h->hst.n_spawn_over = 0;
     return write_state(h);
 }
 
@@ -910,6 +912,7 @@ static int handle_flags(fciqmc_handle *h, int *retries)
     }
     if (++*retries > 64) return fail(h, FCIQMC_ERR_CAPACITY, "capacity growth did not converge");
     const long long need = h->hst.need_spawn;
+    const int n_over = h->hst.n_spawn_over;
     rc = reset_after_error(h);
     if (rc) return rc;
     if (err & (ERRB_SPAWN_CAP | ERRB_MAIN_CAP)) {
@@ -917,8 +920,7 @@ static int handle_flags(fciqmc_handle *h, int *retries)
         // crowded buckets: split buckets.  Spawns concentrated on a few
         // determinants: enlarge the spawn regions to what was needed.
         const long long nbk = 1LL << h->bb;
-        const long long spawns_prev = h->hist.empty() ? 0 : h->hist.back().spawns;
-        const bool even = spawns_prev > nbk * (long long)h->hi.cap_s / 2;
+        const bool even = (long long)n_over * 16 > nbk;  // many buckets overflowed: the load is spread
         if ((err & ERRB_MAIN_CAP) || ((err & ERRB_SPAWN_CAP) && even)) rc = grow_buckets(h);
         else rc = grow_spawn_capacity(h, need);
         if (rc) return rc;
@@ -1590,4 +1592,59 @@ extern "C" void fciqmc_free_system(fciqmc_system *sys)
     std::free((void *)sys->eri);
     sys->h1 = nullptr;
     sys->eri = nullptr;
+}
+
+// ------------------------------------------------------------------ autotuner
+extern "C" int fciqmc_autotune(fciqmc_handle **hs, int32_t k, int64_t n_iter, int32_t out[3])
+{
+    if (!hs || k < 1 || n_iter < 1 || !out) return FCIQMC_ERR_INVALID_ARG;
+    const int spawn_c[] = {2, 4, 8, 16}, anni_c[] = {1, 2, 4}, heavy_c[] = {1, 2, 4};
+    int best_s = 8, best_h = 2, best_a = 2;
+    double best = 1e300;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto timed = [&](int sb, int hb, int ab, double *ms) -> int {
+        set_launch_geometry(sb, hb, ab);
+        for (int i = 0; i < k; i++) {
+            int rc = capture_graph(hs[i]);
+            if (rc) return rc;
+        }
+        cudaStream_t st = hs[0]->stream;
+        cudaEventRecord(e0, st);
+        int rc = fciqmc_step_batch(hs, k, n_iter);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float m = 0.f;
+        cudaEventElapsedTime(&m, e0, e1);
+        *ms = m;
+        return rc;
+    };
+    // one sweep per kernel, the others held at their current best
+    for (int sb : spawn_c) {
+        double ms;
+        int rc = timed(sb, best_h, best_a, &ms);
+        if (rc) return rc;
+        if (ms < best) { best = ms; best_s = sb; }
+    }
+    best = 1e300;
+    for (int ab : anni_c) {
+        double ms;
+        int rc = timed(best_s, best_h, ab, &ms);
+        if (rc) return rc;
+        if (ms < best) { best = ms; best_a = ab; }
+    }
+    best = 1e300;
+    for (int hb : heavy_c) {
+        double ms;
+        int rc = timed(best_s, hb, best_a, &ms);
+        if (rc) return rc;
+        if (ms < best) { best = ms; best_h = hb; }
+    }
+    set_launch_geometry(best_s, best_h, best_a);
+    for (int i = 0; i < k; i++) capture_graph(hs[i]);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    out[0] = best_s; out[1] = best_h; out[2] = best_a;
+    return FCIQMC_OK;
 }

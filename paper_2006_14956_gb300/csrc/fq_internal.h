@@ -72,7 +72,7 @@ struct IterState {  // device-resident iteration state of one run
     int big_n;              // buckets deferred to the large-bucket kernel
     int need_spawn;         // largest spawn count of an overflowing bucket
     int need_main;          // largest new-list size of an overflowing bucket
-    int pad0;
+    int n_spawn_over;       // buckets whose spawns overflowed
     long long stop_iter;    // K5 raises ERRB_STOP when iter reaches it
     long long pad1;
 };
@@ -157,6 +157,8 @@ void launch_build_hd(const DevInst *dinst, int nd, const ulonglong2 *dkey, long 
                      int *col, double *val, int pass, cudaStream_t s);
 void launch_mark_d(const DevInst *dinst, int parity, int nb, cudaStream_t s);
 
+void set_launch_geometry(int spawn_bps, int heavy_bps, int anni_bps);
+void get_launch_geometry(int *spawn_bps, int *heavy_bps, int *anni_bps);
 cudaError_t ref_abs_sum(const DevInst *dinst, double *dpartial, double *out, cudaStream_t s);
 
 // host helpers shared with capi.cu

@@ -747,7 +747,11 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k_annihilate(const DevInst *__r
         const int b = u - I.unit0;
         const int m = I.cnt[par][b], si = I.scnt_i[b], sn = I.scnt_n[b];
         if (si + sn > I.cap_s) {
-            if (t == 0) { atomicOr(&I.st->err, ERRB_SPAWN_CAP); atomicMax(&I.st->need_spawn, si + sn); }
+            if (t == 0) {
+                atomicOr(&I.st->err, ERRB_SPAWN_CAP);
+                atomicMax(&I.st->need_spawn, si + sn);
+                atomicAdd(&I.st->n_spawn_over, 1);
+            }
             continue;
         }
         if (m + si + sn > EMAX) {  // too large for shared memory: deferred to k_annihilate_big
@@ -1005,16 +1009,31 @@ static int num_sms()
     return g_num_sms;
 }
 
+// launch geometry, chosen by fciqmc_autotune (blocks per SM)
+static int g_spawn_bps = 8, g_heavy_bps = 2, g_anni_bps = 2;
+void set_launch_geometry(int spawn_bps, int heavy_bps, int anni_bps)
+{
+    g_spawn_bps = spawn_bps;
+    g_heavy_bps = heavy_bps;
+    g_anni_bps = anni_bps;
+}
+void get_launch_geometry(int *spawn_bps, int *heavy_bps, int *anni_bps)
+{
+    *spawn_bps = g_spawn_bps;
+    *heavy_bps = g_heavy_bps;
+    *anni_bps = g_anni_bps;
+}
+
 void launch_spawn(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, cudaStream_t s)
 {
-    int grid = n_units < num_sms() * 8 ? n_units : num_sms() * 8;
+    int grid = n_units < num_sms() * g_spawn_bps ? n_units : num_sms() * g_spawn_bps;
     if (grid < 1) grid = 1;
     k_spawn<<<grid, K1_THREADS, sizeof(K1Smem), s>>>(dinst, unit_start, n_inst, n_units);
 }
 
 void launch_spawn_heavy(const DevInst *dinst, int n_inst, cudaStream_t s)
 {
-    k_spawn_heavy<<<num_sms() * 2, K1_THREADS, sizeof(K1Smem), s>>>(dinst, n_inst);
+    k_spawn_heavy<<<num_sms() * g_heavy_bps, K1_THREADS, sizeof(K1Smem), s>>>(dinst, n_inst);
 }
 
 cudaError_t init_kernels()
@@ -1031,7 +1050,7 @@ size_t annihilate_smem_bytes() { return sizeof(K3Smem); }
 cudaError_t launch_annihilate(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, cudaStream_t s)
 {
     const size_t smem = sizeof(K3Smem);
-    int grid = n_units < num_sms() * 2 ? n_units : num_sms() * 2;
+    int grid = n_units < num_sms() * g_anni_bps ? n_units : num_sms() * g_anni_bps;
     if (grid < 1) grid = 1;
     k_annihilate<<<grid, K3_THREADS, smem, s>>>(dinst, unit_start, n_inst, n_units);
     return cudaGetLastError();

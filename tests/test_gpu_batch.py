@@ -54,3 +54,20 @@ def test_batch_runs_with_different_targets_stop_on_time():
     c = fq.fciqmc_create(*RUNS[2])
     fq.fciqmc_step(c, 80)
     assert_states_equal(fq.fciqmc_export_state(b), fq.fciqmc_export_state(c))
+
+
+def test_autotuned_geometry_changes_no_result():
+    fq = _fq()
+    runs = RUNS[:3]
+    a = [fq.fciqmc_create(s, p) for s, p in runs]
+    b = [fq.fciqmc_create(s, p) for s, p in runs]
+    fq.fciqmc_step_batch(a, 60)
+    tuned = fq.fciqmc_autotune(b, 6)      # advances b by 10 sweeps of 6 iterations
+    assert tuned["spawn_blocks_per_sm"] in (2, 4, 8, 16)
+    fq.fciqmc_step_batch(a, 0)
+    done = fq.fciqmc_export_shift(b[0])["iteration"]
+    fq.fciqmc_step_batch(a, done - 60)
+    fq.fciqmc_step_batch(a, 20)
+    fq.fciqmc_step_batch(b, 20)
+    for x, y in zip(a, b):
+        assert_states_equal(fq.fciqmc_export_state(x), fq.fciqmc_export_state(y))
