@@ -54,12 +54,13 @@ class Params(C.Structure):
                 ("initial_walkers", C.c_double), ("initial_shift", C.c_double),
                 ("initiator_threshold", C.c_double), ("c_min", C.c_double), ("p_single", C.c_double),
                 ("shift_interval", C.c_int64), ("seed", C.c_uint64),
-                ("semistoch_size", C.c_int64), ("semistoch_start", C.c_int64)]
+                ("semistoch_size", C.c_int64), ("semistoch_start", C.c_int64), ("generator", C.c_int64)]
 
 
 DEFAULT_PARAMS = dict(tau=0.01, shift_damping=0.1, target_walkers=1e4, initial_walkers=10.0,
                       initial_shift=0.0, initiator_threshold=0.0, c_min=1.0, p_single=0.1,
-                      shift_interval=10, seed=1, semistoch_size=0, semistoch_start=100)
+                      shift_interval=10, seed=1, semistoch_size=0, semistoch_start=100,
+                      generator=0)
 
 CLASSES = ("single_a", "single_b", "double_ab", "double_aa", "double_bb", "hop")
 
@@ -101,6 +102,9 @@ def lib():
                 "orc_params_size": (I32, []),
                 "orc_semistoch_info": (I64, [P, C.POINTER(C.c_int64)]),
                 "orc_proj_energy": (None, [P, dp, dp]),
+                "orc_generate_pchb": (I32, [P, U64, U64, up, up, up, dp]),
+                "orc_pchb_table": (I32, [P, I32, I32, I32, dp, dp, dp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                         C.POINTER(C.c_int32), dp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -306,6 +310,31 @@ class Run:
         cc, cp = _f64(c)
         lib().orc_import(self.h, a.size, ap, bp, cp, int(iteration), float(S), int(vary), int(shift_start),
                          int(cnt), (int(nw_last) >> 64) & 0xFFFFFFFFFFFFFFFF, int(nw_last) & 0xFFFFFFFFFFFFFFFF)
+
+    def generate_pchb(self, det, words):
+        """One generation with the heat-bath doubles of this run: (class, target, |H|/p_gen)."""
+        w, wp = _u64(words)
+        ta = C.c_uint64()
+        tb = C.c_uint64()
+        lam = C.c_double()
+        c = lib().orc_generate_pchb(self.h, det[0], det[1], wp, C.byref(ta), C.byref(tb), C.byref(lam))
+        return c, (ta.value, tb.value), lam.value
+
+    def pchb_table(self, same_spin, i, j):
+        N = self.system.norb
+        K = N * N
+        prob = np.zeros(K)
+        alias = np.zeros(K, np.int32)
+        ea = np.zeros(K, np.int32)
+        eb = np.zeros(K, np.int32)
+        val = np.zeros(K)
+        S = C.c_double()
+        lam = C.c_double()
+        K = lib().orc_pchb_table(self.h, int(same_spin), int(i), int(j), C.byref(S), C.byref(lam),
+                                 prob.ctypes.data_as(C.POINTER(C.c_double)),
+                                 alias.ctypes.data_as(C.POINTER(C.c_int32)), ea.ctypes.data_as(C.POINTER(C.c_int32)),
+                                 eb.ctypes.data_as(C.POINTER(C.c_int32)), val.ctypes.data_as(C.POINTER(C.c_double)))
+        return dict(K=K, S=S.value, lam=lam.value, prob=prob[:K], alias=alias[:K], a=ea[:K], b=eb[:K], val=val[:K])
 
     def proj_energy(self):
         """(E_num, E_den) of the current list, Eq. (9)."""

@@ -518,6 +518,7 @@ typedef struct {
     int64_t shift_interval;
     uint64_t seed;
     int64_t semistoch_size, semistoch_start;
+    int64_t generator; /* 0: uniform doubles, 1: pre-computed heat-bath doubles (App. A) */
 } orc_params;
 
 typedef struct { uint64_t a, b; double c, hd; int flags; } odet; /* flags: 1 ref, 2 in D */
@@ -531,10 +532,30 @@ typedef struct {
     int vary;
 } orc_stat;
 
+/* Pre-computed heat-bath tables (App. A, "Pre-computed heat-bath sampling",
+ * Eq. (hbs)): for every pair of occupied spatial orbitals one distribution
+ * over hole pairs with p(ab|ij) = |H_ij^ab| / sum_a'b' |H_ij^a'b'|, sampled by
+ * Walker's alias method.  Reading: the tables carry explicit spins -- one per
+ * ordered pair (i alpha, j beta) over (a alpha, b beta), H = (ai|bj), and one
+ * per same-spin pair i < j over a < b, H = (ai|bj) - (aj|bi) -- which makes
+ * the paper's exchange/no-exchange split of the spatial tables unnecessary. */
+typedef struct {
+    int K;        /* entries */
+    double S;     /* exact sum of |H| over the entries, rounded once */
+    double lam;   /* (tau * S) / p_pair: |H| / p_gen, the same for every entry */
+    double *prob; /* alias thresholds in [0, 1] */
+    int *alias;
+    int *ea, *eb; /* the hole pair of each entry */
+    double *val;  /* H_ij^ab of each entry (without the determinant's sign) */
+} opchb;
+
 typedef struct {
     orc_sys *s;
     orc_params p;
     double lam[NCLS];
+    opchb *pchb_ab; /* [i * N + j], i alpha, j beta */
+    opchb *pchb_ss; /* [i * N + j], i < j, same spin */
+    int pchb_n;     /* N of the tables (kept: the system may be released first) */
     odet *L;
     int64_t n, cap;
     int64_t iter;
@@ -595,6 +616,175 @@ static int64_t find_D(const orc_run *r, uint64_t a, uint64_t b)
 /* floor(|c| 2^32) as an integer (reading R6) */
 static u128 fx32(double c) { return (u128)(uint64_t)floor(fabs(c) * 4294967296.0); }
 
+/* Walker's alias method, Vose's construction in a fixed order:
+ * q_k = (|H_k| / S) * K; indices with q < 1 go on the stack "small", the rest
+ * on "large" (both filled by ascending k, popped from the top); while both are
+ * non-empty: s = pop(small), l = pop(large), prob[s] = q_s, alias[s] = l,
+ * q_l = (q_l + q_s) - 1, and l is pushed on small if q_l < 1, else on large;
+ * whatever remains gets prob = 1 (alias = itself). */
+static void alias_build(int K, const double *absv, double S, double *prob, int *alias)
+{
+    double *q = malloc(sizeof(double) * K);
+    int *sm = malloc(sizeof(int) * K), *lg = malloc(sizeof(int) * K);
+    int ns = 0, nl = 0;
+    for (int k = 0; k < K; k++) {
+        q[k] = (absv[k] / S) * (double)K;
+        if (q[k] < 1.0) sm[ns++] = k; else lg[nl++] = k;
+        alias[k] = k;
+        prob[k] = 1.0;
+    }
+    while (ns > 0 && nl > 0) {
+        int a = sm[--ns], l = lg[--nl];
+        prob[a] = q[a];
+        alias[a] = l;
+        q[l] = (q[l] + q[a]) - 1.0;
+        if (q[l] < 1.0) sm[ns++] = l; else lg[nl++] = l;
+    }
+    free(q); free(sm); free(lg);
+}
+
+static void pchb_fill(opchb *t, int K, const int *ea, const int *eb, const double *val, double tau, double ppair)
+{
+    xacc x;
+    xacc_zero(&x);
+    double *absv = malloc(sizeof(double) * (K ? K : 1));
+    for (int k = 0; k < K; k++) { absv[k] = fabs(val[k]); xacc_add(&x, absv[k], 0); }
+    t->K = K;
+    t->S = xacc_round(&x);
+    t->lam = (tau * t->S) / ppair;
+    t->prob = malloc(sizeof(double) * (K ? K : 1));
+    t->alias = malloc(sizeof(int) * (K ? K : 1));
+    t->ea = malloc(sizeof(int) * (K ? K : 1));
+    t->eb = malloc(sizeof(int) * (K ? K : 1));
+    t->val = malloc(sizeof(double) * (K ? K : 1));
+    memcpy(t->ea, ea, sizeof(int) * K);
+    memcpy(t->eb, eb, sizeof(int) * K);
+    memcpy(t->val, val, sizeof(double) * K);
+    if (t->S > 0.0) alias_build(K, absv, t->S, t->prob, t->alias);
+    free(absv);
+}
+
+static void pchb_build(orc_run *r)
+{
+    const orc_sys *s = r->s;
+    const int N = s->norb, n = s->na + s->nb;
+    const double ppair = ((1.0 - r->p.p_single) * 2.0) / ((double)n * (double)(n - 1));
+    r->pchb_ab = calloc((size_t)N * N, sizeof(opchb));
+    r->pchb_ss = calloc((size_t)N * N, sizeof(opchb));
+    r->pchb_n = N;
+    int *ea = malloc(sizeof(int) * N * N), *eb = malloc(sizeof(int) * N * N);
+    double *val = malloc(sizeof(double) * N * N);
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            int K = 0;
+            for (int a = 0; a < N; a++)
+                for (int b = 0; b < N; b++) { ea[K] = a; eb[K] = b; val[K] = eri(s, a, i, b, j); K++; }
+            pchb_fill(&r->pchb_ab[i * N + j], K, ea, eb, val, r->p.tau, ppair);
+            if (i < j) {
+                K = 0;
+                for (int b = 1; b < N; b++)
+                    for (int a = 0; a < b; a++) {
+                        ea[K] = a; eb[K] = b; val[K] = eri(s, a, i, b, j) - eri(s, a, j, b, i); K++;
+                    }
+                pchb_fill(&r->pchb_ss[i * N + j], K, ea, eb, val, r->p.tau, ppair);
+            }
+        }
+    free(ea); free(eb); free(val);
+}
+
+static void pchb_free(orc_run *r)
+{
+    if (!r->pchb_ab) return;
+    int N = r->pchb_n;
+    for (int k = 0; k < 2 * N * N; k++) {
+        opchb *t = k < N * N ? &r->pchb_ab[k] : &r->pchb_ss[k - N * N];
+        free(t->prob); free(t->alias); free(t->ea); free(t->eb); free(t->val);
+    }
+    free(r->pchb_ab); free(r->pchb_ss);
+}
+
+/* One heat-bath double from D with the words of its draw (w0 has already
+ * chosen a double): ordered electron pair from w1 as in the uniform generator;
+ * bin k = floor(w2 K / 2^64), coin u = ((w2 K mod 2^64) >> 11) 2^-53, entry k
+ * if u < prob[k], else alias[k]; failed if the table is empty (S = 0) or a hole
+ * is occupied.  Returns the class and, through *lam and *hval, |H|/p_gen and the
+ * entry's matrix element. */
+static int pchb_double(const orc_run *r, uint64_t a, uint64_t b, const uint64_t w[4], uint64_t *ta, uint64_t *tb,
+                       double *lam, double *hval)
+{
+    const orc_sys *s = r->s;
+    int N = s->norb, n = s->na + s->nb;
+    *ta = a; *tb = b;
+    if (n < 2) return -1;
+    uint64_t xe = pick(w[1], (uint64_t)n * (uint64_t)(n - 1));
+    int e1 = (int)(xe / (uint64_t)(n - 1)), rr = (int)(xe % (uint64_t)(n - 1));
+    int e2 = rr + (rr >= e1 ? 1 : 0);
+    int s1, s2;
+    int o1 = electron_orb(a, b, s->na, e1, &s1), o2 = electron_orb(a, b, s->na, e2, &s2);
+    const opchb *t;
+    int cls;
+    if (s1 != s2) {
+        int oa = s1 == 0 ? o1 : o2, ob = s1 == 0 ? o2 : o1;
+        t = &r->pchb_ab[oa * N + ob];
+        cls = CLS_DOUBLE_AB;
+    } else {
+        int lo = o1 < o2 ? o1 : o2, hi = o1 < o2 ? o2 : o1;
+        t = &r->pchb_ss[lo * N + hi];
+        cls = s1 ? CLS_DOUBLE_BB : CLS_DOUBLE_AA;
+    }
+    if (!(t->S > 0.0)) return -1;
+    u128 prod = (u128)w[2] * (uint64_t)t->K;
+    int k = (int)(prod >> 64);
+    double u = u53((uint64_t)prod);
+    if (!(u < t->prob[k])) k = t->alias[k];
+    int ha = t->ea[k], hb = t->eb[k];
+    if (s1 != s2) {
+        int oa = s1 == 0 ? o1 : o2, ob = s1 == 0 ? o2 : o1;
+        if (((a >> ha) & 1) || ((b >> hb) & 1)) return -1;
+        *ta = a ^ (1ULL << oa) ^ (1ULL << ha);
+        *tb = b ^ (1ULL << ob) ^ (1ULL << hb);
+    } else {
+        uint64_t *x = s1 ? tb : ta;
+        uint64_t occ = s1 ? b : a;
+        if (((occ >> ha) & 1) || ((occ >> hb) & 1)) return -1;
+        *x ^= (1ULL << o1) | (1ULL << o2) | (1ULL << ha) | (1ULL << hb);
+    }
+    *lam = t->lam;
+    *hval = t->val[k];
+    return cls;
+}
+
+/* heat-bath generation for the tests: class, target, |H|/p_gen */
+int orc_generate_pchb(const orc_run *r, uint64_t a, uint64_t b, const uint64_t w[4], uint64_t *ta, uint64_t *tb,
+                      double *lam)
+{
+    double hv;
+    if (u53(w[0]) < r->p.p_single) {
+        int c = orc_generate(r->s, r->p.p_single, a, b, w, ta, tb);
+        *lam = c >= 0 ? r->lam[c] : 0.0;
+        return c;
+    }
+    return pchb_double(r, a, b, w, ta, tb, lam, &hv);
+}
+
+/* the table of pair (i, j): K, S, lam and (prob, alias, a, b, value) of each entry */
+int orc_pchb_table(const orc_run *r, int same_spin, int i, int j, double *S, double *lam, double *prob, int32_t *alias,
+                   int32_t *ea, int32_t *eb, double *val)
+{
+    int N = r->s->norb;
+    const opchb *t = same_spin ? &r->pchb_ss[i * N + j] : &r->pchb_ab[i * N + j];
+    if (S) *S = t->S;
+    if (lam) *lam = t->lam;
+    for (int k = 0; k < t->K; k++) {
+        if (prob) prob[k] = t->prob[k];
+        if (alias) alias[k] = t->alias[k];
+        if (ea) ea[k] = t->ea[k];
+        if (eb) eb[k] = t->eb[k];
+        if (val) val[k] = t->val[k];
+    }
+    return t->K;
+}
+
 orc_run *orc_create(orc_sys *s, const orc_params *p)
 {
     orc_run *r = calloc(1, sizeof *r);
@@ -607,6 +797,7 @@ orc_run *orc_create(orc_sys *s, const orc_params *p)
     r->L[0].a = s->ref_a; r->L[0].b = s->ref_b; r->L[0].c = p->initial_walkers;
     r->L[0].hd = 0.0; r->L[0].flags = 1;
     r->S = p->initial_shift;
+    if (p->generator == 1 && s->kind == 0) pchb_build(r);
     r->stcap = 1024;
     r->st = malloc(sizeof(orc_stat) * r->stcap);
     return r;
@@ -616,6 +807,7 @@ void orc_destroy(orc_run *r)
 {
     if (!r) return;
     free(r->L); free(r->Da); free(r->Db); free(r->rowptr); free(r->col); free(r->val); free(r->st);
+    pchb_free(r);
     free(r);
 }
 
@@ -708,11 +900,24 @@ static int one_iteration(orc_run *r)
         for (uint64_t k = 0; k < nat; k++) {
             uint64_t w[4], ta, tb;
             draw(P->seed, d->a, d->b, it, k, PURPOSE_SPAWN, w);
-            int cls = orc_generate(s, P->p_single, d->a, d->b, w, &ta, &tb);
-            if (cls < 0) continue;
-            double H = orc_hoff(s, d->a, d->b, ta, tb);
-            if (H == 0.0) continue;
-            double ws = -(H * (r->lam[cls] * cper));
+            double ws;
+            if (r->pchb_ab && !(u53(w[0]) < P->p_single)) {
+                /* heat-bath double: |H| / p_gen = lam for every entry, so the
+                 * weight is -(sign(H) * (lam * C_i / n_att)) */
+                double lam, hv;
+                int cls = pchb_double(r, d->a, d->b, w, &ta, &tb, &lam, &hv);
+                if (cls < 0) continue;
+                double H = orc_hoff(s, d->a, d->b, ta, tb);
+                if (H == 0.0) continue;
+                double wv = lam * cper;
+                ws = H > 0.0 ? -wv : wv;
+            } else {
+                int cls = orc_generate(s, P->p_single, d->a, d->b, w, &ta, &tb);
+                if (cls < 0) continue;
+                double H = orc_hoff(s, d->a, d->b, ta, tb);
+                if (H == 0.0) continue;
+                ws = -(H * (r->lam[cls] * cper));
+            }
             if (fabs(ws) < cmin) {
                 ws = round_stoch(ws, cmin, u53(w[3]));
                 if (ws == 0.0) continue;

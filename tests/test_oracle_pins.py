@@ -279,7 +279,8 @@ def _expected_step(s, dets, c, tau, S, n_a, Hrel):
     return out
 
 
-@pytest.mark.parametrize("case", ["hubbard_plain", "abinitio_plain", "abinitio_initiator", "hubbard_semistoch"])
+@pytest.mark.parametrize("case", ["hubbard_plain", "abinitio_plain", "abinitio_initiator", "hubbard_semistoch",
+                                  "abinitio_pchb"])
 def test_one_step_expectation(case):
     """Averaged over independent seeds, one oracle iteration must reproduce
     (1 - dtau (H - S)) C (plain FCIQMC, Eq. (2)), or its initiator-truncated
@@ -310,7 +311,8 @@ def test_one_step_expectation(case):
     index = {d: i for i, d in enumerate(dets)}
     for seed in range(1, nseeds + 1):
         r = oracle.Run(s, tau=tau, seed=seed, initiator_threshold=n_a, initial_shift=S,
-                       target_walkers=1e12, semistoch_size=40 if semi else 0, semistoch_start=1)
+                       target_walkers=1e12, semistoch_size=40 if semi else 0, semistoch_start=1,
+                       generator=1 if "pchb" in case else 0)
         if semi:
             r.import_state([d[0] for d in dets], [d[1] for d in dets], c, 5, S, vary=1, shift_start=4,
                            cnt=0, nw_last=1 << 70)
@@ -394,3 +396,93 @@ def test_run_is_deterministic_and_keyed():
     r3 = oracle.Run(s, **dict(prm, target_walkers=500, seed=2))
     r3.step(150)
     assert not np.array_equal(r3.export()["c"], e1["c"]) or len(r3.export()["c"]) != len(e1["c"])
+
+
+# ----------------------------------------------------------------- heat-bath doubles (App. A, PCHB)
+def test_pchb_alias_tables_reproduce_heat_bath_weights():
+    """Walker alias tables: the probability of drawing entry k, summed over
+    its own bin and the bins aliased to it, equals |H_ij^ab| / sum |H_ij^ab|."""
+    s = oracle.system_from_workload(workloads.small_abinitio(7, 3, 2, seed=41))
+    r = oracle.Run(s, tau=0.003, generator=1)
+    for same, i, j in [(0, 0, 1), (0, 2, 2), (0, 5, 3), (1, 0, 1), (1, 2, 5)]:
+        t = r.pchb_table(same, i, j)
+        K = t["K"]
+        P = np.zeros(K)
+        for k in range(K):
+            P[k] += t["prob"][k] / K
+            P[t["alias"][k]] += (1.0 - t["prob"][k]) / K
+        target = np.abs(t["val"]) / t["S"]
+        np.testing.assert_allclose(P, target, rtol=1e-12, atol=1e-15)
+        assert t["S"] == math.fsum(np.abs(t["val"]))
+        assert np.all(P[t["val"] == 0.0] < 1e-15)
+
+
+def _word_bin_coin(k, K, frac_lo):
+    """a 64-bit word whose bin floor(w K / 2^64) is k and whose coin
+    (w K mod 2^64) is at least frac_lo (the smallest such word)"""
+    return -((-(k << 64) - frac_lo) // K)
+
+
+def test_pchb_spawn_weight_times_probability_is_tau_H():
+    """Unbiasedness (Sec. II, Eq. (5)): summed over every electron pair, bin
+    and coin outcome of the heat-bath generator, the probability of reaching a
+    target times the spawned weight per walker (|H| / p_gen * dt = lam) equals
+    dt |H_ji|; and the generator, fed words that select a given bin and coin
+    side, returns exactly the entry that the tables say."""
+    tau, ps = 0.003, 0.1
+    s = oracle.system_from_workload(workloads.small_abinitio(6, 2, 2, seed=43))
+    r = oracle.Run(s, tau=tau, generator=1, p_single=ps)
+    det = s.ref
+    N, n = s.norb, s.na + s.nb
+    occ = [(p, 0) for p in range(N) if det[0] >> p & 1] + [(p, 1) for p in range(N) if det[1] >> p & 1]
+    Ptot, lam_of = {}, {}
+    checked = 0
+    for x in range(n * (n - 1)):
+        e1, rr = divmod(x, n - 1)
+        e2 = rr + (rr >= e1)
+        (o1, s1), (o2, s2) = occ[e1], occ[e2]
+        if s1 != s2:
+            i, j = (o1, o2) if s1 == 0 else (o2, o1)
+            t = r.pchb_table(0, i, j)
+        else:
+            i, j = min(o1, o2), max(o1, o2)
+            t = r.pchb_table(1, i, j)
+        K = t["K"]
+        if t["S"] == 0.0:
+            continue
+        pxx = Fraction(1) - Fraction(ps)
+        for k in range(K):
+            for side, pk, entry in ((0, t["prob"][k], k), (1, 1.0 - t["prob"][k], t["alias"][k])):
+                a, b = int(t["a"][entry]), int(t["b"][entry])
+                ta, tb = det
+                if s1 != s2:
+                    if ta >> a & 1 or tb >> b & 1:
+                        continue
+                    ta ^= (1 << i) | (1 << a)
+                    tb ^= (1 << j) | (1 << b)
+                else:
+                    wd = tb if s1 else ta
+                    if wd >> a & 1 or wd >> b & 1:
+                        continue
+                    wd ^= (1 << o1) | (1 << o2) | (1 << a) | (1 << b)
+                    ta, tb = (ta, wd) if s1 else (wd, tb)
+                prob = float(pxx) / (n * (n - 1)) * pk / K
+                Ptot[(ta, tb)] = Ptot.get((ta, tb), 0.0) + prob
+                lam_of[(ta, tb)] = t["lam"]
+                if pk > 0 and checked < 400 and (k * 7 + x) % 5 == 0:
+                    w1 = -((-(x << 64)) // (n * (n - 1)))
+                    w2 = _word_bin_coin(k, K, 0 if side == 0 else (1 << 64) - K)
+                    if w2 < 1 << 64 and ((w2 * K) >> 64) == k and (side == 0 or (w2 * K) % (1 << 64) >= 2 ** 64 - K):
+                        cls, tgt, lam = r.generate_pchb(det, [MASK, w1, w2, 0])
+                        if side == 0 and t["prob"][k] > 2.0 ** -53 or side == 1 and t["prob"][k] < 1.0:
+                            assert tgt == (ta, tb) and lam == t["lam"], (x, k, side)
+                            checked += 1
+    assert checked > 20
+    for tgt, P in Ptot.items():
+        H = s.hoff(det, tgt)
+        assert abs(P * lam_of[tgt] - tau * abs(H)) <= 1e-12 * tau * abs(H), (tgt, P * lam_of[tgt], tau * abs(H))
+    # every double excitation with H != 0 is reached
+    for d in s.determinants():
+        lev = bin(d[0] ^ det[0]).count("1") + bin(d[1] ^ det[1]).count("1")
+        if lev == 4 and s.hoff(det, d) != 0.0:
+            assert d in Ptot, d
