@@ -538,7 +538,10 @@ typedef struct {
  * Walker's alias method.  Reading: the tables carry explicit spins -- one per
  * ordered pair (i alpha, j beta) over (a alpha, b beta), H = (ai|bj), and one
  * per same-spin pair i < j over a < b, H = (ai|bj) - (aj|bi) -- which makes
- * the paper's exchange/no-exchange split of the spatial tables unnecessary. */
+ * the paper's exchange/no-exchange split of the spatial tables unnecessary.
+ * H_ij^ab is the element of a double excitation, so an entry whose hole is
+ * one of the two electrons' own spin orbitals (a = i or b = j for opposite
+ * spins; a or b in {i, j} for equal spins) has weight 0. */
 typedef struct {
     int K;        /* entries */
     double S;     /* exact sum of |H| over the entries, rounded once */
@@ -678,13 +681,20 @@ static void pchb_build(orc_run *r)
         for (int j = 0; j < N; j++) {
             int K = 0;
             for (int a = 0; a < N; a++)
-                for (int b = 0; b < N; b++) { ea[K] = a; eb[K] = b; val[K] = eri(s, a, i, b, j); K++; }
+                for (int b = 0; b < N; b++) {
+                    ea[K] = a; eb[K] = b;
+                    val[K] = (a == i || b == j) ? 0.0 : eri(s, a, i, b, j);
+                    K++;
+                }
             pchb_fill(&r->pchb_ab[i * N + j], K, ea, eb, val, r->p.tau, ppair);
             if (i < j) {
                 K = 0;
                 for (int b = 1; b < N; b++)
                     for (int a = 0; a < b; a++) {
-                        ea[K] = a; eb[K] = b; val[K] = eri(s, a, i, b, j) - eri(s, a, j, b, i); K++;
+                        ea[K] = a; eb[K] = b;
+                        val[K] = (a == i || a == j || b == i || b == j) ? 0.0
+                                                                         : eri(s, a, i, b, j) - eri(s, a, j, b, i);
+                        K++;
                     }
                 pchb_fill(&r->pchb_ss[i * N + j], K, ea, eb, val, r->p.tau, ppair);
             }

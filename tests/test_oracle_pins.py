@@ -415,6 +415,11 @@ def test_pchb_alias_tables_reproduce_heat_bath_weights():
         np.testing.assert_allclose(P, target, rtol=1e-12, atol=1e-15)
         assert t["S"] == math.fsum(np.abs(t["val"]))
         assert np.all(P[t["val"] == 0.0] < 1e-15)
+        # only double excitations carry weight: no hole on an electron's spin orbital
+        a, b = t["a"], t["b"]
+        bad = ((a == i) | (a == j) | (b == i) | (b == j)) if same else ((a == i) | (b == j))
+        assert np.all(t["val"][bad] == 0.0)
+        assert np.any(t["val"][~bad] != 0.0)
 
 
 def _word_bin_coin(k, K, frac_lo):
