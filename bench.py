@@ -35,7 +35,13 @@ EQUIL_ITERS = 300
 E2E_STEPS = 40
 
 
-def workload_params(seed_offset=0, workload="abinitio24"):
+def workload_params(seed_offset=0, workload="abinitio24", generator="uniform"):
+    sysd, prm = _workload_params(seed_offset, workload)
+    prm["generator"] = 1 if generator == "pchb" else 0
+    return sysd, prm
+
+
+def _workload_params(seed_offset=0, workload="abinitio24"):
     if workload == "abinitio50":
         # 50 orbitals, 10+10 electrons, 200 Cholesky vectors: sum_j |H_ref,j| = 39309 Eh,
         # so tau = 0.5 / 39309 rounded down = 1.25e-5 (the prescribed 5e-4 gives 19.7)
@@ -126,7 +132,7 @@ def run_reference(args, rank, world):
     """--impl reference: the oracle on the host cores (rank 0 only)."""
     if rank != 0:
         return None
-    sysd, prm = workload_params()
+    sysd, prm = workload_params(generator=args.generator)
     # bounded sample: the same system and parameters with 2e4 initial walkers,
     # so that one oracle iteration takes a fraction of a second
     prm = dict(prm, initial_walkers=2e4, target_walkers=2e4)
@@ -251,6 +257,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="abinitio24", choices=["abinitio24", "abinitio50", "batch", "serving"])
     ap.add_argument("--equil", type=int, default=EQUIL_ITERS)
+    ap.add_argument("--generator", default="uniform", choices=["uniform", "pchb"],
+                    help="double excitations: uniform, or pre-computed heat-bath alias tables")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--max-iters", type=int, default=20000)
     args = ap.parse_args()
@@ -279,7 +287,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    sysd, prm = workload_params(seed_offset=rank, workload=args.workload)
+    sysd, prm = workload_params(seed_offset=rank, workload=args.workload, generator=args.generator)
     h = fq.fciqmc_create(sysd, prm)
     fq.fciqmc_step(h, args.equil)                        # growth / equilibration, untimed
     fq.fciqmc_step(h, args.warmup)                       # warm-up steps
@@ -394,7 +402,9 @@ def main():
             "config": {"workload": ("abinitio-24orb-6a6b (synthetic: 96 Cholesky vectors, seed 2)"
                                     if args.workload == "abinitio24" else
                                     "abinitio-50orb-10a10b (synthetic: 200 Cholesky vectors, seed 4), D = 1e4"),
-                       "generator": "uniform, p_single 0.1", "initiator_threshold": 3, "tau": prm["tau"],
+                       "generator": ("uniform" if args.generator == "uniform" else
+                                     "pre-computed heat-bath doubles") + ", p_single 0.1",
+                       "initiator_threshold": 3, "tau": prm["tau"],
                        "tau_note": ("prescribed 1e-3 exceeds 1/sum_j|H_ref,j| (2412 Eh): walker number uncontrollable"
                                     if args.workload == "abinitio24" else
                                     "prescribed 5e-4 exceeds 1/sum_j|H_ref,j| (39309 Eh): walker number uncontrollable"),

@@ -90,7 +90,14 @@ typedef struct {
  * max_dets / max_spawns: capacity hints (0 = derived from target_walkers);
  * capacities grow automatically when exceeded, up to max_device_bytes.  stream: a cudaStream_t
  * (NULL = the library creates its own).  alloc/free: optional device
- * allocator (for example a framework's caching allocator); NULL = cudaMalloc. */
+ * allocator (for example a framework's caching allocator); NULL = cudaMalloc.
+ * generator: how double excitations are proposed (App. A).  0: uniformly
+ * (electron pair, then hole pair).  1: pre-computed heat-bath sampling
+ * (App. A, p(ab|ij) proportional to |H_ij^ab|): one Walker alias table per
+ * pair of occupied spin orbitals over hole pairs of matching spin, built on
+ * the device at create time (about 16 (N^4 + (N(N-1)/2)^2) bytes for N
+ * spatial orbitals).  Lattice (HUBBARD) systems ignore it: every hop has the
+ * same |H|.  Singles stay uniform in both. */
 typedef struct {
     double tau;
     double shift_damping;
@@ -111,6 +118,8 @@ typedef struct {
     void *(*alloc)(size_t bytes, void *ctx);
     void (*free)(void *ptr, void *ctx);
     void *alloc_ctx;
+    int32_t generator;
+    int32_t pad0;
 } fciqmc_params;
 
 /* One row per completed iteration.  nw: walker number N_w = 2^-32 sum
@@ -245,6 +254,21 @@ int fciqmc_step_batch(fciqmc_handle **hs, int32_t k, int64_t n_iter);
  * below 1 can the shift hold the walker number. */
 int fciqmc_ref_offdiag_sum(fciqmc_handle *h, double *out);
 double fciqmc_tau(fciqmc_handle *h);
+
+/* Copies one pre-computed heat-bath table (generator 1; App. A) to the host:
+ * same_spin = 0: the table of (i alpha, j beta), entry k = a N + b over
+ * (a alpha, b beta); same_spin = 1: the table of i < j (either spin), entry
+ * k = b (b - 1) / 2 + a over a < b.  *S = sum_k |H_ij^ab| (exact sum rounded
+ * once), *lam = tau S / p_pair with p_pair = (1 - p_single) 2 / (n (n - 1)),
+ * i.e. |H| / p_gen of every entry.  For each of the first min(K, cap) entries:
+ * threshold[k] = ceil(prob_k 2^53), the alias coin keeping entry k when the
+ * top 53 bits of the low word of w K are below it; holes[k] = own hole pair
+ * | alias's hole pair << 16, a hole pair being a | b << 8.  Returns K (>= 0),
+ * or a negative status: FCIQMC_ERR_INVALID_ARG when the run has no tables or
+ * (i, j) is out of range, FCIQMC_ERR_CUDA on a copy failure.  Output pointers
+ * may be NULL. */
+int64_t fciqmc_pchb_table(fciqmc_handle *h, int32_t same_spin, int32_t i, int32_t j, double *S, double *lam,
+                          uint64_t *threshold, uint32_t *holes, int64_t cap);
 
 /* The same sum as fciqmc_ref_offdiag_sum, for callers that cannot allocate
  * device memory: frameworks whose memory pool owns every device byte, jobs

@@ -17,7 +17,7 @@ from . import build as _build
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
-if not os.path.exists(_build.LIB):
+if not os.path.exists(_build.LIB) or not _build.up_to_date():
     if os.environ.get("FCIQMC_GB300_AUTOBUILD", "1") == "1":
         _build.build()
     else:
@@ -63,7 +63,8 @@ class fciqmc_params(C.Structure):
                 ("initiator_threshold", C.c_double), ("c_min", C.c_double), ("p_single", C.c_double),
                 ("shift_interval", C.c_int64), ("seed", C.c_uint64), ("semistoch_size", C.c_int64),
                 ("semistoch_start", C.c_int64), ("max_dets", C.c_int64), ("max_spawns", C.c_int64),
-                ("max_device_bytes", C.c_int64), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p)]
+                ("max_device_bytes", C.c_int64), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
+                ("generator", C.c_int32), ("pad0", C.c_int32)]
 
 
 class fciqmc_iter_stats(C.Structure):
@@ -116,6 +117,8 @@ _SIGS = {
     "fciqmc_layout": (C.c_int, [_H, C.POINTER(C.c_int64)]),
     "fciqmc_ref_offdiag_sum": (C.c_int, [_H, _dp]),
     "fciqmc_tau": (C.c_double, [_H]),
+    "fciqmc_pchb_table": (C.c_int64, [_H, C.c_int32, C.c_int32, C.c_int32, _dp, _dp, _u64p,
+                                      C.POINTER(C.c_uint32), C.c_int64]),
     "fciqmc_autotune": (C.c_int, [C.POINTER(_H), C.c_int32, C.c_int64, C.POINTER(C.c_int32)]),
     "fciqmc_read_fcidump": (C.c_int, [C.c_char_p, C.POINTER(fciqmc_system)]),
     "fciqmc_free_system": (None, [C.POINTER(fciqmc_system)]),
@@ -205,7 +208,7 @@ def _system_struct(system):
 
 DEFAULTS = dict(tau=0.01, shift_damping=0.1, target_walkers=1e4, initial_walkers=10.0, initial_shift=0.0,
                 initiator_threshold=0.0, c_min=1.0, p_single=0.1, shift_interval=10, seed=1, semistoch_size=0,
-                semistoch_start=100, max_dets=0, max_spawns=0, max_device_bytes=0)
+                semistoch_start=100, max_dets=0, max_spawns=0, max_device_bytes=0, generator=0)
 
 
 def _params_struct(params):
@@ -367,6 +370,21 @@ def fciqmc_ref_offdiag_sum_noalloc(norb, n_alpha, n_beta, d_h1, d_eri, ref_alpha
 
 def fciqmc_tau(handle):
     return _lib.fciqmc_tau(handle.h)
+
+
+def fciqmc_pchb_table(handle, same_spin, i, j):
+    """One heat-bath table: dict(S, lam, threshold (uint64[K]), holes (uint32[K]))."""
+    K = _lib.fciqmc_pchb_table(handle.h, int(same_spin), int(i), int(j), None, None, None, None, 0)
+    if K < 0:
+        _check(int(K), handle.h)
+    S, lam = C.c_double(), C.c_double()
+    thr = np.zeros(max(K, 1), np.uint64)
+    holes = np.zeros(max(K, 1), np.uint32)
+    r = _lib.fciqmc_pchb_table(handle.h, int(same_spin), int(i), int(j), C.byref(S), C.byref(lam),
+                               thr.ctypes.data_as(_u64p), holes.ctypes.data_as(C.POINTER(C.c_uint32)), K)
+    if r < 0:
+        _check(int(r), handle.h)
+    return dict(S=S.value, lam=lam.value, threshold=thr[:K], holes=holes[:K])
 
 
 class Server:

@@ -708,6 +708,33 @@ int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_han
         I.cz = P.shift_damping / ((double)P.shift_interval * h->p.tau);
     }
 
+    // pre-computed heat-bath tables (generator 1, ab initio systems with a double)
+    if (P.generator == 1 && h->kind == FCIQMC_ABINITIO && n >= 2) {
+        // the exact table sums add up to N^2 terms of |(ai|bj) - (aj|bi)| < 2^(msb_max + 2)
+        int kb = 0;
+        while ((1LL << kb) < (long long)N * N) kb++;
+        if (any && msb_max + 2 + F + kb + 2 > 125)
+            return bail(FCIQMC_ERR_UNSUPPORTED, "integral dynamic range too wide for the exact heat-bath table sums");
+        const u64 nab = (u64)N * N, kss = (u64)N * (N - 1) / 2;
+        const u64 ss_base = nab * nab;
+        const u64 nent = ss_base + kss * kss;
+        double2 *meta = (double2 *)dev_alloc(h, (size_t)(nab + kss) * sizeof(double2));
+        ulonglong2 *ent = (ulonglong2 *)dev_alloc(h, (size_t)nent * sizeof(ulonglong2));
+        if (!meta || !ent) return bail(FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (heat-bath tables)");
+        // probability of one unordered electron pair: (1 - p_single) 2 / (n (n - 1))
+        const double ppair = ((1.0 - P.p_single) * 2.0) / ((double)n * (double)(n - 1));
+        if (cudaMemcpyAsync(h->dinst, &I, sizeof(DevInst), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+            launch_pchb_build(h->dinst, N, ppair, meta, ent, ss_base, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+            return bail(FCIQMC_ERR_CUDA, "heat-bath table construction failed");
+        I.pchb = 1;
+        I.pchb_meta = meta;
+        I.pchb_ent = ent;
+        I.pchb_ss_base = ss_base;
+    } else if (P.generator != 0 && P.generator != 1) {
+        return bail(FCIQMC_ERR_INVALID_ARG, "generator must be 0 (uniform) or 1 (pre-computed heat-bath)");
+    }
+
     // bucket layout: average occupancy well below the per-bucket capacity
     // start at the expected size (capped: buffers grow on demand)
     double dets_hint = P.max_dets > 0 ? (double)P.max_dets : std::min(std::max(4096.0, P.target_walkers), 8388608.0);
@@ -1304,6 +1331,43 @@ extern "C" int fciqmc_ref_offdiag_sum(fciqmc_handle *h, double *out)
 }
 
 extern "C" double fciqmc_tau(fciqmc_handle *h) { return h ? h->p.tau : NAN; }
+
+extern "C" int64_t fciqmc_pchb_table(fciqmc_handle *h, int32_t same_spin, int32_t i, int32_t j, double *S, double *lam,
+                                     uint64_t *threshold, uint32_t *holes, int64_t cap)
+{
+    if (!h || !h->hi.pchb) return FCIQMC_ERR_INVALID_ARG;
+    const int N = h->norb;
+    if (i < 0 || j < 0 || i >= N || j >= N || (same_spin && i >= j) || cap < 0) return FCIQMC_ERR_INVALID_ARG;
+    int64_t t, K;
+    u64 off;
+    if (!same_spin) {
+        t = (int64_t)i * N + j;
+        K = (int64_t)N * N;
+        off = (u64)t * (u64)K;
+    } else {
+        const int64_t p = (int64_t)j * (j - 1) / 2 + i;
+        t = (int64_t)N * N + p;
+        K = (int64_t)N * (N - 1) / 2;
+        off = h->hi.pchb_ss_base + (u64)p * (u64)K;
+    }
+    double2 mt;
+    if (cudaMemcpy(&mt, h->hi.pchb_meta + t, sizeof(mt), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(h, FCIQMC_ERR_CUDA, "heat-bath table copy failed");
+    if (lam) *lam = mt.x;
+    if (S) *S = mt.y;
+    const int64_t m = std::min(K, cap);
+    if (m > 0 && (threshold || holes)) {
+        std::vector<ulonglong2> e((size_t)m);
+        if (cudaMemcpy(e.data(), h->hi.pchb_ent + off, (size_t)m * sizeof(ulonglong2), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+            return fail(h, FCIQMC_ERR_CUDA, "heat-bath table copy failed");
+        for (int64_t k = 0; k < m; k++) {
+            if (threshold) threshold[k] = e[k].x;
+            if (holes) holes[k] = (uint32_t)e[k].y;
+        }
+    }
+    return K;
+}
 
 // ------------------------------------------------------------------ serving
 #include <chrono>

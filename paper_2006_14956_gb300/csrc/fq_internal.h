@@ -137,6 +137,17 @@ struct DevInst {
     double *dc_cur;         // C_D after the last completed iteration
     const u64 *dhash_keys;  // open-addressing set of D keys (a, b interleaved), size dhash_cap
     int dhash_bits;
+    // pre-computed heat-bath doubles (generator 1): opposite-spin table of
+    // (i alpha, j beta) at meta[i N + j], entries [(i N + j) N^2, +N^2), entry
+    // k = a N + b; same-spin table of i < j at meta[N^2 + p], p = j(j-1)/2 + i,
+    // entries [ss_base + p K_ss, +K_ss), K_ss = N(N-1)/2, entry k = b(b-1)/2 + a
+    // (a < b).  meta = (|H|/p_gen of every entry, sum of |H|); entry =
+    // (alias threshold on 53-bit words, own hole pair | alias's hole pair << 16),
+    // hole pair = a | b << 8.
+    int pchb;
+    const double2 *pchb_meta;
+    const ulonglong2 *pchb_ent;
+    u64 pchb_ss_base;
 };
 
 // host-side launchers (kernels.cu)
@@ -157,6 +168,8 @@ void launch_build_hd(const DevInst *dinst, int nd, const ulonglong2 *dkey, long 
                      int *col, double *val, int pass, cudaStream_t s);
 void launch_mark_d(const DevInst *dinst, int parity, int nb, cudaStream_t s);
 
+cudaError_t launch_pchb_build(const DevInst *dinst, int norb, double ppair, double2 *meta, ulonglong2 *ent,
+                              u64 ss_base, cudaStream_t s);
 void set_launch_geometry(int spawn_bps, int heavy_bps, int anni_bps);
 void get_launch_geometry(int *spawn_bps, int *heavy_bps, int *anni_bps);
 cudaError_t ref_abs_sum(const DevInst *dinst, double *dpartial, double *out, cudaStream_t s);

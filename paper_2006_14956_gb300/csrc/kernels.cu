@@ -61,12 +61,9 @@ __device__ __forceinline__ bool in_D(const DevInst &I, u64 a, u64 b)
 // doubles.  The words each attempt consumes and every decision are the same
 // as if the attempts were processed one by one.
 
-// append a surviving spawn (weight, Eq. (3) rounding, D -> D filter) to its bucket
-__device__ __forceinline__ void emit_spawn(const DevInst &I, u64 ta, u64 tb, double H, int cls, double cper,
-                                           unsigned flags, u64 w3)
+// append a surviving spawn (Eq. (3) rounding of the weight ws, D -> D filter) to its bucket
+__device__ __forceinline__ void emit_weight(const DevInst &I, u64 ta, u64 tb, double ws, unsigned flags, u64 w3)
 {
-    if (is_zero(H)) return;
-    double ws = -(H * (I.lam[cls] * cper));
     if (abs_lt(ws, I.cmin)) {
         ws = round_stoch(ws, I.cmin, I.cmin_log2, I.cmin_pow2, w3);
         if (is_zero(ws)) return;
@@ -91,6 +88,14 @@ __device__ __forceinline__ void emit_spawn(const DevInst &I, u64 ta, u64 tb, dou
             I.sw[o] = ws;
         }
     }
+}
+
+// weight -H tau / p_gen(c) C_i / n_att of a uniformly generated excitation of class c
+__device__ __forceinline__ void emit_spawn(const DevInst &I, u64 ta, u64 tb, double H, int cls, double cper,
+                                           unsigned flags, u64 w3)
+{
+    if (is_zero(H)) return;
+    emit_weight(I, ta, tb, -(H * (I.lam[cls] * cper)), flags, w3);
 }
 
 // lattice hop (Hubbard): electron w1, neighbour slot w2
@@ -168,6 +173,74 @@ __device__ void spawn_double(const DevInst &I, u64 pa, u64 pb, double cper, unsi
     par ^= flip_parity(xa, xb, N, Q0);
     const double v = (cls == CLS_DOUBLE_AB) ? eri4(I, oa, oi, ob, oj) : eri4(I, oa, oi, ob, oj) - eri4(I, oa, oj, ob, oi);
     emit_spawn(I, ta, tb, par ? -v : v, cls, cper, flags, w3);
+}
+
+// heat-bath double (App. A, pre-computed heat-bath sampling): ordered electron
+// pair w1 as in the uniform generator, then the alias table of that pair of
+// spin orbitals: bin k = floor(w2 K / 2^64), coin = the low 64 bits of w2 K
+// (top 53 bits); an occupied hole or an empty table fails the attempt.  With
+// p_gen = p_pair |H| / S the weight is -sign(H) lambda_ij C_i / n_att,
+// lambda_ij = tau S / p_pair (stored per table).
+__device__ void spawn_double_pchb(const DevInst &I, u64 pa, u64 pb, double cper, unsigned flags, u64 w1, u64 w2,
+                                  u64 w3)
+{
+    const int N = I.norb, n = I.n, na = I.na;
+    const unsigned xe = (unsigned)pick(w1, (u64)(n * (n - 1)));
+    const int e1 = (int)(xe / (unsigned)(n - 1)), r = (int)(xe % (unsigned)(n - 1));
+    const int e2 = r + (r >= e1 ? 1 : 0);
+    const int s1 = e1 >= na, s2 = e2 >= na;
+    const int o1 = nth_set(s1 ? pb : pa, s1 ? e1 - na : e1);
+    const int o2 = nth_set(s2 ? pb : pa, s2 ? e2 - na : e2);
+    int oi, oj, t, K;
+    u64 off;
+    if (s1 != s2) {
+        oi = s1 ? o2 : o1;  // alpha electron
+        oj = s1 ? o1 : o2;  // beta electron
+        t = oi * N + oj;
+        K = N * N;
+        off = (u64)t * (u64)K;
+    } else {
+        oi = min(o1, o2);
+        oj = max(o1, o2);
+        const int p = oj * (oj - 1) / 2 + oi;
+        t = N * N + p;
+        K = N * (N - 1) / 2;
+        off = I.pchb_ss_base + (u64)p * (u64)K;
+    }
+    const double2 mt = __ldg(I.pchb_meta + t);
+    if (!(dbits(mt.y) != 0)) return;  // S = 0: nothing to propose
+    const u64 k = __umul64hi(w2, (u64)K), low = w2 * (u64)K;
+    const ulonglong2 e = __ldg(I.pchb_ent + off + k);
+    const unsigned hp = ((low >> 11) < e.x) ? (unsigned)(e.y & 0xffffu) : (unsigned)((e.y >> 16) & 0xffffu);
+    const int oa = (int)(hp & 0xffu), ob = (int)(hp >> 8);
+    int P0, P1, Q0, Q1, cls;
+    u64 ta, tb;
+    if (s1 != s2) {
+        if (((pa >> oa) & 1ULL) || ((pb >> ob) & 1ULL)) return;
+        P0 = oi; P1 = N + oj; Q0 = oa; Q1 = N + ob;
+        ta = pa ^ (1ULL << oi) ^ (1ULL << oa);
+        tb = pb ^ (1ULL << oj) ^ (1ULL << ob);
+        cls = CLS_DOUBLE_AB;
+    } else {
+        u64 x = s1 ? pb : pa;
+        if (((x >> oa) & 1ULL) || ((x >> ob) & 1ULL)) return;
+        const int sh = s1 ? N : 0;
+        P0 = sh + oi; P1 = sh + oj; Q0 = sh + oa; Q1 = sh + ob;
+        x ^= (1ULL << oi) | (1ULL << oj) | (1ULL << oa) | (1ULL << ob);
+        ta = s1 ? pa : x;
+        tb = s1 ? x : pb;
+        cls = s1 ? CLS_DOUBLE_BB : CLS_DOUBLE_AA;
+    }
+    u64 xa = pa, xb = pb;
+    int par = flip_parity(xa, xb, N, P0);
+    par ^= flip_parity(xa, xb, N, P1);
+    par ^= flip_parity(xa, xb, N, Q1);
+    par ^= flip_parity(xa, xb, N, Q0);
+    const double v = (cls == CLS_DOUBLE_AB) ? eri4(I, oa, oi, ob, oj) : eri4(I, oa, oi, ob, oj) - eri4(I, oa, oj, ob, oi);
+    const double H = par ? -v : v;
+    if (is_zero(H)) return;
+    const double wv = mt.x * cper;
+    emit_weight(I, ta, tb, (dbits(H) & SIGN64) ? wv : -wv, flags, w3);
 }
 
 // class of one attempt from its first two words, or -1 for a failed attempt
@@ -251,7 +324,8 @@ __device__ void run_attempts(const DevInst &I, K1Smem &S, long long it, unsigned
         for (int q = t; q < nd; q += K1_THREADS) {
             const SpawnRec r = S.rec[q];
             const ulonglong2 kk = map.key(r.det);
-            spawn_double(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3);
+            if (I.pchb) spawn_double_pchb(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3);
+            else spawn_double(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3);
         }
         for (int q = t; q < ns; q += K1_THREADS) {
             const SpawnRec r = S.rec[CHUNK - 1 - q];
