@@ -46,7 +46,7 @@ class Stat(C.Structure):
     _fields_ = [("iter", C.c_int64), ("nw", C.c_double), ("S", C.c_double), ("e_num", C.c_double),
                 ("e_den", C.c_double), ("ndet", C.c_int64), ("attempts", C.c_int64),
                 ("spawns", C.c_int64), ("rejected", C.c_int64), ("annihilated", C.c_double),
-                ("vary", C.c_int)]
+                ("vary", C.c_int), ("t_num", C.c_double), ("t_den", C.c_double)]
 
 
 class Params(C.Structure):
@@ -54,13 +54,14 @@ class Params(C.Structure):
                 ("initial_walkers", C.c_double), ("initial_shift", C.c_double),
                 ("initiator_threshold", C.c_double), ("c_min", C.c_double), ("p_single", C.c_double),
                 ("shift_interval", C.c_int64), ("seed", C.c_uint64),
-                ("semistoch_size", C.c_int64), ("semistoch_start", C.c_int64), ("generator", C.c_int64)]
+                ("semistoch_size", C.c_int64), ("semistoch_start", C.c_int64), ("generator", C.c_int64),
+                ("trial_size", C.c_int64), ("trial_start", C.c_int64)]
 
 
 DEFAULT_PARAMS = dict(tau=0.01, shift_damping=0.1, target_walkers=1e4, initial_walkers=10.0,
                       initial_shift=0.0, initiator_threshold=0.0, c_min=1.0, p_single=0.1,
                       shift_interval=10, seed=1, semistoch_size=0, semistoch_start=100,
-                      generator=0)
+                      generator=0, trial_size=0, trial_start=100)
 
 CLASSES = ("single_a", "single_b", "double_ab", "double_aa", "double_bb", "hop")
 
@@ -105,6 +106,8 @@ def lib():
                 "orc_generate_pchb": (I32, [P, U64, U64, up, up, up, dp]),
                 "orc_pchb_table": (I32, [P, I32, I32, I32, dp, dp, dp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                          C.POINTER(C.c_int32), dp]),
+                "orc_trial_info": (I64, [P, C.POINTER(C.c_int64), dp, up, up, dp]),
+                "orc_jacobi_lowest": (I32, [I32, dp, dp, dp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -336,6 +339,18 @@ class Run:
                                  eb.ctypes.data_as(C.POINTER(C.c_int32)), val.ctypes.data_as(C.POINTER(C.c_double)))
         return dict(K=K, S=S.value, lam=lam.value, prob=prob[:K], alias=alias[:K], a=ea[:K], b=eb[:K], val=val[:K])
 
+    def trial_info(self):
+        """Trial space of the E_Trial estimator: dict(nt, n_w (|T u C|), ET (E^T - E_ref), a, b, cT)."""
+        nw = C.c_int64()
+        ET = C.c_double()
+        nt = lib().orc_trial_info(self.h, C.byref(nw), C.byref(ET), None, None, None)
+        a = np.zeros(max(nt, 1), np.uint64)
+        b = np.zeros(max(nt, 1), np.uint64)
+        cT = np.zeros(max(nt, 1))
+        lib().orc_trial_info(self.h, None, None, a.ctypes.data_as(C.POINTER(C.c_uint64)),
+                             b.ctypes.data_as(C.POINTER(C.c_uint64)), cT.ctypes.data_as(C.POINTER(C.c_double)))
+        return dict(nt=int(nt), n_w=int(nw.value), ET=ET.value, a=a[:nt], b=b[:nt], cT=cT[:nt])
+
     def proj_energy(self):
         """(E_num, E_den) of the current list, Eq. (9)."""
         num = C.c_double()
@@ -355,6 +370,17 @@ class Run:
             lib().orc_stats(self.h, 0, n, arr)
         cols = {f: np.array([getattr(arr[i], f) for i in range(n)]) for f, _ in Stat._fields_}
         return cols
+
+
+def jacobi_lowest(A):
+    """Lowest eigenpair of a symmetric matrix by the oracle's cyclic Jacobi method."""
+    A = np.ascontiguousarray(A, np.float64).copy()
+    n = A.shape[0]
+    E = C.c_double()
+    v = np.zeros(n)
+    lib().orc_jacobi_lowest(n, A.ctypes.data_as(C.POINTER(C.c_double)), C.byref(E),
+                            v.ctypes.data_as(C.POINTER(C.c_double)))
+    return E.value, v
 
 
 # ---------------------------------------------------------------- statistics

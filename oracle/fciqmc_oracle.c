@@ -519,6 +519,7 @@ typedef struct {
     uint64_t seed;
     int64_t semistoch_size, semistoch_start;
     int64_t generator; /* 0: uniform doubles, 1: pre-computed heat-bath doubles (App. A) */
+    int64_t trial_size, trial_start; /* trial space T of the E_Trial estimator (Sec. IV) */
 } orc_params;
 
 typedef struct { uint64_t a, b; double c, hd; int flags; } odet; /* flags: 1 ref, 2 in D */
@@ -530,6 +531,7 @@ typedef struct {
     int64_t ndet, attempts, spawns, rejected;
     double annihilated;
     int vary;
+    double t_num, t_den; /* E_Trial: <Psi^T|H - E_ref|Psi>, <Psi^T|Psi> after the iteration */
 } orc_stat;
 
 /* Pre-computed heat-bath tables (App. A, "Pre-computed heat-bath sampling",
@@ -574,6 +576,12 @@ typedef struct {
     orc_stat *st;
     int64_t nst, stcap;
     int err;
+    /* trial space T (sorted keys), its H^T ground state (cT, E^T relative to
+     * E_ref), and W_j = sum_{i in T} <D_j|H - E_ref|D_i> cT_i over T and the
+     * space C connected to it (sorted keys) */
+    int64_t nt, nwt;
+    uint64_t *Ta, *Tb, *Wa, *Wb;
+    double *cT, *W, ET;
 } orc_run;
 
 static int cmp_key(uint64_t a1, uint64_t b1, uint64_t a2, uint64_t b2)
@@ -817,6 +825,7 @@ void orc_destroy(orc_run *r)
 {
     if (!r) return;
     free(r->L); free(r->Da); free(r->Db); free(r->rowptr); free(r->col); free(r->val); free(r->st);
+    free(r->Ta); free(r->Tb); free(r->cT); free(r->Wa); free(r->Wb); free(r->W);
     pchb_free(r);
     free(r);
 }
@@ -877,6 +886,200 @@ int64_t orc_semistoch_info(const orc_run *r, int64_t *nnz)
     return r->nd;
 }
 
+/* ---------------------------------------------------------------- trial wave function
+ * E_Trial (Sec. IV): T = the trial_size largest |C| (ties: ascending key) at
+ * iteration shift_start + trial_start; Psi^T = the lowest eigenvector of H^T
+ * (H projected into T); E_Trial = <Psi^T|H|Psi> / <Psi^T|Psi>, accumulated as
+ * the numerator and denominator of every iteration.  W_j = <Psi^T|H - E_ref|D_j>
+ * for every D_j in T and in the space C of determinants connected to T. */
+
+/* lowest eigenpair of the symmetric n x n matrix A (row-major, destroyed) by
+ * cyclic Jacobi rotations (Jacobi 1846; rotation angle from
+ * theta = (A_qq - A_pp) / (2 A_pq), t = sign(theta) / (|theta| + sqrt(theta^2 + 1))),
+ * sweeping until the off-diagonal part is below 1e-15 of the matrix norm */
+static void jacobi_lowest(int n, double *A, double *E, double *v)
+{
+    double *V = calloc((size_t)n * n, sizeof(double));
+    for (int i = 0; i < n; i++) V[(size_t)i * n + i] = 1.0;
+    double norm = 0.0;
+    for (size_t k = 0; k < (size_t)n * n; k++) norm += A[k] * A[k];
+    for (int sweep = 0; sweep < 100; sweep++) {
+        double off = 0.0;
+        for (int p = 0; p < n; p++)
+            for (int q = p + 1; q < n; q++) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+        if (!(off > 1e-30 * norm)) break;
+        for (int p = 0; p < n; p++)
+            for (int q = p + 1; q < n; q++) {
+                double apq = A[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                double theta = (A[(size_t)q * n + q] - A[(size_t)p * n + p]) / (2.0 * apq);
+                double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                /* A <- J^T A J with J the rotation in the (p, q) plane */
+                for (int k = 0; k < n; k++) {
+                    double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = c * akp - sn * akq;
+                    A[(size_t)k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; k++) {
+                    double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = c * apk - sn * aqk;
+                    A[(size_t)q * n + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < n; k++) {
+                    double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+                    V[(size_t)k * n + p] = c * vkp - sn * vkq;
+                    V[(size_t)k * n + q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    int lo = 0;
+    for (int i = 1; i < n; i++) if (A[(size_t)i * n + i] < A[(size_t)lo * n + lo]) lo = i;
+    *E = A[(size_t)lo * n + lo];
+    for (int i = 0; i < n; i++) v[i] = V[(size_t)i * n + lo];
+    free(V);
+}
+
+int orc_jacobi_lowest(int n, double *A, double *E, double *v) { jacobi_lowest(n, A, E, v); return 0; }
+
+typedef struct { uint64_t a, b; double v; } ocontrib;
+static int cmp_contrib(const void *x, const void *y)
+{
+    const ocontrib *p = x, *q = y;
+    return cmp_key(p->a, p->b, q->a, q->b);
+}
+
+/* every determinant connected to (a, b) by one application of H: singles of
+ * either spin, opposite-spin and same-spin doubles (target list, no values) */
+static int64_t connections(const orc_sys *s, uint64_t a, uint64_t b, uint64_t *ta, uint64_t *tb)
+{
+    const int N = s->norb;
+    const uint64_t full = N >= 64 ? ~0ULL : ((1ULL << N) - 1);
+    int64_t k = 0;
+    for (int sp = 0; sp < 2; sp++) {
+        uint64_t w = sp ? b : a, v = ~w & full;
+        for (int i = 0; i < N; i++) {
+            if (!(w >> i & 1)) continue;
+            for (int x = 0; x < N; x++) {
+                if (!(v >> x & 1)) continue;
+                uint64_t y = w ^ (1ULL << i) ^ (1ULL << x);
+                ta[k] = sp ? a : y; tb[k] = sp ? y : b; k++;
+            }
+        }
+    }
+    uint64_t va = ~a & full, vb = ~b & full;
+    for (int i = 0; i < N; i++) {
+        if (!(a >> i & 1)) continue;
+        for (int j = 0; j < N; j++) {
+            if (!(b >> j & 1)) continue;
+            for (int x = 0; x < N; x++) {
+                if (!(va >> x & 1)) continue;
+                for (int y = 0; y < N; y++) {
+                    if (!(vb >> y & 1)) continue;
+                    ta[k] = a ^ (1ULL << i) ^ (1ULL << x); tb[k] = b ^ (1ULL << j) ^ (1ULL << y); k++;
+                }
+            }
+        }
+    }
+    for (int sp = 0; sp < 2; sp++) {
+        uint64_t w = sp ? b : a, v = ~w & full;
+        for (int i = 0; i < N; i++)
+            for (int j = i + 1; j < N; j++) {
+                if (!(w >> i & 1) || !(w >> j & 1)) continue;
+                for (int x = 0; x < N; x++)
+                    for (int y = x + 1; y < N; y++) {
+                        if (!(v >> x & 1) || !(v >> y & 1)) continue;
+                        uint64_t z = w ^ (1ULL << i) ^ (1ULL << j) ^ (1ULL << x) ^ (1ULL << y);
+                        ta[k] = sp ? a : z; tb[k] = sp ? z : b; k++;
+                    }
+            }
+    }
+    return k;
+}
+
+static void build_T(orc_run *r)
+{
+    const orc_sys *s = r->s;
+    int64_t n = r->n, nt = r->p.trial_size < n ? r->p.trial_size : n;
+    ocand *cd = malloc(sizeof(ocand) * (n ? n : 1));
+    for (int64_t i = 0; i < n; i++) { cd[i].m = fabs(r->L[i].c); cd[i].a = r->L[i].a; cd[i].b = r->L[i].b; }
+    qsort(cd, n, sizeof(ocand), cmp_cand);
+    odet *tmp = malloc(sizeof(odet) * (nt ? nt : 1));
+    for (int64_t i = 0; i < nt; i++) { tmp[i].a = cd[i].a; tmp[i].b = cd[i].b; }
+    qsort(tmp, nt, sizeof(odet), cmp_odet);
+    r->nt = nt;
+    r->Ta = malloc(sizeof(uint64_t) * (nt ? nt : 1));
+    r->Tb = malloc(sizeof(uint64_t) * (nt ? nt : 1));
+    for (int64_t i = 0; i < nt; i++) { r->Ta[i] = tmp[i].a; r->Tb[i] = tmp[i].b; }
+    free(cd); free(tmp);
+    /* H^T relative to E_ref, its lowest eigenvector */
+    double *A = malloc(sizeof(double) * (size_t)(nt ? nt * nt : 1));
+    for (int64_t i = 0; i < nt; i++)
+        for (int64_t j = 0; j < nt; j++)
+            A[i * nt + j] = i == j ? orc_hdiag_rel(s, r->Ta[i], r->Tb[i])
+                                   : orc_hoff(s, r->Ta[j], r->Tb[j], r->Ta[i], r->Tb[i]);
+    r->cT = malloc(sizeof(double) * (nt ? nt : 1));
+    jacobi_lowest((int)nt, A, &r->ET, r->cT);
+    free(A);
+    /* W over T and C: contributions <D_j|H - E_ref|D_i> cT_i, summed exactly per j */
+    int64_t cap = 1024, nc = 0;
+    ocontrib *ct = malloc(sizeof(ocontrib) * cap);
+    const int N = s->norb;
+    int64_t maxc = (int64_t)N * N * 2 + (int64_t)N * N * N * N * 2 + 16;
+    uint64_t *ta = malloc(sizeof(uint64_t) * maxc), *tb = malloc(sizeof(uint64_t) * maxc);
+    for (int64_t i = 0; i < nt; i++) {
+        int64_t k = connections(s, r->Ta[i], r->Tb[i], ta, tb);
+        if (nc + k + 1 > cap) { while (nc + k + 1 > cap) cap *= 2; ct = realloc(ct, sizeof(ocontrib) * cap); }
+        ct[nc].a = r->Ta[i]; ct[nc].b = r->Tb[i]; ct[nc].v = orc_hdiag_rel(s, r->Ta[i], r->Tb[i]) * r->cT[i]; nc++;
+        for (int64_t q = 0; q < k; q++) {
+            double h = orc_hoff(s, r->Ta[i], r->Tb[i], ta[q], tb[q]);
+            if (h == 0.0) continue;
+            ct[nc].a = ta[q]; ct[nc].b = tb[q]; ct[nc].v = h * r->cT[i]; nc++;
+        }
+    }
+    free(ta); free(tb);
+    qsort(ct, nc, sizeof(ocontrib), cmp_contrib);
+    r->Wa = malloc(sizeof(uint64_t) * (nc ? nc : 1));
+    r->Wb = malloc(sizeof(uint64_t) * (nc ? nc : 1));
+    r->W = malloc(sizeof(double) * (nc ? nc : 1));
+    int64_t nw = 0;
+    for (int64_t q = 0; q < nc;) {
+        xacc x;
+        xacc_zero(&x);
+        int64_t q1 = q;
+        while (q1 < nc && ct[q1].a == ct[q].a && ct[q1].b == ct[q].b) { xacc_add(&x, ct[q1].v, 0); q1++; }
+        r->Wa[nw] = ct[q].a; r->Wb[nw] = ct[q].b; r->W[nw] = xacc_round(&x); nw++;
+        q = q1;
+    }
+    r->nwt = nw;
+    free(ct);
+}
+
+static int64_t find_key(const uint64_t *ka, const uint64_t *kb, int64_t n, uint64_t a, uint64_t b)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) / 2;
+        int c = cmp_key(ka[mid], kb[mid], a, b);
+        if (c == 0) return mid;
+        if (c < 0) lo = mid + 1; else hi = mid;
+    }
+    return -1;
+}
+
+/* trial space: N_T, |T u C|, E^T (relative to E_ref); cT and keys when the arrays are given */
+int64_t orc_trial_info(const orc_run *r, int64_t *nw, double *ET, uint64_t *ta, uint64_t *tb, double *cT)
+{
+    if (nw) *nw = r->nwt;
+    if (ET) *ET = r->ET;
+    for (int64_t i = 0; i < r->nt; i++) {
+        if (ta) ta[i] = r->Ta[i];
+        if (tb) tb[i] = r->Tb[i];
+        if (cT) cT[i] = r->cT[i];
+    }
+    return r->nt;
+}
+
 static double round_stoch(double v, double cmin, double u)
 {
     /* Eq. (3): keep |v| >= C_min; else sign(v) C_min with prob |v|/C_min, else 0 */
@@ -894,6 +1097,8 @@ static int one_iteration(orc_run *r)
 
     if (P->semistoch_size > 0 && r->nd == 0 && r->vary && it == r->shift_start + P->semistoch_start)
         build_D(r);
+    if (P->trial_size > 0 && r->nt == 0 && r->vary && it == r->shift_start + P->trial_start)
+        build_T(r);
 
     /* (a) spawning from the start-of-iteration amplitudes */
     int64_t ns = 0, scap = 1024, attempts = 0;
@@ -1031,6 +1236,16 @@ static int one_iteration(orc_run *r)
     }
     double nw = (double)W * 0x1p-32;
     if (!(nw == nw)) return 3;
+    /* E_Trial numerator and denominator, in ascending key order */
+    double t_num = 0.0, t_den = 0.0;
+    if (r->nt > 0)
+        for (int64_t i = 0; i < no; i++) {
+            if (out[i].c == 0.0) continue;
+            int64_t q = find_key(r->Wa, r->Wb, r->nwt, out[i].a, out[i].b);
+            if (q >= 0) t_num = t_num + r->W[q] * out[i].c;
+            q = find_key(r->Ta, r->Tb, r->nt, out[i].a, out[i].b);
+            if (q >= 0) t_den = t_den + r->cT[q] * out[i].c;
+        }
 
     /* shift (reading R7) */
     if (!r->vary) {
@@ -1048,6 +1263,7 @@ static int one_iteration(orc_run *r)
     t->iter = it; t->nw = nw; t->S = r->S; t->e_num = e_num; t->e_den = e_den;
     t->ndet = no; t->attempts = attempts; t->spawns = ns; t->rejected = rejected;
     t->annihilated = (double)ann * 0x1p-32; t->vary = r->vary;
+    t->t_num = t_num; t->t_den = t_den;
     r->iter = it + 1;
     return 0;
 }

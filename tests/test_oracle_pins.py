@@ -491,3 +491,82 @@ def test_pchb_spawn_weight_times_probability_is_tau_H():
         lev = bin(d[0] ^ det[0]).count("1") + bin(d[1] ^ det[1]).count("1")
         if lev == 4 and s.hoff(det, d) != 0.0:
             assert d in Ptot, d
+
+
+# ---------------------------------------------------------------- trial wave function (Sec. IV)
+def test_jacobi_lowest_matches_eigh():
+    """The oracle's cyclic Jacobi against LAPACK (numpy.linalg.eigh) on random
+    symmetric matrices, one with a degenerate lowest pair."""
+    rng = np.random.default_rng(11)
+    for n in (1, 2, 5, 17, 40):
+        A = rng.normal(size=(n, n))
+        A = A + A.T
+        E, v = oracle.jacobi_lowest(A)
+        w, V = np.linalg.eigh(A)
+        assert abs(E - w[0]) <= 1e-12 * np.abs(w).max()
+        assert abs(abs(v @ V[:, 0]) - 1.0) < 1e-10
+        np.testing.assert_allclose(A @ v, E * v, atol=1e-11 * np.abs(w).max())
+    D = np.diag([-3.0, -3.0, 1.0, 2.0])
+    Q, _ = np.linalg.qr(rng.normal(size=(4, 4)))
+    E, v = oracle.jacobi_lowest(Q @ D @ Q.T)
+    assert abs(E + 3.0) < 1e-12 and abs(np.linalg.norm(v) - 1.0) < 1e-12
+
+
+def _trial_run(sysd, **kw):
+    s = oracle.system_from_workload(sysd)
+    p = dict(tau=0.01, target_walkers=1000, initial_walkers=1000.0, shift_damping=0.3, shift_interval=5,
+             initiator_threshold=0.0, seed=3, trial_start=20)
+    p.update(kw)
+    return s, oracle.Run(s, **p)
+
+
+def test_trial_numerator_is_psiT_H_psi_by_brute_force():
+    """After the trial space is built, every iteration's numerator equals
+    sum_j (H - E_ref)_jT cT C_j and the denominator sum_T cT C, computed with
+    the dense FCI matrix, so no connected determinant is missed; cT is the
+    lowest eigenvector of H^T."""
+    sysd = workloads.small_abinitio(6, 2, 2, n_chol=2, seed=5)
+    s, r = _trial_run(sysd, trial_size=12)
+    r.step(120)
+    ti = r.trial_info()
+    assert ti["nt"] == 12 and ti["n_w"] > 12
+    dets, H = s.hamiltonian()
+    idx = {d: k for k, d in enumerate(dets)}
+    T = [idx[(int(a), int(b))] for a, b in zip(ti["a"], ti["b"])]
+    HT = H[np.ix_(T, T)]
+    w, V = np.linalg.eigh(HT)
+    assert abs(ti["ET"] - w[0]) < 1e-12 * max(1.0, abs(w[0]))
+    np.testing.assert_allclose(HT @ ti["cT"], ti["ET"] * ti["cT"], atol=1e-11)
+    for extra in range(3):
+        st = r.export()
+        c = np.zeros(len(dets))
+        for a, b, x in zip(st["alpha"], st["beta"], st["c"]):
+            c[idx[(int(a), int(b))]] = x
+        num = float(ti["cT"] @ (H[T, :] @ c))
+        den = float(ti["cT"] @ c[T])
+        last = {k: v[-1] for k, v in r.stats().items()}
+        assert abs(last["t_num"] - num) <= 1e-11 * max(1.0, np.abs(H[T, :]).sum() * np.abs(c).max())
+        assert abs(last["t_den"] - den) <= 1e-12 * max(1.0, np.abs(c).sum())
+        r.step(1)
+
+
+def test_trial_space_equal_to_fci_space_gives_exact_energy():
+    """With T = the whole FCI space, Psi^T is the exact ground state, so
+    <Psi^T|H|Psi> / <Psi^T|Psi> = E_0 for whatever Psi the walkers hold."""
+    sysd = workloads.small_abinitio(6, 2, 2, n_chol=2, seed=5)
+    s, r = _trial_run(sysd, trial_size=10 ** 6)
+    e0, _, dets = s.exact_ground_state()
+    # every determinant occupied when T is chosen: a state with all of them is
+    # imported at the iteration that builds T
+    a = [d[0] for d in dets]
+    b = [d[1] for d in dets]
+    r.import_state(a, b, np.full(len(dets), 3.0), 100, 0.0, vary=1, shift_start=80, cnt=0,
+                   nw_last=int(3 * len(dets)) << 32)
+    r.step(60)
+    ti = r.trial_info()
+    assert ti["nt"] == len(dets)
+    assert abs(ti["ET"] - e0) < 1e-11
+    st = r.stats()
+    sel = st["t_den"] != 0.0
+    assert sel.sum() > 30
+    np.testing.assert_allclose(st["t_num"][sel] / st["t_den"][sel], e0, rtol=0, atol=1e-9)
