@@ -9,6 +9,7 @@ about 1e6 walkers.  Prints one JSON line.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 """
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -381,7 +382,7 @@ def main():
     st2 = fq.fciqmc_iter_stats_get(h2)
     e2e_att = float(np.sum(st2["attempts"][-E2E_STEPS:]))
     h2d = sysd["h1"].nbytes + sysd["eri"].nbytes + host_state["alpha"].nbytes * 2 + host_state["c"].nbytes
-    d2h = sum(v.nbytes for v in out_state.values()) + E2E_STEPS * 88
+    d2h = sum(v.nbytes for v in out_state.values()) + E2E_STEPS * ctypes.sizeof(fq.fciqmc_iter_stats)
     del h2
 
     # ---- CPU baseline: the oracle on the same equilibrated state, bounded sample
@@ -420,7 +421,7 @@ def main():
                     "d2h_bytes_per_step": d2h / E2E_STEPS,
                     "job": "create + import %s checkpoint + %d steps + export + energy" %
                            ("2e5-determinant sample" if big else "1e6-walker", E2E_STEPS)},
-            "gpu_launches": args.steps * (6 if fq.fciqmc_layout(h) and prm.get("semistoch_size", 0) else 5),
+            "gpu_launches": args.steps * (7 if prm.get("semistoch_size", 0) else 6),
             "wall_s_timed": wall,
             "clocks": clk.summary(),
             "energy": {"e_proj_mean": en["e_proj_mean"], "e_proj_sigma": en["e_proj_sigma"], "shift": en["shift"]},

@@ -91,6 +91,11 @@ typedef struct {
  * capacities grow automatically when exceeded, up to max_device_bytes.  stream: a cudaStream_t
  * (NULL = the library creates its own).  alloc/free: optional device
  * allocator (for example a framework's caching allocator); NULL = cudaMalloc.
+ * trial_size, trial_start: the trial-wave-function energy estimator (Sec. IV):
+ * trial_start iterations after the shift starts to vary, T = the trial_size
+ * (at most 1024) largest |C| (ties: ascending key), Psi^T = the lowest
+ * eigenvector of H projected into T (Jacobi rotations on the device), and
+ * every later iteration accumulates <Psi^T|H - E_ref|Psi> and <Psi^T|Psi>.
  * generator: how double excitations are proposed (App. A).  0: uniformly
  * (electron pair, then hole pair).  1: pre-computed heat-bath sampling
  * (App. A, p(ab|ij) proportional to |H_ij^ab|): one Walker alias table per
@@ -120,6 +125,8 @@ typedef struct {
     void *alloc_ctx;
     int32_t generator;
     int32_t pad0;
+    int64_t trial_size;  /* N_T of the trial-wave-function estimator (0 = off) */
+    int64_t trial_start; /* iterations after the shift starts to vary at which T is chosen */
 } fciqmc_params;
 
 /* One row per completed iteration.  nw: walker number N_w = 2^-32 sum
@@ -141,6 +148,8 @@ typedef struct {
     double annihilated;
     int32_t vary;
     int32_t pad0;
+    double trial_num; /* <Psi^T|H - E_ref|Psi> after the iteration (0 before T exists) */
+    double trial_den; /* <Psi^T|Psi> */
 } fciqmc_iter_stats;
 
 /* Summary returned by fciqmc_energy.  Energies are absolute (E_ref added).
@@ -166,6 +175,14 @@ typedef struct {
     double annihilated_total;
     int32_t vary;
     int32_t pad0;
+    /* trial-wave-function estimator: E_Trial = E_ref + mean(trial_num) /
+     * mean(trial_den) over iterations from max(equil_start, T built) on, with
+     * its blocking error; e_trial_T = E^T (absolute), the lowest eigenvalue of
+     * H^T; trial_samples = 0 when the estimator is off or T is not built yet */
+    double e_trial_mean;
+    double e_trial_sigma;
+    double e_trial_T;
+    int64_t trial_samples;
 } fciqmc_stats;
 
 typedef struct fciqmc_handle fciqmc_handle;
@@ -254,6 +271,15 @@ int fciqmc_step_batch(fciqmc_handle **hs, int32_t k, int64_t n_iter);
  * below 1 can the shift hold the walker number. */
 int fciqmc_ref_offdiag_sum(fciqmc_handle *h, double *out);
 double fciqmc_tau(fciqmc_handle *h);
+
+/* The trial space of the E_Trial estimator once it is built (trial_size > 0):
+ * returns N_T (0 before), *n_w = the number of determinants with a stored
+ * W_j = <Psi^T|H - E_ref|D_j> (T and the space connected to it), *ET = E^T -
+ * E_ref; the first min(N_T, cap) keys of T in ascending order and their
+ * components of Psi^T (unit norm, sign arbitrary) when the arrays are given.
+ * Negative status on error. */
+int64_t fciqmc_trial_info(fciqmc_handle *h, int64_t *n_w, double *ET, uint64_t *t_alpha, uint64_t *t_beta,
+                          double *cT, int64_t cap);
 
 /* Copies one pre-computed heat-bath table (generator 1; App. A) to the host:
  * same_spin = 0: the table of (i alpha, j beta), entry k = a N + b over
@@ -344,9 +370,10 @@ int fciqmc_autotune(fciqmc_handle **hs, int32_t k, int64_t n_iter, int32_t out[3
 /* Device timing of the kernels of the last fciqmc_step call (milliseconds per
  * iteration, averaged), measured with CUDA events on the handle's stream:
  * out[0] spawn, out[1] heavy-determinant spawn, out[2] annihilation,
- * out[3] finalize, out[4] semi-stochastic.  Enabled by fciqmc_set_profiling. */
+ * out[3] finalize, out[4] semi-stochastic, out[5] H_jj of the determinants
+ * created in the iteration.  Enabled by fciqmc_set_profiling. */
 int fciqmc_set_profiling(fciqmc_handle *h, int32_t on);
-int fciqmc_kernel_times(fciqmc_handle *h, double out[5]);
+int fciqmc_kernel_times(fciqmc_handle *h, double out[6]);
 
 /* Internal layout figures used to compute algorithmic bytes and to size
  * buffers: out[0] buckets, out[1] main capacity per bucket, out[2] spawn

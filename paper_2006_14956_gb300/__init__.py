@@ -64,13 +64,14 @@ class fciqmc_params(C.Structure):
                 ("shift_interval", C.c_int64), ("seed", C.c_uint64), ("semistoch_size", C.c_int64),
                 ("semistoch_start", C.c_int64), ("max_dets", C.c_int64), ("max_spawns", C.c_int64),
                 ("max_device_bytes", C.c_int64), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
-                ("generator", C.c_int32), ("pad0", C.c_int32)]
+                ("generator", C.c_int32), ("pad0", C.c_int32), ("trial_size", C.c_int64), ("trial_start", C.c_int64)]
 
 
 class fciqmc_iter_stats(C.Structure):
     _fields_ = [("iteration", C.c_int64), ("nw", C.c_double), ("shift", C.c_double), ("e_num", C.c_double),
                 ("e_den", C.c_double), ("ndet", C.c_int64), ("attempts", C.c_int64), ("spawns", C.c_int64),
-                ("rejected", C.c_int64), ("annihilated", C.c_double), ("vary", C.c_int32), ("pad0", C.c_int32)]
+                ("rejected", C.c_int64), ("annihilated", C.c_double), ("vary", C.c_int32), ("pad0", C.c_int32),
+                ("trial_num", C.c_double), ("trial_den", C.c_double)]
 
 
 class fciqmc_stats(C.Structure):
@@ -79,7 +80,8 @@ class fciqmc_stats(C.Structure):
                 ("e_proj_sigma", C.c_double), ("shift_mean", C.c_double), ("shift_sigma", C.c_double),
                 ("equil_start", C.c_int64), ("n_samples", C.c_int64), ("attempts_total", C.c_int64),
                 ("spawns_total", C.c_int64), ("rejected_total", C.c_int64), ("annihilated_total", C.c_double),
-                ("vary", C.c_int32), ("pad0", C.c_int32)]
+                ("vary", C.c_int32), ("pad0", C.c_int32), ("e_trial_mean", C.c_double),
+                ("e_trial_sigma", C.c_double), ("e_trial_T", C.c_double), ("trial_samples", C.c_int64)]
 
 
 class fciqmc_request_status(C.Structure):
@@ -117,6 +119,7 @@ _SIGS = {
     "fciqmc_layout": (C.c_int, [_H, C.POINTER(C.c_int64)]),
     "fciqmc_ref_offdiag_sum": (C.c_int, [_H, _dp]),
     "fciqmc_tau": (C.c_double, [_H]),
+    "fciqmc_trial_info": (C.c_int64, [_H, C.POINTER(C.c_int64), _dp, _u64p, _u64p, _dp, C.c_int64]),
     "fciqmc_pchb_table": (C.c_int64, [_H, C.c_int32, C.c_int32, C.c_int32, _dp, _dp, _u64p,
                                       C.POINTER(C.c_uint32), C.c_int64]),
     "fciqmc_autotune": (C.c_int, [C.POINTER(_H), C.c_int32, C.c_int64, C.POINTER(C.c_int32)]),
@@ -208,7 +211,7 @@ def _system_struct(system):
 
 DEFAULTS = dict(tau=0.01, shift_damping=0.1, target_walkers=1e4, initial_walkers=10.0, initial_shift=0.0,
                 initiator_threshold=0.0, c_min=1.0, p_single=0.1, shift_interval=10, seed=1, semistoch_size=0,
-                semistoch_start=100, max_dets=0, max_spawns=0, max_device_bytes=0, generator=0)
+                semistoch_start=100, max_dets=0, max_spawns=0, max_device_bytes=0, generator=0, trial_size=0, trial_start=100)
 
 
 def _params_struct(params):
@@ -345,9 +348,10 @@ def fciqmc_set_profiling(handle, on=True):
 
 
 def fciqmc_kernel_times(handle):
-    out = (C.c_double * 5)()
+    out = (C.c_double * 6)()
     _check(_lib.fciqmc_kernel_times(handle.h, out), handle.h)
-    return dict(spawn=out[0], spawn_heavy=out[1], annihilate=out[2], finalize=out[3], semistoch=out[4])
+    return dict(spawn=out[0], spawn_heavy=out[1], annihilate=out[2], finalize=out[3], semistoch=out[4],
+                new_diag=out[5])
 
 
 def fciqmc_layout(handle):
@@ -370,6 +374,23 @@ def fciqmc_ref_offdiag_sum_noalloc(norb, n_alpha, n_beta, d_h1, d_eri, ref_alpha
 
 def fciqmc_tau(handle):
     return _lib.fciqmc_tau(handle.h)
+
+
+def fciqmc_trial_info(handle):
+    """Trial space of the E_Trial estimator: dict(nt, n_w, ET (E^T - E_ref), alpha, beta, cT)."""
+    nw = C.c_int64()
+    ET = C.c_double()
+    nt = _lib.fciqmc_trial_info(handle.h, C.byref(nw), C.byref(ET), None, None, None, 0)
+    if nt < 0:
+        _check(int(nt), handle.h)
+    a = np.zeros(max(nt, 1), np.uint64)
+    b = np.zeros(max(nt, 1), np.uint64)
+    cT = np.zeros(max(nt, 1))
+    r = _lib.fciqmc_trial_info(handle.h, None, None, a.ctypes.data_as(_u64p), b.ctypes.data_as(_u64p),
+                               cT.ctypes.data_as(_dp), nt)
+    if r < 0:
+        _check(int(r), handle.h)
+    return dict(nt=int(nt), n_w=int(nw.value), ET=ET.value, alpha=a[:nt], beta=b[:nt], cT=cT[:nt])
 
 
 def fciqmc_pchb_table(handle, same_spin, i, j):

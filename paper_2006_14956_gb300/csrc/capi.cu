@@ -53,7 +53,7 @@ struct fciqmc_handle {
     IterState *dstate = nullptr;
     cudaGraphExec_t graph = nullptr;
     bool profiling = false;
-    double ktime[5] = {0, 0, 0, 0, 0};
+    double ktime[6] = {0, 0, 0, 0, 0, 0};  // spawn, heavy, annihilate, finalize, semistoch, new-determinant H_jj
     // layout
     int bb = 0;
     int heavy_cap = 0;
@@ -66,6 +66,11 @@ struct fciqmc_handle {
     int nd = 0;
     long long nnz = 0;
     double ref_sum = 0.0;
+    // trial-wave-function estimator
+    long long trial_nt = 0, trial_nw = 0;
+    double trial_ET = 0.0;
+    const ulonglong2 *trial_key = nullptr;
+    const double *trial_cT = nullptr;
     // asynchronous stepping
     bool pending = false;
     long long async_base = 0, async_target = 0;
@@ -209,7 +214,8 @@ static int alloc_layout(fciqmc_handle *h, DevInst &I, int bb)
     I.scnt_n = (int *)dev_alloc(h, nbk * sizeof(int));
     I.part = (Partial *)dev_alloc(h, nbk * sizeof(Partial));
     I.big_list = (int *)dev_alloc(h, nbk * sizeof(int));
-    if (!I.skey || !I.sw || !I.scnt_i || !I.scnt_n || !I.part || !I.big_list) return FCIQMC_ERR_OUT_OF_MEMORY;
+    I.newdet = (unsigned *)dev_alloc(h, nm * sizeof(unsigned));
+    if (!I.skey || !I.sw || !I.scnt_i || !I.scnt_n || !I.part || !I.big_list || !I.newdet) return FCIQMC_ERR_OUT_OF_MEMORY;
     cudaMemsetAsync(I.scnt_i, 0, nbk * sizeof(int), h->stream);
     cudaMemsetAsync(I.scnt_n, 0, nbk * sizeof(int), h->stream);
     cudaMemsetAsync(I.part, 0, nbk * sizeof(Partial), h->stream);
@@ -225,8 +231,9 @@ static void free_layout(fciqmc_handle *h, DevInst &I)
         I.key[k] = nullptr; I.c[k] = nullptr; I.hd[k] = nullptr; I.fl[k] = nullptr; I.cnt[k] = nullptr;
     }
     dev_free(h, I.skey); dev_free(h, I.sw); dev_free(h, I.scnt_i); dev_free(h, I.scnt_n); dev_free(h, I.part);
-    dev_free(h, I.big_list);
+    dev_free(h, I.big_list); dev_free(h, I.newdet);
     I.skey = nullptr; I.sw = nullptr; I.scnt_i = nullptr; I.scnt_n = nullptr; I.part = nullptr; I.big_list = nullptr;
+    I.newdet = nullptr;
 }
 
 static int upload_inst(fciqmc_handle *h)
@@ -252,8 +259,10 @@ static int enqueue_iteration(fciqmc_handle *h, cudaEvent_t *ev)
     if (e != cudaSuccess) return fail(h, FCIQMC_ERR_CUDA, std::string("annihilation launch: ") + cudaGetErrorString(e));
     launch_annihilate_big(h->dinst, 1, h->stream);
     if (ev) cudaEventRecord(ev[4], h->stream);
-    launch_finalize(h->dinst, 1, h->stream);
+    launch_new_diag(h->dinst, 1, h->stream);
     if (ev) cudaEventRecord(ev[5], h->stream);
+    launch_finalize(h->dinst, 1, h->stream);
+    if (ev) cudaEventRecord(ev[6], h->stream);
     return FCIQMC_OK;
 }
 
@@ -360,6 +369,7 @@ static int reset_after_error(fciqmc_handle *h)
     h->hst.need_spawn = 0;
     h->hst.need_main = 0;
     h->hst.n_spawn_over = 0;
+    h->hst.new_n = 0;
     return write_state(h);
 }
 
@@ -392,19 +402,22 @@ static int pull_history(fciqmc_handle *h, long long from, long long to)
 // D = the N_D determinants of largest |C| (ties: ascending key), found by a
 // 16-bit-digit radix selection over the bit patterns of |C| on the device;
 // H^D in CSR built on the device; the main list flags D and pins it.
-static int build_semistochastic(fciqmc_handle *h)
+// the `count` determinants of largest |C| (ties: ascending key), returned
+// in ascending key order: a radix selection on the bit patterns of |C|
+// (16-bit digit histograms on the device), then the ties at the threshold
+static int select_top(fciqmc_handle *h, long long count, std::vector<ulonglong2> &sel, long long *nsel)
 {
-    DevInst &I = h->hi;
     const int par = h->hst.parity, nbk = 1 << h->bb;
     std::vector<int> cnt(nbk);
-    CUDA_TRY(h, cudaMemcpy(cnt.data(), I.cnt[par], nbk * sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_TRY(h, cudaMemcpy(cnt.data(), h->hi.cnt[par], nbk * sizeof(int), cudaMemcpyDeviceToHost));
     long long ndet = 0;
     for (int c : cnt) ndet += c;
-    const long long nd = std::min<long long>(h->p.semistoch_size, ndet);
-    h->hst.semi_built = 1;
+    const long long nd = std::min<long long>(count, ndet);
+    *nsel = nd;
+    sel.clear();
     if (nd <= 0) return FCIQMC_OK;
     unsigned *dhist = (unsigned *)dev_alloc(h, 65536 * sizeof(unsigned));
-    if (!dhist) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (semi-stochastic selection)");
+    if (!dhist) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (selection)");
     std::vector<unsigned> hist(65536);
     u64 prefix = 0;
     long long need = nd, ties = 0;
@@ -423,12 +436,12 @@ static int build_semistochastic(fciqmc_handle *h)
         ties = hist[d];
         prefix = (prefix << 16) | (u64)d;
     }
-    const u64 thr = prefix;  // bit pattern of the N_D-th largest |C|
+    const u64 thr = prefix;  // bit pattern of the count-th largest |C|
     const int cap = (int)(nd - need + ties);
     ulonglong2 *ckeys = (ulonglong2 *)dev_alloc(h, (size_t)cap * sizeof(ulonglong2));
     u64 *cmags = (u64 *)dev_alloc(h, (size_t)cap * sizeof(u64));
     int *dn = (int *)dev_alloc(h, sizeof(int));
-    if (!ckeys || !cmags || !dn) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (semi-stochastic selection)");
+    if (!ckeys || !cmags || !dn) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (selection)");
     CUDA_TRY(h, cudaMemsetAsync(dn, 0, sizeof(int), h->stream));
     launch_abs_collect(h->dinst, par, nbk, thr, ckeys, cmags, dn, cap, h->stream);
     std::vector<ulonglong2> keys(cap);
@@ -438,14 +451,52 @@ static int build_semistochastic(fciqmc_handle *h)
     CUDA_TRY(h, cudaMemcpyAsync(keys.data(), ckeys, (size_t)cap * sizeof(ulonglong2), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(mags.data(), cmags, (size_t)cap * sizeof(u64), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    if (ncol != cap) return fail(h, FCIQMC_ERR_CUDA, "semi-stochastic selection count mismatch");
-    std::vector<ulonglong2> sel, tie;
+    if (ncol != cap) return fail(h, FCIQMC_ERR_CUDA, "selection count mismatch");
+    std::vector<ulonglong2> tie;
     for (int i = 0; i < cap; i++) (mags[i] > thr ? sel : tie).push_back(keys[i]);
     auto kless = [](const ulonglong2 &x, const ulonglong2 &y) { return x.x < y.x || (x.x == y.x && x.y < y.y); };
     std::sort(tie.begin(), tie.end(), kless);
     for (long long i = 0; i < need; i++) sel.push_back(tie[(size_t)i]);
     std::sort(sel.begin(), sel.end(), kless);
     dev_free(h, dhist); dev_free(h, ckeys); dev_free(h, cmags); dev_free(h, dn);
+    return FCIQMC_OK;
+}
+
+// H^S (diagonal relative to E_ref) of the sorted keys dkey in CSR on the device
+static int build_hsub(fciqmc_handle *h, const ulonglong2 *dkey, long long nd, long long **rowptr, int **dcol,
+                      double **dval, long long *nnz_out)
+{
+    long long *rowcnt = (long long *)dev_alloc(h, (size_t)nd * sizeof(long long));
+    *rowptr = (long long *)dev_alloc(h, (size_t)(nd + 1) * sizeof(long long));
+    if (!rowcnt || !*rowptr) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (sparse H)");
+    launch_build_hd(h->dinst, (int)nd, dkey, rowcnt, nullptr, nullptr, nullptr, 0, h->stream);
+    std::vector<long long> rc((size_t)nd), rp((size_t)nd + 1, 0);
+    CUDA_TRY(h, cudaMemcpyAsync(rc.data(), rowcnt, (size_t)nd * sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    for (long long r = 0; r < nd; r++) rp[r + 1] = rp[r] + rc[r];
+    const long long nnz = rp[nd];
+    *dcol = (int *)dev_alloc(h, (size_t)std::max(1LL, nnz) * sizeof(int));
+    *dval = (double *)dev_alloc(h, (size_t)std::max(1LL, nnz) * sizeof(double));
+    if (!*dcol || !*dval) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (sparse H)");
+    CUDA_TRY(h, cudaMemcpy(*rowptr, rp.data(), (size_t)(nd + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+    launch_build_hd(h->dinst, (int)nd, dkey, rowcnt, *rowptr, *dcol, *dval, 1, h->stream);
+    CUDA_TRY(h, cudaGetLastError());
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    dev_free(h, rowcnt);
+    *nnz_out = nnz;
+    return FCIQMC_OK;
+}
+
+static int build_semistochastic(fciqmc_handle *h)
+{
+    DevInst &I = h->hi;
+    const int par = h->hst.parity, nbk = 1 << h->bb;
+    h->hst.semi_built = 1;
+    std::vector<ulonglong2> sel;
+    long long nd = 0;
+    int rcs = select_top(h, h->p.semistoch_size, sel, &nd);
+    if (rcs) return rcs;
+    if (nd <= 0) return FCIQMC_OK;
     // open-addressing set of D keys
     int hb = 1;
     while ((1LL << hb) < 2 * nd) hb++;
@@ -458,25 +509,16 @@ static int build_semistochastic(fciqmc_handle *h)
     }
     ulonglong2 *dkey = (ulonglong2 *)dev_alloc(h, (size_t)nd * sizeof(ulonglong2));
     u64 *dtab = (u64 *)dev_alloc(h, tabk.size() * sizeof(u64));
-    long long *rowcnt = (long long *)dev_alloc(h, (size_t)nd * sizeof(long long));
-    long long *rowptr = (long long *)dev_alloc(h, (size_t)(nd + 1) * sizeof(long long));
     double *dcn = (double *)dev_alloc(h, (size_t)nd * sizeof(double));
     double *dcc = (double *)dev_alloc(h, (size_t)nd * sizeof(double));
-    if (!dkey || !dtab || !rowcnt || !rowptr || !dcn || !dcc) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (D)");
+    if (!dkey || !dtab || !dcn || !dcc) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (D)");
     CUDA_TRY(h, cudaMemcpy(dkey, sel.data(), (size_t)nd * sizeof(ulonglong2), cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemcpy(dtab, tabk.data(), tabk.size() * sizeof(u64), cudaMemcpyHostToDevice));
-    launch_build_hd(h->dinst, (int)nd, dkey, rowcnt, nullptr, nullptr, nullptr, 0, h->stream);
-    std::vector<long long> rc((size_t)nd), rp((size_t)nd + 1, 0);
-    CUDA_TRY(h, cudaMemcpyAsync(rc.data(), rowcnt, (size_t)nd * sizeof(long long), cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    for (long long r = 0; r < nd; r++) rp[r + 1] = rp[r] + rc[r];
-    const long long nnz = rp[nd];
-    int *dcol = (int *)dev_alloc(h, (size_t)nnz * sizeof(int));
-    double *dval = (double *)dev_alloc(h, (size_t)nnz * sizeof(double));
-    if (!dcol || !dval) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (H^D)");
-    CUDA_TRY(h, cudaMemcpy(rowptr, rp.data(), (size_t)(nd + 1) * sizeof(long long), cudaMemcpyHostToDevice));
-    launch_build_hd(h->dinst, (int)nd, dkey, rowcnt, rowptr, dcol, dval, 1, h->stream);
-    dev_free(h, rowcnt);
+    long long *rowptr = nullptr, nnz = 0;
+    int *dcol = nullptr;
+    double *dval = nullptr;
+    rcs = build_hsub(h, dkey, nd, &rowptr, &dcol, &dval, &nnz);
+    if (rcs) return rcs;
     I.nd = (int)nd; I.dkey = dkey; I.drow = rowptr; I.dcol = dcol; I.dval = dval; I.dc_new = dcn; I.dc_cur = dcc;
     I.dhash_keys = dtab; I.dhash_bits = hb;
     int rc2 = upload_inst(h);
@@ -486,6 +528,76 @@ static int build_semistochastic(fciqmc_handle *h)
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     h->nd = (int)nd;
     h->nnz = nnz;
+    return capture_graph(h);
+}
+
+// trial-wave-function estimator (Sec. IV): T, H^T, its lowest eigenvector,
+// and the table of W_j over T and the space connected to it
+static int build_trial(fciqmc_handle *h)
+{
+    DevInst &I = h->hi;
+    h->hst.trial_built = 1;
+    std::vector<ulonglong2> sel;
+    long long nt = 0;
+    int rc = select_top(h, h->p.trial_size, sel, &nt);
+    if (rc) return rc;
+    if (nt <= 0) return FCIQMC_OK;
+    ulonglong2 *tkey = (ulonglong2 *)dev_alloc(h, (size_t)nt * sizeof(ulonglong2));
+    double *cT = (double *)dev_alloc(h, (size_t)nt * sizeof(double));
+    double *hdiag = (double *)dev_alloc(h, (size_t)nt * sizeof(double));
+    double *dE = (double *)dev_alloc(h, sizeof(double));
+    int *dsw = (int *)dev_alloc(h, 2 * sizeof(int));
+    if (!tkey || !cT || !hdiag || !dE || !dsw) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (trial space)");
+    CUDA_TRY(h, cudaMemcpy(tkey, sel.data(), (size_t)nt * sizeof(ulonglong2), cudaMemcpyHostToDevice));
+    long long *rowptr = nullptr, nnz = 0;
+    int *col = nullptr;
+    double *val = nullptr;
+    rc = build_hsub(h, tkey, nt, &rowptr, &col, &val, &nnz);
+    if (rc) return rc;
+    // dense H^T (order padded to even), lowest eigenpair
+    const int n2 = (int)(nt + (nt & 1));
+    double *A = (double *)dev_alloc(h, (size_t)n2 * n2 * sizeof(double));
+    double *V = (double *)dev_alloc(h, (size_t)n2 * n2 * sizeof(double));
+    if (!A || !V) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (trial eigenproblem)");
+    CUDA_TRY(h, cudaMemsetAsync(A, 0, (size_t)n2 * n2 * sizeof(double), h->stream));
+    CUDA_TRY(h, launch_trial_dense(rowptr, col, val, (int)nt, n2, A, hdiag, h->stream));
+    CUDA_TRY(h, launch_jacobi_lowest(A, V, (int)nt, n2, dE, cT, dsw, h->stream));
+    int sweeps = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&h->trial_ET, dE, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(&sweeps, dsw, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (sweeps >= 60) return fail(h, FCIQMC_ERR_NUMERIC, "trial eigenproblem did not converge");
+    dev_free(h, A); dev_free(h, V); dev_free(h, rowptr); dev_free(h, col); dev_free(h, val);
+    // W table: at most nt (connections + 1) determinants, at most half full
+    const long long per = connections_per_det(h->na, h->nb, h->norb - h->na, h->norb - h->nb);
+    int bits = 4;
+    while ((1LL << bits) < 2 * nt * (per + 1) && bits < 40) bits++;
+    const size_t slots = (size_t)1 << bits;
+    unsigned *state = (unsigned *)dev_alloc(h, slots * sizeof(unsigned));
+    TrialEnt *tab = (TrialEnt *)dev_alloc(h, slots * sizeof(TrialEnt));
+    unsigned long long *dcount = (unsigned long long *)dev_alloc(h, sizeof(unsigned long long));
+    int *derr = (int *)dev_alloc(h, sizeof(int));
+    if (!state || !tab || !dcount || !derr) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (trial table)");
+    CUDA_TRY(h, cudaMemsetAsync(state, 0, slots * sizeof(unsigned), h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(tab, 0, slots * sizeof(TrialEnt), h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(derr, 0, sizeof(int), h->stream));
+    CUDA_TRY(h, launch_trial_w(h->dinst, tkey, cT, hdiag, (int)nt, per, state, tab, bits, dcount, derr, h->stream));
+    unsigned long long cnt = 0;
+    int terr = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&cnt, dcount, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(&terr, derr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (terr) return fail(h, FCIQMC_ERR_TIMEOUT, "trial table construction failed (wait limit or table full)");
+    h->trial_nt = nt;
+    h->trial_nw = (long long)cnt;
+    h->trial_key = tkey;
+    h->trial_cT = cT;
+    I.trial_bits = bits;
+    I.trial_state = state;
+    I.trial_tab = tab;
+    int rc2 = upload_inst(h);
+    if (rc2) return rc2;
     return capture_graph(h);
 }
 
@@ -522,6 +634,8 @@ int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_han
         !(P.target_walkers > 0.0) || !std::isfinite(P.initial_shift))
         return bail(FCIQMC_ERR_INVALID_ARG, "invalid parameters (tau, c_min, initial_walkers, shift_interval, p_single, "
                                             "initiator_threshold, shift_damping, target_walkers must be positive/finite)");
+    if (P.trial_size < 0 || P.trial_size > 1024 || (P.trial_size > 0 && P.trial_start < 1))
+        return bail(FCIQMC_ERR_INVALID_ARG, "trial_size must be in [0, 1024] and trial_start >= 1");
     h->kind = sys->kind;
     h->na = sys->n_alpha;
     h->nb = sys->n_beta;
@@ -623,15 +737,27 @@ int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_han
     }
 
     // fixed-point tables for the exact diagonal sums
-    std::vector<ulonglong2> hfx(N), Jfx((size_t)N * N), Kfx((size_t)N * N);
+    std::vector<ulonglong2> hfx(N), Jfx((size_t)N * N), JKfx((size_t)N * N);
     auto put = [](ulonglong2 &d, i128 v) { d.x = (u64)(u128)v; d.y = (u64)((u128)v >> 64); };
     for (int p = 0; p < N; p++) {
         put(hfx[p], host_fixed(h->h[(size_t)p * N + p], F));
         for (int q = 0; q < N; q++) {
             put(Jfx[(size_t)p * N + q], host_fixed(h->eri[pair_index(pair_index(p, p), pair_index(q, q))], F));
-            put(Kfx[(size_t)p * N + q], host_fixed(h->eri[pair_index(pair_index(p, q), pair_index(q, p))], F));
+            put(JKfx[(size_t)p * N + q], host_fixed(h->eri[pair_index(pair_index(p, p), pair_index(q, q))], F) -
+                                             host_fixed(h->eri[pair_index(pair_index(p, q), pair_index(q, p))], F));
         }
     }
+    // single-excitation terms: (ai|kk) and (ai|kk) - (ak|ki) per (a, i, k)
+    std::vector<ulonglong2> Sfx((size_t)N * N * N * 2);
+    for (int a = 0; a < N; a++)
+        for (int i = 0; i < N; i++)
+            for (int k = 0; k < N; k++) {
+                const i128 c = host_fixed(h->eri[pair_index(pair_index(a, i), pair_index(k, k))], F);
+                const i128 x = host_fixed(h->eri[pair_index(pair_index(a, k), pair_index(k, i))], F);
+                const size_t o = (((size_t)a * N + i) * N + k) * 2;
+                put(Sfx[o], c);
+                put(Sfx[o + 1], c - x);
+            }
     // X(ref): sum over occupied orbitals and occupied pairs
     std::vector<std::pair<int, int>> occ;
     for (int p = 0; p < N; p++) if ((h->ref_a >> p) & 1) occ.push_back({p, 0});
@@ -668,6 +794,7 @@ int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_han
 
     I.target = P.target_walkers; I.A = P.shift_interval;
     I.semi_start = P.semistoch_start; I.semi_size = P.semistoch_size;
+    I.trial_size = P.trial_size; I.trial_start = P.trial_start;
     I.ring_cap = h->ring_cap;
 
     // integrals and tables on the device
@@ -675,21 +802,23 @@ int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_han
     double *deri = (double *)dev_alloc(h, h->eri.size() * sizeof(double));
     ulonglong2 *dhfx = (ulonglong2 *)dev_alloc(h, hfx.size() * sizeof(ulonglong2));
     ulonglong2 *dJ = (ulonglong2 *)dev_alloc(h, Jfx.size() * sizeof(ulonglong2));
-    ulonglong2 *dK = (ulonglong2 *)dev_alloc(h, Kfx.size() * sizeof(ulonglong2));
+    ulonglong2 *dK = (ulonglong2 *)dev_alloc(h, JKfx.size() * sizeof(ulonglong2));
+    ulonglong2 *dS = (ulonglong2 *)dev_alloc(h, Sfx.size() * sizeof(ulonglong2));
     int *dnbr = (int *)dev_alloc(h, std::max<size_t>(1, h->nbr.size()) * sizeof(int));
     h->dinst = (DevInst *)dev_alloc(h, sizeof(DevInst));
     h->dunit = (int *)dev_alloc(h, 2 * sizeof(int));
     h->dstate = (IterState *)dev_alloc(h, sizeof(IterState));
     I.ring = (fciqmc_iter_stats *)dev_alloc(h, (size_t)h->ring_cap * sizeof(fciqmc_iter_stats));
-    if (!dh || !deri || !dhfx || !dJ || !dK || !dnbr || !h->dinst || !h->dunit || !h->dstate || !I.ring)
+    if (!dh || !deri || !dhfx || !dJ || !dK || !dS || !dnbr || !h->dinst || !h->dunit || !h->dstate || !I.ring)
         return bail(FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (integrals)");
     cudaMemcpyAsync(dh, h->h.data(), h->h.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);
     cudaMemcpyAsync(deri, h->eri.data(), h->eri.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);
     cudaMemcpyAsync(dhfx, hfx.data(), hfx.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice, h->stream);
     cudaMemcpyAsync(dJ, Jfx.data(), Jfx.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice, h->stream);
-    cudaMemcpyAsync(dK, Kfx.data(), Kfx.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(dK, JKfx.data(), JKfx.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice, h->stream);
+    cudaMemcpyAsync(dS, Sfx.data(), Sfx.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice, h->stream);
     if (!h->nbr.empty()) cudaMemcpyAsync(dnbr, h->nbr.data(), h->nbr.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream);
-    I.h = dh; I.eri = deri; I.hfx = dhfx; I.Jfx = dJ; I.Kfx = dK; I.nbr = dnbr;
+    I.h = dh; I.eri = deri; I.hfx = dhfx; I.Jfx = dJ; I.JKfx = dK; I.Sfx = dS; I.nbr = dnbr;
     I.st = h->dstate;
     // time step: given, or 0.5 / sum_j |H_ref,j| (computed on the device)
     {
@@ -788,10 +917,10 @@ int fciqmc_set_profiling(fciqmc_handle *h, int32_t on)
     return FCIQMC_OK;
 }
 
-int fciqmc_kernel_times(fciqmc_handle *h, double out[5])
+int fciqmc_kernel_times(fciqmc_handle *h, double out[6])
 {
     if (!h || !out) return FCIQMC_ERR_INVALID_ARG;
-    for (int k = 0; k < 5; k++) out[k] = h->ktime[k];
+    for (int k = 0; k < 6; k++) out[k] = h->ktime[k];
     return FCIQMC_OK;
 }
 
@@ -858,7 +987,8 @@ static int step_to(fciqmc_handle *h, long long target_iter)
     int rc;
     int retries = 0;
     std::vector<cudaEvent_t> evs;
-    double kt[5] = {0, 0, 0, 0, 0};
+    double kt[6] = {0, 0, 0, 0, 0, 0};
+    static const int slot_of[6] = {0, 1, 4, 2, 5, 3};  // event interval -> ktime slot
     long long kn = 0;
     long long chunk_max = 16;  // grows after clean chunks; an error costs at most one chunk of no-op replays
     for (;;) {
@@ -873,10 +1003,10 @@ static int step_to(fciqmc_handle *h, long long target_iter)
         const long long chunk = std::min<long long>(std::min<long long>(target_iter - start, h->ring_cap), chunk_max);
         chunk_max = std::min<long long>(chunk_max * 2, h->ring_cap);
         if (h->profiling) {
-            evs.resize((size_t)chunk * 6);
+            evs.resize((size_t)chunk * 7);
             for (auto &e : evs) cudaEventCreate(&e);
             for (long long k = 0; k < chunk; k++) {
-                rc = enqueue_iteration(h, evs.data() + 6 * k);
+                rc = enqueue_iteration(h, evs.data() + 7 * k);
                 if (rc) return rc;
             }
         } else {
@@ -887,10 +1017,10 @@ static int step_to(fciqmc_handle *h, long long target_iter)
         if (h->profiling) {
             const long long done = h->hst.iter - start;
             for (long long k = 0; k < done; k++)
-                for (int j = 0; j < 5; j++) {
+                for (int j = 0; j < 6; j++) {
                     float ms = 0.f;
-                    cudaEventElapsedTime(&ms, evs[6 * k + j], evs[6 * k + j + 1]);
-                    kt[j == 2 ? 4 : (j > 2 ? j - 1 : j)] += ms;
+                    cudaEventElapsedTime(&ms, evs[7 * k + j], evs[7 * k + j + 1]);
+                    kt[slot_of[j]] += ms;
                 }
             kn += done;
             for (auto &e : evs) cudaEventDestroy(e);
@@ -913,7 +1043,7 @@ static int step_to(fciqmc_handle *h, long long target_iter)
         }
     }
     if (h->profiling && kn > 0)
-        for (int j = 0; j < 5; j++) h->ktime[j] = kt[j] / (double)kn;
+        for (int j = 0; j < 6; j++) h->ktime[j] = kt[j] / (double)kn;
     return FCIQMC_OK;
 }
 
@@ -931,9 +1061,15 @@ static int handle_flags(fciqmc_handle *h, int *retries)
     if (err & ERRB_NUMERIC)
         return fail(h, FCIQMC_ERR_NUMERIC, "numeric error (NaN/Inf or |C| >= 2^31) at iteration " + std::to_string(h->hst.iter));
     if (err & ERRB_TIMEOUT) return fail(h, FCIQMC_ERR_TIMEOUT, "device wait timed out");
-    if (err == ERRB_PAUSE_SEMI) {
-        rc = build_semistochastic(h);
-        if (rc) return rc;
+    if (err && !(err & ~(ERRB_PAUSE_SEMI | ERRB_PAUSE_TRIAL))) {
+        if (err & ERRB_PAUSE_SEMI) {
+            rc = build_semistochastic(h);
+            if (rc) return rc;
+        }
+        if (err & ERRB_PAUSE_TRIAL) {
+            rc = build_trial(h);
+            if (rc) return rc;
+        }
         h->hst.err = 0;
         return write_state(h);
     }
@@ -1090,6 +1226,20 @@ int fciqmc_import_state(fciqmc_handle *h, int64_t n, const uint64_t *alpha, cons
     h->hst.stop_iter = LLONG_MAX;
     h->hst.iter = iteration; h->hst.parity = par; h->hst.S = S; h->hst.vary = vary;
     h->hst.shift_start = shift_start; h->hst.cnt = cnt; h->hst.nwl_hi = nw_last_hi; h->hst.nwl_lo = nw_last_lo;
+    h->hst.semi_built = h->hi.nd > 0;
+    h->hst.trial_built = h->trial_nt > 0;
+    rc = write_state(h);
+    if (rc) return rc;
+    // a space due at the imported iteration is built now (the kernels raise
+    // its pause at the end of the iteration before)
+    if (vary && h->p.semistoch_size > 0 && !h->hst.semi_built && iteration == shift_start + h->p.semistoch_start) {
+        rc = build_semistochastic(h);
+        if (rc) return rc;
+    }
+    if (vary && h->p.trial_size > 0 && !h->hst.trial_built && iteration == shift_start + h->p.trial_start) {
+        rc = build_trial(h);
+        if (rc) return rc;
+    }
     rc = write_state(h);
     if (rc) return rc;
     h->hist.clear();
@@ -1159,6 +1309,7 @@ int fciqmc_step_batch(fciqmc_handle **hs, int32_t k, int64_t n_iter)
         if (max_nd > 0) launch_semistoch(dinst, k, max_nd, h0->stream);
         cudaError_t le = launch_annihilate(dinst, dunit, k, units, h0->stream);
         launch_annihilate_big(dinst, k, h0->stream);
+        launch_new_diag(dinst, k, h0->stream);
         launch_finalize(dinst, k, h0->stream);
         cudaError_t e = cudaStreamEndCapture(h0->stream, &g);
         if (le != cudaSuccess || e != cudaSuccess) return fail(h0, FCIQMC_ERR_CUDA, "batch graph capture failed");
@@ -1265,6 +1416,28 @@ static double blocking_sigma(std::vector<double> x)
     return lev.back().first;
 }
 
+// ratio of the means of num and den with a delta-method error from the
+// blocking errors of both and their correlation
+static void ratio_blocking(const std::vector<double> &num, const std::vector<double> &den, double *ratio, double *sigma)
+{
+    double mn = 0, md = 0;
+    for (size_t i = 0; i < num.size(); i++) { mn += num[i]; md += den[i]; }
+    mn /= num.size(); md /= den.size();
+    double sn = blocking_sigma(num), sd = blocking_sigma(den);
+    double cov = 0, vn = 0, vd = 0;
+    for (size_t i = 0; i < num.size(); i++) {
+        cov += (num[i] - mn) * (den[i] - md);
+        vn += (num[i] - mn) * (num[i] - mn);
+        vd += (den[i] - md) * (den[i] - md);
+    }
+    double rho = (vn > 0 && vd > 0) ? cov / std::sqrt(vn * vd) : 0.0;
+    double r = mn / md;
+    double rel = (mn != 0.0) ? (sn / mn) * (sn / mn) + (sd / md) * (sd / md) - 2.0 * rho * sn * sd / (mn * md)
+                             : (sn / md) * (sn / md);
+    *ratio = r;
+    *sigma = mn != 0.0 ? std::fabs(r) * std::sqrt(std::max(rel, 0.0)) : std::sqrt(std::max(rel, 0.0));
+}
+
 extern "C" int fciqmc_energy(fciqmc_handle *h, fciqmc_stats *out)
 {
     if (!h || !out) return FCIQMC_ERR_INVALID_ARG;
@@ -1299,27 +1472,56 @@ extern "C" int fciqmc_energy(fciqmc_handle *h, fciqmc_stats *out)
             if (r.iteration >= out->equil_start) { num.push_back(r.e_num); den.push_back(r.e_den); sh.push_back(r.shift); }
         out->n_samples = (int64_t)num.size();
         if (num.size() >= 8) {
-            double mn = 0, md = 0, ms = 0;
-            for (size_t i = 0; i < num.size(); i++) { mn += num[i]; md += den[i]; ms += sh[i]; }
-            mn /= num.size(); md /= den.size(); ms /= sh.size();
-            double sn = blocking_sigma(num), sd = blocking_sigma(den);
-            double cov = 0, vn = 0, vd = 0;
-            for (size_t i = 0; i < num.size(); i++) {
-                cov += (num[i] - mn) * (den[i] - md);
-                vn += (num[i] - mn) * (num[i] - mn);
-                vd += (den[i] - md) * (den[i] - md);
-            }
-            double rho = (vn > 0 && vd > 0) ? cov / std::sqrt(vn * vd) : 0.0;
-            double r = mn / md;
-            double rel = (mn != 0.0) ? (sn / mn) * (sn / mn) + (sd / md) * (sd / md) - 2.0 * rho * sn * sd / (mn * md)
-                                     : (sn / md) * (sn / md);
+            double ms = 0, r, sg;
+            for (size_t i = 0; i < sh.size(); i++) ms += sh[i];
+            ms /= sh.size();
+            ratio_blocking(num, den, &r, &sg);
             out->e_proj_mean = h->eref + r;
-            out->e_proj_sigma = mn != 0.0 ? std::fabs(r) * std::sqrt(std::max(rel, 0.0)) : std::sqrt(std::max(rel, 0.0));
+            out->e_proj_sigma = sg;
             out->shift_mean = h->eref + ms;
             out->shift_sigma = blocking_sigma(sh);
         }
     }
+    // trial-wave-function estimator (Sec. IV)
+    out->e_trial_mean = NAN;
+    out->e_trial_sigma = NAN;
+    out->e_trial_T = h->trial_nt > 0 ? h->eref + h->trial_ET : NAN;
+    if (h->trial_nt > 0 && out->equil_start >= 0) {
+        const long long t0 = std::max<long long>(out->equil_start, h->hst.shift_start + h->p.trial_start);
+        std::vector<double> num, den;
+        for (const auto &r : h->hist)
+            if (r.iteration >= t0 && r.trial_den != 0.0) { num.push_back(r.trial_num); den.push_back(r.trial_den); }
+        out->trial_samples = (int64_t)num.size();
+        if (num.size() >= 8) {
+            double r, sg;
+            ratio_blocking(num, den, &r, &sg);
+            out->e_trial_mean = h->eref + r;
+            out->e_trial_sigma = sg;
+        }
+    }
     return FCIQMC_OK;
+}
+
+extern "C" int64_t fciqmc_trial_info(fciqmc_handle *h, int64_t *n_w, double *ET, uint64_t *t_alpha, uint64_t *t_beta,
+                                     double *cT, int64_t cap)
+{
+    if (!h || cap < 0) return FCIQMC_ERR_INVALID_ARG;
+    if (n_w) *n_w = h->trial_nw;
+    if (ET) *ET = h->trial_ET;
+    const long long m = std::min<long long>(cap, h->trial_nt);
+    if (m > 0 && (t_alpha || t_beta)) {
+        std::vector<ulonglong2> k((size_t)m);
+        if (cudaMemcpy(k.data(), h->trial_key, (size_t)m * sizeof(ulonglong2), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(h, FCIQMC_ERR_CUDA, "trial copy failed");
+        for (long long i = 0; i < m; i++) {
+            if (t_alpha) t_alpha[i] = k[(size_t)i].x;
+            if (t_beta) t_beta[i] = k[(size_t)i].y;
+        }
+    }
+    if (m > 0 && cT &&
+        cudaMemcpy(cT, h->trial_cT, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(h, FCIQMC_ERR_CUDA, "trial copy failed");
+    return h->trial_nt;
 }
 
 // ------------------------------------------------------------------ time step
@@ -1515,7 +1717,7 @@ int fciqmc_server_tick(fciqmc_server *srv, int64_t n_iter, int32_t *n_active)
             for (int64_t id : srv->running) {
                 Request &r = srv->req[id];
                 fciqmc_stats st;
-                if (fciqmc_energy(r.h, &st) != FCIQMC_OK || r.h->hst.err & ~(ERRB_STOP | ERRB_PAUSE_SEMI)) {
+                if (fciqmc_energy(r.h, &st) != FCIQMC_OK || r.h->hst.err & ~(ERRB_STOP | ERRB_PAUSE_SEMI | ERRB_PAUSE_TRIAL)) {
                     r.st.error = rc;
                     retire(srv, r, 4);
                 }

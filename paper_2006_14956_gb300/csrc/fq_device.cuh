@@ -243,20 +243,37 @@ __device__ __forceinline__ double eri4(const DevInst &I, int p, int q, int r, in
 
 // single excitation i -> a of spin sp from (pa, pb):
 // exact sum of h_ai + sum_{k occ, k != i} (ai|kk) - sum_{k occ same spin, k != i} (ak|ki)
+// With the fixed-point table Sfx (entry (a, i, k): (ai|kk) and (ai|kk) - (ak|ki)
+// side by side) every occupied k costs one 16-byte load; the loads are issued
+// four at a time.  Without it (callers that hold only the integrals) the
+// terms are converted on the fly.  Both give the same exact sum.
 static __device__ double single_exact(const DevInst &I, u64 pa, u64 pb, int sp, int i, int a)
 {
     const int N = I.norb, F = I.F;
     i128 acc = to_fixed(__ldg(I.h + a * N + i), F);
+    u64 same = (sp ? pb : pa) & ~(1ULL << i), other = sp ? pa : pb;
+    if (I.Sfx) {
+        const ulonglong2 *row = I.Sfx + (size_t)(a * N + i) * (size_t)N * 2;
+        while (same | other) {
+            ulonglong2 v[4];
+            for (int r = 0; r < 4; r++) {
+                int k = -1, sel = 0;
+                if (same) { k = __ffsll((long long)same) - 1; same &= same - 1; sel = 1; }
+                else if (other) { k = __ffsll((long long)other) - 1; other &= other - 1; }
+                v[r] = k >= 0 ? __ldg(row + 2 * k + sel) : make_ulonglong2(0, 0);
+            }
+            for (int r = 0; r < 4; r++) acc += (i128)(((u128)v[r].y << 64) | (u128)v[r].x);
+        }
+        return fixed_to_double(acc, F);
+    }
     const int pai = pidx(a, i);
-    u64 occ[2] = { pa, pb };
-    occ[sp] &= ~(1ULL << i);
     for (int s = 0; s < 2; s++) {
-        u64 x = occ[s];
+        u64 x = s ? other : same;
         while (x) {
             int k = __ffsll((long long)x) - 1;
             x &= x - 1;
             acc += to_fixed(__ldg(I.eri + pidx(pai, k * (k + 3) / 2)), F);
-            if (s == sp) acc -= to_fixed(__ldg(I.eri + pidx(pidx(a, k), pidx(k, i))), F);
+            if (s == 0) acc -= to_fixed(__ldg(I.eri + pidx(pidx(a, k), pidx(k, i))), F);
         }
     }
     return fixed_to_double(acc, F);
@@ -315,36 +332,85 @@ __device__ __forceinline__ int d_index_of(const DevInst &I, u64 a, u64 b)
     return -1;
 }
 
-// H_ii - E_ref for determinant (a, b), computed by one warp: the exact sum
-// of h_pp over occupied orbitals and (pp|qq) - delta_spin (pq|qp) over
-// occupied pairs, minus the same sum for the reference, rounded once.
-static __device__ double diag_exact_warp(const DevInst &I, u64 a, u64 b)
+// orbital of electron e held in register e >> 5 of lane e & 31 (n: electrons,
+// the same in every lane; all lanes call this together)
+__device__ __forceinline__ int orb_of_electron(const int (&orb)[4], int n, int e)
 {
-    const int lane = threadIdx.x & 31, N = I.norb;
-    i128 part = 0;
-    for (int e = lane; e < I.n; e += 32) {
-        bool sp = e >= I.na;
-        u64 w = sp ? b : a;
-        int p = nth_set(w, sp ? e - I.na : e);
-        part += fx_load(I.hfx, p);
-        u64 same = w & ~mask_below(p + 1);
-        while (same) {
-            int q = __ffsll((long long)same) - 1;
-            same &= same - 1;
-            part += fx_load(I.Jfx, p * N + q) - fx_load(I.Kfx, p * N + q);
+    const int src = e & 31, r = e >> 5;
+    int x = __shfl_sync(0xffffffffu, orb[0], src);
+    for (int k = 1; k < 4; k++)
+        if (n > 32 * k) {
+            const int y = __shfl_sync(0xffffffffu, orb[k], src);
+            if (r == k) x = y;
         }
-        if (!sp) {
-            u64 ob = b;
-            while (ob) {
-                int q = __ffsll((long long)ob) - 1;
-                ob &= ob - 1;
-                part += fx_load(I.Jfx, p * N + q);
+    return x;
+}
+
+// H_ii - E_ref of D determinants (a[d], b[d]), computed together by one warp:
+// the exact sum of h_pp over occupied orbitals and (pp|qq) - delta_spin (pq|qp)
+// over occupied pairs, minus the same sum for the reference, rounded once.
+// The n + n(n-1)/2 terms are spread evenly over the lanes (term t < n: h_pp
+// of electron t; otherwise the pair e1 < e2 with t - n = e2(e2-1)/2 + e1);
+// each lane issues the loads of four terms of every determinant before it
+// adds any of them.
+template <int D>
+static __device__ void diag_exact_warp_multi(const DevInst &I, const u64 (&a)[D], const u64 (&b)[D], double (&out)[D])
+{
+    const int lane = threadIdx.x & 31, N = I.norb, n = I.n, na = I.na;
+    // orbital of electron e (alpha electrons first) in register e >> 5 of lane e & 31
+    int orb[D][4];
+    for (int d = 0; d < D; d++)
+        for (int r = 0; r < 4; r++) {
+            const int e = lane + 32 * r;
+            orb[d][r] = e < n ? (e < na ? nth_set(a[d], e) : nth_set(b[d], e - na)) : 0;
+        }
+    const int T = n + n * (n - 1) / 2;
+    i128 part[D];
+    for (int d = 0; d < D; d++) part[d] = 0;
+    for (int t0 = 0; t0 < T; t0 += 128) {
+        ulonglong2 v[D][4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int t = t0 + 32 * r + lane;
+            int e1, e2;
+            if (t < n) { e1 = t; e2 = -1; }
+            else {
+                const int q = t < T ? t - n : 0;
+                int c = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)q)) * 0.5f);  // estimate, corrected below
+                while (c > 1 && c * (c - 1) / 2 > q) c--;
+                while ((c + 1) * c / 2 <= q) c++;
+                e2 = c;
+                e1 = q - c * (c - 1) / 2;
+            }
+            const bool same = e2 >= 0 && ((e1 < na) == (e2 < na));
+#pragma unroll
+            for (int d = 0; d < D; d++) {
+                const int p1 = orb_of_electron(orb[d], n, e1);
+                const int p2 = orb_of_electron(orb[d], n, e2 < 0 ? 0 : e2);
+                v[d][r] = make_ulonglong2(0, 0);
+                if (t < T) v[d][r] = __ldg(e2 < 0 ? I.hfx + p1 : (same ? I.JKfx : I.Jfx) + p1 * N + p2);
             }
         }
+#pragma unroll
+        for (int d = 0; d < D; d++)
+#pragma unroll
+            for (int r = 0; r < 4; r++) part[d] += (i128)(((u128)v[d][r].y << 64) | (u128)v[d][r].x);
     }
-    for (int m = 16; m >= 1; m >>= 1) part += shfl_xor_i128(part, m);
-    i128 xref = (i128)(((u128)I.xref_hi << 64) | (u128)I.xref_lo);
-    return fixed_to_double(part - xref, I.F);
+    const i128 xref = (i128)(((u128)I.xref_hi << 64) | (u128)I.xref_lo);
+#pragma unroll
+    for (int d = 0; d < D; d++) {
+        i128 x = part[d];
+        for (int m = 16; m >= 1; m >>= 1) x += shfl_xor_i128(x, m);
+        out[d] = fixed_to_double(x - xref, I.F);
+    }
+}
+
+static __device__ double diag_exact_warp(const DevInst &I, u64 a, u64 b)
+{
+    const u64 aa[1] = {a}, bb[1] = {b};
+    double o[1];
+    diag_exact_warp_multi<1>(I, aa, bb, o);
+    return o[0];
 }
 
 }  // namespace fq

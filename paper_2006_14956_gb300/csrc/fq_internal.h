@@ -25,6 +25,7 @@ enum {
     ERRB_TIMEOUT = 16,    // bounded wait expired
     ERRB_PAUSE_SEMI = 32, // iteration boundary at which D must be built (not an error)
     ERRB_STOP = 64,       // the run reached its stop iteration inside a batch (not an error)
+    ERRB_PAUSE_TRIAL = 128,  // iteration boundary at which the trial space must be built (not an error)
 };
 enum { DFLAG_REF = 1, DFLAG_D = 2 };
 
@@ -54,6 +55,7 @@ struct Partial {  // per-bucket reductions of one iteration
     u64 ann_lo, ann_hi;     // annihilated walkers * 2^32 (signed 128-bit)
     long long ndet, rejected, spawns, attempts;
     double e_num;
+    double t_num, t_den;    // trial-wave-function estimator
     double pad;
 };
 
@@ -74,8 +76,12 @@ struct IterState {  // device-resident iteration state of one run
     int need_main;          // largest new-list size of an overflowing bucket
     int n_spawn_over;       // buckets whose spawns overflowed
     long long stop_iter;    // K5 raises ERRB_STOP when iter reaches it
-    long long pad1;
+    long long trial_built;  // 1 once the trial space exists
+    int new_n;              // determinants created in this iteration (their H_jj is computed by k_new_diag)
+    int pad2;
 };
+
+struct TrialEnt;
 
 // one run as seen by the kernels
 struct DevInst {
@@ -88,7 +94,8 @@ struct DevInst {
     const int *nbr;
     const ulonglong2 *hfx;  // h_pp, fixed point (lo, hi)
     const ulonglong2 *Jfx;  // (pp|qq)
-    const ulonglong2 *Kfx;  // (pq|qp)
+    const ulonglong2 *JKfx; // (pp|qq) - (pq|qp)
+    const ulonglong2 *Sfx;  // [(a N + i) N + k][2]: (ai|kk), (ai|kk) - (ak|ki); NULL = convert on the fly
     u64 xref_lo, xref_hi;   // exact diagonal sum of the reference
     u64 ref_a, ref_b;
     u64 normask;
@@ -119,6 +126,7 @@ struct DevInst {
     int cap_s;              // spawn capacity per bucket
     int big_tabbits;        // hash-table bits of the large-bucket path
     int *big_list;          // deferred bucket ids (capacity = buckets)
+    unsigned *newdet;       // main-list slots of the determinants created in this iteration
     unsigned char *big_scratch;  // BIG_BLOCKS slices of big_stride bytes
     size_t big_stride;
     HeavyChunk *heavy;
@@ -148,6 +156,18 @@ struct DevInst {
     const double2 *pchb_meta;
     const ulonglong2 *pchb_ent;
     u64 pchb_ss_base;
+    // trial-wave-function estimator: open-addressing table of W_j and cT_j
+    // (slot state 0 empty, 1 being written, 2 ready), 2^trial_bits slots
+    long long trial_size, trial_start;
+    int trial_bits;
+    const unsigned *trial_state;
+    const TrialEnt *trial_tab;
+};
+
+struct TrialEnt {
+    u64 a, b;
+    double w;   // <Psi^T|H - E_ref|D_j>
+    double cT;  // component of Psi^T (0 outside T)
 };
 
 // host-side launchers (kernels.cu)
@@ -159,6 +179,7 @@ cudaError_t init_kernels();
 size_t annihilate_smem_bytes();
 void launch_annihilate_big(const DevInst *dinst, int n_inst, cudaStream_t s);
 void launch_finalize(const DevInst *dinst, int n_inst, cudaStream_t s);
+void launch_new_diag(const DevInst *dinst, int n_inst, cudaStream_t s);
 void launch_rebucket(const DevInst *src, const DevInst *dst, int nb_src, int parity, cudaStream_t s);
 void launch_diag(const DevInst *dinst, int parity, int nb, cudaStream_t s);
 void launch_abs_hist(const DevInst *dinst, int par, int nb, int shift, u64 prefix, unsigned *hist, cudaStream_t s);
@@ -170,6 +191,14 @@ void launch_mark_d(const DevInst *dinst, int parity, int nb, cudaStream_t s);
 
 cudaError_t launch_pchb_build(const DevInst *dinst, int norb, double ppair, double2 *meta, ulonglong2 *ent,
                               u64 ss_base, cudaStream_t s);
+cudaError_t launch_trial_dense(const long long *rowptr, const int *col, const double *val, int nt, int n2, double *A,
+                               double *hdiag, cudaStream_t s);
+cudaError_t launch_jacobi_lowest(double *A, double *V, int n, int n2, double *E, double *v, int *sweeps,
+                                 cudaStream_t s);
+cudaError_t launch_trial_w(const DevInst *dinst, const ulonglong2 *tkey, const double *cT, const double *hdiag, int nt,
+                           long long per_det, unsigned *state, TrialEnt *tab, int bits, unsigned long long *count,
+                           int *err, cudaStream_t s);
+long long connections_per_det(int na, int nb, int ma, int mb);
 void set_launch_geometry(int spawn_bps, int heavy_bps, int anni_bps);
 void get_launch_geometry(int *spawn_bps, int *heavy_bps, int *anni_bps);
 cudaError_t ref_abs_sum(const DevInst *dinst, double *dpartial, double *out, cudaStream_t s);

@@ -275,13 +275,18 @@ struct K1Smem {
     unsigned char fl[CAP_M];
     SpawnRec rec[CHUNK];
     int qn[NQ];
+    int next;  // evaluation counter of the chunk
     unsigned wsum[K1_THREADS / 32];
     long long wl[K1_THREADS / 32];
     int hdr_err, hdr_par;
     long long hdr_it;
 };
 
-// draw and classify attempts [a0, a1) (attempt a of parent `det`, slot k), then process by class
+// draw and classify the attempts of a chunk (attempt a of parent `det`, slot
+// k), queue them by class, then evaluate them: warps take 32 queued attempts
+// at a time from a shared counter, singles (the long exact sums) first, so
+// that no warp idles at the chunk's closing barrier while others still hold
+// a long queue.
 template <typename MAP>
 __device__ void run_attempts(const DevInst &I, K1Smem &S, long long it, unsigned A, MAP map)
 {
@@ -289,55 +294,69 @@ __device__ void run_attempts(const DevInst &I, K1Smem &S, long long it, unsigned
     for (unsigned a0 = 0; a0 < A; a0 += CHUNK) {
         const unsigned a1 = min(A, a0 + CHUNK);
         if (t < NQ) S.qn[t] = 0;
+        if (t == 0) S.next = 0;
         __syncthreads();
         // queues are laid out back to back: doubles from the front of rec[],
-        // singles and hops from the back (hops only exist without the others)
-        for (unsigned a = a0 + t; a < a1 + ((a1 - a0) % 32 ? 32 - (a1 - a0) % 32 : 0); a += K1_THREADS) {
-            int cls = -1;
-            unsigned det = 0;
-            u64 w[4] = {0, 0, 0, 0};
-            if (a < a1) {
+        // singles and hops from the back (hops only exist without the others);
+        // each thread draws two attempts per round, so that the two Philox
+        // evaluations overlap
+        for (unsigned ab = a0; ab < a1; ab += 2 * K1_THREADS) {
+            u64 w[2][4];
+            unsigned det[2];
+            int cls[2];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const unsigned a = ab + h * K1_THREADS + t;
+                const unsigned ac = a < a1 ? a : a1 - 1;  // clamped: drawn, then discarded
                 u64 k;
-                det = map.det_of(a, k);
-                const ulonglong2 kk = map.key(det);
-                philox(kk.x, kk.y, (u64)it, (k << 8) | (u64)PURPOSE_SPAWN, I.seed, 0ULL, w);
-                cls = classify(I, kk.x, kk.y, w[0], w[1]);
+                det[h] = map.det_of(ac, k);
+                const ulonglong2 kk = map.key(det[h]);
+                philox(kk.x, kk.y, (u64)it, (k << 8) | (u64)PURPOSE_SPAWN, I.seed, 0ULL, w[h]);
+                cls[h] = a < a1 ? classify(I, kk.x, kk.y, w[h][0], w[h][1]) : -1;
             }
-            const bool front = cls == Q_DOUBLE, back = cls == Q_SINGLE || cls == Q_HOP;
-            const unsigned mf = __ballot_sync(0xffffffffu, front), mb = __ballot_sync(0xffffffffu, back);
-            int bf = 0, bk = 0;
-            if (lane == 0) {
-                if (mf) bf = atomicAdd(&S.qn[Q_DOUBLE], __popc(mf));
-                if (mb) bk = atomicAdd(&S.qn[Q_SINGLE], __popc(mb));
-            }
-            bf = __shfl_sync(0xffffffffu, bf, 0);
-            bk = __shfl_sync(0xffffffffu, bk, 0);
-            const unsigned below = (1u << lane) - 1u;
-            if (front || back) {
-                const int slot = front ? bf + __popc(mf & below) : CHUNK - 1 - (bk + __popc(mb & below));
-                SpawnRec &r = S.rec[slot];
-                r.w1 = w[1]; r.w2 = w[2]; r.w3 = w[3]; r.det = det;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const bool front = cls[h] == Q_DOUBLE, back = cls[h] == Q_SINGLE || cls[h] == Q_HOP;
+                const unsigned mf = __ballot_sync(0xffffffffu, front), mb = __ballot_sync(0xffffffffu, back);
+                int bf = 0, bk = 0;
+                if (lane == 0) {
+                    if (mf) bf = atomicAdd(&S.qn[Q_DOUBLE], __popc(mf));
+                    if (mb) bk = atomicAdd(&S.qn[Q_SINGLE], __popc(mb));
+                }
+                bf = __shfl_sync(0xffffffffu, bf, 0);
+                bk = __shfl_sync(0xffffffffu, bk, 0);
+                const unsigned below = (1u << lane) - 1u;
+                if (front || back) {
+                    const int slot = front ? bf + __popc(mf & below) : CHUNK - 1 - (bk + __popc(mb & below));
+                    SpawnRec &r = S.rec[slot];
+                    r.w1 = w[h][1]; r.w2 = w[h][2]; r.w3 = w[h][3]; r.det = det[h];
+                }
             }
         }
         __syncthreads();
-        const int nd = S.qn[Q_DOUBLE], ns = S.qn[Q_SINGLE];
-        for (int q = t; q < nd; q += K1_THREADS) {
-            const SpawnRec r = S.rec[q];
-            const ulonglong2 kk = map.key(r.det);
-            if (I.pchb) spawn_double_pchb(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3);
-            else spawn_double(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3);
-        }
-        for (int q = t; q < ns; q += K1_THREADS) {
-            const SpawnRec r = S.rec[CHUNK - 1 - q];
-            const ulonglong2 kk = map.key(r.det);
-            if (I.kind == FCIQMC_HUBBARD) spawn_hop(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3);
-            else spawn_single(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3);
+        const int nd = S.qn[Q_DOUBLE], ns = S.qn[Q_SINGLE], ntot = ns + nd;
+        while (true) {
+            int g = 0;
+            if (lane == 0) g = atomicAdd(&S.next, 32);
+            g = __shfl_sync(0xffffffffu, g, 0);
+            if (g >= ntot) break;
+            const int q = g + lane;
+            if (q < ns) {
+                const SpawnRec r = S.rec[CHUNK - 1 - q];
+                const ulonglong2 kk = map.key(r.det);
+                if (I.kind == FCIQMC_HUBBARD) spawn_hop(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3);
+                else spawn_single(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3);
+            } else if (q < ntot) {
+                const SpawnRec r = S.rec[q - ns];
+                const ulonglong2 kk = map.key(r.det);
+                if (I.pchb) spawn_double_pchb(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3);
+                else spawn_double(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3);
+            }
         }
         __syncthreads();
     }
 }
 
-// attempts of the light determinants of one bucket
 struct BucketMap {
     const K1Smem *S;
     __device__ unsigned det_of(unsigned a, u64 &k) const
@@ -364,7 +383,7 @@ struct HeavyMap {
     __device__ unsigned flags(unsigned) const { return h.flags; }
 };
 
-__global__ void __launch_bounds__(K1_THREADS) k_spawn(const DevInst *__restrict__ insts, const int *__restrict__ unit_start,
+__global__ void __launch_bounds__(K1_THREADS, 3) k_spawn(const DevInst *__restrict__ insts, const int *__restrict__ unit_start,
                                                       int n_inst, int n_units)
 {
     extern __shared__ __align__(16) unsigned char k1_raw[];
@@ -408,7 +427,7 @@ __global__ void __launch_bounds__(K1_THREADS) k_spawn(const DevInst *__restrict_
                     nat = ceil_abs(c);
                     const bool init = (dbits(c) & ~SIGN64) > dbits(I.n_a) || (f & (DFLAG_REF | DFLAG_D));
                     fl = (init ? 1u : 0u) | ((f & DFLAG_D) ? 2u : 0u);
-                    cper = c / (double)nat;
+                    cper = nat == 1 ? c : c / (double)nat;  // c / 1 is c
                     att += (long long)nat;
                     if (nat > HEAVY_ATT) {  // sliced into the heavy queue
                         const unsigned nch = (unsigned)((nat + HEAVY_ATT - 1) / HEAVY_ATT);
@@ -521,8 +540,9 @@ enum { EF_OWNER = 1, EF_OCC = 2, EF_KEEP = 4, EF_REF = 16, EF_D = 32 };
 struct K3Shared {
     int wsum[K3_THREADS / 32];
     double red_d[K3_THREADS / 32];
+    double red_t[K3_THREADS / 32][2];
     u64 red_u[K3_THREADS / 32][8];
-    int n_new;
+    int n_new, new_base;
     int hdr_err, hdr_par;
     long long hdr_it;
     double hdr_S;
@@ -567,6 +587,19 @@ __device__ __forceinline__ int block_excl_scan(int v, int *wsum, int *total)
     return r;
 }
 
+// slot of determinant (a, b) in the trial-estimator table, or -1
+__device__ __forceinline__ int trial_find(const DevInst &I, u64 a, u64 b)
+{
+    const u64 mask = (1ULL << I.trial_bits) - 1;
+    u64 s = det_hash(a, b) & mask;
+    for (u64 probe = 0; probe <= mask; probe++) {
+        if (__ldg(I.trial_state + s) == 0u) return -1;
+        if (__ldg(&I.trial_tab[s].a) == a && __ldg(&I.trial_tab[s].b) == b) return (int)s;
+        s = (s + 1) & mask;
+    }
+    return -1;
+}
+
 // Death, annihilation and the reductions of one bucket b (steps (b) and (c)
 // of Eq. (4)).  All threads of the block call this together.
 template <typename IDX>
@@ -581,55 +614,99 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
     const double *oc = I.c[par], *ohd = I.hd[par];
     const uint8_t *ofl = I.fl[par];
 
-    // 1. stage: walkers [0, m), initiator spawns [m, m+si), other spawns [m+si, E)
+    // 1. stage: walkers [0, m), initiator spawns [m, m+si), other spawns [m+si, E);
+    //    four records per thread per round, all loads issued before the stores
     for (int q = t; q < TAB; q += K3_THREADS) W.tab[q] = 0;
     if (t == 0) S.n_new = 0;
-    for (int e = t; e < E; e += K3_THREADS) {
-        ulonglong2 k;
-        double v;
-        int f = 0;
-        if (e < m) {
-            k = okey[base + e];
-            v = oc[base + e];
-            uint8_t fl = ofl[base + e];
-            f = EF_OWNER | (is_zero(v) ? 0 : EF_OCC) | ((fl & DFLAG_REF) ? EF_REF : 0) | ((fl & DFLAG_D) ? EF_D : 0);
-        } else if (e < m + si) {
-            k = I.skey[sbase + (e - m)];
-            v = I.sw[sbase + (e - m)];
-        } else {
-            int slot = cap_s - 1 - (e - m - si);
-            k = I.skey[sbase + slot];
-            v = I.sw[sbase + slot];
-        }
-        W.key[e] = k;
-        W.val[e] = v;
-        W.acc_lo[e] = 0;
-        W.acc_hi[e] = 0;
-        W.nacc[e] = 0;
-        W.eflag[e] = f;
-    }
-    __syncthreads();
-    // 2. walkers: insert into the table (keys are distinct); death (b) and Eq. (3)
-    for (int e = t; e < m; e += K3_THREADS) {
-        ulonglong2 k = W.key[e];
-        u64 s = det_hash(k.x, k.y) & tmask;
-        while (atomicCAS(&W.tab[s], (IDX)0, (IDX)(e + 1)) != (IDX)0) s = (s + 1) & tmask;
-        const int f = W.eflag[e];
-        double cp;
-        if (f & EF_D) {
-            cp = I.dc_new[d_index_of(I, k.x, k.y)];
-        } else {
-            // C (1 - tau (H_ii - E_ref - S)), then rounding with the death draw
-            double c0 = W.val[e];
-            double fct = 1.0 - I.tau * (ohd[base + e] - shift);
-            cp = c0 * fct;
-            if (!is_zero(cp) && abs_lt(cp, I.cmin)) {
-                u64 w[4];
-                philox(k.x, k.y, (u64)it, (u64)PURPOSE_DEATH, I.seed, 0ULL, w);
-                cp = round_stoch(cp, I.cmin, I.cmin_log2, I.cmin_pow2, w[0]);
+    for (int e0 = 0; e0 < E; e0 += 4 * K3_THREADS) {
+        ulonglong2 k[4];
+        double v[4];
+        int f[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int e = e0 + r * K3_THREADS + t;
+            k[r] = make_ulonglong2(0, 0);
+            v[r] = 0.0;
+            f[r] = 0;
+            if (e < m) {
+                k[r] = okey[base + e];
+                v[r] = oc[base + e];
+                const uint8_t fl = ofl[base + e];
+                f[r] = EF_OWNER | ((fl & DFLAG_REF) ? EF_REF : 0) | ((fl & DFLAG_D) ? EF_D : 0);
+            } else if (e < m + si) {
+                k[r] = I.skey[sbase + (e - m)];
+                v[r] = I.sw[sbase + (e - m)];
+            } else if (e < E) {
+                const int slot = cap_s - 1 - (e - m - si);
+                k[r] = I.skey[sbase + slot];
+                v[r] = I.sw[sbase + slot];
             }
         }
-        W.val[e] = cp;
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int e = e0 + r * K3_THREADS + t;
+            if (e < E) {
+                W.key[e] = k[r];
+                W.val[e] = v[r];
+                W.acc_lo[e] = 0;
+                W.acc_hi[e] = 0;
+                W.nacc[e] = 0;
+                W.eflag[e] = f[r] | ((e < m && !is_zero(v[r])) ? EF_OCC : 0);
+            }
+        }
+    }
+    __syncthreads();
+    // 2. walkers (thread t holds walkers t + r K3_THREADS, r < 4, whose H_ii -
+    //    E_ref stay in registers for step 6): insert into the table (keys are
+    //    distinct); death (b) and Eq. (3), the rounding draws two at a time
+    static_assert(CAP_M <= 4 * K3_THREADS, "walkers per thread");
+    double hdr[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const int e = t + r * K3_THREADS;
+        hdr[r] = e < m ? ohd[base + e] : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const int e = t + r * K3_THREADS;
+        if (e < m) {
+            const ulonglong2 k = W.key[e];
+            u64 s = det_hash(k.x, k.y) & tmask;
+            while (atomicCAS(&W.tab[s], (IDX)0, (IDX)(e + 1)) != (IDX)0) s = (s + 1) & tmask;
+        }
+    }
+#pragma unroll
+    for (int r0 = 0; r0 < 4; r0 += 2) {
+        double cp[2];
+        bool draw[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int e = t + (r0 + h) * K3_THREADS;
+            draw[h] = false;
+            cp[h] = 0.0;
+            if (e < m) {
+                if (W.eflag[e] & EF_D) {
+                    const ulonglong2 k = W.key[e];
+                    cp[h] = I.dc_new[d_index_of(I, k.x, k.y)];
+                } else {
+                    // C (1 - tau (H_ii - E_ref - S)), then rounding with the death draw
+                    const double fct = 1.0 - I.tau * (hdr[r0 + h] - shift);
+                    cp[h] = W.val[e] * fct;
+                    draw[h] = !is_zero(cp[h]) && abs_lt(cp[h], I.cmin);
+                }
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int e = t + (r0 + h) * K3_THREADS;
+            if (draw[h]) {
+                const ulonglong2 k = W.key[e];
+                u64 w[4];
+                philox(k.x, k.y, (u64)it, (u64)PURPOSE_DEATH, I.seed, 0ULL, w);
+                cp[h] = round_stoch(cp[h], I.cmin, I.cmin_log2, I.cmin_pow2, w[0]);
+            }
+            if (e < m) W.val[e] = cp[h];
+        }
     }
     __syncthreads();
     // 3. spawns: find the target or become the owner of a new determinant;
@@ -713,10 +790,11 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
     double *nc = I.c[np], *nhd = I.hd[np];
     uint8_t *nfl = I.fl[np];
     u128 nw = 0;
-    double enm = 0.0;
+    double enm = 0.0, tnum = 0.0, tden = 0.0;
     bool bad = false;
     if (!overflow) {
-        for (int e = t; e < E; e += K3_THREADS) {
+        for (int r = 0; t + r * K3_THREADS < E; r++) {
+            const int e = t + r * K3_THREADS;
             const int f = W.eflag[e];
             if (!(f & EF_KEEP)) continue;
             const ulonglong2 k = W.key[e];
@@ -725,7 +803,7 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
             nkey[dst] = k;
             nc[dst] = c;
             nfl[dst] = (uint8_t)(((f & EF_REF) ? DFLAG_REF : 0) | ((f & EF_D) ? DFLAG_D : 0));
-            if (e < m) nhd[dst] = ohd[base + e];
+            if (e < m) nhd[dst] = r == 0 ? hdr[0] : r == 1 ? hdr[1] : r == 2 ? hdr[2] : hdr[3];
             else {
                 const int qn = atomicAdd(&S.n_new, 1);
                 W.nacc[qn] = e;  // accumulators are free now: reuse as the list of new determinants
@@ -738,21 +816,33 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
                 if (lev <= 4 && !is_zero(c)) enm = enm + hoff_generic(I, k.x, k.y, I.ref_a, I.ref_b) * c;
             }
             if (f & EF_D) I.dc_cur[d_index_of(I, k.x, k.y)] = c;
+            if (I.trial_bits && !is_zero(c)) {  // trial-wave-function estimator (Sec. IV)
+                const int ts = trial_find(I, k.x, k.y);
+                if (ts >= 0) {
+                    tnum = tnum + __ldg(&I.trial_tab[ts].w) * c;
+                    tden = tden + __ldg(&I.trial_tab[ts].cT) * c;
+                }
+            }
         }
     }
     if (bad) atomicOr(&I.st->err, ERRB_NUMERIC);
     __syncthreads();
-    // 7. H_jj - E_ref for new determinants, one warp each
+    // 7. new determinants: their slots go to the run's list; H_jj - E_ref is
+    //    computed for all of them at once by k_new_diag, whose warps are not
+    //    held back by this block's barriers
     if (!overflow) {
         const int nnew = S.n_new;
-        for (int q = warp; q < nnew; q += K3_THREADS / 32) {
-            const int e = W.nacc[q];
-            const ulonglong2 k = W.key[e];
-            const double hdv = diag_exact_warp(I, k.x, k.y);
-            if (lane == 0) nhd[base + W.opos[e]] = hdv;
-        }
+        if (t == 0 && nnew > 0) S.new_base = atomicAdd(&I.st->new_n, nnew);
+        __syncthreads();
+        for (int q = t; q < nnew; q += K3_THREADS)
+            I.newdet[S.new_base + q] = (unsigned)(base + W.opos[W.nacc[q]]);
     }
     // 8. bucket reductions (fixed order: lanes by xor tree, warps in index order)
+    if (I.trial_bits)  // binary64 adds are slow on this part: only when the estimator is on
+        for (int mm = 16; mm >= 1; mm >>= 1) {
+            tnum = tnum + __shfl_xor_sync(0xffffffffu, tnum, mm);
+            tden = tden + __shfl_xor_sync(0xffffffffu, tden, mm);
+        }
     for (int mm = 16; mm >= 1; mm >>= 1) {
         enm = enm + __shfl_xor_sync(0xffffffffu, enm, mm);
         rejected += __shfl_xor_sync(0xffffffffu, rejected, mm);
@@ -761,6 +851,8 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
     }
     if (lane == 0) {
         S.red_d[warp] = enm;
+        S.red_t[warp][0] = tnum;
+        S.red_t[warp][1] = tden;
         S.red_u[warp][0] = (u64)nw;
         S.red_u[warp][1] = (u64)(nw >> 64);
         S.red_u[warp][2] = (u64)ann;
@@ -769,12 +861,16 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
     }
     __syncthreads();
     if (t == 0) {
-        double e_sum = 0.0;
+        double e_sum = 0.0, tn = 0.0, td = 0.0;
         u128 nws = 0;
         i128 anns = 0;
         long long rej = 0;
         for (int k = 0; k < K3_THREADS / 32; k++) {
             e_sum = e_sum + S.red_d[k];
+            if (I.trial_bits) {
+                tn = tn + S.red_t[k][0];
+                td = td + S.red_t[k][1];
+            }
             nws += ((u128)S.red_u[k][1] << 64) | S.red_u[k][0];
             anns += (i128)(((u128)S.red_u[k][3] << 64) | S.red_u[k][2]);
             rej += (long long)S.red_u[k][4];
@@ -788,6 +884,8 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
         P.rejected = rej;
         P.spawns = si + sn;
         P.e_num = e_sum;
+        P.t_num = tn;
+        P.t_den = td;
         if (!overflow) I.cnt[np][b] = total;
         I.scnt_i[b] = 0;
         I.scnt_n[b] = 0;
@@ -886,6 +984,7 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
     IterState *st = I.st;
     __shared__ int s_err;
     __shared__ double s_d[K5_THREADS / 32];
+    __shared__ double s_t[K5_THREADS / 32][2];
     __shared__ u64 s_u[K5_THREADS / 32][8];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (t == 0) s_err = *(volatile int *)&st->err;
@@ -895,14 +994,24 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
     u128 nw = 0;
     i128 ann = 0;
     long long ndet = 0, rej = 0, sp = 0, att = 0;
-    double en = 0.0;
+    double en = 0.0, tn = 0.0, td = 0.0;
+    const bool trial = I.trial_bits != 0;
     for (int u = t; u < nbk; u += K5_THREADS) {
         const Partial &P = I.part[u];
+        if (trial) {
+            tn = tn + P.t_num;
+            td = td + P.t_den;
+        }
         nw += ((u128)P.nw_hi << 64) | P.nw_lo;
         ann += (i128)(((u128)P.ann_hi << 64) | P.ann_lo);
         ndet += P.ndet; rej += P.rejected; sp += P.spawns; att += P.attempts;
         en = en + P.e_num;
     }
+    if (trial)
+        for (int mm = 16; mm >= 1; mm >>= 1) {
+            tn = tn + __shfl_xor_sync(0xffffffffu, tn, mm);
+            td = td + __shfl_xor_sync(0xffffffffu, td, mm);
+        }
     for (int mm = 16; mm >= 1; mm >>= 1) {
         en = en + __shfl_xor_sync(0xffffffffu, en, mm);
         ndet += __shfl_xor_sync(0xffffffffu, ndet, mm);
@@ -914,18 +1023,24 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
     }
     if (lane == 0) {
         s_d[warp] = en;
+        s_t[warp][0] = tn;
+        s_t[warp][1] = td;
         s_u[warp][0] = (u64)nw; s_u[warp][1] = (u64)(nw >> 64);
         s_u[warp][2] = (u64)ann; s_u[warp][3] = (u64)((u128)ann >> 64);
         s_u[warp][4] = (u64)ndet; s_u[warp][5] = (u64)rej; s_u[warp][6] = (u64)sp; s_u[warp][7] = (u64)att;
     }
     __syncthreads();
     if (t != 0) return;
-    double e_num = 0.0;
+    double e_num = 0.0, t_num = 0.0, t_den = 0.0;
     u128 W = 0;
     i128 A = 0;
     long long nd = 0, rj = 0, sps = 0, at = 0;
     for (int k = 0; k < K5_THREADS / 32; k++) {
         e_num = e_num + s_d[k];
+        if (trial) {
+            t_num = t_num + s_t[k][0];
+            t_den = t_den + s_t[k][1];
+        }
         W += ((u128)s_u[k][1] << 64) | s_u[k][0];
         A += (i128)(((u128)s_u[k][3] << 64) | s_u[k][2]);
         nd += (long long)s_u[k][4]; rj += (long long)s_u[k][5]; sps += (long long)s_u[k][6]; at += (long long)s_u[k][7];
@@ -952,12 +1067,16 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
     R.iteration = it; R.nw = nwd; R.shift = st->S; R.e_num = e_num; R.e_den = st->e_den;
     R.ndet = nd; R.attempts = at; R.spawns = sps; R.rejected = rj;
     R.annihilated = i128_to_double(A) * 0x1p-32; R.vary = st->vary; R.pad0 = 0;
+    R.trial_num = t_num; R.trial_den = t_den;
     st->iter = it + 1;
     st->parity ^= 1;
     st->heavy_n = 0;
     st->big_n = 0;
+    st->new_n = 0;
     if (I.semi_size > 0 && !st->semi_built && st->vary && it + 1 == st->shift_start + I.semi_start)
         st->err |= ERRB_PAUSE_SEMI;
+    if (I.trial_size > 0 && !st->trial_built && st->vary && it + 1 == st->shift_start + I.trial_start)
+        st->err |= ERRB_PAUSE_TRIAL;
     if (it + 1 >= st->stop_iter) st->err |= ERRB_STOP;
 }
 
@@ -1138,6 +1257,37 @@ void launch_annihilate_big(const DevInst *dinst, int n_inst, cudaStream_t s)
 void launch_finalize(const DevInst *dinst, int n_inst, cudaStream_t s)
 {
     k_finalize<<<n_inst, K5_THREADS, 0, s>>>(dinst, n_inst);
+}
+
+// H_jj - E_ref of the determinants created in this iteration (new list,
+// parity ^ 1), two per warp
+__global__ void __launch_bounds__(256) k_new_diag(const DevInst *__restrict__ insts, int n_inst)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarp = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int ii = 0; ii < n_inst; ii++) {
+        const DevInst &I = insts[ii];
+        if (*(volatile int *)&I.st->err) continue;
+        const int nn = I.st->new_n, np = I.st->parity ^ 1;
+        const ulonglong2 *nkey = I.key[np];
+        double *nhd = I.hd[np];
+        for (int q = 2 * gw; q < nn; q += 2 * nwarp) {
+            const unsigned d0 = I.newdet[q], d1 = q + 1 < nn ? I.newdet[q + 1] : d0;
+            const ulonglong2 k0 = nkey[d0], k1 = nkey[d1];
+            const u64 ka[2] = {k0.x, k1.x}, kb[2] = {k0.y, k1.y};
+            double hdv[2];
+            diag_exact_warp_multi<2>(I, ka, kb, hdv);
+            if (lane == 0) {
+                nhd[d0] = hdv[0];
+                if (q + 1 < nn) nhd[d1] = hdv[1];
+            }
+        }
+    }
+}
+
+void launch_new_diag(const DevInst *dinst, int n_inst, cudaStream_t s)
+{
+    k_new_diag<<<num_sms() * 8, 256, 0, s>>>(dinst, n_inst);
 }
 
 void launch_rebucket(const DevInst *src, const DevInst *dst, int nb_src, int parity, cudaStream_t s)
