@@ -46,7 +46,8 @@ class Stat(C.Structure):
     _fields_ = [("iter", C.c_int64), ("nw", C.c_double), ("S", C.c_double), ("e_num", C.c_double),
                 ("e_den", C.c_double), ("ndet", C.c_int64), ("attempts", C.c_int64),
                 ("spawns", C.c_int64), ("rejected", C.c_int64), ("annihilated", C.c_double),
-                ("vary", C.c_int), ("t_num", C.c_double), ("t_den", C.c_double)]
+                ("vary", C.c_int), ("t_num", C.c_double), ("t_den", C.c_double),
+                ("x_overlap", C.c_double), ("x_var_num", C.c_double), ("x_pt2", C.c_double)]
 
 
 class Params(C.Structure):
@@ -55,13 +56,13 @@ class Params(C.Structure):
                 ("initiator_threshold", C.c_double), ("c_min", C.c_double), ("p_single", C.c_double),
                 ("shift_interval", C.c_int64), ("seed", C.c_uint64),
                 ("semistoch_size", C.c_int64), ("semistoch_start", C.c_int64), ("generator", C.c_int64),
-                ("trial_size", C.c_int64), ("trial_start", C.c_int64)]
+                ("trial_size", C.c_int64), ("trial_start", C.c_int64), ("replica", C.c_int64)]
 
 
 DEFAULT_PARAMS = dict(tau=0.01, shift_damping=0.1, target_walkers=1e4, initial_walkers=10.0,
                       initial_shift=0.0, initiator_threshold=0.0, c_min=1.0, p_single=0.1,
                       shift_interval=10, seed=1, semistoch_size=0, semistoch_start=100,
-                      generator=0, trial_size=0, trial_start=100)
+                      generator=0, trial_size=0, trial_start=100, replica=0)
 
 CLASSES = ("single_a", "single_b", "double_ab", "double_aa", "double_bb", "hop")
 
@@ -107,6 +108,7 @@ def lib():
                 "orc_pchb_table": (I32, [P, I32, I32, I32, dp, dp, dp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                          C.POINTER(C.c_int32), dp]),
                 "orc_trial_info": (I64, [P, C.POINTER(C.c_int64), dp, up, up, dp]),
+                "orc_pair_step": (I32, [P, P, I64]),
                 "orc_jacobi_lowest": (I32, [I32, dp, dp, dp]),
             }
             for name, (res, args) in sig.items():
@@ -370,6 +372,22 @@ class Run:
             lib().orc_stats(self.h, 0, n, arr)
         cols = {f: np.array([getattr(arr[i], f) for i in range(n)]) for f, _ in Stat._fields_}
         return cols
+
+
+class Pair:
+    """Two replicas (Philox key word 1 = 0 and 1) of one system stepped
+    together; the first replica's statistics rows carry the cross estimators
+    x_overlap, x_var_num and x_pt2."""
+
+    def __init__(self, system, **params):
+        params = dict(params)
+        params.pop("replica", None)
+        self.r = [Run(system, replica=0, **params), Run(system, replica=1, **params)]
+
+    def step(self, n):
+        e = lib().orc_pair_step(self.r[0].h, self.r[1].h, int(n))
+        if e:
+            raise RuntimeError("oracle pair step failed with code %d" % e)
 
 
 def jacobi_lowest(A):

@@ -77,11 +77,13 @@ void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t ou
 
 enum { PURPOSE_SPAWN = 1, PURPOSE_DEATH = 2, PURPOSE_ANNIH = 3 };
 
-static void draw(uint64_t seed, uint64_t a, uint64_t b, int64_t iter, uint64_t slot,
+/* one Philox block; the key's second word is the replica index (0 for a
+ * single run), so that replicas draw independent streams */
+static void draw(uint64_t seed, uint64_t replica, uint64_t a, uint64_t b, int64_t iter, uint64_t slot,
                  int purpose, uint64_t w[4])
 {
     uint64_t ctr[4] = { a, b, (uint64_t)iter, (slot << 8) | (uint64_t)purpose };
-    uint64_t key[2] = { seed, 0 };
+    uint64_t key[2] = { seed, replica };
     orc_philox4x64_10(ctr, key, w);
 }
 
@@ -520,6 +522,7 @@ typedef struct {
     int64_t semistoch_size, semistoch_start;
     int64_t generator; /* 0: uniform doubles, 1: pre-computed heat-bath doubles (App. A) */
     int64_t trial_size, trial_start; /* trial space T of the E_Trial estimator (Sec. IV) */
+    int64_t replica;                 /* replica index: second word of the Philox key */
 } orc_params;
 
 typedef struct { uint64_t a, b; double c, hd; int flags; } odet; /* flags: 1 ref, 2 in D */
@@ -532,6 +535,9 @@ typedef struct {
     double annihilated;
     int vary;
     double t_num, t_den; /* E_Trial: <Psi^T|H - E_ref|Psi>, <Psi^T|Psi> after the iteration */
+    /* replica pair (Sec. V, VI), filled in the first replica's row:
+     * <Psi^1|Psi^2>, the variational numerator and the PT2 numerator */
+    double x_overlap, x_var_num, x_pt2;
 } orc_stat;
 
 /* Pre-computed heat-bath tables (App. A, "Pre-computed heat-bath sampling",
@@ -582,6 +588,12 @@ typedef struct {
     int64_t nt, nwt;
     uint64_t *Ta, *Tb, *Wa, *Wb;
     double *cT, *W, ET;
+    /* the last iteration's start list and spawns, kept for a replica pair */
+    int keep_last;
+    odet *L0;
+    int64_t n0;
+    ospawn *sp0;
+    int64_t ns0;
 } orc_run;
 
 static int cmp_key(uint64_t a1, uint64_t b1, uint64_t a2, uint64_t b2)
@@ -826,6 +838,7 @@ void orc_destroy(orc_run *r)
     if (!r) return;
     free(r->L); free(r->Da); free(r->Db); free(r->rowptr); free(r->col); free(r->val); free(r->st);
     free(r->Ta); free(r->Tb); free(r->cT); free(r->Wa); free(r->Wb); free(r->W);
+    free(r->L0); free(r->sp0);
     pchb_free(r);
     free(r);
 }
@@ -1100,6 +1113,13 @@ static int one_iteration(orc_run *r)
     if (P->trial_size > 0 && r->nt == 0 && r->vary && it == r->shift_start + P->trial_start)
         build_T(r);
 
+    if (r->keep_last) {
+        free(r->L0);
+        r->L0 = malloc(sizeof(odet) * (r->n ? r->n : 1));
+        memcpy(r->L0, r->L, sizeof(odet) * r->n);
+        r->n0 = r->n;
+    }
+
     /* (a) spawning from the start-of-iteration amplitudes */
     int64_t ns = 0, scap = 1024, attempts = 0;
     ospawn *sp = malloc(sizeof(ospawn) * scap);
@@ -1114,7 +1134,7 @@ static int one_iteration(orc_run *r)
         double cper = d->c / (double)nat;
         for (uint64_t k = 0; k < nat; k++) {
             uint64_t w[4], ta, tb;
-            draw(P->seed, d->a, d->b, it, k, PURPOSE_SPAWN, w);
+            draw(P->seed, (uint64_t)P->replica, d->a, d->b, it, k, PURPOSE_SPAWN, w);
             double ws;
             if (r->pchb_ab && !(u53(w[0]) < P->p_single)) {
                 /* heat-bath double: |H| / p_gen = lam for every entry, so the
@@ -1168,7 +1188,7 @@ static int one_iteration(orc_run *r)
         double cp = d->c * f;
         if (cp != 0.0 && fabs(cp) < cmin) {
             uint64_t w[4];
-            draw(P->seed, d->a, d->b, it, 0, PURPOSE_DEATH, w);
+            draw(P->seed, (uint64_t)P->replica, d->a, d->b, it, 0, PURPOSE_DEATH, w);
             cp = round_stoch(cp, cmin, u53(w[0]));
         }
         d->c = cp;
@@ -1177,6 +1197,12 @@ static int one_iteration(orc_run *r)
 
     /* (c) annihilation with the initiator rule */
     qsort(sp, ns, sizeof(ospawn), cmp_ospawn);
+    if (r->keep_last) {
+        free(r->sp0);
+        r->sp0 = malloc(sizeof(ospawn) * (ns ? ns : 1));
+        memcpy(r->sp0, sp, sizeof(ospawn) * ns);
+        r->ns0 = ns;
+    }
     int64_t outcap = r->n + ns + 1, no = 0, rejected = 0;
     odet *out = malloc(sizeof(odet) * outcap);
     i128 ann = 0;
@@ -1210,7 +1236,7 @@ static int one_iteration(orc_run *r)
                 ann += in - (i128)fx32(acc);
                 if (!(d.flags & 2) && acc != 0.0 && fabs(acc) < cmin) {
                     uint64_t w[4];
-                    draw(P->seed, d.a, d.b, it, 0, PURPOSE_ANNIH, w);
+                    draw(P->seed, (uint64_t)P->replica, d.a, d.b, it, 0, PURPOSE_ANNIH, w);
                     acc = round_stoch(acc, cmin, u53(w[0]));
                 }
             }
@@ -1273,6 +1299,107 @@ int orc_step(orc_run *r, int64_t n)
     for (int64_t k = 0; k < n; k++) {
         int e = one_iteration(r);
         if (e) { r->err = e; return e; }
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------- replicas
+ * Two runs of the same system with replica indices 0 and 1 advance together
+ * (Sec. V: two independent walker distributions).  After every iteration the
+ * first run's row receives, over every determinant j in either start list or
+ * spawned onto in either run (C^r_j: amplitude at the start of the iteration;
+ * S^r_j = RN(accepted spawns onto j) + RN(rejected spawns onto j), each an
+ * exact sum rounded once; R^r_j = RN(rejected spawns onto j), the spawns
+ * removed by the initiator rule):
+ *   x_overlap = sum_j C^1_j C^2_j                                  <Psi^1|Psi^2>
+ *   x_var_num = sum_j (C^1_j (H_jj - E_ref)) C^2_j - (sum_j (C^1_j S^2_j + C^2_j S^1_j)) / (2 tau)
+ *               (an unbiased estimate of <Psi^1|H - E_ref|Psi^2>: a spawn
+ *               from D_i onto D_j has expectation -tau H_ji C_i)
+ *   x_pt2     = (sum over j with R^1_j != 0 and R^2_j != 0 of
+ *               (R^1_j R^2_j) / (E_0 - (H_jj - E_ref))) / tau^2      (Sec. VI, Eq. of Delta E_2)
+ * with E_0 = (S^1 + S^2) / 2, the replicas' shifts at the start of the
+ * iteration (relative to E_ref); sums in ascending key order. */
+typedef struct { uint64_t a, b; double c0, hd, sacc, srej; int has_hd; } oside;
+
+static int cmp_oside(const void *x, const void *y)
+{
+    const oside *p = x, *q = y;
+    return cmp_key(p->a, p->b, q->a, q->b);
+}
+
+/* per determinant of one run's last iteration: C at start, H_jj - E_ref if it
+ * was occupied, accepted and rejected spawn sums (sorted by key) */
+static int64_t side_list(const orc_run *r, oside **out)
+{
+    int64_t cap = r->n0 + r->ns0 + 1, n = 0;
+    oside *v = malloc(sizeof(oside) * cap);
+    int64_t li = 0, si = 0;
+    while (li < r->n0 || si < r->ns0) {
+        int c;
+        if (li >= r->n0) c = 1;
+        else if (si >= r->ns0) c = -1;
+        else c = cmp_key(r->L0[li].a, r->L0[li].b, r->sp0[si].a, r->sp0[si].b);
+        oside e;
+        memset(&e, 0, sizeof e);
+        int occ = 0;
+        if (c <= 0) {
+            e.a = r->L0[li].a; e.b = r->L0[li].b; e.c0 = r->L0[li].c; e.hd = r->L0[li].hd; e.has_hd = 1;
+            occ = e.c0 != 0.0;
+            li++;
+        } else {
+            e.a = r->sp0[si].a; e.b = r->sp0[si].b;
+        }
+        if (c >= 0) {
+            xacc xa, xr;
+            xacc_zero(&xa);
+            xacc_zero(&xr);
+            while (si < r->ns0 && r->sp0[si].a == e.a && r->sp0[si].b == e.b) {
+                if (r->sp0[si].init || occ) xacc_add(&xa, r->sp0[si].w, 0);
+                else xacc_add(&xr, r->sp0[si].w, 0);
+                si++;
+            }
+            e.sacc = xacc_round(&xa);
+            e.srej = xacc_round(&xr);
+        }
+        v[n++] = e;
+    }
+    *out = v;
+    return n;
+}
+
+int orc_pair_step(orc_run *r0, orc_run *r1, int64_t n)
+{
+    r0->keep_last = 1;
+    r1->keep_last = 1;
+    for (int64_t k = 0; k < n; k++) {
+        const double e0 = (r0->S + r1->S) / 2.0;
+        int e = one_iteration(r0);
+        if (!e) e = one_iteration(r1);
+        if (e) { r0->err = r1->err = e; return e; }
+        oside *v0, *v1;
+        int64_t n0 = side_list(r0, &v0), n1 = side_list(r1, &v1);
+        double ov = 0.0, hdg = 0.0, cross = 0.0, pt2 = 0.0;
+        int64_t i = 0, j = 0;
+        while (i < n0 && j < n1) {
+            int c = cmp_key(v0[i].a, v0[i].b, v1[j].a, v1[j].b);
+            if (c < 0) { i++; continue; }
+            if (c > 0) { j++; continue; }
+            const oside *p = &v0[i], *q = &v1[j];
+            ov = ov + p->c0 * q->c0;
+            if (p->c0 != 0.0 && q->c0 != 0.0) hdg = hdg + (p->c0 * p->hd) * q->c0;
+            cross = cross + (p->c0 * (q->sacc + q->srej) + q->c0 * (p->sacc + p->srej));
+            if (p->srej != 0.0 && q->srej != 0.0) {
+                double hd = p->has_hd ? p->hd : (q->has_hd ? q->hd : orc_hdiag_rel(r0->s, p->a, p->b));
+                pt2 = pt2 + (p->srej * q->srej) / (e0 - hd);
+            }
+            i++; j++;
+        }
+        free(v0); free(v1);
+        const double tau = r0->p.tau;
+        orc_stat *t = &r0->st[r0->nst - 1];
+        t->x_overlap = ov;
+        t->x_var_num = hdg - cross / (2.0 * tau);
+        t->x_pt2 = pt2 / (tau * tau);
     }
     return 0;
 }

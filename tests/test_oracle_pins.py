@@ -570,3 +570,76 @@ def test_trial_space_equal_to_fci_space_gives_exact_energy():
     sel = st["t_den"] != 0.0
     assert sel.sum() > 30
     np.testing.assert_allclose(st["t_num"][sel] / st["t_den"][sel], e0, rtol=0, atol=1e-9)
+
+
+# ---------------------------------------------------------------- replicas and PT2 (Sec. V, VI)
+def test_replica_zero_is_the_single_run_and_replica_one_differs():
+    sysd = workloads.small_abinitio(7, 3, 2, seed=8)
+    p = dict(tau=0.004, target_walkers=1500, initial_walkers=200.0, initiator_threshold=2.0, seed=5)
+    s = oracle.system_from_workload(sysd)
+    a, b, c = oracle.Run(s, **p), oracle.Run(s, replica=0, **p), oracle.Run(s, replica=1, **p)
+    for r in (a, b, c):
+        r.step(40)
+    ea, eb, ec = a.export(), b.export(), c.export()
+    assert np.array_equal(ea["c"].view(np.uint64), eb["c"].view(np.uint64))
+    assert ea["c"].size != ec["c"].size or not np.array_equal(ea["c"], ec["c"])
+
+
+def _pair_start(seed):
+    """Both replicas start from the same list: the 20 largest components of
+    the exact ground state, scaled so that some are initiators (|C| > 40) and
+    most are not; C_min = 0.05 keeps most spawns unrounded."""
+    sysd = workloads.small_abinitio(6, 2, 2, n_chol=2, seed=5)
+    s = oracle.system_from_workload(sysd)
+    e0, v, dets = s.exact_ground_state()
+    top = np.argsort(-np.abs(v))[:20]
+    c = np.round(60.0 * v[top] / np.abs(v[top[0]]) * np.sign(v[top[0]]))
+    c[c == 0] = 1.0
+    keys = [dets[k] for k in top]
+    params = dict(tau=0.01, target_walkers=1e9, initial_walkers=10.0, initiator_threshold=40.0, c_min=0.05,
+                  seed=seed)
+    pair = oracle.Pair(s, **params)
+    for r in pair.r:
+        r.import_state([k[0] for k in keys], [k[1] for k in keys], c, 10, -0.2, vary=0)
+    return s, pair, keys, c
+
+
+def test_pair_overlap_is_the_start_overlap():
+    s, pair, keys, c = _pair_start(1)
+    pair.step(1)
+    row = {k: v[-1] for k, v in pair.r[0].stats().items()}
+    assert row["x_overlap"] == math.fsum(c * c) or abs(row["x_overlap"] - float(c @ c)) < 1e-12 * float(c @ c)
+    assert {k: v[-1] for k, v in pair.r[1].stats().items()}["x_overlap"] == 0.0
+
+
+def test_pair_variational_and_pt2_numerators_are_unbiased():
+    """Averaged over independent seeds, x_var_num estimates C (H - E_ref) C of
+    the common start vector, and x_pt2 estimates
+    sum_j (sum_{i non-initiator} H_ji C_i)^2 / (E_0 - (H_jj - E_ref)) over the
+    unoccupied j (the replicas' rejected spawns are independent, each with
+    expectation -tau sum_i H_ji C_i)."""
+    s, _, keys, c = _pair_start(0)
+    dets, H = s.hamiltonian()
+    idx = {d: k for k, d in enumerate(dets)}
+    cv = np.zeros(len(dets))
+    for k, x in zip(keys, c):
+        cv[idx[k]] = x
+    exact_var = float(cv @ H @ cv)
+    non_init = np.where((np.abs(cv) <= 40.0) & (cv != 0.0), cv, 0.0)
+    ref = idx[s.ref]
+    non_init[ref] = 0.0  # the reference is always an initiator
+    Hoff = H - np.diag(np.diag(H))
+    g = Hoff @ non_init
+    unocc = cv == 0.0
+    exact_pt2 = float(np.sum((g[unocc] ** 2) / (-0.2 - np.diag(H)[unocc])))
+    var, pt2 = [], []
+    for seed in range(1, 401):
+        _, pair, _, _ = _pair_start(seed)
+        pair.step(1)
+        row = {k: v[-1] for k, v in pair.r[0].stats().items()}
+        var.append(row["x_var_num"])
+        pt2.append(row["x_pt2"])
+    var, pt2 = np.array(var), np.array(pt2)
+    assert abs(var.mean() - exact_var) < 4.0 * var.std() / math.sqrt(var.size) + 1e-9
+    assert abs(pt2.mean() - exact_pt2) < 4.0 * pt2.std() / math.sqrt(pt2.size) + 1e-9
+    assert np.count_nonzero(pt2) > 50  # the estimator is exercised
