@@ -1318,7 +1318,9 @@ int orc_step(orc_run *r, int64_t n)
  *   x_pt2     = (sum over j with R^1_j != 0 and R^2_j != 0 of
  *               (R^1_j R^2_j) / (E_0 - (H_jj - E_ref))) / tau^2      (Sec. VI, Eq. of Delta E_2)
  * with E_0 = (S^1 + S^2) / 2, the replicas' shifts at the start of the
- * iteration (relative to E_ref); sums in ascending key order. */
+ * iteration (relative to E_ref); a term with E_0 = H_jj - E_ref (possible
+ * before the shift has moved, e.g. lattice models with integer diagonals) is
+ * undefined and left out; sums in ascending key order. */
 typedef struct { uint64_t a, b; double c0, hd, sacc, srej; int has_hd; } oside;
 
 static int cmp_oside(const void *x, const void *y)
@@ -1390,7 +1392,7 @@ int orc_pair_step(orc_run *r0, orc_run *r1, int64_t n)
             cross = cross + (p->c0 * (q->sacc + q->srej) + q->c0 * (p->sacc + p->srej));
             if (p->srej != 0.0 && q->srej != 0.0) {
                 double hd = p->has_hd ? p->hd : (q->has_hd ? q->hd : orc_hdiag_rel(r0->s, p->a, p->b));
-                pt2 = pt2 + (p->srej * q->srej) / (e0 - hd);
+                if (e0 - hd != 0.0) pt2 = pt2 + (p->srej * q->srej) / (e0 - hd); /* undefined term left out */
             }
             i++; j++;
         }
