@@ -228,8 +228,11 @@ def run_serving(args):
             if sysd["kind"] == "abinitio":
                 h1, eri = workloads.synthetic_abinitio(sysd["norb"], sysd["n_chol"], sysd["integral_seed"])
                 sysd = dict(sysd, h1=h1, eri=eri, ecore=0.0)
+            # a 32-determinant trial space (Sec. IV) gives E_Trial, whose error is
+            # far below E_proj's when the reference carries little weight
             prm = dict(tau=0.0, target_walkers=r["target_walkers"], initial_walkers=min(r["target_walkers"], 1e3),
-                       initiator_threshold=3.0, seed=r["seed"], shift_damping=0.5, shift_interval=5)
+                       initiator_threshold=3.0, seed=r["seed"], shift_damping=0.5, shift_interval=5,
+                       trial_size=32, trial_start=50)
             ids[r["id"]] = fq.fciqmc_server_submit(srv, sysd, prm, target_sigma=1e-3, max_iters=args.max_iters)
         active = fq.fciqmc_server_tick(srv, 50) if ids else 0
         if not active and pending:
@@ -239,14 +242,16 @@ def run_serving(args):
     lat = np.array([s["t_done"] - s["t_submit"] for s in st])
     att = float(sum(s["attempts"] for s in st))
     conv = sum(1 for s in st if s["state_name"] == "converged")
+    by_trial = sum(1 for s in st if s["state_name"] == "converged" and s["estimator"] == 1)
     return {"metric": METRIC, "value": float(np.percentile(lat, 50)), "unit": "s (p50 time to answer)",
             "higher_is_better": False, "n_gpus": 1, "steps": len(reqs), "warmup": 0, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "requests": len(reqs), "converged": conv, "capped": len(reqs) - conv,
+            "requests": len(reqs), "converged": conv, "converged_by_trial_estimator": by_trial,
+            "capped": len(reqs) - conv,
             "requests_per_s": len(reqs) / t_end, "attempts_per_s": att / t_end,
             "config": {"workload": "serving stream: Poisson 20/s, 1D/2D Hubbard 8-18 sites and ab initio 16-40 "
-                                   "orbitals, targets 1e4..1e7, to sigma(E_proj) < 1 mEh",
+                                   "orbitals, targets 1e4..1e7, to sigma(E) < 1 mEh (E_proj or E_Trial, N_T = 32)",
                        "max_iters": args.max_iters, "tau": "0.5/sum_j|H_ref,j| per request"}}
 
 

@@ -96,6 +96,11 @@ typedef struct {
  * (at most 1024) largest |C| (ties: ascending key), Psi^T = the lowest
  * eigenvector of H projected into T (Jacobi rotations on the device), and
  * every later iteration accumulates <Psi^T|H - E_ref|Psi> and <Psi^T|Psi>.
+ * replicas = 2: two independent runs of the same system (the second draws
+ * with Philox key word 1 = 1), stepped together in lockstep with one bucket
+ * layout; fciqmc_step and fciqmc_energy on the first handle drive and report
+ * both (the variational-energy and PT2 estimators of fciqmc_stats), and
+ * fciqmc_replica gives the second for read-only queries.
  * generator: how double excitations are proposed (App. A).  0: uniformly
  * (electron pair, then hole pair).  1: pre-computed heat-bath sampling
  * (App. A, p(ab|ij) proportional to |H_ij^ab|): one Walker alias table per
@@ -124,7 +129,7 @@ typedef struct {
     void (*free)(void *ptr, void *ctx);
     void *alloc_ctx;
     int32_t generator;
-    int32_t pad0;
+    int32_t replicas;    /* 1 (or 0): one run; 2: a replica pair (Sec. V) */
     int64_t trial_size;  /* N_T of the trial-wave-function estimator (0 = off) */
     int64_t trial_start; /* iterations after the shift starts to vary at which T is chosen */
 } fciqmc_params;
@@ -150,6 +155,16 @@ typedef struct {
     int32_t pad0;
     double trial_num; /* <Psi^T|H - E_ref|Psi> after the iteration (0 before T exists) */
     double trial_den; /* <Psi^T|Psi> */
+    /* replica pair (first replica's rows; 0 otherwise), from the amplitudes C^r
+     * at the start of the iteration and the spawns S^r of the iteration:
+     * x_overlap = sum_j C^1_j C^2_j; x_var_num = sum_j C^1_j (H_jj - E_ref) C^2_j
+     * - sum_j (C^1_j S^2_j + C^2_j S^1_j) / (2 tau), an estimate of
+     * <Psi^1|H - E_ref|Psi^2>; x_pt2 = sum_j R^1_j R^2_j / (E_0 - H_jj + E_ref) / tau^2
+     * over determinants whose spawns R^r were removed by the initiator rule in
+     * both replicas (Sec. VI), E_0 the mean of the shifts */
+    double x_overlap;
+    double x_var_num;
+    double x_pt2;
 } fciqmc_iter_stats;
 
 /* Summary returned by fciqmc_energy.  Energies are absolute (E_ref added).
@@ -183,6 +198,16 @@ typedef struct {
     double e_trial_sigma;
     double e_trial_T;
     int64_t trial_samples;
+    /* replica pair (first replica only; NaN otherwise): variational energy
+     * E_var = E_ref + mean(x_var_num) / mean(x_overlap) and the PT2 correction
+     * mean(x_pt2) / mean(x_overlap) (Sec. VI; the replicas are not normalised,
+     * so both are divided by <Psi^1|Psi^2>), each with a blocking error, over
+     * iterations from 500 after the later of the two shift starts */
+    double e_var_mean;
+    double e_var_sigma;
+    double pt2_mean;
+    double pt2_sigma;
+    int64_t pair_samples;
 } fciqmc_stats;
 
 typedef struct fciqmc_handle fciqmc_handle;
@@ -224,8 +249,14 @@ void *fciqmc_stream(fciqmc_handle *h);
 /* Fills *out from the iteration history (host-side statistics). */
 int fciqmc_energy(fciqmc_handle *h, fciqmc_stats *out);
 
-/* Frees all resources; NULL is allowed. */
+/* Frees all resources; NULL is allowed.  The second replica of a pair is
+ * released with the first (destroying it directly does nothing). */
 void fciqmc_destroy(fciqmc_handle *h);
+
+/* Replica r (0 or 1) of a pair created with replicas = 2 (r = 0 is h itself),
+ * for export, statistics and queries; NULL for other r or other handles.
+ * The second replica is stepped, and destroyed, through the first. */
+fciqmc_handle *fciqmc_replica(fciqmc_handle *h, int32_t r);
 
 /* Message of the last error on this handle (or of the last failed create
  * when h is NULL). */
@@ -330,15 +361,17 @@ int fciqmc_ref_offdiag_sum_noalloc(int32_t norb, int32_t n_alpha, int32_t n_beta
  * memory of running requests stays within mem_budget_bytes and at most
  * max_active run, advances all running requests together (one batched launch
  * per iteration, fciqmc_step_batch), and retires a request when the blocking
- * error of its projected energy is below target_sigma with at least 200
- * samples after equilibration, or after max_iters iterations.  Each result is
- * identical to running the request alone. */
+ * error of its energy is below target_sigma with at least 200 samples after
+ * equilibration, or after max_iters iterations.  The energy is the projected
+ * estimator E_proj, or E_Trial when the request asked for a trial space
+ * (trial_size > 0) and it has at least 200 samples with the smaller error.
+ * Each result is identical to running the request alone. */
 typedef struct fciqmc_server fciqmc_server;
 typedef struct {
     int32_t state;        /* 0 queued, 1 running, 2 converged, 3 stopped at max_iters, 4 failed */
     int32_t error;        /* status code of a failed request */
     int64_t iterations;
-    double energy;        /* E_proj mean (absolute) */
+    double energy;        /* energy mean (absolute): E_proj or E_Trial, see estimator */
     double sigma;         /* its blocking error */
     double shift;
     double t_submit;      /* seconds on the server's clock */
@@ -347,6 +380,8 @@ typedef struct {
     int64_t attempts;
     int64_t device_bytes; /* peak device memory of the run */
     double tau;
+    int32_t estimator;    /* 0: E_proj (Eq. (9)), 1: E_Trial (Sec. IV) */
+    int32_t pad0;
 } fciqmc_request_status;
 
 int fciqmc_server_create(int64_t mem_budget_bytes, int32_t max_active, void *stream, fciqmc_server **out);

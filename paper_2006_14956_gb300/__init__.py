@@ -64,14 +64,15 @@ class fciqmc_params(C.Structure):
                 ("shift_interval", C.c_int64), ("seed", C.c_uint64), ("semistoch_size", C.c_int64),
                 ("semistoch_start", C.c_int64), ("max_dets", C.c_int64), ("max_spawns", C.c_int64),
                 ("max_device_bytes", C.c_int64), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
-                ("generator", C.c_int32), ("pad0", C.c_int32), ("trial_size", C.c_int64), ("trial_start", C.c_int64)]
+                ("generator", C.c_int32), ("replicas", C.c_int32), ("trial_size", C.c_int64), ("trial_start", C.c_int64)]
 
 
 class fciqmc_iter_stats(C.Structure):
     _fields_ = [("iteration", C.c_int64), ("nw", C.c_double), ("shift", C.c_double), ("e_num", C.c_double),
                 ("e_den", C.c_double), ("ndet", C.c_int64), ("attempts", C.c_int64), ("spawns", C.c_int64),
                 ("rejected", C.c_int64), ("annihilated", C.c_double), ("vary", C.c_int32), ("pad0", C.c_int32),
-                ("trial_num", C.c_double), ("trial_den", C.c_double)]
+                ("trial_num", C.c_double), ("trial_den", C.c_double), ("x_overlap", C.c_double),
+                ("x_var_num", C.c_double), ("x_pt2", C.c_double)]
 
 
 class fciqmc_stats(C.Structure):
@@ -81,13 +82,16 @@ class fciqmc_stats(C.Structure):
                 ("equil_start", C.c_int64), ("n_samples", C.c_int64), ("attempts_total", C.c_int64),
                 ("spawns_total", C.c_int64), ("rejected_total", C.c_int64), ("annihilated_total", C.c_double),
                 ("vary", C.c_int32), ("pad0", C.c_int32), ("e_trial_mean", C.c_double),
-                ("e_trial_sigma", C.c_double), ("e_trial_T", C.c_double), ("trial_samples", C.c_int64)]
+                ("e_trial_sigma", C.c_double), ("e_trial_T", C.c_double), ("trial_samples", C.c_int64),
+                ("e_var_mean", C.c_double), ("e_var_sigma", C.c_double), ("pt2_mean", C.c_double),
+                ("pt2_sigma", C.c_double), ("pair_samples", C.c_int64)]
 
 
 class fciqmc_request_status(C.Structure):
     _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("iterations", C.c_int64), ("energy", C.c_double),
                 ("sigma", C.c_double), ("shift", C.c_double), ("t_submit", C.c_double), ("t_start", C.c_double),
-                ("t_done", C.c_double), ("attempts", C.c_int64), ("device_bytes", C.c_int64), ("tau", C.c_double)]
+                ("t_done", C.c_double), ("attempts", C.c_int64), ("device_bytes", C.c_int64), ("tau", C.c_double),
+                ("estimator", C.c_int32), ("pad0", C.c_int32)]
 
 
 REQUEST_STATES = {0: "queued", 1: "running", 2: "converged", 3: "max_iters", 4: "failed"}
@@ -119,6 +123,7 @@ _SIGS = {
     "fciqmc_layout": (C.c_int, [_H, C.POINTER(C.c_int64)]),
     "fciqmc_ref_offdiag_sum": (C.c_int, [_H, _dp]),
     "fciqmc_tau": (C.c_double, [_H]),
+    "fciqmc_replica": (C.c_void_p, [_H, C.c_int32]),
     "fciqmc_trial_info": (C.c_int64, [_H, C.POINTER(C.c_int64), _dp, _u64p, _u64p, _dp, C.c_int64]),
     "fciqmc_pchb_table": (C.c_int64, [_H, C.c_int32, C.c_int32, C.c_int32, _dp, _dp, _u64p,
                                       C.POINTER(C.c_uint32), C.c_int64]),
@@ -211,7 +216,7 @@ def _system_struct(system):
 
 DEFAULTS = dict(tau=0.01, shift_damping=0.1, target_walkers=1e4, initial_walkers=10.0, initial_shift=0.0,
                 initiator_threshold=0.0, c_min=1.0, p_single=0.1, shift_interval=10, seed=1, semistoch_size=0,
-                semistoch_start=100, max_dets=0, max_spawns=0, max_device_bytes=0, generator=0, trial_size=0, trial_start=100)
+                semistoch_start=100, max_dets=0, max_spawns=0, max_device_bytes=0, generator=0, replicas=1, trial_size=0, trial_start=100)
 
 
 def _params_struct(params):
@@ -255,6 +260,14 @@ class Handle:
         if getattr(self, "h", None):
             _lib.fciqmc_destroy(self.h)
             self.h = None
+
+
+class _Replica:
+    """A replica owned by its pair's first handle (kept alive through it; the
+    library releases it together with the first)."""
+
+    def __init__(self, h, parent):
+        self.h, self._parent = h, parent
 
 
 def fciqmc_destroy(handle):
@@ -374,6 +387,16 @@ def fciqmc_ref_offdiag_sum_noalloc(norb, n_alpha, n_beta, d_h1, d_eri, ref_alpha
 
 def fciqmc_tau(handle):
     return _lib.fciqmc_tau(handle.h)
+
+
+def fciqmc_replica(handle, r):
+    """Replica r of a pair (a handle that the pair owns: do not destroy it), or None."""
+    p = _lib.fciqmc_replica(handle.h, int(r))
+    if not p:
+        return None
+    if int(r) == 0:
+        return handle
+    return _Replica(p, handle)
 
 
 def fciqmc_trial_info(handle):

@@ -71,6 +71,11 @@ struct fciqmc_handle {
     double trial_ET = 0.0;
     const ulonglong2 *trial_key = nullptr;
     const double *trial_cT = nullptr;
+    // replica pair: the other replica (owned by the first), replica index
+    fciqmc_handle *partner = nullptr;
+    bool secondary = false;
+    bool paired = false;
+    int side_nbk = 0;
     // asynchronous stepping
     bool pending = false;
     long long async_base = 0, async_target = 0;
@@ -346,6 +351,24 @@ static int grow_spawn_capacity(fciqmc_handle *h, long long need)
     return FCIQMC_OK;
 }
 
+// per-bucket determinant lists of a replica pair, sized for the current layout
+static int ensure_side(fciqmc_handle *h)
+{
+    if (!h->paired) return FCIQMC_OK;
+    DevInst &I = h->hi;
+    const int nbk = 1 << h->bb, cap = CAP_M + I.cap_s;
+    if (I.side && I.side_cap == cap && h->side_nbk == nbk) return FCIQMC_OK;
+    dev_free(h, I.side);
+    dev_free(h, I.side_cnt);
+    I.side = (SideEnt *)dev_alloc(h, (size_t)nbk * cap * sizeof(SideEnt));
+    I.side_cnt = (int *)dev_alloc(h, (size_t)nbk * sizeof(int));
+    if (!I.side || !I.side_cnt) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (replica lists)");
+    CUDA_TRY(h, cudaMemsetAsync(I.side_cnt, 0, (size_t)nbk * sizeof(int), h->stream));
+    I.side_cap = cap;
+    h->side_nbk = nbk;
+    return FCIQMC_OK;
+}
+
 static int grow_heavy(fciqmc_handle *h)
 {
     int ncap = h->heavy_cap * 4;
@@ -511,7 +534,8 @@ static int build_semistochastic(fciqmc_handle *h)
     u64 *dtab = (u64 *)dev_alloc(h, tabk.size() * sizeof(u64));
     double *dcn = (double *)dev_alloc(h, (size_t)nd * sizeof(double));
     double *dcc = (double *)dev_alloc(h, (size_t)nd * sizeof(double));
-    if (!dkey || !dtab || !dcn || !dcc) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (D)");
+    double *dcc2 = (double *)dev_alloc(h, (size_t)nd * sizeof(double));
+    if (!dkey || !dtab || !dcn || !dcc || !dcc2) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (D)");
     CUDA_TRY(h, cudaMemcpy(dkey, sel.data(), (size_t)nd * sizeof(ulonglong2), cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemcpy(dtab, tabk.data(), tabk.size() * sizeof(u64), cudaMemcpyHostToDevice));
     long long *rowptr = nullptr, nnz = 0;
@@ -519,7 +543,8 @@ static int build_semistochastic(fciqmc_handle *h)
     double *dval = nullptr;
     rcs = build_hsub(h, dkey, nd, &rowptr, &dcol, &dval, &nnz);
     if (rcs) return rcs;
-    I.nd = (int)nd; I.dkey = dkey; I.drow = rowptr; I.dcol = dcol; I.dval = dval; I.dc_new = dcn; I.dc_cur = dcc;
+    I.nd = (int)nd; I.dkey = dkey; I.drow = rowptr; I.dcol = dcol; I.dval = dval; I.dc_new = dcn;
+    I.dc_buf[0] = dcc; I.dc_buf[1] = dcc2;
     I.dhash_keys = dtab; I.dhash_bits = hb;
     int rc2 = upload_inst(h);
     if (rc2) return rc2;
@@ -606,7 +631,7 @@ extern "C" {
 
 const char *fciqmc_last_error(const fciqmc_handle *h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
-void fciqmc_destroy(fciqmc_handle *h)
+static void destroy_run(fciqmc_handle *h)
 {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
@@ -616,7 +641,23 @@ void fciqmc_destroy(fciqmc_handle *h)
     delete h;
 }
 
-int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_handle **out)
+// the second replica of a pair belongs to the first and is released with it
+void fciqmc_destroy(fciqmc_handle *h)
+{
+    if (!h || h->secondary) return;
+    if (h->partner) destroy_run(h->partner);
+    destroy_run(h);
+}
+
+fciqmc_handle *fciqmc_replica(fciqmc_handle *h, int32_t r)
+{
+    if (!h || h->secondary) return nullptr;
+    if (r == 0) return h;
+    if (r == 1) return h->partner;
+    return nullptr;
+}
+
+static int create_run(const fciqmc_system *sys, const fciqmc_params *prm, u64 replica, fciqmc_handle **out)
 {
     if (!out) return fail(nullptr, FCIQMC_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -774,6 +815,8 @@ int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_han
     h->eref = host_fixed_to_double(xref + host_fixed(h->ecore, F), F);
 
     DevInst &I = h->hi;
+    I.replica = replica;
+    I.partner = -1;
     I.kind = h->kind; I.norb = N; I.na = h->na; I.nb = h->nb; I.n = n; I.ma = N - h->na; I.mb = N - h->nb; I.z = h->z;
     I.F = F; I.Fw = Fw;
     I.ref_a = h->ref_a; I.ref_b = h->ref_b; I.normask = normask;
@@ -910,6 +953,42 @@ int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_han
     return FCIQMC_OK;
 }
 
+int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_handle **out)
+{
+    if (prm && (prm->replicas < 0 || prm->replicas > 2)) {
+        if (out) *out = nullptr;
+        return fail(nullptr, FCIQMC_ERR_INVALID_ARG, "replicas must be 1 or 2");
+    }
+    int rc = create_run(sys, prm, 0, out);
+    if (rc || prm->replicas != 2) return rc;
+    // the second replica: same system and parameters, Philox key word 1 = 1,
+    // on the first replica's stream
+    fciqmc_handle *h = *out, *h2 = nullptr;
+    fciqmc_params p2 = *prm;
+    p2.stream = h->stream;
+    rc = create_run(sys, &p2, 1, &h2);
+    if (rc) {
+        fciqmc_destroy(h);
+        *out = nullptr;
+        return rc;
+    }
+    h->partner = h2; h2->partner = h; h2->secondary = true;
+    h->paired = h2->paired = true;
+    rc = replica_kernel_init() == cudaSuccess ? FCIQMC_OK : fail(h, FCIQMC_ERR_CUDA, "replica kernel set-up failed");
+    if (!rc) rc = ensure_side(h);
+    if (!rc) rc = ensure_side(h2);
+    if (!rc) rc = upload_inst(h);
+    if (!rc) rc = upload_inst(h2);
+    if (!rc) rc = capture_graph(h);
+    if (!rc) rc = capture_graph(h2);
+    if (rc) {
+        g_create_error = h->err;
+        fciqmc_destroy(h);
+        *out = nullptr;
+    }
+    return rc;
+}
+
 int fciqmc_set_profiling(fciqmc_handle *h, int32_t on)
 {
     if (!h) return FCIQMC_ERR_INVALID_ARG;
@@ -936,6 +1015,11 @@ static int step_to(fciqmc_handle *h, long long target_iter);
 int fciqmc_step(fciqmc_handle *h, int64_t n_iter)
 {
     if (!h || n_iter < 0) return FCIQMC_ERR_INVALID_ARG;
+    if (h->secondary) return fail(h, FCIQMC_ERR_INVALID_ARG, "step a replica pair through its first replica");
+    if (h->partner) {  // both replicas in one launch per kernel, in lockstep
+        fciqmc_handle *pair[2] = {h, h->partner};
+        return fciqmc_step_batch(pair, 2, n_iter);
+    }
     if (h->pending) {
         int rc = fciqmc_sync(h);
         if (rc) return rc;
@@ -948,6 +1032,7 @@ int fciqmc_step(fciqmc_handle *h, int64_t n_iter)
 int fciqmc_step_async(fciqmc_handle *h, int64_t n_iter)
 {
     if (!h || n_iter < 0) return FCIQMC_ERR_INVALID_ARG;
+    if (h->partner) return fail(h, FCIQMC_ERR_UNSUPPORTED, "replica pairs are stepped with fciqmc_step");
     if (!h->pending) {
         int rc = read_state(h);
         if (rc) return rc;
@@ -1073,6 +1158,11 @@ static int handle_flags(fciqmc_handle *h, int *retries)
         h->hst.err = 0;
         return write_state(h);
     }
+    if (err == ERRB_PARTNER) {  // the other replica failed: repeat the iteration as it was
+        rc = reset_after_error(h);
+        if (rc) return rc;
+        return upload_inst(h);
+    }
     if (++*retries > 64) return fail(h, FCIQMC_ERR_CAPACITY, "capacity growth did not converge");
     const long long need = h->hst.need_spawn;
     const int n_over = h->hst.n_spawn_over;
@@ -1092,6 +1182,34 @@ static int handle_flags(fciqmc_handle *h, int *retries)
     }
     if (err & ERRB_HEAVY_CAP) {
         rc = grow_heavy(h);
+        if (rc) return rc;
+    }
+    rc = ensure_side(h);
+    if (rc) return rc;
+    // a replica pair keeps one bucket layout: the other replica follows a split
+    fciqmc_handle *pt = h->partner;
+    if (pt && pt->bb < h->bb) {
+        // its pending iteration (not committed: the replicas move in lockstep)
+        // is repeated after the split; its own flags come back if still due
+        rc = read_state(pt);
+        if (rc) return rc;
+        const int keep = pt->hst.err & (ERRB_STOP | ERRB_PAUSE_SEMI | ERRB_PAUSE_TRIAL);
+        rc = reset_after_error(pt);
+        if (rc) return rc;
+        if (keep) {
+            pt->hst.err = keep;
+            rc = write_state(pt);
+            if (rc) return rc;
+        }
+        while (pt->bb < h->bb) {
+            rc = grow_buckets(pt);
+            if (rc) return rc;
+        }
+        rc = ensure_side(pt);
+        if (rc) return rc;
+        rc = upload_inst(pt);
+        if (rc) return rc;
+        rc = capture_graph(pt);
         if (rc) return rc;
     }
     rc = upload_inst(h);
@@ -1261,6 +1379,15 @@ int fciqmc_step_batch(fciqmc_handle **hs, int32_t k, int64_t n_iter)
         for (int j = 0; j < i; j++)
             if (hs[j] == hs[i]) return fail(hs[0], FCIQMC_ERR_INVALID_ARG, "a handle appears twice in the batch");
     }
+    std::vector<int> pidx(k, -1);  // position of each run's replica partner in the batch
+    bool any_pair = false;
+    for (int i = 0; i < k; i++) {
+        if (!hs[i]->partner) continue;
+        for (int j = 0; j < k; j++)
+            if (hs[j] == hs[i]->partner) pidx[i] = j;
+        if (pidx[i] < 0) return fail(hs[0], FCIQMC_ERR_INVALID_ARG, "a replica is stepped without its partner");
+        any_pair = true;
+    }
     fciqmc_handle *h0 = hs[0];
     std::vector<long long> target(k);
     for (int i = 0; i < k; i++) {
@@ -1291,8 +1418,11 @@ int fciqmc_step_batch(fciqmc_handle **hs, int32_t k, int64_t n_iter)
         std::vector<int> us(k + 1);
         units = 0;
         max_nd = 0;
+        int max_bk = 1;
         for (int i = 0; i < k; i++) {
             tab[i] = hs[i]->hi;
+            tab[i].partner = pidx[i];
+            max_bk = std::max(max_bk, 1 << hs[i]->bb);
             tab[i].unit0 = units;
             us[i] = units;
             units += 1 << hs[i]->bb;
@@ -1310,9 +1440,11 @@ int fciqmc_step_batch(fciqmc_handle **hs, int32_t k, int64_t n_iter)
         cudaError_t le = launch_annihilate(dinst, dunit, k, units, h0->stream);
         launch_annihilate_big(dinst, k, h0->stream);
         launch_new_diag(dinst, k, h0->stream);
+        cudaError_t xe = any_pair ? launch_replica_cross(dinst, k, max_bk, h0->stream) : cudaSuccess;
         launch_finalize(dinst, k, h0->stream);
         cudaError_t e = cudaStreamEndCapture(h0->stream, &g);
-        if (le != cudaSuccess || e != cudaSuccess) return fail(h0, FCIQMC_ERR_CUDA, "batch graph capture failed");
+        if (le != cudaSuccess || xe != cudaSuccess || e != cudaSuccess)
+            return fail(h0, FCIQMC_ERR_CUDA, "batch graph capture failed");
         e = cudaGraphInstantiate(&gexec, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return fail(h0, FCIQMC_ERR_CUDA, "batch graph instantiate failed");
@@ -1482,6 +1614,31 @@ extern "C" int fciqmc_energy(fciqmc_handle *h, fciqmc_stats *out)
             out->shift_sigma = blocking_sigma(sh);
         }
     }
+    // replica pair (first replica): variational energy and PT2 correction
+    out->e_var_mean = NAN;
+    out->e_var_sigma = NAN;
+    out->pt2_mean = NAN;
+    out->pt2_sigma = NAN;
+    if (h->partner && !h->secondary && out->equil_start >= 0 && h->partner->hst.vary) {
+        const long long t0 = std::max<long long>(out->equil_start, h->partner->hst.shift_start + 500);
+        std::vector<double> ov, vn, pt;
+        for (const auto &r : h->hist)
+            if (r.iteration >= t0 && r.x_overlap != 0.0) {
+                ov.push_back(r.x_overlap);
+                vn.push_back(r.x_var_num);
+                pt.push_back(r.x_pt2);
+            }
+        out->pair_samples = (int64_t)ov.size();
+        if (ov.size() >= 8) {
+            double r, sg;
+            ratio_blocking(vn, ov, &r, &sg);
+            out->e_var_mean = h->eref + r;
+            out->e_var_sigma = sg;
+            ratio_blocking(pt, ov, &r, &sg);
+            out->pt2_mean = r;
+            out->pt2_sigma = sg;
+        }
+    }
     // trial-wave-function estimator (Sec. IV)
     out->e_trial_mean = NAN;
     out->e_trial_sigma = NAN;
@@ -1637,6 +1794,7 @@ int fciqmc_server_submit(fciqmc_server *srv, const fciqmc_system *sys, const fci
                          int64_t max_iters, int64_t *id)
 {
     if (!srv || !sys || !params || !id || !(target_sigma > 0.0) || max_iters < 1) return FCIQMC_ERR_INVALID_ARG;
+    if (params->replicas > 1) return FCIQMC_ERR_UNSUPPORTED;  // the server batches single runs
     Request r;
     r.id = srv->next_id++;
     r.sys = *sys;
@@ -1661,13 +1819,24 @@ int fciqmc_server_submit(fciqmc_server *srv, const fciqmc_system *sys, const fci
     return FCIQMC_OK;
 }
 
+// the energy a request reports: E_Trial when it has enough samples and the
+// smaller error, else E_proj; returns its sample count
+static int64_t best_energy(const fciqmc_stats &st, fciqmc_request_status &o)
+{
+    const bool trial = st.trial_samples >= 200 && std::isfinite(st.e_trial_sigma) &&
+                       !(st.e_proj_sigma <= st.e_trial_sigma);
+    o.energy = trial ? st.e_trial_mean : st.e_proj_mean;
+    o.sigma = trial ? st.e_trial_sigma : st.e_proj_sigma;
+    o.estimator = trial ? 1 : 0;
+    return trial ? st.trial_samples : st.n_samples;
+}
+
 static void retire(fciqmc_server *srv, Request &r, int state)
 {
     fciqmc_stats st;
     if (r.h && fciqmc_energy(r.h, &st) == FCIQMC_OK) {
         r.st.iterations = st.iteration;
-        r.st.energy = st.e_proj_mean;
-        r.st.sigma = st.e_proj_sigma;
+        best_energy(st, r.st);
         r.st.shift = st.shift;
         r.st.attempts = st.attempts_total;
     }
@@ -1733,10 +1902,9 @@ int fciqmc_server_tick(fciqmc_server *srv, int64_t n_iter, int32_t *n_active)
         fciqmc_stats st;
         if (fciqmc_energy(r.h, &st) != FCIQMC_OK) { retire(srv, r, 4); continue; }
         r.st.iterations = st.iteration;
-        r.st.energy = st.e_proj_mean;
-        r.st.sigma = st.e_proj_sigma;
+        const int64_t ns = best_energy(st, r.st);
         r.st.attempts = st.attempts_total;
-        if (st.n_samples >= 200 && st.e_proj_sigma < r.target_sigma) retire(srv, r, 2);
+        if (ns >= 200 && r.st.sigma < r.target_sigma) retire(srv, r, 2);
         else if (st.iteration >= r.max_iters) retire(srv, r, 3);
         else still.push_back(id);
     }

@@ -26,7 +26,11 @@ enum {
     ERRB_PAUSE_SEMI = 32, // iteration boundary at which D must be built (not an error)
     ERRB_STOP = 64,       // the run reached its stop iteration inside a batch (not an error)
     ERRB_PAUSE_TRIAL = 128,  // iteration boundary at which the trial space must be built (not an error)
+    ERRB_PARTNER = 256,      // the other replica of a pair failed this iteration: repeat it (not an error)
 };
+// errors raised before the finalize kernel: a replica commits its iteration
+// only if neither it nor its partner has one
+constexpr int ERRB_STAGE = ERRB_SPAWN_CAP | ERRB_MAIN_CAP | ERRB_HEAVY_CAP | ERRB_NUMERIC | ERRB_TIMEOUT;
 enum { DFLAG_REF = 1, DFLAG_D = 2 };
 
 // launch geometry
@@ -56,7 +60,16 @@ struct Partial {  // per-bucket reductions of one iteration
     long long ndet, rejected, spawns, attempts;
     double e_num;
     double t_num, t_den;    // trial-wave-function estimator
+    double x_ov, x_hd, x_cr, x_pt2;  // replica pair: overlap, diagonal and spawn cross terms, PT2 sum
     double pad;
+};
+
+struct SideEnt {  // one determinant of a bucket in one replica's iteration (pairs only)
+    u64 a, b;
+    double c0;    // amplitude at the start of the iteration
+    double hd;    // H_jj - E_ref if the determinant was in the list, else 0
+    double sacc;  // accepted spawns (exact sum, rounded once)
+    double srej;  // spawns removed by the initiator rule (exact sum, rounded once)
 };
 
 struct IterState {  // device-resident iteration state of one run
@@ -142,7 +155,7 @@ struct DevInst {
     const int *dcol;
     const double *dval;     // H^D - E_ref on the diagonal
     double *dc_new;         // C_D after the exact projection of this iteration
-    double *dc_cur;         // C_D after the last completed iteration
+    double *dc_buf[2];      // C_D after the last completed iteration, by list parity
     const u64 *dhash_keys;  // open-addressing set of D keys (a, b interleaved), size dhash_cap
     int dhash_bits;
     // pre-computed heat-bath doubles (generator 1): opposite-spin table of
@@ -156,6 +169,14 @@ struct DevInst {
     const double2 *pchb_meta;
     const ulonglong2 *pchb_ent;
     u64 pchb_ss_base;
+    // replica pair: key word 1 of every Philox draw; index of the other
+    // replica in the instance table (-1: none); per-bucket lists of the
+    // determinants of the iteration (side_cap entries per bucket)
+    u64 replica;
+    int partner;
+    int side_cap;
+    SideEnt *side;
+    int *side_cnt;
     // trial-wave-function estimator: open-addressing table of W_j and cT_j
     // (slot state 0 empty, 1 being written, 2 ready), 2^trial_bits slots
     long long trial_size, trial_start;
@@ -180,6 +201,8 @@ size_t annihilate_smem_bytes();
 void launch_annihilate_big(const DevInst *dinst, int n_inst, cudaStream_t s);
 void launch_finalize(const DevInst *dinst, int n_inst, cudaStream_t s);
 void launch_new_diag(const DevInst *dinst, int n_inst, cudaStream_t s);
+cudaError_t launch_replica_cross(const DevInst *dinst, int n_inst, int max_buckets, cudaStream_t s);
+cudaError_t replica_kernel_init();
 void launch_rebucket(const DevInst *src, const DevInst *dst, int nb_src, int parity, cudaStream_t s);
 void launch_diag(const DevInst *dinst, int parity, int nb, cudaStream_t s);
 void launch_abs_hist(const DevInst *dinst, int par, int nb, int shift, u64 prefix, unsigned *hist, cudaStream_t s);

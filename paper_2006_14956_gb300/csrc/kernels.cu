@@ -311,7 +311,7 @@ __device__ void run_attempts(const DevInst &I, K1Smem &S, long long it, unsigned
                 u64 k;
                 det[h] = map.det_of(ac, k);
                 const ulonglong2 kk = map.key(det[h]);
-                philox(kk.x, kk.y, (u64)it, (k << 8) | (u64)PURPOSE_SPAWN, I.seed, 0ULL, w[h]);
+                philox(kk.x, kk.y, (u64)it, (k << 8) | (u64)PURPOSE_SPAWN, I.seed, I.replica, w[h]);
                 cls[h] = a < a1 ? classify(I, kk.x, kk.y, w[h][0], w[h][1]) : -1;
             }
 #pragma unroll
@@ -535,14 +535,15 @@ struct Stage {
     IDX *tab;         // hash table: element index + 1, 0 = empty
     IDX *opos;        // output position of kept owners
 };
-enum { EF_OWNER = 1, EF_OCC = 2, EF_KEEP = 4, EF_REF = 16, EF_D = 32 };
+enum { EF_OWNER = 1, EF_OCC = 2, EF_KEEP = 4, EF_REF = 16, EF_D = 32, EF_REJ = 64, EF_RREC = 128 };
+// EF_REJ: a rejected spawn arrived (owners); EF_RREC: this spawn was rejected
 
 struct K3Shared {
     int wsum[K3_THREADS / 32];
     double red_d[K3_THREADS / 32];
     double red_t[K3_THREADS / 32][2];
     u64 red_u[K3_THREADS / 32][8];
-    int n_new, new_base;
+    int n_new, new_base, side_n;
     int hdr_err, hdr_par;
     long long hdr_it;
     double hdr_S;
@@ -696,13 +697,23 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
                 }
             }
         }
+        if (I.side)  // replica pair: walkers' entries (start amplitude, H_ii - E_ref)
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int e = t + (r0 + h) * K3_THREADS;
+                if (e < m) {
+                    SideEnt &se = I.side[(size_t)b * I.side_cap + e];
+                    const ulonglong2 k = W.key[e];
+                    se.a = k.x; se.b = k.y; se.c0 = W.val[e]; se.hd = hdr[r0 + h]; se.sacc = 0.0; se.srej = 0.0;
+                }
+            }
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int e = t + (r0 + h) * K3_THREADS;
             if (draw[h]) {
                 const ulonglong2 k = W.key[e];
                 u64 w[4];
-                philox(k.x, k.y, (u64)it, (u64)PURPOSE_DEATH, I.seed, 0ULL, w);
+                philox(k.x, k.y, (u64)it, (u64)PURPOSE_DEATH, I.seed, I.replica, w);
                 cp[h] = round_stoch(cp[h], I.cmin, I.cmin_log2, I.cmin_pow2, w[0]);
             }
             if (e < m) W.val[e] = cp[h];
@@ -733,7 +744,15 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
         if (target == e) atomicOr(&W.eflag[e], EF_OWNER);
         const bool init = e < m + si;
         const bool accepted = init || (target < m && (W.eflag[target] & EF_OCC));
-        if (!accepted) { rejected++; continue; }
+        if (!accepted) {
+            rejected++;
+            if (I.side) {
+                W.opos[e] = (IDX)target;
+                atomicOr(&W.eflag[e], EF_RREC);
+                atomicOr(&W.eflag[target], EF_REJ);
+            }
+            continue;
+        }
         const double w = W.val[e];
         const i128 x = to_fixed(w, I.Fw);
         const u64 lo = (u64)x, hi = (u64)((u128)x >> 64);
@@ -743,6 +762,48 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
         ann += (i128)fx32(w);
     }
     __syncthreads();
+    // replica pair: every owner's entry receives the accepted and the rejected
+    // spawn sums (exact, rounded once each); the rejected weights are summed
+    // in the accumulators once the accepted sums have been read
+    const bool side = I.side != nullptr;
+    if (side) {
+        if (t == 0) S.side_n = 0;
+        __syncthreads();
+        for (int e = t; e < E; e += K3_THREADS) {
+            const int f = W.eflag[e];
+            if (!(f & EF_OWNER)) continue;
+            const bool had = W.nacc[e] > 0;
+            const double sacc = had ? fixed_to_double((i128)(((u128)W.acc_hi[e] << 64) | (u128)W.acc_lo[e]), I.Fw)
+                                    : 0.0;
+            const int slot = e < m ? e : m + atomicAdd(&S.side_n, 1);
+            SideEnt &se = I.side[(size_t)b * I.side_cap + slot];
+            if (e >= m) {
+                const ulonglong2 k = W.key[e];
+                se.a = k.x; se.b = k.y; se.c0 = 0.0; se.hd = 0.0; se.srej = 0.0;
+            }
+            se.sacc = sacc;
+            W.nacc[e] = (slot << 1) | (had ? 1 : 0);
+            W.acc_lo[e] = 0;
+            W.acc_hi[e] = 0;
+        }
+        __syncthreads();
+        for (int e = m + t; e < E; e += K3_THREADS) {
+            if (!(W.eflag[e] & EF_RREC)) continue;
+            const int target = (int)W.opos[e];
+            const i128 x = to_fixed(W.val[e], I.Fw);
+            const u64 lo = (u64)x, hi = (u64)((u128)x >> 64);
+            const u64 old = atomicAdd((unsigned long long *)&W.acc_lo[target], (unsigned long long)lo);
+            atomicAdd((unsigned long long *)&W.acc_hi[target], (unsigned long long)(hi + (old + lo < old ? 1ULL : 0ULL)));
+        }
+        __syncthreads();
+        for (int e = t; e < E; e += K3_THREADS) {
+            const int f = W.eflag[e];
+            if (!(f & EF_OWNER) || !(f & EF_REJ)) continue;
+            const i128 X = (i128)(((u128)W.acc_hi[e] << 64) | (u128)W.acc_lo[e]);
+            I.side[(size_t)b * I.side_cap + (W.nacc[e] >> 1)].srej = fixed_to_double(X, I.Fw);
+        }
+        if (t == 0) I.side_cnt[b] = m + S.side_n;
+    }
     // 4. owners: sum = C' + exact spawn sum, then Eq. (3) with the annihilation draw
     int nk = 0;
     for (int e = t; e < E; e += K3_THREADS) {
@@ -751,15 +812,15 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
         const bool present = e < m;
         const double cp = present ? W.val[e] : 0.0;
         double accv = cp;
-        if (W.nacc[e] > 0) {
-            const i128 X = (i128)(((u128)W.acc_hi[e] << 64) | (u128)W.acc_lo[e]);
-            const double sw = fixed_to_double(X, I.Fw);
+        if (side ? (W.nacc[e] & 1) : W.nacc[e] > 0) {
+            const double sw = side ? I.side[(size_t)b * I.side_cap + (W.nacc[e] >> 1)].sacc
+                                   : fixed_to_double((i128)(((u128)W.acc_hi[e] << 64) | (u128)W.acc_lo[e]), I.Fw);
             accv = present ? cp + sw : sw;
             ann += (present ? (i128)fx32(cp) : (i128)0) - (i128)fx32(accv);
             if (!(f & EF_D) && !is_zero(accv) && abs_lt(accv, I.cmin)) {
                 const ulonglong2 k = W.key[e];
                 u64 w[4];
-                philox(k.x, k.y, (u64)it, (u64)PURPOSE_ANNIH, I.seed, 0ULL, w);
+                philox(k.x, k.y, (u64)it, (u64)PURPOSE_ANNIH, I.seed, I.replica, w);
                 accv = round_stoch(accv, I.cmin, I.cmin_log2, I.cmin_pow2, w[0]);
             }
         }
@@ -815,7 +876,7 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
                 const int lev = __popcll(k.x ^ I.ref_a) + __popcll(k.y ^ I.ref_b);
                 if (lev <= 4 && !is_zero(c)) enm = enm + hoff_generic(I, k.x, k.y, I.ref_a, I.ref_b) * c;
             }
-            if (f & EF_D) I.dc_cur[d_index_of(I, k.x, k.y)] = c;
+            if (f & EF_D) I.dc_buf[par ^ 1][d_index_of(I, k.x, k.y)] = c;
             if (I.trial_bits && !is_zero(c)) {  // trial-wave-function estimator (Sec. IV)
                 const int ts = trial_find(I, k.x, k.y);
                 if (ts >= 0) {
@@ -985,12 +1046,23 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
     __shared__ int s_err;
     __shared__ double s_d[K5_THREADS / 32];
     __shared__ double s_t[K5_THREADS / 32][2];
+    __shared__ double s_x[K5_THREADS / 32][4];
     __shared__ u64 s_u[K5_THREADS / 32][8];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    if (t == 0) s_err = *(volatile int *)&st->err;
+    if (t == 0) {
+        int e = *(volatile int *)&st->err;
+        // a replica commits its iteration only together with its partner
+        if (!e && I.partner >= 0 && (*(volatile int *)&insts[I.partner].st->err & ERRB_STAGE)) {
+            st->err = ERRB_PARTNER;
+            e = ERRB_PARTNER;
+        }
+        s_err = e;
+    }
     __syncthreads();
     if (s_err) return;
     const int nbk = 1 << I.bb;
+    const bool pair = I.partner > (int)blockIdx.x;  // the first replica reports the cross estimators
+    double xo = 0.0, xh = 0.0, xc = 0.0, xp = 0.0;
     u128 nw = 0;
     i128 ann = 0;
     long long ndet = 0, rej = 0, sp = 0, att = 0;
@@ -1002,6 +1074,12 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
             tn = tn + P.t_num;
             td = td + P.t_den;
         }
+        if (pair) {
+            xo = xo + P.x_ov;
+            xh = xh + P.x_hd;
+            xc = xc + P.x_cr;
+            xp = xp + P.x_pt2;
+        }
         nw += ((u128)P.nw_hi << 64) | P.nw_lo;
         ann += (i128)(((u128)P.ann_hi << 64) | P.ann_lo);
         ndet += P.ndet; rej += P.rejected; sp += P.spawns; att += P.attempts;
@@ -1011,6 +1089,13 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
         for (int mm = 16; mm >= 1; mm >>= 1) {
             tn = tn + __shfl_xor_sync(0xffffffffu, tn, mm);
             td = td + __shfl_xor_sync(0xffffffffu, td, mm);
+        }
+    if (pair)
+        for (int mm = 16; mm >= 1; mm >>= 1) {
+            xo = xo + __shfl_xor_sync(0xffffffffu, xo, mm);
+            xh = xh + __shfl_xor_sync(0xffffffffu, xh, mm);
+            xc = xc + __shfl_xor_sync(0xffffffffu, xc, mm);
+            xp = xp + __shfl_xor_sync(0xffffffffu, xp, mm);
         }
     for (int mm = 16; mm >= 1; mm >>= 1) {
         en = en + __shfl_xor_sync(0xffffffffu, en, mm);
@@ -1025,13 +1110,14 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
         s_d[warp] = en;
         s_t[warp][0] = tn;
         s_t[warp][1] = td;
+        s_x[warp][0] = xo; s_x[warp][1] = xh; s_x[warp][2] = xc; s_x[warp][3] = xp;
         s_u[warp][0] = (u64)nw; s_u[warp][1] = (u64)(nw >> 64);
         s_u[warp][2] = (u64)ann; s_u[warp][3] = (u64)((u128)ann >> 64);
         s_u[warp][4] = (u64)ndet; s_u[warp][5] = (u64)rej; s_u[warp][6] = (u64)sp; s_u[warp][7] = (u64)att;
     }
     __syncthreads();
     if (t != 0) return;
-    double e_num = 0.0, t_num = 0.0, t_den = 0.0;
+    double e_num = 0.0, t_num = 0.0, t_den = 0.0, x_ov = 0.0, x_hd = 0.0, x_cr = 0.0, x_pt = 0.0;
     u128 W = 0;
     i128 A = 0;
     long long nd = 0, rj = 0, sps = 0, at = 0;
@@ -1040,6 +1126,9 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
         if (trial) {
             t_num = t_num + s_t[k][0];
             t_den = t_den + s_t[k][1];
+        }
+        if (pair) {
+            x_ov = x_ov + s_x[k][0]; x_hd = x_hd + s_x[k][1]; x_cr = x_cr + s_x[k][2]; x_pt = x_pt + s_x[k][3];
         }
         W += ((u128)s_u[k][1] << 64) | s_u[k][0];
         A += (i128)(((u128)s_u[k][3] << 64) | s_u[k][2]);
@@ -1068,6 +1157,9 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
     R.ndet = nd; R.attempts = at; R.spawns = sps; R.rejected = rj;
     R.annihilated = i128_to_double(A) * 0x1p-32; R.vary = st->vary; R.pad0 = 0;
     R.trial_num = t_num; R.trial_den = t_den;
+    R.x_overlap = x_ov;
+    R.x_var_num = pair ? x_hd - x_cr / (2.0 * I.tau) : 0.0;
+    R.x_pt2 = pair ? x_pt / (I.tau * I.tau) : 0.0;
     st->iter = it + 1;
     st->parity ^= 1;
     st->heavy_n = 0;

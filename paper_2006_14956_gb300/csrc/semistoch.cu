@@ -90,14 +90,16 @@ __global__ void k_mark_d(const DevInst *__restrict__ I, int par, int nb)
             const int d = d_index_of(*I, k.x, k.y);
             if (d >= 0) {
                 I->fl[par][o] |= DFLAG_D;
-                I->dc_cur[d] = I->c[par][o];
+                I->dc_buf[par][d] = I->c[par][o];
             }
         }
     }
 }
 
 // ------------------------------------------------------------------ per iteration
-// C_D(new) = C_D - tau (y - S C_D), y = sum_c H^D_rc C_D,c summed in column order
+// C_D(new) = C_D - tau (y - S C_D), y = sum_c H^D_rc C_D,c summed in column order; C_D of
+// the current parity (the other buffer receives the iteration's result, so a
+// repeated iteration starts from unchanged values)
 __global__ void k_semistoch(const DevInst *__restrict__ insts, int n_inst)
 {
     for (int ii = 0; ii < n_inst; ii++) {
@@ -105,10 +107,11 @@ __global__ void k_semistoch(const DevInst *__restrict__ insts, int n_inst)
         if (I.nd == 0) continue;
         if (*(volatile int *)&I.st->err) continue;
         const double S = I.st->S;
+        const double *cur = I.dc_buf[I.st->parity];
         for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < I.nd; r += gridDim.x * blockDim.x) {
             double y = 0.0;
-            for (long long q = I.drow[r]; q < I.drow[r + 1]; q++) y = y + I.dval[q] * I.dc_cur[I.dcol[q]];
-            const double c = I.dc_cur[r];
+            for (long long q = I.drow[r]; q < I.drow[r + 1]; q++) y = y + I.dval[q] * cur[I.dcol[q]];
+            const double c = cur[r];
             I.dc_new[r] = c - I.tau * (y - S * c);
         }
     }

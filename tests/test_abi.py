@@ -31,8 +31,8 @@ def test_library_exports_every_declared_symbol():
 def test_struct_sizes_match_header_layout():
     import paper_2006_14956_gb300 as fq
     # 8-byte aligned records; a mismatch would corrupt every call
-    assert ctypes.sizeof(fq.fciqmc_iter_stats) == 104
-    assert ctypes.sizeof(fq.fciqmc_stats) == 168
+    assert ctypes.sizeof(fq.fciqmc_iter_stats) == 128
+    assert ctypes.sizeof(fq.fciqmc_stats) == 208
     assert ctypes.sizeof(fq.fciqmc_system) == 96
     assert ctypes.sizeof(fq.fciqmc_params) == 176
 
