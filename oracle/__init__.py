@@ -56,13 +56,14 @@ class Params(C.Structure):
                 ("initiator_threshold", C.c_double), ("c_min", C.c_double), ("p_single", C.c_double),
                 ("shift_interval", C.c_int64), ("seed", C.c_uint64),
                 ("semistoch_size", C.c_int64), ("semistoch_start", C.c_int64), ("generator", C.c_int64),
-                ("trial_size", C.c_int64), ("trial_start", C.c_int64), ("replica", C.c_int64)]
+                ("trial_size", C.c_int64), ("trial_start", C.c_int64), ("replica", C.c_int64),
+                ("adaptive_shift", C.c_int64)]
 
 
 DEFAULT_PARAMS = dict(tau=0.01, shift_damping=0.1, target_walkers=1e4, initial_walkers=10.0,
                       initial_shift=0.0, initiator_threshold=0.0, c_min=1.0, p_single=0.1,
                       shift_interval=10, seed=1, semistoch_size=0, semistoch_start=100,
-                      generator=0, trial_size=0, trial_start=100, replica=0)
+                      generator=0, trial_size=0, trial_start=100, replica=0, adaptive_shift=0)
 
 CLASSES = ("single_a", "single_b", "double_ab", "double_aa", "double_bb", "hop")
 
@@ -109,6 +110,9 @@ def lib():
                                          C.POINTER(C.c_int32), dp]),
                 "orc_trial_info": (I64, [P, C.POINTER(C.c_int64), dp, up, up, dp]),
                 "orc_pair_step": (I32, [P, P, I64]),
+                "orc_set_keep_last": (None, [P, I32]),
+                "orc_last_iteration": (I64, [P, C.POINTER(C.c_int64), up, up, dp, dp, dp, up, up, dp,
+                                             C.POINTER(C.c_int32), C.POINTER(C.c_int64)]),
                 "orc_jacobi_lowest": (I32, [I32, dp, dp, dp]),
             }
             for name, (res, args) in sig.items():
@@ -340,6 +344,27 @@ class Run:
                                  alias.ctypes.data_as(C.POINTER(C.c_int32)), ea.ctypes.data_as(C.POINTER(C.c_int32)),
                                  eb.ctypes.data_as(C.POINTER(C.c_int32)), val.ctypes.data_as(C.POINTER(C.c_double)))
         return dict(K=K, S=S.value, lam=lam.value, prob=prob[:K], alias=alias[:K], a=ea[:K], b=eb[:K], val=val[:K])
+
+    def last_iteration(self):
+        """Start list (keys, C, H_ii - E_ref, adaptive-shift f_i) and spawns (keys,
+        weight, initiator flag, parent index) of the last iteration; needs
+        keep_last(True) before it."""
+        ns = C.c_int64()
+        n = lib().orc_last_iteration(self.h, C.byref(ns), None, None, None, None, None, None, None, None, None, None)
+        m = ns.value
+        L = {k: np.zeros(max(n, 1), t) for k, t in (("a", np.uint64), ("b", np.uint64), ("c", np.float64),
+                                                     ("hd", np.float64), ("f", np.float64))}
+        S = {k: np.zeros(max(m, 1), t) for k, t in (("a", np.uint64), ("b", np.uint64), ("w", np.float64),
+                                                     ("init", np.int32), ("parent", np.int64))}
+        u = lambda x: x.ctypes.data_as(C.POINTER(C.c_uint64))
+        d = lambda x: x.ctypes.data_as(C.POINTER(C.c_double))
+        lib().orc_last_iteration(self.h, None, u(L["a"]), u(L["b"]), d(L["c"]), d(L["hd"]), d(L["f"]), u(S["a"]),
+                                 u(S["b"]), d(S["w"]), S["init"].ctypes.data_as(C.POINTER(C.c_int32)),
+                                 S["parent"].ctypes.data_as(C.POINTER(C.c_int64)))
+        return {k: v[:n] for k, v in L.items()}, {k: v[:m] for k, v in S.items()}
+
+    def keep_last(self, on=True):
+        lib().orc_set_keep_last(self.h, int(bool(on)))
 
     def trial_info(self):
         """Trial space of the E_Trial estimator: dict(nt, n_w (|T u C|), ET (E^T - E_ref), a, b, cT)."""

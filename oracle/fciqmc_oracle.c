@@ -523,10 +523,11 @@ typedef struct {
     int64_t generator; /* 0: uniform doubles, 1: pre-computed heat-bath doubles (App. A) */
     int64_t trial_size, trial_start; /* trial space T of the E_Trial estimator (Sec. IV) */
     int64_t replica;                 /* replica index: second word of the Philox key */
+    int64_t adaptive_shift;          /* 1: local shift f_i S for non-initiators (Sec. V, adaptive shift) */
 } orc_params;
 
 typedef struct { uint64_t a, b; double c, hd; int flags; } odet; /* flags: 1 ref, 2 in D */
-typedef struct { uint64_t a, b; double w; int init; } ospawn;
+typedef struct { uint64_t a, b; double w; int init; int64_t parent; } ospawn;
 
 typedef struct {
     int64_t iter;
@@ -594,6 +595,7 @@ typedef struct {
     int64_t n0;
     ospawn *sp0;
     int64_t ns0;
+    double *f0; /* the last iteration's f_i per start-list entry (adaptive shift) */
 } orc_run;
 
 static int cmp_key(uint64_t a1, uint64_t b1, uint64_t a2, uint64_t b2)
@@ -838,7 +840,7 @@ void orc_destroy(orc_run *r)
     if (!r) return;
     free(r->L); free(r->Da); free(r->Db); free(r->rowptr); free(r->col); free(r->val); free(r->st);
     free(r->Ta); free(r->Tb); free(r->cT); free(r->Wa); free(r->Wb); free(r->W);
-    free(r->L0); free(r->sp0);
+    free(r->L0); free(r->sp0); free(r->f0);
     pchb_free(r);
     free(r);
 }
@@ -1120,17 +1122,29 @@ static int one_iteration(orc_run *r)
         r->n0 = r->n;
     }
 
-    /* (a) spawning from the start-of-iteration amplitudes */
+    /* (a) spawning from the start-of-iteration amplitudes.  Adaptive shift:
+     * for a non-initiator D_i, every spawn that survives Eq. (3) adds
+     * w_ij = |H_ji| / |H_jj - E_ref - S| (S: the shift at the start of the
+     * iteration, the energy estimate of the run), truncated to the grid 2^-64
+     * and summed exactly, to T_i, and to A_i as well if the spawn is accepted
+     * (its target is occupied at the start of the iteration, the initiator
+     * rule); f_i = A_i / T_i (1 without such spawns) scales the shift in the
+     * death of D_i. */
     int64_t ns = 0, scap = 1024, attempts = 0;
     ospawn *sp = malloc(sizeof(ospawn) * scap);
+    double *fi = malloc(sizeof(double) * (r->n ? r->n : 1));
+    int *initf = malloc(sizeof(int) * (r->n ? r->n : 1));
+    for (int64_t i = 0; i < r->n; i++) { fi[i] = 1.0; initf[i] = 1; }
     for (int64_t i = 0; i < r->n; i++) {
         odet *d = &r->L[i];
         if (d->c == 0.0) continue;
         double mag = fabs(d->c);
-        if (mag >= 0x1p40) { free(sp); return 3; }
+        if (mag >= 0x1p40) { free(sp); free(fi); free(initf); return 3; }
         uint64_t nat = (uint64_t)ceil(mag);
         attempts += (int64_t)nat;
         int init = mag > P->initiator_threshold || (d->flags & 3);
+        initf[i] = init;
+        u128 accA = 0, accT = 0;
         double cper = d->c / (double)nat;
         for (uint64_t k = 0; k < nat; k++) {
             uint64_t w[4], ta, tb;
@@ -1158,9 +1172,27 @@ static int one_iteration(orc_run *r)
                 if (ws == 0.0) continue;
             }
             if ((d->flags & 2) && find_D(r, ta, tb) >= 0) continue; /* D -> D is exact */
+            if (P->adaptive_shift && !init) {
+                int64_t j = find_det(r->L, r->n, ta, tb);
+                int occ = j >= 0 && r->L[j].c != 0.0;
+                double hdj = j >= 0 ? r->L[j].hd : orc_hdiag_rel(s, ta, tb);
+                double den = fabs(hdj - r->S);
+                if (den != 0.0) {
+                    double wij = fabs(orc_hoff(s, d->a, d->b, ta, tb)) / den;
+                    u128 q = (u128)(wij * 0x1p64); /* floor: w >= 0, exact scaling */
+                    accT += q;
+                    if (occ) accA += q;
+                }
+            }
             if (ns == scap) { scap *= 2; sp = realloc(sp, sizeof(ospawn) * scap); }
-            sp[ns].a = ta; sp[ns].b = tb; sp[ns].w = ws; sp[ns].init = init; ns++;
+            sp[ns].a = ta; sp[ns].b = tb; sp[ns].w = ws; sp[ns].init = init; sp[ns].parent = i; ns++;
         }
+        if (P->adaptive_shift && !init && accT != 0) fi[i] = (double)accA / (double)accT;
+    }
+    if (r->keep_last) {
+        free(r->f0);
+        r->f0 = malloc(sizeof(double) * (r->n ? r->n : 1));
+        memcpy(r->f0, fi, sizeof(double) * r->n);
     }
 
     /* (b) death, in place; deterministic space: exact projection (Sec. III) */
@@ -1184,7 +1216,8 @@ static int one_iteration(orc_run *r)
     for (int64_t i = 0; i < r->n; i++) {
         odet *d = &r->L[i];
         if (d->flags & 2) { d->c = cd_new[find_D(r, d->a, d->b)]; continue; }
-        double f = 1.0 - P->tau * (d->hd - r->S);
+        double Si = (P->adaptive_shift && !initf[i]) ? fi[i] * r->S : r->S;
+        double f = 1.0 - P->tau * (d->hd - Si);
         double cp = d->c * f;
         if (cp != 0.0 && fabs(cp) < cmin) {
             uint64_t w[4];
@@ -1194,6 +1227,7 @@ static int one_iteration(orc_run *r)
         d->c = cp;
     }
     free(cd_new);
+    free(fi); free(initf);
 
     /* (c) annihilation with the initiator rule */
     qsort(sp, ns, sizeof(ospawn), cmp_ospawn);
@@ -1290,6 +1324,7 @@ static int one_iteration(orc_run *r)
     t->ndet = no; t->attempts = attempts; t->spawns = ns; t->rejected = rejected;
     t->annihilated = (double)ann * 0x1p-32; t->vary = r->vary;
     t->t_num = t_num; t->t_den = t_den;
+    t->x_overlap = 0.0; t->x_var_num = 0.0; t->x_pt2 = 0.0; /* filled by a replica pair */
     r->iter = it + 1;
     return 0;
 }
@@ -1367,6 +1402,30 @@ static int64_t side_list(const orc_run *r, oside **out)
     }
     *out = v;
     return n;
+}
+
+/* the last iteration (keep_last set): start list, spawns (with parent index
+ * into the start list) and the adaptive-shift factors f_i */
+void orc_set_keep_last(orc_run *r, int on) { r->keep_last = on; }
+int64_t orc_last_iteration(const orc_run *r, int64_t *ns, uint64_t *la, uint64_t *lb, double *lc, double *lhd,
+                           double *lf, uint64_t *sa, uint64_t *sb, double *sw, int32_t *sinit, int64_t *spar)
+{
+    if (ns) *ns = r->ns0;
+    for (int64_t i = 0; i < r->n0; i++) {
+        if (la) la[i] = r->L0[i].a;
+        if (lb) lb[i] = r->L0[i].b;
+        if (lc) lc[i] = r->L0[i].c;
+        if (lhd) lhd[i] = r->L0[i].hd;
+        if (lf) lf[i] = r->f0 ? r->f0[i] : 1.0;
+    }
+    for (int64_t k = 0; k < r->ns0; k++) {
+        if (sa) sa[k] = r->sp0[k].a;
+        if (sb) sb[k] = r->sp0[k].b;
+        if (sw) sw[k] = r->sp0[k].w;
+        if (sinit) sinit[k] = r->sp0[k].init;
+        if (spar) spar[k] = r->sp0[k].parent;
+    }
+    return r->n0;
 }
 
 int orc_pair_step(orc_run *r0, orc_run *r1, int64_t n)

@@ -643,3 +643,65 @@ def test_pair_variational_and_pt2_numerators_are_unbiased():
     assert abs(var.mean() - exact_var) < 4.0 * var.std() / math.sqrt(var.size) + 1e-9
     assert abs(pt2.mean() - exact_pt2) < 4.0 * pt2.std() / math.sqrt(pt2.size) + 1e-9
     assert np.count_nonzero(pt2) > 50  # the estimator is exercised
+
+
+# ---------------------------------------------------------------- adaptive shift (Sec. V)
+def test_adaptive_shift_factor_by_definition():
+    """f_i of every non-initiator, recomputed from the last iteration's spawns:
+    w_ij = |H_ji| / |H_jj - E_ref - S| truncated to 2^-64, summed over the
+    spawns onto determinants occupied at the start (A) and over all (T),
+    f_i = A / T (1 without spawns); initiators keep 1."""
+    sysd = workloads.small_abinitio(7, 3, 2, seed=8)
+    s = oracle.system_from_workload(sysd)
+    n_a = 2.0
+    r = oracle.Run(s, tau=0.004, target_walkers=1500, initial_walkers=200.0, initiator_threshold=n_a, seed=5,
+                   shift_damping=0.5, shift_interval=5, initial_shift=-0.3, adaptive_shift=1)
+    r.step(40)
+    r.keep_last(True)
+    r.step(1)
+    S_start = r.stats()["S"][-2]
+    L, Sp = r.last_iteration()
+    occ = {(int(a), int(b)): (c, hd) for a, b, c, hd in zip(L["a"], L["b"], L["c"], L["hd"])}
+    checked = 0
+    for i in range(len(L["a"])):
+        det = (int(L["a"][i]), int(L["b"][i]))
+        c = L["c"][i]
+        init = abs(c) > n_a or det == s.ref
+        if c == 0.0 or init:
+            assert L["f"][i] == 1.0
+            continue
+        A = T = 0
+        for k in np.nonzero(Sp["parent"] == i)[0]:
+            tgt = (int(Sp["a"][k]), int(Sp["b"][k]))
+            cj, hd = occ.get(tgt, (0.0, None))
+            if hd is None:
+                hd = s.hdiag_rel(*tgt)
+            den = abs(hd - S_start)
+            if den == 0.0:
+                continue
+            q = int(abs(s.hoff(det, tgt)) / den * 2.0 ** 64)
+            T += q
+            if cj != 0.0:
+                A += q
+        f = float(A) / float(T) if T else 1.0
+        assert L["f"][i] == f, (i, L["f"][i], f)
+        checked += T > 0
+    assert checked > 20
+
+
+def test_adaptive_shift_is_inert_without_non_initiators():
+    """With n_a = 0 every occupied determinant is an initiator: the adaptive
+    shift changes nothing, bit for bit."""
+    sysd = workloads.small_abinitio(7, 3, 2, seed=8)
+    s = oracle.system_from_workload(sysd)
+    p = dict(tau=0.004, target_walkers=1500, initial_walkers=100.0, initiator_threshold=0.0, seed=5)
+    a, b = oracle.Run(s, **p), oracle.Run(s, adaptive_shift=1, **p)
+    a.step(60)
+    b.step(60)
+    ea, eb = a.export(), b.export()
+    assert np.array_equal(ea["c"].view(np.uint64), eb["c"].view(np.uint64))
+    c = oracle.Run(s, adaptive_shift=1, **dict(p, initiator_threshold=2.0))
+    d = oracle.Run(s, **dict(p, initiator_threshold=2.0))
+    c.step(60)
+    d.step(60)
+    assert not np.array_equal(c.export()["c"], d.export()["c"])
