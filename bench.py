@@ -248,6 +248,9 @@ def run_serving(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "requests": len(reqs), "converged": conv, "converged_by_trial_estimator": by_trial,
+            "sigma_mEh_at_answer": {k: [round(1e3 * s["sigma"], 3) for s, r in zip(st, reqs)
+                                        if r["system"]["kind"] == k and np.isfinite(s["sigma"])]
+                                    for k in ("hubbard", "abinitio")},
             "capped": len(reqs) - conv,
             "requests_per_s": len(reqs) / t_end, "attempts_per_s": att / t_end,
             "config": {"workload": "serving stream: Poisson 20/s, 1D/2D Hubbard 8-18 sites and ab initio 16-40 "

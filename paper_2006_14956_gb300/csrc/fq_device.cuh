@@ -83,6 +83,8 @@ __device__ __forceinline__ bool is_zero(double x) { return (dbits(x) << 1) == 0;
 // |x| < y for y positive and finite (false for NaN x)
 __device__ __forceinline__ bool abs_lt(double x, double y) { return (dbits(x) & ~SIGN64) < dbits(y); }
 __device__ __forceinline__ double with_sign_of(double mag, double s) { return bitsd(dbits(mag) | (dbits(s) & SIGN64)); }
+// -x (IEEE negation is a flip of the sign bit) without the binary64 pipe; x if !flip
+__device__ __forceinline__ double neg_if(bool flip, double x) { return bitsd(dbits(x) ^ (flip ? SIGN64 : 0ULL)); }
 
 // |x| = M 2^E with M the integer significand
 __device__ __forceinline__ void split_abs(double x, u64 &M, int &E)
@@ -294,7 +296,7 @@ static __device__ double hoff_generic(const DevInst &I, u64 ia, u64 ib, u64 ja, 
         u64 x = sp ? ib : ia;
         u64 between = i < a ? (mask_below(a) & ~mask_below(i + 1)) : (mask_below(i) & ~mask_below(a + 1));
         double v = single_exact(I, ia, ib, sp, i, a);
-        return (__popcll(x & between) & 1) ? -v : v;
+        return neg_if(__popcll(x & between) & 1, v);
     }
     // canonical positions of the two removed and two added spin orbitals
     int P[2], Q[2], np = 0, nq = 0;
@@ -314,9 +316,9 @@ static __device__ double hoff_generic(const DevInst &I, u64 ia, u64 ib, u64 ja, 
     double v;
     if (dir && exch) v = eri4(I, oa, oi, ob, oj) - eri4(I, oa, oj, ob, oi);
     else if (dir) v = eri4(I, oa, oi, ob, oj);
-    else if (exch) v = -eri4(I, oa, oj, ob, oi);
+    else if (exch) v = neg_if(true, eri4(I, oa, oj, ob, oi));
     else v = 0.0;
-    return par ? -v : v;
+    return neg_if(par, v);
 }
 
 // index of a determinant in the sorted key list of D, or -1

@@ -95,7 +95,7 @@ __device__ __forceinline__ void emit_spawn(const DevInst &I, u64 ta, u64 tb, dou
                                            unsigned flags, u64 w3)
 {
     if (is_zero(H)) return;
-    emit_weight(I, ta, tb, -(H * (I.lam[cls] * cper)), flags, w3);
+    emit_weight(I, ta, tb, neg_if(true, H * (I.lam[cls] * cper)), flags, w3);
 }
 
 // lattice hop (Hubbard): electron w1, neighbour slot w2
@@ -108,7 +108,7 @@ __device__ void spawn_hop(const DevInst &I, u64 pa, u64 pb, double cper, unsigne
     const int q = __ldg(I.nbr + 4 * p + (int)pick(w2, (u64)I.z));
     if (q < 0 || ((x >> q) & 1ULL)) return;
     const u64 between = p < q ? (mask_below(q) & ~mask_below(p + 1)) : (mask_below(p) & ~mask_below(q + 1));
-    const double H = (__popcll(x & between) & 1) ? -I.tmt : I.tmt;
+    const double H = neg_if(__popcll(x & between) & 1, I.tmt);
     x ^= (1ULL << p) | (1ULL << q);
     emit_spawn(I, sp ? pa : x, sp ? x : pb, H, CLS_HOP, cper, flags, w3);
 }
@@ -124,7 +124,7 @@ __device__ void spawn_single(const DevInst &I, u64 pa, u64 pb, double cper, unsi
     const int a = nth_set(~x & I.normask, (int)pick(w2, (u64)m));
     const u64 between = i < a ? (mask_below(a) & ~mask_below(i + 1)) : (mask_below(i) & ~mask_below(a + 1));
     const double v = single_exact(I, pa, pb, sp, i, a);
-    const double H = (__popcll(x & between) & 1) ? -v : v;
+    const double H = neg_if(__popcll(x & between) & 1, v);
     x ^= (1ULL << i) | (1ULL << a);
     emit_spawn(I, sp ? pa : x, sp ? x : pb, H, sp ? CLS_SINGLE_B : CLS_SINGLE_A, cper, flags, w3);
 }
@@ -172,7 +172,7 @@ __device__ void spawn_double(const DevInst &I, u64 pa, u64 pb, double cper, unsi
     par ^= flip_parity(xa, xb, N, Q1);
     par ^= flip_parity(xa, xb, N, Q0);
     const double v = (cls == CLS_DOUBLE_AB) ? eri4(I, oa, oi, ob, oj) : eri4(I, oa, oi, ob, oj) - eri4(I, oa, oj, ob, oi);
-    emit_spawn(I, ta, tb, par ? -v : v, cls, cper, flags, w3);
+    emit_spawn(I, ta, tb, neg_if(par, v), cls, cper, flags, w3);
 }
 
 // heat-bath double (App. A, pre-computed heat-bath sampling): ordered electron
@@ -237,10 +237,10 @@ __device__ void spawn_double_pchb(const DevInst &I, u64 pa, u64 pb, double cper,
     par ^= flip_parity(xa, xb, N, Q1);
     par ^= flip_parity(xa, xb, N, Q0);
     const double v = (cls == CLS_DOUBLE_AB) ? eri4(I, oa, oi, ob, oj) : eri4(I, oa, oi, ob, oj) - eri4(I, oa, oj, ob, oi);
-    const double H = par ? -v : v;
+    const double H = neg_if(par, v);
     if (is_zero(H)) return;
     const double wv = mt.x * cper;
-    emit_weight(I, ta, tb, (dbits(H) & SIGN64) ? wv : -wv, flags, w3);
+    emit_weight(I, ta, tb, neg_if(!(dbits(H) & SIGN64), wv), flags, w3);
 }
 
 // class of one attempt from its first two words, or -1 for a failed attempt
@@ -1116,24 +1116,38 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
         s_u[warp][4] = (u64)ndet; s_u[warp][5] = (u64)rej; s_u[warp][6] = (u64)sp; s_u[warp][7] = (u64)att;
     }
     __syncthreads();
-    if (t != 0) return;
-    double e_num = 0.0, t_num = 0.0, t_den = 0.0, x_ov = 0.0, x_hd = 0.0, x_cr = 0.0, x_pt = 0.0;
-    u128 W = 0;
-    i128 A = 0;
-    long long nd = 0, rj = 0, sps = 0, at = 0;
-    for (int k = 0; k < K5_THREADS / 32; k++) {
-        e_num = e_num + s_d[k];
-        if (trial) {
-            t_num = t_num + s_t[k][0];
-            t_den = t_den + s_t[k][1];
-        }
-        if (pair) {
-            x_ov = x_ov + s_x[k][0]; x_hd = x_hd + s_x[k][1]; x_cr = x_cr + s_x[k][2]; x_pt = x_pt + s_x[k][3];
-        }
-        W += ((u128)s_u[k][1] << 64) | s_u[k][0];
-        A += (i128)(((u128)s_u[k][3] << 64) | s_u[k][2]);
-        nd += (long long)s_u[k][4]; rj += (long long)s_u[k][5]; sps += (long long)s_u[k][6]; at += (long long)s_u[k][7];
+    // the warps' partial sums, reduced by warp 0 in the same xor tree
+    static_assert(K5_THREADS / 32 == 32, "one partial per lane");
+    if (warp != 0) return;
+    double e_num = s_d[lane], t_num = 0.0, t_den = 0.0, x_ov = 0.0, x_hd = 0.0, x_cr = 0.0, x_pt = 0.0;
+    u128 W = ((u128)s_u[lane][1] << 64) | s_u[lane][0];
+    i128 A = (i128)(((u128)s_u[lane][3] << 64) | s_u[lane][2]);
+    long long nd = (long long)s_u[lane][4], rj = (long long)s_u[lane][5], sps = (long long)s_u[lane][6],
+              at = (long long)s_u[lane][7];
+    if (trial) { t_num = s_t[lane][0]; t_den = s_t[lane][1]; }
+    if (pair) { x_ov = s_x[lane][0]; x_hd = s_x[lane][1]; x_cr = s_x[lane][2]; x_pt = s_x[lane][3]; }
+    for (int mm = 16; mm >= 1; mm >>= 1) {
+        e_num = e_num + __shfl_xor_sync(0xffffffffu, e_num, mm);
+        W += (u128)shfl_xor_i128((i128)W, mm);
+        A += shfl_xor_i128(A, mm);
+        nd += __shfl_xor_sync(0xffffffffu, nd, mm);
+        rj += __shfl_xor_sync(0xffffffffu, rj, mm);
+        sps += __shfl_xor_sync(0xffffffffu, sps, mm);
+        at += __shfl_xor_sync(0xffffffffu, at, mm);
     }
+    if (trial)
+        for (int mm = 16; mm >= 1; mm >>= 1) {
+            t_num = t_num + __shfl_xor_sync(0xffffffffu, t_num, mm);
+            t_den = t_den + __shfl_xor_sync(0xffffffffu, t_den, mm);
+        }
+    if (pair)
+        for (int mm = 16; mm >= 1; mm >>= 1) {
+            x_ov = x_ov + __shfl_xor_sync(0xffffffffu, x_ov, mm);
+            x_hd = x_hd + __shfl_xor_sync(0xffffffffu, x_hd, mm);
+            x_cr = x_cr + __shfl_xor_sync(0xffffffffu, x_cr, mm);
+            x_pt = x_pt + __shfl_xor_sync(0xffffffffu, x_pt, mm);
+        }
+    if (lane != 0) return;
     const double nwd = u128_to_double(W) * 0x1p-32;
     const long long it = st->iter;
     // shift update (Booth, Thom, Alavi 2009)
@@ -1352,10 +1366,16 @@ void launch_finalize(const DevInst *dinst, int n_inst, cudaStream_t s)
 }
 
 // H_jj - E_ref of the determinants created in this iteration (new list,
-// parity ^ 1), two per warp
+// parity ^ 1), two per warp.  The terms (h_pp of electron e1, or the pair
+// e1 < e2) are listed once per block in shared memory, and each warp keeps
+// the occupied orbitals of its two determinants there, so a term costs two
+// shared loads and one table load.
+constexpr int ND_PAIRS = 2080;  // n (n + 1) / 2 terms for up to 64 electrons
 __global__ void __launch_bounds__(256) k_new_diag(const DevInst *__restrict__ insts, int n_inst)
 {
-    const int lane = threadIdx.x & 31;
+    __shared__ unsigned short s_term[ND_PAIRS];   // e1 | e2 << 8, e2 = 255 for h_pp
+    __shared__ unsigned char s_orb[8][2][64];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarp = (int)((gridDim.x * blockDim.x) >> 5);
     for (int ii = 0; ii < n_inst; ii++) {
         const DevInst &I = insts[ii];
@@ -1363,16 +1383,71 @@ __global__ void __launch_bounds__(256) k_new_diag(const DevInst *__restrict__ in
         const int nn = I.st->new_n, np = I.st->parity ^ 1;
         const ulonglong2 *nkey = I.key[np];
         double *nhd = I.hd[np];
-        for (int q = 2 * gw; q < nn; q += 2 * nwarp) {
-            const unsigned d0 = I.newdet[q], d1 = q + 1 < nn ? I.newdet[q + 1] : d0;
-            const ulonglong2 k0 = nkey[d0], k1 = nkey[d1];
-            const u64 ka[2] = {k0.x, k1.x}, kb[2] = {k0.y, k1.y};
-            double hdv[2];
-            diag_exact_warp_multi<2>(I, ka, kb, hdv);
-            if (lane == 0) {
-                nhd[d0] = hdv[0];
-                if (q + 1 < nn) nhd[d1] = hdv[1];
+        const int n = I.n, na = I.na, N = I.norb, T = n + n * (n - 1) / 2;
+        if (n > 64) {  // beyond the table: the generic warp sum
+            for (int q = 2 * gw; q < nn; q += 2 * nwarp) {
+                const unsigned d0 = I.newdet[q], d1 = q + 1 < nn ? I.newdet[q + 1] : d0;
+                const ulonglong2 k0 = nkey[d0], k1 = nkey[d1];
+                const u64 ka[2] = {k0.x, k1.x}, kb[2] = {k0.y, k1.y};
+                double hdv[2];
+                diag_exact_warp_multi<2>(I, ka, kb, hdv);
+                if (lane == 0) {
+                    nhd[d0] = hdv[0];
+                    if (q + 1 < nn) nhd[d1] = hdv[1];
+                }
             }
+            continue;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < T; t += blockDim.x) {
+            if (t < n) { s_term[t] = (unsigned short)(t | (255 << 8)); continue; }
+            const int q = t - n;
+            int c = 1;
+            while ((c + 1) * c / 2 <= q) c++;
+            s_term[t] = (unsigned short)((q - c * (c - 1) / 2) | (c << 8));
+        }
+        __syncthreads();
+        for (int q = 2 * gw; q < nn; q += 2 * nwarp) {
+            const unsigned d[2] = {I.newdet[q], q + 1 < nn ? I.newdet[q + 1] : I.newdet[q]};
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const ulonglong2 key = nkey[d[k]];
+                for (int e = lane; e < n; e += 32)
+                    s_orb[wl][k][e] = (unsigned char)(e < na ? nth_set(key.x, e) : nth_set(key.y, e - na));
+            }
+            __syncwarp();
+            i128 part[2] = {0, 0};
+            for (int t0 = 0; t0 < T; t0 += 128) {
+                ulonglong2 v[2][4];
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    const int t = t0 + 32 * r + lane;
+                    const unsigned tm = t < T ? s_term[t] : 0u;
+                    const int e1 = (int)(tm & 0xffu), e2 = (int)(tm >> 8);
+                    const bool same = e2 != 255 && ((e1 < na) == (e2 < na));
+#pragma unroll
+                    for (int k = 0; k < 2; k++) {
+                        v[k][r] = make_ulonglong2(0, 0);
+                        if (t < T) {
+                            const int p1 = s_orb[wl][k][e1];
+                            v[k][r] = e2 == 255 ? __ldg(I.hfx + p1)
+                                                : __ldg((same ? I.JKfx : I.Jfx) + p1 * N + s_orb[wl][k][e2]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 2; k++)
+#pragma unroll
+                    for (int r = 0; r < 4; r++) part[k] += (i128)(((u128)v[k][r].y << 64) | (u128)v[k][r].x);
+            }
+            const i128 xref = (i128)(((u128)I.xref_hi << 64) | (u128)I.xref_lo);
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                i128 x = part[k];
+                for (int m = 16; m >= 1; m >>= 1) x += shfl_xor_i128(x, m);
+                if (lane == 0 && (k == 0 || q + 1 < nn)) nhd[d[k]] = fixed_to_double(x - xref, I.F);
+            }
+            __syncwarp();
         }
     }
 }
