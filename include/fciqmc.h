@@ -101,6 +101,12 @@ typedef struct {
  * layout; fciqmc_step and fciqmc_energy on the first handle drive and report
  * both (the variational-energy and PT2 estimators of fciqmc_stats), and
  * fciqmc_replica gives the second for read-only queries.
+ * adaptive_shift = 1 (Sec. V, adaptive shift): a non-initiator D_i dies with
+ * the local shift f_i S instead of S, f_i = A_i / T_i (1 without spawns),
+ * where every spawn of D_i in the iteration that survives Eq. (3) adds
+ * w = |H_ji| / |H_jj - E_ref - S| (truncated to 2^-64; w >= 2^36 left out)
+ * to T_i, and to A_i too if its target is occupied at the start of the
+ * iteration (the initiator rule accepts it).
  * generator: how double excitations are proposed (App. A).  0: uniformly
  * (electron pair, then hole pair).  1: pre-computed heat-bath sampling
  * (App. A, p(ab|ij) proportional to |H_ij^ab|): one Walker alias table per
@@ -132,6 +138,8 @@ typedef struct {
     int32_t replicas;    /* 1 (or 0): one run; 2: a replica pair (Sec. V) */
     int64_t trial_size;  /* N_T of the trial-wave-function estimator (0 = off) */
     int64_t trial_start; /* iterations after the shift starts to vary at which T is chosen */
+    int32_t adaptive_shift; /* 1: the adaptive shift of Sec. V for non-initiators */
+    int32_t pad1;
 } fciqmc_params;
 
 /* One row per completed iteration.  nw: walker number N_w = 2^-32 sum

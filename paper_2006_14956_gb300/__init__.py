@@ -64,7 +64,8 @@ class fciqmc_params(C.Structure):
                 ("shift_interval", C.c_int64), ("seed", C.c_uint64), ("semistoch_size", C.c_int64),
                 ("semistoch_start", C.c_int64), ("max_dets", C.c_int64), ("max_spawns", C.c_int64),
                 ("max_device_bytes", C.c_int64), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
-                ("generator", C.c_int32), ("replicas", C.c_int32), ("trial_size", C.c_int64), ("trial_start", C.c_int64)]
+                ("generator", C.c_int32), ("replicas", C.c_int32), ("trial_size", C.c_int64), ("trial_start", C.c_int64),
+                ("adaptive_shift", C.c_int32), ("pad1", C.c_int32)]
 
 
 class fciqmc_iter_stats(C.Structure):
@@ -216,7 +217,8 @@ def _system_struct(system):
 
 DEFAULTS = dict(tau=0.01, shift_damping=0.1, target_walkers=1e4, initial_walkers=10.0, initial_shift=0.0,
                 initiator_threshold=0.0, c_min=1.0, p_single=0.1, shift_interval=10, seed=1, semistoch_size=0,
-                semistoch_start=100, max_dets=0, max_spawns=0, max_device_bytes=0, generator=0, replicas=1, trial_size=0, trial_start=100)
+                semistoch_start=100, max_dets=0, max_spawns=0, max_device_bytes=0, generator=0, replicas=1, trial_size=0, trial_start=100,
+                adaptive_shift=0)
 
 
 def _params_struct(params):

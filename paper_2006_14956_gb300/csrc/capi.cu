@@ -221,6 +221,15 @@ static int alloc_layout(fciqmc_handle *h, DevInst &I, int bb)
     I.big_list = (int *)dev_alloc(h, nbk * sizeof(int));
     I.newdet = (unsigned *)dev_alloc(h, nm * sizeof(unsigned));
     if (!I.skey || !I.sw || !I.scnt_i || !I.scnt_n || !I.part || !I.big_list || !I.newdet) return FCIQMC_ERR_OUT_OF_MEMORY;
+    if (h->p.adaptive_shift)
+        for (int k = 0; k < 2; k++) {
+            I.facc[k] = (u64 *)dev_alloc(h, nm * 4 * sizeof(u64));
+            I.kidx[k] = (unsigned short *)dev_alloc(h, nbk * KIDX * sizeof(unsigned short));
+            if (!I.facc[k] || !I.kidx[k]) return FCIQMC_ERR_OUT_OF_MEMORY;
+            if (cudaMemsetAsync(I.kidx[k], 0, nbk * KIDX * sizeof(unsigned short), h->stream) != cudaSuccess ||
+                cudaMemsetAsync(I.facc[k], 0, nm * 4 * sizeof(u64), h->stream) != cudaSuccess)
+                return FCIQMC_ERR_CUDA;
+        }
     cudaMemsetAsync(I.scnt_i, 0, nbk * sizeof(int), h->stream);
     cudaMemsetAsync(I.scnt_n, 0, nbk * sizeof(int), h->stream);
     cudaMemsetAsync(I.part, 0, nbk * sizeof(Partial), h->stream);
@@ -237,6 +246,10 @@ static void free_layout(fciqmc_handle *h, DevInst &I)
     }
     dev_free(h, I.skey); dev_free(h, I.sw); dev_free(h, I.scnt_i); dev_free(h, I.scnt_n); dev_free(h, I.part);
     dev_free(h, I.big_list); dev_free(h, I.newdet);
+    for (int k = 0; k < 2; k++) {
+        dev_free(h, I.facc[k]); dev_free(h, I.kidx[k]);
+        I.facc[k] = nullptr; I.kidx[k] = nullptr;
+    }
     I.skey = nullptr; I.sw = nullptr; I.scnt_i = nullptr; I.scnt_n = nullptr; I.part = nullptr; I.big_list = nullptr;
     I.newdet = nullptr;
 }
@@ -314,6 +327,7 @@ static int grow_buckets(fciqmc_handle *h)
     CUDA_TRY(h, cudaMemcpyAsync(tmp + 1, &nI, sizeof(DevInst), cudaMemcpyHostToDevice, h->stream));
     const int par = h->hst.parity;
     launch_rebucket(tmp, tmp + 1, 1 << h->bb, par, h->stream);
+    if (h->p.adaptive_shift) launch_build_kidx(tmp + 1, par, 1 << nI.bb, h->stream);
     CUDA_TRY(h, cudaGetLastError());
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     int rc2 = read_state(h);
@@ -393,6 +407,10 @@ static int reset_after_error(fciqmc_handle *h)
     h->hst.need_main = 0;
     h->hst.n_spawn_over = 0;
     h->hst.new_n = 0;
+    if (h->p.adaptive_shift) {  // the failed iteration's weight sums are discarded
+        launch_build_kidx(h->dinst, h->hst.parity, (int)nbk, h->stream);
+        CUDA_TRY(h, cudaGetLastError());
+    }
     return write_state(h);
 }
 
@@ -838,6 +856,7 @@ static int create_run(const fciqmc_system *sys, const fciqmc_params *prm, u64 re
     I.target = P.target_walkers; I.A = P.shift_interval;
     I.semi_start = P.semistoch_start; I.semi_size = P.semistoch_size;
     I.trial_size = P.trial_size; I.trial_start = P.trial_start;
+    I.adaptive = P.adaptive_shift ? 1 : 0;
     I.ring_cap = h->ring_cap;
 
     // integrals and tables on the device
@@ -948,6 +967,11 @@ static int create_run(const fciqmc_system *sys, const fciqmc_params *prm, u64 re
     h->hst.stop_iter = LLONG_MAX;
     if (write_state(h)) return bail(FCIQMC_ERR_CUDA, h->err);
     if (upload_inst(h)) return bail(FCIQMC_ERR_CUDA, h->err);
+    if (P.adaptive_shift) {
+        launch_build_kidx(h->dinst, 0, 1 << bb, h->stream);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess)
+            return bail(FCIQMC_ERR_CUDA, "adaptive-shift index set-up failed");
+    }
     if (capture_graph(h)) return bail(FCIQMC_ERR_CUDA, h->err);
     *out = h;
     return FCIQMC_OK;
@@ -1336,9 +1360,12 @@ int fciqmc_import_state(fciqmc_handle *h, int64_t n, const uint64_t *alpha, cons
     CUDA_TRY(h, cudaMemcpy(h->hi.cnt[par], cnt_b.data(), nbk * sizeof(int), cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemset(h->hi.scnt_i, 0, nbk * sizeof(int)));
     CUDA_TRY(h, cudaMemset(h->hi.scnt_n, 0, nbk * sizeof(int)));
+    rc = ensure_side(h);
+    if (rc) return rc;
     rc = upload_inst(h);
     if (rc) return rc;
     launch_diag(h->dinst, par, (int)nbk, h->stream);
+    if (h->p.adaptive_shift) launch_build_kidx(h->dinst, par, (int)nbk, h->stream);
     CUDA_TRY(h, cudaGetLastError());
     memset(&h->hst, 0, sizeof(IterState));
     h->hst.stop_iter = LLONG_MAX;

@@ -415,4 +415,36 @@ static __device__ double diag_exact_warp(const DevInst &I, u64 a, u64 b)
     return o[0];
 }
 
+// exact H_ii - E_ref of one determinant by one thread (the same sum as the
+// warp version, term by term)
+static __device__ double diag_exact_thread(const DevInst &I, u64 a, u64 b)
+{
+    const int N = I.norb;
+    i128 x = 0;
+    for (int s = 0; s < 2; s++) {
+        u64 w = s ? b : a;
+        while (w) {
+            const int p = __ffsll((long long)w) - 1;
+            w &= w - 1;
+            x += fx_load(I.hfx, p);
+            u64 same = w;  // higher orbitals of the same spin
+            while (same) {
+                const int q = __ffsll((long long)same) - 1;
+                same &= same - 1;
+                x += fx_load(I.JKfx, p * N + q);
+            }
+            if (!s) {
+                u64 ob = b;
+                while (ob) {
+                    const int q = __ffsll((long long)ob) - 1;
+                    ob &= ob - 1;
+                    x += fx_load(I.Jfx, p * N + q);
+                }
+            }
+        }
+    }
+    const i128 xref = (i128)(((u128)I.xref_hi << 64) | (u128)I.xref_lo);
+    return fixed_to_double(x - xref, I.F);
+}
+
 }  // namespace fq

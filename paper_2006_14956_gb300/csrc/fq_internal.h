@@ -45,6 +45,7 @@ constexpr int BIG_BLOCKS = 64;        // blocks of the large-bucket annihilation
 constexpr int GBITS = 11;             // sub-hash groups per bucket in the annihilation sort
 constexpr int NGROUP = 1 << GBITS;
 constexpr int K5_THREADS = 1024;
+constexpr int KIDX = 2048;            // slots of the per-bucket list index (adaptive shift)
 
 struct HeavyChunk {  // a slice of the attempts of one determinant with many walkers
     u64 a, b;
@@ -52,6 +53,8 @@ struct HeavyChunk {  // a slice of the attempts of one determinant with many wal
     u64 k0;
     uint32_t count;
     uint32_t flags;  // bit 0: initiator, bit 1: parent in D
+    uint32_t slot;   // the determinant's main-list slot (adaptive shift)
+    uint32_t pad;
 };
 
 struct Partial {  // per-bucket reductions of one iteration
@@ -91,7 +94,7 @@ struct IterState {  // device-resident iteration state of one run
     long long stop_iter;    // K5 raises ERRB_STOP when iter reaches it
     long long trial_built;  // 1 once the trial space exists
     int new_n;              // determinants created in this iteration (their H_jj is computed by k_new_diag)
-    int pad2;
+    int err_at_start;       // err when the iteration's spawning began (nonzero: the iteration was skipped)
 };
 
 struct TrialEnt;
@@ -169,6 +172,13 @@ struct DevInst {
     const double2 *pchb_meta;
     const ulonglong2 *pchb_ent;
     u64 pchb_ss_base;
+    // adaptive shift (Sec. V): per main-list slot the exact sums A (accepted)
+    // and T (all) of the weights of the iteration's spawns, 4 words (A lo, hi,
+    // T lo, hi), by parity; per bucket KIDX slots of list positions + 1 (an
+    // open-addressing index of the list on the determinant hash), by parity
+    int adaptive;
+    u64 *facc[2];
+    unsigned short *kidx[2];
     // replica pair: key word 1 of every Philox draw; index of the other
     // replica in the instance table (-1: none); per-bucket lists of the
     // determinants of the iteration (side_cap entries per bucket)
@@ -201,6 +211,7 @@ size_t annihilate_smem_bytes();
 void launch_annihilate_big(const DevInst *dinst, int n_inst, cudaStream_t s);
 void launch_finalize(const DevInst *dinst, int n_inst, cudaStream_t s);
 void launch_new_diag(const DevInst *dinst, int n_inst, cudaStream_t s);
+void launch_build_kidx(const DevInst *dinst, int parity, int nb, cudaStream_t s);
 cudaError_t launch_replica_cross(const DevInst *dinst, int n_inst, int max_buckets, cudaStream_t s);
 cudaError_t replica_kernel_init();
 void launch_rebucket(const DevInst *src, const DevInst *dst, int nb_src, int parity, cudaStream_t s);

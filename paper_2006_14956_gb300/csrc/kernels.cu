@@ -1,6 +1,6 @@
 // kernels.cu -- the projector iteration of initiator-FCIQMC on GB300.
 //
-// One iteration (Eq. (4) of Guther et al. 2020) is four launches over the
+// One iteration (Eq. (4) of Guther et al. 2020) is six launches over the
 // bucketed walker list of every run in the batch:
 //   k_spawn        (a) spawning: ceil(|C_i|) attempts per determinant, one
 //                  Philox block, one excitation and one Slater-Condon element
@@ -10,13 +10,20 @@
 //                  split into fixed-size slices so no block waits on one
 //                  heavily populated determinant.
 //   k_annihilate   (b)+(c) per bucket: stage the bucket's walkers and spawns
-//                  in shared memory, group equal determinants by a sub-hash
-//                  counting sort, apply death and rounding, sum the spawns
-//                  exactly, apply the initiator rule and rounding, write the
-//                  new bucket, compute H_jj for new determinants, and reduce
-//                  N_w, E_num (Eq. (9)) and counters per bucket.
+//                  in shared memory, group equal determinants in a shared
+//                  open-addressing table, apply death and rounding, sum the
+//                  spawns exactly, apply the initiator rule and rounding,
+//                  write the new bucket, list the new determinants, and
+//                  reduce N_w, E_num (Eq. (9)) and counters per bucket.
+//   k_annihilate_big  the same for buckets too large for shared memory.
+//   k_new_diag     exact H_jj of the determinants created in the iteration.
 //   k_finalize     per run: total the bucket reductions, update the shift,
 //                  append the statistics row, flip the buffers.
+// Options add work to these launches or one more: the semi-stochastic
+// projection (semistoch.cu) before annihilation, the trial-estimator probe
+// (trial.cu tables) and the adaptive shift's weight sums inside spawning and
+// annihilation, and for a replica pair the cross join (replica.cu) before
+// k_finalize.
 // All of them read the iteration state from device memory, so one iteration
 // is captured once as a CUDA graph and replayed.
 #include <cuda_runtime.h>
@@ -61,8 +68,64 @@ __device__ __forceinline__ bool in_D(const DevInst &I, u64 a, u64 b)
 // doubles.  The words each attempt consumes and every decision are the same
 // as if the attempts were processed one by one.
 
+// what the spawning code knows about the parent beyond its key: its
+// main-list slot, the list parity and the shift at the start of the iteration
+struct SpawnCtx {
+    unsigned pslot;
+    int par;
+    double S;
+};
+
+// 128-bit add of q to the words p[0] (low), p[1] (high)
+__device__ __forceinline__ void atomic_add128(u64 *p, u128 q)
+{
+    const u64 lo = (u64)q, hi = (u64)(q >> 64);
+    const u64 old = atomicAdd((unsigned long long *)p, (unsigned long long)lo);
+    atomicAdd((unsigned long long *)(p + 1), (unsigned long long)(hi + (old + lo < old ? 1ULL : 0ULL)));
+}
+
+// adaptive shift (Sec. V): the weight |H_ji| / |H_jj - E_ref - S| of a spawn
+// from a non-initiator, truncated to 2^-64, into T of the parent, and into A
+// as well when the target is occupied at the start of the iteration (the
+// initiator rule accepts it); weights of 2^36 or more (|H_jj - E_ref - S| far
+// below |H_ji|) and zero denominators are left out
+__device__ __noinline__ void adaptive_account(const DevInst &I, u64 ta, u64 tb, double H, int bt, const SpawnCtx &cx)
+{
+    const unsigned short *kx = I.kidx[cx.par] + (size_t)bt * KIDX;
+    unsigned s = (unsigned)det_hash(ta, tb) & (unsigned)(KIDX - 1);
+    double hdj = 0.0;
+    bool occ = false, found = false;
+    for (int probe = 0; probe < KIDX; probe++) {
+        const unsigned v = __ldg(kx + s);
+        if (!v) break;
+        const size_t o = (size_t)bt * CAP_M + (v - 1);
+        const ulonglong2 k = I.key[cx.par][o];
+        if (k.x == ta && k.y == tb) {
+            found = true;
+            occ = !is_zero(I.c[cx.par][o]);
+            hdj = I.hd[cx.par][o];
+            break;
+        }
+        s = (s + 1) & (unsigned)(KIDX - 1);
+    }
+    if (!found) hdj = diag_exact_thread(I, ta, tb);
+    const double den = bitsd(dbits(hdj - cx.S) & ~SIGN64);
+    if (is_zero(den)) return;
+    const double w = bitsd(dbits(H) & ~SIGN64) / den;
+    u64 M;
+    int E;
+    split_abs(w, M, E);
+    const int sh = E + 64;  // w 2^64 = M 2^sh
+    if (sh + 53 > 100) return;  // w >= 2^36
+    const u128 q = sh >= 0 ? ((u128)M << sh) : (sh > -64 ? (u128)(M >> (-sh)) : (u128)0);
+    u64 *acc = I.facc[cx.par] + (size_t)cx.pslot * 4;
+    atomic_add128(acc + 2, q);
+    if (occ) atomic_add128(acc, q);
+}
+
 // append a surviving spawn (Eq. (3) rounding of the weight ws, D -> D filter) to its bucket
-__device__ __forceinline__ void emit_weight(const DevInst &I, u64 ta, u64 tb, double ws, unsigned flags, u64 w3)
+__device__ __forceinline__ void emit_weight(const DevInst &I, u64 ta, u64 tb, double ws, unsigned flags, u64 w3,
+                                            double H, const SpawnCtx &cx)
 {
     if (abs_lt(ws, I.cmin)) {
         ws = round_stoch(ws, I.cmin, I.cmin_log2, I.cmin_pow2, w3);
@@ -71,6 +134,7 @@ __device__ __forceinline__ void emit_weight(const DevInst &I, u64 ta, u64 tb, do
     if (!abs_lt(ws, 0x1p31)) { atomicOr(&I.st->err, ERRB_NUMERIC); return; }
     if ((flags & 2u) && in_D(I, ta, tb)) return;  // D -> D is applied exactly
     const int bt = bucket_of(det_hash(ta, tb), I.bb);
+    if (I.adaptive && !(flags & 1u)) adaptive_account(I, ta, tb, H, bt, cx);
     const int cap_s = I.cap_s;
     if (flags & 1u) {
         const int s = atomicAdd(I.scnt_i + bt, 1);
@@ -92,14 +156,15 @@ __device__ __forceinline__ void emit_weight(const DevInst &I, u64 ta, u64 tb, do
 
 // weight -H tau / p_gen(c) C_i / n_att of a uniformly generated excitation of class c
 __device__ __forceinline__ void emit_spawn(const DevInst &I, u64 ta, u64 tb, double H, int cls, double cper,
-                                           unsigned flags, u64 w3)
+                                           unsigned flags, u64 w3, const SpawnCtx &cx)
 {
     if (is_zero(H)) return;
-    emit_weight(I, ta, tb, neg_if(true, H * (I.lam[cls] * cper)), flags, w3);
+    emit_weight(I, ta, tb, neg_if(true, H * (I.lam[cls] * cper)), flags, w3, H, cx);
 }
 
 // lattice hop (Hubbard): electron w1, neighbour slot w2
-__device__ void spawn_hop(const DevInst &I, u64 pa, u64 pb, double cper, unsigned flags, u64 w1, u64 w2, u64 w3)
+__device__ void spawn_hop(const DevInst &I, u64 pa, u64 pb, double cper, unsigned flags, u64 w1, u64 w2, u64 w3,
+                       const SpawnCtx &cx)
 {
     const int e = (int)pick(w1, (u64)I.n);
     const int sp = e >= I.na;
@@ -110,11 +175,12 @@ __device__ void spawn_hop(const DevInst &I, u64 pa, u64 pb, double cper, unsigne
     const u64 between = p < q ? (mask_below(q) & ~mask_below(p + 1)) : (mask_below(p) & ~mask_below(q + 1));
     const double H = neg_if(__popcll(x & between) & 1, I.tmt);
     x ^= (1ULL << p) | (1ULL << q);
-    emit_spawn(I, sp ? pa : x, sp ? x : pb, H, CLS_HOP, cper, flags, w3);
+    emit_spawn(I, sp ? pa : x, sp ? x : pb, H, CLS_HOP, cper, flags, w3, cx);
 }
 
 // single excitation (App. A): electron w1, hole of its spin w2
-__device__ void spawn_single(const DevInst &I, u64 pa, u64 pb, double cper, unsigned flags, u64 w1, u64 w2, u64 w3)
+__device__ void spawn_single(const DevInst &I, u64 pa, u64 pb, double cper, unsigned flags, u64 w1, u64 w2, u64 w3,
+                       const SpawnCtx &cx)
 {
     const int e = (int)pick(w1, (u64)I.n);
     const int sp = e >= I.na;
@@ -126,11 +192,12 @@ __device__ void spawn_single(const DevInst &I, u64 pa, u64 pb, double cper, unsi
     const double v = single_exact(I, pa, pb, sp, i, a);
     const double H = neg_if(__popcll(x & between) & 1, v);
     x ^= (1ULL << i) | (1ULL << a);
-    emit_spawn(I, sp ? pa : x, sp ? x : pb, H, sp ? CLS_SINGLE_B : CLS_SINGLE_A, cper, flags, w3);
+    emit_spawn(I, sp ? pa : x, sp ? x : pb, H, sp ? CLS_SINGLE_B : CLS_SINGLE_A, cper, flags, w3, cx);
 }
 
 // double excitation (App. A): ordered electron pair w1, hole pair w2
-__device__ void spawn_double(const DevInst &I, u64 pa, u64 pb, double cper, unsigned flags, u64 w1, u64 w2, u64 w3)
+__device__ void spawn_double(const DevInst &I, u64 pa, u64 pb, double cper, unsigned flags, u64 w1, u64 w2, u64 w3,
+                       const SpawnCtx &cx)
 {
     const int N = I.norb, n = I.n, na = I.na;
     const unsigned xe = (unsigned)pick(w1, (u64)(n * (n - 1)));
@@ -172,7 +239,7 @@ __device__ void spawn_double(const DevInst &I, u64 pa, u64 pb, double cper, unsi
     par ^= flip_parity(xa, xb, N, Q1);
     par ^= flip_parity(xa, xb, N, Q0);
     const double v = (cls == CLS_DOUBLE_AB) ? eri4(I, oa, oi, ob, oj) : eri4(I, oa, oi, ob, oj) - eri4(I, oa, oj, ob, oi);
-    emit_spawn(I, ta, tb, neg_if(par, v), cls, cper, flags, w3);
+    emit_spawn(I, ta, tb, neg_if(par, v), cls, cper, flags, w3, cx);
 }
 
 // heat-bath double (App. A, pre-computed heat-bath sampling): ordered electron
@@ -182,7 +249,7 @@ __device__ void spawn_double(const DevInst &I, u64 pa, u64 pb, double cper, unsi
 // p_gen = p_pair |H| / S the weight is -sign(H) lambda_ij C_i / n_att,
 // lambda_ij = tau S / p_pair (stored per table).
 __device__ void spawn_double_pchb(const DevInst &I, u64 pa, u64 pb, double cper, unsigned flags, u64 w1, u64 w2,
-                                  u64 w3)
+                                  u64 w3, const SpawnCtx &cx)
 {
     const int N = I.norb, n = I.n, na = I.na;
     const unsigned xe = (unsigned)pick(w1, (u64)(n * (n - 1)));
@@ -240,7 +307,7 @@ __device__ void spawn_double_pchb(const DevInst &I, u64 pa, u64 pb, double cper,
     const double H = neg_if(par, v);
     if (is_zero(H)) return;
     const double wv = mt.x * cper;
-    emit_weight(I, ta, tb, neg_if(!(dbits(H) & SIGN64), wv), flags, w3);
+    emit_weight(I, ta, tb, neg_if(!(dbits(H) & SIGN64), wv), flags, w3, H, cx);
 }
 
 // class of one attempt from its first two words, or -1 for a failed attempt
@@ -280,6 +347,7 @@ struct K1Smem {
     long long wl[K1_THREADS / 32];
     int hdr_err, hdr_par;
     long long hdr_it;
+    double hdr_S;
 };
 
 // draw and classify the attempts of a chunk (attempt a of parent `det`, slot
@@ -288,7 +356,7 @@ struct K1Smem {
 // that no warp idles at the chunk's closing barrier while others still hold
 // a long queue.
 template <typename MAP>
-__device__ void run_attempts(const DevInst &I, K1Smem &S, long long it, unsigned A, MAP map)
+__device__ void run_attempts(const DevInst &I, K1Smem &S, long long it, unsigned A, MAP map, int par, double shift)
 {
     const int t = threadIdx.x, lane = t & 31;
     for (unsigned a0 = 0; a0 < A; a0 += CHUNK) {
@@ -344,13 +412,16 @@ __device__ void run_attempts(const DevInst &I, K1Smem &S, long long it, unsigned
             if (q < ns) {
                 const SpawnRec r = S.rec[CHUNK - 1 - q];
                 const ulonglong2 kk = map.key(r.det);
-                if (I.kind == FCIQMC_HUBBARD) spawn_hop(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3);
-                else spawn_single(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3);
+                const SpawnCtx cx{map.slot(r.det), par, shift};
+                if (I.kind == FCIQMC_HUBBARD)
+                    spawn_hop(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3, cx);
+                else spawn_single(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3, cx);
             } else if (q < ntot) {
                 const SpawnRec r = S.rec[q - ns];
                 const ulonglong2 kk = map.key(r.det);
-                if (I.pchb) spawn_double_pchb(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3);
-                else spawn_double(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3);
+                const SpawnCtx cx{map.slot(r.det), par, shift};
+                if (I.pchb) spawn_double_pchb(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3, cx);
+                else spawn_double(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3, cx);
             }
         }
         __syncthreads();
@@ -372,6 +443,8 @@ struct BucketMap {
     __device__ ulonglong2 key(unsigned d) const { return S->key[d]; }
     __device__ double cper(unsigned d) const { return S->cper[d]; }
     __device__ unsigned flags(unsigned d) const { return S->fl[d]; }
+    __device__ unsigned slot(unsigned d) const { return base + d; }
+    unsigned base;
 };
 
 // attempts k0 .. k0+count-1 of one heavy determinant
@@ -381,6 +454,7 @@ struct HeavyMap {
     __device__ ulonglong2 key(unsigned) const { return make_ulonglong2(h.a, h.b); }
     __device__ double cper(unsigned) const { return h.cper; }
     __device__ unsigned flags(unsigned) const { return h.flags; }
+    __device__ unsigned slot(unsigned) const { return h.slot; }
 };
 
 __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn(const DevInst *__restrict__ insts, const int *__restrict__ unit_start,
@@ -397,10 +471,13 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn(const DevInst *__restri
             S.hdr_err = *(volatile int *)&I.st->err;
             S.hdr_par = I.st->parity;
             S.hdr_it = I.st->iter;
+            S.hdr_S = I.st->S;
+            I.st->err_at_start = S.hdr_err;  // the same value from every block of the run
         }
         __syncthreads();
         const int err = S.hdr_err, par = S.hdr_par;
         const long long it = S.hdr_it;
+        const double shift = S.hdr_S;
         __syncthreads();
         if (err) continue;
         const int b = u - I.unit0;
@@ -440,6 +517,8 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn(const DevInst *__restri
                                 const u64 left = nat - h.k0;
                                 h.count = (unsigned)(left < HEAVY_ATT ? left : HEAVY_ATT);
                                 h.flags = fl;
+                                h.slot = (uint32_t)(base + d);
+                                h.pad = 0;
                                 I.heavy[q0 + q] = h;
                             }
                     } else {
@@ -477,8 +556,8 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn(const DevInst *__restri
         if (t == K1_THREADS - 1) S.off[CAP_M] = ex;
         __syncthreads();
         const unsigned total = S.off[CAP_M];
-        BucketMap map{&S};
-        run_attempts(I, S, it, total, map);
+        BucketMap map{&S, (unsigned)base};
+        run_attempts(I, S, it, total, map, par, shift);
         // attempts of this bucket (light and heavy)
         for (int o = 16; o >= 1; o >>= 1) att += __shfl_xor_sync(0xffffffffu, att, o);
         if (lane == 0) S.wl[warp] = att;
@@ -502,15 +581,18 @@ __global__ void __launch_bounds__(K1_THREADS) k_spawn_heavy(const DevInst *__res
             S.hdr_err = *(volatile int *)&I.st->err;
             S.qn[0] = I.st->heavy_n;
             S.hdr_it = I.st->iter;
+            S.hdr_par = I.st->parity;
+            S.hdr_S = I.st->S;
         }
         __syncthreads();
-        const int err = S.hdr_err, nh = S.qn[0];
+        const int err = S.hdr_err, nh = S.qn[0], par = S.hdr_par;
         const long long it = S.hdr_it;
+        const double shift = S.hdr_S;
         __syncthreads();
         if (err) continue;
         for (int q = blockIdx.x; q < nh; q += gridDim.x) {
             HeavyMap map{I.heavy[q]};
-            run_attempts(I, S, it, map.h.count, map);
+            run_attempts(I, S, it, map.h.count, map, par, shift);
         }
     }
 }
@@ -690,8 +772,16 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
                     const ulonglong2 k = W.key[e];
                     cp[h] = I.dc_new[d_index_of(I, k.x, k.y)];
                 } else {
-                    // C (1 - tau (H_ii - E_ref - S)), then rounding with the death draw
-                    const double fct = 1.0 - I.tau * (hdr[r0 + h] - shift);
+                    // C (1 - tau (H_ii - E_ref - S_i)), then rounding with the death draw;
+                    // S_i = f_i S for a non-initiator with the adaptive shift (Sec. V)
+                    double Si = shift;
+                    const bool init = (dbits(W.val[e]) & ~SIGN64) > dbits(I.n_a) || (W.eflag[e] & EF_REF);
+                    if (I.adaptive && !init) {
+                        const u64 *acc = I.facc[par] + (base + e) * 4;
+                        const u128 A = ((u128)acc[1] << 64) | acc[0], T = ((u128)acc[3] << 64) | acc[2];
+                        if (T != 0) Si = (u128_to_double(A) / u128_to_double(T)) * shift;
+                    }
+                    const double fct = 1.0 - I.tau * (hdr[r0 + h] - Si);
                     cp[h] = W.val[e] * fct;
                     draw[h] = !is_zero(cp[h]) && abs_lt(cp[h], I.cmin);
                 }
@@ -888,6 +978,23 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
     }
     if (bad) atomicOr(&I.st->err, ERRB_NUMERIC);
     __syncthreads();
+    // adaptive shift: the new list's index (hash -> position + 1) and zeroed
+    // weight sums for the next iteration's spawns
+    if (I.adaptive && !overflow) {
+        for (int q = t; q < KIDX; q += K3_THREADS) W.tab[q] = 0;
+        __syncthreads();
+        for (int r = 0; t + r * K3_THREADS < E; r++) {
+            const int e = t + r * K3_THREADS;
+            if (!(W.eflag[e] & EF_KEEP)) continue;
+            const ulonglong2 k = W.key[e];
+            unsigned sl = (unsigned)det_hash(k.x, k.y) & (unsigned)(KIDX - 1);
+            while (atomicCAS(&W.tab[sl], (IDX)0, (IDX)(W.opos[e] + 1)) != (IDX)0) sl = (sl + 1) & (unsigned)(KIDX - 1);
+            u64 *acc = I.facc[np] + (base + W.opos[e]) * 4;
+            acc[0] = 0; acc[1] = 0; acc[2] = 0; acc[3] = 0;
+        }
+        __syncthreads();
+        for (int q = t; q < KIDX; q += K3_THREADS) I.kidx[np][(size_t)b * KIDX + q] = (unsigned short)W.tab[q];
+    }
     // 7. new determinants: their slots go to the run's list; H_jj - E_ref is
     //    computed for all of them at once by k_new_diag, whose warps are not
     //    held back by this block's barriers
@@ -1051,8 +1158,12 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (t == 0) {
         int e = *(volatile int *)&st->err;
-        // a replica commits its iteration only together with its partner
-        if (!e && I.partner >= 0 && (*(volatile int *)&insts[I.partner].st->err & ERRB_STAGE)) {
+        // a replica commits its iteration only together with its partner: not
+        // if the partner skipped it (a flag was up when its spawning began) or
+        // failed in it
+        const IterState *pst = I.partner >= 0 ? insts[I.partner].st : nullptr;
+        if (!e && pst && (*(volatile const int *)&pst->err_at_start ||
+                          (*(volatile const int *)&pst->err & ERRB_STAGE))) {
             st->err = ERRB_PARTNER;
             e = ERRB_PARTNER;
         }
@@ -1187,6 +1298,28 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
 }
 
 // ------------------------------------------------------------------ growth and import
+// per-bucket list index of list `par` (adaptive shift), and zeroed weight sums
+__global__ void k_build_kidx(const DevInst *__restrict__ Ip, int par, int nb)
+{
+    __shared__ unsigned short tab[KIDX];
+    const DevInst &I = *Ip;
+    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+        for (int q = threadIdx.x; q < KIDX; q += blockDim.x) tab[q] = 0;
+        __syncthreads();
+        const int m = min(I.cnt[par][b], CAP_M);
+        for (int e = threadIdx.x; e < m; e += blockDim.x) {
+            const ulonglong2 k = I.key[par][(size_t)b * CAP_M + e];
+            unsigned sl = (unsigned)det_hash(k.x, k.y) & (unsigned)(KIDX - 1);
+            while (atomicCAS(&tab[sl], (unsigned short)0, (unsigned short)(e + 1)) != 0) sl = (sl + 1) & (unsigned)(KIDX - 1);
+            u64 *acc = I.facc[par] + ((size_t)b * CAP_M + e) * 4;
+            acc[0] = 0; acc[1] = 0; acc[2] = 0; acc[3] = 0;
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < KIDX; q += blockDim.x) I.kidx[par][(size_t)b * KIDX + q] = tab[q];
+        __syncthreads();
+    }
+}
+
 // split every bucket of src (bb bits) into two buckets of dst (bb+1 bits)
 __global__ void k_rebucket(const DevInst *__restrict__ src, const DevInst *__restrict__ dst, int nb_src, int par)
 {
@@ -1306,6 +1439,12 @@ static int num_sms()
         if (g_num_sms <= 0) g_num_sms = 1;
     }
     return g_num_sms;
+}
+
+void launch_build_kidx(const DevInst *dinst, int parity, int nb, cudaStream_t s)
+{
+    int grid = nb < num_sms() * 8 ? nb : num_sms() * 8;
+    k_build_kidx<<<grid, 256, 0, s>>>(dinst, parity, nb);
 }
 
 // launch geometry, chosen by fciqmc_autotune (blocks per SM)

@@ -24,37 +24,6 @@ constexpr int XC_THREADS = 256;
 constexpr int XC_TABBITS = 14;   // hash table of up to 8192 first-replica entries
 constexpr int XC_PT2CAP = 1024;  // matched rejected determinants queued for the warps
 
-// exact H_ii - E_ref by one thread (overflow of the warp queue)
-__device__ double diag_exact_thread(const DevInst &I, u64 a, u64 b)
-{
-    const int N = I.norb;
-    i128 x = 0;
-    for (int s = 0; s < 2; s++) {
-        u64 w = s ? b : a;
-        while (w) {
-            const int p = __ffsll((long long)w) - 1;
-            w &= w - 1;
-            x += fx_load(I.hfx, p);
-            u64 same = w;  // higher orbitals of the same spin
-            while (same) {
-                const int q = __ffsll((long long)same) - 1;
-                same &= same - 1;
-                x += fx_load(I.JKfx, p * N + q);
-            }
-            if (!s) {
-                u64 ob = b;
-                while (ob) {
-                    const int q = __ffsll((long long)ob) - 1;
-                    ob &= ob - 1;
-                    x += fx_load(I.Jfx, p * N + q);
-                }
-            }
-        }
-    }
-    const i128 xref = (i128)(((u128)I.xref_hi << 64) | (u128)I.xref_lo);
-    return fixed_to_double(x - xref, I.F);
-}
-
 __global__ void __launch_bounds__(XC_THREADS) k_replica_cross(const DevInst *__restrict__ insts, int n_inst)
 {
     extern __shared__ unsigned xtab[];
@@ -68,7 +37,7 @@ __global__ void __launch_bounds__(XC_THREADS) k_replica_cross(const DevInst *__r
         if (A.partner <= ii || !A.side) continue;  // the first replica of each pair does the join
         const DevInst &B = insts[A.partner];
         const int errs = *(volatile int *)&A.st->err | *(volatile int *)&B.st->err;
-        if (errs & ERRB_STAGE) continue;  // the iteration will be repeated
+        if ((errs & ERRB_STAGE) || A.st->err_at_start || B.st->err_at_start) continue;  // not committed: repeated
         const double e0 = (A.st->S + B.st->S) * 0.5;
         const int nbk = 1 << A.bb;
         if (A.bb != B.bb) {  // the host keeps the layouts equal; never join unequal ones

@@ -34,7 +34,7 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(fq.fciqmc_iter_stats) == 128
     assert ctypes.sizeof(fq.fciqmc_stats) == 208
     assert ctypes.sizeof(fq.fciqmc_system) == 96
-    assert ctypes.sizeof(fq.fciqmc_params) == 176
+    assert ctypes.sizeof(fq.fciqmc_params) == 184
 
 
 def test_create_without_gpu_fails_cleanly():
