@@ -71,6 +71,8 @@ struct fciqmc_handle {
     double trial_ET = 0.0;
     const ulonglong2 *trial_key = nullptr;
     const double *trial_cT = nullptr;
+    // adaptive shift: list index and weight sums to rebuild at the next upload
+    bool kidx_dirty = false;
     // replica pair: the other replica (owned by the first), replica index
     fciqmc_handle *partner = nullptr;
     bool secondary = false;
@@ -259,6 +261,11 @@ static int upload_inst(fciqmc_handle *h)
     CUDA_TRY(h, cudaMemcpyAsync(h->dinst, &h->hi, sizeof(DevInst), cudaMemcpyHostToDevice, h->stream));
     int us[2] = {0, 1 << h->bb};
     CUDA_TRY(h, cudaMemcpyAsync(h->dunit, us, sizeof(us), cudaMemcpyHostToDevice, h->stream));
+    if (h->p.adaptive_shift && h->kidx_dirty) {  // index of the current list, zeroed weight sums
+        launch_build_kidx(h->dinst, h->hst.parity, 1 << h->bb, h->stream);
+        CUDA_TRY(h, cudaGetLastError());
+        h->kidx_dirty = false;
+    }
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return FCIQMC_OK;
 }
@@ -407,10 +414,10 @@ static int reset_after_error(fciqmc_handle *h)
     h->hst.need_main = 0;
     h->hst.n_spawn_over = 0;
     h->hst.new_n = 0;
-    if (h->p.adaptive_shift) {  // the failed iteration's weight sums are discarded
-        launch_build_kidx(h->dinst, h->hst.parity, (int)nbk, h->stream);
-        CUDA_TRY(h, cudaGetLastError());
-    }
+    // the failed iteration's adaptive-shift weight sums are discarded when the
+    // descriptor is next uploaded (the device copy may still describe an old
+    // layout here)
+    h->kidx_dirty = true;
     return write_state(h);
 }
 
