@@ -381,12 +381,16 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h2 = fq.fciqmc_create(sysd, dict(prm, semistoch_size=0) if big else prm)
+    t1 = time.perf_counter()
     fq.fciqmc_import_state(h2, host_state["alpha"], host_state["beta"], host_state["c"], shift["iteration"],
                            shift["S"], shift["vary"], shift["shift_start"], shift["cnt"], shift["nw_last"])
+    t2 = time.perf_counter()
     fq.fciqmc_step(h2, E2E_STEPS)
+    t3 = time.perf_counter()
     out_state = fq.fciqmc_export_state(h2)
     en = fq.fciqmc_energy(h2)
     e2e_el = time.perf_counter() - t0
+    e2e_phases = {"create": t1 - t0, "import": t2 - t1, "steps": t3 - t2, "export_energy": t0 + e2e_el - t3}
     st2 = fq.fciqmc_iter_stats_get(h2)
     e2e_att = float(np.sum(st2["attempts"][-E2E_STEPS:]))
     h2d = sysd["h1"].nbytes + sysd["eri"].nbytes + host_state["alpha"].nbytes * 2 + host_state["c"].nbytes
@@ -428,7 +432,8 @@ def main():
             "e2e": {"value": e2e_att / e2e_el, "unit": "spawn attempts/s", "h2d_bytes_per_step": h2d / E2E_STEPS,
                     "d2h_bytes_per_step": d2h / E2E_STEPS,
                     "job": "create + import %s checkpoint + %d steps + export + energy" %
-                           ("2e5-determinant sample" if big else "1e6-walker", E2E_STEPS)},
+                           ("2e5-determinant sample" if big else "1e6-walker", E2E_STEPS),
+                    "phases_s": e2e_phases},
             "gpu_launches": args.steps * (7 if prm.get("semistoch_size", 0) else 6),
             "wall_s_timed": wall,
             "clocks": clk.summary(),

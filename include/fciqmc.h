@@ -276,7 +276,10 @@ int64_t fciqmc_num_dets(fciqmc_handle *h);
 /* Copies the walker list to host arrays of capacity cap, sorted by (alpha,
  * beta) ascending; hdiag = H_ii - E_ref; flags bit 0 = reference, bit 1 =
  * in D.  *n_out receives the number of determinants (also when it exceeds
- * cap, in which case FCIQMC_ERR_CAPACITY is returned and nothing copied). */
+ * cap, in which case FCIQMC_ERR_CAPACITY is returned and nothing copied).
+ * The list is compacted and radix-sorted on the device in transient scratch
+ * (about 68 bytes per determinant, from the run's allocator); when
+ * max_device_bytes leaves no room for it the sort runs on the host. */
 int fciqmc_export_state(fciqmc_handle *h, int64_t cap, uint64_t *alpha, uint64_t *beta, double *c,
                         double *hdiag, int32_t *flags, int64_t *n_out);
 
@@ -288,7 +291,11 @@ int fciqmc_export_shift(fciqmc_handle *h, int64_t *iteration, double *S, int32_t
 
 /* Replaces the walker list and the shift state (a restart from a checkpoint).
  * Keys must be distinct, with the right electron counts; the reference
- * determinant is kept (added with C = 0 when absent). */
+ * determinant is kept (added with C = 0 when absent).  The bucket count grows
+ * (one allocation) until every bucket holds at most half its capacity.
+ * FCIQMC_ERR_INVALID_ARG for a wrong electron count, an orbital beyond norb,
+ * a non-finite amplitude, or keys that crowd one bucket even at 2^24 buckets
+ * (duplicates); duplicates that do not are not detected. */
 int fciqmc_import_state(fciqmc_handle *h, int64_t n, const uint64_t *alpha, const uint64_t *beta,
                         const double *c, int64_t iteration, double S, int32_t vary, int64_t shift_start,
                         int64_t cnt, uint64_t nw_last_hi, uint64_t nw_last_lo);

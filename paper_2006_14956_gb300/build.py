@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfciqmc_gb300.so")
-SOURCES = ["kernels.cu", "capi.cu", "semistoch.cu", "noalloc.cu", "pchb.cu", "trial.cu", "replica.cu"]
+SOURCES = ["kernels.cu", "capi.cu", "semistoch.cu", "noalloc.cu", "pchb.cu", "trial.cu", "replica.cu", "export.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",

@@ -73,6 +73,7 @@ struct fciqmc_handle {
     const double *trial_cT = nullptr;
     // adaptive shift: list index and weight sums to rebuild at the next upload
     bool kidx_dirty = false;
+    int step_rc = 0;  // error of the last step that failed on this run (cleared by the next good step)
     // replica pair: the other replica (owned by the first), replica index
     fciqmc_handle *partner = nullptr;
     bool secondary = false;
@@ -1275,6 +1276,38 @@ int fciqmc_export_state(fciqmc_handle *h, int64_t cap, uint64_t *alpha, uint64_t
     *n_out = n;
     if (n > cap) return fail(h, FCIQMC_ERR_CAPACITY, "export buffer too small");
     if (n > 0 && (!alpha || !beta || !c)) return FCIQMC_ERR_INVALID_ARG;
+    if (n == 0) return FCIQMC_OK;
+    // on the device: compaction, radix sort by (alpha, beta), gather; only the
+    // n live entries are copied out.  Transient scratch from the run's
+    // allocator; where it cannot be had, the same order is produced on the host.
+    {
+        std::vector<long long> off(nbk + 1, 0);
+        for (size_t b = 0; b < nbk; b++) off[b + 1] = off[b] + cnt[b];
+        const size_t off_bytes = ((nbk + 1) * sizeof(long long) + 255) & ~(size_t)255;
+        unsigned char *scr = (unsigned char *)dev_alloc(h, off_bytes + export_scratch_bytes(n));
+        if (scr) {
+            const u64 *oa, *ob;
+            const double *oc, *ohd;
+            const int32_t *ofl;
+            cudaError_t e = cudaMemcpyAsync(scr, off.data(), (nbk + 1) * sizeof(long long), cudaMemcpyHostToDevice,
+                                            h->stream);
+            if (e == cudaSuccess)
+                e = export_sorted(h->hi.key[par], h->hi.c[par], h->hi.hd[par], h->hi.fl[par], h->hi.cnt[par],
+                                  (const long long *)scr, (int)nbk, n, h->norb, scr + off_bytes, &oa, &ob, &oc, &ohd,
+                                  &ofl, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(alpha, oa, n * sizeof(u64), cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(beta, ob, n * sizeof(u64), cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(c, oc, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess && hdiag)
+                e = cudaMemcpyAsync(hdiag, ohd, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess && flags)
+                e = cudaMemcpyAsync(flags, ofl, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            dev_free(h, scr);
+            if (e != cudaSuccess) return fail(h, FCIQMC_ERR_CUDA, std::string("export: ") + cudaGetErrorString(e));
+            return FCIQMC_OK;
+        }
+    }
     std::vector<ulonglong2> k(nm);
     std::vector<double> cc(nm), hh(nm);
     std::vector<uint8_t> ff(nm);
@@ -1321,50 +1354,94 @@ int fciqmc_import_state(fciqmc_handle *h, int64_t n, const uint64_t *alpha, cons
 {
     if (!h || n < 0 || (n > 0 && (!alpha || !beta || !c)) || iteration < 0) return FCIQMC_ERR_INVALID_ARG;
     const u64 normask = h->norb >= 64 ? ~0ULL : ((1ULL << h->norb) - 1);
-    std::vector<u64> A(alpha, alpha + n), B(beta, beta + n);
-    std::vector<double> C(c, c + n);
     bool has_ref = false;
     for (int64_t i = 0; i < n; i++) {
-        if (__builtin_popcountll(A[i]) != h->na || __builtin_popcountll(B[i]) != h->nb || ((A[i] | B[i]) & ~normask) ||
-            !std::isfinite(C[i]))
+        if (__builtin_popcountll(alpha[i]) != h->na || __builtin_popcountll(beta[i]) != h->nb ||
+            ((alpha[i] | beta[i]) & ~normask) || !std::isfinite(c[i]))
             return fail(h, FCIQMC_ERR_INVALID_ARG, "imported determinant with wrong electron count or bad amplitude");
-        if (A[i] == h->ref_a && B[i] == h->ref_b) has_ref = true;
+        if (alpha[i] == h->ref_a && beta[i] == h->ref_b) has_ref = true;
     }
-    if (!has_ref) { A.push_back(h->ref_a); B.push_back(h->ref_b); C.push_back(0.0); }
+    // the reference, when absent, is appended as entry n with C = 0
+    const int64_t nt = n + (has_ref ? 0 : 1);
+    auto key_a = [&](int64_t i) { return i < n ? (u64)alpha[i] : h->ref_a; };
+    auto key_b = [&](int64_t i) { return i < n ? (u64)beta[i] : h->ref_b; };
     int rc = read_state(h);
     if (rc) return rc;
-    for (;;) {
-        const size_t nbk = (size_t)1 << h->bb;
-        std::vector<int> cnt_b(nbk, 0);
+    // the fewest buckets (at least the current number) that hold every
+    // bucket's determinants within half the main capacity; one allocation
+    std::vector<u64> hash((size_t)nt);
+    for (int64_t i = 0; i < nt; i++) hash[i] = det_hash_host(key_a(i), key_b(i));
+    int bb = h->bb;
+    for (;; bb++) {
+        std::vector<int> cnt_b((size_t)1 << bb, 0);
         bool over = false;
-        for (size_t i = 0; i < A.size(); i++) {
-            int b = h->bb ? (int)(det_hash_host(A[i], B[i]) >> (64 - h->bb)) : 0;
-            if (++cnt_b[b] > CAP_M / 2) over = true;
-        }
+        for (int64_t i = 0; i < nt && !over; i++)
+            if (++cnt_b[bb ? (size_t)(hash[i] >> (64 - bb)) : 0] > CAP_M / 2) over = true;
         if (!over) break;
+        if (bb >= 24)  // distinct keys never crowd one bucket at 2^24 buckets
+            return fail(h, FCIQMC_ERR_INVALID_ARG, "imported keys crowd one bucket (duplicate determinants?)");
+    }
+    if (bb != h->bb) {
         DevInst nI = h->hi;
-        rc = alloc_layout(h, nI, h->bb + 1);
+        rc = alloc_layout(h, nI, bb);
         if (rc) return fail(h, rc, "out of device memory");
         free_layout(h, h->hi);
         h->hi = nI;
         h->bb = nI.bb;
     }
+    // slot of every determinant: its bucket, in input order
     const size_t nbk = (size_t)1 << h->bb, nm = nbk * CAP_M;
     std::vector<int> cnt_b(nbk, 0);
-    std::vector<ulonglong2> k(nm);
-    std::vector<double> cc(nm, 0.0);
-    std::vector<uint8_t> ff(nm, 0);
-    for (size_t i = 0; i < A.size(); i++) {
-        int b = h->bb ? (int)(det_hash_host(A[i], B[i]) >> (64 - h->bb)) : 0;
-        size_t o = (size_t)b * CAP_M + cnt_b[b]++;
-        k[o].x = A[i]; k[o].y = B[i];
-        cc[o] = C[i];
+    std::vector<u64> slot((size_t)nt);
+    for (int64_t i = 0; i < nt; i++) {
+        const size_t b = h->bb ? (size_t)(hash[i] >> (64 - h->bb)) : 0;
+        slot[i] = b * CAP_M + (size_t)cnt_b[b]++;
     }
     const int par = 0;
-    CUDA_TRY(h, cudaMemcpy(h->hi.key[par], k.data(), nm * sizeof(ulonglong2), cudaMemcpyHostToDevice));
-    CUDA_TRY(h, cudaMemcpy(h->hi.c[par], cc.data(), nm * sizeof(double), cudaMemcpyHostToDevice));
-    CUDA_TRY(h, cudaMemcpy(h->hi.fl[par], ff.data(), nm, cudaMemcpyHostToDevice));
-    CUDA_TRY(h, cudaMemcpy(h->hi.cnt[par], cnt_b.data(), nbk * sizeof(int), cudaMemcpyHostToDevice));
+    // the compact input goes to the device and a kernel scatters it into the
+    // bucket layout (transient scratch from the run's allocator); where that
+    // scratch cannot be had, the padded layout is built on the host
+    unsigned char *scr = (unsigned char *)dev_alloc(h, (size_t)nt * 32);
+    if (scr) {
+        u64 *da = (u64 *)scr, *db = da + nt, *ds = db + nt;
+        double *dc = (double *)(ds + nt);
+        const u64 ra = h->ref_a, rb = h->ref_b;
+        const double zero = 0.0;
+        cudaError_t e = cudaSuccess;
+        if (n > 0) {
+            e = cudaMemcpyAsync(da, alpha, (size_t)n * sizeof(u64), cudaMemcpyHostToDevice, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(db, beta, (size_t)n * sizeof(u64), cudaMemcpyHostToDevice, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dc, c, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        }
+        if (e == cudaSuccess && !has_ref) {
+            e = cudaMemcpyAsync(da + n, &ra, sizeof(u64), cudaMemcpyHostToDevice, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(db + n, &rb, sizeof(u64), cudaMemcpyHostToDevice, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dc + n, &zero, sizeof(double), cudaMemcpyHostToDevice, h->stream);
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ds, slot.data(), (size_t)nt * sizeof(u64), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->hi.c[par], 0, nm * sizeof(double), h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->hi.fl[par], 0, nm, h->stream);
+        if (e == cudaSuccess) e = launch_import_scatter(da, db, dc, ds, nt, h->hi.key[par], h->hi.c[par], h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->hi.cnt[par], cnt_b.data(), nbk * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        dev_free(h, scr);
+        if (e != cudaSuccess) return fail(h, FCIQMC_ERR_CUDA, std::string("import: ") + cudaGetErrorString(e));
+    } else {
+        std::vector<ulonglong2> k(nm);
+        std::vector<double> cc(nm, 0.0);
+        std::vector<uint8_t> ff(nm, 0);
+        for (int64_t i = 0; i < nt; i++) {
+            k[slot[i]].x = key_a(i);
+            k[slot[i]].y = key_b(i);
+            cc[slot[i]] = i < n ? c[i] : 0.0;
+        }
+        CUDA_TRY(h, cudaMemcpy(h->hi.key[par], k.data(), nm * sizeof(ulonglong2), cudaMemcpyHostToDevice));
+        CUDA_TRY(h, cudaMemcpy(h->hi.c[par], cc.data(), nm * sizeof(double), cudaMemcpyHostToDevice));
+        CUDA_TRY(h, cudaMemcpy(h->hi.fl[par], ff.data(), nm, cudaMemcpyHostToDevice));
+        CUDA_TRY(h, cudaMemcpy(h->hi.cnt[par], cnt_b.data(), nbk * sizeof(int), cudaMemcpyHostToDevice));
+    }
     CUDA_TRY(h, cudaMemset(h->hi.scnt_i, 0, nbk * sizeof(int)));
     CUDA_TRY(h, cudaMemset(h->hi.scnt_n, 0, nbk * sizeof(int)));
     rc = ensure_side(h);
@@ -1518,7 +1595,7 @@ int fciqmc_step_batch(fciqmc_handle **hs, int32_t k, int64_t n_iter)
                 const int bb0 = h->bb, nd0 = h->nd, cap0 = h->hi.cap_s, hc0 = h->heavy_cap;
                 h->hst.err = err;  // keep the stop flag off while handling
                 rc = handle_flags(h, &retries[i]);
-                if (rc) break;
+                if (rc) { h->step_rc = rc; break; }
                 if (h->bb != bb0 || h->nd != nd0 || h->hi.cap_s != cap0 || h->heavy_cap != hc0) changed = true;
                 h->hst.stop_iter = target[i];
                 if (h->hst.iter >= target[i]) h->hst.err |= ERRB_STOP;
@@ -1543,6 +1620,8 @@ int fciqmc_step_batch(fciqmc_handle **hs, int32_t k, int64_t n_iter)
     cleanup();
     dev_free(h0, dinst);
     dev_free(h0, dunit);
+    if (!rc)
+        for (int i = 0; i < k; i++) hs[i]->step_rc = 0;
     return rc;
 }
 
@@ -1796,7 +1875,9 @@ struct fciqmc_server {
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
 };
 
-// device memory a request needs when admitted (its initial layout and integrals)
+// device memory a request needs when admitted: its initial layout and
+// integrals, and the first growth of the spawn regions (to 4 CAP_S0 slots per
+// bucket, old and new buffers held together, with the large-bucket scratch)
 static int64_t estimate_bytes(const Request &r)
 {
     const int N = r.sys.kind == FCIQMC_HUBBARD ? r.sys.lx * r.sys.ly : r.sys.norb;
@@ -1804,8 +1885,14 @@ static int64_t estimate_bytes(const Request &r)
     double dets = r.p.max_dets > 0 ? (double)r.p.max_dets : std::min(std::max(4096.0, r.p.target_walkers), 8388608.0);
     int bb = 0;
     while (((double)(1LL << bb)) * (CAP_M / 2.5) < dets && bb < 24) bb++;
-    const double per_bucket = 2.0 * CAP_M * (16 + 8 + 8 + 1) + CAP_S0 * 24.0 + 2 * 8 + sizeof(Partial) + 3 * 4;
-    return (int64_t)((double)(1LL << bb) * per_bucket + 8.0 * (N * N + ne) + 48.0 * N * N + 4096.0 * 88 + 1.0e6);
+    const double per_bucket = 2.0 * CAP_M * (16 + 8 + 8 + 1) + 5.0 * CAP_S0 * 24.0 + 2 * 8 + sizeof(Partial) + 3 * 4 +
+                              4.0 * CAP_M;
+    const double ecap = CAP_M + 4.0 * CAP_S0;
+    int tb = TABBITS;
+    while ((double)(1 << tb) < 2.0 * ecap) tb++;
+    const double scratch = (double)BIG_BLOCKS * (ecap * 52.0 + 4.0 * (double)(1 << tb) + 256.0);
+    return (int64_t)((double)(1LL << bb) * per_bucket + scratch + 8.0 * (N * N + ne) + 48.0 * N * N + 4096.0 * 88 +
+                     1.0e6);
 }
 
 extern "C" {
@@ -1916,15 +2003,26 @@ int fciqmc_server_tick(fciqmc_server *srv, int64_t n_iter, int32_t *n_active)
         for (int64_t id : srv->running) hs.push_back(srv->req[id].h);
         int rc = fciqmc_step_batch(hs.data(), (int32_t)hs.size(), n_iter);
         if (rc) {
-            // find the failing run(s): step each alone to isolate the error
+            // the failing run(s): a recorded step error, a flag left up, or no
+            // readable energy; when none can be told apart every run of the
+            // batch is retired, so that a tick never repeats a failing batch
+            int n_retired = 0;
             for (int64_t id : srv->running) {
                 Request &r = srv->req[id];
                 fciqmc_stats st;
-                if (fciqmc_energy(r.h, &st) != FCIQMC_OK || r.h->hst.err & ~(ERRB_STOP | ERRB_PAUSE_SEMI | ERRB_PAUSE_TRIAL)) {
+                if (r.h->step_rc || fciqmc_energy(r.h, &st) != FCIQMC_OK ||
+                    r.h->hst.err & ~(ERRB_STOP | ERRB_PAUSE_SEMI | ERRB_PAUSE_TRIAL)) {
+                    r.st.error = r.h->step_rc ? r.h->step_rc : rc;
+                    retire(srv, r, 4);
+                    n_retired++;
+                }
+            }
+            if (!n_retired)
+                for (int64_t id : srv->running) {
+                    Request &r = srv->req[id];
                     r.st.error = rc;
                     retire(srv, r, 4);
                 }
-            }
         }
     }
     // 3. retire converged or exhausted requests
@@ -2066,8 +2164,8 @@ extern "C" void fciqmc_free_system(fciqmc_system *sys)
 extern "C" int fciqmc_autotune(fciqmc_handle **hs, int32_t k, int64_t n_iter, int32_t out[3])
 {
     if (!hs || k < 1 || n_iter < 1 || !out) return FCIQMC_ERR_INVALID_ARG;
-    const int spawn_c[] = {2, 4, 8, 16}, anni_c[] = {1, 2, 4}, heavy_c[] = {1, 2, 4};
-    int best_s = 8, best_h = 2, best_a = 2;
+    const int spawn_c[] = {2, 4, 8, 16}, anni_c[] = {1, 2, 3}, heavy_c[] = {1, 2, 4};
+    int best_s = 8, best_h = 2, best_a = 3;
     double best = 1e300;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);

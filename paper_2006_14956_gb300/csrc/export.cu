@@ -1,0 +1,219 @@
+// export.cu -- moving the walker list between the host and the bucket layout.
+// Import: the compact input is scattered into its slots by one kernel.
+// Export, in (alpha, beta) order: the occupied slots of every bucket are compacted,
+// sorted by a least-significant-digit radix sort over the orbital bits in use
+// (8-bit digits, beta word first, each pass stable), and C, H_ii - E_ref and
+// the flags are gathered in that order.  Only the n live entries then cross
+// to the host.
+#include <cuda_runtime.h>
+
+#include "fq_internal.h"
+
+namespace fq {
+
+constexpr int XS_THREADS = 256;  // one thread per digit value in the scatter
+constexpr int XS_ROUNDS = 8;
+constexpr int XS_TILE = XS_THREADS * XS_ROUNDS;
+constexpr int XS_SCAN = 1024;
+
+// occupied slots of bucket b go to [off[b], off[b] + cnt[b])
+__global__ void k_export_compact(const ulonglong2 *__restrict__ key, const int *__restrict__ cnt,
+                                 const long long *__restrict__ off, int nbk, u64 *ka, u64 *kb, u64 *idx)
+{
+    for (int b = blockIdx.x; b < nbk; b += gridDim.x) {
+        const int m = cnt[b];
+        const long long o = off[b];
+        for (int e = threadIdx.x; e < m; e += blockDim.x) {
+            const size_t s = (size_t)b * CAP_M + e;
+            const ulonglong2 k = key[s];
+            ka[o + e] = k.x;
+            kb[o + e] = k.y;
+            idx[o + e] = s;
+        }
+    }
+}
+
+__device__ __forceinline__ int digit_of(const u64 *ka, const u64 *kb, long long i, int word, int shift)
+{
+    return (int)(((word ? ka[i] : kb[i]) >> shift) & 255u);
+}
+
+// digit counts of every tile, stored digit-major: hist[d * ntiles + tile]
+__global__ void __launch_bounds__(XS_THREADS) k_export_hist(const u64 *__restrict__ ka, const u64 *__restrict__ kb,
+                                                            long long n, int word, int shift, int *hist, int ntiles)
+{
+    __shared__ int s_h[256];
+    const int t = threadIdx.x;
+    s_h[t] = 0;
+    __syncthreads();
+    const long long i0 = (long long)blockIdx.x * XS_TILE;
+    for (int r = 0; r < XS_ROUNDS; r++) {
+        const long long i = i0 + (long long)r * XS_THREADS + t;
+        if (i < n) atomicAdd(&s_h[digit_of(ka, kb, i, word, shift)], 1);
+    }
+    __syncthreads();
+    hist[(size_t)t * ntiles + blockIdx.x] = s_h[t];
+}
+
+// exclusive scan of hist[0 .. m) in place (one block): each thread takes a
+// contiguous segment, the segment sums are scanned in shared memory
+__global__ void __launch_bounds__(XS_SCAN) k_export_scan(int *hist, int m)
+{
+    __shared__ long long s[XS_SCAN];
+    const int t = threadIdx.x;
+    const int per = (m + XS_SCAN - 1) / XS_SCAN;
+    const int a = min(m, t * per), b = min(m, a + per);
+    long long sum = 0;
+    for (int q = a; q < b; q++) sum += hist[q];
+    s[t] = sum;
+    __syncthreads();
+    for (int o = 1; o < XS_SCAN; o <<= 1) {
+        const long long v = t >= o ? s[t - o] : 0;
+        __syncthreads();
+        s[t] += v;
+        __syncthreads();
+    }
+    long long run = s[t] - sum;
+    for (int q = a; q < b; q++) {
+        const int c = hist[q];
+        hist[q] = (int)run;
+        run += c;
+    }
+}
+
+// stable scatter of one tile: rounds of XS_THREADS keys in index order; the
+// rank of a key among the equal digits before it is its tile's offset for
+// the digit, plus the counts of the earlier warps of the round, plus its
+// rank among the lanes of its warp that share the digit
+__global__ void __launch_bounds__(XS_THREADS) k_export_scatter(const u64 *__restrict__ ka, const u64 *__restrict__ kb,
+                                                               const u64 *__restrict__ idx, long long n, int word,
+                                                               int shift, const int *__restrict__ hist, int ntiles,
+                                                               u64 *ka2, u64 *kb2, u64 *idx2)
+{
+    constexpr int NW = XS_THREADS / 32;
+    __shared__ int s_base[256];
+    __shared__ int s_w[NW][256];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    s_base[t] = hist[(size_t)t * ntiles + blockIdx.x];
+    const long long i0 = (long long)blockIdx.x * XS_TILE;
+    const unsigned below = (1u << lane) - 1u;
+    for (int r = 0; r < XS_ROUNDS; r++) {
+        const long long i = i0 + (long long)r * XS_THREADS + t;
+        const bool valid = i < n;
+        u64 a = 0, b = 0, x = 0;
+        int d = 256;  // invalid lanes share a value no key has
+        if (valid) {
+            a = ka[i];
+            b = kb[i];
+            x = idx[i];
+            d = (int)(((word ? a : b) >> shift) & 255u);
+        }
+        for (int q = t; q < NW * 256; q += XS_THREADS) (&s_w[0][0])[q] = 0;
+        __syncthreads();
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (valid && lane == __ffs(peers) - 1) s_w[warp][d] = __popc(peers);
+        __syncthreads();
+        {  // thread t: digit t, prefix over the warps of this round
+            int s = s_base[t];
+            for (int w = 0; w < NW; w++) {
+                const int c = s_w[w][t];
+                s_w[w][t] = s;
+                s += c;
+            }
+            s_base[t] = s;
+        }
+        __syncthreads();
+        if (valid) {
+            const int o = s_w[warp][d] + __popc(peers & below);
+            ka2[o] = a;
+            kb2[o] = b;
+            idx2[o] = x;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_export_gather(const u64 *__restrict__ idx, long long n, const double *__restrict__ c,
+                                const double *__restrict__ hd, const uint8_t *__restrict__ fl, double *oc, double *ohd,
+                                int32_t *ofl)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const u64 s = idx[i];
+        oc[i] = c[s];
+        ohd[i] = hd[s];
+        ofl[i] = fl[s];
+    }
+}
+
+// import: determinant i (compact input) goes to bucket-layout slot slot[i]
+__global__ void k_import_scatter(const u64 *__restrict__ a, const u64 *__restrict__ b, const double *__restrict__ c,
+                                 const u64 *__restrict__ slot, long long n, ulonglong2 *key, double *oc)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const u64 s = slot[i];
+        key[s] = make_ulonglong2(a[i], b[i]);
+        oc[s] = c[i];
+    }
+}
+
+cudaError_t launch_import_scatter(const u64 *a, const u64 *b, const double *c, const u64 *slot, long long n,
+                                  ulonglong2 *key, double *oc, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const long long g = (n + 255) / 256;
+    k_import_scatter<<<(unsigned)(g < 4096 ? g : 4096), 256, 0, s>>>(a, b, c, slot, n, key, oc);
+    return cudaGetLastError();
+}
+
+size_t export_scratch_bytes(long long n)
+{
+    const long long ntiles = (n + XS_TILE - 1) / XS_TILE;
+    return (size_t)n * (6 * sizeof(u64) + 2 * sizeof(double) + sizeof(int32_t)) + (size_t)ntiles * 256 * sizeof(int) +
+           8 * 256;
+}
+
+// the n occupied determinants of list `par` sorted by (alpha, beta) into
+// device arrays carved from `scratch` (export_scratch_bytes(n) bytes); the
+// sorted keys end in *oa / *ob, the gathered values in *oc, *ohd, *ofl
+cudaError_t export_sorted(const ulonglong2 *key, const double *c, const double *hd, const uint8_t *fl, const int *cnt,
+                          const long long *off, int nbk, long long n, int norb, void *scratch, const u64 **oa,
+                          const u64 **ob, const double **oc, const double **ohd, const int32_t **ofl, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    if (n > 0x7fffffffLL) return cudaErrorInvalidValue;  // 32-bit positions in the scatter
+    const long long ntiles = (n + XS_TILE - 1) / XS_TILE;
+    unsigned char *p = (unsigned char *)scratch;
+    u64 *ka[2], *kb[2], *ix[2];
+    for (int k = 0; k < 2; k++) {
+        ka[k] = (u64 *)p; p += (size_t)n * sizeof(u64);
+        kb[k] = (u64 *)p; p += (size_t)n * sizeof(u64);
+        ix[k] = (u64 *)p; p += (size_t)n * sizeof(u64);
+    }
+    double *dc = (double *)p; p += (size_t)n * sizeof(double);
+    double *dh = (double *)p; p += (size_t)n * sizeof(double);
+    int32_t *df = (int32_t *)p; p += (size_t)n * sizeof(int32_t);
+    p = (unsigned char *)(((uintptr_t)p + 255) & ~(uintptr_t)255);
+    int *hist = (int *)p;
+
+    k_export_compact<<<nbk < 4096 ? nbk : 4096, 256, 0, s>>>(key, cnt, off, nbk, ka[0], kb[0], ix[0]);
+    int cur = 0;
+    for (int word = 0; word < 2; word++)  // beta first: the less significant word
+        for (int shift = 0; shift < norb; shift += 8) {
+            k_export_hist<<<(unsigned)ntiles, XS_THREADS, 0, s>>>(ka[cur], kb[cur], n, word, shift, hist, (int)ntiles);
+            k_export_scan<<<1, XS_SCAN, 0, s>>>(hist, (int)(256 * ntiles));
+            k_export_scatter<<<(unsigned)ntiles, XS_THREADS, 0, s>>>(ka[cur], kb[cur], ix[cur], n, word, shift, hist,
+                                                                      (int)ntiles, ka[cur ^ 1], kb[cur ^ 1],
+                                                                      ix[cur ^ 1]);
+            cur ^= 1;
+        }
+    const int gb = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    k_export_gather<<<gb, 256, 0, s>>>(ix[cur], n, c, hd, fl, dc, dh, df);
+    *oa = ka[cur];
+    *ob = kb[cur];
+    *oc = dc;
+    *ohd = dh;
+    *ofl = df;
+    return cudaGetLastError();
+}
+
+}  // namespace fq

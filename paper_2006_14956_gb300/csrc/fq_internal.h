@@ -37,7 +37,7 @@ enum { DFLAG_REF = 1, DFLAG_D = 2 };
 constexpr int K1_THREADS = 256;
 constexpr unsigned HEAVY_ATT = 2048;  // attempts per heavy chunk
 constexpr int K3_THREADS = 256;
-constexpr int EMAX = 2048;            // main + spawned records staged per bucket in shared memory
+constexpr int EMAX = 1280;            // main + spawned records staged per bucket in shared memory (3 blocks per SM)
 constexpr int CAP_M = 1024;           // main-list capacity per bucket
 constexpr int CAP_S0 = EMAX - CAP_M;  // initial spawn capacity per bucket (grows at run time)
 constexpr int TABBITS = 12;           // shared-memory hash table of the annihilation (2 x EMAX slots)
@@ -236,6 +236,12 @@ long long connections_per_det(int na, int nb, int ma, int mb);
 void set_launch_geometry(int spawn_bps, int heavy_bps, int anni_bps);
 void get_launch_geometry(int *spawn_bps, int *heavy_bps, int *anni_bps);
 cudaError_t ref_abs_sum(const DevInst *dinst, double *dpartial, double *out, cudaStream_t s);
+size_t export_scratch_bytes(long long n);
+cudaError_t launch_import_scatter(const u64 *a, const u64 *b, const double *c, const u64 *slot, long long n,
+                                  ulonglong2 *key, double *oc, cudaStream_t s);
+cudaError_t export_sorted(const ulonglong2 *key, const double *c, const double *hd, const uint8_t *fl, const int *cnt,
+                          const long long *off, int nbk, long long n, int norb, void *scratch, const u64 **oa,
+                          const u64 **ob, const double **oc, const double **ohd, const int32_t **ofl, cudaStream_t s);
 
 // host helpers shared with capi.cu
 u64 det_hash_host(u64 a, u64 b);

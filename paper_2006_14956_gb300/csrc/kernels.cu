@@ -349,6 +349,7 @@ struct K1Smem {
     long long hdr_it;
     double hdr_S;
 };
+static_assert(3 * (sizeof(K1Smem) + 1024) <= 233472, "three spawn blocks per SM (228 KB, 1 KB reserved per block)");
 
 // draw and classify the attempts of a chunk (attempt a of parent `det`, slot
 // k), queue them by class, then evaluate them: warps take 32 queued attempts
@@ -375,12 +376,16 @@ __device__ void run_attempts(const DevInst &I, K1Smem &S, long long it, unsigned
 #pragma unroll
             for (int h = 0; h < 2; h++) {
                 const unsigned a = ab + h * K1_THREADS + t;
-                const unsigned ac = a < a1 ? a : a1 - 1;  // clamped: drawn, then discarded
-                u64 k;
-                det[h] = map.det_of(ac, k);
-                const ulonglong2 kk = map.key(det[h]);
-                philox(kk.x, kk.y, (u64)it, (k << 8) | (u64)PURPOSE_SPAWN, I.seed, I.replica, w[h]);
-                cls[h] = a < a1 ? classify(I, kk.x, kk.y, w[h][0], w[h][1]) : -1;
+                cls[h] = -1;
+                det[h] = 0;
+                if (ab + h * K1_THREADS + (unsigned)(t & ~31) < a1) {  // a warp with no attempt left draws nothing
+                    const unsigned ac = a < a1 ? a : a1 - 1;           // clamped: drawn, then discarded
+                    u64 k;
+                    det[h] = map.det_of(ac, k);
+                    const ulonglong2 kk = map.key(det[h]);
+                    philox(kk.x, kk.y, (u64)it, (k << 8) | (u64)PURPOSE_SPAWN, I.seed, I.replica, w[h]);
+                    cls[h] = a < a1 ? classify(I, kk.x, kk.y, w[h][0], w[h][1]) : -1;
+                }
             }
 #pragma unroll
             for (int h = 0; h < 2; h++) {
@@ -411,17 +416,19 @@ __device__ void run_attempts(const DevInst &I, K1Smem &S, long long it, unsigned
             const int q = g + lane;
             if (q < ns) {
                 const SpawnRec r = S.rec[CHUNK - 1 - q];
-                const ulonglong2 kk = map.key(r.det);
-                const SpawnCtx cx{map.slot(r.det), par, shift};
+                const unsigned d = r.det;
+                const ulonglong2 kk = map.key(d);
+                const SpawnCtx cx{map.slot(d), par, shift};
                 if (I.kind == FCIQMC_HUBBARD)
-                    spawn_hop(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3, cx);
-                else spawn_single(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3, cx);
+                    spawn_hop(I, kk.x, kk.y, map.cper(d), map.flags(d), r.w1, r.w2, r.w3, cx);
+                else spawn_single(I, kk.x, kk.y, map.cper(d), map.flags(d), r.w1, r.w2, r.w3, cx);
             } else if (q < ntot) {
                 const SpawnRec r = S.rec[q - ns];
-                const ulonglong2 kk = map.key(r.det);
-                const SpawnCtx cx{map.slot(r.det), par, shift};
-                if (I.pchb) spawn_double_pchb(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3, cx);
-                else spawn_double(I, kk.x, kk.y, map.cper(r.det), map.flags(r.det), r.w1, r.w2, r.w3, cx);
+                const unsigned d = r.det;
+                const ulonglong2 kk = map.key(d);
+                const SpawnCtx cx{map.slot(d), par, shift};
+                if (I.pchb) spawn_double_pchb(I, kk.x, kk.y, map.cper(d), map.flags(d), r.w1, r.w2, r.w3, cx);
+                else spawn_double(I, kk.x, kk.y, map.cper(d), map.flags(d), r.w1, r.w2, r.w3, cx);
             }
         }
         __syncthreads();
@@ -642,6 +649,7 @@ struct K3Smem {
     unsigned short tab[1 << TABBITS];
     unsigned short opos[EMAX];
 };
+static_assert(3 * (sizeof(K3Smem) + 1024) <= 233472, "three annihilation blocks per SM");
 
 __device__ __forceinline__ bool key_less(u64 a1, u64 b1, u64 a2, u64 b2) { return a1 < a2 || (a1 == a2 && b1 < b2); }
 
@@ -739,9 +747,9 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
         }
     }
     __syncthreads();
-    // 2. walkers (thread t holds walkers t + r K3_THREADS, r < 4, whose H_ii -
-    //    E_ref stay in registers for step 6): insert into the table (keys are
-    //    distinct); death (b) and Eq. (3), the rounding draws two at a time
+    // 2. walkers (thread t holds walkers t + r K3_THREADS, r < 4): insert into
+    //    the table (keys are distinct); death (b) and Eq. (3), the rounding
+    //    draws two at a time
     static_assert(CAP_M <= 4 * K3_THREADS, "walkers per thread");
     double hdr[4];
 #pragma unroll
@@ -954,7 +962,7 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
             nkey[dst] = k;
             nc[dst] = c;
             nfl[dst] = (uint8_t)(((f & EF_REF) ? DFLAG_REF : 0) | ((f & EF_D) ? DFLAG_D : 0));
-            if (e < m) nhd[dst] = r == 0 ? hdr[0] : r == 1 ? hdr[1] : r == 2 ? hdr[2] : hdr[3];
+            if (e < m) nhd[dst] = ohd[base + e];  // read again: an L2 hit, fewer live registers
             else {
                 const int qn = atomicAdd(&S.n_new, 1);
                 W.nacc[qn] = e;  // accumulators are free now: reuse as the list of new determinants
@@ -1061,7 +1069,7 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(K3_THREADS, 2) k_annihilate(const DevInst *__restrict__ insts,
+__global__ void __launch_bounds__(K3_THREADS, 3) k_annihilate(const DevInst *__restrict__ insts,
                                                               const int *__restrict__ unit_start, int n_inst, int n_units)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1146,15 +1154,30 @@ __global__ void __launch_bounds__(K3_THREADS) k_annihilate_big(const DevInst *__
 }
 
 // ------------------------------------------------------------------ finalize
+// one 16-byte chunk of a partial added into (x, y): chunks 0 and 1 are
+// 128-bit integers, 2 and 3 pairs of 64-bit counts, 4..7 pairs of binary64
+// sums (the second word of chunk 4 only when `both`)
+__device__ __forceinline__ void chunk_add(int c, bool both, u64 &x, u64 &y, u64 ox, u64 oy)
+{
+    if (c < 2) {
+        const u128 s = (((u128)y << 64) | x) + (((u128)oy << 64) | ox);
+        x = (u64)s;
+        y = (u64)(s >> 64);
+    } else if (c < 4) {
+        x += ox;
+        y += oy;
+    } else {
+        x = (u64)__double_as_longlong(__longlong_as_double((long long)x) + __longlong_as_double((long long)ox));
+        if (both) y = (u64)__double_as_longlong(__longlong_as_double((long long)y) + __longlong_as_double((long long)oy));
+    }
+}
+
 __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restrict__ insts, int n_inst)
 {
     const DevInst &I = insts[blockIdx.x];
     IterState *st = I.st;
     __shared__ int s_err;
-    __shared__ double s_d[K5_THREADS / 32];
-    __shared__ double s_t[K5_THREADS / 32][2];
-    __shared__ double s_x[K5_THREADS / 32][4];
-    __shared__ u64 s_u[K5_THREADS / 32][8];
+    __shared__ ulonglong2 s_w[K5_THREADS / 32][8];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (t == 0) {
         int e = *(volatile int *)&st->err;
@@ -1173,91 +1196,59 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
     if (s_err) return;
     const int nbk = 1 << I.bb;
     const bool pair = I.partner > (int)blockIdx.x;  // the first replica reports the cross estimators
-    double xo = 0.0, xh = 0.0, xc = 0.0, xp = 0.0;
-    u128 nw = 0;
-    i128 ann = 0;
-    long long ndet = 0, rej = 0, sp = 0, att = 0;
-    double en = 0.0, tn = 0.0, td = 0.0;
     const bool trial = I.trial_bits != 0;
-    for (int u = t; u < nbk; u += K5_THREADS) {
-        const Partial &P = I.part[u];
-        if (trial) {
-            tn = tn + P.t_num;
-            td = td + P.t_den;
+    // The partials as 16-byte chunks: chunk q holds words 2 (q % 8) and
+    // 2 (q % 8) + 1 of partial q / 8, so thread t always reads chunk t % 8 and
+    // each load instruction of a warp covers four whole partials.  Chunk 0:
+    // N_w, 1: annihilated (128-bit integers); 2, 3: counts; 4: E_num and the
+    // trial numerator; 5..7: trial denominator and replica-pair sums (binary64,
+    // added only when the run has them: binary64 adds are slow on this part).
+    static_assert(sizeof(Partial) == 128 && K5_THREADS % 256 == 0, "eight 16-byte chunks per partial");
+    const int c = t & 7;
+    const bool need = c <= 4 || trial || pair, both = c != 4 || trial;
+    u64 x = 0, y = 0;
+    if (need) {
+        const ulonglong2 *pc = reinterpret_cast<const ulonglong2 *>(I.part);
+        for (int q = t; q < nbk * 8; q += K5_THREADS) {
+            const ulonglong2 v = pc[q];
+            chunk_add(c, both, x, y, v.x, v.y);
         }
-        if (pair) {
-            xo = xo + P.x_ov;
-            xh = xh + P.x_hd;
-            xc = xc + P.x_cr;
-            xp = xp + P.x_pt2;
-        }
-        nw += ((u128)P.nw_hi << 64) | P.nw_lo;
-        ann += (i128)(((u128)P.ann_hi << 64) | P.ann_lo);
-        ndet += P.ndet; rej += P.rejected; sp += P.spawns; att += P.attempts;
-        en = en + P.e_num;
     }
-    if (trial)
-        for (int mm = 16; mm >= 1; mm >>= 1) {
-            tn = tn + __shfl_xor_sync(0xffffffffu, tn, mm);
-            td = td + __shfl_xor_sync(0xffffffffu, td, mm);
-        }
-    if (pair)
-        for (int mm = 16; mm >= 1; mm >>= 1) {
-            xo = xo + __shfl_xor_sync(0xffffffffu, xo, mm);
-            xh = xh + __shfl_xor_sync(0xffffffffu, xh, mm);
-            xc = xc + __shfl_xor_sync(0xffffffffu, xc, mm);
-            xp = xp + __shfl_xor_sync(0xffffffffu, xp, mm);
-        }
-    for (int mm = 16; mm >= 1; mm >>= 1) {
-        en = en + __shfl_xor_sync(0xffffffffu, en, mm);
-        ndet += __shfl_xor_sync(0xffffffffu, ndet, mm);
-        rej += __shfl_xor_sync(0xffffffffu, rej, mm);
-        sp += __shfl_xor_sync(0xffffffffu, sp, mm);
-        att += __shfl_xor_sync(0xffffffffu, att, mm);
-        ann += shfl_xor_i128(ann, mm);
-        nw += (u128)shfl_xor_i128((i128)nw, mm);
+    for (int mm = 8; mm <= 16; mm <<= 1) {  // lanes l, l ^ 8, l ^ 16, l ^ 24 hold the same chunk
+        const u64 ox = __shfl_xor_sync(0xffffffffu, x, mm), oy = __shfl_xor_sync(0xffffffffu, y, mm);
+        if (need) chunk_add(c, both, x, y, ox, oy);
     }
-    if (lane == 0) {
-        s_d[warp] = en;
-        s_t[warp][0] = tn;
-        s_t[warp][1] = td;
-        s_x[warp][0] = xo; s_x[warp][1] = xh; s_x[warp][2] = xc; s_x[warp][3] = xp;
-        s_u[warp][0] = (u64)nw; s_u[warp][1] = (u64)(nw >> 64);
-        s_u[warp][2] = (u64)ann; s_u[warp][3] = (u64)((u128)ann >> 64);
-        s_u[warp][4] = (u64)ndet; s_u[warp][5] = (u64)rej; s_u[warp][6] = (u64)sp; s_u[warp][7] = (u64)att;
-    }
+    if (lane < 8) s_w[warp][lane] = make_ulonglong2(x, y);
     __syncthreads();
-    // the warps' partial sums, reduced by warp 0 in the same xor tree
-    static_assert(K5_THREADS / 32 == 32, "one partial per lane");
+    // warp 0: lane l sums chunk l % 8 over warps 8 (l / 8) .. 8 (l / 8) + 7, then
+    // the four lanes of each chunk in the same xor tree
+    static_assert(K5_THREADS / 32 == 32, "four groups of eight warps");
     if (warp != 0) return;
-    double e_num = s_d[lane], t_num = 0.0, t_den = 0.0, x_ov = 0.0, x_hd = 0.0, x_cr = 0.0, x_pt = 0.0;
-    u128 W = ((u128)s_u[lane][1] << 64) | s_u[lane][0];
-    i128 A = (i128)(((u128)s_u[lane][3] << 64) | s_u[lane][2]);
-    long long nd = (long long)s_u[lane][4], rj = (long long)s_u[lane][5], sps = (long long)s_u[lane][6],
-              at = (long long)s_u[lane][7];
-    if (trial) { t_num = s_t[lane][0]; t_den = s_t[lane][1]; }
-    if (pair) { x_ov = s_x[lane][0]; x_hd = s_x[lane][1]; x_cr = s_x[lane][2]; x_pt = s_x[lane][3]; }
-    for (int mm = 16; mm >= 1; mm >>= 1) {
-        e_num = e_num + __shfl_xor_sync(0xffffffffu, e_num, mm);
-        W += (u128)shfl_xor_i128((i128)W, mm);
-        A += shfl_xor_i128(A, mm);
-        nd += __shfl_xor_sync(0xffffffffu, nd, mm);
-        rj += __shfl_xor_sync(0xffffffffu, rj, mm);
-        sps += __shfl_xor_sync(0xffffffffu, sps, mm);
-        at += __shfl_xor_sync(0xffffffffu, at, mm);
+    x = 0;
+    y = 0;
+    if (need)
+        for (int w = 8 * (lane >> 3); w < 8 * (lane >> 3) + 8; w++) chunk_add(c, both, x, y, s_w[w][c].x, s_w[w][c].y);
+    for (int mm = 8; mm <= 16; mm <<= 1) {
+        const u64 ox = __shfl_xor_sync(0xffffffffu, x, mm), oy = __shfl_xor_sync(0xffffffffu, y, mm);
+        if (need) chunk_add(c, both, x, y, ox, oy);
     }
-    if (trial)
-        for (int mm = 16; mm >= 1; mm >>= 1) {
-            t_num = t_num + __shfl_xor_sync(0xffffffffu, t_num, mm);
-            t_den = t_den + __shfl_xor_sync(0xffffffffu, t_den, mm);
-        }
-    if (pair)
-        for (int mm = 16; mm >= 1; mm >>= 1) {
-            x_ov = x_ov + __shfl_xor_sync(0xffffffffu, x_ov, mm);
-            x_hd = x_hd + __shfl_xor_sync(0xffffffffu, x_hd, mm);
-            x_cr = x_cr + __shfl_xor_sync(0xffffffffu, x_cr, mm);
-            x_pt = x_pt + __shfl_xor_sync(0xffffffffu, x_pt, mm);
-        }
+    u64 tot[8][2];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        tot[k][0] = __shfl_sync(0xffffffffu, x, k);
+        tot[k][1] = __shfl_sync(0xffffffffu, y, k);
+    }
+    const u128 W = ((u128)tot[0][1] << 64) | tot[0][0];
+    const i128 A = (i128)(((u128)tot[1][1] << 64) | tot[1][0]);
+    const long long nd = (long long)tot[2][0], rj = (long long)tot[2][1], sps = (long long)tot[3][0],
+                    at = (long long)tot[3][1];
+    const double e_num = __longlong_as_double((long long)tot[4][0]);
+    const double t_num = trial ? __longlong_as_double((long long)tot[4][1]) : 0.0;
+    const double t_den = trial ? __longlong_as_double((long long)tot[5][0]) : 0.0;
+    const double x_ov = pair ? __longlong_as_double((long long)tot[5][1]) : 0.0;
+    const double x_hd = pair ? __longlong_as_double((long long)tot[6][0]) : 0.0;
+    const double x_cr = pair ? __longlong_as_double((long long)tot[6][1]) : 0.0;
+    const double x_pt = pair ? __longlong_as_double((long long)tot[7][0]) : 0.0;
     if (lane != 0) return;
     const double nwd = u128_to_double(W) * 0x1p-32;
     const long long it = st->iter;
@@ -1448,7 +1439,7 @@ void launch_build_kidx(const DevInst *dinst, int parity, int nb, cudaStream_t s)
 }
 
 // launch geometry, chosen by fciqmc_autotune (blocks per SM)
-static int g_spawn_bps = 8, g_heavy_bps = 2, g_anni_bps = 2;
+static int g_spawn_bps = 8, g_heavy_bps = 2, g_anni_bps = 3;
 void set_launch_geometry(int spawn_bps, int heavy_bps, int anni_bps)
 {
     g_spawn_bps = spawn_bps;

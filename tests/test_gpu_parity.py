@@ -150,6 +150,33 @@ def test_capacity_growth_is_bit_identical():
     assert_stats_equal(fq.fciqmc_iter_stats_get(g), o.stats())
 
 
+@pytest.mark.parametrize("name,sysd,params", [
+    ("hubbard_1d_8", workloads.hubbard_1d(8, 1.0, 4.0),
+     dict(tau=0.01, target_walkers=2000, seed=11, max_dets=40000, initiator_threshold=3.0)),
+    ("abinitio_24_orbitals", workloads.config_abinitio_24()[0],
+     dict(workloads.config_abinitio_24()[1], tau=2e-4, target_walkers=2e4, max_dets=5000000)),
+])
+def test_export_device_sort_and_host_fallback_agree(name, sysd, params):
+    """The export sorts on the device (compaction, radix sort over the
+    orbital bits, gather); a run whose memory cap leaves no room for that
+    scratch sorts on the host.  Both orders must be the oracle's."""
+    fq = _fq()
+    params = dict(DAMP, **params)
+    g = fq.fciqmc_create(sysd, params)
+    b0 = fq.fciqmc_layout(g)
+    fq.fciqmc_step(g, 150)
+    b1 = fq.fciqmc_layout(g)
+    assert (b0["buckets"], b0["cap_spawn"]) == (b1["buckets"], b1["cap_spawn"])  # no growth: the capped twin fits
+    tight = fq.fciqmc_create(sysd, dict(params, max_device_bytes=b1["device_bytes"] + 4096))
+    fq.fciqmc_step(tight, 150)
+    o = oracle.Run(oracle.system_from_workload(sysd), **{k: v for k, v in params.items() if k != "max_dets"})
+    o.step(150)
+    dev, host = fq.fciqmc_export_state(g), fq.fciqmc_export_state(tight)
+    assert dev["alpha"].size > 100
+    assert_states_equal(dev, o.export())
+    assert_states_equal(host, o.export())
+
+
 def test_checkpoint_restart_continues_identically():
     fq = _fq()
     sysd, params = workloads.small_abinitio(8, 3, 3, seed=5), dict(DAMP, tau=0.005, target_walkers=3000,

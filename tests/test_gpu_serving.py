@@ -60,6 +60,29 @@ def test_admission_respects_the_memory_budget():
     assert all(fq.fciqmc_server_poll(srv, i)["state_name"] == "max_iters" for i in ids)
 
 
+def test_request_that_cannot_grow_is_retired():
+    """A request whose spawn regions must grow past its own device-memory cap
+    fails with OUT_OF_MEMORY; the server retires it as failed and the tick
+    loop ends, while the other request in the batch still finishes."""
+    fq = _fq()
+    mix = _mix()
+    s, p = mix[0]
+    p = dict(p, initial_walkers=2e4, target_walkers=1e5)
+    alone = fq.fciqmc_create(s, p)
+    cap = fq.fciqmc_layout(alone)["device_bytes"] + (64 << 10)  # no room for larger spawn buffers
+    del alone
+    srv = fq.fciqmc_server_create(8 << 30, max_active=4)
+    bad = fq.fciqmc_server_submit(srv, s, dict(p, max_device_bytes=cap), target_sigma=1e-12, max_iters=100)
+    good = fq.fciqmc_server_submit(srv, *mix[1], target_sigma=1e-12, max_iters=100)
+    for _ in range(50):  # a handful of ticks; never unbounded
+        if fq.fciqmc_server_tick(srv, 20) == 0:
+            break
+    st = fq.fciqmc_server_poll(srv, bad)
+    assert st["state_name"] == "failed" and st["error"] == fq.FCIQMC_ERR_OUT_OF_MEMORY, st
+    assert fq.fciqmc_server_poll(srv, good)["state_name"] == "max_iters"
+    assert fq.fciqmc_server_tick(srv, 20) == 0
+
+
 def test_auto_time_step_bounds_spawning():
     fq = _fq()
     s, p = _mix()[2]
