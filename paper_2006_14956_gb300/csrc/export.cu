@@ -14,7 +14,6 @@ namespace fq {
 constexpr int XS_THREADS = 256;  // one thread per digit value in the scatter
 constexpr int XS_ROUNDS = 8;
 constexpr int XS_TILE = XS_THREADS * XS_ROUNDS;
-constexpr int XS_SCAN = 1024;
 
 // occupied slots of bucket b go to [off[b], off[b] + cnt[b])
 __global__ void k_export_compact(const ulonglong2 *__restrict__ key, const int *__restrict__ cnt,
@@ -55,30 +54,34 @@ __global__ void __launch_bounds__(XS_THREADS) k_export_hist(const u64 *__restric
     hist[(size_t)t * ntiles + blockIdx.x] = s_h[t];
 }
 
-// exclusive scan of hist[0 .. m) in place (one block): each thread takes a
-// contiguous segment, the segment sums are scanned in shared memory
-__global__ void __launch_bounds__(XS_SCAN) k_export_scan(int *hist, int m)
+// exclusive scan of each digit's row of tile counts, hist[d * ntiles ..
+// (d + 1) * ntiles), in place (block d), and the row total in dtot[d]
+__global__ void __launch_bounds__(XS_THREADS) k_export_scan(int *hist, int ntiles, int *dtot)
 {
-    __shared__ long long s[XS_SCAN];
-    const int t = threadIdx.x;
-    const int per = (m + XS_SCAN - 1) / XS_SCAN;
-    const int a = min(m, t * per), b = min(m, a + per);
-    long long sum = 0;
-    for (int q = a; q < b; q++) sum += hist[q];
-    s[t] = sum;
+    __shared__ int s_w[XS_THREADS / 32];
+    __shared__ int s_carry;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    int *row = hist + (size_t)blockIdx.x * ntiles;
+    if (t == 0) s_carry = 0;
     __syncthreads();
-    for (int o = 1; o < XS_SCAN; o <<= 1) {
-        const long long v = t >= o ? s[t - o] : 0;
+    for (int q0 = 0; q0 < ntiles; q0 += XS_THREADS) {
+        const int q = q0 + t;
+        const int v = q < ntiles ? row[q] : 0;
+        int incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_w[warp] = incl;
         __syncthreads();
-        s[t] += v;
+        int before = s_carry;
+        for (int w = 0; w < warp; w++) before += s_w[w];
+        if (q < ntiles) row[q] = before + incl - v;
+        __syncthreads();
+        if (t == XS_THREADS - 1) s_carry = before + incl;
         __syncthreads();
     }
-    long long run = s[t] - sum;
-    for (int q = a; q < b; q++) {
-        const int c = hist[q];
-        hist[q] = (int)run;
-        run += c;
-    }
+    if (t == 0) dtot[blockIdx.x] = s_carry;
 }
 
 // stable scatter of one tile: rounds of XS_THREADS keys in index order; the
@@ -88,13 +91,27 @@ __global__ void __launch_bounds__(XS_SCAN) k_export_scan(int *hist, int m)
 __global__ void __launch_bounds__(XS_THREADS) k_export_scatter(const u64 *__restrict__ ka, const u64 *__restrict__ kb,
                                                                const u64 *__restrict__ idx, long long n, int word,
                                                                int shift, const int *__restrict__ hist, int ntiles,
-                                                               u64 *ka2, u64 *kb2, u64 *idx2)
+                                                               const int *__restrict__ dtot, u64 *ka2, u64 *kb2,
+                                                               u64 *idx2)
 {
     constexpr int NW = XS_THREADS / 32;
     __shared__ int s_base[256];
     __shared__ int s_w[NW][256];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    s_base[t] = hist[(size_t)t * ntiles + blockIdx.x];
+    {  // keys with a smaller digit (exclusive scan of the digit totals), then this tile's row prefix
+        const int v = dtot[t];
+        int incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_w[0][warp] = incl;
+        __syncthreads();
+        int before = 0;
+        for (int w = 0; w < warp; w++) before += s_w[0][w];
+        s_base[t] = before + incl - v + hist[(size_t)t * ntiles + blockIdx.x];
+        __syncthreads();
+    }
     const long long i0 = (long long)blockIdx.x * XS_TILE;
     const unsigned below = (1u << lane) - 1u;
     for (int r = 0; r < XS_ROUNDS; r++) {
@@ -169,7 +186,7 @@ size_t export_scratch_bytes(long long n)
 {
     const long long ntiles = (n + XS_TILE - 1) / XS_TILE;
     return (size_t)n * (6 * sizeof(u64) + 2 * sizeof(double) + sizeof(int32_t)) + (size_t)ntiles * 256 * sizeof(int) +
-           8 * 256;
+           256 * sizeof(int) + 8 * 256;
 }
 
 // the n occupied determinants of list `par` sorted by (alpha, beta) into
@@ -193,6 +210,8 @@ cudaError_t export_sorted(const ulonglong2 *key, const double *c, const double *
     double *dh = (double *)p; p += (size_t)n * sizeof(double);
     int32_t *df = (int32_t *)p; p += (size_t)n * sizeof(int32_t);
     p = (unsigned char *)(((uintptr_t)p + 255) & ~(uintptr_t)255);
+    int *dtot = (int *)p;
+    p += 256 * sizeof(int);
     int *hist = (int *)p;
 
     k_export_compact<<<nbk < 4096 ? nbk : 4096, 256, 0, s>>>(key, cnt, off, nbk, ka[0], kb[0], ix[0]);
@@ -200,9 +219,9 @@ cudaError_t export_sorted(const ulonglong2 *key, const double *c, const double *
     for (int word = 0; word < 2; word++)  // beta first: the less significant word
         for (int shift = 0; shift < norb; shift += 8) {
             k_export_hist<<<(unsigned)ntiles, XS_THREADS, 0, s>>>(ka[cur], kb[cur], n, word, shift, hist, (int)ntiles);
-            k_export_scan<<<1, XS_SCAN, 0, s>>>(hist, (int)(256 * ntiles));
+            k_export_scan<<<256, XS_THREADS, 0, s>>>(hist, (int)ntiles, dtot);
             k_export_scatter<<<(unsigned)ntiles, XS_THREADS, 0, s>>>(ka[cur], kb[cur], ix[cur], n, word, shift, hist,
-                                                                      (int)ntiles, ka[cur ^ 1], kb[cur ^ 1],
+                                                                      (int)ntiles, dtot, ka[cur ^ 1], kb[cur ^ 1],
                                                                       ix[cur ^ 1]);
             cur ^= 1;
         }

@@ -1154,10 +1154,9 @@ __global__ void __launch_bounds__(K3_THREADS) k_annihilate_big(const DevInst *__
 }
 
 // ------------------------------------------------------------------ finalize
-// one 16-byte chunk of a partial added into (x, y): chunks 0 and 1 are
-// 128-bit integers, 2 and 3 pairs of 64-bit counts, 4..7 pairs of binary64
-// sums (the second word of chunk 4 only when `both`)
-__device__ __forceinline__ void chunk_add(int c, bool both, u64 &x, u64 &y, u64 ox, u64 oy)
+// one 16-byte integer chunk of a partial added into (x, y): chunks 0 and 1
+// are 128-bit integers, 2 and 3 pairs of 64-bit counts; others are left alone
+__device__ __forceinline__ void int_chunk_add(int c, u64 &x, u64 &y, u64 ox, u64 oy)
 {
     if (c < 2) {
         const u128 s = (((u128)y << 64) | x) + (((u128)oy << 64) | ox);
@@ -1166,9 +1165,6 @@ __device__ __forceinline__ void chunk_add(int c, bool both, u64 &x, u64 &y, u64 
     } else if (c < 4) {
         x += ox;
         y += oy;
-    } else {
-        x = (u64)__double_as_longlong(__longlong_as_double((long long)x) + __longlong_as_double((long long)ox));
-        if (both) y = (u64)__double_as_longlong(__longlong_as_double((long long)y) + __longlong_as_double((long long)oy));
     }
 }
 
@@ -1177,7 +1173,8 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
     const DevInst &I = insts[blockIdx.x];
     IterState *st = I.st;
     __shared__ int s_err;
-    __shared__ ulonglong2 s_w[K5_THREADS / 32][8];
+    __shared__ ulonglong2 s_w[K5_THREADS / 32][4];
+    __shared__ double s_r[K5_THREADS];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (t == 0) {
         int e = *(volatile int *)&st->err;
@@ -1197,44 +1194,77 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
     const int nbk = 1 << I.bb;
     const bool pair = I.partner > (int)blockIdx.x;  // the first replica reports the cross estimators
     const bool trial = I.trial_bits != 0;
-    // The partials as 16-byte chunks: chunk q holds words 2 (q % 8) and
-    // 2 (q % 8) + 1 of partial q / 8, so thread t always reads chunk t % 8 and
-    // each load instruction of a warp covers four whole partials.  Chunk 0:
-    // N_w, 1: annihilated (128-bit integers); 2, 3: counts; 4: E_num and the
-    // trial numerator; 5..7: trial denominator and replica-pair sums (binary64,
-    // added only when the run has them: binary64 adds are slow on this part).
+    // Integer sums: the partials as 16-byte chunks (chunk q holds words
+    // 2 (q % 8) and 2 (q % 8) + 1 of partial q / 8); thread t always takes
+    // chunk t % 8, so each warp load covers four whole partials, and eight
+    // loads are in flight per thread.  Chunk 0: N_w, 1: annihilated (128-bit
+    // integers); 2, 3: counts.
     static_assert(sizeof(Partial) == 128 && K5_THREADS % 256 == 0, "eight 16-byte chunks per partial");
     const int c = t & 7;
-    const bool need = c <= 4 || trial || pair, both = c != 4 || trial;
     u64 x = 0, y = 0;
-    if (need) {
+    if (c < 4) {
         const ulonglong2 *pc = reinterpret_cast<const ulonglong2 *>(I.part);
-        for (int q = t; q < nbk * 8; q += K5_THREADS) {
-            const ulonglong2 v = pc[q];
-            chunk_add(c, both, x, y, v.x, v.y);
+        const int nq = nbk * 8;
+        for (int q0 = t; q0 < nq; q0 += 8 * K5_THREADS) {
+            ulonglong2 v[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int q = q0 + k * K5_THREADS;
+                v[k] = q < nq ? pc[q] : make_ulonglong2(0, 0);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; k++) int_chunk_add(c, x, y, v[k].x, v[k].y);
         }
     }
     for (int mm = 8; mm <= 16; mm <<= 1) {  // lanes l, l ^ 8, l ^ 16, l ^ 24 hold the same chunk
         const u64 ox = __shfl_xor_sync(0xffffffffu, x, mm), oy = __shfl_xor_sync(0xffffffffu, y, mm);
-        if (need) chunk_add(c, both, x, y, ox, oy);
+        int_chunk_add(c, x, y, ox, oy);
     }
-    if (lane < 8) s_w[warp][lane] = make_ulonglong2(x, y);
+    if (lane < 4) s_w[warp][lane] = make_ulonglong2(x, y);
+    // Binary64 sums (E_num; trial numerator and denominator; replica-pair
+    // terms), per tile of K5_THREADS buckets: one value per thread into shared
+    // memory and a halving tree, so that every binary64 add is a full-warp
+    // instruction (a partly active warp costs as much on this part's slow
+    // binary64 pipe); tile sums are added in tile order by thread 0.
+    constexpr int NF = 7;  // words 8 .. 14 of a partial
+    double dsum[NF];
+#pragma unroll
+    for (int f = 0; f < NF; f++) dsum[f] = 0.0;
+    for (int tile0 = 0; tile0 < nbk; tile0 += K5_THREADS) {
+#pragma unroll
+        for (int f = 0; f < NF; f++) {
+            if ((f == 1 || f == 2) ? !trial : (f >= 3 && !pair)) continue;
+            const int u = tile0 + t;
+            s_r[t] = u < nbk ? __longlong_as_double(reinterpret_cast<const long long *>(I.part + u)[8 + f]) : 0.0;
+            __syncthreads();
+            for (int h = K5_THREADS / 2; h >= 32; h >>= 1) {
+                if (t < h) s_r[t] = s_r[t] + s_r[t + h];
+                __syncthreads();
+            }
+            if (warp == 0) {
+                double v = s_r[lane];
+                for (int mm = 16; mm >= 1; mm >>= 1) v = v + __shfl_xor_sync(0xffffffffu, v, mm);
+                if (lane == 0) dsum[f] = dsum[f] + v;
+            }
+            __syncthreads();
+        }
+    }
     __syncthreads();
-    // warp 0: lane l sums chunk l % 8 over warps 8 (l / 8) .. 8 (l / 8) + 7, then
-    // the four lanes of each chunk in the same xor tree
-    static_assert(K5_THREADS / 32 == 32, "four groups of eight warps");
+    // warp 0: lane l sums integer chunk l % 4 over warps 4 (l / 4) .. 4 (l / 4) + 3,
+    // then the eight lanes of each chunk in an xor tree
+    static_assert(K5_THREADS / 32 == 32, "eight groups of four warps");
     if (warp != 0) return;
     x = 0;
     y = 0;
-    if (need)
-        for (int w = 8 * (lane >> 3); w < 8 * (lane >> 3) + 8; w++) chunk_add(c, both, x, y, s_w[w][c].x, s_w[w][c].y);
-    for (int mm = 8; mm <= 16; mm <<= 1) {
+    const int ci = lane & 3, g = lane >> 2;  // chunk, group of four warps
+    for (int w = 4 * g; w < 4 * g + 4; w++) int_chunk_add(ci, x, y, s_w[w][ci].x, s_w[w][ci].y);
+    for (int mm = 4; mm <= 16; mm <<= 1) {
         const u64 ox = __shfl_xor_sync(0xffffffffu, x, mm), oy = __shfl_xor_sync(0xffffffffu, y, mm);
-        if (need) chunk_add(c, both, x, y, ox, oy);
+        int_chunk_add(ci, x, y, ox, oy);
     }
-    u64 tot[8][2];
+    u64 tot[4][2];
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
+    for (int k = 0; k < 4; k++) {
         tot[k][0] = __shfl_sync(0xffffffffu, x, k);
         tot[k][1] = __shfl_sync(0xffffffffu, y, k);
     }
@@ -1242,13 +1272,10 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
     const i128 A = (i128)(((u128)tot[1][1] << 64) | tot[1][0]);
     const long long nd = (long long)tot[2][0], rj = (long long)tot[2][1], sps = (long long)tot[3][0],
                     at = (long long)tot[3][1];
-    const double e_num = __longlong_as_double((long long)tot[4][0]);
-    const double t_num = trial ? __longlong_as_double((long long)tot[4][1]) : 0.0;
-    const double t_den = trial ? __longlong_as_double((long long)tot[5][0]) : 0.0;
-    const double x_ov = pair ? __longlong_as_double((long long)tot[5][1]) : 0.0;
-    const double x_hd = pair ? __longlong_as_double((long long)tot[6][0]) : 0.0;
-    const double x_cr = pair ? __longlong_as_double((long long)tot[6][1]) : 0.0;
-    const double x_pt = pair ? __longlong_as_double((long long)tot[7][0]) : 0.0;
+    const double e_num = dsum[0];
+    const double t_num = trial ? dsum[1] : 0.0, t_den = trial ? dsum[2] : 0.0;
+    const double x_ov = pair ? dsum[3] : 0.0, x_hd = pair ? dsum[4] : 0.0, x_cr = pair ? dsum[5] : 0.0;
+    const double x_pt = pair ? dsum[6] : 0.0;
     if (lane != 0) return;
     const double nwd = u128_to_double(W) * 0x1p-32;
     const long long it = st->iter;
