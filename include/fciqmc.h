@@ -411,10 +411,11 @@ double fciqmc_server_clock(fciqmc_server *srv);
 void fciqmc_server_destroy(fciqmc_server *srv);
 
 /* Autotuner of the launch geometry: times n_iter iterations of the batch
- * hs[0..k-1] (advancing it) for each candidate number of blocks per SM of the
- * spawning, heavy-spawning and annihilation kernels, keeps the fastest for
- * every later launch in the process, and writes it to out[3] (spawn, heavy,
- * annihilation).  Results of the runs do not depend on the geometry. */
+ * hs[0..k-1] (advancing it) for each candidate grid size, in blocks per SM, of
+ * the spawning (2, 4, 8, 16), heavy-spawning (1, 2, 4) and annihilation
+ * (3, 9, 24) kernels, keeps the fastest for every later launch in the
+ * process, and writes it to out[3] (spawn, heavy, annihilation).  Defaults:
+ * 8, 2, 9.  Results of the runs do not depend on the geometry. */
 int fciqmc_autotune(fciqmc_handle **hs, int32_t k, int64_t n_iter, int32_t out[3]);
 
 /* Device timing of the kernels of the last fciqmc_step call (milliseconds per

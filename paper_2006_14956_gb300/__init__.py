@@ -313,11 +313,13 @@ def fciqmc_export_state(handle):
     n = C.c_int64()
     _lib.fciqmc_export_state(handle.h, 0, None, None, None, None, None, C.byref(n))
     m = max(n.value, 1)
-    a = np.zeros(m, np.uint64)
-    b = np.zeros(m, np.uint64)
-    c = np.zeros(m, np.float64)
-    hd = np.zeros(m, np.float64)
-    fl = np.zeros(m, np.int32)
+    # output pages are touched here: a first touch inside the driver's
+    # pageable device-to-host copy costs ten times the copy itself
+    a, b = np.empty(m, np.uint64), np.empty(m, np.uint64)
+    c, hd = np.empty(m, np.float64), np.empty(m, np.float64)
+    fl = np.empty(m, np.int32)
+    for x in (a, b, c, hd, fl):
+        x.fill(0)
     _check(_lib.fciqmc_export_state(handle.h, m, a.ctypes.data_as(_u64p), b.ctypes.data_as(_u64p),
                                     c.ctypes.data_as(_dp), hd.ctypes.data_as(_dp),
                                     fl.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(n)), handle.h)

@@ -274,6 +274,8 @@ static int upload_inst(fciqmc_handle *h)
 static int enqueue_iteration(fciqmc_handle *h, cudaEvent_t *ev)
 {
     const int units = 1 << h->bb;
+    set_pdl(ev == nullptr);  // kernels timed one by one are launched plainly
+    struct PdlOff { ~PdlOff() { set_pdl(false); } } pdl_off;
     if (ev) cudaEventRecord(ev[0], h->stream);
     launch_spawn(h->dinst, h->dunit, 1, units, h->stream);
     if (ev) cudaEventRecord(ev[1], h->stream);
@@ -1354,23 +1356,26 @@ int fciqmc_import_state(fciqmc_handle *h, int64_t n, const uint64_t *alpha, cons
 {
     if (!h || n < 0 || (n > 0 && (!alpha || !beta || !c)) || iteration < 0) return FCIQMC_ERR_INVALID_ARG;
     const u64 normask = h->norb >= 64 ? ~0ULL : ((1ULL << h->norb) - 1);
+    // one pass: checks, the reference's presence, the bucket hash of every key
+    // (the reference, when absent, is appended as entry n with C = 0)
+    std::vector<u64> hash((size_t)n + 1);
     bool has_ref = false;
     for (int64_t i = 0; i < n; i++) {
-        if (__builtin_popcountll(alpha[i]) != h->na || __builtin_popcountll(beta[i]) != h->nb ||
-            ((alpha[i] | beta[i]) & ~normask) || !std::isfinite(c[i]))
+        const u64 a = alpha[i], b = beta[i];
+        if (__builtin_popcountll(a) != h->na || __builtin_popcountll(b) != h->nb || ((a | b) & ~normask) ||
+            !std::isfinite(c[i]))
             return fail(h, FCIQMC_ERR_INVALID_ARG, "imported determinant with wrong electron count or bad amplitude");
-        if (alpha[i] == h->ref_a && beta[i] == h->ref_b) has_ref = true;
+        has_ref |= a == h->ref_a && b == h->ref_b;
+        hash[i] = det_hash_host(a, b);
     }
-    // the reference, when absent, is appended as entry n with C = 0
     const int64_t nt = n + (has_ref ? 0 : 1);
+    if (!has_ref) hash[n] = det_hash_host(h->ref_a, h->ref_b);
     auto key_a = [&](int64_t i) { return i < n ? (u64)alpha[i] : h->ref_a; };
     auto key_b = [&](int64_t i) { return i < n ? (u64)beta[i] : h->ref_b; };
     int rc = read_state(h);
     if (rc) return rc;
     // the fewest buckets (at least the current number) that hold every
     // bucket's determinants within half the main capacity; one allocation
-    std::vector<u64> hash((size_t)nt);
-    for (int64_t i = 0; i < nt; i++) hash[i] = det_hash_host(key_a(i), key_b(i));
     int bb = h->bb;
     for (;; bb++) {
         std::vector<int> cnt_b((size_t)1 << bb, 0);
@@ -1545,6 +1550,8 @@ int fciqmc_step_batch(fciqmc_handle **hs, int32_t k, int64_t n_iter)
         cleanup();
         cudaGraph_t g;
         CUDA_TRY(h0, cudaStreamBeginCapture(h0->stream, cudaStreamCaptureModeThreadLocal));
+        set_pdl(true);
+        struct PdlOff { ~PdlOff() { set_pdl(false); } } pdl_off;
         launch_spawn(dinst, dunit, k, units, h0->stream);
         launch_spawn_heavy(dinst, k, h0->stream);
         if (max_nd > 0) launch_semistoch(dinst, k, max_nd, h0->stream);
@@ -2164,8 +2171,8 @@ extern "C" void fciqmc_free_system(fciqmc_system *sys)
 extern "C" int fciqmc_autotune(fciqmc_handle **hs, int32_t k, int64_t n_iter, int32_t out[3])
 {
     if (!hs || k < 1 || n_iter < 1 || !out) return FCIQMC_ERR_INVALID_ARG;
-    const int spawn_c[] = {2, 4, 8, 16}, anni_c[] = {1, 2, 3}, heavy_c[] = {1, 2, 4};
-    int best_s = 8, best_h = 2, best_a = 3;
+    const int spawn_c[] = {2, 4, 8, 16}, anni_c[] = {3, 9, 24}, heavy_c[] = {1, 2, 4};
+    int best_s = 8, best_h = 2, best_a = 9;
     double best = 1e300;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);

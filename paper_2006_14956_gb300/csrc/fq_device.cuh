@@ -7,6 +7,37 @@
 
 namespace fq {
 
+// ---------------------------------------------------------------- programmatic dependent launch
+// The kernels of one iteration run back to back on one stream.  Launched with
+// programmatic stream serialisation, a kernel may be scheduled while its
+// predecessor's last blocks still run; it then waits here, before any read,
+// until the predecessor has completed and its writes are visible, and it lets
+// its own successor be scheduled once every one of its blocks has started.
+// Launched without that attribute both instructions return at once.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// launch with programmatic stream serialisation when `pdl`, else a plain launch
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s, bool pdl,
+                     Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, ((KArgs)args)...);
+}
+
 // ---------------------------------------------------------------- bit tricks
 __device__ __forceinline__ u64 mask_below(int p) { return p >= 64 ? ~0ULL : ((1ULL << p) - 1ULL); }
 

@@ -196,13 +196,11 @@ __device__ void spawn_single(const DevInst &I, u64 pa, u64 pb, double cper, unsi
 }
 
 // double excitation (App. A): ordered electron pair w1, hole pair w2
-__device__ void spawn_double(const DevInst &I, u64 pa, u64 pb, double cper, unsigned flags, u64 w1, u64 w2, u64 w3,
+__device__ void spawn_double(const DevInst &I, u64 pa, u64 pb, double cper, unsigned flags, unsigned ep, u64 w2, u64 w3,
                        const SpawnCtx &cx)
 {
-    const int N = I.norb, n = I.n, na = I.na;
-    const unsigned xe = (unsigned)pick(w1, (u64)(n * (n - 1)));
-    const int e1 = (int)(xe / (unsigned)(n - 1)), r = (int)(xe % (unsigned)(n - 1));
-    const int e2 = r + (r >= e1 ? 1 : 0);
+    const int N = I.norb, na = I.na;
+    const int e1 = (int)(ep & 0xffu), e2 = (int)(ep >> 8);  // the ordered pair drawn from w1 (classify)
     const int s1 = e1 >= na, s2 = e2 >= na;
     const int o1 = nth_set(s1 ? pb : pa, s1 ? e1 - na : e1);
     const int o2 = nth_set(s2 ? pb : pa, s2 ? e2 - na : e2);
@@ -248,13 +246,11 @@ __device__ void spawn_double(const DevInst &I, u64 pa, u64 pb, double cper, unsi
 // (top 53 bits); an occupied hole or an empty table fails the attempt.  With
 // p_gen = p_pair |H| / S the weight is -sign(H) lambda_ij C_i / n_att,
 // lambda_ij = tau S / p_pair (stored per table).
-__device__ void spawn_double_pchb(const DevInst &I, u64 pa, u64 pb, double cper, unsigned flags, u64 w1, u64 w2,
+__device__ void spawn_double_pchb(const DevInst &I, u64 pa, u64 pb, double cper, unsigned flags, unsigned ep, u64 w2,
                                   u64 w3, const SpawnCtx &cx)
 {
-    const int N = I.norb, n = I.n, na = I.na;
-    const unsigned xe = (unsigned)pick(w1, (u64)(n * (n - 1)));
-    const int e1 = (int)(xe / (unsigned)(n - 1)), r = (int)(xe % (unsigned)(n - 1));
-    const int e2 = r + (r >= e1 ? 1 : 0);
+    const int N = I.norb, na = I.na;
+    const int e1 = (int)(ep & 0xffu), e2 = (int)(ep >> 8);  // the ordered pair drawn from w1 (classify)
     const int s1 = e1 >= na, s2 = e2 >= na;
     const int o1 = nth_set(s1 ? pb : pa, s1 ? e1 - na : e1);
     const int o2 = nth_set(s2 ? pb : pa, s2 ? e2 - na : e2);
@@ -310,10 +306,12 @@ __device__ void spawn_double_pchb(const DevInst &I, u64 pa, u64 pb, double cper,
     emit_weight(I, ta, tb, neg_if(!(dbits(H) & SIGN64), wv), flags, w3, H, cx);
 }
 
-// class of one attempt from its first two words, or -1 for a failed attempt
+// class of one attempt from its first two words, or -1 for a failed attempt;
+// for a double, *ep = e1 | e2 << 8 (the ordered electron pair drawn from w1)
 enum { Q_DOUBLE = 0, Q_SINGLE = 1, Q_HOP = 2, NQ = 3 };
-__device__ __forceinline__ int classify(const DevInst &I, u64 pa, u64 pb, u64 w0, u64 w1)
+__device__ __forceinline__ int classify(const DevInst &I, u64 pa, u64 pb, u64 w0, u64 w1, unsigned *ep)
 {
+    *ep = 0;
     if (I.kind == FCIQMC_HUBBARD) return Q_HOP;
     if ((w0 >> 11) < I.tsingle) {
         const int e = (int)pick(w1, (u64)I.n);
@@ -324,6 +322,7 @@ __device__ __forceinline__ int classify(const DevInst &I, u64 pa, u64 pb, u64 w0
     const unsigned xe = (unsigned)pick(w1, (u64)(n * (n - 1)));
     const int e1 = (int)(xe / (unsigned)(n - 1)), r = (int)(xe % (unsigned)(n - 1));
     const int e2 = r + (r >= e1 ? 1 : 0);
+    *ep = (unsigned)e1 | ((unsigned)e2 << 8);
     const int s1 = e1 >= I.na, s2 = e2 >= I.na;
     if (s1 != s2) return (I.ma == 0 || I.mb == 0) ? -1 : Q_DOUBLE;
     return (s1 ? I.mb : I.ma) < 2 ? -1 : Q_DOUBLE;
@@ -333,7 +332,7 @@ constexpr int CHUNK = 1024;  // attempts drawn and queued per round
 struct SpawnRec {
     u64 w1, w2, w3;
     unsigned det;
-    unsigned pad;
+    unsigned ep;  // electron pair of a double (classify)
 };
 struct K1Smem {
     ulonglong2 key[CAP_M];
@@ -371,20 +370,22 @@ __device__ void run_attempts(const DevInst &I, K1Smem &S, long long it, unsigned
         // evaluations overlap
         for (unsigned ab = a0; ab < a1; ab += 2 * K1_THREADS) {
             u64 w[2][4];
-            unsigned det[2];
+            unsigned det[2], ep[2];
             int cls[2];
 #pragma unroll
             for (int h = 0; h < 2; h++) {
                 const unsigned a = ab + h * K1_THREADS + t;
                 cls[h] = -1;
                 det[h] = 0;
+                ep[h] = 0;
                 if (ab + h * K1_THREADS + (unsigned)(t & ~31) < a1) {  // a warp with no attempt left draws nothing
                     const unsigned ac = a < a1 ? a : a1 - 1;           // clamped: drawn, then discarded
                     u64 k;
                     det[h] = map.det_of(ac, k);
                     const ulonglong2 kk = map.key(det[h]);
                     philox(kk.x, kk.y, (u64)it, (k << 8) | (u64)PURPOSE_SPAWN, I.seed, I.replica, w[h]);
-                    cls[h] = a < a1 ? classify(I, kk.x, kk.y, w[h][0], w[h][1]) : -1;
+                    const int q = classify(I, kk.x, kk.y, w[h][0], w[h][1], &ep[h]);
+                    cls[h] = a < a1 ? q : -1;
                 }
             }
 #pragma unroll
@@ -402,7 +403,7 @@ __device__ void run_attempts(const DevInst &I, K1Smem &S, long long it, unsigned
                 if (front || back) {
                     const int slot = front ? bf + __popc(mf & below) : CHUNK - 1 - (bk + __popc(mb & below));
                     SpawnRec &r = S.rec[slot];
-                    r.w1 = w[h][1]; r.w2 = w[h][2]; r.w3 = w[h][3]; r.det = det[h];
+                    r.w1 = w[h][1]; r.w2 = w[h][2]; r.w3 = w[h][3]; r.det = det[h]; r.ep = ep[h];
                 }
             }
         }
@@ -427,8 +428,8 @@ __device__ void run_attempts(const DevInst &I, K1Smem &S, long long it, unsigned
                 const unsigned d = r.det;
                 const ulonglong2 kk = map.key(d);
                 const SpawnCtx cx{map.slot(d), par, shift};
-                if (I.pchb) spawn_double_pchb(I, kk.x, kk.y, map.cper(d), map.flags(d), r.w1, r.w2, r.w3, cx);
-                else spawn_double(I, kk.x, kk.y, map.cper(d), map.flags(d), r.w1, r.w2, r.w3, cx);
+                if (I.pchb) spawn_double_pchb(I, kk.x, kk.y, map.cper(d), map.flags(d), r.ep, r.w2, r.w3, cx);
+                else spawn_double(I, kk.x, kk.y, map.cper(d), map.flags(d), r.ep, r.w2, r.w3, cx);
             }
         }
         __syncthreads();
@@ -467,6 +468,7 @@ struct HeavyMap {
 __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn(const DevInst *__restrict__ insts, const int *__restrict__ unit_start,
                                                       int n_inst, int n_units)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char k1_raw[];
     K1Smem &S = *reinterpret_cast<K1Smem *>(k1_raw);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -580,6 +582,7 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn(const DevInst *__restri
 
 __global__ void __launch_bounds__(K1_THREADS) k_spawn_heavy(const DevInst *__restrict__ insts, int n_inst)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char k1_raw[];
     K1Smem &S = *reinterpret_cast<K1Smem *>(k1_raw);
     for (int ii = 0; ii < n_inst; ii++) {
@@ -1072,6 +1075,7 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
 __global__ void __launch_bounds__(K3_THREADS, 3) k_annihilate(const DevInst *__restrict__ insts,
                                                               const int *__restrict__ unit_start, int n_inst, int n_units)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     K3Smem &Sm = *reinterpret_cast<K3Smem *>(smem_raw);
     K3Shared &S = Sm.sh;
@@ -1112,6 +1116,7 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k_annihilate(const DevInst *__r
 
 __global__ void __launch_bounds__(K3_THREADS) k_annihilate_big(const DevInst *__restrict__ insts, int n_inst)
 {
+    pdl_enter();
     __shared__ K3Shared S;
     const int t = threadIdx.x;
     for (int ii = 0; ii < n_inst; ii++) {
@@ -1170,6 +1175,7 @@ __device__ __forceinline__ void int_chunk_add(int c, u64 &x, u64 &y, u64 ox, u64
 
 __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restrict__ insts, int n_inst)
 {
+    pdl_enter();
     const DevInst &I = insts[blockIdx.x];
     IterState *st = I.st;
     __shared__ int s_err;
@@ -1465,8 +1471,16 @@ void launch_build_kidx(const DevInst *dinst, int parity, int nb, cudaStream_t s)
     k_build_kidx<<<grid, 256, 0, s>>>(dinst, parity, nb);
 }
 
-// launch geometry, chosen by fciqmc_autotune (blocks per SM)
-static int g_spawn_bps = 8, g_heavy_bps = 2, g_anni_bps = 3;
+// launch geometry, chosen by fciqmc_autotune (grid blocks per SM; beyond the
+// resident count, here 3 per SM for the spawning and annihilation kernels, the
+// hardware hands the next block to whichever slot frees first, which evens out
+// buckets of unequal size)
+static int g_spawn_bps = 8, g_heavy_bps = 2, g_anni_bps = 9;
+// iteration kernels after the first are launched with programmatic stream
+// serialisation unless their launches are timed one by one
+static thread_local bool g_pdl = false;
+void set_pdl(bool on) { g_pdl = on; }
+bool pdl_on() { return g_pdl; }
 void set_launch_geometry(int spawn_bps, int heavy_bps, int anni_bps)
 {
     g_spawn_bps = spawn_bps;
@@ -1484,12 +1498,12 @@ void launch_spawn(const DevInst *dinst, const int *unit_start, int n_inst, int n
 {
     int grid = n_units < num_sms() * g_spawn_bps ? n_units : num_sms() * g_spawn_bps;
     if (grid < 1) grid = 1;
-    k_spawn<<<grid, K1_THREADS, sizeof(K1Smem), s>>>(dinst, unit_start, n_inst, n_units);
+    launch_k(k_spawn, (unsigned)grid, K1_THREADS, sizeof(K1Smem), s, false, dinst, unit_start, n_inst, n_units);
 }
 
 void launch_spawn_heavy(const DevInst *dinst, int n_inst, cudaStream_t s)
 {
-    k_spawn_heavy<<<num_sms() * g_heavy_bps, K1_THREADS, sizeof(K1Smem), s>>>(dinst, n_inst);
+    launch_k(k_spawn_heavy, (unsigned)(num_sms() * g_heavy_bps), K1_THREADS, sizeof(K1Smem), s, g_pdl, dinst, n_inst);
 }
 
 cudaError_t init_kernels()
@@ -1508,18 +1522,17 @@ cudaError_t launch_annihilate(const DevInst *dinst, const int *unit_start, int n
     const size_t smem = sizeof(K3Smem);
     int grid = n_units < num_sms() * g_anni_bps ? n_units : num_sms() * g_anni_bps;
     if (grid < 1) grid = 1;
-    k_annihilate<<<grid, K3_THREADS, smem, s>>>(dinst, unit_start, n_inst, n_units);
-    return cudaGetLastError();
+    return launch_k(k_annihilate, (unsigned)grid, K3_THREADS, smem, s, g_pdl, dinst, unit_start, n_inst, n_units);
 }
 
 void launch_annihilate_big(const DevInst *dinst, int n_inst, cudaStream_t s)
 {
-    k_annihilate_big<<<BIG_BLOCKS, K3_THREADS, 0, s>>>(dinst, n_inst);
+    launch_k(k_annihilate_big, BIG_BLOCKS, K3_THREADS, 0, s, g_pdl, dinst, n_inst);
 }
 
 void launch_finalize(const DevInst *dinst, int n_inst, cudaStream_t s)
 {
-    k_finalize<<<n_inst, K5_THREADS, 0, s>>>(dinst, n_inst);
+    launch_k(k_finalize, (unsigned)n_inst, K5_THREADS, 0, s, g_pdl, dinst, n_inst);
 }
 
 // H_jj - E_ref of the determinants created in this iteration (new list,
@@ -1530,6 +1543,7 @@ void launch_finalize(const DevInst *dinst, int n_inst, cudaStream_t s)
 constexpr int ND_PAIRS = 2080;  // n (n + 1) / 2 terms for up to 64 electrons
 __global__ void __launch_bounds__(256) k_new_diag(const DevInst *__restrict__ insts, int n_inst)
 {
+    pdl_enter();
     __shared__ unsigned short s_term[ND_PAIRS];   // e1 | e2 << 8, e2 = 255 for h_pp
     __shared__ unsigned char s_orb[8][2][64];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -1611,7 +1625,7 @@ __global__ void __launch_bounds__(256) k_new_diag(const DevInst *__restrict__ in
 
 void launch_new_diag(const DevInst *dinst, int n_inst, cudaStream_t s)
 {
-    k_new_diag<<<num_sms() * 8, 256, 0, s>>>(dinst, n_inst);
+    launch_k(k_new_diag, (unsigned)(num_sms() * 8), 256, 0, s, g_pdl, dinst, n_inst);
 }
 
 void launch_rebucket(const DevInst *src, const DevInst *dst, int nb_src, int parity, cudaStream_t s)
