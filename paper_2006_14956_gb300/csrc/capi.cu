@@ -274,8 +274,6 @@ static int upload_inst(fciqmc_handle *h)
 static int enqueue_iteration(fciqmc_handle *h, cudaEvent_t *ev)
 {
     const int units = 1 << h->bb;
-    set_pdl(ev == nullptr);  // kernels timed one by one are launched plainly
-    struct PdlOff { ~PdlOff() { set_pdl(false); } } pdl_off;
     if (ev) cudaEventRecord(ev[0], h->stream);
     launch_spawn(h->dinst, h->dunit, 1, units, h->stream);
     if (ev) cudaEventRecord(ev[1], h->stream);
@@ -1550,8 +1548,6 @@ int fciqmc_step_batch(fciqmc_handle **hs, int32_t k, int64_t n_iter)
         cleanup();
         cudaGraph_t g;
         CUDA_TRY(h0, cudaStreamBeginCapture(h0->stream, cudaStreamCaptureModeThreadLocal));
-        set_pdl(true);
-        struct PdlOff { ~PdlOff() { set_pdl(false); } } pdl_off;
         launch_spawn(dinst, dunit, k, units, h0->stream);
         launch_spawn_heavy(dinst, k, h0->stream);
         if (max_nd > 0) launch_semistoch(dinst, k, max_nd, h0->stream);

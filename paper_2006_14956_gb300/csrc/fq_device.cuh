@@ -7,37 +7,6 @@
 
 namespace fq {
 
-// ---------------------------------------------------------------- programmatic dependent launch
-// The kernels of one iteration run back to back on one stream.  Launched with
-// programmatic stream serialisation, a kernel may be scheduled while its
-// predecessor's last blocks still run; it then waits here, before any read,
-// until the predecessor has completed and its writes are visible, and it lets
-// its own successor be scheduled once every one of its blocks has started.
-// Launched without that attribute both instructions return at once.
-__device__ __forceinline__ void pdl_enter()
-{
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
-// launch with programmatic stream serialisation when `pdl`, else a plain launch
-template <typename... KArgs, typename... Args>
-cudaError_t launch_k(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s, bool pdl,
-                     Args... args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, kern, ((KArgs)args)...);
-}
-
 // ---------------------------------------------------------------- bit tricks
 __device__ __forceinline__ u64 mask_below(int p) { return p >= 64 ? ~0ULL : ((1ULL << p) - 1ULL); }
 
@@ -94,8 +63,9 @@ __device__ __forceinline__ void philox(u64 c0, u64 c1, u64 c2, u64 c3, u64 k0, u
 #pragma unroll
     for (int r = 0; r < 10; r++) {
         if (r) { k0 += W0; k1 += W1; }
-        u64 hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
-        u64 hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        const u128 p0 = (u128)M0 * c0, p1 = (u128)M1 * c2;  // one 128-bit product each (fewer
+        const u64 hi0 = (u64)(p0 >> 64), lo0 = (u64)p0;        // instructions than separate high and
+        const u64 hi1 = (u64)(p1 >> 64), lo1 = (u64)p1;        // low multiplies)
         u64 n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
         c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
     }

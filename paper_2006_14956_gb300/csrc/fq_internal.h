@@ -234,8 +234,6 @@ cudaError_t launch_trial_w(const DevInst *dinst, const ulonglong2 *tkey, const d
                            int *err, cudaStream_t s);
 long long connections_per_det(int na, int nb, int ma, int mb);
 void set_launch_geometry(int spawn_bps, int heavy_bps, int anni_bps);
-void set_pdl(bool on);  // programmatic dependent launch of the iteration kernels after the first
-bool pdl_on();
 void get_launch_geometry(int *spawn_bps, int *heavy_bps, int *anni_bps);
 cudaError_t ref_abs_sum(const DevInst *dinst, double *dpartial, double *out, cudaStream_t s);
 size_t export_scratch_bytes(long long n);

@@ -468,26 +468,35 @@ struct HeavyMap {
 __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn(const DevInst *__restrict__ insts, const int *__restrict__ unit_start,
                                                       int n_inst, int n_units)
 {
-    pdl_enter();
     extern __shared__ __align__(16) unsigned char k1_raw[];
     K1Smem &S = *reinterpret_cast<K1Smem *>(k1_raw);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     constexpr int PER = CAP_M / K1_THREADS;
+    // the run's state at the start of the iteration, read once per run a
+    // block meets (a flag raised by another block during this kernel makes the
+    // host repeat the iteration, whose output is then discarded)
+    int cur = -1, err = 0, par = 0;
+    long long it = 0;
+    double shift = 0.0;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
         const int ii = find_inst(unit_start, n_inst, u);
         const DevInst &I = insts[ii];
-        if (t == 0) {
-            S.hdr_err = *(volatile int *)&I.st->err;
-            S.hdr_par = I.st->parity;
-            S.hdr_it = I.st->iter;
-            S.hdr_S = I.st->S;
-            I.st->err_at_start = S.hdr_err;  // the same value from every block of the run
+        if (ii != cur) {
+            if (t == 0) {
+                S.hdr_err = *(volatile int *)&I.st->err;
+                S.hdr_par = I.st->parity;
+                S.hdr_it = I.st->iter;
+                S.hdr_S = I.st->S;
+                I.st->err_at_start = S.hdr_err;  // the same value from every block of the run
+            }
+            __syncthreads();
+            err = S.hdr_err;
+            par = S.hdr_par;
+            it = S.hdr_it;
+            shift = S.hdr_S;
+            cur = ii;
+            __syncthreads();
         }
-        __syncthreads();
-        const int err = S.hdr_err, par = S.hdr_par;
-        const long long it = S.hdr_it;
-        const double shift = S.hdr_S;
-        __syncthreads();
         if (err) continue;
         const int b = u - I.unit0;
         const int m = I.cnt[par][b];
@@ -582,7 +591,6 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn(const DevInst *__restri
 
 __global__ void __launch_bounds__(K1_THREADS) k_spawn_heavy(const DevInst *__restrict__ insts, int n_inst)
 {
-    pdl_enter();
     extern __shared__ __align__(16) unsigned char k1_raw[];
     K1Smem &S = *reinterpret_cast<K1Smem *>(k1_raw);
     for (int ii = 0; ii < n_inst; ii++) {
@@ -1075,7 +1083,6 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
 __global__ void __launch_bounds__(K3_THREADS, 3) k_annihilate(const DevInst *__restrict__ insts,
                                                               const int *__restrict__ unit_start, int n_inst, int n_units)
 {
-    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     K3Smem &Sm = *reinterpret_cast<K3Smem *>(smem_raw);
     K3Shared &S = Sm.sh;
@@ -1116,7 +1123,6 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k_annihilate(const DevInst *__r
 
 __global__ void __launch_bounds__(K3_THREADS) k_annihilate_big(const DevInst *__restrict__ insts, int n_inst)
 {
-    pdl_enter();
     __shared__ K3Shared S;
     const int t = threadIdx.x;
     for (int ii = 0; ii < n_inst; ii++) {
@@ -1175,7 +1181,6 @@ __device__ __forceinline__ void int_chunk_add(int c, u64 &x, u64 &y, u64 ox, u64
 
 __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restrict__ insts, int n_inst)
 {
-    pdl_enter();
     const DevInst &I = insts[blockIdx.x];
     IterState *st = I.st;
     __shared__ int s_err;
@@ -1476,11 +1481,6 @@ void launch_build_kidx(const DevInst *dinst, int parity, int nb, cudaStream_t s)
 // hardware hands the next block to whichever slot frees first, which evens out
 // buckets of unequal size)
 static int g_spawn_bps = 8, g_heavy_bps = 2, g_anni_bps = 9;
-// iteration kernels after the first are launched with programmatic stream
-// serialisation unless their launches are timed one by one
-static thread_local bool g_pdl = false;
-void set_pdl(bool on) { g_pdl = on; }
-bool pdl_on() { return g_pdl; }
 void set_launch_geometry(int spawn_bps, int heavy_bps, int anni_bps)
 {
     g_spawn_bps = spawn_bps;
@@ -1498,12 +1498,12 @@ void launch_spawn(const DevInst *dinst, const int *unit_start, int n_inst, int n
 {
     int grid = n_units < num_sms() * g_spawn_bps ? n_units : num_sms() * g_spawn_bps;
     if (grid < 1) grid = 1;
-    launch_k(k_spawn, (unsigned)grid, K1_THREADS, sizeof(K1Smem), s, false, dinst, unit_start, n_inst, n_units);
+    k_spawn<<<grid, K1_THREADS, sizeof(K1Smem), s>>>(dinst, unit_start, n_inst, n_units);
 }
 
 void launch_spawn_heavy(const DevInst *dinst, int n_inst, cudaStream_t s)
 {
-    launch_k(k_spawn_heavy, (unsigned)(num_sms() * g_heavy_bps), K1_THREADS, sizeof(K1Smem), s, g_pdl, dinst, n_inst);
+    k_spawn_heavy<<<num_sms() * g_heavy_bps, K1_THREADS, sizeof(K1Smem), s>>>(dinst, n_inst);
 }
 
 cudaError_t init_kernels()
@@ -1522,30 +1522,31 @@ cudaError_t launch_annihilate(const DevInst *dinst, const int *unit_start, int n
     const size_t smem = sizeof(K3Smem);
     int grid = n_units < num_sms() * g_anni_bps ? n_units : num_sms() * g_anni_bps;
     if (grid < 1) grid = 1;
-    return launch_k(k_annihilate, (unsigned)grid, K3_THREADS, smem, s, g_pdl, dinst, unit_start, n_inst, n_units);
+    k_annihilate<<<grid, K3_THREADS, smem, s>>>(dinst, unit_start, n_inst, n_units);
+    return cudaGetLastError();
 }
 
 void launch_annihilate_big(const DevInst *dinst, int n_inst, cudaStream_t s)
 {
-    launch_k(k_annihilate_big, BIG_BLOCKS, K3_THREADS, 0, s, g_pdl, dinst, n_inst);
+    k_annihilate_big<<<BIG_BLOCKS, K3_THREADS, 0, s>>>(dinst, n_inst);
 }
 
 void launch_finalize(const DevInst *dinst, int n_inst, cudaStream_t s)
 {
-    launch_k(k_finalize, (unsigned)n_inst, K5_THREADS, 0, s, g_pdl, dinst, n_inst);
+    k_finalize<<<n_inst, K5_THREADS, 0, s>>>(dinst, n_inst);
 }
 
 // H_jj - E_ref of the determinants created in this iteration (new list,
-// parity ^ 1), two per warp.  The terms (h_pp of electron e1, or the pair
-// e1 < e2) are listed once per block in shared memory, and each warp keeps
-// the occupied orbitals of its two determinants there, so a term costs two
-// shared loads and one table load.
+// parity ^ 1), four per warp with eight lanes each.  The terms (h_pp of
+// electron e1, or the pair e1 < e2) are listed once per block in shared
+// memory, and each warp keeps the occupied orbitals of its four determinants
+// there, so a term costs two shared loads and one table load; each lane group
+// sums its terms exactly and reduces over its eight lanes.
 constexpr int ND_PAIRS = 2080;  // n (n + 1) / 2 terms for up to 64 electrons
 __global__ void __launch_bounds__(256) k_new_diag(const DevInst *__restrict__ insts, int n_inst)
 {
-    pdl_enter();
     __shared__ unsigned short s_term[ND_PAIRS];   // e1 | e2 << 8, e2 = 255 for h_pp
-    __shared__ unsigned char s_orb[8][2][64];
+    __shared__ unsigned char s_orb[8][4][64];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarp = (int)((gridDim.x * blockDim.x) >> 5);
     for (int ii = 0; ii < n_inst; ii++) {
@@ -1578,46 +1579,37 @@ __global__ void __launch_bounds__(256) k_new_diag(const DevInst *__restrict__ in
             s_term[t] = (unsigned short)((q - c * (c - 1) / 2) | (c << 8));
         }
         __syncthreads();
-        for (int q = 2 * gw; q < nn; q += 2 * nwarp) {
-            const unsigned d[2] = {I.newdet[q], q + 1 < nn ? I.newdet[q + 1] : I.newdet[q]};
-#pragma unroll
-            for (int k = 0; k < 2; k++) {
-                const ulonglong2 key = nkey[d[k]];
-                for (int e = lane; e < n; e += 32)
-                    s_orb[wl][k][e] = (unsigned char)(e < na ? nth_set(key.x, e) : nth_set(key.y, e - na));
-            }
+        // four determinants per warp, eight lanes each: lane group g takes
+        // determinant q + g (a short last round repeats determinant q and
+        // stores nothing for it), its lanes the terms sl, sl + 8, ...
+        const int g = lane >> 3, sl = lane & 7;
+        const i128 xref = (i128)(((u128)I.xref_hi << 64) | (u128)I.xref_lo);
+        for (int q = 4 * gw; q < nn; q += 4 * nwarp) {
+            const unsigned d = I.newdet[q + g < nn ? q + g : q];
+            const ulonglong2 key = nkey[d];
+            for (int e = sl; e < n; e += 8)
+                s_orb[wl][g][e] = (unsigned char)(e < na ? nth_set(key.x, e) : nth_set(key.y, e - na));
             __syncwarp();
-            i128 part[2] = {0, 0};
-            for (int t0 = 0; t0 < T; t0 += 128) {
-                ulonglong2 v[2][4];
+            i128 part = 0;
+            for (int t0 = sl; t0 < T; t0 += 32) {
+                ulonglong2 v[4];
 #pragma unroll
                 for (int r = 0; r < 4; r++) {
-                    const int t = t0 + 32 * r + lane;
-                    const unsigned tm = t < T ? s_term[t] : 0u;
-                    const int e1 = (int)(tm & 0xffu), e2 = (int)(tm >> 8);
-                    const bool same = e2 != 255 && ((e1 < na) == (e2 < na));
-#pragma unroll
-                    for (int k = 0; k < 2; k++) {
-                        v[k][r] = make_ulonglong2(0, 0);
-                        if (t < T) {
-                            const int p1 = s_orb[wl][k][e1];
-                            v[k][r] = e2 == 255 ? __ldg(I.hfx + p1)
-                                                : __ldg((same ? I.JKfx : I.Jfx) + p1 * N + s_orb[wl][k][e2]);
-                        }
+                    const int t = t0 + 8 * r;
+                    v[r] = make_ulonglong2(0, 0);
+                    if (t < T) {
+                        const unsigned tm = s_term[t];
+                        const int e1 = (int)(tm & 0xffu), e2 = (int)(tm >> 8);
+                        const int p1 = s_orb[wl][g][e1];
+                        if (e2 == 255) v[r] = __ldg(I.hfx + p1);
+                        else v[r] = __ldg((((e1 < na) == (e2 < na)) ? I.JKfx : I.Jfx) + p1 * N + s_orb[wl][g][e2]);
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < 2; k++)
-#pragma unroll
-                    for (int r = 0; r < 4; r++) part[k] += (i128)(((u128)v[k][r].y << 64) | (u128)v[k][r].x);
+                for (int r = 0; r < 4; r++) part += (i128)(((u128)v[r].y << 64) | (u128)v[r].x);
             }
-            const i128 xref = (i128)(((u128)I.xref_hi << 64) | (u128)I.xref_lo);
-#pragma unroll
-            for (int k = 0; k < 2; k++) {
-                i128 x = part[k];
-                for (int m = 16; m >= 1; m >>= 1) x += shfl_xor_i128(x, m);
-                if (lane == 0 && (k == 0 || q + 1 < nn)) nhd[d[k]] = fixed_to_double(x - xref, I.F);
-            }
+            for (int m = 4; m >= 1; m >>= 1) part += shfl_xor_i128(part, m);
+            if (sl == 0 && q + g < nn) nhd[d] = fixed_to_double(part - xref, I.F);
             __syncwarp();
         }
     }
@@ -1625,7 +1617,7 @@ __global__ void __launch_bounds__(256) k_new_diag(const DevInst *__restrict__ in
 
 void launch_new_diag(const DevInst *dinst, int n_inst, cudaStream_t s)
 {
-    launch_k(k_new_diag, (unsigned)(num_sms() * 8), 256, 0, s, g_pdl, dinst, n_inst);
+    k_new_diag<<<num_sms() * 8, 256, 0, s>>>(dinst, n_inst);
 }
 
 void launch_rebucket(const DevInst *src, const DevInst *dst, int nb_src, int parity, cudaStream_t s)

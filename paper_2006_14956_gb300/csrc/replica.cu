@@ -26,7 +26,6 @@ constexpr int XC_PT2CAP = 1024;  // matched rejected determinants queued for the
 
 __global__ void __launch_bounds__(XC_THREADS) k_replica_cross(const DevInst *__restrict__ insts, int n_inst)
 {
-    pdl_enter();
     extern __shared__ unsigned xtab[];
     __shared__ int s_np;
     __shared__ int s_pair[XC_PT2CAP][2];
@@ -138,7 +137,8 @@ cudaError_t launch_replica_cross(const DevInst *dinst, int n_inst, int max_bucke
     int blocks = sm * 2;
     if (blocks > max_buckets) blocks = max_buckets;
     if (blocks < 1) blocks = 1;
-    return launch_k(k_replica_cross, (unsigned)blocks, XC_THREADS, smem, s, pdl_on(), dinst, n_inst);
+    k_replica_cross<<<blocks, XC_THREADS, smem, s>>>(dinst, n_inst);
+    return cudaGetLastError();
 }
 
 }  // namespace fq

@@ -102,7 +102,6 @@ __global__ void k_mark_d(const DevInst *__restrict__ I, int par, int nb)
 // repeated iteration starts from unchanged values)
 __global__ void k_semistoch(const DevInst *__restrict__ insts, int n_inst)
 {
-    pdl_enter();
     for (int ii = 0; ii < n_inst; ii++) {
         const DevInst &I = insts[ii];
         if (I.nd == 0) continue;
@@ -131,7 +130,7 @@ void launch_semistoch(const DevInst *dinst, int n_inst, int max_nd, cudaStream_t
     int blocks = (max_nd + 255) / 256;
     if (blocks > sms() * 4) blocks = sms() * 4;
     if (blocks < 1) blocks = 1;
-    launch_k(k_semistoch, (unsigned)blocks, 256, 0, s, pdl_on(), dinst, n_inst);
+    k_semistoch<<<blocks, 256, 0, s>>>(dinst, n_inst);
 }
 
 void launch_abs_hist(const DevInst *dinst, int par, int nb, int shift, u64 prefix, unsigned *hist, cudaStream_t s)
