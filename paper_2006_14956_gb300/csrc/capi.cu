@@ -415,6 +415,7 @@ static int reset_after_error(fciqmc_handle *h)
     h->hst.need_main = 0;
     h->hst.n_spawn_over = 0;
     h->hst.new_n = 0;
+    CUDA_TRY(h, cudaMemsetAsync(h->hi.acc, 0, NSHARD * ACC_STRIDE * sizeof(u64), h->stream));  // partial totals
     // the failed iteration's adaptive-shift weight sums are discarded when the
     // descriptor is next uploaded (the device copy may still describe an old
     // layout here)
@@ -845,6 +846,14 @@ static int create_run(const fciqmc_system *sys, const fciqmc_params *prm, u64 re
     I.partner = -1;
     I.kind = h->kind; I.norb = N; I.na = h->na; I.nb = h->nb; I.n = n; I.ma = N - h->na; I.mb = N - h->nb; I.z = h->z;
     I.F = F; I.Fw = Fw;
+    {
+        // E_num total on the grid 2^-Fe: |H_ref,j| < (2n + 1) 2^(msb_max + 1), |C_j| < 2^31 and at most
+        // 2^34 determinants, so |E_num| 2^Fe stays below 2^126 with Fe = 60 - msb_max - ceil(log2(2n + 1))
+        int L = 0;
+        while ((1LL << L) < 2LL * n + 1) L++;
+        const int fe = any ? 60 - msb_max - L : 64;
+        I.Fe = fe > 64 ? 64 : fe;
+    }
     I.ref_a = h->ref_a; I.ref_b = h->ref_b; I.normask = normask;
     I.xref_lo = (u64)(u128)xref; I.xref_hi = (u64)((u128)xref >> 64);
     const bool auto_tau = !(P.tau > 0.0);
@@ -879,8 +888,10 @@ static int create_run(const fciqmc_system *sys, const fciqmc_params *prm, u64 re
     h->dunit = (int *)dev_alloc(h, 2 * sizeof(int));
     h->dstate = (IterState *)dev_alloc(h, sizeof(IterState));
     I.ring = (fciqmc_iter_stats *)dev_alloc(h, (size_t)h->ring_cap * sizeof(fciqmc_iter_stats));
-    if (!dh || !deri || !dhfx || !dJ || !dK || !dS || !dnbr || !h->dinst || !h->dunit || !h->dstate || !I.ring)
+    I.acc = (u64 *)dev_alloc(h, NSHARD * ACC_STRIDE * sizeof(u64));
+    if (!dh || !deri || !dhfx || !dJ || !dK || !dS || !dnbr || !h->dinst || !h->dunit || !h->dstate || !I.ring || !I.acc)
         return bail(FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (integrals)");
+    cudaMemsetAsync(I.acc, 0, NSHARD * ACC_STRIDE * sizeof(u64), h->stream);
     cudaMemcpyAsync(dh, h->h.data(), h->h.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);
     cudaMemcpyAsync(deri, h->eri.data(), h->eri.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);
     cudaMemcpyAsync(dhfx, hfx.data(), hfx.size() * sizeof(ulonglong2), cudaMemcpyHostToDevice, h->stream);
@@ -1455,6 +1466,7 @@ int fciqmc_import_state(fciqmc_handle *h, int64_t n, const uint64_t *alpha, cons
     if (h->p.adaptive_shift) launch_build_kidx(h->dinst, par, (int)nbk, h->stream);
     CUDA_TRY(h, cudaGetLastError());
     memset(&h->hst, 0, sizeof(IterState));
+    CUDA_TRY(h, cudaMemsetAsync(h->hi.acc, 0, NSHARD * ACC_STRIDE * sizeof(u64), h->stream));
     h->hst.stop_iter = LLONG_MAX;
     h->hst.iter = iteration; h->hst.parity = par; h->hst.S = S; h->hst.vary = vary;
     h->hst.shift_start = shift_start; h->hst.cnt = cnt; h->hst.nwl_hi = nw_last_hi; h->hst.nwl_lo = nw_last_lo;

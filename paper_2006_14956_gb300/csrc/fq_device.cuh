@@ -202,6 +202,31 @@ __device__ __forceinline__ double u128_to_double(u128 u) { return fixed_to_doubl
 __device__ __forceinline__ double i128_to_double(i128 v) { return fixed_to_double(v, 0); }
 
 
+// a global add whose result nobody reads: a reduction, not an atomic that
+// returns the old value
+__device__ __forceinline__ void red_add(u64 *p, u64 v)
+{
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// exact per-iteration totals (ACC_* in fq_internal.h): v added as three
+// limbs, no add waiting for another's result
+__device__ __forceinline__ void limb_add(u64 *acc, i128 v)
+{
+    const u128 u = (u128)v;
+    const u64 mask = (1ULL << LIMB) - 1ULL;
+    const u64 l0 = (u64)u & mask, l1 = (u64)(u >> LIMB) & mask, l2 = (u64)(long long)(v >> (2 * LIMB));
+    if (l0) red_add(acc, l0);
+    if (l1) red_add(acc + 1, l1);
+    if (l2) red_add(acc + 2, l2);
+}
+
+__device__ __forceinline__ i128 limb_total(const u64 *acc)
+{
+    const u128 top = (u128)(i128)(long long)acc[2];  // the signed limb, two's complement
+    return (i128)((u128)acc[0] + ((u128)acc[1] << LIMB) + (top << (2 * LIMB)));
+}
+
 __device__ __forceinline__ i128 shfl_xor_i128(i128 v, int m)
 {
     u64 lo = (u64)v, hi = (u64)((u128)v >> 64);

@@ -57,15 +57,28 @@ struct HeavyChunk {  // a slice of the attempts of one determinant with many wal
     uint32_t pad;
 };
 
-struct Partial {  // per-bucket reductions of one iteration
-    u64 nw_lo, nw_hi;       // N_w * 2^32 as a 128-bit integer
-    u64 ann_lo, ann_hi;     // annihilated walkers * 2^32 (signed 128-bit)
-    long long ndet, rejected, spawns, attempts;
-    double e_num;
+struct Partial {  // per-bucket binary64 sums of one iteration (estimators that need them)
     double t_num, t_den;    // trial-wave-function estimator
     double x_ov, x_hd, x_cr, x_pt2;  // replica pair: overlap, diagonal and spawn cross terms, PT2 sum
-    double pad;
+    double pad[2];
 };
+
+// Exact per-iteration totals, accumulated by atomic adds of every bucket's
+// share into one of NSHARD 128-byte lines (bucket b uses line b % NSHARD, so
+// the adds spread over L2 slices): 128-bit integers as three limbs (bits 0-39
+// and 40-79 unsigned, the rest signed), so that no add needs another's result
+// and every order gives the same sum; counts as plain 64-bit adds.  k_finalize
+// sums the lines and clears them when it commits the iteration; the host
+// clears them before a repeated one.
+enum {
+    ACC_NW = 0,      // N_w * 2^32, three limbs
+    ACC_ANN = 3,     // annihilated walkers * 2^32, three limbs
+    ACC_ENUM = 6,    // E_num * 2^Fe (each bucket's binary64 sum placed on the grid), three limbs
+    ACC_NDET = 9, ACC_REJ, ACC_SPAWNS, ACC_ATT,
+    NACC
+};
+constexpr int LIMB = 40;
+constexpr int NSHARD = 32, ACC_STRIDE = 16;  // lines, words per line (NACC <= ACC_STRIDE)
 
 struct SideEnt {  // one determinant of a bucket in one replica's iteration (pairs only)
     u64 a, b;
@@ -105,6 +118,7 @@ struct DevInst {
     int kind, norb, na, nb, n, ma, mb, z;
     int F;    // exact-sum scale of the integrals: value = X * 2^-F
     int Fw;   // exact-sum scale of spawned weights
+    int Fe;   // fixed-point scale of the E_num total
     const double *h;
     const double *eri;
     const int *nbr;
@@ -148,6 +162,7 @@ struct DevInst {
     HeavyChunk *heavy;
     int heavy_cap;
     Partial *part;
+    u64 *acc;  // exact totals of the iteration: NSHARD lines of ACC_STRIDE words (see ACC_*)
     IterState *st;
     fciqmc_iter_stats *ring;
     int ring_cap;

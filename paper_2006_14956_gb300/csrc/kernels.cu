@@ -343,7 +343,6 @@ struct K1Smem {
     int qn[NQ];
     int next;  // evaluation counter of the chunk
     unsigned wsum[K1_THREADS / 32];
-    long long wl[K1_THREADS / 32];
     int hdr_err, hdr_par;
     long long hdr_it;
     double hdr_S;
@@ -576,16 +575,9 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn(const DevInst *__restri
         const unsigned total = S.off[CAP_M];
         BucketMap map{&S, (unsigned)base};
         run_attempts(I, S, it, total, map, par, shift);
-        // attempts of this bucket (light and heavy)
+        // attempts of this bucket (light and heavy) into the run's exact total
         for (int o = 16; o >= 1; o >>= 1) att += __shfl_xor_sync(0xffffffffu, att, o);
-        if (lane == 0) S.wl[warp] = att;
-        __syncthreads();
-        if (t == 0) {
-            long long sm = 0;
-            for (int k = 0; k < K1_THREADS / 32; k++) sm += S.wl[k];
-            I.part[b].attempts = sm;
-        }
-        __syncthreads();
+        if (lane == 0 && att) red_add(&I.acc[(b % NSHARD) * ACC_STRIDE + ACC_ATT], (u64)att);
     }
 }
 
@@ -1062,17 +1054,20 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
             anns += (i128)(((u128)S.red_u[k][3] << 64) | S.red_u[k][2]);
             rej += (long long)S.red_u[k][4];
         }
-        Partial &P = I.part[b];
-        P.nw_lo = (u64)nws;
-        P.nw_hi = (u64)(nws >> 64);
-        P.ann_lo = (u64)anns;
-        P.ann_hi = (u64)((u128)anns >> 64);
-        P.ndet = total;
-        P.rejected = rej;
-        P.spawns = si + sn;
-        P.e_num = e_sum;
-        P.t_num = tn;
-        P.t_den = td;
+        // the bucket's share of the run's exact totals (its line b % NSHARD); the
+        // bucket's E_num, summed in a fixed order, is placed on the grid 2^-Fe
+        u64 *acc = I.acc + (b % NSHARD) * ACC_STRIDE;
+        limb_add(acc + ACC_NW, (i128)nws);
+        limb_add(acc + ACC_ANN, anns);
+        limb_add(acc + ACC_ENUM, to_fixed(e_sum, I.Fe));
+        red_add(&acc[ACC_NDET], (u64)total);
+        if (rej) red_add(&acc[ACC_REJ], (u64)rej);
+        red_add(&acc[ACC_SPAWNS], (u64)(si + sn));
+        if (I.trial_bits) {
+            Partial &P = I.part[b];
+            P.t_num = tn;
+            P.t_den = td;
+        }
         if (!overflow) I.cnt[np][b] = total;
         I.scnt_i[b] = 0;
         I.scnt_n[b] = 0;
@@ -1165,26 +1160,11 @@ __global__ void __launch_bounds__(K3_THREADS) k_annihilate_big(const DevInst *__
 }
 
 // ------------------------------------------------------------------ finalize
-// one 16-byte integer chunk of a partial added into (x, y): chunks 0 and 1
-// are 128-bit integers, 2 and 3 pairs of 64-bit counts; others are left alone
-__device__ __forceinline__ void int_chunk_add(int c, u64 &x, u64 &y, u64 ox, u64 oy)
-{
-    if (c < 2) {
-        const u128 s = (((u128)y << 64) | x) + (((u128)oy << 64) | ox);
-        x = (u64)s;
-        y = (u64)(s >> 64);
-    } else if (c < 4) {
-        x += ox;
-        y += oy;
-    }
-}
-
 __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restrict__ insts, int n_inst)
 {
     const DevInst &I = insts[blockIdx.x];
     IterState *st = I.st;
     __shared__ int s_err;
-    __shared__ ulonglong2 s_w[K5_THREADS / 32][4];
     __shared__ double s_r[K5_THREADS];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (t == 0) {
@@ -1205,89 +1185,58 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
     const int nbk = 1 << I.bb;
     const bool pair = I.partner > (int)blockIdx.x;  // the first replica reports the cross estimators
     const bool trial = I.trial_bits != 0;
-    // Integer sums: the partials as 16-byte chunks (chunk q holds words
-    // 2 (q % 8) and 2 (q % 8) + 1 of partial q / 8); thread t always takes
-    // chunk t % 8, so each warp load covers four whole partials, and eight
-    // loads are in flight per thread.  Chunk 0: N_w, 1: annihilated (128-bit
-    // integers); 2, 3: counts.
-    static_assert(sizeof(Partial) == 128 && K5_THREADS % 256 == 0, "eight 16-byte chunks per partial");
-    const int c = t & 7;
-    u64 x = 0, y = 0;
-    if (c < 4) {
-        const ulonglong2 *pc = reinterpret_cast<const ulonglong2 *>(I.part);
-        const int nq = nbk * 8;
-        for (int q0 = t; q0 < nq; q0 += 8 * K5_THREADS) {
-            ulonglong2 v[8];
-#pragma unroll
-            for (int k = 0; k < 8; k++) {
-                const int q = q0 + k * K5_THREADS;
-                v[k] = q < nq ? pc[q] : make_ulonglong2(0, 0);
-            }
-#pragma unroll
-            for (int k = 0; k < 8; k++) int_chunk_add(c, x, y, v[k].x, v[k].y);
-        }
-    }
-    for (int mm = 8; mm <= 16; mm <<= 1) {  // lanes l, l ^ 8, l ^ 16, l ^ 24 hold the same chunk
-        const u64 ox = __shfl_xor_sync(0xffffffffu, x, mm), oy = __shfl_xor_sync(0xffffffffu, y, mm);
-        int_chunk_add(c, x, y, ox, oy);
-    }
-    if (lane < 4) s_w[warp][lane] = make_ulonglong2(x, y);
-    // Binary64 sums (E_num; trial numerator and denominator; replica-pair
-    // terms), per tile of K5_THREADS buckets: one value per thread into shared
-    // memory and a halving tree, so that every binary64 add is a full-warp
-    // instruction (a partly active warp costs as much on this part's slow
-    // binary64 pipe); tile sums are added in tile order by thread 0.
-    constexpr int NF = 7;  // words 8 .. 14 of a partial
+    // Binary64 sums of the estimators that have them (trial numerator and
+    // denominator; replica-pair terms), per tile of K5_THREADS buckets: one
+    // value per thread into shared memory and a halving tree, so that every
+    // binary64 add is a full-warp instruction (a partly active warp costs as
+    // much on this part's slow binary64 pipe); tile sums added in tile order.
+    constexpr int NF = 6;  // words 0 .. 5 of a partial
     double dsum[NF];
 #pragma unroll
     for (int f = 0; f < NF; f++) dsum[f] = 0.0;
-    for (int tile0 = 0; tile0 < nbk; tile0 += K5_THREADS) {
+    if (trial || pair)
+        for (int tile0 = 0; tile0 < nbk; tile0 += K5_THREADS) {
 #pragma unroll
-        for (int f = 0; f < NF; f++) {
-            if ((f == 1 || f == 2) ? !trial : (f >= 3 && !pair)) continue;
-            const int u = tile0 + t;
-            s_r[t] = u < nbk ? __longlong_as_double(reinterpret_cast<const long long *>(I.part + u)[8 + f]) : 0.0;
-            __syncthreads();
-            for (int h = K5_THREADS / 2; h >= 32; h >>= 1) {
-                if (t < h) s_r[t] = s_r[t] + s_r[t + h];
+            for (int f = 0; f < NF; f++) {
+                if (f < 2 ? !trial : !pair) continue;
+                const int u = tile0 + t;
+                s_r[t] = u < nbk ? reinterpret_cast<const double *>(I.part + u)[f] : 0.0;
+                __syncthreads();
+                for (int h = K5_THREADS / 2; h >= 32; h >>= 1) {
+                    if (t < h) s_r[t] = s_r[t] + s_r[t + h];
+                    __syncthreads();
+                }
+                if (warp == 0) {
+                    double v = s_r[lane];
+                    for (int mm = 16; mm >= 1; mm >>= 1) v = v + __shfl_xor_sync(0xffffffffu, v, mm);
+                    if (lane == 0) dsum[f] = dsum[f] + v;
+                }
                 __syncthreads();
             }
-            if (warp == 0) {
-                double v = s_r[lane];
-                for (int mm = 16; mm >= 1; mm >>= 1) v = v + __shfl_xor_sync(0xffffffffu, v, mm);
-                if (lane == 0) dsum[f] = dsum[f] + v;
-            }
-            __syncthreads();
         }
-    }
-    __syncthreads();
-    // warp 0: lane l sums integer chunk l % 4 over warps 4 (l / 4) .. 4 (l / 4) + 3,
-    // then the eight lanes of each chunk in an xor tree
-    static_assert(K5_THREADS / 32 == 32, "eight groups of four warps");
+    // the exact totals the buckets added up: lane i reads and clears line i,
+    // the lines are summed word by word (each limb's total stays below 2^64)
+    static_assert(NSHARD == 32, "one line per lane");
     if (warp != 0) return;
-    x = 0;
-    y = 0;
-    const int ci = lane & 3, g = lane >> 2;  // chunk, group of four warps
-    for (int w = 4 * g; w < 4 * g + 4; w++) int_chunk_add(ci, x, y, s_w[w][ci].x, s_w[w][ci].y);
-    for (int mm = 4; mm <= 16; mm <<= 1) {
-        const u64 ox = __shfl_xor_sync(0xffffffffu, x, mm), oy = __shfl_xor_sync(0xffffffffu, y, mm);
-        int_chunk_add(ci, x, y, ox, oy);
-    }
-    u64 tot[4][2];
+    u64 w[NACC];
+    u64 *line = I.acc + lane * ACC_STRIDE;
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-        tot[k][0] = __shfl_sync(0xffffffffu, x, k);
-        tot[k][1] = __shfl_sync(0xffffffffu, y, k);
+    for (int k = 0; k < NACC; k++) {
+        w[k] = line[k];
+        line[k] = 0;
     }
-    const u128 W = ((u128)tot[0][1] << 64) | tot[0][0];
-    const i128 A = (i128)(((u128)tot[1][1] << 64) | tot[1][0]);
-    const long long nd = (long long)tot[2][0], rj = (long long)tot[2][1], sps = (long long)tot[3][0],
-                    at = (long long)tot[3][1];
-    const double e_num = dsum[0];
-    const double t_num = trial ? dsum[1] : 0.0, t_den = trial ? dsum[2] : 0.0;
-    const double x_ov = pair ? dsum[3] : 0.0, x_hd = pair ? dsum[4] : 0.0, x_cr = pair ? dsum[5] : 0.0;
-    const double x_pt = pair ? dsum[6] : 0.0;
+#pragma unroll
+    for (int k = 0; k < NACC; k++)
+        for (int mm = 16; mm >= 1; mm >>= 1) w[k] += __shfl_xor_sync(0xffffffffu, w[k], mm);
     if (lane != 0) return;
+    const u128 W = (u128)limb_total(w + ACC_NW);
+    const i128 A = limb_total(w + ACC_ANN), EN = limb_total(w + ACC_ENUM);
+    const long long nd = (long long)w[ACC_NDET], rj = (long long)w[ACC_REJ], sps = (long long)w[ACC_SPAWNS],
+                    at = (long long)w[ACC_ATT];
+    const double e_num = fixed_to_double(EN, I.Fe);
+    const double t_num = trial ? dsum[0] : 0.0, t_den = trial ? dsum[1] : 0.0;
+    const double x_ov = pair ? dsum[2] : 0.0, x_hd = pair ? dsum[3] : 0.0, x_cr = pair ? dsum[4] : 0.0;
+    const double x_pt = pair ? dsum[5] : 0.0;
     const double nwd = u128_to_double(W) * 0x1p-32;
     const long long it = st->iter;
     // shift update (Booth, Thom, Alavi 2009)
