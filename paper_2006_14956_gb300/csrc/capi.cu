@@ -57,7 +57,7 @@ struct fciqmc_handle {
     // layout
     int bb = 0;
     int heavy_cap = 0;
-    int ring_cap = 4096;
+    int ring_cap = 4096;  // a power of two (the finalize kernel masks the iteration)
     // host-side history
     std::vector<fciqmc_iter_stats> hist;
     IterState hst{};

@@ -44,7 +44,7 @@ constexpr int TABBITS = 12;           // shared-memory hash table of the annihil
 constexpr int BIG_BLOCKS = 64;        // blocks of the large-bucket annihilation kernel
 constexpr int GBITS = 11;             // sub-hash groups per bucket in the annihilation sort
 constexpr int NGROUP = 1 << GBITS;
-constexpr int K5_THREADS = 1024;
+constexpr int K5_THREADS = 256;
 constexpr int KIDX = 2048;            // slots of the per-bucket list index (adaptive shift)
 
 struct HeavyChunk {  // a slice of the attempts of one determinant with many walkers

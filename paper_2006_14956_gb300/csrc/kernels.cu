@@ -1167,8 +1167,14 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
     __shared__ int s_err;
     __shared__ double s_r[K5_THREADS];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int nbk = 1 << I.bb;
+    const bool pair = I.partner > (int)blockIdx.x;  // the first replica reports the cross estimators
+    const bool trial = I.trial_bits != 0;
+    const bool tree = trial || pair;  // binary64 estimator sums need the whole block; otherwise warp 0 alone
+    if (!tree && warp != 0) return;
+    int e = 0;
     if (t == 0) {
-        int e = *(volatile int *)&st->err;
+        e = *(volatile int *)&st->err;
         // a replica commits its iteration only together with its partner: not
         // if the partner skipped it (a flag was up when its spawning began) or
         // failed in it
@@ -1178,13 +1184,15 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
             st->err = ERRB_PARTNER;
             e = ERRB_PARTNER;
         }
-        s_err = e;
     }
-    __syncthreads();
-    if (s_err) return;
-    const int nbk = 1 << I.bb;
-    const bool pair = I.partner > (int)blockIdx.x;  // the first replica reports the cross estimators
-    const bool trial = I.trial_bits != 0;
+    if (tree) {
+        if (t == 0) s_err = e;
+        __syncthreads();
+        e = s_err;
+    } else {
+        e = __shfl_sync(0xffffffffu, e, 0);
+    }
+    if (e) return;
     // Binary64 sums of the estimators that have them (trial numerator and
     // denominator; replica-pair terms), per tile of K5_THREADS buckets: one
     // value per thread into shared memory and a halving tree, so that every
@@ -1194,7 +1202,7 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
     double dsum[NF];
 #pragma unroll
     for (int f = 0; f < NF; f++) dsum[f] = 0.0;
-    if (trial || pair)
+    if (tree)
         for (int tile0 = 0; tile0 < nbk; tile0 += K5_THREADS) {
 #pragma unroll
             for (int f = 0; f < NF; f++) {
@@ -1214,20 +1222,29 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
                 __syncthreads();
             }
         }
-    // the exact totals the buckets added up: lane i reads and clears line i,
-    // the lines are summed word by word (each limb's total stays below 2^64)
-    static_assert(NSHARD == 32, "one line per lane");
     if (warp != 0) return;
-    u64 w[NACC];
-    u64 *line = I.acc + lane * ACC_STRIDE;
+    // the shift state, loaded now so that its latency overlaps the totals'
+    const long long it = st->iter, cnt0 = st->cnt, shift_start0 = st->shift_start, stop_iter = st->stop_iter;
+    const long long semi_built = st->semi_built, trial_built = st->trial_built;
+    const int vary0 = st->vary, par0 = st->parity;
+    const double S0 = st->S, e_den = st->e_den;
+    const u64 nwl_lo0 = st->nwl_lo, nwl_hi0 = st->nwl_hi;
+    // the exact totals the buckets added up: lane k sums word k of the NSHARD
+    // lines (each limb's total stays below 2^64) and clears it
+    u64 v = 0;
+    if (lane < NACC) {
+        u64 x[NSHARD];
 #pragma unroll
-    for (int k = 0; k < NACC; k++) {
-        w[k] = line[k];
-        line[k] = 0;
+        for (int j = 0; j < NSHARD; j++) x[j] = I.acc[j * ACC_STRIDE + lane];
+#pragma unroll
+        for (int j = 0; j < NSHARD; j++) {
+            I.acc[j * ACC_STRIDE + lane] = 0;
+            v += x[j];
+        }
     }
+    u64 w[NACC];
 #pragma unroll
-    for (int k = 0; k < NACC; k++)
-        for (int mm = 16; mm >= 1; mm >>= 1) w[k] += __shfl_xor_sync(0xffffffffu, w[k], mm);
+    for (int k = 0; k < NACC; k++) w[k] = __shfl_sync(0xffffffffu, v, k);
     if (lane != 0) return;
     const u128 W = (u128)limb_total(w + ACC_NW);
     const i128 A = limb_total(w + ACC_ANN), EN = limb_total(w + ACC_ENUM);
@@ -1238,41 +1255,46 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
     const double x_ov = pair ? dsum[2] : 0.0, x_hd = pair ? dsum[3] : 0.0, x_cr = pair ? dsum[4] : 0.0;
     const double x_pt = pair ? dsum[5] : 0.0;
     const double nwd = u128_to_double(W) * 0x1p-32;
-    const long long it = st->iter;
     // shift update (Booth, Thom, Alavi 2009)
-    if (!st->vary) {
+    int vary = vary0;
+    long long cnt = cnt0, shift_start = shift_start0;
+    double S = S0;
+    u64 nwl_lo = nwl_lo0, nwl_hi = nwl_hi0;
+    if (!vary) {
         if (nwd >= I.target) {
-            st->vary = 1;
-            st->shift_start = it;
-            st->nwl_lo = (u64)W; st->nwl_hi = (u64)(W >> 64);
-            st->cnt = 0;
+            vary = 1;
+            shift_start = it;
+            nwl_lo = (u64)W; nwl_hi = (u64)(W >> 64);
+            cnt = 0;
         }
-    } else if (++st->cnt == I.A) {
-        u128 L = ((u128)st->nwl_hi << 64) | st->nwl_lo;
-        double ratio = nwd / (u128_to_double(L) * 0x1p-32);
-        st->S = st->S - I.cz * fq_ln(ratio);
-        st->nwl_lo = (u64)W; st->nwl_hi = (u64)(W >> 64);
-        st->cnt = 0;
+    } else if (++cnt == I.A) {
+        const u128 L = ((u128)nwl_hi << 64) | nwl_lo;
+        const double ratio = nwd / (u128_to_double(L) * 0x1p-32);
+        S = S - I.cz * fq_ln(ratio);
+        nwl_lo = (u64)W; nwl_hi = (u64)(W >> 64);
+        cnt = 0;
     }
-    if (!(st->S == st->S) || !(nwd == nwd)) st->err |= ERRB_NUMERIC;
-    fciqmc_iter_stats &R = I.ring[it % I.ring_cap];
-    R.iteration = it; R.nw = nwd; R.shift = st->S; R.e_num = e_num; R.e_den = st->e_den;
+    int flags = 0;
+    if (!(S == S) || !(nwd == nwd)) flags |= ERRB_NUMERIC;
+    fciqmc_iter_stats &R = I.ring[it & (long long)(I.ring_cap - 1)];  // ring_cap is a power of two
+    R.iteration = it; R.nw = nwd; R.shift = S; R.e_num = e_num; R.e_den = e_den;
     R.ndet = nd; R.attempts = at; R.spawns = sps; R.rejected = rj;
-    R.annihilated = i128_to_double(A) * 0x1p-32; R.vary = st->vary; R.pad0 = 0;
+    R.annihilated = i128_to_double(A) * 0x1p-32; R.vary = vary; R.pad0 = 0;
     R.trial_num = t_num; R.trial_den = t_den;
     R.x_overlap = x_ov;
     R.x_var_num = pair ? x_hd - x_cr / (2.0 * I.tau) : 0.0;
     R.x_pt2 = pair ? x_pt / (I.tau * I.tau) : 0.0;
+    st->vary = vary; st->shift_start = shift_start; st->cnt = cnt; st->S = S;
+    st->nwl_lo = nwl_lo; st->nwl_hi = nwl_hi;
     st->iter = it + 1;
-    st->parity ^= 1;
+    st->parity = par0 ^ 1;
     st->heavy_n = 0;
     st->big_n = 0;
     st->new_n = 0;
-    if (I.semi_size > 0 && !st->semi_built && st->vary && it + 1 == st->shift_start + I.semi_start)
-        st->err |= ERRB_PAUSE_SEMI;
-    if (I.trial_size > 0 && !st->trial_built && st->vary && it + 1 == st->shift_start + I.trial_start)
-        st->err |= ERRB_PAUSE_TRIAL;
-    if (it + 1 >= st->stop_iter) st->err |= ERRB_STOP;
+    if (I.semi_size > 0 && !semi_built && vary && it + 1 == shift_start + I.semi_start) flags |= ERRB_PAUSE_SEMI;
+    if (I.trial_size > 0 && !trial_built && vary && it + 1 == shift_start + I.trial_start) flags |= ERRB_PAUSE_TRIAL;
+    if (it + 1 >= stop_iter) flags |= ERRB_STOP;
+    if (flags) st->err |= flags;
 }
 
 // ------------------------------------------------------------------ growth and import

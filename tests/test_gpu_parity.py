@@ -200,6 +200,34 @@ def test_checkpoint_restart_continues_identically():
     assert_states_equal(s2, o.export())
 
 
+def test_import_rejects_bad_input_and_keeps_the_run_usable():
+    """A wrong electron count or hundreds of copies of one key (more than a
+    bucket holds at any bucket count) are refused with INVALID_ARG before
+    anything changes; a valid import afterwards continues as a fresh handle."""
+    fq = _fq()
+    sysd, params = workloads.small_abinitio(8, 3, 3, seed=5), dict(DAMP, tau=0.005, target_walkers=3000,
+                                                                    initiator_threshold=3.0, seed=11)
+    g1 = fq.fciqmc_create(sysd, params)
+    fq.fciqmc_step(g1, 100)
+    st, sh = fq.fciqmc_export_state(g1), fq.fciqmc_export_shift(g1)
+    args = (sh["iteration"], sh["S"], sh["vary"], sh["shift_start"], sh["cnt"], sh["nw_last"])
+    a0 = int(st["alpha"][3])
+    free = next(p for p in range(8) if not (a0 >> p) & 1)
+    bad_a = st["alpha"].copy()
+    bad_a[3] = np.uint64(a0 | (1 << free))  # one alpha electron too many
+    for a, b, c in [(bad_a, st["beta"], st["c"]),
+                    (np.repeat(st["alpha"][:1], 600), np.repeat(st["beta"][:1], 600), np.ones(600))]:
+        with pytest.raises(fq.FciqmcError) as e:
+            fq.fciqmc_import_state(g1, a, b, c, *args)
+        assert e.value.code == fq.FCIQMC_ERR_INVALID_ARG
+    fq.fciqmc_import_state(g1, st["alpha"], st["beta"], st["c"], *args)
+    g2 = fq.fciqmc_create(sysd, params)
+    fq.fciqmc_import_state(g2, st["alpha"], st["beta"], st["c"], *args)
+    fq.fciqmc_step(g1, 30)
+    fq.fciqmc_step(g2, 30)
+    assert_states_equal(fq.fciqmc_export_state(g1), fq.fciqmc_export_state(g2))
+
+
 def test_energy_within_3sigma_of_exact_diagonalisation():
     """8-site Hubbard ring, U=4, plain FCIQMC (n_a = 0), 2000 iterations at
     1e4 walkers: E_proj within 3 sigma of the exact ground state."""
