@@ -365,7 +365,9 @@ def main():
             tr = json.load(f)
         import hashlib
         src = open(os.path.join(ROOT, "paper_2006_14956_gb300", "csrc", "kernels.cu"), "rb").read()
-        if tr.get("kernels_sha256") == hashlib.sha256(src).hexdigest():
+        # counters apply only to the kernels and the workload they were captured on
+        if (tr.get("kernels_sha256") == hashlib.sha256(src).hexdigest() and
+                tr.get("bench_args") == {"workload": args.workload, "generator": args.generator}):
             traffic = tr["dram_bytes_per_launch"]
     except Exception:
         pass
