@@ -395,9 +395,8 @@ def main():
     e2e_phases = {"create": t1 - t0, "import": t2 - t1, "steps": t3 - t2, "export_energy": t0 + e2e_el - t3}
     st2 = fq.fciqmc_iter_stats_get(h2)
     e2e_att = float(np.sum(st2["attempts"][-E2E_STEPS:]))
-    # integrals, the checkpoint's keys and amplitudes, and the import's slot index (8 B per determinant)
-    h2d = (sysd["h1"].nbytes + sysd["eri"].nbytes + host_state["alpha"].nbytes * 2 + host_state["c"].nbytes +
-           8 * host_state["c"].size)
+    # integrals and the checkpoint's keys and amplitudes
+    h2d = sysd["h1"].nbytes + sysd["eri"].nbytes + host_state["alpha"].nbytes * 2 + host_state["c"].nbytes
     d2h = sum(v.nbytes for v in out_state.values()) + E2E_STEPS * ctypes.sizeof(fq.fciqmc_iter_stats)
     del h2
 

@@ -1359,38 +1359,52 @@ int fciqmc_export_shift(fciqmc_handle *h, int64_t *iteration, double *S, int32_t
     return FCIQMC_OK;
 }
 
-int fciqmc_import_state(fciqmc_handle *h, int64_t n, const uint64_t *alpha, const uint64_t *beta, const double *c,
-                        int64_t iteration, double S, int32_t vary, int64_t shift_start, int64_t cnt, uint64_t nw_last_hi,
-                        uint64_t nw_last_lo)
+// import on the device: the compact input in `scr` ((n + 1) keys, amplitudes
+// and four flag words), checked, counted per bucket to choose the bucket
+// count, and placed; the slots are listed in newdet for the H_ii kernel
+static int import_device(fciqmc_handle *h, int64_t n, const uint64_t *alpha, const uint64_t *beta, const double *c,
+                         u64 normask, unsigned char *scr, int64_t *nt_out)
 {
-    if (!h || n < 0 || (n > 0 && (!alpha || !beta || !c)) || iteration < 0) return FCIQMC_ERR_INVALID_ARG;
-    const u64 normask = h->norb >= 64 ? ~0ULL : ((1ULL << h->norb) - 1);
-    // one pass: checks, the reference's presence, the bucket hash of every key
-    // (the reference, when absent, is appended as entry n with C = 0)
-    std::vector<u64> hash((size_t)n + 1);
-    bool has_ref = false;
-    for (int64_t i = 0; i < n; i++) {
-        const u64 a = alpha[i], b = beta[i];
-        if (__builtin_popcountll(a) != h->na || __builtin_popcountll(b) != h->nb || ((a | b) & ~normask) ||
-            !std::isfinite(c[i]))
-            return fail(h, FCIQMC_ERR_INVALID_ARG, "imported determinant with wrong electron count or bad amplitude");
-        has_ref |= a == h->ref_a && b == h->ref_b;
-        hash[i] = det_hash_host(a, b);
+    cudaStream_t s = h->stream;
+    u64 *da = (u64 *)scr, *db = da + (n + 1);
+    double *dc = (double *)(db + (n + 1));
+    int *dflag = (int *)(dc + (n + 1));
+    CUDA_TRY(h, cudaMemsetAsync(dflag, 0, 4 * sizeof(int), s));
+    if (n > 0) {
+        CUDA_TRY(h, cudaMemcpyAsync(da, alpha, (size_t)n * sizeof(u64), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(h, cudaMemcpyAsync(db, beta, (size_t)n * sizeof(u64), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(h, cudaMemcpyAsync(dc, c, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s));
     }
-    const int64_t nt = n + (has_ref ? 0 : 1);
-    if (!has_ref) hash[n] = det_hash_host(h->ref_a, h->ref_b);
-    auto key_a = [&](int64_t i) { return i < n ? (u64)alpha[i] : h->ref_a; };
-    auto key_b = [&](int64_t i) { return i < n ? (u64)beta[i] : h->ref_b; };
-    int rc = read_state(h);
+    CUDA_TRY(h, launch_import_check(da, db, dc, n, h->na, h->nb, normask, h->ref_a, h->ref_b, dflag, s));
+    int flags = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&flags, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    if (flags & 1) return fail(h, FCIQMC_ERR_INVALID_ARG, "imported determinant with wrong electron count or bad amplitude");
+    int64_t nt = n;
+    const u64 ra = h->ref_a, rb = h->ref_b;
+    const double zero = 0.0;
+    if (!(flags & 2)) {  // the reference, when absent, is appended as entry n with C = 0
+        CUDA_TRY(h, cudaMemcpyAsync(da + n, &ra, sizeof(u64), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(h, cudaMemcpyAsync(db + n, &rb, sizeof(u64), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(h, cudaMemcpyAsync(dc + n, &zero, sizeof(double), cudaMemcpyHostToDevice, s));
+        nt = n + 1;
+    }
+    int rc = read_state(h);  // also completes the copies above
     if (rc) return rc;
     // the fewest buckets (at least the current number) that hold every
     // bucket's determinants within half the main capacity; one allocation
     int bb = h->bb;
     for (;; bb++) {
-        std::vector<int> cnt_b((size_t)1 << bb, 0);
-        bool over = false;
-        for (int64_t i = 0; i < nt && !over; i++)
-            if (++cnt_b[bb ? (size_t)(hash[i] >> (64 - bb)) : 0] > CAP_M / 2) over = true;
+        int *cntb = (int *)dev_alloc(h, ((size_t)1 << bb) * sizeof(int));
+        if (!cntb) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (import counts)");
+        int over = 0;
+        cudaError_t e = cudaMemsetAsync(cntb, 0, ((size_t)1 << bb) * sizeof(int), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(dflag + 1, 0, sizeof(int), s);
+        if (e == cudaSuccess) e = launch_import_count(da, db, nt, bb, cntb, dflag + 1, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&over, dflag + 1, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        dev_free(h, cntb);
+        if (e != cudaSuccess) return fail(h, FCIQMC_ERR_CUDA, std::string("import: ") + cudaGetErrorString(e));
         if (!over) break;
         if (bb >= 24)  // distinct keys never crowd one bucket at 2^24 buckets
             return fail(h, FCIQMC_ERR_INVALID_ARG, "imported keys crowd one bucket (duplicate determinants?)");
@@ -1403,66 +1417,98 @@ int fciqmc_import_state(fciqmc_handle *h, int64_t n, const uint64_t *alpha, cons
         h->hi = nI;
         h->bb = nI.bb;
     }
-    // slot of every determinant: its bucket, in input order
+    const int par = 0;
+    CUDA_TRY(h, cudaMemsetAsync(h->hi.cnt[par], 0, ((size_t)1 << h->bb) * sizeof(int), s));
+    CUDA_TRY(h, launch_import_place(da, db, dc, nt, h->bb, ra, rb, h->hi.cnt[par], h->hi.key[par], h->hi.c[par],
+                                    h->hi.fl[par], h->hi.newdet, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    *nt_out = nt;
+    return FCIQMC_OK;
+}
+
+// import on the host (when no device scratch can be had): the same checks and
+// bucket count, the padded layout built here and copied
+static int import_host(fciqmc_handle *h, int64_t n, const uint64_t *alpha, const uint64_t *beta, const double *c,
+                       u64 normask)
+{
+    std::vector<u64> hash((size_t)n + 1);
+    bool has_ref = false;
+    for (int64_t i = 0; i < n; i++) {
+        const u64 a = alpha[i], b = beta[i];
+        if (__builtin_popcountll(a) != h->na || __builtin_popcountll(b) != h->nb || ((a | b) & ~normask) ||
+            !std::isfinite(c[i]))
+            return fail(h, FCIQMC_ERR_INVALID_ARG, "imported determinant with wrong electron count or bad amplitude");
+        has_ref |= a == h->ref_a && b == h->ref_b;
+        hash[i] = det_hash_host(a, b);
+    }
+    const int64_t nt = n + (has_ref ? 0 : 1);  // the reference, when absent, as entry n with C = 0
+    if (!has_ref) hash[n] = det_hash_host(h->ref_a, h->ref_b);
+    auto key_a = [&](int64_t i) { return i < n ? (u64)alpha[i] : h->ref_a; };
+    auto key_b = [&](int64_t i) { return i < n ? (u64)beta[i] : h->ref_b; };
+    int rc = read_state(h);
+    if (rc) return rc;
+    int bb = h->bb;
+    for (;; bb++) {
+        std::vector<int> cnt_b((size_t)1 << bb, 0);
+        bool over = false;
+        for (int64_t i = 0; i < nt && !over; i++)
+            if (++cnt_b[bb ? (size_t)(hash[i] >> (64 - bb)) : 0] > CAP_M / 2) over = true;
+        if (!over) break;
+        if (bb >= 24)
+            return fail(h, FCIQMC_ERR_INVALID_ARG, "imported keys crowd one bucket (duplicate determinants?)");
+    }
+    if (bb != h->bb) {
+        DevInst nI = h->hi;
+        rc = alloc_layout(h, nI, bb);
+        if (rc) return fail(h, rc, "out of device memory");
+        free_layout(h, h->hi);
+        h->hi = nI;
+        h->bb = nI.bb;
+    }
     const size_t nbk = (size_t)1 << h->bb, nm = nbk * CAP_M;
     std::vector<int> cnt_b(nbk, 0);
-    std::vector<u64> slot((size_t)nt);
+    std::vector<ulonglong2> k(nm);
+    std::vector<double> cc(nm, 0.0);
+    std::vector<uint8_t> ff(nm, 0);
     for (int64_t i = 0; i < nt; i++) {
         const size_t b = h->bb ? (size_t)(hash[i] >> (64 - h->bb)) : 0;
-        slot[i] = b * CAP_M + (size_t)cnt_b[b]++;
+        const size_t o = b * CAP_M + (size_t)cnt_b[b]++;
+        k[o].x = key_a(i);
+        k[o].y = key_b(i);
+        cc[o] = i < n ? c[i] : 0.0;
     }
     const int par = 0;
-    // the compact input goes to the device and a kernel scatters it into the
-    // bucket layout (transient scratch from the run's allocator); where that
-    // scratch cannot be had, the padded layout is built on the host
-    unsigned char *scr = (unsigned char *)dev_alloc(h, (size_t)nt * 32);
-    if (scr) {
-        u64 *da = (u64 *)scr, *db = da + nt, *ds = db + nt;
-        double *dc = (double *)(ds + nt);
-        const u64 ra = h->ref_a, rb = h->ref_b;
-        const double zero = 0.0;
-        cudaError_t e = cudaSuccess;
-        if (n > 0) {
-            e = cudaMemcpyAsync(da, alpha, (size_t)n * sizeof(u64), cudaMemcpyHostToDevice, h->stream);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(db, beta, (size_t)n * sizeof(u64), cudaMemcpyHostToDevice, h->stream);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(dc, c, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
-        }
-        if (e == cudaSuccess && !has_ref) {
-            e = cudaMemcpyAsync(da + n, &ra, sizeof(u64), cudaMemcpyHostToDevice, h->stream);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(db + n, &rb, sizeof(u64), cudaMemcpyHostToDevice, h->stream);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(dc + n, &zero, sizeof(double), cudaMemcpyHostToDevice, h->stream);
-        }
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(ds, slot.data(), (size_t)nt * sizeof(u64), cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->hi.c[par], 0, nm * sizeof(double), h->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->hi.fl[par], 0, nm, h->stream);
-        if (e == cudaSuccess) e = launch_import_scatter(da, db, dc, ds, nt, h->hi.key[par], h->hi.c[par], h->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(h->hi.cnt[par], cnt_b.data(), nbk * sizeof(int), cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-        dev_free(h, scr);
-        if (e != cudaSuccess) return fail(h, FCIQMC_ERR_CUDA, std::string("import: ") + cudaGetErrorString(e));
-    } else {
-        std::vector<ulonglong2> k(nm);
-        std::vector<double> cc(nm, 0.0);
-        std::vector<uint8_t> ff(nm, 0);
-        for (int64_t i = 0; i < nt; i++) {
-            k[slot[i]].x = key_a(i);
-            k[slot[i]].y = key_b(i);
-            cc[slot[i]] = i < n ? c[i] : 0.0;
-        }
-        CUDA_TRY(h, cudaMemcpy(h->hi.key[par], k.data(), nm * sizeof(ulonglong2), cudaMemcpyHostToDevice));
-        CUDA_TRY(h, cudaMemcpy(h->hi.c[par], cc.data(), nm * sizeof(double), cudaMemcpyHostToDevice));
-        CUDA_TRY(h, cudaMemcpy(h->hi.fl[par], ff.data(), nm, cudaMemcpyHostToDevice));
-        CUDA_TRY(h, cudaMemcpy(h->hi.cnt[par], cnt_b.data(), nbk * sizeof(int), cudaMemcpyHostToDevice));
-    }
+    CUDA_TRY(h, cudaMemcpy(h->hi.key[par], k.data(), nm * sizeof(ulonglong2), cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(h->hi.c[par], cc.data(), nm * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(h->hi.fl[par], ff.data(), nm, cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(h->hi.cnt[par], cnt_b.data(), nbk * sizeof(int), cudaMemcpyHostToDevice));
+    return FCIQMC_OK;
+}
+
+int fciqmc_import_state(fciqmc_handle *h, int64_t n, const uint64_t *alpha, const uint64_t *beta, const double *c,
+                        int64_t iteration, double S, int32_t vary, int64_t shift_start, int64_t cnt, uint64_t nw_last_hi,
+                        uint64_t nw_last_lo)
+{
+    if (!h || n < 0 || (n > 0 && (!alpha || !beta || !c)) || iteration < 0) return FCIQMC_ERR_INVALID_ARG;
+    const u64 normask = h->norb >= 64 ? ~0ULL : ((1ULL << h->norb) - 1);
+    const int par = 0;
+    // on the device (transient scratch from the run's allocator); where that
+    // scratch cannot be had, on the host
+    int64_t nt = 0;
+    unsigned char *scr = (unsigned char *)dev_alloc(h, ((size_t)n + 1) * 24 + 4 * sizeof(int));
+    const bool listed = scr != nullptr;  // H_ii from the list of placed slots
+    int rc = listed ? import_device(h, n, alpha, beta, c, normask, scr, &nt) : import_host(h, n, alpha, beta, c, normask);
+    if (scr) dev_free(h, scr);
+    if (rc) return rc;
+    const size_t nbk = (size_t)1 << h->bb;
     CUDA_TRY(h, cudaMemset(h->hi.scnt_i, 0, nbk * sizeof(int)));
     CUDA_TRY(h, cudaMemset(h->hi.scnt_n, 0, nbk * sizeof(int)));
     rc = ensure_side(h);
     if (rc) return rc;
     rc = upload_inst(h);
     if (rc) return rc;
-    launch_diag(h->dinst, par, (int)nbk, h->stream);
+    if (listed) launch_diag_list(h->dinst, par, h->hi.newdet, (int)nt, h->stream);
+    else launch_diag(h->dinst, par, (int)nbk, h->stream);
     if (h->p.adaptive_shift) launch_build_kidx(h->dinst, par, (int)nbk, h->stream);
     CUDA_TRY(h, cudaGetLastError());
     memset(&h->hst, 0, sizeof(IterState));

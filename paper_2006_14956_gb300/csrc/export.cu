@@ -1,5 +1,8 @@
 // export.cu -- moving the walker list between the host and the bucket layout.
-// Import: the compact input is scattered into its slots by one kernel.
+// Import: the compact input is checked, counted per bucket (to choose the
+// bucket count) and placed on the device, each determinant into the next free
+// slot of its bucket (order inside a bucket affects no result: every draw is
+// keyed and every sum exact), and its slot listed for the H_ii kernel.
 // Export, in (alpha, beta) order: the occupied slots of every bucket are compacted,
 // sorted by a least-significant-digit radix sort over the orbital bits in use
 // (8-bit digits, beta word first, each pass stable), and C, H_ii - E_ref and
@@ -7,7 +10,7 @@
 // to the host.
 #include <cuda_runtime.h>
 
-#include "fq_internal.h"
+#include "fq_device.cuh"
 
 namespace fq {
 
@@ -162,23 +165,74 @@ __global__ void k_export_gather(const u64 *__restrict__ idx, long long n, const 
     }
 }
 
-// import: determinant i (compact input) goes to bucket-layout slot slot[i]
-__global__ void k_import_scatter(const u64 *__restrict__ a, const u64 *__restrict__ b, const double *__restrict__ c,
-                                 const u64 *__restrict__ slot, long long n, ulonglong2 *key, double *oc)
+// import, step 1: flags bit 0 = an entry with a wrong electron count, an
+// orbital beyond norb or a non-finite amplitude; bit 1 = the reference present
+__global__ void k_import_check(const u64 *__restrict__ a, const u64 *__restrict__ b, const double *__restrict__ c,
+                               long long n, int na, int nb, u64 normask, u64 ra, u64 rb, int *flags)
+{
+    int f = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const u64 x = a[i], y = b[i];
+        const bool finite = (dbits(c[i]) & 0x7ff0000000000000ULL) != 0x7ff0000000000000ULL;
+        if (__popcll(x) != na || __popcll(y) != nb || ((x | y) & ~normask) || !finite) f |= 1;
+        if (x == ra && y == rb) f |= 2;
+    }
+    f = __reduce_or_sync(0xffffffffu, f);
+    if ((threadIdx.x & 31) == 0 && f) atomicOr(flags, f);
+}
+
+// import, step 2: bucket counts at 2^bb buckets; *over = 1 once a bucket
+// holds more than half its capacity
+__global__ void k_import_count(const u64 *__restrict__ a, const u64 *__restrict__ b, long long n, int bb, int *cnt,
+                               int *over)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const u64 s = slot[i];
-        key[s] = make_ulonglong2(a[i], b[i]);
-        oc[s] = c[i];
+        const int o = atomicAdd(&cnt[bucket_of(det_hash(a[i], b[i]), bb)], 1);
+        if (o == CAP_M / 2) atomicOr(over, 1);
     }
 }
 
-cudaError_t launch_import_scatter(const u64 *a, const u64 *b, const double *c, const u64 *slot, long long n,
-                                  ulonglong2 *key, double *oc, cudaStream_t s)
+// import, step 3: each determinant into the next free slot of its bucket
+// (fill = the zeroed counts of the list), flags (the reference's), and its
+// slot into list[i]
+__global__ void k_import_place(const u64 *__restrict__ a, const u64 *__restrict__ b, const double *__restrict__ c,
+                               long long n, int bb, u64 ra, u64 rb, int *fill, ulonglong2 *key, double *oc,
+                               uint8_t *ofl, unsigned *list)
 {
-    if (n <= 0) return cudaSuccess;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const u64 x = a[i], y = b[i];
+        const int bk = bucket_of(det_hash(x, y), bb);
+        const size_t s = (size_t)bk * CAP_M + (size_t)atomicAdd(&fill[bk], 1);
+        key[s] = make_ulonglong2(x, y);
+        oc[s] = c[i];
+        ofl[s] = (uint8_t)((x == ra && y == rb) ? DFLAG_REF : 0);
+        list[i] = (unsigned)s;
+    }
+}
+
+static unsigned grid_for(long long n)
+{
     const long long g = (n + 255) / 256;
-    k_import_scatter<<<(unsigned)(g < 4096 ? g : 4096), 256, 0, s>>>(a, b, c, slot, n, key, oc);
+    return (unsigned)(g < 1 ? 1 : (g < 4096 ? g : 4096));
+}
+
+cudaError_t launch_import_check(const u64 *a, const u64 *b, const double *c, long long n, int na, int nb, u64 normask,
+                                u64 ra, u64 rb, int *flags, cudaStream_t s)
+{
+    if (n > 0) k_import_check<<<grid_for(n), 256, 0, s>>>(a, b, c, n, na, nb, normask, ra, rb, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_import_count(const u64 *a, const u64 *b, long long n, int bb, int *cnt, int *over, cudaStream_t s)
+{
+    k_import_count<<<grid_for(n), 256, 0, s>>>(a, b, n, bb, cnt, over);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_import_place(const u64 *a, const u64 *b, const double *c, long long n, int bb, u64 ra, u64 rb,
+                                int *fill, ulonglong2 *key, double *oc, uint8_t *ofl, unsigned *list, cudaStream_t s)
+{
+    k_import_place<<<grid_for(n), 256, 0, s>>>(a, b, c, n, bb, ra, rb, fill, key, oc, ofl, list);
     return cudaGetLastError();
 }
 

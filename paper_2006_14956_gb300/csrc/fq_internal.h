@@ -231,6 +231,12 @@ cudaError_t launch_replica_cross(const DevInst *dinst, int n_inst, int max_bucke
 cudaError_t replica_kernel_init();
 void launch_rebucket(const DevInst *src, const DevInst *dst, int nb_src, int parity, cudaStream_t s);
 void launch_diag(const DevInst *dinst, int parity, int nb, cudaStream_t s);
+void launch_diag_list(const DevInst *dinst, int par, const unsigned *list, int nn, cudaStream_t s);
+cudaError_t launch_import_check(const u64 *a, const u64 *b, const double *c, long long n, int na, int nb, u64 normask,
+                                u64 ra, u64 rb, int *flags, cudaStream_t s);
+cudaError_t launch_import_count(const u64 *a, const u64 *b, long long n, int bb, int *cnt, int *over, cudaStream_t s);
+cudaError_t launch_import_place(const u64 *a, const u64 *b, const double *c, long long n, int bb, u64 ra, u64 rb,
+                                int *fill, ulonglong2 *key, double *oc, uint8_t *ofl, unsigned *list, cudaStream_t s);
 void launch_abs_hist(const DevInst *dinst, int par, int nb, int shift, u64 prefix, unsigned *hist, cudaStream_t s);
 void launch_abs_collect(const DevInst *dinst, int par, int nb, u64 thr, ulonglong2 *keys, u64 *mags, int *n, int cap,
                         cudaStream_t s);
@@ -252,8 +258,6 @@ void set_launch_geometry(int spawn_bps, int heavy_bps, int anni_bps);
 void get_launch_geometry(int *spawn_bps, int *heavy_bps, int *anni_bps);
 cudaError_t ref_abs_sum(const DevInst *dinst, double *dpartial, double *out, cudaStream_t s);
 size_t export_scratch_bytes(long long n);
-cudaError_t launch_import_scatter(const u64 *a, const u64 *b, const double *c, const u64 *slot, long long n,
-                                  ulonglong2 *key, double *oc, cudaStream_t s);
 cudaError_t export_sorted(const ulonglong2 *key, const double *c, const double *hd, const uint8_t *fl, const int *cnt,
                           const long long *off, int nbk, long long n, int norb, void *scratch, const u64 **oa,
                           const u64 **ob, const double **oc, const double **ohd, const int32_t **ofl, cudaStream_t s);

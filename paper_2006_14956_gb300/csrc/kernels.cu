@@ -1514,81 +1514,103 @@ void launch_finalize(const DevInst *dinst, int n_inst, cudaStream_t s)
 // there, so a term costs two shared loads and one table load; each lane group
 // sums its terms exactly and reduces over its eight lanes.
 constexpr int ND_PAIRS = 2080;  // n (n + 1) / 2 terms for up to 64 electrons
+
+// H_ii - E_ref of the determinants at the slots list[0 .. nn) of list `np`
+// (whole block; every thread calls it)
+__device__ void diag_list(const DevInst &I, const unsigned *__restrict__ list, int nn, int np,
+                          unsigned short *s_term, unsigned char (*s_orb)[4][64])
+{
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarp = (int)((gridDim.x * blockDim.x) >> 5);
+    const ulonglong2 *nkey = I.key[np];
+    double *nhd = I.hd[np];
+    const int n = I.n, na = I.na, N = I.norb, T = n + n * (n - 1) / 2;
+    if (n > 64) {  // beyond the table: the generic warp sum
+        for (int q = 2 * gw; q < nn; q += 2 * nwarp) {
+            const unsigned d0 = list[q], d1 = q + 1 < nn ? list[q + 1] : d0;
+            const ulonglong2 k0 = nkey[d0], k1 = nkey[d1];
+            const u64 ka[2] = {k0.x, k1.x}, kb[2] = {k0.y, k1.y};
+            double hdv[2];
+            diag_exact_warp_multi<2>(I, ka, kb, hdv);
+            if (lane == 0) {
+                nhd[d0] = hdv[0];
+                if (q + 1 < nn) nhd[d1] = hdv[1];
+            }
+        }
+        return;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        if (t < n) { s_term[t] = (unsigned short)(t | (255 << 8)); continue; }
+        const int q = t - n;
+        int c = 1;
+        while ((c + 1) * c / 2 <= q) c++;
+        s_term[t] = (unsigned short)((q - c * (c - 1) / 2) | (c << 8));
+    }
+    __syncthreads();
+    // four determinants per warp, eight lanes each: lane group g takes
+    // determinant q + g (a short last round repeats determinant q and
+    // stores nothing for it), its lanes the terms sl, sl + 8, ...
+    const int g = lane >> 3, sl = lane & 7;
+    const i128 xref = (i128)(((u128)I.xref_hi << 64) | (u128)I.xref_lo);
+    for (int q = 4 * gw; q < nn; q += 4 * nwarp) {
+        const unsigned d = list[q + g < nn ? q + g : q];
+        const ulonglong2 key = nkey[d];
+        for (int e = sl; e < n; e += 8)
+            s_orb[wl][g][e] = (unsigned char)(e < na ? nth_set(key.x, e) : nth_set(key.y, e - na));
+        __syncwarp();
+        i128 part = 0;
+        for (int t0 = sl; t0 < T; t0 += 32) {
+            ulonglong2 v[4];
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const int t = t0 + 8 * r;
+                v[r] = make_ulonglong2(0, 0);
+                if (t < T) {
+                    const unsigned tm = s_term[t];
+                    const int e1 = (int)(tm & 0xffu), e2 = (int)(tm >> 8);
+                    const int p1 = s_orb[wl][g][e1];
+                    if (e2 == 255) v[r] = __ldg(I.hfx + p1);
+                    else v[r] = __ldg((((e1 < na) == (e2 < na)) ? I.JKfx : I.Jfx) + p1 * N + s_orb[wl][g][e2]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 4; r++) part += (i128)(((u128)v[r].y << 64) | (u128)v[r].x);
+        }
+        for (int m = 4; m >= 1; m >>= 1) part += shfl_xor_i128(part, m);
+        if (sl == 0 && q + g < nn) nhd[d] = fixed_to_double(part - xref, I.F);
+        __syncwarp();
+    }
+}
+
 __global__ void __launch_bounds__(256) k_new_diag(const DevInst *__restrict__ insts, int n_inst)
 {
     __shared__ unsigned short s_term[ND_PAIRS];   // e1 | e2 << 8, e2 = 255 for h_pp
     __shared__ unsigned char s_orb[8][4][64];
-    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarp = (int)((gridDim.x * blockDim.x) >> 5);
     for (int ii = 0; ii < n_inst; ii++) {
         const DevInst &I = insts[ii];
         if (*(volatile int *)&I.st->err) continue;
-        const int nn = I.st->new_n, np = I.st->parity ^ 1;
-        const ulonglong2 *nkey = I.key[np];
-        double *nhd = I.hd[np];
-        const int n = I.n, na = I.na, N = I.norb, T = n + n * (n - 1) / 2;
-        if (n > 64) {  // beyond the table: the generic warp sum
-            for (int q = 2 * gw; q < nn; q += 2 * nwarp) {
-                const unsigned d0 = I.newdet[q], d1 = q + 1 < nn ? I.newdet[q + 1] : d0;
-                const ulonglong2 k0 = nkey[d0], k1 = nkey[d1];
-                const u64 ka[2] = {k0.x, k1.x}, kb[2] = {k0.y, k1.y};
-                double hdv[2];
-                diag_exact_warp_multi<2>(I, ka, kb, hdv);
-                if (lane == 0) {
-                    nhd[d0] = hdv[0];
-                    if (q + 1 < nn) nhd[d1] = hdv[1];
-                }
-            }
-            continue;
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < T; t += blockDim.x) {
-            if (t < n) { s_term[t] = (unsigned short)(t | (255 << 8)); continue; }
-            const int q = t - n;
-            int c = 1;
-            while ((c + 1) * c / 2 <= q) c++;
-            s_term[t] = (unsigned short)((q - c * (c - 1) / 2) | (c << 8));
-        }
-        __syncthreads();
-        // four determinants per warp, eight lanes each: lane group g takes
-        // determinant q + g (a short last round repeats determinant q and
-        // stores nothing for it), its lanes the terms sl, sl + 8, ...
-        const int g = lane >> 3, sl = lane & 7;
-        const i128 xref = (i128)(((u128)I.xref_hi << 64) | (u128)I.xref_lo);
-        for (int q = 4 * gw; q < nn; q += 4 * nwarp) {
-            const unsigned d = I.newdet[q + g < nn ? q + g : q];
-            const ulonglong2 key = nkey[d];
-            for (int e = sl; e < n; e += 8)
-                s_orb[wl][g][e] = (unsigned char)(e < na ? nth_set(key.x, e) : nth_set(key.y, e - na));
-            __syncwarp();
-            i128 part = 0;
-            for (int t0 = sl; t0 < T; t0 += 32) {
-                ulonglong2 v[4];
-#pragma unroll
-                for (int r = 0; r < 4; r++) {
-                    const int t = t0 + 8 * r;
-                    v[r] = make_ulonglong2(0, 0);
-                    if (t < T) {
-                        const unsigned tm = s_term[t];
-                        const int e1 = (int)(tm & 0xffu), e2 = (int)(tm >> 8);
-                        const int p1 = s_orb[wl][g][e1];
-                        if (e2 == 255) v[r] = __ldg(I.hfx + p1);
-                        else v[r] = __ldg((((e1 < na) == (e2 < na)) ? I.JKfx : I.Jfx) + p1 * N + s_orb[wl][g][e2]);
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < 4; r++) part += (i128)(((u128)v[r].y << 64) | (u128)v[r].x);
-            }
-            for (int m = 4; m >= 1; m >>= 1) part += shfl_xor_i128(part, m);
-            if (sl == 0 && q + g < nn) nhd[d] = fixed_to_double(part - xref, I.F);
-            __syncwarp();
-        }
+        diag_list(I, I.newdet, I.st->new_n, I.st->parity ^ 1, s_term, s_orb);
     }
+}
+
+// H_ii - E_ref of every determinant of list `par`, given by its slots (import)
+__global__ void __launch_bounds__(256) k_diag_list(const DevInst *__restrict__ I, int par, const unsigned *list, int nn)
+{
+    __shared__ unsigned short s_term[ND_PAIRS];
+    __shared__ unsigned char s_orb[8][4][64];
+    diag_list(*I, list, nn, par, s_term, s_orb);
+}
+
+void launch_diag_list(const DevInst *dinst, int par, const unsigned *list, int nn, cudaStream_t s)
+{
+    if (nn > 0) k_diag_list<<<num_sms() * 3, 256, 0, s>>>(dinst, par, list, nn);
 }
 
 void launch_new_diag(const DevInst *dinst, int n_inst, cudaStream_t s)
 {
-    k_new_diag<<<num_sms() * 8, 256, 0, s>>>(dinst, n_inst);
+    // one resident wave (3 blocks per SM at 80 registers): fewer blocks repeat the term-table set-up
+    k_new_diag<<<num_sms() * 3, 256, 0, s>>>(dinst, n_inst);
 }
 
 void launch_rebucket(const DevInst *src, const DevInst *dst, int nb_src, int parity, cudaStream_t s)

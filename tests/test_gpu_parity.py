@@ -156,10 +156,11 @@ def test_capacity_growth_is_bit_identical():
     ("abinitio_24_orbitals", workloads.config_abinitio_24()[0],
      dict(workloads.config_abinitio_24()[1], tau=2e-4, target_walkers=2e4, max_dets=5000000)),
 ])
-def test_export_device_sort_and_host_fallback_agree(name, sysd, params):
+def test_export_import_device_and_host_fallback_agree(name, sysd, params):
     """The export sorts on the device (compaction, radix sort over the
-    orbital bits, gather); a run whose memory cap leaves no room for that
-    scratch sorts on the host.  Both orders must be the oracle's."""
+    orbital bits, gather) and the import places on the device; a run whose
+    memory cap leaves no room for their scratch does both on the host.  Both
+    must give the oracle's list, before and after further iterations."""
     fq = _fq()
     params = dict(DAMP, **params)
     g = fq.fciqmc_create(sysd, params)
@@ -175,6 +176,20 @@ def test_export_device_sort_and_host_fallback_agree(name, sysd, params):
     assert dev["alpha"].size > 100
     assert_states_equal(dev, o.export())
     assert_states_equal(host, o.export())
+    # import the same way round: placed by kernels (g) or laid out on the host
+    # (tight: no room for the scratch); H_ii by the slot-list kernel or per
+    # bucket; both lists, and the runs continued from them, must agree
+    sh = fq.fciqmc_export_shift(g)
+    args = (sh["iteration"], sh["S"], sh["vary"], sh["shift_start"], sh["cnt"], sh["nw_last"])
+    for h in (g, tight):
+        fq.fciqmc_import_state(h, dev["alpha"], dev["beta"], dev["c"], *args)
+    assert_states_equal(fq.fciqmc_export_state(g), dev)
+    assert_states_equal(fq.fciqmc_export_state(tight), dev)
+    fq.fciqmc_step(g, 20)
+    fq.fciqmc_step(tight, 20)
+    o.step(20)
+    assert_states_equal(fq.fciqmc_export_state(g), o.export())
+    assert_states_equal(fq.fciqmc_export_state(tight), o.export())
 
 
 def test_checkpoint_restart_continues_identically():
