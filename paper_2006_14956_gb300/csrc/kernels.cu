@@ -677,8 +677,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int *wsum, int *total)
     __syncthreads();
     int r = x - v + (warp ? wsum[warp - 1] : 0);
     *total = wsum[K3_THREADS / 32 - 1];
-    __syncthreads();
-    return r;
+    return r;  // wsum is written again only after the caller's next barrier
 }
 
 // slot of determinant (a, b) in the trial-estimator table, or -1
@@ -1009,12 +1008,15 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
     // 7. new determinants: their slots go to the run's list; H_jj - E_ref is
     //    computed for all of them at once by k_new_diag, whose warps are not
     //    held back by this block's barriers
-    if (!overflow) {
+    if (!overflow) {  // each warp reserves the entries it writes (q = 32 warp + lane + K3_THREADS k)
         const int nnew = S.n_new;
-        if (t == 0 && nnew > 0) S.new_base = atomicAdd(&I.st->new_n, nnew);
-        __syncthreads();
-        for (int q = t; q < nnew; q += K3_THREADS)
-            I.newdet[S.new_base + q] = (unsigned)(base + W.opos[W.nacc[q]]);
+        int cntw = 0;
+        for (int q0 = warp * 32; q0 < nnew; q0 += K3_THREADS) cntw += min(32, nnew - q0);
+        int nb0 = 0;
+        if (lane == 0 && cntw > 0) nb0 = atomicAdd(&I.st->new_n, cntw);
+        nb0 = __shfl_sync(0xffffffffu, nb0, 0);
+        for (int q = t, k = 0; q < nnew; q += K3_THREADS, k++)
+            I.newdet[nb0 + 32 * k + lane] = (unsigned)(base + W.opos[W.nacc[q]]);
     }
     // 8. bucket reductions (fixed order: lanes by xor tree, warps in index order)
     if (I.trial_bits)  // binary64 adds are slow on this part: only when the estimator is on
@@ -1072,7 +1074,8 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
         I.scnt_i[b] = 0;
         I.scnt_n[b] = 0;
     }
-    __syncthreads();
+    // no closing barrier: what thread 0 still reads (the warp sums) is written
+    // again only after the next bucket's barriers
 }
 
 __global__ void __launch_bounds__(K3_THREADS, 3) k_annihilate(const DevInst *__restrict__ insts,
