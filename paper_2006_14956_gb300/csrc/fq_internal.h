@@ -42,8 +42,6 @@ constexpr int CAP_M = 1024;           // main-list capacity per bucket
 constexpr int CAP_S0 = EMAX - CAP_M;  // initial spawn capacity per bucket (grows at run time)
 constexpr int TABBITS = 12;           // shared-memory hash table of the annihilation (2 x EMAX slots)
 constexpr int BIG_BLOCKS = 64;        // blocks of the large-bucket annihilation kernel
-constexpr int GBITS = 11;             // sub-hash groups per bucket in the annihilation sort
-constexpr int NGROUP = 1 << GBITS;
 constexpr int K5_THREADS = 256;
 constexpr int KIDX = 2048;            // slots of the per-bucket list index (adaptive shift)
 

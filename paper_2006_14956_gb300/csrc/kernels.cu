@@ -14,11 +14,12 @@
 //                  open-addressing table, apply death and rounding, sum the
 //                  spawns exactly, apply the initiator rule and rounding,
 //                  write the new bucket, list the new determinants, and
-//                  reduce N_w, E_num (Eq. (9)) and counters per bucket.
+//                  add the bucket's N_w, E_num (Eq. (9)) and counts to the
+//                  run's exact totals by global reductions.
 //   k_annihilate_big  the same for buckets too large for shared memory.
 //   k_new_diag     exact H_jj of the determinants created in the iteration.
-//   k_finalize     per run: total the bucket reductions, update the shift,
-//                  append the statistics row, flip the buffers.
+//   k_finalize     per run: read and clear the exact totals, update the
+//                  shift, append the statistics row, flip the buffers.
 // Options add work to these launches or one more: the semi-stochastic
 // projection (semistoch.cu) before annihilation, the trial-estimator probe
 // (trial.cu tables) and the adaptive shift's weight sums inside spawning and
@@ -635,7 +636,7 @@ struct K3Shared {
     double red_d[K3_THREADS / 32];
     double red_t[K3_THREADS / 32][2];
     u64 red_u[K3_THREADS / 32][8];
-    int n_new, new_base, side_n;
+    int n_new, side_n;
     int hdr_err, hdr_par;
     long long hdr_it;
     double hdr_S;
@@ -653,8 +654,6 @@ struct K3Smem {
     unsigned short opos[EMAX];
 };
 static_assert(3 * (sizeof(K3Smem) + 1024) <= 233472, "three annihilation blocks per SM");
-
-__device__ __forceinline__ bool key_less(u64 a1, u64 b1, u64 a2, u64 b2) { return a1 < a2 || (a1 == a2 && b1 < b2); }
 
 __device__ __forceinline__ int block_excl_scan(int v, int *wsum, int *total)
 {
