@@ -292,7 +292,10 @@ int fciqmc_export_shift(fciqmc_handle *h, int64_t *iteration, double *S, int32_t
 /* Replaces the walker list and the shift state (a restart from a checkpoint).
  * Keys must be distinct, with the right electron counts; the reference
  * determinant is kept (added with C = 0 when absent).  The bucket count grows
- * (one allocation) until every bucket holds at most half its capacity.
+ * (one allocation) until every bucket holds at most half its capacity.  The
+ * entries are checked, counted and placed on the device in transient scratch
+ * (about 24 bytes per determinant, from the run's allocator); when
+ * max_device_bytes leaves no room for it, on the host.
  * FCIQMC_ERR_INVALID_ARG for a wrong electron count, an orbital beyond norb,
  * a non-finite amplitude, or keys that crowd one bucket even at 2^24 buckets
  * (duplicates); duplicates that do not are not detected. */
