@@ -347,9 +347,13 @@ def main():
     n_in = nd[n0 - 1:n0 - 1 + kprof_iters].astype(np.float64)
     n_out = nd[n0:n0 + kprof_iters].astype(np.float64)
     n_sp = st["spawns"][n0:n0 + kprof_iters].astype(np.float64)
-    # algorithmic bytes: the annihilation kernel reads the old list (key+C, 24 B),
-    # reads the spawns (key+w, 24 B) and writes the new list (24 B)
-    b_ann = float(np.mean(24.0 * (n_in + n_sp + n_out)))
+    # algorithmic bytes per launch: the spawning kernel reads the list (key + C,
+    # 24 B per determinant) and writes the spawns (key + w, 24 B each); the
+    # annihilation kernel reads the old list and the spawns and writes the new
+    # list (24 B per determinant)
+    alg = {"k_spawn": float(np.mean(24.0 * (n_in + n_sp))),
+           "k_annihilate": float(np.mean(24.0 * (n_in + n_sp + n_out)))}
+    tms = {"k_spawn": kt["spawn"], "k_annihilate": kt["annihilate"]}
     b_iter = float(np.mean(24.0 * n_in + 24.0 * n_out + 48.0 * n_sp))
     peaks = {}
     try:
@@ -358,19 +362,29 @@ def main():
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     except Exception:
         peak, peak_src = 6800.0, "fallback"
-    achieved = b_ann / (kt["annihilate"] * 1e-3) / 1e9
-    traffic = None
+    traffic_rec = {}
     try:
-        with open(os.path.join(ROOT, "profiles", "annihilate_abinitio24_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic_abinitio24.json")) as f:
             tr = json.load(f)
         import hashlib
         src = open(os.path.join(ROOT, "paper_2006_14956_gb300", "csrc", "kernels.cu"), "rb").read()
         # counters apply only to the kernels and the workload they were captured on
         if (tr.get("kernels_sha256") == hashlib.sha256(src).hexdigest() and
                 tr.get("bench_args") == {"workload": args.workload, "generator": args.generator}):
-            traffic = tr["dram_bytes_per_launch"]
+            traffic_rec = tr["kernels"]
     except Exception:
         pass
+
+    def roof(k):
+        ach = alg[k] / (tms[k] * 1e-3) / 1e9
+        return {"kernel": k, "achieved": ach, "frac": ach / peak,
+                "traffic": (traffic_rec.get(k) or {}).get("dram_bytes_per_launch"),
+                "alg_bytes_per_launch": alg[k], "launch_ms": tms[k]}
+
+    dominant = max(tms, key=tms.get)  # the kernel with the longest launches
+    other = "k_annihilate" if dominant == "k_spawn" else "k_spawn"
+    roofline = {"bound": "hbm", "peak": peak, "peak_source": peak_src + " hbm_gbs", "unit": "GB/s", **roof(dominant),
+                "iteration_frac": b_iter / (t_dev / args.steps) / 1e9 / peak, "other": roof(other)}
 
     big = args.workload == "abinitio50"
     # ---- end to end through the public API: restart from a host checkpoint
@@ -426,10 +440,7 @@ def main():
                                     "prescribed 5e-4 exceeds 1/sum_j|H_ref,j| (39309 Eh): walker number uncontrollable"),
                        "walkers_mean": nw_mean, "dets_mean": ndet_mean, "l2": "flushed (256 MB write) between steps",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "hbm", "kernel": "k_annihilate", "achieved": achieved, "peak": peak,
-                         "peak_source": peak_src + " hbm_gbs", "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": traffic, "alg_bytes_per_launch": b_ann,
-                         "launch_ms": kt["annihilate"], "iteration_frac": b_iter / (t_dev / args.steps) / 1e9 / peak},
+            "roofline": roofline,
             "kernel_ms": kt,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_att / e2e_el, "unit": "spawn attempts/s", "h2d_bytes_per_step": h2d / E2E_STEPS,
