@@ -109,23 +109,40 @@ __global__ void k_semistoch(const DevInst *__restrict__ insts, int n_inst)
         const double S = I.st->S;
         const double *cur = I.dc_buf[I.st->parity];
         for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < I.nd; r += gridDim.x * blockDim.x) {
-            // y = sum_c H_rc C_c in column order; the loads of eight terms are
-            // issued before their adds, which keep that order
+            // y = sum_c H_rc C_c in column order, eight terms at a time: the
+            // next eight terms' loads are issued before this eight's adds,
+            // which keep the order
             double y = 0.0;
             const long long q1 = I.drow[r + 1];
             long long q = I.drow[r];
-            for (; q + 8 <= q1; q += 8) {
-                int col[8];
-                double v[8], x[8];
+            double v[8], x[8];
+            const bool full = q + 8 <= q1;
+            if (full) {
 #pragma unroll
                 for (int k = 0; k < 8; k++) {
-                    col[k] = I.dcol[q + k];
                     v[k] = I.dval[q + k];
+                    x[k] = cur[I.dcol[q + k]];
+                }
+            }
+            while (q + 8 <= q1) {
+                double vn[8], xn[8];
+                const bool more = q + 16 <= q1;
+                if (more) {
+#pragma unroll
+                    for (int k = 0; k < 8; k++) {
+                        vn[k] = I.dval[q + 8 + k];
+                        xn[k] = cur[I.dcol[q + 8 + k]];
+                    }
                 }
 #pragma unroll
-                for (int k = 0; k < 8; k++) x[k] = cur[col[k]];
-#pragma unroll
                 for (int k = 0; k < 8; k++) y = y + v[k] * x[k];
+                q += 8;
+                if (!more) break;
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    v[k] = vn[k];
+                    x[k] = xn[k];
+                }
             }
             for (; q < q1; q++) y = y + I.dval[q] * cur[I.dcol[q]];
             const double c = cur[r];
