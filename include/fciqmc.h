@@ -39,7 +39,8 @@
 extern "C" {
 #endif
 
-/* status codes */
+/* status codes (no C++ exception leaves the library: a host allocation that
+ * fails inside a call returns FCIQMC_ERR_OUT_OF_MEMORY) */
 enum {
     FCIQMC_OK = 0,
     FCIQMC_ERR_INVALID_ARG = 1,   /* bad argument; nothing changed */

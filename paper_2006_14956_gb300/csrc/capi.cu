@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <new>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -996,7 +997,7 @@ static int create_run(const fciqmc_system *sys, const fciqmc_params *prm, u64 re
     return FCIQMC_OK;
 }
 
-int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_handle **out)
+static int create_impl(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_handle **out)
 {
     if (prm && (prm->replicas < 0 || prm->replicas > 2)) {
         if (out) *out = nullptr;
@@ -1032,6 +1033,17 @@ int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_han
     return rc;
 }
 
+int fciqmc_create(const fciqmc_system *sys, const fciqmc_params *prm, fciqmc_handle **out)
+{
+    try {
+        return create_impl(sys, prm, out);
+    } catch (const std::bad_alloc &) {
+        return fail(nullptr, FCIQMC_ERR_OUT_OF_MEMORY, "host allocation failed");
+    } catch (...) {
+        return fail(nullptr, FCIQMC_ERR_OUT_OF_MEMORY, "host exception");
+    }
+}
+
 int fciqmc_set_profiling(fciqmc_handle *h, int32_t on)
 {
     if (!h) return FCIQMC_ERR_INVALID_ARG;
@@ -1055,7 +1067,7 @@ int fciqmc_layout(fciqmc_handle *h, int64_t out[4])
 
 static int step_to(fciqmc_handle *h, long long target_iter);
 
-int fciqmc_step(fciqmc_handle *h, int64_t n_iter)
+static int step_impl(fciqmc_handle *h, int64_t n_iter)
 {
     if (!h || n_iter < 0) return FCIQMC_ERR_INVALID_ARG;
     if (h->secondary) return fail(h, FCIQMC_ERR_INVALID_ARG, "step a replica pair through its first replica");
@@ -1072,7 +1084,18 @@ int fciqmc_step(fciqmc_handle *h, int64_t n_iter)
     return step_to(h, h->hst.iter + n_iter);
 }
 
-int fciqmc_step_async(fciqmc_handle *h, int64_t n_iter)
+int fciqmc_step(fciqmc_handle *h, int64_t n_iter)
+{
+    try {
+        return step_impl(h, n_iter);
+    } catch (const std::bad_alloc &) {
+        return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "host allocation failed");
+    } catch (...) {
+        return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "host exception");
+    }
+}
+
+static int step_async_impl(fciqmc_handle *h, int64_t n_iter)
 {
     if (!h || n_iter < 0) return FCIQMC_ERR_INVALID_ARG;
     if (h->partner) return fail(h, FCIQMC_ERR_UNSUPPORTED, "replica pairs are stepped with fciqmc_step");
@@ -1088,7 +1111,18 @@ int fciqmc_step_async(fciqmc_handle *h, int64_t n_iter)
     return FCIQMC_OK;
 }
 
-int fciqmc_sync(fciqmc_handle *h)
+int fciqmc_step_async(fciqmc_handle *h, int64_t n_iter)
+{
+    try {
+        return step_async_impl(h, n_iter);
+    } catch (const std::bad_alloc &) {
+        return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "host allocation failed");
+    } catch (...) {
+        return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "host exception");
+    }
+}
+
+static int sync_impl(fciqmc_handle *h)
 {
     if (!h) return FCIQMC_ERR_INVALID_ARG;
     if (!h->pending) return FCIQMC_OK;
@@ -1101,6 +1135,17 @@ int fciqmc_sync(fciqmc_handle *h)
     if (rc) return rc;
     if (!h->hst.err) return FCIQMC_OK;
     return step_to(h, h->async_target);
+}
+
+int fciqmc_sync(fciqmc_handle *h)
+{
+    try {
+        return sync_impl(h);
+    } catch (const std::bad_alloc &) {
+        return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "host allocation failed");
+    } catch (...) {
+        return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "host exception");
+    }
 }
 
 void *fciqmc_stream(fciqmc_handle *h) { return h ? (void *)h->stream : nullptr; }
@@ -1272,7 +1317,7 @@ int64_t fciqmc_num_dets(fciqmc_handle *h)
     return s;
 }
 
-int fciqmc_export_state(fciqmc_handle *h, int64_t cap, uint64_t *alpha, uint64_t *beta, double *c, double *hdiag,
+static int export_state_impl(fciqmc_handle *h, int64_t cap, uint64_t *alpha, uint64_t *beta, double *c, double *hdiag,
                         int32_t *flags, int64_t *n_out)
 {
     if (!h || !n_out) return FCIQMC_ERR_INVALID_ARG;
@@ -1341,6 +1386,18 @@ int fciqmc_export_state(fciqmc_handle *h, int64_t cap, uint64_t *alpha, uint64_t
         if (flags) flags[i] = ff[idx[i]];
     }
     return FCIQMC_OK;
+}
+
+int fciqmc_export_state(fciqmc_handle *h, int64_t cap, uint64_t *alpha, uint64_t *beta, double *c, double *hdiag,
+                        int32_t *flags, int64_t *n_out)
+{
+    try {
+        return export_state_impl(h, cap, alpha, beta, c, hdiag, flags, n_out);
+    } catch (const std::bad_alloc &) {
+        return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "host allocation failed");
+    } catch (...) {
+        return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "host exception");
+    }
 }
 
 int fciqmc_export_shift(fciqmc_handle *h, int64_t *iteration, double *S, int32_t *vary, int64_t *shift_start,
@@ -1485,7 +1542,7 @@ static int import_host(fciqmc_handle *h, int64_t n, const uint64_t *alpha, const
     return FCIQMC_OK;
 }
 
-int fciqmc_import_state(fciqmc_handle *h, int64_t n, const uint64_t *alpha, const uint64_t *beta, const double *c,
+static int import_state_impl(fciqmc_handle *h, int64_t n, const uint64_t *alpha, const uint64_t *beta, const double *c,
                         int64_t iteration, double S, int32_t vary, int64_t shift_start, int64_t cnt, uint64_t nw_last_hi,
                         uint64_t nw_last_lo)
 {
@@ -1538,12 +1595,25 @@ int fciqmc_import_state(fciqmc_handle *h, int64_t n, const uint64_t *alpha, cons
     return capture_graph(h);
 }
 
+int fciqmc_import_state(fciqmc_handle *h, int64_t n, const uint64_t *alpha, const uint64_t *beta, const double *c,
+                        int64_t iteration, double S, int32_t vary, int64_t shift_start, int64_t cnt, uint64_t nw_last_hi,
+                        uint64_t nw_last_lo)
+{
+    try {
+        return import_state_impl(h, n, alpha, beta, c, iteration, S, vary, shift_start, cnt, nw_last_hi, nw_last_lo);
+    } catch (const std::bad_alloc &) {
+        return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "host allocation failed");
+    } catch (...) {
+        return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "host exception");
+    }
+}
+
 int64_t fciqmc_iter_stats_count(fciqmc_handle *h) { return h ? (int64_t)h->hist.size() : -1; }
 
 // Many runs per launch: one descriptor table covering the buckets of all
 // runs, one captured iteration graph; each run stops at its own target via
 // the stop iteration, and capacity flags are handled run by run.
-int fciqmc_step_batch(fciqmc_handle **hs, int32_t k, int64_t n_iter)
+static int step_batch_impl(fciqmc_handle **hs, int32_t k, int64_t n_iter)
 {
     if (!hs || k < 1 || n_iter < 0) return FCIQMC_ERR_INVALID_ARG;
     for (int i = 0; i < k; i++) {
@@ -1686,6 +1756,17 @@ int fciqmc_step_batch(fciqmc_handle **hs, int32_t k, int64_t n_iter)
     return rc;
 }
 
+int fciqmc_step_batch(fciqmc_handle **hs, int32_t k, int64_t n_iter)
+{
+    try {
+        return step_batch_impl(hs, k, n_iter);
+    } catch (const std::bad_alloc &) {
+        return fail((hs ? hs[0] : nullptr), FCIQMC_ERR_OUT_OF_MEMORY, "host allocation failed");
+    } catch (...) {
+        return fail((hs ? hs[0] : nullptr), FCIQMC_ERR_OUT_OF_MEMORY, "host exception");
+    }
+}
+
 int fciqmc_iter_stats_get(fciqmc_handle *h, int64_t first, int64_t count, fciqmc_iter_stats *out)
 {
     if (!h || !out || first < 0 || count < 0 || first + count > (int64_t)h->hist.size()) return FCIQMC_ERR_INVALID_ARG;
@@ -1744,7 +1825,7 @@ static void ratio_blocking(const std::vector<double> &num, const std::vector<dou
     *sigma = mn != 0.0 ? std::fabs(r) * std::sqrt(std::max(rel, 0.0)) : std::sqrt(std::max(rel, 0.0));
 }
 
-extern "C" int fciqmc_energy(fciqmc_handle *h, fciqmc_stats *out)
+static int energy_impl(fciqmc_handle *h, fciqmc_stats *out)
 {
     if (!h || !out) return FCIQMC_ERR_INVALID_ARG;
     memset(out, 0, sizeof(*out));
@@ -1831,6 +1912,17 @@ extern "C" int fciqmc_energy(fciqmc_handle *h, fciqmc_stats *out)
         }
     }
     return FCIQMC_OK;
+}
+
+extern "C" int fciqmc_energy(fciqmc_handle *h, fciqmc_stats *out)
+{
+    try {
+        return energy_impl(h, out);
+    } catch (const std::bad_alloc &) {
+        return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "host allocation failed");
+    } catch (...) {
+        return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "host exception");
+    }
 }
 
 extern "C" int64_t fciqmc_trial_info(fciqmc_handle *h, int64_t *n_w, double *ET, uint64_t *t_alpha, uint64_t *t_beta,
@@ -1972,7 +2064,7 @@ int fciqmc_server_create(int64_t mem_budget_bytes, int32_t max_active, void *str
 
 double fciqmc_server_clock(fciqmc_server *srv) { return srv ? srv->now() : NAN; }
 
-int fciqmc_server_submit(fciqmc_server *srv, const fciqmc_system *sys, const fciqmc_params *params, double target_sigma,
+static int server_submit_impl(fciqmc_server *srv, const fciqmc_system *sys, const fciqmc_params *params, double target_sigma,
                          int64_t max_iters, int64_t *id)
 {
     if (!srv || !sys || !params || !id || !(target_sigma > 0.0) || max_iters < 1) return FCIQMC_ERR_INVALID_ARG;
@@ -1999,6 +2091,18 @@ int fciqmc_server_submit(fciqmc_server *srv, const fciqmc_system *sys, const fci
     srv->req[r.id] = std::move(r);
     srv->queue.push_back(*id);
     return FCIQMC_OK;
+}
+
+int fciqmc_server_submit(fciqmc_server *srv, const fciqmc_system *sys, const fciqmc_params *params, double target_sigma,
+                         int64_t max_iters, int64_t *id)
+{
+    try {
+        return server_submit_impl(srv, sys, params, target_sigma, max_iters, id);
+    } catch (const std::bad_alloc &) {
+        return fail(nullptr, FCIQMC_ERR_OUT_OF_MEMORY, "host allocation failed");
+    } catch (...) {
+        return fail(nullptr, FCIQMC_ERR_OUT_OF_MEMORY, "host exception");
+    }
 }
 
 // the energy a request reports: E_Trial when it has enough samples and the
@@ -2031,7 +2135,7 @@ static void retire(fciqmc_server *srv, Request &r, int state)
     r.st.t_done = srv->now();
 }
 
-int fciqmc_server_tick(fciqmc_server *srv, int64_t n_iter, int32_t *n_active)
+static int server_tick_impl(fciqmc_server *srv, int64_t n_iter, int32_t *n_active)
 {
     if (!srv || n_iter < 1) return FCIQMC_ERR_INVALID_ARG;
     // 1. admission: first come, first served, by device memory
@@ -2106,6 +2210,17 @@ int fciqmc_server_tick(fciqmc_server *srv, int64_t n_iter, int32_t *n_active)
     return FCIQMC_OK;
 }
 
+int fciqmc_server_tick(fciqmc_server *srv, int64_t n_iter, int32_t *n_active)
+{
+    try {
+        return server_tick_impl(srv, n_iter, n_active);
+    } catch (const std::bad_alloc &) {
+        return fail(nullptr, FCIQMC_ERR_OUT_OF_MEMORY, "host allocation failed");
+    } catch (...) {
+        return fail(nullptr, FCIQMC_ERR_OUT_OF_MEMORY, "host exception");
+    }
+}
+
 int fciqmc_server_poll(fciqmc_server *srv, int64_t id, fciqmc_request_status *out)
 {
     if (!srv || !out) return FCIQMC_ERR_INVALID_ARG;
@@ -2152,7 +2267,7 @@ static bool namelist_int(const std::string &nl, const char *key, long long *v)
     return false;
 }
 
-extern "C" int fciqmc_read_fcidump(const char *path, fciqmc_system *out)
+static int read_fcidump_impl(const char *path, fciqmc_system *out)
 {
     if (!path || !out) return FCIQMC_ERR_INVALID_ARG;
     std::ifstream f(path);
@@ -2212,6 +2327,17 @@ extern "C" int fciqmc_read_fcidump(const char *path, fciqmc_system *out)
     return FCIQMC_OK;
 }
 
+extern "C" int fciqmc_read_fcidump(const char *path, fciqmc_system *out)
+{
+    try {
+        return read_fcidump_impl(path, out);
+    } catch (const std::bad_alloc &) {
+        return fail(nullptr, FCIQMC_ERR_OUT_OF_MEMORY, "host allocation failed");
+    } catch (...) {
+        return fail(nullptr, FCIQMC_ERR_OUT_OF_MEMORY, "host exception");
+    }
+}
+
 extern "C" void fciqmc_free_system(fciqmc_system *sys)
 {
     if (!sys) return;
@@ -2222,7 +2348,7 @@ extern "C" void fciqmc_free_system(fciqmc_system *sys)
 }
 
 // ------------------------------------------------------------------ autotuner
-extern "C" int fciqmc_autotune(fciqmc_handle **hs, int32_t k, int64_t n_iter, int32_t out[3])
+static int autotune_impl(fciqmc_handle **hs, int32_t k, int64_t n_iter, int32_t out[3])
 {
     if (!hs || k < 1 || n_iter < 1 || !out) return FCIQMC_ERR_INVALID_ARG;
     const int spawn_c[] = {2, 4, 8, 16}, anni_c[] = {3, 9, 24}, heavy_c[] = {1, 2, 4};
@@ -2274,4 +2400,15 @@ extern "C" int fciqmc_autotune(fciqmc_handle **hs, int32_t k, int64_t n_iter, in
     cudaEventDestroy(e1);
     out[0] = best_s; out[1] = best_h; out[2] = best_a;
     return FCIQMC_OK;
+}
+
+extern "C" int fciqmc_autotune(fciqmc_handle **hs, int32_t k, int64_t n_iter, int32_t out[3])
+{
+    try {
+        return autotune_impl(hs, k, n_iter, out);
+    } catch (const std::bad_alloc &) {
+        return fail((hs ? hs[0] : nullptr), FCIQMC_ERR_OUT_OF_MEMORY, "host allocation failed");
+    } catch (...) {
+        return fail((hs ? hs[0] : nullptr), FCIQMC_ERR_OUT_OF_MEMORY, "host exception");
+    }
 }
