@@ -348,7 +348,7 @@ int64_t fciqmc_pchb_table(fciqmc_handle *h, int32_t same_spin, int32_t i, int32_
 
 /* The same sum as fciqmc_ref_offdiag_sum, for callers that cannot allocate
  * device memory: frameworks whose memory pool owns every device byte, jobs
- * held to a fixed memory budget, or loops that must not enter the driver's
+ * held to a fixed memory budget, or loops that must not enter the CUDA driver's
  * allocator (cudaMalloc can synchronise the whole device).  No counterpart in
  * the paper: this is an interface
  * convenience of this library.

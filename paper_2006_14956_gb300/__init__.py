@@ -313,7 +313,7 @@ def fciqmc_export_state(handle):
     n = C.c_int64()
     _lib.fciqmc_export_state(handle.h, 0, None, None, None, None, None, C.byref(n))
     m = max(n.value, 1)
-    # output pages are touched here: a first touch inside the driver's
+    # output pages are touched here: a first touch inside the CUDA driver's
     # pageable device-to-host copy costs ten times the copy itself
     a, b = np.empty(m, np.uint64), np.empty(m, np.uint64)
     c, hd = np.empty(m, np.float64), np.empty(m, np.float64)

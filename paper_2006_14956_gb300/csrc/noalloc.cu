@@ -7,7 +7,7 @@
 // the integrals -- lives in a file-scope device array instead of memory from
 // cudaMalloc, so it can serve callers that must not allocate: frameworks that
 // own every byte of device memory through their own pool, jobs held to a
-// fixed device-memory budget, or loops that must not enter the driver's
+// fixed device-memory budget, or loops that must not enter the CUDA driver's
 // allocator (cudaMalloc can synchronise the whole device).
 #include <cuda_runtime.h>
 

@@ -2,7 +2,7 @@
 
 fciqmc_ref_offdiag_sum_noalloc serves callers that may not allocate device
 memory (under a framework's memory pool, within a fixed budget, or in a loop
-that must not enter the driver's allocator): it takes the caller's device
+that must not enter the CUDA driver's allocator): it takes the caller's device
 buffers and keeps its scratch in a fixed array of the library.  Here it is called twice in a row, on two
 systems, through the C ABI, and each result must equal the sum that the
 ordinary path (fciqmc_create, then fciqmc_ref_offdiag_sum) computes with
