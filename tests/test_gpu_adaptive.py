@@ -27,6 +27,15 @@ CASES = {
     "abinitio_semistoch": (workloads.small_abinitio(8, 3, 3, seed=5),
                            dict(tau=0.005, target_walkers=3000, initiator_threshold=3.0, seed=11,
                                 semistoch_size=60, semistoch_start=5), 200),
+    # 3e5 walkers on the reference: its attempts go through the sliced heavy
+    # path, whose slices carry the parent's slot for the weight sums (a
+    # non-zero shift, held fixed below the target, so that f_i S differs from S)
+    "abinitio_heavy": (workloads.small_abinitio(8, 3, 3, seed=21),
+                       dict(tau=0.002, target_walkers=1e9, initial_walkers=3e5, initiator_threshold=3.0, seed=4,
+                            initial_shift=-2.0), 6),
+    "abinitio_trial": (workloads.small_abinitio(8, 3, 3, seed=5),
+                       dict(tau=0.005, target_walkers=3000, initiator_threshold=3.0, seed=11, trial_size=25,
+                            trial_start=5), 200),
 }
 
 
