@@ -57,6 +57,11 @@ CASES = {
     "abinitio_pchb_cmin_half": (workloads.small_abinitio(7, 3, 2, seed=8),
                                 dict(tau=0.004, target_walkers=1500, c_min=0.5, initiator_threshold=2.0, seed=5,
                                      generator=1), 200),
+    # both replicas with a trial space: the first replica's finalize sums the
+    # trial and the cross estimators together
+    "abinitio_trial": (workloads.small_abinitio(8, 3, 3, seed=5),
+                       dict(tau=0.005, target_walkers=3000, initiator_threshold=3.0, seed=11, trial_size=25,
+                            trial_start=5), 200),
 }
 
 
