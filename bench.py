@@ -301,7 +301,7 @@ def main():
     fq.fciqmc_step(h, args.equil)                        # growth / equilibration, untimed
     fq.fciqmc_step(h, args.warmup)                       # warm-up steps
     stream = torch.cuda.ExternalStream(fq.fciqmc_stream(h))
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     n_before = fq.fciqmc_iter_stats_get(h)["iteration"].size
 
     # ---- timed region: K single iterations, L2 flushed before each, device events on the run's stream
