@@ -298,7 +298,7 @@ int fciqmc_export_shift(fciqmc_handle *h, int64_t *iteration, double *S, int32_t
  * (about 24 bytes per determinant, from the run's allocator); when
  * max_device_bytes leaves no room for it, on the host.
  * FCIQMC_ERR_INVALID_ARG for a wrong electron count, an orbital beyond norb,
- * a non-finite amplitude, or keys that crowd one bucket even at 2^24 buckets
+ * a non-finite amplitude, or keys that crowd one bucket even at 2^22 buckets
  * (duplicates); duplicates that do not are not detected. */
 int fciqmc_import_state(fciqmc_handle *h, int64_t n, const uint64_t *alpha, const uint64_t *beta,
                         const double *c, int64_t iteration, double S, int32_t vary, int64_t shift_start,

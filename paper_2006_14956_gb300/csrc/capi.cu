@@ -325,7 +325,7 @@ static int write_state(fciqmc_handle *h)
 // split every bucket in two (one more hash bit)
 static int grow_buckets(fciqmc_handle *h)
 {
-    if (h->bb >= 24) return fail(h, FCIQMC_ERR_CAPACITY, "walker list exceeds 2^24 buckets");
+    if (h->bb >= MAX_BB) return fail(h, FCIQMC_ERR_CAPACITY, "walker list exceeds 2^22 buckets");
     DevInst nI = h->hi;
     if (nI.cap_s > CAP_S0) nI.cap_s /= 2;  // each new bucket receives about half the spawns
     int rc = alloc_layout(h, nI, h->bb + 1);
@@ -956,7 +956,7 @@ static int create_run(const fciqmc_system *sys, const fciqmc_params *prm, u64 re
         if (P.max_dets <= 0) dets_hint = std::min(dets_hint, std::max(1.0, fci));
     }
     int bb = 0;
-    while (((double)(1LL << bb)) * 640.0 < dets_hint && bb < 24) bb++;
+    while (((double)(1LL << bb)) * 640.0 < dets_hint && bb < MAX_BB) bb++;
     I.cap_s = CAP_S0;
     int rc = alloc_layout(h, I, bb);
     if (rc) return bail(rc, "out of device memory (walker buffers)");
@@ -1202,7 +1202,7 @@ static int step_to(fciqmc_handle *h, long long target_iter)
         rc = pull_history(h, start, h->hst.iter);
         if (rc) return rc;
         if (!h->hst.err && !h->hist.empty() && h->hist.back().ndet > (1LL << h->bb) * (long long)(CAP_M / 2) &&
-            h->bb < 24) {
+            h->bb < MAX_BB) {
             // keep head-room in the main buckets: split once the average
             // occupancy passes half the capacity
             rc = grow_buckets(h);
@@ -1463,7 +1463,7 @@ static int import_device(fciqmc_handle *h, int64_t n, const uint64_t *alpha, con
         dev_free(h, cntb);
         if (e != cudaSuccess) return fail(h, FCIQMC_ERR_CUDA, std::string("import: ") + cudaGetErrorString(e));
         if (!over) break;
-        if (bb >= 24)  // distinct keys never crowd one bucket at 2^24 buckets
+        if (bb >= MAX_BB)  // distinct keys crowd one bucket at the largest bucket count only if duplicated
             return fail(h, FCIQMC_ERR_INVALID_ARG, "imported keys crowd one bucket (duplicate determinants?)");
     }
     if (bb != h->bb) {
@@ -1511,7 +1511,7 @@ static int import_host(fciqmc_handle *h, int64_t n, const uint64_t *alpha, const
         for (int64_t i = 0; i < nt && !over; i++)
             if (++cnt_b[bb ? (size_t)(hash[i] >> (64 - bb)) : 0] > CAP_M / 2) over = true;
         if (!over) break;
-        if (bb >= 24)
+        if (bb >= MAX_BB)
             return fail(h, FCIQMC_ERR_INVALID_ARG, "imported keys crowd one bucket (duplicate determinants?)");
     }
     if (bb != h->bb) {
@@ -2037,7 +2037,7 @@ static int64_t estimate_bytes(const Request &r)
     const double np = (double)N * (N + 1) / 2, ne = np * (np + 1) / 2;
     double dets = r.p.max_dets > 0 ? (double)r.p.max_dets : std::min(std::max(4096.0, r.p.target_walkers), 8388608.0);
     int bb = 0;
-    while (((double)(1LL << bb)) * (CAP_M / 2.5) < dets && bb < 24) bb++;
+    while (((double)(1LL << bb)) * (CAP_M / 2.5) < dets && bb < MAX_BB) bb++;
     const double per_bucket = 2.0 * CAP_M * (16 + 8 + 8 + 1) + 5.0 * CAP_S0 * 24.0 + 2 * 8 + sizeof(Partial) + 3 * 4 +
                               4.0 * CAP_M;
     const double ecap = CAP_M + 4.0 * CAP_S0;

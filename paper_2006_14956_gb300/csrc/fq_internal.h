@@ -39,6 +39,7 @@ constexpr unsigned HEAVY_ATT = 2048;  // attempts per heavy chunk
 constexpr int K3_THREADS = 256;
 constexpr int EMAX = 1280;            // main + spawned records staged per bucket in shared memory (3 blocks per SM)
 constexpr int CAP_M = 1024;           // main-list capacity per bucket
+constexpr int MAX_BB = 22;            // at most 2^22 buckets: slot indices (bucket * CAP_M + position) fit 32 bits
 constexpr int CAP_S0 = EMAX - CAP_M;  // initial spawn capacity per bucket (grows at run time)
 constexpr int TABBITS = 12;           // shared-memory hash table of the annihilation (2 x EMAX slots)
 constexpr int BIG_BLOCKS = 64;        // blocks of the large-bucket annihilation kernel
