@@ -11,7 +11,6 @@ about 1e6 walkers.  Prints one JSON line.
 import argparse
 import ctypes
 import json
-import math
 import os
 import statistics
 import subprocess

@@ -5,7 +5,6 @@ routine (numpy Philox, math.fsum, numpy.log), brute-force operator algebra,
 closed-form energies, exact enumeration of generation probabilities, and the
 exact expectation value of one projector step (Eq. (2) of the paper).
 """
-import itertools
 import math
 from fractions import Fraction
 

@@ -9,7 +9,6 @@ Hubbard lattices at half filling).
 """
 from __future__ import annotations
 
-import math
 
 import numpy as np
 
