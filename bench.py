@@ -46,7 +46,7 @@ def _workload_params(seed_offset=0, workload="abinitio24"):
         # 50 orbitals, 10+10 electrons, 200 Cholesky vectors: sum_j |H_ref,j| = 39309 Eh,
         # so tau = 0.5 / 39309 rounded down = 1.25e-5 (the prescribed 5e-4 gives 19.7)
         sysd, prm = workloads.config_abinitio_50()
-        prm = dict(prm, tau=1.25e-5, target_walkers=6e7, initial_walkers=1e6, shift_damping=1.0, shift_interval=2,
+        prm = dict(prm, tau=1.25e-5, target_walkers=1e8, initial_walkers=1e6, shift_damping=1.0, shift_interval=2,
                    seed=prm["seed"] + seed_offset, semistoch_size=10000, semistoch_start=100)
         return sysd, prm
     sysd, prm = workloads.config_abinitio_24()
@@ -210,51 +210,76 @@ def run_batch(args):
 def run_serving(args):
     """Poisson arrivals (20/s) of mixed FCIQMC requests (1D/2D Hubbard and
     synthetic ab initio systems, walker targets 1e4..1e7), each run until the
-    blocking error of E_proj is below 1 mEh (or an iteration cap).  Reports
-    p50/p99 time from arrival to answer and throughput."""
+    blocking error of its energy is below 1 mEh (or an iteration cap).  Each
+    request is submitted when it arrives, with its arrival time; the server
+    admits it at its next scheduling round (every `--tick` iterations of the
+    running batch).  Latency = completion - arrival.  Reports p50/p99 over the
+    requests that reached the target, by system kind, with the count and the
+    errors reached by the others, and the throughput of the whole stream."""
     import paper_2006_14956_gb300 as fq
     reqs = workloads.serving_requests(args.requests, rate=20.0, seed=5)
+    # the client's own preparation (integral generation) happens before the clock starts
+    prepared = []
+    for r in reqs:
+        sysd = r["system"]
+        if sysd["kind"] == "abinitio":
+            h1, eri = workloads.synthetic_abinitio(sysd["norb"], sysd["n_chol"], sysd["integral_seed"])
+            sysd = dict(sysd, h1=h1, eri=eri, ecore=0.0)
+        # a trial space (Sec. IV) gives E_Trial, whose error is far below E_proj's
+        # when the reference carries little weight
+        prm = dict(tau=0.0, target_walkers=r["target_walkers"], initial_walkers=min(r["target_walkers"], 1e3),
+                   initiator_threshold=3.0, seed=r["seed"], shift_damping=0.5, shift_interval=5,
+                   trial_size=args.trial_size, trial_start=50)
+        prepared.append((r, sysd, prm))
     srv = fq.fciqmc_server_create(200 << 30, max_active=64)
-    pending = list(reqs)
-    ids = {}
     t0 = fq.fciqmc_server_clock(srv)
+    pending = list(prepared)
+    ids = {}
     active = 0
     while pending or active:
         now = fq.fciqmc_server_clock(srv) - t0
-        while pending and pending[0]["arrival"] <= now:
-            r = pending.pop(0)
-            sysd = r["system"]
-            if sysd["kind"] == "abinitio":
-                h1, eri = workloads.synthetic_abinitio(sysd["norb"], sysd["n_chol"], sysd["integral_seed"])
-                sysd = dict(sysd, h1=h1, eri=eri, ecore=0.0)
-            # a 32-determinant trial space (Sec. IV) gives E_Trial, whose error is
-            # far below E_proj's when the reference carries little weight
-            prm = dict(tau=0.0, target_walkers=r["target_walkers"], initial_walkers=min(r["target_walkers"], 1e3),
-                       initiator_threshold=3.0, seed=r["seed"], shift_damping=0.5, shift_interval=5,
-                       trial_size=32, trial_start=50)
-            ids[r["id"]] = fq.fciqmc_server_submit(srv, sysd, prm, target_sigma=1e-3, max_iters=args.max_iters)
-        active = fq.fciqmc_server_tick(srv, 50) if ids else 0
+        while pending and pending[0][0]["arrival"] <= now:
+            r, sysd, prm = pending.pop(0)
+            ids[r["id"]] = fq.fciqmc_server_submit(srv, sysd, prm, target_sigma=1e-3, max_iters=args.max_iters,
+                                                   t_arrival=t0 + r["arrival"])
+        active = fq.fciqmc_server_tick(srv, args.tick) if ids else 0
         if not active and pending:
-            time.sleep(max(0.0, pending[0]["arrival"] - (fq.fciqmc_server_clock(srv) - t0)))
+            time.sleep(max(0.0, pending[0][0]["arrival"] - (fq.fciqmc_server_clock(srv) - t0)))
     t_end = fq.fciqmc_server_clock(srv) - t0
     st = [fq.fciqmc_server_poll(srv, ids[r["id"]]) for r in reqs]
-    lat = np.array([s["t_done"] - s["t_submit"] for s in st])
     att = float(sum(s["attempts"] for s in st))
-    conv = sum(1 for s in st if s["state_name"] == "converged")
-    by_trial = sum(1 for s in st if s["state_name"] == "converged" and s["estimator"] == 1)
-    return {"metric": METRIC, "value": float(np.percentile(lat, 50)), "unit": "s (p50 time to answer)",
+    kinds = {"hubbard": [], "abinitio": []}
+    for s, r in zip(st, reqs):
+        kinds[r["system"]["kind"]].append(s)
+
+    def summary(group):
+        conv = [s for s in group if s["state_name"] == "converged"]
+        lat = np.array([s["t_done"] - s["t_arrival"] for s in conv])
+        wait = np.array([s["t_start"] - s["t_arrival"] for s in group if s["t_start"] > 0])
+        return {"requests": len(group), "converged": len(conv),
+                "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
+                "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
+                "by_trial_estimator": sum(1 for s in conv if s["estimator"] == 1),
+                "admission_wait_p50_s": float(np.percentile(wait, 50)) if wait.size else None,
+                "sigma_mEh_not_converged": sorted(round(1e3 * s["sigma"], 2) for s in group
+                                                  if s["state_name"] != "converged" and np.isfinite(s["sigma"])),
+                "failed": sum(1 for s in group if s["state_name"] == "failed")}
+
+    allc = [s for s in st if s["state_name"] == "converged"]
+    lat = np.array([s["t_done"] - s["t_arrival"] for s in allc])
+    p50 = float(np.percentile(lat, 50)) if lat.size else None
+    return {"metric": METRIC, "value": p50, "unit": "s (p50 time from arrival to sigma(E) < 1 mEh)",
             "higher_is_better": False, "n_gpus": 1, "steps": len(reqs), "warmup": 0, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "requests": len(reqs), "converged": conv, "converged_by_trial_estimator": by_trial,
-            "sigma_mEh_at_answer": {k: [round(1e3 * s["sigma"], 3) for s, r in zip(st, reqs)
-                                        if r["system"]["kind"] == k and np.isfinite(s["sigma"])]
-                                    for k in ("hubbard", "abinitio")},
-            "capped": len(reqs) - conv,
-            "requests_per_s": len(reqs) / t_end, "attempts_per_s": att / t_end,
+            "p50_s": p50, "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
+            "converged": len(allc), "requests": len(reqs),
+            "by_kind": {k: summary(v) for k, v in kinds.items()},
+            "requests_per_s": len(reqs) / t_end, "attempts_per_s": att / t_end, "wall_s": t_end,
             "config": {"workload": "serving stream: Poisson 20/s, 1D/2D Hubbard 8-18 sites and ab initio 16-40 "
-                                   "orbitals, targets 1e4..1e7, to sigma(E) < 1 mEh (E_proj or E_Trial, N_T = 32)",
-                       "max_iters": args.max_iters, "tau": "0.5/sum_j|H_ref,j| per request"}}
+                                   "orbitals, targets 1e4..1e7, to sigma(E) < 1 mEh (E_proj or E_Trial, N_T = %d)"
+                                   % args.trial_size,
+                       "max_iters": args.max_iters, "tick_iters": args.tick,
+                       "tau": "0.5/sum_j|H_ref,j| per request"}}
 
 
 def main():
@@ -269,6 +294,8 @@ def main():
                     help="double excitations: uniform, or pre-computed heat-bath alias tables")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--max-iters", type=int, default=20000)
+    ap.add_argument("--tick", type=int, default=10, help="serving: iterations per scheduling round")
+    ap.add_argument("--trial-size", type=int, default=32, help="serving: trial-space size of every request")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank = int(os.environ.get("RANK", "0"))

@@ -401,12 +401,20 @@ typedef struct {
     double tau;
     int32_t estimator;    /* 0: E_proj (Eq. (9)), 1: E_Trial (Sec. IV) */
     int32_t pad0;
+    double t_arrival;     /* arrival time on the server's clock; latency = t_done - t_arrival */
 } fciqmc_request_status;
 
 int fciqmc_server_create(int64_t mem_budget_bytes, int32_t max_active, void *stream, fciqmc_server **out);
-/* copies sys (including the integral arrays) and params; returns the request id */
+/* Copies sys (including the integral arrays) and params; returns the request
+ * id.  t_arrival is the request's arrival time in seconds on the server's
+ * clock (fciqmc_server_clock); a negative or NaN value means now.  Requests
+ * are admitted in order of arrival, never before their arrival time, so a
+ * client may hand over a future arrival schedule up front or submit each
+ * request when it arrives; its latency counts from t_arrival either way.
+ * Errors: FCIQMC_ERR_INVALID_ARG (missing pointers, target_sigma <= 0,
+ * max_iters < 1, norb outside 1..64), FCIQMC_ERR_UNSUPPORTED (replicas > 1). */
 int fciqmc_server_submit(fciqmc_server *srv, const fciqmc_system *sys, const fciqmc_params *params,
-                         double target_sigma, int64_t max_iters, int64_t *id);
+                         double target_sigma, double t_arrival, int64_t max_iters, int64_t *id);
 /* one scheduling round: admit, advance every running request by n_iter
  * iterations, retire finished ones; *n_active = running + queued afterwards */
 int fciqmc_server_tick(fciqmc_server *srv, int64_t n_iter, int32_t *n_active);

@@ -104,6 +104,8 @@ def lib():
                 "orc_stat_size": (I32, []),
                 "orc_params_size": (I32, []),
                 "orc_semistoch_info": (I64, [P, C.POINTER(C.c_int64)]),
+                "orc_semistoch_csr": (None, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), dp, up, up]),
+                "orc_semistoch_rows": (None, [P, dp, dp]),
                 "orc_proj_energy": (None, [P, dp, dp]),
                 "orc_generate_pchb": (I32, [P, U64, U64, up, up, up, dp]),
                 "orc_pchb_table": (I32, [P, I32, I32, I32, dp, dp, dp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -390,6 +392,28 @@ class Run:
         nd = lib().orc_semistoch_info(self.h, C.byref(nnz))
         return nd, nnz.value
 
+    def semistoch_csr(self):
+        """D (keys in ascending order) and H^D - E_ref in CSR."""
+        nd, nnz = self.semistoch_info()
+        rp = np.zeros(nd + 1, np.int64)
+        col = np.zeros(max(nnz, 1), np.int64)
+        val = np.zeros(max(nnz, 1))
+        da = np.zeros(max(nd, 1), np.uint64)
+        db = np.zeros(max(nd, 1), np.uint64)
+        i64 = lambda x: x.ctypes.data_as(C.POINTER(C.c_int64))
+        lib().orc_semistoch_csr(self.h, i64(rp), i64(col), val.ctypes.data_as(C.POINTER(C.c_double)),
+                                da.ctypes.data_as(C.POINTER(C.c_uint64)), db.ctypes.data_as(C.POINTER(C.c_uint64)))
+        return dict(rowptr=rp, col=col[:nnz], val=val[:nnz], alpha=da[:nd], beta=db[:nd])
+
+    def semistoch_rows(self, cD):
+        """Row sums y_k = sum_c H^D_kc cD_c of the semi-stochastic update."""
+        nd, _ = self.semistoch_info()
+        x, xp = _f64(cD)
+        assert x.size == nd
+        y = np.zeros(nd)
+        lib().orc_semistoch_rows(self.h, xp, y.ctypes.data_as(C.POINTER(C.c_double)))
+        return y
+
     def stats(self):
         n = lib().orc_nstats(self.h)
         arr = (Stat * max(n, 1))()
@@ -427,38 +451,75 @@ def jacobi_lowest(A):
 
 
 # ---------------------------------------------------------------- statistics
-def blocking(x):
-    """Flyvbjerg-Petersen blocking: returns (mean, sigma, sigma per level).
-    The plateau is taken as the first level whose error is within its own
-    statistical uncertainty of the next level's."""
-    x = np.asarray(x, np.float64)
-    mean = float(np.mean(x))
-    errs = []
-    y = x.copy()
+# The paper gives no error analysis for its energy estimators.  Reading: the
+# blocking transformation of Flyvbjerg and Petersen (J. Chem. Phys. 91, 461
+# (1989)) with the block length chosen by the criterion of Lee, Conduit,
+# Nemec, Lopez Rios and Drummond (Phys. Rev. E 83, 066706 (2011)): the
+# smallest level k whose block length B = 2^k satisfies
+# B^3 > 2 n (SE_k / SE_0)^4, n the number of samples.
+def blocking_levels(x):
+    """Levels of the blocking transformation: level 0 is the series, level
+    k + 1 the means of neighbouring pairs of level k (an odd last element is
+    dropped), down to two elements."""
+    y = np.asarray(x, np.float64)
+    out = []
     while y.size >= 2:
-        n = y.size
-        v = np.var(y, ddof=0) / (n - 1)
-        errs.append((math.sqrt(v), math.sqrt(v) / math.sqrt(2.0 * (n - 1))))
-        y = 0.5 * (y[0:(n // 2) * 2:2] + y[1:(n // 2) * 2:2])
-    sig = errs[-1][0] if errs else float("nan")
-    for k in range(len(errs) - 1):
-        if abs(errs[k + 1][0] - errs[k][0]) < errs[k][1]:
-            sig = errs[k][0]
-            break
-    return mean, sig, [e for e, _ in errs]
+        out.append(y)
+        m = y.size // 2
+        y = 0.5 * (y[0:2 * m:2] + y[1:2 * m:2])
+    return out
+
+
+def _se(y):
+    """Standard error of the mean of a level, treating its elements as independent."""
+    return math.sqrt(float(np.mean((y - np.mean(y)) ** 2)) / (y.size - 1))
+
+
+def optimal_level(x):
+    """Index of the blocking level chosen by the B^3 > 2 n (SE_k/SE_0)^4 rule
+    (the last level if none satisfies it; 0 for a constant series)."""
+    lev = blocking_levels(x)
+    if not lev:
+        return -1
+    n = lev[0].size
+    se0 = _se(lev[0])
+    if se0 == 0.0:
+        return 0
+    for k, y in enumerate(lev):
+        if (2.0 ** k) ** 3 > 2.0 * n * (_se(y) / se0) ** 4:
+            return k
+    return len(lev) - 1
+
+
+def blocking(x):
+    """(mean, sigma of the mean, standard error of every level)."""
+    x = np.asarray(x, np.float64)
+    lev = blocking_levels(x)
+    if not lev:
+        return float(np.mean(x)) if x.size else float("nan"), float("nan"), []
+    errs = [_se(y) for y in lev]
+    return float(np.mean(x)), errs[optimal_level(x)], errs
 
 
 def ratio_estimate(num, den):
-    """Ratio of means with a delta-method error from blocked covariances."""
+    """mean(num) / mean(den) with the delta-method error
+    sigma^2 = (s_n^2 - 2 r c + r^2 s_d^2) / mean(den)^2, where s_n, s_d and the
+    covariance c of the two means are taken at one blocking level, the larger
+    of the two series' optimal levels."""
     num = np.asarray(num, np.float64)
     den = np.asarray(den, np.float64)
-    mn, sn, _ = blocking(num)
-    md, sd, _ = blocking(den)
-    # correlation at the plateau block size approximated by the raw correlation
-    rho = float(np.corrcoef(num, den)[0, 1]) if num.size > 2 and np.std(num) > 0 and np.std(den) > 0 else 0.0
+    mn, md = float(np.mean(num)), float(np.mean(den))
     r = mn / md
-    var = r * r * ((sn / mn) ** 2 + (sd / md) ** 2 - 2.0 * rho * sn * sd / (mn * md)) if mn != 0 else (sn / md) ** 2
-    return r, math.sqrt(max(var, 0.0))
+    ln, ld = blocking_levels(num), blocking_levels(den)
+    if not ln:
+        return r, float("nan")
+    k = max(optimal_level(num), optimal_level(den))
+    yn, yd = ln[k], ld[k]
+    m = yn.size
+    vn = float(np.mean((yn - np.mean(yn)) ** 2)) / (m - 1)
+    vd = float(np.mean((yd - np.mean(yd)) ** 2)) / (m - 1)
+    c = float(np.mean((yn - np.mean(yn)) * (yd - np.mean(yd)))) / (m - 1)
+    return r, math.sqrt(max(vn - 2.0 * r * c + r * r * vd, 0.0)) / abs(md)
 
 
 def system_from_workload(sysd) -> System:

@@ -895,6 +895,30 @@ static void build_D(orc_run *r)
     free(cd); free(tmp);
 }
 
+/* CSR of H^D - E_ref (rows and columns in ascending key order of D); any
+ * output pointer may be NULL */
+void orc_semistoch_csr(const orc_run *r, int64_t *rowptr, int64_t *col, double *val, uint64_t *da, uint64_t *db)
+{
+    for (int64_t k = 0; k < r->nd; k++) {
+        if (da) da[k] = r->Da[k];
+        if (db) db[k] = r->Db[k];
+    }
+    if (rowptr) for (int64_t k = 0; k <= r->nd; k++) rowptr[k] = r->rowptr[k];
+    int64_t nnz = r->nd ? r->rowptr[r->nd] : 0;
+    for (int64_t q = 0; q < nnz; q++) {
+        if (col) col[q] = r->col[q];
+        if (val) val[q] = r->val[q];
+    }
+}
+
+static double semi_row_sum(const orc_run *r, const double *cD, int64_t k);
+
+/* y_k of every row for the amplitudes cD (the row sum of the semi-stochastic update) */
+void orc_semistoch_rows(const orc_run *r, const double *cD, double *y)
+{
+    for (int64_t k = 0; k < r->nd; k++) y[k] = semi_row_sum(r, cD, k);
+}
+
 int64_t orc_semistoch_info(const orc_run *r, int64_t *nnz)
 {
     if (nnz) *nnz = r->nd ? r->rowptr[r->nd] : 0;
@@ -1102,6 +1126,32 @@ static double round_stoch(double v, double cmin, double u)
     return u < fabs(v) / cmin ? copysign(cmin, v) : 0.0;
 }
 
+/* Semi-stochastic row sum (reading R13): y_k = sum_c H^D_kc C_c, where each
+ * product is rounded to binary64, then truncated toward zero to a multiple
+ * of 2^-64, and the truncated products are summed exactly and rounded once;
+ * the new amplitude is C_k - tau (y_k - S C_k), evaluated as written. */
+static double trunc_grid64(double p)
+{
+    /* p 2^64 and its integer part are exact; the result has at most 53
+     * significant bits and is 0 or at least 2^-64 in magnitude, so scaling
+     * back is exact too */
+    return ldexp(trunc(ldexp(p, 64)), -64);
+}
+
+static double semi_row_sum(const orc_run *r, const double *cD, int64_t k)
+{
+    xacc x;
+    xacc_zero(&x);
+    for (int64_t q = r->rowptr[k]; q < r->rowptr[k + 1]; q++) xacc_add(&x, trunc_grid64(r->val[q] * cD[r->col[q]]), 0);
+    return xacc_round(&x);
+}
+
+static double semi_update(const orc_run *r, const double *cD, int64_t k)
+{
+    double y = semi_row_sum(r, cD, k);
+    return cD[k] - r->p.tau * (y - r->S * cD[k]);
+}
+
 /* one projector iteration; returns 0 or a nonzero error code */
 static int one_iteration(orc_run *r)
 {
@@ -1206,11 +1256,7 @@ static int one_iteration(orc_run *r)
             cD[k] = i >= 0 ? c0[i] : 0.0;
         }
         cd_new = malloc(sizeof(double) * r->nd);
-        for (int64_t k = 0; k < r->nd; k++) {
-            double y = 0.0;
-            for (int64_t q = r->rowptr[k]; q < r->rowptr[k + 1]; q++) y = y + r->val[q] * cD[r->col[q]];
-            cd_new[k] = cD[k] - P->tau * (y - r->S * cD[k]);
-        }
+        for (int64_t k = 0; k < r->nd; k++) cd_new[k] = semi_update(r, cD, k);
         free(cD);
     }
     for (int64_t i = 0; i < r->n; i++) {

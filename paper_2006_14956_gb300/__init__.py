@@ -92,7 +92,7 @@ class fciqmc_request_status(C.Structure):
     _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("iterations", C.c_int64), ("energy", C.c_double),
                 ("sigma", C.c_double), ("shift", C.c_double), ("t_submit", C.c_double), ("t_start", C.c_double),
                 ("t_done", C.c_double), ("attempts", C.c_int64), ("device_bytes", C.c_int64), ("tau", C.c_double),
-                ("estimator", C.c_int32), ("pad0", C.c_int32)]
+                ("estimator", C.c_int32), ("pad0", C.c_int32), ("t_arrival", C.c_double)]
 
 
 REQUEST_STATES = {0: "queued", 1: "running", 2: "converged", 3: "max_iters", 4: "failed"}
@@ -135,7 +135,7 @@ _SIGS = {
                                                  C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p]),
     "fciqmc_server_create": (C.c_int, [C.c_int64, C.c_int32, C.c_void_p, C.POINTER(_H)]),
     "fciqmc_server_submit": (C.c_int, [_H, C.POINTER(fciqmc_system), C.POINTER(fciqmc_params), C.c_double,
-                                       C.c_int64, C.POINTER(C.c_int64)]),
+                                       C.c_double, C.c_int64, C.POINTER(C.c_int64)]),
     "fciqmc_server_tick": (C.c_int, [_H, C.c_int64, C.POINTER(C.c_int32)]),
     "fciqmc_server_poll": (C.c_int, [_H, C.c_int64, C.POINTER(fciqmc_request_status)]),
     "fciqmc_server_clock": (C.c_double, [_H]),
@@ -454,12 +454,12 @@ def fciqmc_server_create(mem_budget_bytes, max_active=64, stream=None):
     return Server(h)
 
 
-def fciqmc_server_submit(server, system, params, target_sigma, max_iters):
+def fciqmc_server_submit(server, system, params, target_sigma, max_iters, t_arrival=-1.0):
     s, keep = _system_struct(system)
     prm = _params_struct(params)
     rid = C.c_int64()
-    _check(_lib.fciqmc_server_submit(server.h, C.byref(s), C.byref(prm), float(target_sigma), int(max_iters),
-                                     C.byref(rid)))
+    _check(_lib.fciqmc_server_submit(server.h, C.byref(s), C.byref(prm), float(target_sigma), float(t_arrival),
+                                     int(max_iters), C.byref(rid)))
     return rid.value
 
 

@@ -1777,52 +1777,75 @@ int fciqmc_iter_stats_get(fciqmc_handle *h, int64_t first, int64_t count, fciqmc
 }  // extern "C"
 
 // ------------------------------------------------------------------ statistics
-// Flyvbjerg-Petersen blocking: repeatedly average neighbouring pairs; the
-// standard error at each level is sqrt(var/(n-1)); the first level whose
-// error agrees with the next within the error's own uncertainty is taken.
-static double blocking_sigma(std::vector<double> x)
+// Error analysis of the estimators (the paper gives none): Flyvbjerg-Petersen
+// blocking (J. Chem. Phys. 91, 461 (1989)) -- level k+1 holds the means of
+// neighbouring pairs of level k, an odd last element dropped, down to two
+// elements; the standard error of level k is sqrt(var_pop / (n_k - 1)) -- with
+// the block length chosen by the rule of Lee et al. (Phys. Rev. E 83, 066706
+// (2011)): the smallest level k with (2^k)^3 > 2 n_0 (SE_k / SE_0)^4 (the last
+// level if none qualifies; level 0 for a constant series).
+static std::vector<std::vector<double>> blocking_levels(const std::vector<double> &x)
 {
-    std::vector<std::pair<double, double>> lev;
-    while (x.size() >= 2) {
-        size_t n = x.size();
-        double mean = 0.0;
-        for (double v : x) mean += v;
-        mean /= (double)n;
-        double var = 0.0;
-        for (double v : x) var += (v - mean) * (v - mean);
-        var /= (double)n;
-        double se = std::sqrt(var / (double)(n - 1));
-        lev.push_back({se, se / std::sqrt(2.0 * (double)(n - 1))});
-        std::vector<double> y(n / 2);
-        for (size_t i = 0; i < n / 2; i++) y[i] = 0.5 * (x[2 * i] + x[2 * i + 1]);
-        x.swap(y);
+    std::vector<std::vector<double>> lev;
+    std::vector<double> y = x;
+    while (y.size() >= 2) {
+        std::vector<double> z(y.size() / 2);
+        for (size_t i = 0; i < z.size(); i++) z[i] = 0.5 * (y[2 * i] + y[2 * i + 1]);
+        lev.push_back(std::move(y));
+        y = std::move(z);
     }
-    if (lev.empty()) return NAN;
-    for (size_t k = 0; k + 1 < lev.size(); k++)
-        if (std::fabs(lev[k + 1].first - lev[k].first) < lev[k].second) return lev[k].first;
-    return lev.back().first;
+    return lev;
 }
 
-// ratio of the means of num and den with a delta-method error from the
-// blocking errors of both and their correlation
+static double mean_of(const std::vector<double> &y)
+{
+    double m = 0.0;
+    for (double v : y) m += v;
+    return m / (double)y.size();
+}
+
+// (co)variance of the means of two equally long levels, their elements taken as independent
+static double level_cov(const std::vector<double> &y, const std::vector<double> &z)
+{
+    const double my = mean_of(y), mz = mean_of(z);
+    double c = 0.0;
+    for (size_t i = 0; i < y.size(); i++) c += (y[i] - my) * (z[i] - mz);
+    return c / (double)y.size() / (double)(y.size() - 1);
+}
+
+static int optimal_level(const std::vector<std::vector<double>> &lev)
+{
+    if (lev.empty()) return -1;
+    const double n0 = (double)lev[0].size(), se0 = std::sqrt(level_cov(lev[0], lev[0]));
+    if (se0 == 0.0) return 0;
+    for (size_t k = 0; k < lev.size(); k++) {
+        const double q = std::sqrt(level_cov(lev[k], lev[k])) / se0;
+        const double b = std::ldexp(1.0, (int)k);
+        if (b * b * b > 2.0 * n0 * (q * q) * (q * q)) return (int)k;
+    }
+    return (int)lev.size() - 1;
+}
+
+static double blocking_sigma(const std::vector<double> &x)
+{
+    const auto lev = blocking_levels(x);
+    if (lev.empty()) return NAN;
+    const int k = optimal_level(lev);
+    return std::sqrt(level_cov(lev[k], lev[k]));
+}
+
+// ratio of the means of num and den; delta-method error
+// (s_n^2 - 2 r c + r^2 s_d^2) / mean(den)^2 with the variances and the
+// covariance of the two means at one level, the larger of the two optimal levels
 static void ratio_blocking(const std::vector<double> &num, const std::vector<double> &den, double *ratio, double *sigma)
 {
-    double mn = 0, md = 0;
-    for (size_t i = 0; i < num.size(); i++) { mn += num[i]; md += den[i]; }
-    mn /= num.size(); md /= den.size();
-    double sn = blocking_sigma(num), sd = blocking_sigma(den);
-    double cov = 0, vn = 0, vd = 0;
-    for (size_t i = 0; i < num.size(); i++) {
-        cov += (num[i] - mn) * (den[i] - md);
-        vn += (num[i] - mn) * (num[i] - mn);
-        vd += (den[i] - md) * (den[i] - md);
-    }
-    double rho = (vn > 0 && vd > 0) ? cov / std::sqrt(vn * vd) : 0.0;
-    double r = mn / md;
-    double rel = (mn != 0.0) ? (sn / mn) * (sn / mn) + (sd / md) * (sd / md) - 2.0 * rho * sn * sd / (mn * md)
-                             : (sn / md) * (sn / md);
+    const double mn = mean_of(num), md = mean_of(den), r = mn / md;
     *ratio = r;
-    *sigma = mn != 0.0 ? std::fabs(r) * std::sqrt(std::max(rel, 0.0)) : std::sqrt(std::max(rel, 0.0));
+    const auto ln = blocking_levels(num), ld = blocking_levels(den);
+    if (ln.empty()) { *sigma = NAN; return; }
+    const int k = std::max(optimal_level(ln), optimal_level(ld));
+    const double vn = level_cov(ln[k], ln[k]), vd = level_cov(ld[k], ld[k]), c = level_cov(ln[k], ld[k]);
+    *sigma = std::sqrt(std::max(vn - 2.0 * r * c + r * r * vd, 0.0)) / std::fabs(md);
 }
 
 static int energy_impl(fciqmc_handle *h, fciqmc_stats *out)
@@ -2065,7 +2088,7 @@ int fciqmc_server_create(int64_t mem_budget_bytes, int32_t max_active, void *str
 double fciqmc_server_clock(fciqmc_server *srv) { return srv ? srv->now() : NAN; }
 
 static int server_submit_impl(fciqmc_server *srv, const fciqmc_system *sys, const fciqmc_params *params, double target_sigma,
-                         int64_t max_iters, int64_t *id)
+                              double t_arrival, int64_t max_iters, int64_t *id)
 {
     if (!srv || !sys || !params || !id || !(target_sigma > 0.0) || max_iters < 1) return FCIQMC_ERR_INVALID_ARG;
     if (params->replicas > 1) return FCIQMC_ERR_UNSUPPORTED;  // the server batches single runs
@@ -2085,19 +2108,24 @@ static int server_submit_impl(fciqmc_server *srv, const fciqmc_system *sys, cons
     r.est_bytes = estimate_bytes(r);
     r.st.state = 0;
     r.st.t_submit = srv->now();
+    r.st.t_arrival = (t_arrival >= 0.0) ? t_arrival : r.st.t_submit;  // NaN compares false: now
     r.st.energy = NAN;
     r.st.sigma = NAN;
     *id = r.id;
+    const double ta = r.st.t_arrival;
     srv->req[r.id] = std::move(r);
-    srv->queue.push_back(*id);
+    // queued in order of arrival (ties: order of submission)
+    auto pos = srv->queue.end();
+    while (pos != srv->queue.begin() && srv->req[*(pos - 1)].st.t_arrival > ta) --pos;
+    srv->queue.insert(pos, *id);
     return FCIQMC_OK;
 }
 
 int fciqmc_server_submit(fciqmc_server *srv, const fciqmc_system *sys, const fciqmc_params *params, double target_sigma,
-                         int64_t max_iters, int64_t *id)
+                         double t_arrival, int64_t max_iters, int64_t *id)
 {
     try {
-        return server_submit_impl(srv, sys, params, target_sigma, max_iters, id);
+        return server_submit_impl(srv, sys, params, target_sigma, t_arrival, max_iters, id);
     } catch (const std::bad_alloc &) {
         return fail(nullptr, FCIQMC_ERR_OUT_OF_MEMORY, "host allocation failed");
     } catch (...) {
@@ -2141,8 +2169,10 @@ static int server_tick_impl(fciqmc_server *srv, int64_t n_iter, int32_t *n_activ
     // 1. admission: first come, first served, by device memory
     int64_t used = 0;
     for (int64_t id : srv->running) used += (int64_t)srv->req[id].h->bytes;
+    const double now = srv->now();
     while (!srv->queue.empty() && (int)srv->running.size() < srv->max_active) {
         Request &r = srv->req[srv->queue.front()];
+        if (r.st.t_arrival > now) break;  // not arrived yet
         if (!srv->running.empty() && used + r.est_bytes > srv->budget) break;
         srv->queue.pop_front();
         fciqmc_system sys = r.sys;

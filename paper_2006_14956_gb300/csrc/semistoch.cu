@@ -97,57 +97,60 @@ __global__ void k_mark_d(const DevInst *__restrict__ I, int par, int nb)
 }
 
 // ------------------------------------------------------------------ per iteration
-// C_D(new) = C_D - tau (y - S C_D), y = sum_c H^D_rc C_D,c summed in column order; C_D of
-// the current parity (the other buffer receives the iteration's result, so a
-// repeated iteration starts from unchanged values)
-__global__ void k_semistoch(const DevInst *__restrict__ insts, int n_inst)
+// C_D(new) = C_D - tau (y - S C_D) with y_r = sum_c H^D_rc C_D,c: every
+// product is rounded to binary64, truncated toward zero to a multiple of
+// 2^-64, and the row's truncated products are summed exactly (128-bit fixed
+// point on the grid 2^-64) and rounded once.  The sum does not depend on
+// the order of its terms, so a warp shares a row: lane k takes the columns
+// k, k + 32, ... and the lanes' partial sums are joined by a shuffle tree.
+// Products of magnitude 2^48 or more (beyond what 2^14 of them can sum to
+// in 127 bits) raise the numeric error.  C_D of the current parity is read;
+// the other buffer receives the iteration's result, so a repeated iteration
+// starts from unchanged values.
+constexpr int SEMI_GRID = 64;
+__global__ void __launch_bounds__(256) k_semistoch(const DevInst *__restrict__ insts, int n_inst)
 {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarp = (gridDim.x * blockDim.x) >> 5;
     for (int ii = 0; ii < n_inst; ii++) {
         const DevInst &I = insts[ii];
         if (I.nd == 0) continue;
         if (*(volatile int *)&I.st->err) continue;
         const double S = I.st->S;
         const double *cur = I.dc_buf[I.st->parity];
-        for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < I.nd; r += gridDim.x * blockDim.x) {
-            // y = sum_c H_rc C_c in column order, eight terms at a time: the
-            // next eight terms' loads are issued before this eight's adds,
-            // which keep the order
-            double y = 0.0;
-            const long long q1 = I.drow[r + 1];
-            long long q = I.drow[r];
-            double v[8], x[8];
-            const bool full = q + 8 <= q1;
-            if (full) {
+        bool bad = false;
+        for (int r = gw; r < I.nd; r += nwarp) {
+            const long long q0 = I.drow[r], q1 = I.drow[r + 1];
+            i128 acc = 0;
+            // four terms per lane in flight: their loads issued before the adds
+            long long q = q0 + lane;
+            for (; q + 96 < q1; q += 128) {
+                double v[4], x[4];
 #pragma unroll
-                for (int k = 0; k < 8; k++) {
-                    v[k] = I.dval[q + k];
-                    x[k] = cur[I.dcol[q + k]];
+                for (int k = 0; k < 4; k++) {
+                    v[k] = __ldg(I.dval + q + 32 * k);
+                    x[k] = cur[__ldg(I.dcol + q + 32 * k)];
+                }
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const double p = v[k] * x[k];
+                    bad |= !abs_lt(p, 0x1p48);
+                    acc += to_fixed(p, SEMI_GRID);
                 }
             }
-            while (q + 8 <= q1) {
-                double vn[8], xn[8];
-                const bool more = q + 16 <= q1;
-                if (more) {
-#pragma unroll
-                    for (int k = 0; k < 8; k++) {
-                        vn[k] = I.dval[q + 8 + k];
-                        xn[k] = cur[I.dcol[q + 8 + k]];
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < 8; k++) y = y + v[k] * x[k];
-                q += 8;
-                if (!more) break;
-#pragma unroll
-                for (int k = 0; k < 8; k++) {
-                    v[k] = vn[k];
-                    x[k] = xn[k];
-                }
+            for (; q < q1; q += 32) {
+                const double p = __ldg(I.dval + q) * cur[__ldg(I.dcol + q)];
+                bad |= !abs_lt(p, 0x1p48);
+                acc += to_fixed(p, SEMI_GRID);
             }
-            for (; q < q1; q++) y = y + I.dval[q] * cur[I.dcol[q]];
-            const double c = cur[r];
-            I.dc_new[r] = c - I.tau * (y - S * c);
+            for (int m = 16; m >= 1; m >>= 1) acc += shfl_xor_i128(acc, m);
+            if (lane == 0) {
+                const double y = fixed_to_double(acc, SEMI_GRID);
+                const double c = cur[r];
+                I.dc_new[r] = c - I.tau * (y - S * c);
+            }
         }
+        if (bad) atomicOr(&I.st->err, ERRB_NUMERIC);
     }
 }
 
@@ -161,12 +164,11 @@ static int sms()
 
 void launch_semistoch(const DevInst *dinst, int n_inst, int max_nd, cudaStream_t s)
 {
-    // one thread per row in blocks of 64, so that the rows spread over every SM
-    // (1e4 rows in blocks of 256 left three quarters of the SMs idle)
-    int blocks = (max_nd + 63) / 64;
-    if (blocks > sms() * 16) blocks = sms() * 16;
+    // one warp per row, eight rows per block, at most eight blocks per SM
+    int blocks = (max_nd + 7) / 8;
+    if (blocks > sms() * 8) blocks = sms() * 8;
     if (blocks < 1) blocks = 1;
-    k_semistoch<<<blocks, 64, 0, s>>>(dinst, n_inst);
+    k_semistoch<<<blocks, 256, 0, s>>>(dinst, n_inst);
 }
 
 void launch_abs_hist(const DevInst *dinst, int par, int nb, int shift, u64 prefix, unsigned *hist, cudaStream_t s)

@@ -258,6 +258,32 @@ def test_energy_within_3sigma_of_exact_diagonalisation():
     assert en["e_proj_sigma"] < 0.05
 
 
+def test_energy_statistics_match_the_oracle_estimator():
+    """fciqmc_energy's E_proj, shift and their blocking errors (host code of
+    the library) against the oracle's estimator applied to the same rows of
+    the run's statistics: the same blocking level must be chosen, so the
+    means agree to rounding and the errors to the rounding of the variance
+    sums."""
+    fq = _fq()
+    sysd, params = workloads.config_hubbard_ring()
+    s = oracle.system_from_workload(sysd)
+    e0, _, _ = s.exact_ground_state()
+    g = fq.fciqmc_create(sysd, dict(params, initial_shift=e0 + 0.3, initial_walkers=500.0, seed=5))
+    fq.fciqmc_step(g, 3000)
+    en = fq.fciqmc_energy(g)
+    st = fq.fciqmc_iter_stats_get(g)
+    sel = st["iteration"] >= en["equil_start"]
+    assert en["n_samples"] == int(np.sum(sel)) > 1000
+    r, sg = oracle.ratio_estimate(st["e_num"][sel], st["e_den"][sel])
+    eref = s.eref
+    np.testing.assert_allclose(en["e_proj_mean"] - eref, r, rtol=1e-12)
+    np.testing.assert_allclose(en["e_proj_sigma"], sg, rtol=1e-9)
+    ms, ss, _ = oracle.blocking(st["shift"][sel])
+    np.testing.assert_allclose(en["shift_mean"] - eref, ms, rtol=1e-12)
+    np.testing.assert_allclose(en["shift_sigma"], ss, rtol=1e-9)
+    assert 0.0 < en["e_proj_sigma"] < 0.05
+
+
 def test_full_size_sampled_parity_abinitio_24():
     """At the full 1e6-walker size of the 24-orbital system, in the launch
     configuration the benchmark times: the GPU state after equilibration is

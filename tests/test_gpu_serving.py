@@ -43,7 +43,7 @@ def test_requests_in_the_mix_equal_alone():
             a, b = st[k_srv], en[k_alone]
             assert (np.isnan(a) and np.isnan(b)) or a == b, (k_srv, a, b)
         assert st["attempts"] == en["attempts_total"]
-        assert st["t_done"] >= st["t_start"] >= st["t_submit"]
+        assert st["t_done"] >= st["t_start"] >= st["t_submit"] == st["t_arrival"]
 
 
 def test_admission_respects_the_memory_budget():
@@ -89,3 +89,32 @@ def test_auto_time_step_bounds_spawning():
     h = fq.fciqmc_create(s, p)
     sm = fq.fciqmc_ref_offdiag_sum(h)
     assert sm > 0 and fq.fciqmc_tau(h) == 0.5 / sm
+
+
+def test_arrival_while_others_run_is_admitted_at_the_next_tick():
+    """Continuous batching: a request that arrives while another is on the
+    GPU joins the running batch at the next scheduling round, without waiting
+    for the running request to finish, and its latency counts from its
+    arrival time; a request with a future arrival time is not admitted early."""
+    fq = _fq()
+    mix = _mix()
+    srv = fq.fciqmc_server_create(8 << 30, max_active=8)
+    first = fq.fciqmc_server_submit(srv, *mix[0], target_sigma=1e-12, max_iters=2000)
+    fq.fciqmc_server_tick(srv, 20)
+    assert fq.fciqmc_server_poll(srv, first)["state_name"] == "running"
+    now = fq.fciqmc_server_clock(srv)
+    second = fq.fciqmc_server_submit(srv, *mix[1], target_sigma=1e-12, max_iters=100, t_arrival=now)
+    later = fq.fciqmc_server_submit(srv, *mix[2], target_sigma=1e-12, max_iters=100, t_arrival=now + 3600.0)
+    fq.fciqmc_server_tick(srv, 20)
+    s1, s2, s3 = (fq.fciqmc_server_poll(srv, i) for i in (first, second, later))
+    assert s1["state_name"] == "running" and s2["state_name"] == "running", (s1, s2)
+    assert s3["state_name"] == "queued"
+    assert s2["t_arrival"] == now and s2["t_start"] >= now
+    assert s1["iterations"] == 40 and s2["iterations"] == 20
+    for _ in range(10):
+        fq.fciqmc_server_tick(srv, 20)
+    s2 = fq.fciqmc_server_poll(srv, second)
+    assert s2["state_name"] == "max_iters" and s2["iterations"] == 100
+    assert s2["t_done"] > s2["t_start"] >= s2["t_arrival"]
+    assert fq.fciqmc_server_poll(srv, first)["state_name"] == "running"
+    assert fq.fciqmc_server_poll(srv, later)["state_name"] == "queued"

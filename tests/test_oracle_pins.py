@@ -356,6 +356,54 @@ def test_semistochastic_whole_space_is_power_method():
     assert abs(num / den - e0) < 1e-9
 
 
+def test_semistochastic_row_sum_is_exact_sum_of_truncated_products():
+    """Reading R13: y_k = sum_c H^D_kc C_c with every binary64 product
+    truncated toward zero to a multiple of 2^-64, summed exactly and rounded
+    once to nearest-even, against exact rational arithmetic (fractions).  The
+    amplitudes span 1e-25 .. 1e8 so that products fall on both sides of
+    2^-64 and the in-order binary64 sum, or the untruncated exact sum, differ
+    from it in some rows."""
+    sysd = workloads.small_abinitio(8, 3, 3, seed=5)
+    s = oracle.system_from_workload(sysd)
+    dets = s.determinants()
+    r = oracle.Run(s, tau=0.001, seed=3, target_walkers=1e12, semistoch_size=300, semistoch_start=1)
+    c0 = np.linspace(1.0, 50.0, len(dets))
+    r.import_state([d[0] for d in dets], [d[1] for d in dets], c0, 1, 0.0, vary=1, shift_start=0, cnt=0,
+                   nw_last=0)
+    r.step(1)
+    csr = r.semistoch_csr()
+    nd = csr["rowptr"].size - 1
+    assert nd == 300 and csr["val"].size > 3000
+    rng = np.random.default_rng(11)
+    two64 = 2 ** 64
+
+    def check(cD):
+        y = r.semistoch_rows(cD)
+        differs_seq = differs_full = 0
+        for k in range(nd):
+            q0, q1 = csr["rowptr"][k], csr["rowptr"][k + 1]
+            p = csr["val"][q0:q1] * cD[csr["col"][q0:q1]]   # binary64 products
+            exact = Fraction(0)
+            full = Fraction(0)
+            for v in p:
+                f = Fraction(float(v))
+                t = Fraction(math.floor(abs(f) * two64), two64)
+                exact += t if f >= 0 else -t
+                full += f
+            assert np.float64(y[k]).view(np.uint64) == np.float64(float(exact)).view(np.uint64), k
+            seq = 0.0
+            for v in p:
+                seq = seq + float(v)
+            differs_seq += seq != float(exact)
+            differs_full += float(full) != float(exact)
+        return differs_seq, differs_full
+
+    # amplitudes over 33 decades: in-order binary64 sums differ from the exact ones
+    assert check(rng.normal(size=nd) * 10.0 ** rng.uniform(-25.0, 8.0, size=nd))[0] > 0
+    # amplitudes near 2^-64 / |H|: the truncation decides the rounded sums
+    assert check(rng.normal(size=nd) * 1e-19)[1] > 0
+
+
 # ----------------------------------------------------------------- full runs
 @pytest.mark.parametrize("which", ["hubbard", "abinitio"])
 def test_fciqmc_energy_within_3sigma_of_exact(which):
