@@ -1,12 +1,14 @@
 """Benchmark of the GB300 initiator-FCIQMC projector iteration.
 
 One step = one full projector iteration (spawning, death, annihilation with
-the initiator rule, shift update, E_proj reduction) over a resident walker
-list.  Default workload: the 24-orbital, 6+6-electron synthetic ab initio
-system (96 Cholesky vectors, uniform generator, initiator threshold 3) at
-about 1e6 walkers.  Prints one JSON line.
+the initiator rule, semi-stochastic projection, shift update, E_proj
+reduction) over a resident walker list.  Default workload: the 50-orbital,
+10+10-electron synthetic ab initio system (200 Cholesky vectors, uniform
+generator, initiator threshold 3, deterministic space of 1e4 determinants)
+at about 1e8 walkers.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+                  [--workload abinitio50|abinitio24|batch|serving]
 """
 import argparse
 import ctypes
@@ -31,17 +33,16 @@ METRIC = "spawn attempts/s + annihilated walkers/s; p50/p99 time-to-sigma(E)<1 m
 # number; 0.5 / 2412.4 rounded down gives 2e-4.
 TAU = 2e-4
 TARGET = 6.25e5
-EQUIL_ITERS = 300
 E2E_STEPS = 40
 
 
-def workload_params(seed_offset=0, workload="abinitio24", generator="uniform"):
+def workload_params(seed_offset=0, workload="abinitio50", generator="uniform"):
     sysd, prm = _workload_params(seed_offset, workload)
     prm["generator"] = 1 if generator == "pchb" else 0
     return sysd, prm
 
 
-def _workload_params(seed_offset=0, workload="abinitio24"):
+def _workload_params(seed_offset=0, workload="abinitio50"):
     if workload == "abinitio50":
         # 50 orbitals, 10+10 electrons, 200 Cholesky vectors: sum_j |H_ref,j| = 39309 Eh,
         # so tau = 0.5 / 39309 rounded down = 1.25e-5 (the prescribed 5e-4 gives 19.7)
@@ -101,7 +102,8 @@ class ClockSampler:
 
 
 def oracle_rate(sysd, prm, state, shift, iters):
-    """The CPU oracle, as it stands, on a bounded sample of the workload."""
+    """The CPU oracle, as it stands, on a bounded sample of the workload:
+    `iters` iterations from the given (sampled) state, one host core."""
     import oracle
     s = oracle.system_from_workload(sysd)
     r = oracle.Run(s, **prm)
@@ -117,6 +119,15 @@ def oracle_rate(sysd, prm, state, shift, iters):
     return att / el, ann / el, att, el
 
 
+def key_sample(state, every):
+    """The determinants whose key hash is 0 mod `every` (a uniform sample that
+    always holds the same determinants of a given list)."""
+    h = (state["alpha"] * np.uint64(0x9E3779B97F4A7C15)) ^ (state["beta"] * np.uint64(0xC2B2AE3D27D4EB4F))
+    h ^= h >> np.uint64(29)
+    sel = (h % np.uint64(every)) == 0
+    return {k: v[sel] for k, v in state.items()}
+
+
 def aggregate_ranks(t_dev, attempts, annihilated, dist, device):
     """Replicas (one independent run per rank): the job's time is the slowest
     rank's, its work the sum over ranks."""
@@ -129,13 +140,16 @@ def aggregate_ranks(t_dev, attempts, annihilated, dist, device):
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the oracle on the host cores (rank 0 only)."""
+    """--impl reference: the oracle on the host cores (rank 0 only), on the
+    benchmark's workload from a bounded walker population."""
     if rank != 0:
         return None
-    sysd, prm = workload_params(generator=args.generator)
-    # bounded sample: the same system and parameters with 2e4 initial walkers,
-    # so that one oracle iteration takes a fraction of a second
-    prm = dict(prm, initial_walkers=2e4, target_walkers=2e4)
+    sysd, prm = workload_params(workload=args.workload if args.workload.startswith("abinitio") else "abinitio50",
+                                generator=args.generator)
+    # bounded sample: the same system and parameters (semi-stochastic space
+    # off) from 2e5 walkers, so that one oracle iteration takes a fraction of
+    # a second
+    prm = dict(prm, initial_walkers=2e5, target_walkers=2e5, semistoch_size=0)
     import oracle
     r = oracle.Run(oracle.system_from_workload(sysd), **prm)
     r.step(args.warmup)
@@ -150,11 +164,18 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "annihilated_per_s": ann / el,
-            "config": {"workload": "abinitio-24orb-6a6b (synthetic, 96 Cholesky vectors), oracle sample",
-                       "tau": prm["tau"], "initiator_threshold": 3, "walkers": prm["target_walkers"]},
+            "config": {"workload": WORKLOAD_NAMES[args.workload if args.workload in WORKLOAD_NAMES else "abinitio50"]
+                       + ", oracle sample", "tau": prm["tau"], "initiator_threshold": 3, "walkers": 2e5,
+                       "semistoch": "off in the sample"},
             "cpu_baseline": {"value": value, "unit": "spawn attempts/s", "cores": 1, "kind": "oracle",
-                             "sample": "%d oracle iterations from 2e4 walkers on the reference" % args.steps},
+                             "sample": "%d oracle iterations from 2e5 walkers (semi-stochastic space off)" % args.steps},
             "e2e": {"value": value, "unit": "spawn attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+WORKLOAD_NAMES = {
+    "abinitio50": "abinitio-50orb-10a10b (synthetic: 200 Cholesky vectors, seed 4), D = 1e4, ~1e8 walkers",
+    "abinitio24": "abinitio-24orb-6a6b (synthetic: 96 Cholesky vectors, seed 2), ~1e6 walkers",
+}
 
 
 def run_batch(args):
@@ -288,8 +309,9 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="abinitio24", choices=["abinitio24", "abinitio50", "batch", "serving"])
-    ap.add_argument("--equil", type=int, default=EQUIL_ITERS)
+    ap.add_argument("--workload", default="abinitio50", choices=["abinitio50", "abinitio24", "batch", "serving"])
+    ap.add_argument("--equil", type=int, default=200,
+                    help="untimed iterations after E_proj's equilibration start (shift start + 500)")
     ap.add_argument("--generator", default="uniform", choices=["uniform", "pchb"],
                     help="double excitations: uniform, or pre-computed heat-bath alias tables")
     ap.add_argument("--requests", type=int, default=200)
@@ -323,8 +345,17 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     sysd, prm = workload_params(seed_offset=rank, workload=args.workload, generator=args.generator)
+    big = args.workload == "abinitio50"
     h = fq.fciqmc_create(sysd, prm)
-    fq.fciqmc_step(h, args.equil)                        # growth / equilibration, untimed
+    # growth and equilibration, untimed: until E_proj has `--equil` samples
+    # after its equilibration start (the shift's start + 500 iterations)
+    n_grow = 0
+    while True:
+        fq.fciqmc_step(h, 50)
+        n_grow += 50
+        en = fq.fciqmc_energy(h)
+        if en["n_samples"] >= args.equil or n_grow >= 5000:
+            break
     fq.fciqmc_step(h, args.warmup)                       # warm-up steps
     stream = torch.cuda.ExternalStream(fq.fciqmc_stream(h))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
@@ -351,6 +382,7 @@ def main():
         dist.barrier()
     dev_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_dev = sum(dev_ms) / 1e3
+    launches_per_iter = fq.fciqmc_graph_kernels(h)
     st = fq.fciqmc_iter_stats_get(h)
     sel = slice(n_before, n_before + args.steps)
     attempts = float(np.sum(st["attempts"][sel]))
@@ -360,6 +392,7 @@ def main():
     if dist:
         t_dev, attempts, annihilated = aggregate_ranks(t_dev, attempts, annihilated, dist, "cuda")
     value = attempts / t_dev
+    en = fq.fciqmc_energy(h)
 
     # ---- per-kernel device times for the roofline (events around each launch)
     fq.fciqmc_set_profiling(h, True)
@@ -381,7 +414,9 @@ def main():
            "k_annihilate": float(np.mean(24.0 * (n_in + n_sp + n_out)))}
     tms = {"k_spawn": kt["spawn"], "k_annihilate": kt["annihilate"]}
     b_iter = float(np.mean(24.0 * n_in + 24.0 * n_out + 48.0 * n_sp))
-    peaks = {}
+    if big:
+        nnz = fq.fciqmc_semistoch_info(h)["nnz"]
+        b_iter += 12.0 * nnz + 16.0 * 1e4
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             peaks = json.load(f)
@@ -390,7 +425,7 @@ def main():
         peak, peak_src = 6800.0, "fallback"
     traffic_rec = {}
     try:
-        with open(os.path.join(ROOT, "profiles", "dram_traffic_abinitio24.json")) as f:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic_%s.json" % args.workload)) as f:
             tr = json.load(f)
         import hashlib
         src = open(os.path.join(ROOT, "paper_2006_14956_gb300", "csrc", "kernels.cu"), "rb").read()
@@ -403,8 +438,11 @@ def main():
 
     def roof(k):
         ach = alg[k] / (tms[k] * 1e-3) / 1e9
-        return {"kernel": k, "achieved": ach, "frac": ach / peak,
-                "traffic": (traffic_rec.get(k) or {}).get("dram_bytes_per_launch"),
+        rec = traffic_rec.get(k) or {}
+        # DRAM bytes were captured on a smaller list; they scale with the records a launch processes
+        units = float(np.mean(n_in + n_sp))
+        tr_b = rec["dram_bytes_per_unit"] * units if "dram_bytes_per_unit" in rec else rec.get("dram_bytes_per_launch")
+        return {"kernel": k, "achieved": ach, "frac": ach / peak, "traffic": tr_b,
                 "alg_bytes_per_launch": alg[k], "launch_ms": tms[k]}
 
     dominant = max(tms, key=tms.get)  # the kernel with the longest launches
@@ -412,17 +450,18 @@ def main():
     roofline = {"bound": "hbm", "peak": peak, "peak_source": peak_src + " hbm_gbs", "unit": "GB/s", **roof(dominant),
                 "iteration_frac": b_iter / (t_dev / args.steps) / 1e9 / peak, "other": roof(other)}
 
-    big = args.workload == "abinitio50"
-    # ---- end to end through the public API: restart from a host checkpoint
+    # ---- end to end through the public API: restart from a pinned host checkpoint
     state = fq.fciqmc_export_state(h)
-    if big:  # the oracle and the restart job take a bounded sample of the list (first 2e5 keys)
-        state = {k: v[:200000] for k, v in state.items()}
     shift = fq.fciqmc_export_shift(h)
-    pinned = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in state.items()}
+    keep = ("alpha", "beta", "c")
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(state[k])).pin_memory() for k in keep}
     host_state = {k: v.numpy() for k, v in pinned.items()}
+    # the restarted run selects its deterministic space from the imported list
+    prm2 = dict(prm, semistoch_start=shift["iteration"] - shift["shift_start"]) if big else prm
+    del h
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h2 = fq.fciqmc_create(sysd, dict(prm, semistoch_size=0) if big else prm)
+    h2 = fq.fciqmc_create(sysd, prm2)
     t1 = time.perf_counter()
     fq.fciqmc_import_state(h2, host_state["alpha"], host_state["beta"], host_state["c"], shift["iteration"],
                            shift["S"], shift["vary"], shift["shift_start"], shift["cnt"], shift["nw_last"])
@@ -430,24 +469,30 @@ def main():
     fq.fciqmc_step(h2, E2E_STEPS)
     t3 = time.perf_counter()
     out_state = fq.fciqmc_export_state(h2)
-    en = fq.fciqmc_energy(h2)
+    en2 = fq.fciqmc_energy(h2)
     e2e_el = time.perf_counter() - t0
     e2e_phases = {"create": t1 - t0, "import": t2 - t1, "steps": t3 - t2, "export_energy": t0 + e2e_el - t3}
     st2 = fq.fciqmc_iter_stats_get(h2)
     e2e_att = float(np.sum(st2["attempts"][-E2E_STEPS:]))
-    # integrals and the checkpoint's keys and amplitudes
-    h2d = sysd["h1"].nbytes + sysd["eri"].nbytes + host_state["alpha"].nbytes * 2 + host_state["c"].nbytes
+    # integrals and the checkpoint's keys and amplitudes in; the final list and statistics out
+    h2d = sysd["h1"].nbytes + sysd["eri"].nbytes + sum(host_state[k].nbytes for k in keep)
     d2h = sum(v.nbytes for v in out_state.values()) + E2E_STEPS * ctypes.sizeof(fq.fciqmc_iter_stats)
-    del h2
+    assert np.isfinite(en2["nw"])
+    del h2, pinned, host_state, out_state
 
-    # ---- CPU baseline: the oracle on the same equilibrated state, bounded sample
+    # ---- CPU baseline: the oracle on a key-hash sample of the same state, bounded
     cpu = None
-    if rank == 0 and world >= 1:
-        o_att_rate, o_ann_rate, o_att, o_el = oracle_rate(sysd, dict(prm, semistoch_size=0) if big else prm, state,
-                                                          shift, 1)
+    if rank == 0:
+        every = 16 if big else 1
+        sample = key_sample({k: state[k] for k in keep}, every) if every > 1 else {k: state[k] for k in keep}
+        iters = 3 if big else 1
+        o_att_rate, o_ann_rate, o_att, o_el = oracle_rate(sysd, dict(prm, semistoch_size=0), sample, shift, iters)
         cpu = {"value": o_att_rate, "unit": "spawn attempts/s", "cores": 1, "kind": "oracle",
-               "sample": "1 oracle iteration (%.3g attempts, %.1f s) from the GPU state at %.3g walkers" %
-                         (o_att, o_el, nw_mean)}
+               "sample": "%d oracle iteration(s) (%.3g attempts, %.1f s) from %s of the GPU state at %.3g walkers "
+                         "(semi-stochastic space off)" %
+                         (iters, o_att, o_el, ("a 1/%d key-hash sample (%d determinants)" % (every, sample["c"].size))
+                          if every > 1 else "all", nw_mean)}
+    del state
 
     if rank == 0:
         out = {
@@ -455,29 +500,32 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "annihilated_per_s": annihilated / t_dev,
-            "config": {"workload": ("abinitio-24orb-6a6b (synthetic: 96 Cholesky vectors, seed 2)"
-                                    if args.workload == "abinitio24" else
-                                    "abinitio-50orb-10a10b (synthetic: 200 Cholesky vectors, seed 4), D = 1e4"),
+            "config": {"workload": WORKLOAD_NAMES[args.workload],
                        "generator": ("uniform" if args.generator == "uniform" else
                                      "pre-computed heat-bath doubles") + ", p_single 0.1",
                        "initiator_threshold": 3, "tau": prm["tau"],
-                       "tau_note": ("prescribed 1e-3 exceeds 1/sum_j|H_ref,j| (2412 Eh): walker number uncontrollable"
-                                    if args.workload == "abinitio24" else
-                                    "prescribed 5e-4 exceeds 1/sum_j|H_ref,j| (39309 Eh): walker number uncontrollable"),
+                       "tau_note": ("prescribed 5e-4 exceeds 1/sum_j|H_ref,j| (39309 Eh): walker number uncontrollable"
+                                    if big else
+                                    "prescribed 1e-3 exceeds 1/sum_j|H_ref,j| (2412 Eh): walker number uncontrollable"),
+                       "semistoch_size": prm.get("semistoch_size", 0),
                        "walkers_mean": nw_mean, "dets_mean": ndet_mean, "l2": "flushed (256 MB write) between steps",
+                       "untimed_iterations_before": n_grow + args.warmup,
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline,
             "kernel_ms": kt,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_att / e2e_el, "unit": "spawn attempts/s", "h2d_bytes_per_step": h2d / E2E_STEPS,
                     "d2h_bytes_per_step": d2h / E2E_STEPS,
-                    "job": "create + import %s checkpoint + %d steps + export + energy" %
-                           ("2e5-determinant sample" if big else "1e6-walker", E2E_STEPS),
+                    "job": "create + import the %.3g-determinant checkpoint from pinned host memory + %d steps + "
+                           "export + energy" % (ndet_mean, E2E_STEPS),
                     "phases_s": e2e_phases},
-            "gpu_launches": args.steps * (7 if prm.get("semistoch_size", 0) else 6),
+            "gpu_launches": args.steps * launches_per_iter,
+            "gpu_launches_per_step": launches_per_iter,
             "wall_s_timed": wall,
             "clocks": clk.summary(),
-            "energy": {"e_proj_mean": en["e_proj_mean"], "e_proj_sigma": en["e_proj_sigma"], "shift": en["shift"]},
+            "energy": {"e_proj_mean": en["e_proj_mean"], "e_proj_sigma": en["e_proj_sigma"],
+                       "e_proj_samples": en["n_samples"], "shift_mean": en["shift_mean"],
+                       "shift_sigma": en["shift_sigma"], "eref": en["eref"]},
         }
         print(json.dumps(out), flush=True)
     if dist:

@@ -363,7 +363,10 @@ int64_t fciqmc_pchb_table(fciqmc_handle *h, int32_t same_spin, int32_t i, int32_
  * partial sums and the integral exponent range); every GPU that loads the
  * library keeps it until the process exits.  The first call on a device looks
  * up that array's device address (cudaGetSymbolAddress) with the device
- * current; make that first call before any stream capture.  All calls share
+ * current; make that first call before any stream capture.  The address is
+ * kept for the rest of the process: after cudaDeviceReset, or anything else
+ * that destroys the device's primary context, it is stale, and the entry
+ * point must not be called again on that device.  All calls share
  * the array: calls that overlap on the GPU race and must not be issued
  * concurrently.  Synchronises the stream before returning.  Errors:
  * FCIQMC_ERR_INVALID_ARG for bad sizes/pointers, a reference with the wrong
@@ -442,6 +445,17 @@ int fciqmc_kernel_times(fciqmc_handle *h, double out[6]);
  * buffers: out[0] buckets, out[1] main capacity per bucket, out[2] spawn
  * capacity per bucket, out[3] device bytes allocated. */
 int fciqmc_layout(fciqmc_handle *h, int64_t out[4]);
+
+/* Kernel launches in one iteration of the handle's captured CUDA graph (a
+ * count of the graph's kernel nodes, taken when the graph was captured;
+ * 0 before the first step, -1 for a NULL handle).  One fciqmc_step of n
+ * iterations replays the graph n times. */
+int32_t fciqmc_graph_kernels(fciqmc_handle *h);
+
+/* Size of the semi-stochastic space D (Sec. III) once it has been selected
+ * (0 before), and in *nnz (may be NULL) the stored entries of H^D, whose CSR
+ * the projection reads every iteration; FCIQMC_ERR_INVALID_ARG for NULL. */
+int64_t fciqmc_semistoch_info(fciqmc_handle *h, int64_t *nnz);
 
 #ifdef __cplusplus
 }

@@ -133,6 +133,8 @@ _SIGS = {
     "fciqmc_free_system": (None, [C.POINTER(fciqmc_system)]),
     "fciqmc_ref_offdiag_sum_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                                  C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p]),
+    "fciqmc_graph_kernels": (C.c_int32, [_H]),
+    "fciqmc_semistoch_info": (C.c_int64, [_H, C.POINTER(C.c_int64)]),
     "fciqmc_server_create": (C.c_int, [C.c_int64, C.c_int32, C.c_void_p, C.POINTER(_H)]),
     "fciqmc_server_submit": (C.c_int, [_H, C.POINTER(fciqmc_system), C.POINTER(fciqmc_params), C.c_double,
                                        C.c_double, C.c_int64, C.POINTER(C.c_int64)]),
@@ -375,6 +377,20 @@ def fciqmc_layout(handle):
     out = (C.c_int64 * 4)()
     _check(_lib.fciqmc_layout(handle.h, out), handle.h)
     return dict(buckets=out[0], cap_main=out[1], cap_spawn=out[2], device_bytes=out[3])
+
+
+def fciqmc_graph_kernels(handle):
+    """Kernel launches per iteration in the handle's captured graph."""
+    return int(_lib.fciqmc_graph_kernels(handle.h))
+
+
+def fciqmc_semistoch_info(handle):
+    """dict(nd, nnz): size of the deterministic space and stored entries of H^D."""
+    nnz = C.c_int64()
+    nd = _lib.fciqmc_semistoch_info(handle.h, C.byref(nnz))
+    if nd < 0:
+        _check(int(nd), handle.h)
+    return dict(nd=int(nd), nnz=int(nnz.value))
 
 
 def fciqmc_ref_offdiag_sum(handle):

@@ -53,6 +53,7 @@ struct fciqmc_handle {
     int *dunit = nullptr;         // unit_start {0, nb}
     IterState *dstate = nullptr;
     cudaGraphExec_t graph = nullptr;
+    int graph_kernels = 0;  // kernel nodes of the captured iteration
     bool profiling = false;
     double ktime[6] = {0, 0, 0, 0, 0, 0};  // spawn, heavy, annihilate, finalize, semistoch, new-determinant H_jj
     // layout
@@ -282,7 +283,8 @@ static int enqueue_iteration(fciqmc_handle *h, cudaEvent_t *ev)
     if (ev) cudaEventRecord(ev[2], h->stream);
     if (h->nd > 0) launch_semistoch(h->dinst, 1, h->nd, h->stream);
     if (ev) cudaEventRecord(ev[3], h->stream);
-    cudaError_t e = launch_annihilate(h->dinst, h->dunit, 1, units, h->stream);
+    cudaError_t e = launch_annihilate(h->dinst, h->dunit, 1, units, h->hi.side || h->hi.adaptive,
+                                      staged_annihilation_fits(h->hi), h->stream);
     if (e != cudaSuccess) return fail(h, FCIQMC_ERR_CUDA, std::string("annihilation launch: ") + cudaGetErrorString(e));
     launch_annihilate_big(h->dinst, 1, h->stream);
     if (ev) cudaEventRecord(ev[4], h->stream);
@@ -291,6 +293,21 @@ static int enqueue_iteration(fciqmc_handle *h, cudaEvent_t *ev)
     launch_finalize(h->dinst, 1, h->stream);
     if (ev) cudaEventRecord(ev[6], h->stream);
     return FCIQMC_OK;
+}
+
+// kernel launches recorded in a captured graph
+static int count_kernel_nodes(cudaGraph_t g)
+{
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return 0;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+    int k = 0;
+    for (size_t i = 0; i < n; i++) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) k++;
+    }
+    return k;
 }
 
 static int capture_graph(fciqmc_handle *h)
@@ -302,6 +319,7 @@ static int capture_graph(fciqmc_handle *h)
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (rc) return rc;
     if (e != cudaSuccess) return fail(h, FCIQMC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    h->graph_kernels = count_kernel_nodes(g);
     e = cudaGraphInstantiate(&h->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(h, FCIQMC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
@@ -552,20 +570,26 @@ static int build_semistochastic(fciqmc_handle *h)
     int hb = 1;
     while ((1LL << hb) < 2 * nd) hb++;
     std::vector<u64> tabk((size_t)2 << hb, 0ULL);
-    for (const auto &k : sel) {
+    std::vector<int> tabi((size_t)1 << hb, -1);  // position of the key in D (ascending key order)
+    for (size_t q = 0; q < sel.size(); q++) {
+        const auto &k = sel[q];
         u64 sl = det_hash_host(k.x, k.y) & (((u64)1 << hb) - 1);
         while (tabk[2 * sl] || tabk[2 * sl + 1]) sl = (sl + 1) & (((u64)1 << hb) - 1);
         tabk[2 * sl] = k.x;
         tabk[2 * sl + 1] = k.y;
+        tabi[sl] = (int)q;
     }
     ulonglong2 *dkey = (ulonglong2 *)dev_alloc(h, (size_t)nd * sizeof(ulonglong2));
     u64 *dtab = (u64 *)dev_alloc(h, tabk.size() * sizeof(u64));
+    int *dtabi = (int *)dev_alloc(h, tabi.size() * sizeof(int));
     double *dcn = (double *)dev_alloc(h, (size_t)nd * sizeof(double));
     double *dcc = (double *)dev_alloc(h, (size_t)nd * sizeof(double));
     double *dcc2 = (double *)dev_alloc(h, (size_t)nd * sizeof(double));
-    if (!dkey || !dtab || !dcn || !dcc || !dcc2) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (D)");
+    if (!dkey || !dtab || !dtabi || !dcn || !dcc || !dcc2)
+        return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (D)");
     CUDA_TRY(h, cudaMemcpy(dkey, sel.data(), (size_t)nd * sizeof(ulonglong2), cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemcpy(dtab, tabk.data(), tabk.size() * sizeof(u64), cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(dtabi, tabi.data(), tabi.size() * sizeof(int), cudaMemcpyHostToDevice));
     long long *rowptr = nullptr, nnz = 0;
     int *dcol = nullptr;
     double *dval = nullptr;
@@ -573,7 +597,7 @@ static int build_semistochastic(fciqmc_handle *h)
     if (rcs) return rcs;
     I.nd = (int)nd; I.dkey = dkey; I.drow = rowptr; I.dcol = dcol; I.dval = dval; I.dc_new = dcn;
     I.dc_buf[0] = dcc; I.dc_buf[1] = dcc2;
-    I.dhash_keys = dtab; I.dhash_bits = hb;
+    I.dhash_keys = dtab; I.dhash_idx = dtabi; I.dhash_bits = hb;
     int rc2 = upload_inst(h);
     if (rc2) return rc2;
     launch_mark_d(h->dinst, par, nbk, h->stream);
@@ -1063,6 +1087,15 @@ int fciqmc_layout(fciqmc_handle *h, int64_t out[4])
     if (!h || !out) return FCIQMC_ERR_INVALID_ARG;
     out[0] = 1LL << h->bb; out[1] = CAP_M; out[2] = h->hi.cap_s; out[3] = (int64_t)h->bytes;
     return FCIQMC_OK;
+}
+
+int32_t fciqmc_graph_kernels(fciqmc_handle *h) { return h ? h->graph_kernels : -1; }
+
+int64_t fciqmc_semistoch_info(fciqmc_handle *h, int64_t *nnz)
+{
+    if (!h) return FCIQMC_ERR_INVALID_ARG;
+    if (nnz) *nnz = h->nd > 0 ? (int64_t)h->nnz : 0;
+    return h->nd;
 }
 
 static int step_to(fciqmc_handle *h, long long target_iter);
@@ -1679,7 +1712,12 @@ static int step_batch_impl(fciqmc_handle **hs, int32_t k, int64_t n_iter)
         launch_spawn(dinst, dunit, k, units, h0->stream);
         launch_spawn_heavy(dinst, k, h0->stream);
         if (max_nd > 0) launch_semistoch(dinst, k, max_nd, h0->stream);
-        cudaError_t le = launch_annihilate(dinst, dunit, k, units, h0->stream);
+        bool general = false, staged = true;
+        for (int i = 0; i < k; i++) {
+            general = general || tab[i].side || tab[i].adaptive;
+            staged = staged && staged_annihilation_fits(tab[i]);
+        }
+        cudaError_t le = launch_annihilate(dinst, dunit, k, units, general, staged, h0->stream);
         launch_annihilate_big(dinst, k, h0->stream);
         launch_new_diag(dinst, k, h0->stream);
         cudaError_t xe = any_pair ? launch_replica_cross(dinst, k, max_bk, h0->stream) : cudaSuccess;

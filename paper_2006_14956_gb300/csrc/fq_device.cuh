@@ -347,9 +347,22 @@ static __device__ double hoff_generic(const DevInst &I, u64 ia, u64 ib, u64 ja, 
     return neg_if(par, v);
 }
 
-// index of a determinant in the sorted key list of D, or -1
+// index of a determinant in the sorted key list of D, or -1: through the
+// open-addressing set of D keys (one or two probes), or by bisection of the
+// sorted keys where the set is not there
 __device__ __forceinline__ int d_index_of(const DevInst &I, u64 a, u64 b)
 {
+    if (I.dhash_idx) {
+        const u64 msk = (1ULL << I.dhash_bits) - 1;
+        u64 s = det_hash(a, b) & msk;
+        for (u64 probe = 0; probe <= msk; probe++) {
+            const u64 ka = __ldg(I.dhash_keys + 2 * s), kb = __ldg(I.dhash_keys + 2 * s + 1);
+            if (ka == a && kb == b) return __ldg(I.dhash_idx + s);
+            if (ka == 0 && kb == 0) return -1;
+            s = (s + 1) & msk;
+        }
+        return -1;
+    }
     int lo = 0, hi = I.nd;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;

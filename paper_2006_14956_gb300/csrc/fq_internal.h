@@ -45,6 +45,7 @@ constexpr int TABBITS = 12;           // shared-memory hash table of the annihil
 constexpr int BIG_BLOCKS = 64;        // blocks of the large-bucket annihilation kernel
 constexpr int K5_THREADS = 256;
 constexpr int KIDX = 2048;            // slots of the per-bucket list index (adaptive shift)
+constexpr int STAGED_SCAP = 256;      // spawn records per bucket the staged annihilation holds
 
 struct HeavyChunk {  // a slice of the attempts of one determinant with many walkers
     u64 a, b;
@@ -174,6 +175,7 @@ struct DevInst {
     double *dc_new;         // C_D after the exact projection of this iteration
     double *dc_buf[2];      // C_D after the last completed iteration, by list parity
     const u64 *dhash_keys;  // open-addressing set of D keys (a, b interleaved), size dhash_cap
+    const int *dhash_idx;   // per slot of that set: the key's position in dkey
     int dhash_bits;
     // pre-computed heat-bath doubles (generator 1): opposite-spin table of
     // (i alpha, j beta) at meta[i N + j], entries [(i N + j) N^2, +N^2), entry
@@ -219,7 +221,9 @@ struct TrialEnt {
 void launch_spawn(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, cudaStream_t s);
 void launch_spawn_heavy(const DevInst *dinst, int n_inst, cudaStream_t s);
 void launch_semistoch(const DevInst *dinst, int n_inst, int max_nd, cudaStream_t s);
-cudaError_t launch_annihilate(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, cudaStream_t s);
+cudaError_t launch_annihilate(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, bool general,
+                              bool staged, cudaStream_t s);
+bool staged_annihilation_fits(const DevInst &I);
 cudaError_t init_kernels();
 size_t annihilate_smem_bytes();
 void launch_annihilate_big(const DevInst *dinst, int n_inst, cudaStream_t s);

@@ -163,11 +163,10 @@ __device__ __forceinline__ void emit_spawn(const DevInst &I, u64 ta, u64 tb, dou
     emit_weight(I, ta, tb, neg_if(true, H * (I.lam[cls] * cper)), flags, w3, H, cx);
 }
 
-// lattice hop (Hubbard): electron w1, neighbour slot w2
-__device__ void spawn_hop(const DevInst &I, u64 pa, u64 pb, double cper, unsigned flags, u64 w1, u64 w2, u64 w3,
-                       const SpawnCtx &cx)
+// lattice hop (Hubbard): electron e (drawn from w1), neighbour slot w2
+__device__ void spawn_hop_e(const DevInst &I, u64 pa, u64 pb, double cper, unsigned flags, int e, u64 w2, u64 w3,
+                            const SpawnCtx &cx)
 {
-    const int e = (int)pick(w1, (u64)I.n);
     const int sp = e >= I.na;
     u64 x = sp ? pb : pa;
     const int p = nth_set(x, sp ? e - I.na : e);
@@ -179,11 +178,10 @@ __device__ void spawn_hop(const DevInst &I, u64 pa, u64 pb, double cper, unsigne
     emit_spawn(I, sp ? pa : x, sp ? x : pb, H, CLS_HOP, cper, flags, w3, cx);
 }
 
-// single excitation (App. A): electron w1, hole of its spin w2
-__device__ void spawn_single(const DevInst &I, u64 pa, u64 pb, double cper, unsigned flags, u64 w1, u64 w2, u64 w3,
-                       const SpawnCtx &cx)
+// single excitation (App. A): electron e (drawn from w1), hole of its spin w2
+__device__ void spawn_single_e(const DevInst &I, u64 pa, u64 pb, double cper, unsigned flags, int e, u64 w2, u64 w3,
+                               const SpawnCtx &cx)
 {
-    const int e = (int)pick(w1, (u64)I.n);
     const int sp = e >= I.na;
     u64 x = sp ? pb : pa;
     const int i = nth_set(x, sp ? e - I.na : e);
@@ -420,9 +418,10 @@ __device__ void run_attempts(const DevInst &I, K1Smem &S, long long it, unsigned
                 const unsigned d = r.det;
                 const ulonglong2 kk = map.key(d);
                 const SpawnCtx cx{map.slot(d), par, shift};
+                const int e = (int)pick(r.w1, (u64)I.n);
                 if (I.kind == FCIQMC_HUBBARD)
-                    spawn_hop(I, kk.x, kk.y, map.cper(d), map.flags(d), r.w1, r.w2, r.w3, cx);
-                else spawn_single(I, kk.x, kk.y, map.cper(d), map.flags(d), r.w1, r.w2, r.w3, cx);
+                    spawn_hop_e(I, kk.x, kk.y, map.cper(d), map.flags(d), e, r.w2, r.w3, cx);
+                else spawn_single_e(I, kk.x, kk.y, map.cper(d), map.flags(d), e, r.w2, r.w3, cx);
             } else if (q < ntot) {
                 const SpawnRec r = S.rec[q - ns];
                 const unsigned d = r.det;
@@ -628,8 +627,9 @@ struct Stage {
     IDX *tab;         // hash table: element index + 1, 0 = empty
     IDX *opos;        // output position of kept owners
 };
-enum { EF_OWNER = 1, EF_OCC = 2, EF_KEEP = 4, EF_REF = 16, EF_D = 32, EF_REJ = 64, EF_RREC = 128 };
-// EF_REJ: a rejected spawn arrived (owners); EF_RREC: this spawn was rejected
+enum { EF_OWNER = 1, EF_OCC = 2, EF_KEEP = 4, EF_ACC = 8, EF_REF = 16, EF_D = 32, EF_REJ = 64, EF_RREC = 128 };
+// EF_REJ: a rejected spawn arrived (owners); EF_RREC: this spawn was rejected;
+// EF_ACC: an accepted spawn arrived (owners, three-phase path)
 
 struct K3Shared {
     int wsum[K3_THREADS / 32];
@@ -1077,6 +1077,515 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
     // again only after the next bucket's barriers
 }
 
+// The same steps for a run without replica side lists or adaptive shift, in
+// three block phases per bucket: (A) walkers inserted into the table, death
+// and Eq. (3); (B) every spawn finds its target or becomes the owner of a new
+// determinant, initiator rule, exact accumulation; (C) owners finalised
+// (Eq. (3) with the annihilation draw), each kept one written straight to the
+// new bucket at a position taken from a shared counter (the order inside a
+// bucket affects no result), the new determinants listed, the bucket's totals
+// reduced, and the table cleared for the next bucket.  Writes beyond the
+// bucket's capacity are skipped: the overflow flag makes the host repeat the
+// iteration after growth.
+//
+// Where the records come from is a policy: LoadStage reads them from global
+// memory in phase A into the block's shared arrays; BulkStage finds them
+// already in shared memory, placed there by bulk copies issued while the
+// previous bucket was processed.
+struct Work3 {       // per-record working arrays shared by both policies
+    u64 *acc_lo, *acc_hi;
+    int *eflag;
+    unsigned short *tab;
+};
+
+struct LoadStage {
+    ulonglong2 *key;  // [EMAX]: walkers, then spawns
+    double *val;      // [EMAX]: C' after death (walkers), w (spawns)
+    int m, si, sn, cap_s;
+    size_t base, sbase;
+    const DevInst *I;
+    int par;
+    __device__ void walker(int e, ulonglong2 &k, double &c, double &hd, uint8_t &f) const
+    {
+        k = I->key[par][base + e];
+        c = I->c[par][base + e];
+        hd = I->hd[par][base + e];
+        f = I->fl[par][base + e];
+    }
+    __device__ void put_walker(int e, ulonglong2 k) const { key[e] = k; }
+    __device__ void stage_spawns(int t) const  // spawns: initiator [m, m+si), the others [m+si, E)
+    {
+        for (int e = m + t; e < m + si + sn; e += K3_THREADS) {
+            const int q = e - m;
+            const size_t o = sbase + (q < si ? q : cap_s - 1 - (q - si));
+            key[e] = I->skey[o];
+            val[e] = I->sw[o];
+        }
+    }
+    __device__ ulonglong2 k(int e) const { return key[e]; }
+    __device__ double v(int e) const { return val[e]; }
+    __device__ void set_v(int e, double x) const { val[e] = x; }
+    __device__ double hd_out(int e) const { return I->hd[par][base + e]; }  // read again: an L2 hit
+};
+
+// one bucket's raw records in shared memory, filled by bulk copies
+template <int SCAP>
+struct AStage {
+    ulonglong2 wkey[CAP_M];
+    ulonglong2 skey[SCAP];      // initiator spawns [0, si), the others [si, si + sn)
+    double wc[CAP_M];           // C; after death C'
+    double whd[CAP_M];
+    double sw[SCAP + 2];        // initiator weights [0, si), the others from swo (16-byte aligned copies)
+    uint8_t wfl[CAP_M];
+};
+
+template <int SCAP>
+struct BulkStage {
+    AStage<SCAP> *st;
+    int m, si, swo;
+    __device__ void walker(int e, ulonglong2 &k, double &c, double &hd, uint8_t &f) const
+    {
+        k = st->wkey[e];
+        c = st->wc[e];
+        hd = st->whd[e];
+        f = st->wfl[e];
+    }
+    __device__ void put_walker(int, ulonglong2) const {}
+    __device__ void stage_spawns(int) const {}
+    __device__ ulonglong2 k(int e) const { return e < m ? st->wkey[e] : st->skey[e - m]; }
+    __device__ double v(int e) const
+    {
+        if (e < m) return st->wc[e];
+        const int q = e - m;
+        return q < si ? st->sw[q] : st->sw[swo + (q - si)];
+    }
+    __device__ void set_v(int e, double x) const { st->wc[e] = x; }  // walkers only
+    __device__ double hd_out(int e) const { return st->whd[e]; }
+};
+
+template <typename SRC>
+__device__ void anni_bucket_3p(const DevInst &I, K3Shared &S, const Work3 &W, const SRC &R, int b, int par,
+                               long long it, double shift, int m, int si, int sn)
+{
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int E = m + si + sn;
+    constexpr u64 tmask = (u64)((1 << TABBITS) - 1);
+    const size_t base = (size_t)b * CAP_M;
+    const unsigned below = (1u << lane) - 1u;
+
+    // A. walkers, two per thread at a time: loads issued first, then
+    //    insertion and death (b) with Eq. (3)
+    static_assert(CAP_M <= 4 * K3_THREADS, "walkers per thread");
+#pragma unroll
+    for (int r0 = 0; r0 < 4; r0 += 2) {
+        ulonglong2 k[2];
+        double c[2], hd[2];
+        int f[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int e = t + (r0 + h) * K3_THREADS;
+            k[h] = make_ulonglong2(0, 0);
+            c[h] = 0.0;
+            hd[h] = 0.0;
+            f[h] = 0;
+            if (e < m) {
+                uint8_t fl;
+                R.walker(e, k[h], c[h], hd[h], fl);
+                f[h] = EF_OWNER | ((fl & DFLAG_REF) ? EF_REF : 0) | ((fl & DFLAG_D) ? EF_D : 0);
+            }
+        }
+        double cp[2];
+        bool draw[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int e = t + (r0 + h) * K3_THREADS;
+            draw[h] = false;
+            cp[h] = 0.0;
+            if (e < m) {
+                R.put_walker(e, k[h]);
+                W.acc_lo[e] = 0;
+                W.acc_hi[e] = 0;
+                W.eflag[e] = f[h] | (!is_zero(c[h]) ? EF_OCC : 0);
+                u64 sl = det_hash(k[h].x, k[h].y) & tmask;
+                while (atomicCAS(&W.tab[sl], (unsigned short)0, (unsigned short)(e + 1)) != 0) sl = (sl + 1) & tmask;
+                if (f[h] & EF_D) cp[h] = I.dc_new[d_index_of(I, k[h].x, k[h].y)];
+                else {
+                    cp[h] = c[h] * (1.0 - I.tau * (hd[h] - shift));
+                    draw[h] = !is_zero(cp[h]) && abs_lt(cp[h], I.cmin);
+                }
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int e = t + (r0 + h) * K3_THREADS;
+            if (draw[h]) {
+                u64 w[4];
+                philox(k[h].x, k[h].y, (u64)it, (u64)PURPOSE_DEATH, I.seed, I.replica, w);
+                cp[h] = round_stoch(cp[h], I.cmin, I.cmin_log2, I.cmin_pow2, w[0]);
+            }
+            if (e < m) R.set_v(e, cp[h]);
+        }
+    }
+    R.stage_spawns(t);
+    for (int e = m + t; e < E; e += K3_THREADS) {
+        W.acc_lo[e] = 0;
+        W.acc_hi[e] = 0;
+        W.eflag[e] = 0;
+    }
+    __syncthreads();
+
+    // B. spawns: find the target or become the owner of a new determinant;
+    //    initiator rule (Sec. I): a non-initiator spawn survives only onto a
+    //    determinant occupied at the start of the iteration
+    long long rejected = 0;
+    i128 ann = 0;
+    for (int e = m + t; e < E; e += K3_THREADS) {
+        const ulonglong2 k = R.k(e);
+        u64 sl = det_hash(k.x, k.y) & tmask;
+        int target = -1;
+        while (true) {
+            unsigned short v = ((volatile unsigned short *)W.tab)[sl];
+            if (v == 0) {
+                const unsigned short old = atomicCAS(&W.tab[sl], (unsigned short)0, (unsigned short)(e + 1));
+                if (old == 0) { target = e; break; }
+                v = old;
+            }
+            const int tt = (int)v - 1;
+            const ulonglong2 kk = R.k(tt);
+            if (kk.x == k.x && kk.y == k.y) { target = tt; break; }
+            sl = (sl + 1) & tmask;
+        }
+        if (target == e) atomicOr(&W.eflag[e], EF_OWNER);  // EF_ACC may be arriving from another spawn
+        const bool accepted = (e < m + si) || (target < m && (W.eflag[target] & EF_OCC));
+        if (!accepted) { rejected++; continue; }
+        const double w = R.v(e);
+        const i128 x = to_fixed(w, I.Fw);
+        const u64 lo = (u64)x, hi = (u64)((u128)x >> 64);
+        const u64 old = atomicAdd((unsigned long long *)&W.acc_lo[target], (unsigned long long)lo);
+        atomicAdd((unsigned long long *)&W.acc_hi[target], (unsigned long long)(hi + (old + lo < old ? 1ULL : 0ULL)));
+        atomicOr(&W.eflag[target], EF_ACC);
+        ann += (i128)fx32(w);
+    }
+    __syncthreads();
+
+    // C. owners: sum = C' + exact spawn sum, Eq. (3) with the annihilation
+    //    draw; kept determinants written to the new bucket
+    const int np = par ^ 1;
+    ulonglong2 *nkey = I.key[np];
+    double *nc = I.c[np], *nhd = I.hd[np];
+    uint8_t *nfl = I.fl[np];
+    u128 nw = 0;
+    double enm = 0.0, tnum = 0.0, tden = 0.0;
+    bool bad = false;
+    for (int e0 = 0; e0 < E; e0 += K3_THREADS) {
+        const int e = e0 + t;
+        int f = 0;
+        double accv = 0.0;
+        bool keep = false;
+        if (e < E) {
+            f = W.eflag[e];
+            if (f & EF_OWNER) {
+                const bool present = e < m;
+                const double cp = present ? R.v(e) : 0.0;
+                accv = cp;
+                if (f & EF_ACC) {
+                    const double sw = fixed_to_double((i128)(((u128)W.acc_hi[e] << 64) | (u128)W.acc_lo[e]), I.Fw);
+                    accv = present ? cp + sw : sw;
+                    ann += (present ? (i128)fx32(cp) : (i128)0) - (i128)fx32(accv);
+                    if (!(f & EF_D) && !is_zero(accv) && abs_lt(accv, I.cmin)) {
+                        const ulonglong2 k = R.k(e);
+                        u64 w[4];
+                        philox(k.x, k.y, (u64)it, (u64)PURPOSE_ANNIH, I.seed, I.replica, w);
+                        accv = round_stoch(accv, I.cmin, I.cmin_log2, I.cmin_pow2, w[0]);
+                    }
+                }
+                keep = !is_zero(accv) || (f & (EF_REF | EF_D));
+            }
+        }
+        // positions in the new bucket from a shared counter, one atomic per warp
+        const unsigned mk = __ballot_sync(0xffffffffu, keep);
+        int pb = 0;
+        if (lane == 0 && mk) pb = atomicAdd(&S.n_new, __popc(mk));
+        pb = __shfl_sync(0xffffffffu, pb, 0);
+        const int pos = pb + __popc(mk & below);
+        const bool write = keep && pos < CAP_M;
+        // the slots of new determinants go to the run's list (H_jj by k_new_diag)
+        const unsigned mn = __ballot_sync(0xffffffffu, write && e >= m);
+        int qb = 0;
+        if (lane == 0 && mn) qb = atomicAdd(&I.st->new_n, __popc(mn));
+        qb = __shfl_sync(0xffffffffu, qb, 0);
+        if (write) {
+            const ulonglong2 k = R.k(e);
+            const size_t dst = base + pos;
+            nkey[dst] = k;
+            nc[dst] = accv;
+            nfl[dst] = (uint8_t)(((f & EF_REF) ? DFLAG_REF : 0) | ((f & EF_D) ? DFLAG_D : 0));
+            if (e < m) nhd[dst] = R.hd_out(e);
+            else I.newdet[qb + __popc(mn & below)] = (unsigned)dst;
+            if (!abs_lt(accv, 0x1p31)) bad = true;
+            else nw += fx32(accv);
+            if (f & EF_REF) I.st->e_den = accv;
+            else {
+                const int lev = __popcll(k.x ^ I.ref_a) + __popcll(k.y ^ I.ref_b);
+                if (lev <= 4 && !is_zero(accv)) enm = enm + hoff_generic(I, k.x, k.y, I.ref_a, I.ref_b) * accv;
+            }
+            if (f & EF_D) I.dc_buf[np][d_index_of(I, k.x, k.y)] = accv;
+            if (I.trial_bits && !is_zero(accv)) {  // trial-wave-function estimator (Sec. IV)
+                const int ts = trial_find(I, k.x, k.y);
+                if (ts >= 0) {
+                    tnum = tnum + __ldg(&I.trial_tab[ts].w) * accv;
+                    tden = tden + __ldg(&I.trial_tab[ts].cT) * accv;
+                }
+            }
+        }
+    }
+    // the table is read no more in this bucket: clear it for the next one
+    {
+        uint4 *tz = reinterpret_cast<uint4 *>(W.tab);
+        for (int q = t; q < (int)((sizeof(unsigned short) << TABBITS) / sizeof(uint4)); q += K3_THREADS)
+            tz[q] = make_uint4(0, 0, 0, 0);
+    }
+    if (bad) atomicOr(&I.st->err, ERRB_NUMERIC);
+    // bucket reductions (fixed order: lanes by xor tree, warps in index order)
+    if (I.trial_bits)
+        for (int mm = 16; mm >= 1; mm >>= 1) {
+            tnum = tnum + __shfl_xor_sync(0xffffffffu, tnum, mm);
+            tden = tden + __shfl_xor_sync(0xffffffffu, tden, mm);
+        }
+    for (int mm = 16; mm >= 1; mm >>= 1) {
+        enm = enm + __shfl_xor_sync(0xffffffffu, enm, mm);
+        rejected += __shfl_xor_sync(0xffffffffu, rejected, mm);
+        ann += shfl_xor_i128(ann, mm);
+        nw += (u128)shfl_xor_i128((i128)nw, mm);
+    }
+    if (lane == 0) {
+        S.red_d[warp] = enm;
+        S.red_t[warp][0] = tnum;
+        S.red_t[warp][1] = tden;
+        S.red_u[warp][0] = (u64)nw;
+        S.red_u[warp][1] = (u64)(nw >> 64);
+        S.red_u[warp][2] = (u64)ann;
+        S.red_u[warp][3] = (u64)((u128)ann >> 64);
+        S.red_u[warp][4] = (u64)rejected;
+    }
+    __syncthreads();
+    if (t == 0) {
+        const int total = S.n_new;
+        S.n_new = 0;  // next used after two more barriers
+        double e_sum = 0.0, tn = 0.0, td = 0.0;
+        u128 nws = 0;
+        i128 anns = 0;
+        long long rej = 0;
+        for (int k = 0; k < K3_THREADS / 32; k++) {
+            e_sum = e_sum + S.red_d[k];
+            if (I.trial_bits) {
+                tn = tn + S.red_t[k][0];
+                td = td + S.red_t[k][1];
+            }
+            nws += ((u128)S.red_u[k][1] << 64) | S.red_u[k][0];
+            anns += (i128)(((u128)S.red_u[k][3] << 64) | S.red_u[k][2]);
+            rej += (long long)S.red_u[k][4];
+        }
+        if (total > CAP_M) { atomicOr(&I.st->err, ERRB_MAIN_CAP); atomicMax(&I.st->need_main, total); }
+        u64 *acc = I.acc + (b % NSHARD) * ACC_STRIDE;
+        limb_add(acc + ACC_NW, (i128)nws);
+        limb_add(acc + ACC_ANN, anns);
+        limb_add(acc + ACC_ENUM, to_fixed(e_sum, I.Fe));
+        red_add(&acc[ACC_NDET], (u64)total);
+        if (rej) red_add(&acc[ACC_REJ], (u64)rej);
+        red_add(&acc[ACC_SPAWNS], (u64)(si + sn));
+        if (I.trial_bits) {
+            Partial &P = I.part[b];
+            P.t_num = tn;
+            P.t_den = td;
+        }
+        if (total <= CAP_M) I.cnt[np][b] = total;
+        I.scnt_i[b] = 0;
+        I.scnt_n[b] = 0;
+    }
+}
+
+// ------------------------------------------------------------------ staged annihilation
+// Bulk copies (cp.async.bulk, global -> this CTA's shared memory; source in
+// this GPU's own memory, no multicast), completion counted in bytes on an
+// mbarrier.  Addresses and sizes are multiples of 16 bytes.
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(u64 *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(u64 *bar, unsigned bytes)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, u64 *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+// one bounded probe of the barrier's phase (the hardware may suspend the thread a while)
+__device__ __forceinline__ bool mbar_test(u64 *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_addr(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+constexpr long long MBAR_POLLS = 1LL << 24;  // bound on the polls of one wait
+__device__ __forceinline__ bool mbar_wait(u64 *bar, unsigned parity)
+{
+    for (long long k = 0; k < MBAR_POLLS; k++)
+        if (mbar_test(bar, parity)) return true;
+    return false;
+}
+
+template <int SCAP>
+struct K4Smem {
+    K3Shared sh;
+    u64 bar[2];
+    int binfo[2][8];  // per stage: bucket (-1: nothing staged), m, si, sn, swo, run, parity, error
+    long long bit[2];
+    double bS[2];
+    AStage<SCAP> st[2];
+    u64 acc_lo[CAP_M + SCAP], acc_hi[CAP_M + SCAP];
+    int eflag[CAP_M + SCAP];
+    unsigned short tab[1 << TABBITS];
+};
+static_assert(2 * (sizeof(K4Smem<STAGED_SCAP>) + 1024) <= 233472, "two staged annihilation blocks per SM");
+
+// thread 0: checks of unit u as in k_annihilate, then the bulk copies of its
+// bucket into stage q (completion on bar[q]); the stage's info tells the
+// block whether and what to process
+template <int SCAP>
+__device__ void stage_issue(const DevInst *__restrict__ insts, const int *__restrict__ unit_start, int n_inst, int u,
+                            K4Smem<SCAP> &Sm, int q)
+{
+    int *bi = Sm.binfo[q];
+    bi[0] = -1;
+    const int ii = find_inst(unit_start, n_inst, u);
+    const DevInst &I = insts[ii];
+    const int err = *(volatile int *)&I.st->err;
+    if (err) return;
+    const int par = I.st->parity;
+    const int b = u - I.unit0;
+    const int m = I.cnt[par][b], si = I.scnt_i[b], sn = I.scnt_n[b], cap_s = I.cap_s;
+    if (si + sn > cap_s) {
+        atomicOr(&I.st->err, ERRB_SPAWN_CAP);
+        atomicMax(&I.st->need_spawn, si + sn);
+        atomicAdd(&I.st->n_spawn_over, 1);
+        return;
+    }
+    if (m + si + sn > EMAX || si + sn > SCAP) {  // too large for shared memory: deferred to k_annihilate_big
+        I.big_list[atomicAdd(&I.st->big_n, 1)] = b;
+        return;
+    }
+    AStage<SCAP> &st = Sm.st[q];
+    const size_t base = (size_t)b * CAP_M, sbase = (size_t)b * cap_s;
+    // 16-byte multiples: C and H_ii rounded up to an even count, flags to 16
+    // (all within the bucket's CAP_M slots); the non-initiator weights start
+    // at an even slot (one slot early when cap_s - sn is odd)
+    const unsigned m2 = (unsigned)((m + 1) & ~1), m16 = (unsigned)((m + 15) & ~15);
+    const unsigned si2 = (unsigned)((si + 1) & ~1);
+    const int n0 = cap_s - sn, n0e = n0 & ~1;
+    const unsigned nw_cnt = (unsigned)(cap_s - n0e);
+    const unsigned bytes = (unsigned)m * 16u + m2 * 8u * 2u + m16 + (unsigned)(si + sn) * 16u + (si ? si2 * 8u : 0u) +
+                           (sn ? nw_cnt * 8u : 0u);
+    bi[1] = m; bi[2] = si; bi[3] = sn; bi[4] = (int)si2 + (n0 - n0e); bi[5] = ii; bi[6] = par; bi[7] = 0;
+    Sm.bit[q] = I.st->iter;
+    Sm.bS[q] = I.st->S;
+    bi[0] = b;
+    if (bytes == 0) {  // an empty bucket: complete the phase without copies
+        asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(&Sm.bar[q]))
+                     : "memory");
+        return;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier generic accesses of the stage first
+    mbar_expect_tx(&Sm.bar[q], bytes);
+    if (m) {
+        bulk_g2s(st.wkey, I.key[par] + base, (unsigned)m * 16u, &Sm.bar[q]);
+        bulk_g2s(st.wc, I.c[par] + base, m2 * 8u, &Sm.bar[q]);
+        bulk_g2s(st.whd, I.hd[par] + base, m2 * 8u, &Sm.bar[q]);
+        bulk_g2s(st.wfl, I.fl[par] + base, m16, &Sm.bar[q]);
+    }
+    if (si) {
+        bulk_g2s(st.skey, I.skey + sbase, (unsigned)si * 16u, &Sm.bar[q]);
+        bulk_g2s(st.sw, I.sw + sbase, si2 * 8u, &Sm.bar[q]);
+    }
+    if (sn) {
+        bulk_g2s(st.skey + si, I.skey + sbase + n0, (unsigned)sn * 16u, &Sm.bar[q]);
+        bulk_g2s(st.sw + si2, I.sw + sbase + n0e, nw_cnt * 8u, &Sm.bar[q]);
+    }
+}
+
+// The three-phase annihilation with every bucket's records brought into
+// shared memory by bulk copies one bucket ahead: while a block works on one
+// bucket, the next one's keys, amplitudes, H_ii, flags and spawns are in
+// flight.  For runs without replica side lists or adaptive shift whose spawn
+// capacity fits the stage (the host picks this kernel then).
+__global__ void __launch_bounds__(K3_THREADS, 2) k_annihilate_staged(const DevInst *__restrict__ insts,
+                                                                     const int *__restrict__ unit_start, int n_inst,
+                                                                     int n_units)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    K4Smem<STAGED_SCAP> &Sm = *reinterpret_cast<K4Smem<STAGED_SCAP> *>(smem_raw);
+    K3Shared &S = Sm.sh;
+    const int t = threadIdx.x;
+    {
+        uint4 *tz = reinterpret_cast<uint4 *>(Sm.tab);
+        for (int q = t; q < (int)(sizeof(Sm.tab) / sizeof(uint4)); q += K3_THREADS) tz[q] = make_uint4(0, 0, 0, 0);
+    }
+    if (t == 0) {
+        S.n_new = 0;
+        mbar_init(&Sm.bar[0], 1);
+        mbar_init(&Sm.bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if ((int)blockIdx.x < n_units) stage_issue(insts, unit_start, n_inst, blockIdx.x, Sm, 0);
+    }
+    __syncthreads();
+    unsigned phase[2] = {0u, 0u};
+    const Work3 W3{Sm.acc_lo, Sm.acc_hi, Sm.eflag, Sm.tab};
+    int q = 0;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x, q ^= 1) {
+        // the next bucket's copies go out before this one is processed; its
+        // stage was last read before the previous bucket's closing barrier
+        if (t == 0) {
+            if (u + (int)gridDim.x < n_units) stage_issue(insts, unit_start, n_inst, u + gridDim.x, Sm, q ^ 1);
+            else Sm.binfo[q ^ 1][0] = -1;
+        }
+        const int b = Sm.binfo[q][0];
+        if (b < 0) {
+            __syncthreads();  // binfo[q ^ 1] is written before anyone reads it
+            continue;
+        }
+        const bool ok = mbar_wait(&Sm.bar[q], phase[q]);
+        const int ii = Sm.binfo[q][5];
+        const DevInst &I = insts[ii];
+        if (__syncthreads_or(!ok)) {
+            // the copies did not land within the bound: report, wait once
+            // more (bounded) for both stages' copies, stop
+            if (t == 0) atomicOr(&I.st->err, ERRB_TIMEOUT);
+            mbar_wait(&Sm.bar[q], phase[q]);
+            if (Sm.binfo[q ^ 1][0] >= 0) mbar_wait(&Sm.bar[q ^ 1], phase[q ^ 1]);
+            return;
+        }
+        phase[q] ^= 1u;
+        const int m = Sm.binfo[q][1], si = Sm.binfo[q][2], sn = Sm.binfo[q][3], swo = Sm.binfo[q][4];
+        const int par = Sm.binfo[q][6];
+        const BulkStage<STAGED_SCAP> R{&Sm.st[q], m, si, swo};
+        anni_bucket_3p(I, S, W3, R, b, par, Sm.bit[q], Sm.bS[q], m, si, sn);
+    }
+}
+
+// GENERAL: the batch holds a run with replica side lists or adaptive shift,
+// whose buckets take the general path (anni_bucket); the others the
+// three-phase one.  Without it the kernel holds the three-phase path alone.
+template <bool GENERAL>
 __global__ void __launch_bounds__(K3_THREADS, 3) k_annihilate(const DevInst *__restrict__ insts,
                                                               const int *__restrict__ unit_start, int n_inst, int n_units)
 {
@@ -1085,20 +1594,32 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k_annihilate(const DevInst *__r
     K3Shared &S = Sm.sh;
     Stage<unsigned short> W{Sm.key, Sm.val, Sm.acc_lo, Sm.acc_hi, Sm.nacc, Sm.eflag, Sm.tab, Sm.opos};
     const int t = threadIdx.x;
+    // the three-phase path expects a cleared table and output counter; the
+    // general path (replica side lists, adaptive shift) leaves both used
+    bool clean = false;
+    // the run's state at the start of the iteration, read once per run a
+    // block meets
+    int cur = -1, err = 0, par = 0;
+    long long it = 0;
+    double shift = 0.0;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
         const int ii = find_inst(unit_start, n_inst, u);
         const DevInst &I = insts[ii];
-        if (t == 0) {
-            S.hdr_err = *(volatile int *)&I.st->err;
-            S.hdr_par = I.st->parity;
-            S.hdr_it = I.st->iter;
-            S.hdr_S = I.st->S;
+        if (ii != cur) {
+            if (t == 0) {
+                S.hdr_err = *(volatile int *)&I.st->err;
+                S.hdr_par = I.st->parity;
+                S.hdr_it = I.st->iter;
+                S.hdr_S = I.st->S;
+            }
+            __syncthreads();
+            err = S.hdr_err;
+            par = S.hdr_par;
+            it = S.hdr_it;
+            shift = S.hdr_S;
+            cur = ii;
+            __syncthreads();
         }
-        __syncthreads();
-        const int err = S.hdr_err, par = S.hdr_par;
-        const long long it = S.hdr_it;
-        const double shift = S.hdr_S;
-        __syncthreads();
         if (err) continue;
         const int b = u - I.unit0;
         const int m = I.cnt[par][b], si = I.scnt_i[b], sn = I.scnt_n[b];
@@ -1114,7 +1635,21 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k_annihilate(const DevInst *__r
             if (t == 0) I.big_list[atomicAdd(&I.st->big_n, 1)] = b;
             continue;
         }
-        anni_bucket<unsigned short>(I, S, W, TABBITS, b, par, it, shift, m, si, sn);
+        if (GENERAL && (I.side || I.adaptive)) {
+            anni_bucket<unsigned short>(I, S, W, TABBITS, b, par, it, shift, m, si, sn);
+            clean = false;
+            continue;
+        }
+        if (!clean) {
+            uint4 *tz = reinterpret_cast<uint4 *>(Sm.tab);
+            for (int q = t; q < (int)(sizeof(Sm.tab) / sizeof(uint4)); q += K3_THREADS) tz[q] = make_uint4(0, 0, 0, 0);
+            if (t == 0) S.n_new = 0;
+            __syncthreads();
+            clean = true;
+        }
+        const LoadStage R{Sm.key, Sm.val, m, si, sn, I.cap_s, (size_t)b * CAP_M, (size_t)b * I.cap_s, &I, par};
+        const Work3 W3{Sm.acc_lo, Sm.acc_hi, Sm.eflag, Sm.tab};
+        anni_bucket_3p(I, S, W3, R, b, par, it, shift, m, si, sn);
     }
 }
 
@@ -1481,7 +2016,13 @@ void launch_spawn_heavy(const DevInst *dinst, int n_inst, cudaStream_t s)
 
 cudaError_t init_kernels()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_annihilate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K3Smem));
+    cudaError_t e = cudaFuncSetAttribute(k_annihilate<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(K3Smem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_annihilate<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K3Smem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_annihilate_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(K4Smem<STAGED_SCAP>));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spawn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K1Smem));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_spawn_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K1Smem));
@@ -1490,12 +2031,35 @@ cudaError_t init_kernels()
 
 size_t annihilate_smem_bytes() { return sizeof(K3Smem); }
 
-cudaError_t launch_annihilate(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, cudaStream_t s)
+// Whether a run's buckets can go through the staged kernel: spawn regions
+// that fit its stage, and every array a bulk copy reads on a 16-byte
+// boundary (a caller-supplied allocator may return less aligned memory)
+bool staged_annihilation_fits(const DevInst &I)
 {
+    auto al = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
+    if (I.side || I.adaptive || I.cap_s > STAGED_SCAP || (I.cap_s & 1)) return false;
+    for (int k = 0; k < 2; k++)
+        if (!al(I.key[k]) || !al(I.c[k]) || !al(I.hd[k]) || !al(I.fl[k])) return false;
+    return al(I.skey) && al(I.sw);
+}
+
+// general: some run of the batch has replica side lists or adaptive shift;
+// staged: every run fits the staged kernel (bulk copies one bucket ahead),
+// launched as one resident wave of blocks (two per SM)
+cudaError_t launch_annihilate(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, bool general,
+                              bool staged, cudaStream_t s)
+{
+    if (staged && !general) {
+        int grid = n_units < num_sms() * 2 ? n_units : num_sms() * 2;
+        if (grid < 1) grid = 1;
+        k_annihilate_staged<<<grid, K3_THREADS, sizeof(K4Smem<STAGED_SCAP>), s>>>(dinst, unit_start, n_inst, n_units);
+        return cudaGetLastError();
+    }
     const size_t smem = sizeof(K3Smem);
     int grid = n_units < num_sms() * g_anni_bps ? n_units : num_sms() * g_anni_bps;
     if (grid < 1) grid = 1;
-    k_annihilate<<<grid, K3_THREADS, smem, s>>>(dinst, unit_start, n_inst, n_units);
+    if (general) k_annihilate<true><<<grid, K3_THREADS, smem, s>>>(dinst, unit_start, n_inst, n_units);
+    else k_annihilate<false><<<grid, K3_THREADS, smem, s>>>(dinst, unit_start, n_inst, n_units);
     return cudaGetLastError();
 }
 

@@ -114,6 +114,9 @@ __global__ void k_noalloc_total(const double *partial, double *out)
     *out = acc;
 }
 
+// the array's device address per device, looked up by the first call on that
+// device and kept for the process (stale after the device's primary context
+// is destroyed, e.g. by cudaDeviceReset)
 static std::mutex g_noalloc_mu;
 static unsigned char *g_noalloc_ptr[256];
 
