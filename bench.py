@@ -228,6 +228,50 @@ def run_batch(args):
             "batched_over_sequential": (att_b / tb) / (att_s / ts)}
 
 
+def run_batch_to_sigma(args):
+    """The batched set run to sigma(E_proj) < 1 mEh: the 64 Hubbard runs of
+    run_batch submitted together to a server that steps every admitted run
+    in one launch per kernel (max_active 64), against the same 64 run one at
+    a time (max_active 1).  Each run retires at the first 50-iteration check
+    with sigma < 1 mEh after 200 post-equilibration samples, or at
+    --max-iters.  A run is bit-identical alone and in the batch, so both
+    sides do the same iterations and the ratio of wall times is the ratio of
+    throughputs; the identity is checked run by run."""
+    import paper_2006_14956_gb300 as fq
+    runs = workloads.batched_hubbard_instances(64)
+    runs = [(s, dict(p, shift_damping=0.5, shift_interval=5)) for s, p in runs]
+    res = {}
+    for mode, active in (("batched", 64), ("sequential", 1)):
+        srv = fq.fciqmc_server_create(100 << 30, max_active=active)
+        ids = [fq.fciqmc_server_submit(srv, s, p, target_sigma=1e-3, max_iters=args.max_iters) for s, p in runs]
+        t0 = time.perf_counter()
+        while fq.fciqmc_server_tick(srv, 50) > 0:
+            pass
+        wall = time.perf_counter() - t0
+        st = [fq.fciqmc_server_poll(srv, i) for i in ids]
+        res[mode] = {"wall_s": wall, "status": st}
+        del srv
+    sb, ss = res["batched"]["status"], res["sequential"]["status"]
+    same = all(a["iterations"] == b["iterations"] and a["energy"] == b["energy"] and a["sigma"] == b["sigma"] and
+               a["attempts"] == b["attempts"] for a, b in zip(sb, ss))
+    att = float(sum(a["attempts"] for a in sb))
+    tb, ts = res["batched"]["wall_s"], res["sequential"]["wall_s"]
+    conv = sum(1 for a in sb if a["state_name"] == "converged")
+    iters = [a["iterations"] for a in sb]
+    return {"metric": METRIC, "value": att / tb, "unit": "spawn attempts/s", "n_gpus": 1, "steps": len(runs),
+            "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "64 2D Hubbard runs (3x4/4x4/4x5, U/t 2/4/8, targets 1e4..1e6) each to "
+                                   "sigma(E_proj) < 1 mEh", "tau": 0.005, "initiator_threshold": 3,
+                       "max_iters": args.max_iters, "check_every": 50},
+            "batched_wall_s": tb, "sequential_wall_s": ts, "batched_over_sequential": ts / tb,
+            "sequential_attempts_per_s": att / ts, "converged": conv, "runs": len(runs),
+            "iterations_min": min(iters), "iterations_max": max(iters), "iterations_sum": int(sum(iters)),
+            "identical_alone_and_batched": bool(same),
+            "sigma_mEh_not_converged": sorted(round(1e3 * a["sigma"], 2) for a in sb
+                                              if a["state_name"] != "converged" and np.isfinite(a["sigma"]))}
+
+
 def run_serving(args):
     """Poisson arrivals (20/s) of mixed FCIQMC requests (1D/2D Hubbard and
     synthetic ab initio systems, walker targets 1e4..1e7), each run until the
@@ -309,7 +353,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="abinitio50", choices=["abinitio50", "abinitio24", "batch", "serving"])
+    ap.add_argument("--workload", default="abinitio50",
+                    choices=["abinitio50", "abinitio24", "batch", "batch-sigma", "serving"])
     ap.add_argument("--equil", type=int, default=200,
                     help="untimed iterations after E_proj's equilibration start (shift start + 500)")
     ap.add_argument("--generator", default="uniform", choices=["uniform", "pchb"],
@@ -328,10 +373,10 @@ def main():
         if out is not None:
             print(json.dumps(out), flush=True)
         return
-    if args.workload in ("batch", "serving"):
+    if args.workload in ("batch", "batch-sigma", "serving"):
         import torch
         torch.cuda.set_device(local)
-        out = run_batch(args) if args.workload == "batch" else run_serving(args)
+        out = {"batch": run_batch, "batch-sigma": run_batch_to_sigma, "serving": run_serving}[args.workload](args)
         if rank == 0:
             print(json.dumps(out), flush=True)
         return

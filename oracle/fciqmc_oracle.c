@@ -342,6 +342,52 @@ static int sys_finish(orc_sys *s)
     return 0;
 }
 
+/* Integral grid (reading): the GPU library sums integrals exactly in 128-bit
+ * fixed point, which caps the span between the largest integral and the
+ * finest bit it must represent.  Where the integrals' finest bit lies beyond
+ * that span, every h_pq, (pq|rs) and E_core is replaced by its nearest
+ * multiple of 2^-G (ties to even), with
+ *   G = 125 - m - 2 - max(ceil(log2(n^2 + 2n + 4)), ceil(log2(N^2)) + 2),
+ * m = floor(log2 max |integral|), n electrons, N orbitals; otherwise the
+ * integrals are used as given.  Returns nonzero when no such grid exists. */
+static int lowest_bit(double x)  /* exponent of the lowest set bit of x != 0 */
+{
+    int e;
+    double m = frexp(fabs(x), &e); /* |x| = m 2^e, m in [0.5, 1) */
+    uint64_t q = (uint64_t)ldexp(m, 53);  /* exact: 53-bit integer */
+    int z = 0;
+    while (!(q & 1)) { q >>= 1; z++; }
+    return e - 53 + z;
+}
+
+static int integral_grid(orc_sys *s, int64_t ne)
+{
+    int64_t nh = (int64_t)s->norb * s->norb;
+    int any = 0, lo = 0, hi = 0;
+    for (int64_t i = 0; i < nh + ne + 1; i++) {
+        double x = i < nh ? s->h[i] : (i < nh + ne ? s->eri[i - nh] : s->ecore);
+        if (x == 0.0) continue;
+        if (!isfinite(x)) return 1;
+        int e;
+        frexp(fabs(x), &e);
+        int l = lowest_bit(x);
+        if (!any || l < lo) lo = l;
+        if (!any || e - 1 > hi) hi = e - 1;
+        any = 1;
+    }
+    if (!any) return 0;
+    int n = s->na + s->nb, tb = 0, kb = 0;
+    while ((1LL << tb) < (long long)n * n + 2 * n + 4) tb++;
+    while ((1LL << kb) < (long long)s->norb * s->norb) kb++;
+    int G = 125 - hi - 2 - (tb > kb + 2 ? tb : kb + 2);
+    if (-lo <= G) return 0;
+    if (G < 0) return 1;
+    for (int64_t i = 0; i < nh; i++) s->h[i] = ldexp(nearbyint(ldexp(s->h[i], G)), -G);
+    for (int64_t i = 0; i < ne; i++) s->eri[i] = ldexp(nearbyint(ldexp(s->eri[i], G)), -G);
+    s->ecore = ldexp(nearbyint(ldexp(s->ecore, G)), -G);
+    return 0;
+}
+
 orc_sys *orc_sys_abinitio(int norb, int na, int nb, double ecore, const double *h,
                           const double *eri_packed, const uint64_t *ref)
 {
@@ -353,6 +399,7 @@ orc_sys *orc_sys_abinitio(int norb, int na, int nb, double ecore, const double *
     s->eri = malloc(sizeof(double) * ne);
     memcpy(s->h, h, sizeof(double) * norb * norb);
     memcpy(s->eri, eri_packed, sizeof(double) * ne);
+    if (integral_grid(s, ne)) { orc_sys_free(s); return NULL; }
     if (ref) { s->ref_a = ref[0]; s->ref_b = ref[1]; }
     else { s->ref_a = lowmask(na); s->ref_b = lowmask(nb); } /* aufbau */
     if (sys_finish(s)) { orc_sys_free(s); return NULL; }

@@ -807,9 +807,32 @@ static int create_run(const fciqmc_system *sys, const fciqmc_params *prm, u64 re
     for (double x : h->eri) if (!scan(x)) return bail(FCIQMC_ERR_INVALID_ARG, "non-finite two-electron integral");
     if (!scan(h->ecore)) return bail(FCIQMC_ERR_INVALID_ARG, "non-finite core energy");
     const int n = h->na + h->nb;
-    const int F = any ? std::max(0, -lsb_min) : 0;
+    int F = any ? std::max(0, -lsb_min) : 0;
     int terms_bits = 0;
     while ((1LL << terms_bits) < (long long)n * n + 2 * n + 4) terms_bits++;
+    // Integral grid: the exact sums (H_ii, single excitations, heat-bath table
+    // sums of up to N^2 terms) must fit 125 bits.  Where the integrals' own
+    // finest bit lies below what that allows (FCIDUMP files print values of
+    // 1e-17 .. 1e-20 next to O(10) Eh), every integral and E_core is rounded
+    // to the nearest multiple of 2^-G (ties to even), G = 125 - msb - 2 -
+    // max(terms, table bits), before any use; otherwise nothing changes.
+    int table_bits = 0;
+    while ((1LL << table_bits) < (long long)N * N) table_bits++;
+    const int G = 125 - msb_max - 2 - std::max(terms_bits, table_bits + 2);
+    if (any && F > G) {
+        if (G < 0) return bail(FCIQMC_ERR_UNSUPPORTED, "integrals too large for the 128-bit exact accumulator");
+        auto to_grid = [G](double x) { return std::ldexp(std::nearbyint(std::ldexp(x, G)), -G); };
+        for (double &x : h->h) x = to_grid(x);
+        for (double &x : h->eri) x = to_grid(x);
+        h->ecore = to_grid(h->ecore);
+        msb_max = -1100;
+        any = false;
+        lsb_min = 0;
+        for (double x : h->h) scan(x);
+        for (double x : h->eri) scan(x);
+        scan(h->ecore);
+        F = any ? std::max(0, -lsb_min) : 0;
+    }
     if (any && msb_max + F + terms_bits + 2 > 125)
         return bail(FCIQMC_ERR_UNSUPPORTED, "integral dynamic range too wide for the 128-bit exact accumulator");
     const int ecm = exponent_of(P.c_min);

@@ -1459,22 +1459,46 @@ struct K4Smem {
 };
 static_assert(2 * (sizeof(K4Smem<STAGED_SCAP>) + 1024) <= 233472, "two staged annihilation blocks per SM");
 
-// thread 0: checks of unit u as in k_annihilate, then the bulk copies of its
-// bucket into stage q (completion on bar[q]); the stage's info tells the
+// What thread 0 knows of a unit before its copies go out: the run's state
+// (read once per run the block meets) and the bucket's counts, loaded one
+// bucket ahead of their use so that their latency is hidden
+struct StageMeta {
+    int u, ii, b, m, si, sn, par, err;
+    long long it;
+    double S;
+};
+
+__device__ __forceinline__ void meta_load(const DevInst *__restrict__ insts, const int *__restrict__ unit_start,
+                                          int n_inst, int u, StageMeta &M)
+{
+    M.u = u;
+    if (u < 0) return;
+    const int ii = find_inst(unit_start, n_inst, u);
+    const DevInst &I = insts[ii];
+    if (ii != M.ii) {
+        M.ii = ii;
+        M.err = *(volatile int *)&I.st->err;
+        M.par = I.st->parity;
+        M.it = I.st->iter;
+        M.S = I.st->S;
+    }
+    M.b = u - I.unit0;
+    M.m = I.cnt[M.par][M.b];
+    M.si = I.scnt_i[M.b];
+    M.sn = I.scnt_n[M.b];
+}
+
+// thread 0: the checks of k_annihilate on unit M.u, then the bulk copies of
+// its bucket into stage q (completion on bar[q]); the stage's info tells the
 // block whether and what to process
 template <int SCAP>
-__device__ void stage_issue(const DevInst *__restrict__ insts, const int *__restrict__ unit_start, int n_inst, int u,
-                            K4Smem<SCAP> &Sm, int q)
+__device__ void stage_issue(const DevInst *__restrict__ insts, const StageMeta &M, K4Smem<SCAP> &Sm, int q)
 {
     int *bi = Sm.binfo[q];
     bi[0] = -1;
-    const int ii = find_inst(unit_start, n_inst, u);
-    const DevInst &I = insts[ii];
-    const int err = *(volatile int *)&I.st->err;
-    if (err) return;
-    const int par = I.st->parity;
-    const int b = u - I.unit0;
-    const int m = I.cnt[par][b], si = I.scnt_i[b], sn = I.scnt_n[b], cap_s = I.cap_s;
+    if (M.u < 0 || M.err) return;
+    const DevInst &I = insts[M.ii];
+    const int par = M.par, b = M.b, m = M.m, si = M.si, sn = M.sn, cap_s = I.cap_s;
     if (si + sn > cap_s) {
         atomicOr(&I.st->err, ERRB_SPAWN_CAP);
         atomicMax(&I.st->need_spawn, si + sn);
@@ -1494,11 +1518,11 @@ __device__ void stage_issue(const DevInst *__restrict__ insts, const int *__rest
     const unsigned si2 = (unsigned)((si + 1) & ~1);
     const int n0 = cap_s - sn, n0e = n0 & ~1;
     const unsigned nw_cnt = (unsigned)(cap_s - n0e);
-    const unsigned bytes = (unsigned)m * 16u + m2 * 8u * 2u + m16 + (unsigned)(si + sn) * 16u + (si ? si2 * 8u : 0u) +
-                           (sn ? nw_cnt * 8u : 0u);
-    bi[1] = m; bi[2] = si; bi[3] = sn; bi[4] = (int)si2 + (n0 - n0e); bi[5] = ii; bi[6] = par; bi[7] = 0;
-    Sm.bit[q] = I.st->iter;
-    Sm.bS[q] = I.st->S;
+    const unsigned bytes = (m ? (unsigned)m * 16u + m2 * 8u * 2u + m16 : 0u) + (unsigned)(si + sn) * 16u +
+                           (si ? si2 * 8u : 0u) + (sn ? nw_cnt * 8u : 0u);
+    bi[1] = m; bi[2] = si; bi[3] = sn; bi[4] = (int)si2 + (n0 - n0e); bi[5] = M.ii; bi[6] = par; bi[7] = 0;
+    Sm.bit[q] = M.it;
+    Sm.bS[q] = M.S;
     bi[0] = b;
     if (bytes == 0) {  // an empty bucket: complete the phase without copies
         asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(&Sm.bar[q]))
@@ -1540,12 +1564,22 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k_annihilate_staged(const DevIn
         uint4 *tz = reinterpret_cast<uint4 *>(Sm.tab);
         for (int q = t; q < (int)(sizeof(Sm.tab) / sizeof(uint4)); q += K3_THREADS) tz[q] = make_uint4(0, 0, 0, 0);
     }
+    // thread 0 keeps the counts of the bucket whose copies go out next
+    StageMeta nxt;
+    nxt.ii = -1;
     if (t == 0) {
         S.n_new = 0;
         mbar_init(&Sm.bar[0], 1);
         mbar_init(&Sm.bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        if ((int)blockIdx.x < n_units) stage_issue(insts, unit_start, n_inst, blockIdx.x, Sm, 0);
+        StageMeta first;
+        first.ii = -1;
+        meta_load(insts, unit_start, n_inst, (int)blockIdx.x < n_units ? (int)blockIdx.x : -1, first);
+        stage_issue(insts, first, Sm, 0);
+        nxt.ii = first.ii;
+        nxt.err = first.err; nxt.par = first.par; nxt.it = first.it; nxt.S = first.S;
+        const int un = (int)blockIdx.x + (int)gridDim.x;
+        meta_load(insts, unit_start, n_inst, un < n_units ? un : -1, nxt);
     }
     __syncthreads();
     unsigned phase[2] = {0u, 0u};
@@ -1555,8 +1589,9 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k_annihilate_staged(const DevIn
         // the next bucket's copies go out before this one is processed; its
         // stage was last read before the previous bucket's closing barrier
         if (t == 0) {
-            if (u + (int)gridDim.x < n_units) stage_issue(insts, unit_start, n_inst, u + gridDim.x, Sm, q ^ 1);
-            else Sm.binfo[q ^ 1][0] = -1;
+            stage_issue(insts, nxt, Sm, q ^ 1);
+            const int un = u + 2 * (int)gridDim.x;
+            meta_load(insts, unit_start, n_inst, un < n_units ? un : -1, nxt);
         }
         const int b = Sm.binfo[q][0];
         if (b < 0) {
