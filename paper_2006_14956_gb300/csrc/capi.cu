@@ -910,6 +910,14 @@ static int create_run(const fciqmc_system *sys, const fciqmc_params *prm, u64 re
         double q = P.p_single * 0x1p53;  // exact
         I.tsingle = (u64)std::ceil(q);
     }
+    {
+        // ceil(2^64 / d) of the generators' fixed divisors (0 for d <= 1)
+        auto magic = [](long long d) -> u64 { return d > 1 ? (u64)(~0ULL / (u64)d) + 1ULL : 0ULL; };
+        I.mg_n1 = magic(n - 1);
+        I.mg_mb = magic(I.mb);
+        I.mg_ma1 = magic(I.ma - 1);
+        I.mg_mb1 = magic(I.mb - 1);
+    }
     I.seed = P.seed; I.cmin = P.c_min; I.n_a = P.initiator_threshold;
     {
         int e2;

@@ -32,6 +32,11 @@ __device__ __forceinline__ int nth_set(u64 x, int k)
 // floor(w * m / 2^64): an integer in [0, m)
 __device__ __forceinline__ u64 pick(u64 w, u64 m) { return __umul64hi(w, m); }
 
+// x / d for x < 2^32 by the precomputed M = ceil(2^64 / d) (M = 0: d = 1):
+// x M / 2^64 = x / d + x e / (d 2^64) with 0 <= e < d, and the second term
+// is below 2^-32 < 1/d, so the floor is exact
+__device__ __forceinline__ unsigned div_by(unsigned x, u64 M) { return M ? (unsigned)__umul64hi((u64)x, M) : x; }
+
 // number of occupied spin orbitals before canonical position pos, then flip it
 __device__ __forceinline__ int flip_parity(u64 &a, u64 &b, int N, int pos)
 {

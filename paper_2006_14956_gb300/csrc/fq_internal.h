@@ -132,6 +132,10 @@ struct DevInst {
     double lam[NCLS];
     double tmt;             // -t (Hubbard hopping matrix element)
     u64 tsingle;            // single excitation iff (w0 >> 11) < tsingle
+    // ceil(2^64 / d) for the run's fixed divisors d = n - 1, m_beta,
+    // m_alpha - 1, m_beta - 1 (0 for d = 1): x / d = umulhi(x, M) exactly
+    // for x < 2^32
+    u64 mg_n1, mg_mb, mg_ma1, mg_mb1;
     u64 seed;
     double tau, cmin, n_a;
     int cmin_log2;          // c_min = 2^cmin_log2 when cmin_pow2

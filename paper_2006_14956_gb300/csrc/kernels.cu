@@ -209,8 +209,9 @@ __device__ void spawn_double(const DevInst &I, u64 pa, u64 pb, double cper, unsi
         oi = s1 ? o2 : o1;
         oj = s1 ? o1 : o2;
         const unsigned y = (unsigned)pick(w2, (u64)(I.ma * I.mb));
-        oa = nth_set(~pa & I.normask, (int)(y / (unsigned)I.mb));
-        ob = nth_set(~pb & I.normask, (int)(y % (unsigned)I.mb));
+        const unsigned ya = div_by(y, I.mg_mb);
+        oa = nth_set(~pa & I.normask, (int)ya);
+        ob = nth_set(~pb & I.normask, (int)(y - ya * (unsigned)I.mb));
         P0 = oi; P1 = N + oj; Q0 = oa; Q1 = N + ob;
         ta = pa ^ (1ULL << oi) ^ (1ULL << oa);
         tb = pb ^ (1ULL << oj) ^ (1ULL << ob);
@@ -219,7 +220,8 @@ __device__ void spawn_double(const DevInst &I, u64 pa, u64 pb, double cper, unsi
         const int m = s1 ? I.mb : I.ma;
         u64 x = s1 ? pb : pa;
         const unsigned y = (unsigned)pick(w2, (u64)(m * (m - 1)));
-        const int h1 = (int)(y / (unsigned)(m - 1)), rr = (int)(y % (unsigned)(m - 1));
+        const unsigned yh = div_by(y, s1 ? I.mg_mb1 : I.mg_ma1);
+        const int h1 = (int)yh, rr = (int)(y - yh * (unsigned)(m - 1));
         const int h2 = rr + (rr >= h1 ? 1 : 0);
         const int q1 = nth_set(~x & I.normask, h1), q2 = nth_set(~x & I.normask, h2);
         oi = min(o1, o2); oj = max(o1, o2); oa = min(q1, q2); ob = max(q1, q2);
@@ -319,7 +321,8 @@ __device__ __forceinline__ int classify(const DevInst &I, u64 pa, u64 pb, u64 w0
     const int n = I.n;
     if (n < 2) return -1;
     const unsigned xe = (unsigned)pick(w1, (u64)(n * (n - 1)));
-    const int e1 = (int)(xe / (unsigned)(n - 1)), r = (int)(xe % (unsigned)(n - 1));
+    const unsigned q1 = div_by(xe, I.mg_n1);
+    const int e1 = (int)q1, r = (int)(xe - q1 * (unsigned)(n - 1));
     const int e2 = r + (r >= e1 ? 1 : 0);
     *ep = (unsigned)e1 | ((unsigned)e2 << 8);
     const int s1 = e1 >= I.na, s2 = e2 >= I.na;
@@ -337,6 +340,7 @@ struct K1Smem {
     ulonglong2 key[CAP_M];
     double cper[CAP_M];
     unsigned off[CAP_M + 1];
+    unsigned short att_det[CHUNK];  // parent of attempt a < CHUNK of a bucket, 0xffff: look it up in off[]
     unsigned char fl[CAP_M];
     SpawnRec rec[CHUNK];
     int qn[NQ];
@@ -439,6 +443,13 @@ struct BucketMap {
     const K1Smem *S;
     __device__ unsigned det_of(unsigned a, u64 &k) const
     {
+        if (a < (unsigned)CHUNK) {
+            const unsigned d = S->att_det[a];
+            if (d != 0xffffu) {
+                k = a - S->off[d];
+                return d;
+            }
+        }
         int lo = 0, hi = CAP_M;  // largest d with off[d] <= a (off[CAP_M] = total > a)
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -548,6 +559,9 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn(const DevInst *__restri
             S.fl[d] = (unsigned char)fl;
             mine += nl[j];
         }
+        // the parents of the first CHUNK attempts, written below by the
+        // determinants with few attempts; the others are found by bisection
+        for (int q = t; q < CHUNK; q += K1_THREADS) S.att_det[q] = 0xffffu;
         // exclusive scan of the light attempt counts in determinant order
         unsigned v = mine;
         for (int o = 1; o < 32; o <<= 1) {
@@ -568,6 +582,8 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn(const DevInst *__restri
         unsigned ex = v - mine + (warp ? S.wsum[warp - 1] : 0u);
         for (int j = 0; j < PER; j++) {
             S.off[PER * t + j] = ex;
+            if (nl[j] <= 8u && ex + nl[j] <= (unsigned)CHUNK)
+                for (unsigned q = 0; q < nl[j]; q++) S.att_det[ex + q] = (unsigned short)(PER * t + j);
             ex += nl[j];
         }
         if (t == K1_THREADS - 1) S.off[CAP_M] = ex;
@@ -2066,13 +2082,14 @@ cudaError_t init_kernels()
 
 size_t annihilate_smem_bytes() { return sizeof(K3Smem); }
 
-// Whether a run's buckets can go through the staged kernel: spawn regions
-// that fit its stage, and every array a bulk copy reads on a 16-byte
-// boundary (a caller-supplied allocator may return less aligned memory)
+// Whether a run's buckets can go through the staged kernel: every array a
+// bulk copy reads on a 16-byte boundary (a caller-supplied allocator may
+// return less aligned memory) and an even spawn capacity; buckets whose
+// spawns exceed the stage are deferred to the large-bucket kernel
 bool staged_annihilation_fits(const DevInst &I)
 {
     auto al = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
-    if (I.side || I.adaptive || I.cap_s > STAGED_SCAP || (I.cap_s & 1)) return false;
+    if (I.side || I.adaptive || (I.cap_s & 1)) return false;
     for (int k = 0; k < 2; k++)
         if (!al(I.key[k]) || !al(I.c[k]) || !al(I.hd[k]) || !al(I.fl[k])) return false;
     return al(I.skey) && al(I.sw);

@@ -71,3 +71,21 @@ def test_autotuned_geometry_changes_no_result():
     fq.fciqmc_step_batch(b, 20)
     for x, y in zip(a, b):
         assert_states_equal(fq.fciqmc_export_state(x), fq.fciqmc_export_state(y))
+
+
+def test_all_64_batched_hubbard_runs_equal_alone():
+    """The batched set (64 uneven 2D Hubbard runs: 3x4, 4x4, 4x5, U/t 2/4/8,
+    targets 1e4 .. 1e6): after 150 iterations in one batch every run's
+    walker list, shift and counters equal the same run stepped alone."""
+    fq = _fq()
+    runs = [(s, dict(p, shift_damping=0.5, shift_interval=5)) for s, p in workloads.batched_hubbard_instances(64)]
+    batch = [fq.fciqmc_create(s, p) for s, p in runs]
+    fq.fciqmc_step_batch(batch, 150)
+    for (s, p), hb in zip(runs, batch):
+        ha = fq.fciqmc_create(s, p)
+        fq.fciqmc_step(ha, 150)
+        assert_states_equal(fq.fciqmc_export_state(hb), fq.fciqmc_export_state(ha))
+        sb, sa = fq.fciqmc_iter_stats_get(hb), fq.fciqmc_iter_stats_get(ha)
+        for k in ["nw", "shift", "ndet", "attempts", "spawns", "rejected", "annihilated", "e_den"]:
+            np.testing.assert_array_equal(np.asarray(sb[k]), np.asarray(sa[k]), err_msg=k)
+        del ha
