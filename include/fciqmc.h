@@ -425,12 +425,18 @@ int fciqmc_server_poll(fciqmc_server *srv, int64_t id, fciqmc_request_status *ou
 double fciqmc_server_clock(fciqmc_server *srv);
 void fciqmc_server_destroy(fciqmc_server *srv);
 
-/* Autotuner of the launch geometry: times n_iter iterations of the batch
- * hs[0..k-1] (advancing it) for each candidate grid size, in blocks per SM, of
- * the spawning (2, 4, 8, 16), heavy-spawning (1, 2, 4) and annihilation
- * (3, 9, 24) kernels, keeps the fastest for every later launch in the
- * process, and writes it to out[3] (spawn, heavy, annihilation).  Defaults:
- * 8, 2, 9.  Results of the runs do not depend on the geometry. */
+/* Autotuner of the launch configuration: times n_iter iterations of the
+ * batch hs[0..k-1] (advancing it) for each candidate, keeps the fastest for
+ * every later launch in the process, and writes it to out[3] (spawn, heavy,
+ * annihilation).  Candidates: for the spawning kernel 0 = the staged kernel
+ * (256-thread blocks, three per SM, each bucket's keys, amplitudes and flags
+ * brought into shared memory by bulk copies one bucket ahead) or 2, 4, 8, 16
+ * = the plain-load kernel with that many blocks per SM; the heavy-spawning
+ * kernel's grid (1, 2, 4 blocks per SM); for the annihilation 0 = the staged
+ * kernel (two 256-thread blocks per SM, bulk copies one bucket ahead) or 3,
+ * 9, 24 = the plain-load kernel (three resident per SM) with that grid.
+ * Defaults: 0, 2, 0.  Results of the runs do not depend on the
+ * configuration. */
 int fciqmc_autotune(fciqmc_handle **hs, int32_t k, int64_t n_iter, int32_t out[3]);
 
 /* Device timing of the kernels of the last fciqmc_step call (milliseconds per

@@ -277,7 +277,7 @@ static int enqueue_iteration(fciqmc_handle *h, cudaEvent_t *ev)
 {
     const int units = 1 << h->bb;
     if (ev) cudaEventRecord(ev[0], h->stream);
-    launch_spawn(h->dinst, h->dunit, 1, units, h->stream);
+    launch_spawn(h->dinst, h->dunit, 1, units, staged_spawn_fits(h->hi), h->stream);
     if (ev) cudaEventRecord(ev[1], h->stream);
     launch_spawn_heavy(h->dinst, 1, h->stream);
     if (ev) cudaEventRecord(ev[2], h->stream);
@@ -1740,7 +1740,9 @@ static int step_batch_impl(fciqmc_handle **hs, int32_t k, int64_t n_iter)
         cleanup();
         cudaGraph_t g;
         CUDA_TRY(h0, cudaStreamBeginCapture(h0->stream, cudaStreamCaptureModeThreadLocal));
-        launch_spawn(dinst, dunit, k, units, h0->stream);
+        bool sp_staged = true;
+        for (int i = 0; i < k; i++) sp_staged = sp_staged && staged_spawn_fits(tab[i]);
+        launch_spawn(dinst, dunit, k, units, sp_staged, h0->stream);
         launch_spawn_heavy(dinst, k, h0->stream);
         if (max_nd > 0) launch_semistoch(dinst, k, max_nd, h0->stream);
         bool general = false, staged = true;
@@ -2450,8 +2452,10 @@ extern "C" void fciqmc_free_system(fciqmc_system *sys)
 static int autotune_impl(fciqmc_handle **hs, int32_t k, int64_t n_iter, int32_t out[3])
 {
     if (!hs || k < 1 || n_iter < 1 || !out) return FCIQMC_ERR_INVALID_ARG;
-    const int spawn_c[] = {2, 4, 8, 16}, anni_c[] = {3, 9, 24}, heavy_c[] = {1, 2, 4};
-    int best_s = 8, best_h = 2, best_a = 9;
+    // annihilation: 0 = the staged kernel (bulk copies one bucket ahead, two
+    // blocks per SM), else the plain-load kernel with that many blocks per SM
+    const int spawn_c[] = {0, 2, 4, 8, 16}, anni_c[] = {0, 3, 9, 24}, heavy_c[] = {1, 2, 4};
+    int best_s = 0, best_h = 2, best_a = 0;
     double best = 1e300;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);

@@ -222,7 +222,8 @@ struct TrialEnt {
 };
 
 // host-side launchers (kernels.cu)
-void launch_spawn(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, cudaStream_t s);
+void launch_spawn(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, bool staged, cudaStream_t s);
+bool staged_spawn_fits(const DevInst &I);
 void launch_spawn_heavy(const DevInst *dinst, int n_inst, cudaStream_t s);
 void launch_semistoch(const DevInst *dinst, int n_inst, int max_nd, cudaStream_t s);
 cudaError_t launch_annihilate(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, bool general,

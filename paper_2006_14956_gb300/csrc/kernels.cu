@@ -308,14 +308,18 @@ __device__ void spawn_double_pchb(const DevInst &I, u64 pa, u64 pb, double cper,
 }
 
 // class of one attempt from its first two words, or -1 for a failed attempt;
-// for a double, *ep = e1 | e2 << 8 (the ordered electron pair drawn from w1)
+// *ep = the electron of a single or a hop, or for a double e1 | e2 << 8 (the
+// ordered electron pair), all drawn from w1
 enum { Q_DOUBLE = 0, Q_SINGLE = 1, Q_HOP = 2, NQ = 3 };
 __device__ __forceinline__ int classify(const DevInst &I, u64 pa, u64 pb, u64 w0, u64 w1, unsigned *ep)
 {
-    *ep = 0;
-    if (I.kind == FCIQMC_HUBBARD) return Q_HOP;
+    if (I.kind == FCIQMC_HUBBARD) {
+        *ep = (unsigned)pick(w1, (u64)I.n);  // the electron that hops
+        return Q_HOP;
+    }
     if ((w0 >> 11) < I.tsingle) {
         const int e = (int)pick(w1, (u64)I.n);
+        *ep = (unsigned)e;  // the excited electron
         return (e >= I.na ? I.mb : I.ma) == 0 ? -1 : Q_SINGLE;
     }
     const int n = I.n;
@@ -332,11 +336,12 @@ __device__ __forceinline__ int classify(const DevInst &I, u64 pa, u64 pb, u64 w0
 
 constexpr int CHUNK = 1024;  // attempts drawn and queued per round
 struct SpawnRec {
-    u64 w1, w2, w3;
+    u64 w2, w3;
     unsigned det;
-    unsigned ep;  // electron pair of a double (classify)
+    unsigned ep;  // electron (single, hop) or electron pair (double) drawn from w1 (classify)
 };
 struct K1Smem {
+    static constexpr int chunk = CHUNK;
     ulonglong2 key[CAP_M];
     double cper[CAP_M];
     unsigned off[CAP_M + 1];
@@ -357,9 +362,10 @@ static_assert(3 * (sizeof(K1Smem) + 1024) <= 233472, "three spawn blocks per SM 
 // at a time from a shared counter, singles (the long exact sums) first, so
 // that no warp idles at the chunk's closing barrier while others still hold
 // a long queue.
-template <typename MAP>
-__device__ void run_attempts(const DevInst &I, K1Smem &S, long long it, unsigned A, MAP map, int par, double shift)
+template <typename MAP, typename SM>
+__device__ void run_attempts(const DevInst &I, SM &S, long long it, unsigned A, MAP map, int par, double shift)
 {
+    constexpr int CHUNK = SM::chunk;
     const int t = threadIdx.x, lane = t & 31;
     for (unsigned a0 = 0; a0 < A; a0 += CHUNK) {
         const unsigned a1 = min(A, a0 + CHUNK);
@@ -405,7 +411,7 @@ __device__ void run_attempts(const DevInst &I, K1Smem &S, long long it, unsigned
                 if (front || back) {
                     const int slot = front ? bf + __popc(mf & below) : CHUNK - 1 - (bk + __popc(mb & below));
                     SpawnRec &r = S.rec[slot];
-                    r.w1 = w[h][1]; r.w2 = w[h][2]; r.w3 = w[h][3]; r.det = det[h]; r.ep = ep[h];
+                    r.w2 = w[h][2]; r.w3 = w[h][3]; r.det = det[h]; r.ep = ep[h];
                 }
             }
         }
@@ -422,7 +428,7 @@ __device__ void run_attempts(const DevInst &I, K1Smem &S, long long it, unsigned
                 const unsigned d = r.det;
                 const ulonglong2 kk = map.key(d);
                 const SpawnCtx cx{map.slot(d), par, shift};
-                const int e = (int)pick(r.w1, (u64)I.n);
+                const int e = (int)r.ep;
                 if (I.kind == FCIQMC_HUBBARD)
                     spawn_hop_e(I, kk.x, kk.y, map.cper(d), map.flags(d), e, r.w2, r.w3, cx);
                 else spawn_single_e(I, kk.x, kk.y, map.cper(d), map.flags(d), e, r.w2, r.w3, cx);
@@ -1633,6 +1639,244 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k_annihilate_staged(const DevIn
     }
 }
 
+// ------------------------------------------------------------------ staged spawning
+// The spawning kernel with every bucket's keys, amplitudes and flags brought
+// into shared memory by bulk copies one bucket ahead (the bucket's count one
+// bucket earlier still), as in the staged annihilation; C_i / n_att is
+// written over the staged amplitude.  Chunks of 512 attempts keep three
+// blocks per SM.
+constexpr int CHUNK_S = 512;
+struct K6Smem {
+    static constexpr int chunk = CHUNK_S;
+    ulonglong2 skey[2][CAP_M];
+    double sc[2][CAP_M];            // C as copied; C / n_att once the bucket is loaded
+    unsigned char sfl[2][CAP_M];
+    unsigned off[CAP_M + 1];
+    unsigned short att_det[CHUNK_S];
+    unsigned char fl[CAP_M];        // initiator | in-D bits of the current bucket
+    SpawnRec rec[CHUNK_S];
+    int qn[NQ];
+    int next;
+    unsigned wsum[K1_THREADS / 32];
+    u64 bar[2];
+    int binfo[2][4];                // per stage: bucket (-1: nothing staged), m, run, parity
+    long long bit[2];
+    double bS[2];
+};
+static_assert(3 * (sizeof(K6Smem) + 1024) <= 233472, "three staged spawning blocks per SM");
+
+struct StagedBucketMap {
+    const K6Smem *S;
+    int q;
+    __device__ unsigned det_of(unsigned a, u64 &k) const
+    {
+        if (a < (unsigned)CHUNK_S) {
+            const unsigned d = S->att_det[a];
+            if (d != 0xffffu) {
+                k = a - S->off[d];
+                return d;
+            }
+        }
+        int lo = 0, hi = CAP_M;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (S->off[mid] <= a) lo = mid; else hi = mid;
+        }
+        k = a - S->off[lo];
+        return (unsigned)lo;
+    }
+    __device__ ulonglong2 key(unsigned d) const { return S->skey[q][d]; }
+    __device__ double cper(unsigned d) const { return S->sc[q][d]; }
+    __device__ unsigned flags(unsigned d) const { return S->fl[d]; }
+    __device__ unsigned slot(unsigned d) const { return base + d; }
+    unsigned base;
+};
+
+struct SpawnMeta {
+    int u, ii, b, m, par, err;
+    long long it;
+    double S;
+};
+
+// thread 0: the run's state (once per run the block meets) and the bucket's count
+__device__ __forceinline__ void spawn_meta_load(const DevInst *__restrict__ insts, const int *__restrict__ unit_start,
+                                                int n_inst, int u, SpawnMeta &M)
+{
+    M.u = u;
+    if (u < 0) return;
+    const int ii = find_inst(unit_start, n_inst, u);
+    const DevInst &I = insts[ii];
+    if (ii != M.ii) {
+        M.ii = ii;
+        M.err = *(volatile int *)&I.st->err;
+        M.par = I.st->parity;
+        M.it = I.st->iter;
+        M.S = I.st->S;
+        I.st->err_at_start = M.err;  // the state seen when this run's spawning began
+    }
+    M.b = u - I.unit0;
+    M.m = I.cnt[M.par][M.b];
+}
+
+// thread 0: the bulk copies of unit M.u's bucket into stage q
+__device__ void spawn_stage_issue(const DevInst *__restrict__ insts, const SpawnMeta &M, K6Smem &S, int q)
+{
+    int *bi = S.binfo[q];
+    bi[0] = -1;
+    if (M.u < 0 || M.err) return;
+    const DevInst &I = insts[M.ii];
+    const int m = M.m, par = M.par;
+    const size_t base = (size_t)M.b * CAP_M;
+    const unsigned m2 = (unsigned)((m + 1) & ~1), m16 = (unsigned)((m + 15) & ~15);
+    const unsigned bytes = m ? (unsigned)m * 16u + m2 * 8u + m16 : 0u;
+    bi[1] = m; bi[2] = M.ii; bi[3] = par;
+    S.bit[q] = M.it;
+    S.bS[q] = M.S;
+    bi[0] = M.b;
+    if (bytes == 0) {
+        asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(&S.bar[q]))
+                     : "memory");
+        return;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&S.bar[q], bytes);
+    bulk_g2s(S.skey[q], I.key[par] + base, (unsigned)m * 16u, &S.bar[q]);
+    bulk_g2s(S.sc[q], I.c[par] + base, m2 * 8u, &S.bar[q]);
+    bulk_g2s(S.sfl[q], I.fl[par] + base, m16, &S.bar[q]);
+}
+
+__global__ void __launch_bounds__(K1_THREADS, 3) k_spawn_staged(const DevInst *__restrict__ insts,
+                                                             const int *__restrict__ unit_start, int n_inst,
+                                                             int n_units)
+{
+    extern __shared__ __align__(128) unsigned char k6_raw[];
+    K6Smem &S = *reinterpret_cast<K6Smem *>(k6_raw);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    constexpr int PER = CAP_M / K1_THREADS;
+    SpawnMeta nxt;
+    nxt.ii = -1;
+    if (t == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        SpawnMeta first;
+        first.ii = -1;
+        spawn_meta_load(insts, unit_start, n_inst, (int)blockIdx.x < n_units ? (int)blockIdx.x : -1, first);
+        spawn_stage_issue(insts, first, S, 0);
+        nxt.ii = first.ii;
+        nxt.err = first.err; nxt.par = first.par; nxt.it = first.it; nxt.S = first.S;
+        const int un = (int)blockIdx.x + (int)gridDim.x;
+        spawn_meta_load(insts, unit_start, n_inst, un < n_units ? un : -1, nxt);
+    }
+    __syncthreads();
+    unsigned phase[2] = {0u, 0u};
+    int q = 0;
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x, q ^= 1) {
+        if (t == 0) {
+            spawn_stage_issue(insts, nxt, S, q ^ 1);
+            const int un = u + 2 * (int)gridDim.x;
+            spawn_meta_load(insts, unit_start, n_inst, un < n_units ? un : -1, nxt);
+        }
+        const int b = S.binfo[q][0];
+        if (b < 0) {
+            __syncthreads();  // binfo[q ^ 1] is written before anyone reads it
+            continue;
+        }
+        const bool ok = mbar_wait(&S.bar[q], phase[q]);
+        const int m = S.binfo[q][1], ii = S.binfo[q][2], par = S.binfo[q][3];
+        const long long it = S.bit[q];
+        const double shift = S.bS[q];
+        const DevInst &I = insts[ii];
+        if (__syncthreads_or(!ok)) {  // the copies did not land within the bound
+            if (t == 0) atomicOr(&I.st->err, ERRB_TIMEOUT);
+            mbar_wait(&S.bar[q], phase[q]);
+            if (S.binfo[q ^ 1][0] >= 0) mbar_wait(&S.bar[q ^ 1], phase[q ^ 1]);
+            return;
+        }
+        phase[q] ^= 1u;
+        const size_t base = (size_t)b * CAP_M;
+        // the bucket from the stage: thread t owns determinants PER*t .. PER*t+PER-1
+        long long att = 0;
+        unsigned mine = 0;
+        unsigned nl[PER];
+        for (int j = 0; j < PER; j++) {
+            const int d = PER * t + j;
+            nl[j] = 0;
+            if (d >= m) continue;
+            const double c = S.sc[q][d];
+            const uint8_t f = S.sfl[q][d];
+            unsigned fl = 0;
+            double cper = 0.0;
+            u64 nat = 0;
+            if (!is_zero(c)) {
+                if (!abs_lt(c, 0x1p31)) {
+                    atomicOr(&I.st->err, ERRB_NUMERIC);
+                } else {
+                    nat = ceil_abs(c);
+                    const bool init = (dbits(c) & ~SIGN64) > dbits(I.n_a) || (f & (DFLAG_REF | DFLAG_D));
+                    fl = (init ? 1u : 0u) | ((f & DFLAG_D) ? 2u : 0u);
+                    cper = nat == 1 ? c : c / (double)nat;  // c / 1 is c
+                    att += (long long)nat;
+                    if (nat > HEAVY_ATT) {  // sliced into the heavy queue
+                        const ulonglong2 kk = S.skey[q][d];
+                        const unsigned nch = (unsigned)((nat + HEAVY_ATT - 1) / HEAVY_ATT);
+                        const int q0 = atomicAdd(&I.st->heavy_n, (int)nch);
+                        if ((long long)q0 + nch > (long long)I.heavy_cap) atomicOr(&I.st->err, ERRB_HEAVY_CAP);
+                        else
+                            for (unsigned h = 0; h < nch; h++) {
+                                HeavyChunk hc;
+                                hc.a = kk.x; hc.b = kk.y; hc.cper = cper; hc.k0 = (u64)h * HEAVY_ATT;
+                                const u64 left = nat - hc.k0;
+                                hc.count = (unsigned)(left < HEAVY_ATT ? left : HEAVY_ATT);
+                                hc.flags = fl;
+                                hc.slot = (uint32_t)(base + d);
+                                hc.pad = 0;
+                                I.heavy[q0 + h] = hc;
+                            }
+                    } else {
+                        nl[j] = (unsigned)nat;
+                    }
+                }
+            }
+            S.sc[q][d] = cper;
+            S.fl[d] = (unsigned char)fl;
+            mine += nl[j];
+        }
+        for (int a = t; a < CHUNK_S; a += K1_THREADS) S.att_det[a] = 0xffffu;
+        // exclusive scan of the light attempt counts in determinant order
+        unsigned v = mine;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane == 31) S.wsum[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned x = lane < K1_THREADS / 32 ? S.wsum[lane] : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane < K1_THREADS / 32) S.wsum[lane] = x;
+        }
+        __syncthreads();
+        unsigned ex = v - mine + (warp ? S.wsum[warp - 1] : 0u);
+        for (int j = 0; j < PER; j++) {
+            S.off[PER * t + j] = ex;
+            if (nl[j] <= 8u && ex + nl[j] <= (unsigned)CHUNK_S)
+                for (unsigned a = 0; a < nl[j]; a++) S.att_det[ex + a] = (unsigned short)(PER * t + j);
+            ex += nl[j];
+        }
+        if (t == K1_THREADS - 1) S.off[CAP_M] = ex;
+        __syncthreads();
+        const unsigned total = S.off[CAP_M];
+        StagedBucketMap map{&S, q, (unsigned)base};
+        run_attempts(I, S, it, total, map, par, shift);
+        for (int o = 16; o >= 1; o >>= 1) att += __shfl_xor_sync(0xffffffffu, att, o);
+        if (lane == 0 && att) red_add(&I.acc[(b % NSHARD) * ACC_STRIDE + ACC_ATT], (u64)att);
+    }
+}
+
 // GENERAL: the batch holds a run with replica side lists or adaptive shift,
 // whose buckets take the general path (anni_bucket); the others the
 // three-phase one.  Without it the kernel holds the three-phase path alone.
@@ -2039,7 +2283,10 @@ void launch_build_kidx(const DevInst *dinst, int parity, int nb, cudaStream_t s)
 // resident count, here 3 per SM for the spawning and annihilation kernels, the
 // hardware hands the next block to whichever slot frees first, which evens out
 // buckets of unequal size)
-static int g_spawn_bps = 8, g_heavy_bps = 2, g_anni_bps = 9;
+// g_spawn_bps = 0 and g_anni_bps = 0 select the staged kernels (one resident
+// wave, bulk copies one bucket ahead) wherever the batch fits them; otherwise
+// the plain-load kernels with that many blocks per SM
+static int g_spawn_bps = 0, g_heavy_bps = 2, g_anni_bps = 0;
 void set_launch_geometry(int spawn_bps, int heavy_bps, int anni_bps)
 {
     g_spawn_bps = spawn_bps;
@@ -2053,11 +2300,29 @@ void get_launch_geometry(int *spawn_bps, int *heavy_bps, int *anni_bps)
     *anni_bps = g_anni_bps;
 }
 
-void launch_spawn(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, cudaStream_t s)
+// the staged spawning kernel (g_spawn_bps = 0: one resident wave of three
+// blocks per SM) where every run's list arrays are 16-byte aligned; else the
+// plain-load kernel with g_spawn_bps blocks per SM
+void launch_spawn(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, bool staged, cudaStream_t s)
 {
-    int grid = n_units < num_sms() * g_spawn_bps ? n_units : num_sms() * g_spawn_bps;
+    if (staged && g_spawn_bps == 0) {
+        int grid = n_units < num_sms() * 3 ? n_units : num_sms() * 3;
+        if (grid < 1) grid = 1;
+        k_spawn_staged<<<grid, K1_THREADS, sizeof(K6Smem), s>>>(dinst, unit_start, n_inst, n_units);
+        return;
+    }
+    const int bps = g_spawn_bps > 0 ? g_spawn_bps : 8;
+    int grid = n_units < num_sms() * bps ? n_units : num_sms() * bps;
     if (grid < 1) grid = 1;
     k_spawn<<<grid, K1_THREADS, sizeof(K1Smem), s>>>(dinst, unit_start, n_inst, n_units);
+}
+
+bool staged_spawn_fits(const DevInst &I)
+{
+    auto al = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
+    for (int k = 0; k < 2; k++)
+        if (!al(I.key[k]) || !al(I.c[k]) || !al(I.fl[k])) return false;
+    return true;
 }
 
 void launch_spawn_heavy(const DevInst *dinst, int n_inst, cudaStream_t s)
@@ -2075,6 +2340,8 @@ cudaError_t init_kernels()
         e = cudaFuncSetAttribute(k_annihilate_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(K4Smem<STAGED_SCAP>));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spawn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K1Smem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_spawn_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K6Smem));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_spawn_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K1Smem));
     return e;
@@ -2101,14 +2368,15 @@ bool staged_annihilation_fits(const DevInst &I)
 cudaError_t launch_annihilate(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, bool general,
                               bool staged, cudaStream_t s)
 {
-    if (staged && !general) {
+    if (staged && !general && g_anni_bps == 0) {
         int grid = n_units < num_sms() * 2 ? n_units : num_sms() * 2;
         if (grid < 1) grid = 1;
         k_annihilate_staged<<<grid, K3_THREADS, sizeof(K4Smem<STAGED_SCAP>), s>>>(dinst, unit_start, n_inst, n_units);
         return cudaGetLastError();
     }
     const size_t smem = sizeof(K3Smem);
-    int grid = n_units < num_sms() * g_anni_bps ? n_units : num_sms() * g_anni_bps;
+    const int bps = g_anni_bps > 0 ? g_anni_bps : 9;
+    int grid = n_units < num_sms() * bps ? n_units : num_sms() * bps;
     if (grid < 1) grid = 1;
     if (general) k_annihilate<true><<<grid, K3_THREADS, smem, s>>>(dinst, unit_start, n_inst, n_units);
     else k_annihilate<false><<<grid, K3_THREADS, smem, s>>>(dinst, unit_start, n_inst, n_units);
