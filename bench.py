@@ -361,6 +361,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="abinitio50",
                     choices=["abinitio50", "abinitio24", "batch", "batch-sigma", "serving"])
+    ap.add_argument("--target", type=float, default=0.0,
+                    help="walker target in place of the workload's (smaller cases for profiling)")
     ap.add_argument("--equil", type=int, default=200,
                     help="untimed iterations after E_proj's equilibration start (shift start + 500)")
     ap.add_argument("--generator", default="uniform", choices=["uniform", "pchb"],
@@ -398,6 +400,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     sysd, prm = workload_params(seed_offset=rank, workload=args.workload, generator=args.generator)
+    if args.target:  # a smaller list of the same workload (profiling captures)
+        prm = dict(prm, target_walkers=args.target, initial_walkers=min(prm["initial_walkers"], args.target / 100.0))
     big = args.workload == "abinitio50"
     h = fq.fciqmc_create(sysd, prm)
     # growth and equilibration, untimed: until E_proj has `--equil` samples

@@ -430,14 +430,27 @@ void fciqmc_server_destroy(fciqmc_server *srv);
  * every later launch in the process, and writes it to out[3] (spawn, heavy,
  * annihilation).  Candidates: for the spawning kernel 0 = the staged kernel
  * (256-thread blocks, three per SM, each bucket's keys, amplitudes and flags
- * brought into shared memory by bulk copies one bucket ahead) or 2, 4, 8, 16
- * = the plain-load kernel with that many blocks per SM; the heavy-spawning
+ * brought into shared memory by bulk copies one bucket ahead), 1 = split
+ * spawning (see fciqmc_set_launch_config) or 2, 4, 8, 16 = the plain-load
+ * kernel with that many blocks per SM; the heavy-spawning
  * kernel's grid (1, 2, 4 blocks per SM); for the annihilation 0 = the staged
  * kernel (two 256-thread blocks per SM, bulk copies one bucket ahead) or 3,
  * 9, 24 = the plain-load kernel (three resident per SM) with that grid.
- * Defaults: 0, 2, 0.  Results of the runs do not depend on the
+ * Defaults: 1, 2, 0.  Results of the runs do not depend on the
  * configuration. */
 int fciqmc_autotune(fciqmc_handle **hs, int32_t k, int64_t n_iter, int32_t out[3]);
+
+/* Sets (or reads) the launch configuration the autotuner chooses from, for
+ * every later launch in the process: spawn 0 = the staged kernel, 1 = split
+ * spawning (the staged kernel draws and queues every attempt in global
+ * memory by class, 48 bytes each; a flat kernel evaluates them one per
+ * thread), 2, 4, 8, 16 = the plain-load kernel with that many blocks per SM;
+ * heavy = blocks per SM of the heavy-determinant kernel (1..16); annihilate
+ * as for fciqmc_autotune (0, 3, 9, 24).  A handle captures its iteration graph
+ * again at its next step.  FCIQMC_ERR_INVALID_ARG for other values.  Results
+ * of the runs do not depend on the configuration. */
+int fciqmc_set_launch_config(int32_t spawn, int32_t heavy, int32_t annihilate);
+int fciqmc_get_launch_config(int32_t out[3]);
 
 /* Device timing of the kernels of the last fciqmc_step call (milliseconds per
  * iteration, averaged), measured with CUDA events on the handle's stream:

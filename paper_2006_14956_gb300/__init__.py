@@ -134,6 +134,8 @@ _SIGS = {
     "fciqmc_ref_offdiag_sum_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                                  C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p]),
     "fciqmc_graph_kernels": (C.c_int32, [_H]),
+    "fciqmc_set_launch_config": (C.c_int, [C.c_int32, C.c_int32, C.c_int32]),
+    "fciqmc_get_launch_config": (C.c_int, [C.POINTER(C.c_int32)]),
     "fciqmc_semistoch_info": (C.c_int64, [_H, C.POINTER(C.c_int64)]),
     "fciqmc_server_create": (C.c_int, [C.c_int64, C.c_int32, C.c_void_p, C.POINTER(_H)]),
     "fciqmc_server_submit": (C.c_int, [_H, C.POINTER(fciqmc_system), C.POINTER(fciqmc_params), C.c_double,
@@ -516,6 +518,17 @@ def fciqmc_read_fcidump(path):
         return dict(kind="abinitio", norb=N, n_alpha=s.n_alpha, n_beta=s.n_beta, h1=h1, eri=eri, ecore=s.ecore)
     finally:
         _lib.fciqmc_free_system(C.byref(s))
+
+
+def fciqmc_set_launch_config(spawn, heavy, annihilate):
+    """Launch configuration of every later launch (see include/fciqmc.h)."""
+    _check(_lib.fciqmc_set_launch_config(int(spawn), int(heavy), int(annihilate)))
+
+
+def fciqmc_get_launch_config():
+    out = (C.c_int32 * 3)()
+    _check(_lib.fciqmc_get_launch_config(out))
+    return dict(spawn=out[0], heavy=out[1], annihilate=out[2])
 
 
 def fciqmc_autotune(handles, n_iter):

@@ -54,6 +54,7 @@ struct fciqmc_handle {
     IterState *dstate = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_kernels = 0;  // kernel nodes of the captured iteration
+    int graph_gen = -1;     // launch-configuration generation the graph was captured with
     bool profiling = false;
     double ktime[6] = {0, 0, 0, 0, 0, 0};  // spawn, heavy, annihilate, finalize, semistoch, new-determinant H_jj
     // layout
@@ -277,7 +278,9 @@ static int enqueue_iteration(fciqmc_handle *h, cudaEvent_t *ev)
 {
     const int units = 1 << h->bb;
     if (ev) cudaEventRecord(ev[0], h->stream);
-    launch_spawn(h->dinst, h->dunit, 1, units, staged_spawn_fits(h->hi), h->stream);
+    const bool st = staged_spawn_fits(h->hi), split = st && h->hi.qcnt != nullptr && spawn_split_selected();
+    launch_spawn(h->dinst, h->dunit, 1, units, st, split, h->stream);
+    if (split) launch_spawn_eval(h->dinst, 1, h->stream);
     if (ev) cudaEventRecord(ev[1], h->stream);
     launch_spawn_heavy(h->dinst, 1, h->stream);
     if (ev) cudaEventRecord(ev[2], h->stream);
@@ -310,16 +313,53 @@ static int count_kernel_nodes(cudaGraph_t g)
     return k;
 }
 
+// the attempt queues of split spawning, allocated when that mode is selected
+// (and the run's arrays suit the staged kernels): QSEG segments per class, each
+// sized from the requested count (need, per class), at least 4096 entries
+static int ensure_queues(fciqmc_handle *h, long long need0 = 0, long long need1 = 0)
+{
+    DevInst &I = h->hi;
+    if (!spawn_split_selected() || !staged_spawn_fits(I)) return FCIQMC_OK;
+    bool changed = false;
+    if (!I.qcnt) {
+        I.qcnt = (int *)dev_alloc(h, 2 * QSEG * QSTRIDE * sizeof(int));
+        if (!I.qcnt) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (attempt queues)");
+        CUDA_TRY(h, cudaMemsetAsync(I.qcnt, 0, 2 * QSEG * QSTRIDE * sizeof(int), h->stream));
+        changed = true;
+    }
+    const long long want[2] = {std::max<long long>(4096, need0), std::max<long long>(4096, need1)};
+    for (int c = 0; c < 2; c++) {
+        if (I.qrec[c] && I.qcap[c] >= want[c]) continue;
+        long long cap = I.qcap[c] > 0 ? I.qcap[c] : 4096;
+        while (cap < want[c]) cap = cap + cap / 2;
+        if (cap > (1LL << 30)) return fail(h, FCIQMC_ERR_CAPACITY, "attempt queue limit reached");
+        dev_free(h, I.qrec[c]);
+        I.qrec[c] = (QRec *)dev_alloc(h, (size_t)QSEG * (size_t)cap * sizeof(QRec));
+        if (!I.qrec[c]) {
+            I.qcap[c] = 0;
+            return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (attempt queues)");
+        }
+        I.qcap[c] = cap;
+        changed = true;
+    }
+    return changed ? upload_inst(h) : FCIQMC_OK;  // the device copy of the descriptor follows
+}
+
 static int capture_graph(fciqmc_handle *h)
 {
     if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
     cudaGraph_t g;
+    {
+        const int rq = ensure_queues(h);
+        if (rq) return rq;
+    }
     CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     int rc = enqueue_iteration(h, nullptr);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (rc) return rc;
     if (e != cudaSuccess) return fail(h, FCIQMC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     h->graph_kernels = count_kernel_nodes(g);
+    h->graph_gen = launch_geometry_generation();
     e = cudaGraphInstantiate(&h->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(h, FCIQMC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
@@ -434,6 +474,9 @@ static int reset_after_error(fciqmc_handle *h)
     h->hst.need_main = 0;
     h->hst.n_spawn_over = 0;
     h->hst.new_n = 0;
+    h->hst.need_queue[0] = 0;
+    h->hst.need_queue[1] = 0;
+    if (h->hi.qcnt) CUDA_TRY(h, cudaMemsetAsync(h->hi.qcnt, 0, 2 * QSEG * QSTRIDE * sizeof(int), h->stream));
     CUDA_TRY(h, cudaMemsetAsync(h->hi.acc, 0, NSHARD * ACC_STRIDE * sizeof(u64), h->stream));  // partial totals
     // the failed iteration's adaptive-shift weight sums are discarded when the
     // descriptor is next uploaded (the device copy may still describe an old
@@ -1122,6 +1165,25 @@ int fciqmc_layout(fciqmc_handle *h, int64_t out[4])
 
 int32_t fciqmc_graph_kernels(fciqmc_handle *h) { return h ? h->graph_kernels : -1; }
 
+int fciqmc_set_launch_config(int32_t spawn, int32_t heavy, int32_t annihilate)
+{
+    const bool sp_ok = spawn == 0 || spawn == 1 || spawn == 2 || spawn == 4 || spawn == 8 || spawn == 16;
+    const bool hv_ok = heavy >= 1 && heavy <= 16;
+    const bool an_ok = annihilate == 0 || annihilate == 3 || annihilate == 9 || annihilate == 24;
+    if (!sp_ok || !hv_ok || !an_ok) return FCIQMC_ERR_INVALID_ARG;
+    set_launch_geometry(spawn, heavy, annihilate);
+    return FCIQMC_OK;
+}
+
+int fciqmc_get_launch_config(int32_t out[3])
+{
+    if (!out) return FCIQMC_ERR_INVALID_ARG;
+    int a, b, c;
+    get_launch_geometry(&a, &b, &c);
+    out[0] = a; out[1] = b; out[2] = c;
+    return FCIQMC_OK;
+}
+
 int64_t fciqmc_semistoch_info(fciqmc_handle *h, int64_t *nnz)
 {
     if (!h) return FCIQMC_ERR_INVALID_ARG;
@@ -1145,6 +1207,10 @@ static int step_impl(fciqmc_handle *h, int64_t n_iter)
     }
     int rc = read_state(h);
     if (rc) return rc;
+    if (h->graph && h->graph_gen != launch_geometry_generation()) {  // the launch configuration changed
+        rc = capture_graph(h);
+        if (rc) return rc;
+    }
     return step_to(h, h->hst.iter + n_iter);
 }
 
@@ -1168,6 +1234,10 @@ static int step_async_impl(fciqmc_handle *h, int64_t n_iter)
         if (rc) return rc;
         h->async_base = h->hst.iter;
         h->async_target = h->hst.iter;
+        if (h->graph && h->graph_gen != launch_geometry_generation()) {  // the launch configuration changed
+            rc = capture_graph(h);
+            if (rc) return rc;
+        }
     }
     for (int64_t k = 0; k < n_iter; k++) CUDA_TRY(h, cudaGraphLaunch(h->graph, h->stream));
     h->async_target += n_iter;
@@ -1318,6 +1388,7 @@ static int handle_flags(fciqmc_handle *h, int *retries)
     if (++*retries > 64) return fail(h, FCIQMC_ERR_CAPACITY, "capacity growth did not converge");
     const long long need = h->hst.need_spawn;
     const int n_over = h->hst.n_spawn_over;
+    const long long needq0 = h->hst.need_queue[0], needq1 = h->hst.need_queue[1];
     rc = reset_after_error(h);
     if (rc) return rc;
     if (err & (ERRB_SPAWN_CAP | ERRB_MAIN_CAP)) {
@@ -1334,6 +1405,10 @@ static int handle_flags(fciqmc_handle *h, int *retries)
     }
     if (err & ERRB_HEAVY_CAP) {
         rc = grow_heavy(h);
+        if (rc) return rc;
+    }
+    if (err & ERRB_QUEUE_CAP) {  // a segment of the attempt queues was too short: a quarter above the need
+        rc = ensure_queues(h, needq0 + needq0 / 4, needq1 + needq1 / 4);
         if (rc) return rc;
     }
     rc = ensure_side(h);
@@ -1726,6 +1801,8 @@ static int step_batch_impl(fciqmc_handle **hs, int32_t k, int64_t n_iter)
         max_nd = 0;
         int max_bk = 1;
         for (int i = 0; i < k; i++) {
+            int rq = ensure_queues(hs[i]);
+            if (rq) return rq;
             tab[i] = hs[i]->hi;
             tab[i].partner = pidx[i];
             max_bk = std::max(max_bk, 1 << hs[i]->bb);
@@ -1740,9 +1817,13 @@ static int step_batch_impl(fciqmc_handle **hs, int32_t k, int64_t n_iter)
         cleanup();
         cudaGraph_t g;
         CUDA_TRY(h0, cudaStreamBeginCapture(h0->stream, cudaStreamCaptureModeThreadLocal));
-        bool sp_staged = true;
-        for (int i = 0; i < k; i++) sp_staged = sp_staged && staged_spawn_fits(tab[i]);
-        launch_spawn(dinst, dunit, k, units, sp_staged, h0->stream);
+        bool sp_staged = true, split = spawn_split_selected();
+        for (int i = 0; i < k; i++) {
+            sp_staged = sp_staged && staged_spawn_fits(tab[i]);
+            split = split && tab[i].qcnt != nullptr;
+        }
+        launch_spawn(dinst, dunit, k, units, sp_staged, split, h0->stream);
+        if (split && sp_staged) launch_spawn_eval(dinst, k, h0->stream);
         launch_spawn_heavy(dinst, k, h0->stream);
         if (max_nd > 0) launch_semistoch(dinst, k, max_nd, h0->stream);
         bool general = false, staged = true;
@@ -2454,8 +2535,8 @@ static int autotune_impl(fciqmc_handle **hs, int32_t k, int64_t n_iter, int32_t 
     if (!hs || k < 1 || n_iter < 1 || !out) return FCIQMC_ERR_INVALID_ARG;
     // annihilation: 0 = the staged kernel (bulk copies one bucket ahead, two
     // blocks per SM), else the plain-load kernel with that many blocks per SM
-    const int spawn_c[] = {0, 2, 4, 8, 16}, anni_c[] = {0, 3, 9, 24}, heavy_c[] = {1, 2, 4};
-    int best_s = 0, best_h = 2, best_a = 0;
+    const int spawn_c[] = {0, 1, 2, 4, 8, 16}, anni_c[] = {0, 3, 9, 24}, heavy_c[] = {1, 2, 4};
+    int best_s = 1, best_h = 2, best_a = 0;
     double best = 1e300;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);

@@ -27,10 +27,11 @@ enum {
     ERRB_STOP = 64,       // the run reached its stop iteration inside a batch (not an error)
     ERRB_PAUSE_TRIAL = 128,  // iteration boundary at which the trial space must be built (not an error)
     ERRB_PARTNER = 256,      // the other replica of a pair failed this iteration: repeat it (not an error)
+    ERRB_QUEUE_CAP = 512,    // a segment of the attempt queues overflowed (split spawning)
 };
 // errors raised before the finalize kernel: a replica commits its iteration
 // only if neither it nor its partner has one
-constexpr int ERRB_STAGE = ERRB_SPAWN_CAP | ERRB_MAIN_CAP | ERRB_HEAVY_CAP | ERRB_NUMERIC | ERRB_TIMEOUT;
+constexpr int ERRB_STAGE = ERRB_SPAWN_CAP | ERRB_MAIN_CAP | ERRB_HEAVY_CAP | ERRB_NUMERIC | ERRB_TIMEOUT | ERRB_QUEUE_CAP;
 enum { DFLAG_REF = 1, DFLAG_D = 2 };
 
 // launch geometry
@@ -55,6 +56,19 @@ struct HeavyChunk {  // a slice of the attempts of one determinant with many wal
     uint32_t flags;  // bit 0: initiator, bit 1: parent in D
     uint32_t slot;   // the determinant's main-list slot (adaptive shift)
     uint32_t pad;
+};
+
+// Split spawning: every drawn attempt of a bucket is queued in global memory
+// by class (0: singles and lattice hops, 1: doubles), in segment b % QSEG of
+// its class, and evaluated by a flat kernel with one attempt per thread.
+constexpr int QSEG = 64;
+constexpr int QSTRIDE = 32;  // ints between two segment counters: each counter on its own 128-byte line
+struct QRec {  // 48 bytes
+    u64 ka, kb;      // parent
+    double cper;     // C_i / n_att
+    u64 w2, w3;      // hole word, rounding word
+    unsigned slot;   // parent's main-list slot (adaptive shift)
+    unsigned info;   // electron (single, hop) or pair e1 | e2 << 8 (double) | parent flags << 16
 };
 
 struct Partial {  // per-bucket binary64 sums of one iteration (estimators that need them)
@@ -108,6 +122,7 @@ struct IterState {  // device-resident iteration state of one run
     long long trial_built;  // 1 once the trial space exists
     int new_n;              // determinants created in this iteration (their H_jj is computed by k_new_diag)
     int err_at_start;       // err when the iteration's spawning began (nonzero: the iteration was skipped)
+    int need_queue[2];      // largest count a queue segment of each class needed (split spawning)
 };
 
 struct TrialEnt;
@@ -165,6 +180,9 @@ struct DevInst {
     size_t big_stride;
     HeavyChunk *heavy;
     int heavy_cap;
+    QRec *qrec[2];          // attempt queues by class: QSEG segments of qcap[class] entries each
+    int *qcnt;              // [2 * QSEG] counters, QSTRIDE ints apart: entries queued per segment (cleared by k_finalize)
+    long long qcap[2];
     Partial *part;
     u64 *acc;  // exact totals of the iteration: NSHARD lines of ACC_STRIDE words (see ACC_*)
     IterState *st;
@@ -222,7 +240,10 @@ struct TrialEnt {
 };
 
 // host-side launchers (kernels.cu)
-void launch_spawn(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, bool staged, cudaStream_t s);
+void launch_spawn(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, bool staged, bool split,
+                  cudaStream_t s);
+bool spawn_split_selected();
+void launch_spawn_eval(const DevInst *dinst, int n_inst, cudaStream_t s);
 bool staged_spawn_fits(const DevInst &I);
 void launch_spawn_heavy(const DevInst *dinst, int n_inst, cudaStream_t s);
 void launch_semistoch(const DevInst *dinst, int n_inst, int max_nd, cudaStream_t s);
@@ -263,6 +284,7 @@ cudaError_t launch_trial_w(const DevInst *dinst, const ulonglong2 *tkey, const d
                            int *err, cudaStream_t s);
 long long connections_per_det(int na, int nb, int ma, int mb);
 void set_launch_geometry(int spawn_bps, int heavy_bps, int anni_bps);
+int launch_geometry_generation();
 void get_launch_geometry(int *spawn_bps, int *heavy_bps, int *anni_bps);
 cudaError_t ref_abs_sum(const DevInst *dinst, double *dpartial, double *out, cudaStream_t s);
 size_t export_scratch_bytes(long long n);

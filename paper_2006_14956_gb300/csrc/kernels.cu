@@ -28,6 +28,7 @@
 // All of them read the iteration state from device memory, so one iteration
 // is captured once as a CUDA graph and replayed.
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "fq_device.cuh"
@@ -351,6 +352,7 @@ struct K1Smem {
     int qn[NQ];
     int next;  // evaluation counter of the chunk
     unsigned wsum[K1_THREADS / 32];
+    int qbase[2];
     int hdr_err, hdr_par;
     long long hdr_it;
     double hdr_S;
@@ -362,8 +364,12 @@ static_assert(3 * (sizeof(K1Smem) + 1024) <= 233472, "three spawn blocks per SM 
 // at a time from a shared counter, singles (the long exact sums) first, so
 // that no warp idles at the chunk's closing barrier while others still hold
 // a long queue.
-template <typename MAP, typename SM>
-__device__ void run_attempts(const DevInst &I, SM &S, long long it, unsigned A, MAP map, int par, double shift)
+// SPLIT: instead of evaluating the queues, the chunk's attempts are written
+// to the run's global attempt queues (segment b % QSEG of each class), with
+// everything the evaluation needs about the parent, for k_spawn_eval.
+template <bool SPLIT = false, typename MAP, typename SM>
+__device__ void run_attempts(const DevInst &I, SM &S, long long it, unsigned A, MAP map, int par, double shift,
+                             int b = 0)
 {
     constexpr int CHUNK = SM::chunk;
     const int t = threadIdx.x, lane = t & 31;
@@ -417,6 +423,37 @@ __device__ void run_attempts(const DevInst &I, SM &S, long long it, unsigned A, 
         }
         __syncthreads();
         const int nd = S.qn[Q_DOUBLE], ns = S.qn[Q_SINGLE], ntot = ns + nd;
+        if constexpr (SPLIT) {
+            // one reservation per class and chunk in the bucket's segments
+            const int seg = b % QSEG;
+            if (t == 0) {
+                S.qbase[0] = ns ? atomicAdd(I.qcnt + seg * QSTRIDE, ns) : 0;
+                S.qbase[1] = nd ? atomicAdd(I.qcnt + (QSEG + seg) * QSTRIDE, nd) : 0;
+            }
+            __syncthreads();
+            const int b0 = S.qbase[0], b1 = S.qbase[1];
+            bool over = false;
+            for (int q = t; q < ntot; q += K1_THREADS) {
+                const bool single = q < ns;
+                const SpawnRec r = single ? S.rec[CHUNK - 1 - q] : S.rec[q - ns];
+                const long long idx = single ? (long long)b0 + q : (long long)b1 + (q - ns);
+                if (idx >= I.qcap[single ? 0 : 1]) { over = true; continue; }
+                const unsigned d = r.det;
+                const ulonglong2 kk = map.key(d);
+                QRec o;
+                o.ka = kk.x; o.kb = kk.y; o.cper = map.cper(d); o.w2 = r.w2; o.w3 = r.w3;
+                o.slot = map.slot(d);
+                o.info = (r.ep & 0xffffu) | (map.flags(d) << 16);
+                I.qrec[single ? 0 : 1][(size_t)seg * I.qcap[single ? 0 : 1] + idx] = o;
+            }
+            if (over) atomicOr(&I.st->err, ERRB_QUEUE_CAP);
+            if (t == 0) {
+                if (b0 + ns > I.qcap[0]) atomicMax(&I.st->need_queue[0], b0 + ns);
+                if (b1 + nd > I.qcap[1]) atomicMax(&I.st->need_queue[1], b1 + nd);
+            }
+            __syncthreads();
+            continue;
+        }
         while (true) {
             int g = 0;
             if (lane == 0) g = atomicAdd(&S.next, 32);
@@ -1527,8 +1564,19 @@ __device__ void stage_issue(const DevInst *__restrict__ insts, const StageMeta &
         atomicAdd(&I.st->n_spawn_over, 1);
         return;
     }
-    if (m + si + sn > EMAX || si + sn > SCAP) {  // too large for shared memory: deferred to k_annihilate_big
+    if (m + si + sn > EMAX) {  // too large for shared memory: deferred to k_annihilate_big
         I.big_list[atomicAdd(&I.st->big_n, 1)] = b;
+        return;
+    }
+    if (si + sn > SCAP) {
+        // more spawns than the stage holds, but within the working arrays: the
+        // block loads this bucket itself (no copies; the phase completes at once)
+        bi[1] = m; bi[2] = si; bi[3] = sn; bi[4] = 0; bi[5] = M.ii; bi[6] = par; bi[7] = 1;
+        Sm.bit[q] = M.it;
+        Sm.bS[q] = M.S;
+        bi[0] = b;
+        asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(&Sm.bar[q]))
+                     : "memory");
         return;
     }
     AStage<SCAP> &st = Sm.st[q];
@@ -1634,6 +1682,21 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k_annihilate_staged(const DevIn
         phase[q] ^= 1u;
         const int m = Sm.binfo[q][1], si = Sm.binfo[q][2], sn = Sm.binfo[q][3], swo = Sm.binfo[q][4];
         const int par = Sm.binfo[q][6];
+        if (Sm.binfo[q][7]) {
+            // loaded by the block: the stage's contiguous key arrays (walkers,
+            // then spawns: CAP_M + SCAP = EMAX entries) and amplitude arrays
+            // (2 CAP_M >= EMAX) serve as the records of LoadStage
+            static_assert(CAP_M + STAGED_SCAP >= EMAX && 2 * CAP_M >= EMAX, "stage arrays hold EMAX records");
+            static_assert(offsetof(AStage<STAGED_SCAP>, skey) == offsetof(AStage<STAGED_SCAP>, wkey) +
+                                                                     sizeof(ulonglong2) * CAP_M &&
+                              offsetof(AStage<STAGED_SCAP>, whd) == offsetof(AStage<STAGED_SCAP>, wc) +
+                                                                    sizeof(double) * CAP_M,
+                          "walker and spawn key arrays, and amplitude and H_ii arrays, adjacent");
+            AStage<STAGED_SCAP> &st = Sm.st[q];
+            const LoadStage R{st.wkey, st.wc, m, si, sn, I.cap_s, (size_t)b * CAP_M, (size_t)b * I.cap_s, &I, par};
+            anni_bucket_3p(I, S, W3, R, b, par, Sm.bit[q], Sm.bS[q], m, si, sn);
+            continue;
+        }
         const BulkStage<STAGED_SCAP> R{&Sm.st[q], m, si, swo};
         anni_bucket_3p(I, S, W3, R, b, par, Sm.bit[q], Sm.bS[q], m, si, sn);
     }
@@ -1658,6 +1721,7 @@ struct K6Smem {
     int qn[NQ];
     int next;
     unsigned wsum[K1_THREADS / 32];
+    int qbase[2];                   // the chunk's reservations in the attempt queues (split)
     u64 bar[2];
     int binfo[2][4];                // per stage: bucket (-1: nothing staged), m, run, parity
     long long bit[2];
@@ -1745,6 +1809,7 @@ __device__ void spawn_stage_issue(const DevInst *__restrict__ insts, const Spawn
     bulk_g2s(S.sfl[q], I.fl[par] + base, m16, &S.bar[q]);
 }
 
+template <bool SPLIT>
 __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn_staged(const DevInst *__restrict__ insts,
                                                              const int *__restrict__ unit_start, int n_inst,
                                                              int n_units)
@@ -1871,9 +1936,73 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn_staged(const DevInst *_
         __syncthreads();
         const unsigned total = S.off[CAP_M];
         StagedBucketMap map{&S, q, (unsigned)base};
-        run_attempts(I, S, it, total, map, par, shift);
+        run_attempts<SPLIT>(I, S, it, total, map, par, shift, b);
         for (int o = 16; o >= 1; o >>= 1) att += __shfl_xor_sync(0xffffffffu, att, o);
         if (lane == 0 && att) red_add(&I.acc[(b % NSHARD) * ACC_STRIDE + ACC_ATT], (u64)att);
+    }
+}
+
+// The evaluation of the queued attempts of every run: one attempt per
+// thread, doubles first, then singles and hops, with no block barrier; the
+// parent's key, C_i / n_att, flags and slot travel in the record.
+__global__ void __launch_bounds__(256) k_spawn_eval(const DevInst *__restrict__ insts, int n_inst)
+{
+    __shared__ long long s_off[2][QSEG + 1];
+    __shared__ int s_err, s_par;
+    __shared__ double s_S;
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x, gs = (long long)gridDim.x * blockDim.x;
+    for (int ii = 0; ii < n_inst; ii++) {
+        const DevInst &I = insts[ii];
+        if (threadIdx.x < 32) {  // warp 0: the segment offsets of both classes by a warp scan
+            const int lane = threadIdx.x;
+            if (lane == 0) {
+                s_err = I.st->err_at_start;  // the state this run's spawning began with
+                s_par = I.st->parity;
+                s_S = I.st->S;
+            }
+            static_assert(QSEG % 32 == 0, "segments per lane");
+            constexpr int PERL = QSEG / 32;
+            for (int c = 0; c < 2; c++) {
+                long long v[PERL], mine = 0;
+                for (int r = 0; r < PERL; r++) {
+                    v[r] = min((long long)I.qcnt[(c * QSEG + lane * PERL + r) * QSTRIDE], I.qcap[c]);
+                    mine += v[r];
+                }
+                long long inc = mine;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const long long y = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += y;
+                }
+                long long ex = inc - mine;
+                for (int r = 0; r < PERL; r++) {
+                    s_off[c][lane * PERL + r] = ex;
+                    ex += v[r];
+                }
+                if (lane == 31) s_off[c][QSEG] = inc;
+            }
+        }
+        __syncthreads();
+        const int err = s_err, par = s_par;
+        const double shift = s_S;
+        const long long nd = s_off[1][QSEG], ntot = nd + s_off[0][QSEG];
+        if (!err)
+            for (long long i = gt; i < ntot; i += gs) {
+                const int c = i < nd ? 1 : 0;
+                const long long j = c ? i : i - nd;
+                int g = 0;  // the segment holding entry j: the last g with s_off[c][g] <= j
+#pragma unroll
+                for (int step = QSEG / 2; step >= 1; step >>= 1)
+                    if (s_off[c][g + step] <= j) g += step;
+                const QRec r = I.qrec[c][(size_t)g * I.qcap[c] + (j - s_off[c][g])];
+                const SpawnCtx cx{r.slot, par, shift};
+                const unsigned flags = r.info >> 16, sel = r.info & 0xffffu;
+                if (c == 1) {
+                    if (I.pchb) spawn_double_pchb(I, r.ka, r.kb, r.cper, flags, sel, r.w2, r.w3, cx);
+                    else spawn_double(I, r.ka, r.kb, r.cper, flags, sel, r.w2, r.w3, cx);
+                } else if (I.kind == FCIQMC_HUBBARD) spawn_hop_e(I, r.ka, r.kb, r.cper, flags, (int)sel, r.w2, r.w3, cx);
+                else spawn_single_e(I, r.ka, r.kb, r.cper, flags, (int)sel, r.w2, r.w3, cx);
+            }
+        __syncthreads();
     }
 }
 
@@ -2077,6 +2206,8 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
     u64 w[NACC];
 #pragma unroll
     for (int k = 0; k < NACC; k++) w[k] = __shfl_sync(0xffffffffu, v, k);
+    if (I.qcnt)  // the attempt queues of split spawning start empty
+        for (int g = lane; g < 2 * QSEG; g += 32) I.qcnt[g * QSTRIDE] = 0;
     if (lane != 0) return;
     const u128 W = (u128)limb_total(w + ACC_NW);
     const i128 A = limb_total(w + ACC_ANN), EN = limb_total(w + ACC_ENUM);
@@ -2284,11 +2415,15 @@ void launch_build_kidx(const DevInst *dinst, int parity, int nb, cudaStream_t s)
 // hardware hands the next block to whichever slot frees first, which evens out
 // buckets of unequal size)
 // g_spawn_bps = 0 and g_anni_bps = 0 select the staged kernels (one resident
-// wave, bulk copies one bucket ahead) wherever the batch fits them; otherwise
-// the plain-load kernels with that many blocks per SM
-static int g_spawn_bps = 0, g_heavy_bps = 2, g_anni_bps = 0;
+// wave, bulk copies one bucket ahead) wherever the batch fits them, and
+// g_spawn_bps = 1 the staged draw with the flat evaluation (split spawning);
+// otherwise the plain-load kernels with that many blocks per SM
+static int g_spawn_bps = 1, g_heavy_bps = 2, g_anni_bps = 0;
+static int g_geometry_gen = 0;  // changes with every set_launch_geometry
+int launch_geometry_generation() { return g_geometry_gen; }
 void set_launch_geometry(int spawn_bps, int heavy_bps, int anni_bps)
 {
+    g_geometry_gen++;
     g_spawn_bps = spawn_bps;
     g_heavy_bps = heavy_bps;
     g_anni_bps = anni_bps;
@@ -2303,18 +2438,29 @@ void get_launch_geometry(int *spawn_bps, int *heavy_bps, int *anni_bps)
 // the staged spawning kernel (g_spawn_bps = 0: one resident wave of three
 // blocks per SM) where every run's list arrays are 16-byte aligned; else the
 // plain-load kernel with g_spawn_bps blocks per SM
-void launch_spawn(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, bool staged, cudaStream_t s)
+void launch_spawn(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, bool staged, bool split,
+                  cudaStream_t s)
 {
-    if (staged && g_spawn_bps == 0) {
+    if (staged && (g_spawn_bps == 0 || g_spawn_bps == 1)) {
         int grid = n_units < num_sms() * 3 ? n_units : num_sms() * 3;
         if (grid < 1) grid = 1;
-        k_spawn_staged<<<grid, K1_THREADS, sizeof(K6Smem), s>>>(dinst, unit_start, n_inst, n_units);
+        if (split && g_spawn_bps == 1)
+            k_spawn_staged<true><<<grid, K1_THREADS, sizeof(K6Smem), s>>>(dinst, unit_start, n_inst, n_units);
+        else k_spawn_staged<false><<<grid, K1_THREADS, sizeof(K6Smem), s>>>(dinst, unit_start, n_inst, n_units);
         return;
     }
     const int bps = g_spawn_bps > 0 ? g_spawn_bps : 8;
     int grid = n_units < num_sms() * bps ? n_units : num_sms() * bps;
     if (grid < 1) grid = 1;
     k_spawn<<<grid, K1_THREADS, sizeof(K1Smem), s>>>(dinst, unit_start, n_inst, n_units);
+}
+
+// split spawning (queues in global memory, flat evaluation): geometry 1
+bool spawn_split_selected() { return g_spawn_bps == 1; }
+
+void launch_spawn_eval(const DevInst *dinst, int n_inst, cudaStream_t s)
+{
+    k_spawn_eval<<<num_sms() * 4, 256, 0, s>>>(dinst, n_inst);  // one resident wave (64 registers)
 }
 
 bool staged_spawn_fits(const DevInst &I)
@@ -2341,7 +2487,11 @@ cudaError_t init_kernels()
                                  (int)sizeof(K4Smem<STAGED_SCAP>));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spawn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K1Smem));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_spawn_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K6Smem));
+        e = cudaFuncSetAttribute(k_spawn_staged<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(K6Smem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_spawn_staged<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(K6Smem));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_spawn_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K1Smem));
     return e;
