@@ -119,6 +119,25 @@ def oracle_rate(sysd, prm, state, shift, iters):
     return att / el, ann / el, att, el
 
 
+def _oracle_job(job):
+    sysd, prm, state, shift, iters = job
+    return oracle_rate(sysd, prm, state, shift, iters)[2:]
+
+
+def oracle_pool_rate(jobs):
+    """The CPU oracle over all host cores: one process per job (spawned, not
+    forked, so that no child inherits a CUDA context), attempts over the
+    wall time of the whole pool."""
+    import multiprocessing as mp
+    cores = min(os.cpu_count() or 1, len(jobs))
+    t = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        out = pool.map(_oracle_job, jobs, chunksize=1)
+    el = time.perf_counter() - t
+    att = float(sum(a for a, _ in out))
+    return att / el, att, el, cores
+
+
 def key_sample(state, every):
     """The determinants whose key hash is 0 mod `every` (a uniform sample that
     always holds the same determinants of a given list)."""
@@ -217,6 +236,13 @@ def run_batch(args):
     ts = time.perf_counter() - t
     att_s = sum(float(np.sum(fq.fciqmc_iter_stats_get(g)["attempts"][m0[i]:])) for i, g in enumerate(seq))
     walkers = [float(fq.fciqmc_iter_stats_get(h)["nw"][-1]) for h in hs]
+    # CPU baseline: the oracle on every run's final state, 2 iterations each, all host cores
+    jobs = []
+    for (s, p), g in zip(runs, seq):
+        st, sh = fq.fciqmc_export_state(g), fq.fciqmc_export_shift(g)
+        jobs.append((s, p, {k: st[k] for k in ("alpha", "beta", "c")}, sh, 2))
+    del hs, seq
+    o_rate, o_att, o_el, cores = oracle_pool_rate(jobs)
     return {"metric": METRIC, "value": att_b / tb, "unit": "spawn attempts/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tb / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -225,7 +251,11 @@ def run_batch(args):
                        "walkers_min": min(walkers), "walkers_max": max(walkers)},
             "sequential": {"value": att_s / ts, "ms_per_step": ts / args.steps * 1e3},
             "autotuned": tuned,
-            "batched_over_sequential": (att_b / tb) / (att_s / ts)}
+            "batched_over_sequential": (att_b / tb) / (att_s / ts),
+            "cpu_baseline": {"value": o_rate, "unit": "spawn attempts/s", "cores": cores, "kind": "oracle",
+                             "sample": "2 oracle iterations of each of the 64 runs from its final state, one "
+                                       "process per run over %d host cores (%.3g attempts, %.1f s)" %
+                                       (cores, o_att, o_el)}}
 
 
 def run_batch_to_sigma(args):

@@ -314,17 +314,28 @@ static int count_kernel_nodes(cudaGraph_t g)
 }
 
 // the attempt queues of split spawning, allocated when that mode is selected
-// (and the run's arrays suit the staged kernels): QSEG segments per class, each
-// sized from the requested count (need, per class), at least 4096 entries
+// (and the run's arrays suit the staged kernels): min(draw grid, buckets)
+// segments per class, each sized from the requested count (need, per class),
+// at least 4096 entries (two determinants' worth of light attempts)
 static int ensure_queues(fciqmc_handle *h, long long need0 = 0, long long need1 = 0)
 {
     DevInst &I = h->hi;
     if (!spawn_split_selected() || !staged_spawn_fits(I)) return FCIQMC_OK;
     bool changed = false;
+    const int nseg = std::min(draw_segments(), 1 << h->bb);
+    if (I.qcnt && I.qnseg != nseg) {  // more buckets or another grid: new queues
+        dev_free(h, I.qcnt);
+        dev_free(h, I.qrec[0]);
+        dev_free(h, I.qrec[1]);
+        I.qcnt = nullptr;
+        I.qrec[0] = I.qrec[1] = nullptr;
+        I.qcap[0] = I.qcap[1] = 0;
+    }
     if (!I.qcnt) {
-        I.qcnt = (int *)dev_alloc(h, 2 * QSEG * QSTRIDE * sizeof(int));
+        I.qcnt = (int *)dev_alloc(h, 2 * (size_t)nseg * sizeof(int));
         if (!I.qcnt) return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (attempt queues)");
-        CUDA_TRY(h, cudaMemsetAsync(I.qcnt, 0, 2 * QSEG * QSTRIDE * sizeof(int), h->stream));
+        CUDA_TRY(h, cudaMemsetAsync(I.qcnt, 0, 2 * (size_t)nseg * sizeof(int), h->stream));
+        I.qnseg = nseg;
         changed = true;
     }
     const long long want[2] = {std::max<long long>(4096, need0), std::max<long long>(4096, need1)};
@@ -334,7 +345,7 @@ static int ensure_queues(fciqmc_handle *h, long long need0 = 0, long long need1 
         while (cap < want[c]) cap = cap + cap / 2;
         if (cap > (1LL << 30)) return fail(h, FCIQMC_ERR_CAPACITY, "attempt queue limit reached");
         dev_free(h, I.qrec[c]);
-        I.qrec[c] = (QRec *)dev_alloc(h, (size_t)QSEG * (size_t)cap * sizeof(QRec));
+        I.qrec[c] = (QRec *)dev_alloc(h, (size_t)nseg * (size_t)cap * sizeof(QRec));
         if (!I.qrec[c]) {
             I.qcap[c] = 0;
             return fail(h, FCIQMC_ERR_OUT_OF_MEMORY, "out of device memory (attempt queues)");
@@ -476,7 +487,7 @@ static int reset_after_error(fciqmc_handle *h)
     h->hst.new_n = 0;
     h->hst.need_queue[0] = 0;
     h->hst.need_queue[1] = 0;
-    if (h->hi.qcnt) CUDA_TRY(h, cudaMemsetAsync(h->hi.qcnt, 0, 2 * QSEG * QSTRIDE * sizeof(int), h->stream));
+    if (h->hi.qcnt) CUDA_TRY(h, cudaMemsetAsync(h->hi.qcnt, 0, 2 * (size_t)h->hi.qnseg * sizeof(int), h->stream));
     CUDA_TRY(h, cudaMemsetAsync(h->hi.acc, 0, NSHARD * ACC_STRIDE * sizeof(u64), h->stream));  // partial totals
     // the failed iteration's adaptive-shift weight sums are discarded when the
     // descriptor is next uploaded (the device copy may still describe an old
@@ -2204,7 +2215,7 @@ struct fciqmc_server {
 };
 
 // device memory a request needs when admitted: its initial layout and
-// integrals, and the first growth of the spawn regions (to 4 CAP_S0 slots per
+// integrals, the attempt queues, and the first growth of the spawn regions (to 4 CAP_S0 slots per
 // bucket, old and new buffers held together, with the large-bucket scratch)
 static int64_t estimate_bytes(const Request &r)
 {
@@ -2219,8 +2230,10 @@ static int64_t estimate_bytes(const Request &r)
     int tb = TABBITS;
     while ((double)(1 << tb) < 2.0 * ecap) tb++;
     const double scratch = (double)BIG_BLOCKS * (ecap * 52.0 + 4.0 * (double)(1 << tb) + 256.0);
-    return (int64_t)((double)(1LL << bb) * per_bucket + scratch + 8.0 * (N * N + ne) + 48.0 * N * N + 4096.0 * 88 +
-                     1.0e6);
+    // the attempt queues of split spawning at their first size
+    const double queues = 2.0 * (double)std::min(draw_segments(), 1 << bb) * (4096.0 * sizeof(QRec) + 4.0);
+    return (int64_t)((double)(1LL << bb) * per_bucket + scratch + queues + 8.0 * (N * N + ne) + 48.0 * N * N +
+                     4096.0 * 88 + 1.0e6);
 }
 
 extern "C" {

@@ -58,11 +58,11 @@ struct HeavyChunk {  // a slice of the attempts of one determinant with many wal
     uint32_t pad;
 };
 
-// Split spawning: every drawn attempt of a bucket is queued in global memory
-// by class (0: singles and lattice hops, 1: doubles), in segment b % QSEG of
-// its class, and evaluated by a flat kernel with one attempt per thread.
-constexpr int QSEG = 64;
-constexpr int QSTRIDE = 32;  // ints between two segment counters: each counter on its own 128-byte line
+// Split spawning: every drawn attempt is queued in global memory by class
+// (0: singles and lattice hops, 1: doubles), in the segment of the drawing
+// block (bucket b of a run goes to segment b mod the draw kernel's grid), and
+// evaluated by a flat kernel with one attempt per thread.
+constexpr int NSEG_MAX = 1024;  // segments per class (the draw kernel's grid) at most
 struct QRec {  // 48 bytes
     u64 ka, kb;      // parent
     double cper;     // C_i / n_att
@@ -180,8 +180,9 @@ struct DevInst {
     size_t big_stride;
     HeavyChunk *heavy;
     int heavy_cap;
-    QRec *qrec[2];          // attempt queues by class: QSEG segments of qcap[class] entries each
-    int *qcnt;              // [2 * QSEG] counters, QSTRIDE ints apart: entries queued per segment (cleared by k_finalize)
+    QRec *qrec[2];          // attempt queues by class: qnseg segments of qcap[class] entries each
+    int *qcnt;              // [2 * qnseg]: entries queued per segment, singles then doubles (cleared by k_finalize)
+    int qnseg;              // segments per class
     long long qcap[2];
     Partial *part;
     u64 *acc;  // exact totals of the iteration: NSHARD lines of ACC_STRIDE words (see ACC_*)
@@ -243,6 +244,7 @@ struct TrialEnt {
 void launch_spawn(const DevInst *dinst, const int *unit_start, int n_inst, int n_units, bool staged, bool split,
                   cudaStream_t s);
 bool spawn_split_selected();
+int draw_segments();  // the draw kernel's largest grid: a run needs min(this, buckets) queue segments
 void launch_spawn_eval(const DevInst *dinst, int n_inst, cudaStream_t s);
 bool staged_spawn_fits(const DevInst &I);
 void launch_spawn_heavy(const DevInst *dinst, int n_inst, cudaStream_t s);

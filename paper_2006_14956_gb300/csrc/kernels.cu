@@ -335,6 +335,31 @@ __device__ __forceinline__ int classify(const DevInst &I, u64 pa, u64 pb, u64 w0
     return (s1 ? I.mb : I.ma) < 2 ? -1 : Q_DOUBLE;
 }
 
+// Division of C_i by n_att > 1 (binary64, correctly rounded) occupies the
+// binary64 pipe for a whole warp's turn whatever its active lanes, so the
+// determinants that need it are listed (one warp-aggregated shared atomic)
+// and divided afterwards by full warps.
+template <typename SM>
+__device__ __forceinline__ void queue_div(SM &S, bool dv, int d, int lane)
+{
+    const unsigned md = __ballot_sync(0xffffffffu, dv);
+    if (!md) return;
+    int b0 = 0;
+    if (lane == 0) b0 = atomicAdd(&S.ndiv, __popc(md));
+    b0 = __shfl_sync(0xffffffffu, b0, 0);
+    if (dv) S.divl[b0 + __popc(md & ((1u << lane) - 1u))] = (unsigned short)d;
+}
+
+// C / n_att in place for the listed determinants i0, i0 + stride, ...
+__device__ __forceinline__ void divide_listed(const unsigned short *divl, int nd, double *c, int i0, int stride)
+{
+    for (int i = i0; i < nd; i += stride) {
+        const int d = divl[i];
+        const double x = c[d];
+        c[d] = x / (double)ceil_abs(x);
+    }
+}
+
 constexpr int CHUNK = 1024;  // attempts drawn and queued per round
 struct SpawnRec {
     u64 w2, w3;
@@ -349,27 +374,75 @@ struct K1Smem {
     unsigned short att_det[CHUNK];  // parent of attempt a < CHUNK of a bucket, 0xffff: look it up in off[]
     unsigned char fl[CAP_M];
     SpawnRec rec[CHUNK];
+    unsigned short divl[CAP_M];  // determinants whose C / n_att (n_att > 1) is still to be divided
+    int ndiv;
     int qn[NQ];
     int next;  // evaluation counter of the chunk
     unsigned wsum[K1_THREADS / 32];
-    int qbase[2];
     int hdr_err, hdr_par;
     long long hdr_it;
     double hdr_S;
 };
 static_assert(3 * (sizeof(K1Smem) + 1024) <= 233472, "three spawn blocks per SM (228 KB, 1 KB reserved per block)");
 
-// draw and classify the attempts of a chunk (attempt a of parent `det`, slot
-// k), queue them by class, then evaluate them: warps take 32 queued attempts
-// at a time from a shared counter, singles (the long exact sums) first, so
-// that no warp idles at the chunk's closing barrier while others still hold
-// a long queue.
-// SPLIT: instead of evaluating the queues, the chunk's attempts are written
-// to the run's global attempt queues (segment b % QSEG of each class), with
-// everything the evaluation needs about the parent, for k_spawn_eval.
-template <bool SPLIT = false, typename MAP, typename SM>
-__device__ void run_attempts(const DevInst &I, SM &S, long long it, unsigned A, MAP map, int par, double shift,
-                             int b = 0)
+// draw and classify attempts a0 .. a1-1 of a bucket (attempt a of parent
+// `det`, slot k) and queue them by class in S.rec: doubles from the front,
+// singles and hops from the back (hops only exist without the others), with
+// the counts in qn[Q_DOUBLE], qn[Q_SINGLE] (zero on entry); each thread
+// draws two attempts per round, so that the two Philox evaluations overlap
+template <typename MAP, typename SM>
+__device__ __forceinline__ void draw_classify(const DevInst &I, SM &S, long long it, unsigned a0, unsigned a1,
+                                              const MAP &map, int *qn)
+{
+    constexpr int CHUNK = SM::chunk;
+    const int t = threadIdx.x, lane = t & 31;
+    for (unsigned ab = a0; ab < a1; ab += 2 * K1_THREADS) {
+        u64 w[2][4];
+        unsigned det[2], ep[2];
+        int cls[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const unsigned a = ab + h * K1_THREADS + t;
+            cls[h] = -1;
+            det[h] = 0;
+            ep[h] = 0;
+            if (ab + h * K1_THREADS + (unsigned)(t & ~31) < a1) {  // a warp with no attempt left draws nothing
+                const unsigned ac = a < a1 ? a : a1 - 1;           // clamped: drawn, then discarded
+                u64 k;
+                det[h] = map.det_of(ac, k);
+                const ulonglong2 kk = map.key(det[h]);
+                philox(kk.x, kk.y, (u64)it, (k << 8) | (u64)PURPOSE_SPAWN, I.seed, I.replica, w[h]);
+                const int q = classify(I, kk.x, kk.y, w[h][0], w[h][1], &ep[h]);
+                cls[h] = a < a1 ? q : -1;
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const bool front = cls[h] == Q_DOUBLE, back = cls[h] == Q_SINGLE || cls[h] == Q_HOP;
+            const unsigned mf = __ballot_sync(0xffffffffu, front), mb = __ballot_sync(0xffffffffu, back);
+            int bf = 0, bk = 0;
+            if (lane == 0) {
+                if (mf) bf = atomicAdd(&qn[Q_DOUBLE], __popc(mf));
+                if (mb) bk = atomicAdd(&qn[Q_SINGLE], __popc(mb));
+            }
+            bf = __shfl_sync(0xffffffffu, bf, 0);
+            bk = __shfl_sync(0xffffffffu, bk, 0);
+            const unsigned below = (1u << lane) - 1u;
+            if (front || back) {
+                const int slot = front ? bf + __popc(mf & below) : CHUNK - 1 - (bk + __popc(mb & below));
+                SpawnRec &r = S.rec[slot];
+                r.w2 = w[h][2]; r.w3 = w[h][3]; r.det = det[h]; r.ep = ep[h];
+            }
+        }
+    }
+}
+
+// draw and classify the attempts of a bucket chunk by chunk, queue them by
+// class, then evaluate them: warps take 32 queued attempts at a time from a
+// shared counter, singles (the long exact sums) first, so that no warp idles
+// at the chunk's closing barrier while others still hold a long queue
+template <typename MAP, typename SM>
+__device__ void run_attempts(const DevInst &I, SM &S, long long it, unsigned A, MAP map, int par, double shift)
 {
     constexpr int CHUNK = SM::chunk;
     const int t = threadIdx.x, lane = t & 31;
@@ -378,82 +451,9 @@ __device__ void run_attempts(const DevInst &I, SM &S, long long it, unsigned A, 
         if (t < NQ) S.qn[t] = 0;
         if (t == 0) S.next = 0;
         __syncthreads();
-        // queues are laid out back to back: doubles from the front of rec[],
-        // singles and hops from the back (hops only exist without the others);
-        // each thread draws two attempts per round, so that the two Philox
-        // evaluations overlap
-        for (unsigned ab = a0; ab < a1; ab += 2 * K1_THREADS) {
-            u64 w[2][4];
-            unsigned det[2], ep[2];
-            int cls[2];
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const unsigned a = ab + h * K1_THREADS + t;
-                cls[h] = -1;
-                det[h] = 0;
-                ep[h] = 0;
-                if (ab + h * K1_THREADS + (unsigned)(t & ~31) < a1) {  // a warp with no attempt left draws nothing
-                    const unsigned ac = a < a1 ? a : a1 - 1;           // clamped: drawn, then discarded
-                    u64 k;
-                    det[h] = map.det_of(ac, k);
-                    const ulonglong2 kk = map.key(det[h]);
-                    philox(kk.x, kk.y, (u64)it, (k << 8) | (u64)PURPOSE_SPAWN, I.seed, I.replica, w[h]);
-                    const int q = classify(I, kk.x, kk.y, w[h][0], w[h][1], &ep[h]);
-                    cls[h] = a < a1 ? q : -1;
-                }
-            }
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const bool front = cls[h] == Q_DOUBLE, back = cls[h] == Q_SINGLE || cls[h] == Q_HOP;
-                const unsigned mf = __ballot_sync(0xffffffffu, front), mb = __ballot_sync(0xffffffffu, back);
-                int bf = 0, bk = 0;
-                if (lane == 0) {
-                    if (mf) bf = atomicAdd(&S.qn[Q_DOUBLE], __popc(mf));
-                    if (mb) bk = atomicAdd(&S.qn[Q_SINGLE], __popc(mb));
-                }
-                bf = __shfl_sync(0xffffffffu, bf, 0);
-                bk = __shfl_sync(0xffffffffu, bk, 0);
-                const unsigned below = (1u << lane) - 1u;
-                if (front || back) {
-                    const int slot = front ? bf + __popc(mf & below) : CHUNK - 1 - (bk + __popc(mb & below));
-                    SpawnRec &r = S.rec[slot];
-                    r.w2 = w[h][2]; r.w3 = w[h][3]; r.det = det[h]; r.ep = ep[h];
-                }
-            }
-        }
+        draw_classify(I, S, it, a0, a1, map, S.qn);
         __syncthreads();
         const int nd = S.qn[Q_DOUBLE], ns = S.qn[Q_SINGLE], ntot = ns + nd;
-        if constexpr (SPLIT) {
-            // one reservation per class and chunk in the bucket's segments
-            const int seg = b % QSEG;
-            if (t == 0) {
-                S.qbase[0] = ns ? atomicAdd(I.qcnt + seg * QSTRIDE, ns) : 0;
-                S.qbase[1] = nd ? atomicAdd(I.qcnt + (QSEG + seg) * QSTRIDE, nd) : 0;
-            }
-            __syncthreads();
-            const int b0 = S.qbase[0], b1 = S.qbase[1];
-            bool over = false;
-            for (int q = t; q < ntot; q += K1_THREADS) {
-                const bool single = q < ns;
-                const SpawnRec r = single ? S.rec[CHUNK - 1 - q] : S.rec[q - ns];
-                const long long idx = single ? (long long)b0 + q : (long long)b1 + (q - ns);
-                if (idx >= I.qcap[single ? 0 : 1]) { over = true; continue; }
-                const unsigned d = r.det;
-                const ulonglong2 kk = map.key(d);
-                QRec o;
-                o.ka = kk.x; o.kb = kk.y; o.cper = map.cper(d); o.w2 = r.w2; o.w3 = r.w3;
-                o.slot = map.slot(d);
-                o.info = (r.ep & 0xffffu) | (map.flags(d) << 16);
-                I.qrec[single ? 0 : 1][(size_t)seg * I.qcap[single ? 0 : 1] + idx] = o;
-            }
-            if (over) atomicOr(&I.st->err, ERRB_QUEUE_CAP);
-            if (t == 0) {
-                if (b0 + ns > I.qcap[0]) atomicMax(&I.st->need_queue[0], b0 + ns);
-                if (b1 + nd > I.qcap[1]) atomicMax(&I.st->need_queue[1], b1 + nd);
-            }
-            __syncthreads();
-            continue;
-        }
         while (true) {
             int g = 0;
             if (lane == 0) g = atomicAdd(&S.next, 32);
@@ -531,6 +531,7 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn(const DevInst *__restri
     int cur = -1, err = 0, par = 0;
     long long it = 0;
     double shift = 0.0;
+    if (t == 0) S.ndiv = 0;  // visible after the first run header's barrier
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
         const int ii = find_inst(unit_start, n_inst, u);
         const DevInst &I = insts[ii];
@@ -561,46 +562,51 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn(const DevInst *__restri
         for (int j = 0; j < PER; j++) {
             const int d = PER * t + j;
             nl[j] = 0;
-            if (d >= m) continue;
-            const ulonglong2 kk = I.key[par][base + d];
-            const double c = I.c[par][base + d];
-            const uint8_t f = I.fl[par][base + d];
-            unsigned fl = 0;
-            double cper = 0.0;
-            u64 nat = 0;
-            if (!is_zero(c)) {
-                if (!abs_lt(c, 0x1p31)) {
-                    atomicOr(&I.st->err, ERRB_NUMERIC);
-                } else {
-                    nat = ceil_abs(c);
-                    const bool init = (dbits(c) & ~SIGN64) > dbits(I.n_a) || (f & (DFLAG_REF | DFLAG_D));
-                    fl = (init ? 1u : 0u) | ((f & DFLAG_D) ? 2u : 0u);
-                    cper = nat == 1 ? c : c / (double)nat;  // c / 1 is c
-                    att += (long long)nat;
-                    if (nat > HEAVY_ATT) {  // sliced into the heavy queue
-                        const unsigned nch = (unsigned)((nat + HEAVY_ATT - 1) / HEAVY_ATT);
-                        const int q0 = atomicAdd(&I.st->heavy_n, (int)nch);
-                        if ((long long)q0 + nch > (long long)I.heavy_cap) atomicOr(&I.st->err, ERRB_HEAVY_CAP);
-                        else
-                            for (unsigned q = 0; q < nch; q++) {
-                                HeavyChunk h;
-                                h.a = kk.x; h.b = kk.y; h.cper = cper; h.k0 = (u64)q * HEAVY_ATT;
-                                const u64 left = nat - h.k0;
-                                h.count = (unsigned)(left < HEAVY_ATT ? left : HEAVY_ATT);
-                                h.flags = fl;
-                                h.slot = (uint32_t)(base + d);
-                                h.pad = 0;
-                                I.heavy[q0 + q] = h;
-                            }
+            bool dv = false;
+            if (d < m) {
+                const ulonglong2 kk = I.key[par][base + d];
+                const double c = I.c[par][base + d];
+                const uint8_t f = I.fl[par][base + d];
+                unsigned fl = 0;
+                double cper = 0.0;
+                u64 nat = 0;
+                if (!is_zero(c)) {
+                    if (!abs_lt(c, 0x1p31)) {
+                        atomicOr(&I.st->err, ERRB_NUMERIC);
                     } else {
-                        nl[j] = (unsigned)nat;
+                        nat = ceil_abs(c);
+                        const bool init = (dbits(c) & ~SIGN64) > dbits(I.n_a) || (f & (DFLAG_REF | DFLAG_D));
+                        fl = (init ? 1u : 0u) | ((f & DFLAG_D) ? 2u : 0u);
+                        cper = c;  // C / n_att: below for n_att > 1 (c / 1 is c)
+                        att += (long long)nat;
+                        if (nat > HEAVY_ATT) {  // sliced into the heavy queue
+                            cper = c / (double)nat;
+                            const unsigned nch = (unsigned)((nat + HEAVY_ATT - 1) / HEAVY_ATT);
+                            const int q0 = atomicAdd(&I.st->heavy_n, (int)nch);
+                            if ((long long)q0 + nch > (long long)I.heavy_cap) atomicOr(&I.st->err, ERRB_HEAVY_CAP);
+                            else
+                                for (unsigned q = 0; q < nch; q++) {
+                                    HeavyChunk h;
+                                    h.a = kk.x; h.b = kk.y; h.cper = cper; h.k0 = (u64)q * HEAVY_ATT;
+                                    const u64 left = nat - h.k0;
+                                    h.count = (unsigned)(left < HEAVY_ATT ? left : HEAVY_ATT);
+                                    h.flags = fl;
+                                    h.slot = (uint32_t)(base + d);
+                                    h.pad = 0;
+                                    I.heavy[q0 + q] = h;
+                                }
+                        } else {
+                            nl[j] = (unsigned)nat;
+                            dv = nat > 1;
+                        }
                     }
                 }
+                S.key[d] = kk;
+                S.cper[d] = cper;
+                S.fl[d] = (unsigned char)fl;
+                mine += nl[j];
             }
-            S.key[d] = kk;
-            S.cper[d] = cper;
-            S.fl[d] = (unsigned char)fl;
-            mine += nl[j];
+            queue_div(S, dv, d, lane);
         }
         // the parents of the first CHUNK attempts, written below by the
         // determinants with few attempts; the others are found by bisection
@@ -620,8 +626,11 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn(const DevInst *__restri
                 if (lane >= o) x += y;
             }
             if (lane < K1_THREADS / 32) S.wsum[lane] = x;
+        } else {
+            divide_listed(S.divl, S.ndiv, S.cper, t - 32, K1_THREADS - 32);  // warp 0 scans meanwhile
         }
         __syncthreads();
+        if (t == 0) S.ndiv = 0;  // read by every thread before the barrier above
         unsigned ex = v - mine + (warp ? S.wsum[warp - 1] : 0u);
         for (int j = 0; j < PER; j++) {
             S.off[PER * t + j] = ex;
@@ -1222,9 +1231,44 @@ struct BulkStage {
     __device__ double hd_out(int e) const { return st->whd[e]; }
 };
 
+// A thread's share of a run's exact integer totals over the buckets its
+// block meets in one annihilation launch (integer sums: any order gives the
+// same total), added to the run's accumulators once, when the block leaves
+// the run
+struct AnniTotals {
+    u128 nw = 0;            // N_w * 2^32
+    i128 ann = 0;           // annihilated walkers * 2^32
+    long long rej = 0;      // rejected non-initiator spawns
+    long long ndet = 0;     // determinants kept (thread 0)
+    long long spawns = 0;   // spawns received (thread 0)
+};
+
+// every thread of the block: the totals into the run's accumulators (line
+// blockIdx.x % NSHARD), then zero
+__device__ void anni_flush(const DevInst &I, AnniTotals &T)
+{
+    const int lane = threadIdx.x & 31;
+    for (int mm = 16; mm >= 1; mm >>= 1) {
+        T.rej += __shfl_xor_sync(0xffffffffu, T.rej, mm);
+        T.ann += shfl_xor_i128(T.ann, mm);
+        T.nw += (u128)shfl_xor_i128((i128)T.nw, mm);
+    }
+    u64 *acc = I.acc + (blockIdx.x % NSHARD) * ACC_STRIDE;
+    if (lane == 0) {
+        limb_add(acc + ACC_NW, (i128)T.nw);
+        limb_add(acc + ACC_ANN, T.ann);
+        if (T.rej) red_add(&acc[ACC_REJ], (u64)T.rej);
+    }
+    if (threadIdx.x == 0) {
+        if (T.ndet) red_add(&acc[ACC_NDET], (u64)T.ndet);
+        if (T.spawns) red_add(&acc[ACC_SPAWNS], (u64)T.spawns);
+    }
+    T = AnniTotals{};
+}
+
 template <typename SRC>
 __device__ void anni_bucket_3p(const DevInst &I, K3Shared &S, const Work3 &W, const SRC &R, int b, int par,
-                               long long it, double shift, int m, int si, int sn)
+                               long long it, double shift, int m, int si, int sn, AnniTotals &T)
 {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int E = m + si + sn;
@@ -1406,53 +1450,42 @@ __device__ void anni_bucket_3p(const DevInst &I, K3Shared &S, const Work3 &W, co
     }
     if (bad) atomicOr(&I.st->err, ERRB_NUMERIC);
     // bucket reductions (fixed order: lanes by xor tree, warps in index order)
+    // the integer totals stay in the thread (added to the run's accumulators
+    // when the block leaves the run); E_num and the trial sums are binary64,
+    // summed per bucket in a fixed order (lanes by xor tree, warps in index
+    // order; a warp or block whose terms are all +0 adds nothing, and none of
+    // these sums is ever -0)
+    T.rej += rejected;
+    T.ann += ann;
+    T.nw += nw;
     if (I.trial_bits)
         for (int mm = 16; mm >= 1; mm >>= 1) {
             tnum = tnum + __shfl_xor_sync(0xffffffffu, tnum, mm);
             tden = tden + __shfl_xor_sync(0xffffffffu, tden, mm);
         }
-    for (int mm = 16; mm >= 1; mm >>= 1) {
-        enm = enm + __shfl_xor_sync(0xffffffffu, enm, mm);
-        rejected += __shfl_xor_sync(0xffffffffu, rejected, mm);
-        ann += shfl_xor_i128(ann, mm);
-        nw += (u128)shfl_xor_i128((i128)nw, mm);
-    }
+    if (__any_sync(0xffffffffu, dbits(enm) != 0))
+        for (int mm = 16; mm >= 1; mm >>= 1) enm = enm + __shfl_xor_sync(0xffffffffu, enm, mm);
     if (lane == 0) {
         S.red_d[warp] = enm;
         S.red_t[warp][0] = tnum;
         S.red_t[warp][1] = tden;
-        S.red_u[warp][0] = (u64)nw;
-        S.red_u[warp][1] = (u64)(nw >> 64);
-        S.red_u[warp][2] = (u64)ann;
-        S.red_u[warp][3] = (u64)((u128)ann >> 64);
-        S.red_u[warp][4] = (u64)rejected;
     }
     __syncthreads();
     if (t == 0) {
         const int total = S.n_new;
         S.n_new = 0;  // next used after two more barriers
         double e_sum = 0.0, tn = 0.0, td = 0.0;
-        u128 nws = 0;
-        i128 anns = 0;
-        long long rej = 0;
         for (int k = 0; k < K3_THREADS / 32; k++) {
-            e_sum = e_sum + S.red_d[k];
+            if (dbits(S.red_d[k])) e_sum = e_sum + S.red_d[k];
             if (I.trial_bits) {
                 tn = tn + S.red_t[k][0];
                 td = td + S.red_t[k][1];
             }
-            nws += ((u128)S.red_u[k][1] << 64) | S.red_u[k][0];
-            anns += (i128)(((u128)S.red_u[k][3] << 64) | S.red_u[k][2]);
-            rej += (long long)S.red_u[k][4];
         }
         if (total > CAP_M) { atomicOr(&I.st->err, ERRB_MAIN_CAP); atomicMax(&I.st->need_main, total); }
-        u64 *acc = I.acc + (b % NSHARD) * ACC_STRIDE;
-        limb_add(acc + ACC_NW, (i128)nws);
-        limb_add(acc + ACC_ANN, anns);
-        limb_add(acc + ACC_ENUM, to_fixed(e_sum, I.Fe));
-        red_add(&acc[ACC_NDET], (u64)total);
-        if (rej) red_add(&acc[ACC_REJ], (u64)rej);
-        red_add(&acc[ACC_SPAWNS], (u64)(si + sn));
+        if (dbits(e_sum)) limb_add(I.acc + (b % NSHARD) * ACC_STRIDE + ACC_ENUM, to_fixed(e_sum, I.Fe));
+        T.ndet += total;
+        T.spawns += si + sn;
         if (I.trial_bits) {
             Partial &P = I.part[b];
             P.t_num = tn;
@@ -1654,7 +1687,8 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k_annihilate_staged(const DevIn
     __syncthreads();
     unsigned phase[2] = {0u, 0u};
     const Work3 W3{Sm.acc_lo, Sm.acc_hi, Sm.eflag, Sm.tab};
-    int q = 0;
+    AnniTotals T;
+    int q = 0, cur = -1;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x, q ^= 1) {
         // the next bucket's copies go out before this one is processed; its
         // stage was last read before the previous bucket's closing barrier
@@ -1680,6 +1714,10 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k_annihilate_staged(const DevIn
             return;
         }
         phase[q] ^= 1u;
+        if (ii != cur) {  // a new run: the previous run's totals are complete
+            if (cur >= 0) anni_flush(insts[cur], T);
+            cur = ii;
+        }
         const int m = Sm.binfo[q][1], si = Sm.binfo[q][2], sn = Sm.binfo[q][3], swo = Sm.binfo[q][4];
         const int par = Sm.binfo[q][6];
         if (Sm.binfo[q][7]) {
@@ -1694,12 +1732,13 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k_annihilate_staged(const DevIn
                           "walker and spawn key arrays, and amplitude and H_ii arrays, adjacent");
             AStage<STAGED_SCAP> &st = Sm.st[q];
             const LoadStage R{st.wkey, st.wc, m, si, sn, I.cap_s, (size_t)b * CAP_M, (size_t)b * I.cap_s, &I, par};
-            anni_bucket_3p(I, S, W3, R, b, par, Sm.bit[q], Sm.bS[q], m, si, sn);
+            anni_bucket_3p(I, S, W3, R, b, par, Sm.bit[q], Sm.bS[q], m, si, sn, T);
             continue;
         }
         const BulkStage<STAGED_SCAP> R{&Sm.st[q], m, si, swo};
-        anni_bucket_3p(I, S, W3, R, b, par, Sm.bit[q], Sm.bS[q], m, si, sn);
+        anni_bucket_3p(I, S, W3, R, b, par, Sm.bit[q], Sm.bS[q], m, si, sn, T);
     }
+    if (cur >= 0) anni_flush(insts[cur], T);
 }
 
 // ------------------------------------------------------------------ staged spawning
@@ -1718,10 +1757,11 @@ struct K6Smem {
     unsigned short att_det[CHUNK_S];
     unsigned char fl[CAP_M];        // initiator | in-D bits of the current bucket
     SpawnRec rec[CHUNK_S];
+    unsigned short divl[CAP_M];     // determinants whose C / n_att (n_att > 1) is still to be divided
+    int ndiv;
     int qn[NQ];
     int next;
     unsigned wsum[K1_THREADS / 32];
-    int qbase[2];                   // the chunk's reservations in the attempt queues (split)
     u64 bar[2];
     int binfo[2][4];                // per stage: bucket (-1: nothing staged), m, run, parity
     long long bit[2];
@@ -1809,7 +1849,6 @@ __device__ void spawn_stage_issue(const DevInst *__restrict__ insts, const Spawn
     bulk_g2s(S.sfl[q], I.fl[par] + base, m16, &S.bar[q]);
 }
 
-template <bool SPLIT>
 __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn_staged(const DevInst *__restrict__ insts,
                                                              const int *__restrict__ unit_start, int n_inst,
                                                              int n_units)
@@ -1821,6 +1860,7 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn_staged(const DevInst *_
     SpawnMeta nxt;
     nxt.ii = -1;
     if (t == 0) {
+        S.ndiv = 0;
         mbar_init(&S.bar[0], 1);
         mbar_init(&S.bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1867,45 +1907,50 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn_staged(const DevInst *_
         for (int j = 0; j < PER; j++) {
             const int d = PER * t + j;
             nl[j] = 0;
-            if (d >= m) continue;
-            const double c = S.sc[q][d];
-            const uint8_t f = S.sfl[q][d];
-            unsigned fl = 0;
-            double cper = 0.0;
-            u64 nat = 0;
-            if (!is_zero(c)) {
-                if (!abs_lt(c, 0x1p31)) {
-                    atomicOr(&I.st->err, ERRB_NUMERIC);
-                } else {
-                    nat = ceil_abs(c);
-                    const bool init = (dbits(c) & ~SIGN64) > dbits(I.n_a) || (f & (DFLAG_REF | DFLAG_D));
-                    fl = (init ? 1u : 0u) | ((f & DFLAG_D) ? 2u : 0u);
-                    cper = nat == 1 ? c : c / (double)nat;  // c / 1 is c
-                    att += (long long)nat;
-                    if (nat > HEAVY_ATT) {  // sliced into the heavy queue
-                        const ulonglong2 kk = S.skey[q][d];
-                        const unsigned nch = (unsigned)((nat + HEAVY_ATT - 1) / HEAVY_ATT);
-                        const int q0 = atomicAdd(&I.st->heavy_n, (int)nch);
-                        if ((long long)q0 + nch > (long long)I.heavy_cap) atomicOr(&I.st->err, ERRB_HEAVY_CAP);
-                        else
-                            for (unsigned h = 0; h < nch; h++) {
-                                HeavyChunk hc;
-                                hc.a = kk.x; hc.b = kk.y; hc.cper = cper; hc.k0 = (u64)h * HEAVY_ATT;
-                                const u64 left = nat - hc.k0;
-                                hc.count = (unsigned)(left < HEAVY_ATT ? left : HEAVY_ATT);
-                                hc.flags = fl;
-                                hc.slot = (uint32_t)(base + d);
-                                hc.pad = 0;
-                                I.heavy[q0 + h] = hc;
-                            }
+            bool dv = false;
+            if (d < m) {
+                const double c = S.sc[q][d];
+                const uint8_t f = S.sfl[q][d];
+                unsigned fl = 0;
+                double cper = 0.0;
+                u64 nat = 0;
+                if (!is_zero(c)) {
+                    if (!abs_lt(c, 0x1p31)) {
+                        atomicOr(&I.st->err, ERRB_NUMERIC);
                     } else {
-                        nl[j] = (unsigned)nat;
+                        nat = ceil_abs(c);
+                        const bool init = (dbits(c) & ~SIGN64) > dbits(I.n_a) || (f & (DFLAG_REF | DFLAG_D));
+                        fl = (init ? 1u : 0u) | ((f & DFLAG_D) ? 2u : 0u);
+                        cper = c;  // C / n_att: below for n_att > 1 (c / 1 is c)
+                        att += (long long)nat;
+                        if (nat > HEAVY_ATT) {  // sliced into the heavy queue
+                            cper = c / (double)nat;
+                            const ulonglong2 kk = S.skey[q][d];
+                            const unsigned nch = (unsigned)((nat + HEAVY_ATT - 1) / HEAVY_ATT);
+                            const int q0 = atomicAdd(&I.st->heavy_n, (int)nch);
+                            if ((long long)q0 + nch > (long long)I.heavy_cap) atomicOr(&I.st->err, ERRB_HEAVY_CAP);
+                            else
+                                for (unsigned h = 0; h < nch; h++) {
+                                    HeavyChunk hc;
+                                    hc.a = kk.x; hc.b = kk.y; hc.cper = cper; hc.k0 = (u64)h * HEAVY_ATT;
+                                    const u64 left = nat - hc.k0;
+                                    hc.count = (unsigned)(left < HEAVY_ATT ? left : HEAVY_ATT);
+                                    hc.flags = fl;
+                                    hc.slot = (uint32_t)(base + d);
+                                    hc.pad = 0;
+                                    I.heavy[q0 + h] = hc;
+                                }
+                        } else {
+                            nl[j] = (unsigned)nat;
+                            dv = nat > 1;
+                        }
                     }
                 }
+                S.sc[q][d] = cper;
+                S.fl[d] = (unsigned char)fl;
+                mine += nl[j];
             }
-            S.sc[q][d] = cper;
-            S.fl[d] = (unsigned char)fl;
-            mine += nl[j];
+            queue_div(S, dv, d, lane);
         }
         for (int a = t; a < CHUNK_S; a += K1_THREADS) S.att_det[a] = 0xffffu;
         // exclusive scan of the light attempt counts in determinant order
@@ -1923,8 +1968,11 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn_staged(const DevInst *_
                 if (lane >= o) x += y;
             }
             if (lane < K1_THREADS / 32) S.wsum[lane] = x;
+        } else {
+            divide_listed(S.divl, S.ndiv, S.sc[q], t - 32, K1_THREADS - 32);  // warp 0 scans meanwhile
         }
         __syncthreads();
+        if (t == 0) S.ndiv = 0;  // read by every thread before the barrier above
         unsigned ex = v - mine + (warp ? S.wsum[warp - 1] : 0u);
         for (int j = 0; j < PER; j++) {
             S.off[PER * t + j] = ex;
@@ -1936,10 +1984,282 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn_staged(const DevInst *_
         __syncthreads();
         const unsigned total = S.off[CAP_M];
         StagedBucketMap map{&S, q, (unsigned)base};
-        run_attempts<SPLIT>(I, S, it, total, map, par, shift, b);
+        run_attempts(I, S, it, total, map, par, shift);
         for (int o = 16; o >= 1; o >>= 1) att += __shfl_xor_sync(0xffffffffu, att, o);
         if (lane == 0 && att) red_add(&I.acc[(b % NSHARD) * ACC_STRIDE + ACC_ATT], (u64)att);
     }
+}
+
+// ------------------------------------------------------------------ split spawning: the draw
+// The first half of split spawning: the staged bucket (bulk copies one bucket
+// ahead, as above), n_att and C_i / n_att per determinant, then the attempts
+// drawn, classified and written to the run's attempt queues for
+// k_spawn_eval.  The block that draws bucket b of a run owns segment
+// b mod (grid size) of both of the run's queues (every bucket of the run it
+// meets has the same residue), so its fill is a count every thread of the
+// block keeps alike and no global atomic is needed; a run needs
+// min(grid size, buckets) segments.  With double-buffered stage, flags and
+// class counters a bucket
+// takes three block barriers (one more per extra chunk of attempts):
+//   A  the bucket is in shared memory, n_att counted per warp
+//   B  the block scan of the attempt offsets and the divisions are done
+//   C  the chunk's attempts are drawn and queued in shared memory
+// after which the chunk's records go out while the next bucket starts.
+struct K7Smem {
+    static constexpr int chunk = CHUNK_S;
+    ulonglong2 skey[2][CAP_M];
+    double sc[2][CAP_M];            // C as copied; C / n_att once the bucket is loaded
+    unsigned char sfl[2][CAP_M];
+    unsigned char fl[2][CAP_M];     // initiator | in-D bits, per stage
+    unsigned off[CAP_M];
+    unsigned short att_det[CHUNK_S];
+    unsigned short divl[CAP_M];
+    SpawnRec rec[CHUNK_S];
+    int ndiv;
+    int qn[2][NQ];                  // class counts, by chunk parity
+    unsigned wsum[K1_THREADS / 32];
+    u64 bar[2];
+    int binfo[2][4];
+    long long bit[2];
+    double bS[2];
+};
+static_assert(3 * (sizeof(K7Smem) + 1024) <= 233472, "three draw blocks per SM");
+
+struct DrawBucketMap {
+    const K7Smem *S;
+    int q;
+    unsigned base;
+    __device__ unsigned det_of(unsigned a, u64 &k) const
+    {
+        if (a < (unsigned)CHUNK_S) {
+            const unsigned d = S->att_det[a];
+            if (d != 0xffffu) {
+                k = a - S->off[d];
+                return d;
+            }
+        }
+        int lo = 0, hi = CAP_M;  // largest d with off[d] <= a (determinants past the count hold the total)
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (S->off[mid] <= a) lo = mid; else hi = mid;
+        }
+        k = a - S->off[lo];
+        return (unsigned)lo;
+    }
+    __device__ ulonglong2 key(unsigned d) const { return S->skey[q][d]; }
+    __device__ double cper(unsigned d) const { return S->sc[q][d]; }
+    __device__ unsigned flags(unsigned d) const { return S->fl[q][d]; }
+    __device__ unsigned slot(unsigned d) const { return base + d; }
+};
+
+// thread 0: the bulk copies of unit M.u's bucket into stage q of the draw kernel
+__device__ void draw_stage_issue(const DevInst *__restrict__ insts, const SpawnMeta &M, K7Smem &S, int q)
+{
+    int *bi = S.binfo[q];
+    bi[0] = -1;
+    if (M.u < 0 || M.err) return;
+    const DevInst &I = insts[M.ii];
+    const int m = M.m, par = M.par;
+    const size_t base = (size_t)M.b * CAP_M;
+    const unsigned m2 = (unsigned)((m + 1) & ~1), m16 = (unsigned)((m + 15) & ~15);
+    const unsigned bytes = m ? (unsigned)m * 16u + m2 * 8u + m16 : 0u;
+    bi[1] = m; bi[2] = M.ii; bi[3] = par;
+    S.bit[q] = M.it;
+    S.bS[q] = M.S;
+    bi[0] = M.b;
+    if (bytes == 0) {
+        asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(&S.bar[q]))
+                     : "memory");
+        return;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&S.bar[q], bytes);
+    bulk_g2s(S.skey[q], I.key[par] + base, (unsigned)m * 16u, &S.bar[q]);
+    bulk_g2s(S.sc[q], I.c[par] + base, m2 * 8u, &S.bar[q]);
+    bulk_g2s(S.sfl[q], I.fl[par] + base, m16, &S.bar[q]);
+}
+
+// thread 0: the queue fill of this block's segment of a run
+__device__ __forceinline__ void draw_flush(const DevInst &I, int seg, long long q0, long long q1)
+{
+    I.qcnt[seg] = (int)min(q0, 0x7fffffffLL);
+    I.qcnt[I.qnseg + seg] = (int)min(q1, 0x7fffffffLL);
+}
+
+__global__ void __launch_bounds__(K1_THREADS, 3) k_spawn_draw(const DevInst *__restrict__ insts,
+                                                              const int *__restrict__ unit_start, int n_inst,
+                                                              int n_units)
+{
+    extern __shared__ __align__(128) unsigned char k7_raw[];
+    K7Smem &S = *reinterpret_cast<K7Smem *>(k7_raw);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    constexpr int PER = CAP_M / K1_THREADS;
+    SpawnMeta nxt;
+    nxt.ii = -1;
+    if (t == 0) {
+        S.ndiv = 0;
+        for (int k = 0; k < 2 * NQ; k++) S.qn[k / NQ][k % NQ] = 0;
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        SpawnMeta first;
+        first.ii = -1;
+        spawn_meta_load(insts, unit_start, n_inst, (int)blockIdx.x < n_units ? (int)blockIdx.x : -1, first);
+        draw_stage_issue(insts, first, S, 0);
+        nxt.ii = first.ii;
+        nxt.err = first.err; nxt.par = first.par; nxt.it = first.it; nxt.S = first.S;
+        const int un = (int)blockIdx.x + (int)gridDim.x;
+        spawn_meta_load(insts, unit_start, n_inst, un < n_units ? un : -1, nxt);
+    }
+    __syncthreads();
+    unsigned phase[2] = {0u, 0u};
+    int q = 0, cp = 0;             // stage, chunk parity
+    int cur = -1, seg = 0;         // the run whose segment (seg) fill is held in qf0, qf1
+    long long qf0 = 0, qf1 = 0;    // entries this block queued for run `cur` (singles, doubles)
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x, q ^= 1) {
+        const int b = S.binfo[q][0];
+        bool ok = true;
+        int m = 0, ii = 0;
+        if (b >= 0) {
+            ok = mbar_wait(&S.bar[q], phase[q]);
+            m = S.binfo[q][1];
+            ii = S.binfo[q][2];
+        }
+        const DevInst &I = insts[ii];
+        // A: the bucket from the stage; thread t owns determinants PER*t .. PER*t+PER-1
+        long long att = 0;
+        unsigned mine = 0;
+        unsigned nl[PER];
+        for (int j = 0; j < PER; j++) {
+            const int d = PER * t + j;
+            nl[j] = 0;
+            bool dv = false;
+            if (d < m && ok) {
+                const double c = S.sc[q][d];
+                const uint8_t f = S.sfl[q][d];
+                unsigned fl = 0;
+                double cper = 0.0;
+                u64 nat = 0;
+                if (!is_zero(c)) {
+                    if (!abs_lt(c, 0x1p31)) {
+                        atomicOr(&I.st->err, ERRB_NUMERIC);
+                    } else {
+                        nat = ceil_abs(c);
+                        const bool init = (dbits(c) & ~SIGN64) > dbits(I.n_a) || (f & (DFLAG_REF | DFLAG_D));
+                        fl = (init ? 1u : 0u) | ((f & DFLAG_D) ? 2u : 0u);
+                        cper = c;  // C / n_att: after A for n_att > 1 (c / 1 is c)
+                        att += (long long)nat;
+                        if (nat > HEAVY_ATT) {  // sliced into the heavy queue
+                            cper = c / (double)nat;
+                            const ulonglong2 kk = S.skey[q][d];
+                            const unsigned nch = (unsigned)((nat + HEAVY_ATT - 1) / HEAVY_ATT);
+                            const int q0 = atomicAdd(&I.st->heavy_n, (int)nch);
+                            if ((long long)q0 + nch > (long long)I.heavy_cap) atomicOr(&I.st->err, ERRB_HEAVY_CAP);
+                            else
+                                for (unsigned h = 0; h < nch; h++) {
+                                    HeavyChunk hc;
+                                    hc.a = kk.x; hc.b = kk.y; hc.cper = cper; hc.k0 = (u64)h * HEAVY_ATT;
+                                    const u64 left = nat - hc.k0;
+                                    hc.count = (unsigned)(left < HEAVY_ATT ? left : HEAVY_ATT);
+                                    hc.flags = fl;
+                                    hc.slot = (uint32_t)((size_t)b * CAP_M + d);
+                                    hc.pad = 0;
+                                    I.heavy[q0 + h] = hc;
+                                }
+                        } else {
+                            nl[j] = (unsigned)nat;
+                            dv = nat > 1;
+                        }
+                    }
+                }
+                S.sc[q][d] = cper;
+                S.fl[q][d] = (unsigned char)fl;
+                mine += nl[j];
+            }
+            queue_div(S, dv, d, lane);
+        }
+        for (int a = t; a < CHUNK_S; a += K1_THREADS) S.att_det[a] = 0xffffu;
+        unsigned v = mine;  // inclusive warp scan of the light attempt counts in determinant order
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane == 31) S.wsum[warp] = v;
+        if (__syncthreads_or(!ok)) {  // A; the copies did not land within the bound
+            if (t == 0) atomicOr(&I.st->err, ERRB_TIMEOUT);
+            mbar_wait(&S.bar[q], phase[q]);
+            return;
+        }
+        if (t == 0) {  // every thread is past the last reads of stage q ^ 1 (bucket u - grid)
+            draw_stage_issue(insts, nxt, S, q ^ 1);
+            const int un = u + 2 * (int)gridDim.x;
+            spawn_meta_load(insts, unit_start, n_inst, un < n_units ? un : -1, nxt);
+        }
+        if (b < 0) {
+            __syncthreads();  // stage q ^ 1's info is written before anyone reads it
+            continue;
+        }
+        phase[q] ^= 1u;
+        if (ii != cur) {  // a new run: the previous run's segment fill is final
+            if (t == 0 && cur >= 0) draw_flush(insts[cur], seg, qf0, qf1);
+            cur = ii;
+            seg = b % (int)gridDim.x;
+            qf0 = qf1 = 0;
+        }
+        const long long it = S.bit[q];
+        // B: attempt offsets (each warp sums the warp totals before its own), parents of the first
+        // CHUNK_S attempts, and C / n_att of the listed determinants
+        unsigned ex = v - mine, total = 0;
+        for (int w = 0; w < K1_THREADS / 32; w++) {
+            const unsigned x = S.wsum[w];
+            ex += w < warp ? x : 0u;
+            total += x;
+        }
+        for (int j = 0; j < PER; j++) {
+            S.off[PER * t + j] = ex;
+            if (nl[j] <= 8u && ex + nl[j] <= (unsigned)CHUNK_S)
+                for (unsigned a = 0; a < nl[j]; a++) S.att_det[ex + a] = (unsigned short)(PER * t + j);
+            ex += nl[j];
+        }
+        divide_listed(S.divl, S.ndiv, S.sc[q], t, K1_THREADS);
+        __syncthreads();  // B
+        if (t == 0) S.ndiv = 0;
+        const DrawBucketMap map{&S, q, (unsigned)((size_t)b * CAP_M)};
+        for (unsigned a0 = 0; a0 < total; a0 += CHUNK_S) {
+            if (a0) __syncthreads();  // the previous chunk's records are out before rec[] is reused
+            draw_classify(I, S, it, a0, min(total, a0 + CHUNK_S), map, S.qn[cp]);
+            __syncthreads();  // C
+            const int nd = S.qn[cp][Q_DOUBLE], ns = S.qn[cp][Q_SINGLE], ntot = ns + nd;
+            if (t < NQ) S.qn[cp ^ 1][t] = 0;  // every thread read the other counts before C
+            cp ^= 1;
+            const long long b0 = qf0, b1 = qf1;
+            qf0 += ns;
+            qf1 += nd;
+            bool over = false;
+            for (int r = t; r < ntot; r += K1_THREADS) {
+                const bool single = r < ns;
+                const SpawnRec rr = single ? S.rec[CHUNK_S - 1 - r] : S.rec[r - ns];
+                const int c = single ? 0 : 1;
+                const long long idx = single ? b0 + r : b1 + (r - ns);
+                if (idx >= I.qcap[c]) { over = true; continue; }
+                const unsigned d = rr.det;
+                const ulonglong2 kk = map.key(d);
+                QRec o;
+                o.ka = kk.x; o.kb = kk.y; o.cper = map.cper(d); o.w2 = rr.w2; o.w3 = rr.w3;
+                o.slot = map.slot(d);
+                o.info = (rr.ep & 0xffffu) | (map.flags(d) << 16);
+                I.qrec[c][(size_t)seg * I.qcap[c] + idx] = o;
+            }
+            if (over) atomicOr(&I.st->err, ERRB_QUEUE_CAP);
+            if (t == 0) {
+                if (qf0 > I.qcap[0]) atomicMax(&I.st->need_queue[0], (int)min(qf0, 0x7fffffffLL));
+                if (qf1 > I.qcap[1]) atomicMax(&I.st->need_queue[1], (int)min(qf1, 0x7fffffffLL));
+            }
+        }
+        for (int o = 16; o >= 1; o >>= 1) att += __shfl_xor_sync(0xffffffffu, att, o);
+        if (lane == 0 && att) red_add(&I.acc[(b % NSHARD) * ACC_STRIDE + ACC_ATT], (u64)att);
+    }
+    if (t == 0 && cur >= 0) draw_flush(insts[cur], seg, qf0, qf1);
 }
 
 // The evaluation of the queued attempts of every run: one attempt per
@@ -1947,12 +2267,13 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn_staged(const DevInst *_
 // parent's key, C_i / n_att, flags and slot travel in the record.
 __global__ void __launch_bounds__(256) k_spawn_eval(const DevInst *__restrict__ insts, int n_inst)
 {
-    __shared__ long long s_off[2][QSEG + 1];
+    __shared__ long long s_off[2][NSEG_MAX + 1];
     __shared__ int s_err, s_par;
     __shared__ double s_S;
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x, gs = (long long)gridDim.x * blockDim.x;
     for (int ii = 0; ii < n_inst; ii++) {
         const DevInst &I = insts[ii];
+        const int ns = I.qnseg;
         if (threadIdx.x < 32) {  // warp 0: the segment offsets of both classes by a warp scan
             const int lane = threadIdx.x;
             if (lane == 0) {
@@ -1960,13 +2281,12 @@ __global__ void __launch_bounds__(256) k_spawn_eval(const DevInst *__restrict__ 
                 s_par = I.st->parity;
                 s_S = I.st->S;
             }
-            static_assert(QSEG % 32 == 0, "segments per lane");
-            constexpr int PERL = QSEG / 32;
+            const int per = (ns + 31) / 32;  // segments lane*per .. lane*per+per-1
             for (int c = 0; c < 2; c++) {
-                long long v[PERL], mine = 0;
-                for (int r = 0; r < PERL; r++) {
-                    v[r] = min((long long)I.qcnt[(c * QSEG + lane * PERL + r) * QSTRIDE], I.qcap[c]);
-                    mine += v[r];
+                long long mine = 0;
+                for (int r = 0; r < per; r++) {
+                    const int g = lane * per + r;
+                    if (g < ns) mine += min((long long)I.qcnt[c * ns + g], I.qcap[c]);
                 }
                 long long inc = mine;
                 for (int o = 1; o < 32; o <<= 1) {
@@ -1974,26 +2294,30 @@ __global__ void __launch_bounds__(256) k_spawn_eval(const DevInst *__restrict__ 
                     if (lane >= o) inc += y;
                 }
                 long long ex = inc - mine;
-                for (int r = 0; r < PERL; r++) {
-                    s_off[c][lane * PERL + r] = ex;
-                    ex += v[r];
+                for (int r = 0; r < per; r++) {
+                    const int g = lane * per + r;
+                    if (g < ns) {
+                        s_off[c][g] = ex;
+                        ex += min((long long)I.qcnt[c * ns + g], I.qcap[c]);
+                    }
                 }
-                if (lane == 31) s_off[c][QSEG] = inc;
+                if (lane == 31) s_off[c][ns] = inc;
             }
         }
         __syncthreads();
         const int err = s_err, par = s_par;
         const double shift = s_S;
-        const long long nd = s_off[1][QSEG], ntot = nd + s_off[0][QSEG];
+        const long long nd = s_off[1][ns], ntot = nd + s_off[0][ns];
         if (!err)
             for (long long i = gt; i < ntot; i += gs) {
                 const int c = i < nd ? 1 : 0;
                 const long long j = c ? i : i - nd;
-                int g = 0;  // the segment holding entry j: the last g with s_off[c][g] <= j
-#pragma unroll
-                for (int step = QSEG / 2; step >= 1; step >>= 1)
-                    if (s_off[c][g + step] <= j) g += step;
-                const QRec r = I.qrec[c][(size_t)g * I.qcap[c] + (j - s_off[c][g])];
+                int lo = 0, hi = ns;  // the segment holding entry j: the last g with s_off[c][g] <= j
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_off[c][mid] <= j) lo = mid; else hi = mid;
+                }
+                const QRec r = I.qrec[c][(size_t)lo * I.qcap[c] + (j - s_off[c][lo])];
                 const SpawnCtx cx{r.slot, par, shift};
                 const unsigned flags = r.info >> 16, sel = r.info & 0xffffu;
                 if (c == 1) {
@@ -2013,7 +2337,7 @@ template <bool GENERAL>
 __global__ void __launch_bounds__(K3_THREADS, 3) k_annihilate(const DevInst *__restrict__ insts,
                                                               const int *__restrict__ unit_start, int n_inst, int n_units)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     K3Smem &Sm = *reinterpret_cast<K3Smem *>(smem_raw);
     K3Shared &S = Sm.sh;
     Stage<unsigned short> W{Sm.key, Sm.val, Sm.acc_lo, Sm.acc_hi, Sm.nacc, Sm.eflag, Sm.tab, Sm.opos};
@@ -2026,10 +2350,12 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k_annihilate(const DevInst *__r
     int cur = -1, err = 0, par = 0;
     long long it = 0;
     double shift = 0.0;
+    AnniTotals T;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
         const int ii = find_inst(unit_start, n_inst, u);
         const DevInst &I = insts[ii];
         if (ii != cur) {
+            if (cur >= 0) anni_flush(insts[cur], T);  // the previous run's totals are complete
             if (t == 0) {
                 S.hdr_err = *(volatile int *)&I.st->err;
                 S.hdr_par = I.st->parity;
@@ -2073,8 +2399,9 @@ __global__ void __launch_bounds__(K3_THREADS, 3) k_annihilate(const DevInst *__r
         }
         const LoadStage R{Sm.key, Sm.val, m, si, sn, I.cap_s, (size_t)b * CAP_M, (size_t)b * I.cap_s, &I, par};
         const Work3 W3{Sm.acc_lo, Sm.acc_hi, Sm.eflag, Sm.tab};
-        anni_bucket_3p(I, S, W3, R, b, par, it, shift, m, si, sn);
+        anni_bucket_3p(I, S, W3, R, b, par, it, shift, m, si, sn, T);
     }
+    if (cur >= 0) anni_flush(insts[cur], T);
 }
 
 __global__ void __launch_bounds__(K3_THREADS) k_annihilate_big(const DevInst *__restrict__ insts, int n_inst)
@@ -2207,7 +2534,7 @@ __global__ void __launch_bounds__(K5_THREADS) k_finalize(const DevInst *__restri
 #pragma unroll
     for (int k = 0; k < NACC; k++) w[k] = __shfl_sync(0xffffffffu, v, k);
     if (I.qcnt)  // the attempt queues of split spawning start empty
-        for (int g = lane; g < 2 * QSEG; g += 32) I.qcnt[g * QSTRIDE] = 0;
+        for (int g = lane; g < 2 * I.qnseg; g += 32) I.qcnt[g] = 0;
     if (lane != 0) return;
     const u128 W = (u128)limb_total(w + ACC_NW);
     const i128 A = limb_total(w + ACC_ANN), EN = limb_total(w + ACC_ENUM);
@@ -2444,9 +2771,9 @@ void launch_spawn(const DevInst *dinst, const int *unit_start, int n_inst, int n
     if (staged && (g_spawn_bps == 0 || g_spawn_bps == 1)) {
         int grid = n_units < num_sms() * 3 ? n_units : num_sms() * 3;
         if (grid < 1) grid = 1;
-        if (split && g_spawn_bps == 1)
-            k_spawn_staged<true><<<grid, K1_THREADS, sizeof(K6Smem), s>>>(dinst, unit_start, n_inst, n_units);
-        else k_spawn_staged<false><<<grid, K1_THREADS, sizeof(K6Smem), s>>>(dinst, unit_start, n_inst, n_units);
+        if (split && g_spawn_bps == 1)  // grid <= draw_segments(): at most one queue segment per block and run
+            k_spawn_draw<<<grid, K1_THREADS, sizeof(K7Smem), s>>>(dinst, unit_start, n_inst, n_units);
+        else k_spawn_staged<<<grid, K1_THREADS, sizeof(K6Smem), s>>>(dinst, unit_start, n_inst, n_units);
         return;
     }
     const int bps = g_spawn_bps > 0 ? g_spawn_bps : 8;
@@ -2456,7 +2783,8 @@ void launch_spawn(const DevInst *dinst, const int *unit_start, int n_inst, int n
 }
 
 // split spawning (queues in global memory, flat evaluation): geometry 1
-bool spawn_split_selected() { return g_spawn_bps == 1; }
+bool spawn_split_selected() { return g_spawn_bps == 1 && draw_segments() <= NSEG_MAX; }
+int draw_segments() { return num_sms() * 3; }
 
 void launch_spawn_eval(const DevInst *dinst, int n_inst, cudaStream_t s)
 {
@@ -2487,11 +2815,9 @@ cudaError_t init_kernels()
                                  (int)sizeof(K4Smem<STAGED_SCAP>));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_spawn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K1Smem));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_spawn_staged<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(K6Smem));
+        e = cudaFuncSetAttribute(k_spawn_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K6Smem));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_spawn_staged<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(K6Smem));
+        e = cudaFuncSetAttribute(k_spawn_draw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K7Smem));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_spawn_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(K1Smem));
     return e;
