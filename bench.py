@@ -191,6 +191,9 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": "spawn attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+KERNEL_NAMES = {"k_spawn": "k_spawn_draw + k_spawn_eval (split spawning)",
+                "k_annihilate": "k_annihilate_staged + k_annihilate_big"}
+
 WORKLOAD_NAMES = {
     "abinitio50": "abinitio-50orb-10a10b (synthetic: 200 Cholesky vectors, seed 4), D = 1e4, ~1e8 walkers",
     "abinitio24": "abinitio-24orb-6a6b (synthetic: 96 Cholesky vectors, seed 2), ~1e6 walkers",
@@ -475,6 +478,8 @@ def main():
     attempts = float(np.sum(st["attempts"][sel]))
     annihilated = float(np.sum(st["annihilated"][sel]))
     ndet_mean = float(np.mean(st["ndet"][sel]))
+    spawns_mean = float(np.mean(st["spawns"][sel]))
+    attempts_mean = attempts / args.steps  # this rank's
     nw_mean = float(np.mean(st["nw"][sel]))
     if dist:
         t_dev, attempts, annihilated = aggregate_ranks(t_dev, attempts, annihilated, dist, "cuda")
@@ -523,14 +528,28 @@ def main():
     except Exception:
         pass
 
+    # issue ceiling: every SM sub-partition issues at most one warp instruction per clock
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    clk_sum = clk.summary()
+    sm_hz = (clk_sum.get("sm_mhz") or clk_sum.get("sm_max_mhz") or 2070.0) * 1e6
+    issue_peak = 4.0 * n_sm * sm_hz
+
     def roof(k):
         ach = alg[k] / (tms[k] * 1e-3) / 1e9
         rec = traffic_rec.get(k) or {}
-        # DRAM bytes were captured on a smaller list; they scale with the records a launch processes
+        # DRAM bytes and warp instructions were counted on a smaller list; both
+        # scale with the records a launch processes
         units = float(np.mean(n_in + n_sp))
         tr_b = rec["dram_bytes_per_unit"] * units if "dram_bytes_per_unit" in rec else rec.get("dram_bytes_per_launch")
-        return {"kernel": k, "achieved": ach, "frac": ach / peak, "traffic": tr_b,
-                "alg_bytes_per_launch": alg[k], "launch_ms": tms[k]}
+        out = {"kernel": k, "kernels": KERNEL_NAMES[k], "achieved": ach, "frac": ach / peak, "traffic": tr_b,
+               "alg_bytes_per_launch": alg[k], "launch_ms": tms[k]}
+        if "inst_per_unit" in rec:
+            inst = rec["inst_per_unit"] * units
+            out["issue"] = {"bound": "issue", "warp_instructions_per_launch": inst,
+                            "achieved": inst / (tms[k] * 1e-3), "peak": issue_peak,
+                            "unit": "warp instructions/s", "frac": inst / (tms[k] * 1e-3) / issue_peak,
+                            "peak_source": "4 per SM per clock x %d SMs x the median SM clock under load" % n_sm}
+        return out
 
     dominant = max(tms, key=tms.get)  # the kernel with the longest launches
     other = "k_annihilate" if dominant == "k_spawn" else "k_spawn"
@@ -595,7 +614,8 @@ def main():
                                     if big else
                                     "prescribed 1e-3 exceeds 1/sum_j|H_ref,j| (2412 Eh): walker number uncontrollable"),
                        "semistoch_size": prm.get("semistoch_size", 0),
-                       "walkers_mean": nw_mean, "dets_mean": ndet_mean, "l2": "flushed (256 MB write) between steps",
+                       "walkers_mean": nw_mean, "dets_mean": ndet_mean, "spawns_mean": spawns_mean,
+                       "attempts_mean": attempts_mean, "l2": "flushed (256 MB write) between steps",
                        "untimed_iterations_before": n_grow + args.warmup,
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": roofline,
