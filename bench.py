@@ -562,6 +562,15 @@ def main():
     keep = ("alpha", "beta", "c")
     pinned = {k: torch.from_numpy(np.ascontiguousarray(state[k])).pin_memory() for k in keep}
     host_state = {k: v.numpy() for k, v in pinned.items()}
+    # the job's output buffers: pinned host memory allocated before the job
+    # (a checkpointing user keeps them), room for 25 % more determinants
+    cap_out = int(state["c"].size * 1.25) + 4096
+    pin_out = {"alpha": torch.empty(cap_out, dtype=torch.int64, pin_memory=True),
+               "beta": torch.empty(cap_out, dtype=torch.int64, pin_memory=True),
+               "c": torch.empty(cap_out, dtype=torch.float64, pin_memory=True),
+               "hdiag": torch.empty(cap_out, dtype=torch.float64, pin_memory=True),
+               "flags": torch.empty(cap_out, dtype=torch.int32, pin_memory=True)}
+    out_bufs = {k: (v.numpy().view(np.uint64) if k in ("alpha", "beta") else v.numpy()) for k, v in pin_out.items()}
     # the restarted run selects its deterministic space from the imported list
     prm2 = dict(prm, semistoch_start=shift["iteration"] - shift["shift_start"]) if big else prm
     del h
@@ -574,7 +583,7 @@ def main():
     t2 = time.perf_counter()
     fq.fciqmc_step(h2, E2E_STEPS)
     t3 = time.perf_counter()
-    out_state = fq.fciqmc_export_state(h2)
+    out_state = fq.fciqmc_export_state(h2, out=out_bufs)
     en2 = fq.fciqmc_energy(h2)
     e2e_el = time.perf_counter() - t0
     e2e_phases = {"create": t1 - t0, "import": t2 - t1, "steps": t3 - t2, "export_energy": t0 + e2e_el - t3}
@@ -584,7 +593,7 @@ def main():
     h2d = sysd["h1"].nbytes + sysd["eri"].nbytes + sum(host_state[k].nbytes for k in keep)
     d2h = sum(v.nbytes for v in out_state.values()) + E2E_STEPS * ctypes.sizeof(fq.fciqmc_iter_stats)
     assert np.isfinite(en2["nw"])
-    del h2, pinned, host_state, out_state
+    del h2, pinned, host_state, out_state, out_bufs, pin_out
 
     # ---- CPU baseline: the oracle on a key-hash sample of the same state, bounded
     cpu = None
@@ -624,7 +633,7 @@ def main():
             "e2e": {"value": e2e_att / e2e_el, "unit": "spawn attempts/s", "h2d_bytes_per_step": h2d / E2E_STEPS,
                     "d2h_bytes_per_step": d2h / E2E_STEPS,
                     "job": "create + import the %.3g-determinant checkpoint from pinned host memory + %d steps + "
-                           "export + energy" % (ndet_mean, E2E_STEPS),
+                           "export into pinned host memory + energy" % (ndet_mean, E2E_STEPS),
                     "phases_s": e2e_phases},
             "gpu_launches": args.steps * launches_per_iter,
             "gpu_launches_per_step": launches_per_iter,

@@ -313,17 +313,28 @@ def fciqmc_num_dets(handle):
     return _lib.fciqmc_num_dets(handle.h)
 
 
-def fciqmc_export_state(handle):
+def fciqmc_export_state(handle, out=None):
+    """The walker list (sorted by key) as arrays alpha, beta, c, hdiag, flags.
+    `out`: optional dict of caller-owned arrays with those keys (uint64,
+    uint64, float64, float64, int32; C-contiguous, e.g. views of pinned host
+    memory kept across checkpoints); used when all hold the whole list, and
+    the result is then views of them."""
     n = C.c_int64()
     _lib.fciqmc_export_state(handle.h, 0, None, None, None, None, None, C.byref(n))
     m = max(n.value, 1)
-    # output pages are touched here: a first touch inside the CUDA driver's
-    # pageable device-to-host copy costs ten times the copy itself
-    a, b = np.empty(m, np.uint64), np.empty(m, np.uint64)
-    c, hd = np.empty(m, np.float64), np.empty(m, np.float64)
-    fl = np.empty(m, np.int32)
-    for x in (a, b, c, hd, fl):
-        x.fill(0)
+    want = (("alpha", np.uint64), ("beta", np.uint64), ("c", np.float64), ("hdiag", np.float64), ("flags", np.int32))
+    if out is not None and all(k in out and out[k].dtype == t and out[k].ndim == 1 and out[k].size >= m and
+                               out[k].flags["C_CONTIGUOUS"] and out[k].flags["WRITEABLE"] for k, t in want):
+        a, b, c, hd, fl = (out[k] for k, _ in want)
+        m = min(x.size for x in (a, b, c, hd, fl))
+    else:
+        # output pages are touched here: a first touch inside the CUDA driver's
+        # pageable device-to-host copy costs ten times the copy itself
+        a, b = np.empty(m, np.uint64), np.empty(m, np.uint64)
+        c, hd = np.empty(m, np.float64), np.empty(m, np.float64)
+        fl = np.empty(m, np.int32)
+        for x in (a, b, c, hd, fl):
+            x.fill(0)
     _check(_lib.fciqmc_export_state(handle.h, m, a.ctypes.data_as(_u64p), b.ctypes.data_as(_u64p),
                                     c.ctypes.data_as(_dp), hd.ctypes.data_as(_dp),
                                     fl.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(n)), handle.h)

@@ -192,6 +192,31 @@ def test_export_import_device_and_host_fallback_agree(name, sysd, params):
     assert_states_equal(fq.fciqmc_export_state(tight), o.export())
 
 
+def test_export_into_caller_arrays():
+    """fciqmc_export_state(h, out=...) fills caller-owned arrays (here larger
+    than the list) with the same list as the allocating form; arrays of the
+    wrong type or too small are not used."""
+    fq = _fq()
+    sysd, params = workloads.small_abinitio(8, 3, 3, seed=5), dict(DAMP, tau=0.005, target_walkers=3000,
+                                                                    initiator_threshold=3.0, seed=11)
+    g = fq.fciqmc_create(sysd, params)
+    fq.fciqmc_step(g, 120)
+    ref = fq.fciqmc_export_state(g)
+    n = ref["c"].size
+    types = dict(alpha=np.uint64, beta=np.uint64, c=np.float64, hdiag=np.float64, flags=np.int32)
+    out = {k: np.full(n + 77, 7, t) for k, t in types.items()}
+    got = fq.fciqmc_export_state(g, out=out)
+    assert_states_equal(got, ref)
+    for k in types:
+        assert np.shares_memory(got[k], out[k])
+    small = {k: np.zeros(max(n - 1, 1), t) for k, t in types.items()}
+    assert_states_equal(fq.fciqmc_export_state(g, out=small), ref)
+    wrong = dict(out, c=np.zeros(n + 77, np.float32))
+    got2 = fq.fciqmc_export_state(g, out=wrong)
+    assert_states_equal(got2, ref)
+    assert not np.shares_memory(got2["alpha"], out["alpha"])
+
+
 def test_checkpoint_restart_continues_identically():
     fq = _fq()
     sysd, params = workloads.small_abinitio(8, 3, 3, seed=5), dict(DAMP, tau=0.005, target_walkers=3000,
