@@ -442,9 +442,10 @@ int fciqmc_autotune(fciqmc_handle **hs, int32_t k, int64_t n_iter, int32_t out[3
 
 /* Sets (or reads) the launch configuration the autotuner chooses from, for
  * every later launch in the process: spawn 0 = the staged kernel, 1 = split
- * spawning (the staged kernel draws and queues every attempt in global
- * memory by class, 48 bytes each; a flat kernel evaluates them one per
- * thread), 2, 4, 8, 16 = the plain-load kernel with that many blocks per SM;
+ * spawning (a staged draw kernel queues every attempt in global memory by
+ * class, 48 bytes each, in per-run segments owned by its blocks, about 7 GB at
+ * 1.2e8 attempts; a flat kernel evaluates them one per thread), 2, 4, 8, 16 =
+ * the plain-load kernel with that many blocks per SM;
  * heavy = blocks per SM of the heavy-determinant kernel (1..16); annihilate
  * as for fciqmc_autotune (0, 3, 9, 24).  A handle captures its iteration graph
  * again at its next step.  FCIQMC_ERR_INVALID_ARG for other values.  Results
