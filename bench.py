@@ -285,11 +285,10 @@ def run_batch_to_sigma(args):
         res[mode] = {"wall_s": wall, "status": st}
         del srv
     sb, ss = res["batched"]["status"], res["sequential"]["status"]
-    # walker dynamics bit-identical: iterations, attempts; the energy within the
-    # rounding of E_num's per-bucket binary64 sums (their order follows the
-    # order of arrival of spawns)
+    # bit-identical: iterations, attempts, the energy and its error (every
+    # statistics row is exact, E_num included)
     def close(x, y):
-        return (np.isnan(x) and np.isnan(y)) or abs(x - y) <= 1e-9 * max(abs(x), abs(y), 1e-300)
+        return (np.isnan(x) and np.isnan(y)) or x == y
     same = all(a["iterations"] == b["iterations"] and a["attempts"] == b["attempts"] and close(a["energy"], b["energy"])
                and close(a["sigma"], b["sigma"]) for a, b in zip(sb, ss))
     att = float(sum(a["attempts"] for a in sb))

@@ -146,7 +146,10 @@ typedef struct {
 /* One row per completed iteration.  nw: walker number N_w = 2^-32 sum
  * floor(|C| 2^32).  shift: S after the iteration (relative to E_ref).
  * e_num = sum_{j != ref} H_ref,j C_j and e_den = C_ref after the iteration
- * (Eq. (9)); attempts = sum ceil(|C|); spawns = spawned walkers stored;
+ * (Eq. (9); every term of e_num is the binary64 product truncated toward zero
+ * to a multiple of 2^-Fe, Fe = min(64, 60 - floor(log2 max |integral|) -
+ * ceil(log2(2n + 1))), and the terms are summed exactly and rounded once, so
+ * e_num depends on no order); attempts = sum ceil(|C|); spawns = spawned walkers stored;
  * rejected = spawns removed by the initiator rule; annihilated = walkers
  * removed by summing opposite-sign contributions. */
 typedef struct {

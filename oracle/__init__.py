@@ -107,6 +107,7 @@ def lib():
                 "orc_semistoch_csr": (None, [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), dp, up, up]),
                 "orc_semistoch_rows": (None, [P, dp, dp]),
                 "orc_proj_energy": (None, [P, dp, dp]),
+                "orc_enum_grid": (I32, [P]),
                 "orc_generate_pchb": (I32, [P, U64, U64, up, up, up, dp]),
                 "orc_pchb_table": (I32, [P, I32, I32, I32, dp, dp, dp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                          C.POINTER(C.c_int32), dp]),
@@ -211,6 +212,11 @@ class System:
 
     def hdiag_rel(self, a, b) -> float:
         return lib().orc_hdiag_rel(self.h, a, b)
+
+    @property
+    def enum_grid(self) -> int:
+        """Fe: E_num's terms are truncated to multiples of 2^-Fe (reading R12)."""
+        return lib().orc_enum_grid(self.h)
 
     def hoff(self, i, j) -> float:
         """<D_j|H|D_i> for determinants i=(a,b), j=(a,b), i != j."""

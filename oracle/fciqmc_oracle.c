@@ -218,6 +218,7 @@ typedef struct {
     uint64_t ref_a, ref_b;
     xacc xref; /* exact diagonal sum X(D_ref) */
     double eref;
+    int Fe;    /* grid 2^-Fe of the E_num terms (reading R12) */
 } orc_sys;
 
 void orc_sys_free(orc_sys *s);
@@ -331,10 +332,43 @@ double orc_hoff(const orc_sys *s, uint64_t ia, uint64_t ib, uint64_t ja, uint64_
     return g < 0 ? -v : v;
 }
 
+/* E_num of Eq. (9) (reading R12): each term H_ref,j C_j is the binary64
+ * product truncated toward zero to a multiple of 2^-Fe; the truncated terms
+ * are summed exactly and the sum is rounded once.  Fe = min(64, 60 - m - L),
+ * m = floor(log2 max |integral|) over h, (pq|rs) and E_core (Fe = 64 when all
+ * vanish), L = ceil(log2(2n + 1)): |H_ref,j| < (2n + 1) 2^(m + 1), |C_j| <
+ * 2^31 and at most 2^34 terms keep the sum below 2^126 grid steps. */
+static int enum_grid(const orc_sys *s)
+{
+    int64_t nh = (int64_t)s->norb * s->norb, np = (int64_t)s->norb * (s->norb + 1) / 2, ne = np * (np + 1) / 2;
+    int any = 0, m = 0;
+    for (int64_t i = 0; i < nh + ne + 1; i++) {
+        double x = i < nh ? s->h[i] : (i < nh + ne ? s->eri[i - nh] : s->ecore);
+        if (x == 0.0) continue;
+        int e;
+        frexp(fabs(x), &e); /* |x| in [2^(e-1), 2^e) */
+        if (!any || e - 1 > m) m = e - 1;
+        any = 1;
+    }
+    if (!any) return 64;
+    int n = s->na + s->nb, L = 0;
+    while ((1LL << L) < 2LL * n + 1) L++;
+    int fe = 60 - m - L;
+    return fe > 64 ? 64 : fe;
+}
+
+static double trunc_grid(double p, int F)
+{
+    /* exact: p 2^F stays far below 2^1023, its integer part has at most 53
+     * significant bits, and a nonzero result is at least 2^-F >= 2^-64 */
+    return ldexp(trunc(ldexp(p, F)), -F);
+}
+
 static int sys_finish(orc_sys *s)
 {
     if (popc(s->ref_a) != s->na || popc(s->ref_b) != s->nb) return -1;
     if (s->norb < 64 && ((s->ref_a | s->ref_b) >> s->norb) != 0) return -1;
+    s->Fe = enum_grid(s);
     xdiag(s, s->ref_a, s->ref_b, &s->xref);
     xacc x = s->xref;
     xacc_add(&x, s->ecore, 0);
@@ -1376,17 +1410,21 @@ static int one_iteration(orc_run *r)
     free(sp); free(c0); free(r->L);
     r->L = out; r->n = no; r->cap = outcap;
 
-    /* reductions: N_w (R6), E_num / E_den (Eq. (9)) */
+    /* reductions: N_w (R6), E_num (R12) / E_den (Eq. (9)) */
     u128 W = 0;
-    double e_num = 0.0, e_den = 0.0;
+    double e_den = 0.0;
+    xacc xe;
+    xacc_zero(&xe);
     for (int64_t i = 0; i < no; i++) {
         odet *d = &out[i];
         if (fabs(d->c) >= 0x1p31) return 3;
         W += fx32(d->c);
         if (d->flags & 1) { e_den = d->c; continue; }
         int lev = popc(d->a ^ s->ref_a) + popc(d->b ^ s->ref_b);
-        if (lev <= 4 && d->c != 0.0) e_num = e_num + orc_hoff(s, d->a, d->b, s->ref_a, s->ref_b) * d->c;
+        if (lev <= 4 && d->c != 0.0)
+            xacc_add(&xe, trunc_grid(orc_hoff(s, d->a, d->b, s->ref_a, s->ref_b) * d->c, s->Fe), 0);
     }
+    double e_num = xacc_round(&xe);
     double nw = (double)W * 0x1p-32;
     if (!(nw == nw)) return 3;
     /* E_Trial numerator and denominator, in ascending key order */
@@ -1605,16 +1643,22 @@ int orc_stat_size(void) { return (int)sizeof(orc_stat); }
 int orc_params_size(void) { return (int)sizeof(orc_params); }
 
 /* E_num, E_den of the current list (Eq. (9)): E_num = sum_{j != ref} H_ref,j C_j
- * summed in ascending key order, E_den = C_ref */
+ * as in reading R12 (terms truncated to 2^-Fe, summed exactly, rounded once),
+ * E_den = C_ref */
 void orc_proj_energy(const orc_run *r, double *num, double *den)
 {
     const orc_sys *s = r->s;
-    double e_num = 0.0, e_den = 0.0;
+    double e_den = 0.0;
+    xacc xe;
+    xacc_zero(&xe);
     for (int64_t i = 0; i < r->n; i++) {
         const odet *d = &r->L[i];
         if (d->a == s->ref_a && d->b == s->ref_b) { e_den = d->c; continue; }
         int lev = popc(d->a ^ s->ref_a) + popc(d->b ^ s->ref_b);
-        if (lev <= 4 && d->c != 0.0) e_num = e_num + orc_hoff(s, d->a, d->b, s->ref_a, s->ref_b) * d->c;
+        if (lev <= 4 && d->c != 0.0)
+            xacc_add(&xe, trunc_grid(orc_hoff(s, d->a, d->b, s->ref_a, s->ref_b) * d->c, s->Fe), 0);
     }
-    *num = e_num; *den = e_den;
+    *num = xacc_round(&xe); *den = e_den;
 }
+
+int orc_enum_grid(const orc_sys *s) { return s->Fe; }

@@ -87,7 +87,7 @@ struct Partial {  // per-bucket binary64 sums of one iteration (estimators that 
 enum {
     ACC_NW = 0,      // N_w * 2^32, three limbs
     ACC_ANN = 3,     // annihilated walkers * 2^32, three limbs
-    ACC_ENUM = 6,    // E_num * 2^Fe (each bucket's binary64 sum placed on the grid), three limbs
+    ACC_ENUM = 6,    // E_num * 2^Fe (every term truncated to the grid), three limbs
     ACC_NDET = 9, ACC_REJ, ACC_SPAWNS, ACC_ATT,
     NACC
 };

@@ -701,7 +701,6 @@ enum { EF_OWNER = 1, EF_OCC = 2, EF_KEEP = 4, EF_ACC = 8, EF_REF = 16, EF_D = 32
 
 struct K3Shared {
     int wsum[K3_THREADS / 32];
-    double red_d[K3_THREADS / 32];
     double red_t[K3_THREADS / 32][2];
     u64 red_u[K3_THREADS / 32][8];
     int n_new, side_n;
@@ -1018,7 +1017,8 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
     double *nc = I.c[np], *nhd = I.hd[np];
     uint8_t *nfl = I.fl[np];
     u128 nw = 0;
-    double enm = 0.0, tnum = 0.0, tden = 0.0;
+    i128 enm = 0;  // E_num: each term truncated to the grid 2^-Fe (R12), summed exactly
+    double tnum = 0.0, tden = 0.0;
     bool bad = false;
     if (!overflow) {
         for (int r = 0; t + r * K3_THREADS < E; r++) {
@@ -1041,7 +1041,7 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
             if (f & EF_REF) I.st->e_den = c;
             else {
                 const int lev = __popcll(k.x ^ I.ref_a) + __popcll(k.y ^ I.ref_b);
-                if (lev <= 4 && !is_zero(c)) enm = enm + hoff_generic(I, k.x, k.y, I.ref_a, I.ref_b) * c;
+                if (lev <= 4 && !is_zero(c)) enm += to_fixed(hoff_generic(I, k.x, k.y, I.ref_a, I.ref_b) * c, I.Fe);
             }
             if (f & EF_D) I.dc_buf[par ^ 1][d_index_of(I, k.x, k.y)] = c;
             if (I.trial_bits && !is_zero(c)) {  // trial-wave-function estimator (Sec. IV)
@@ -1092,13 +1092,12 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
             tden = tden + __shfl_xor_sync(0xffffffffu, tden, mm);
         }
     for (int mm = 16; mm >= 1; mm >>= 1) {
-        enm = enm + __shfl_xor_sync(0xffffffffu, enm, mm);
+        enm += shfl_xor_i128(enm, mm);
         rejected += __shfl_xor_sync(0xffffffffu, rejected, mm);
         ann += shfl_xor_i128(ann, mm);
         nw += (u128)shfl_xor_i128((i128)nw, mm);
     }
     if (lane == 0) {
-        S.red_d[warp] = enm;
         S.red_t[warp][0] = tnum;
         S.red_t[warp][1] = tden;
         S.red_u[warp][0] = (u64)nw;
@@ -1106,15 +1105,16 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
         S.red_u[warp][2] = (u64)ann;
         S.red_u[warp][3] = (u64)((u128)ann >> 64);
         S.red_u[warp][4] = (u64)rejected;
+        S.red_u[warp][5] = (u64)enm;
+        S.red_u[warp][6] = (u64)((u128)enm >> 64);
     }
     __syncthreads();
     if (t == 0) {
-        double e_sum = 0.0, tn = 0.0, td = 0.0;
+        double tn = 0.0, td = 0.0;
         u128 nws = 0;
-        i128 anns = 0;
+        i128 anns = 0, ens = 0;
         long long rej = 0;
         for (int k = 0; k < K3_THREADS / 32; k++) {
-            e_sum = e_sum + S.red_d[k];
             if (I.trial_bits) {
                 tn = tn + S.red_t[k][0];
                 td = td + S.red_t[k][1];
@@ -1122,13 +1122,13 @@ __device__ void anni_bucket(const DevInst &I, K3Shared &S, Stage<IDX> W, int tab
             nws += ((u128)S.red_u[k][1] << 64) | S.red_u[k][0];
             anns += (i128)(((u128)S.red_u[k][3] << 64) | S.red_u[k][2]);
             rej += (long long)S.red_u[k][4];
+            ens += (i128)(((u128)S.red_u[k][6] << 64) | S.red_u[k][5]);
         }
-        // the bucket's share of the run's exact totals (its line b % NSHARD); the
-        // bucket's E_num, summed in a fixed order, is placed on the grid 2^-Fe
+        // the bucket's share of the run's exact totals (its line b % NSHARD)
         u64 *acc = I.acc + (b % NSHARD) * ACC_STRIDE;
         limb_add(acc + ACC_NW, (i128)nws);
         limb_add(acc + ACC_ANN, anns);
-        limb_add(acc + ACC_ENUM, to_fixed(e_sum, I.Fe));
+        limb_add(acc + ACC_ENUM, ens);
         red_add(&acc[ACC_NDET], (u64)total);
         if (rej) red_add(&acc[ACC_REJ], (u64)rej);
         red_add(&acc[ACC_SPAWNS], (u64)(si + sn));
@@ -1238,6 +1238,7 @@ struct BulkStage {
 struct AnniTotals {
     u128 nw = 0;            // N_w * 2^32
     i128 ann = 0;           // annihilated walkers * 2^32
+    i128 enm = 0;           // E_num * 2^Fe (terms truncated to the grid)
     long long rej = 0;      // rejected non-initiator spawns
     long long ndet = 0;     // determinants kept (thread 0)
     long long spawns = 0;   // spawns received (thread 0)
@@ -1252,11 +1253,13 @@ __device__ void anni_flush(const DevInst &I, AnniTotals &T)
         T.rej += __shfl_xor_sync(0xffffffffu, T.rej, mm);
         T.ann += shfl_xor_i128(T.ann, mm);
         T.nw += (u128)shfl_xor_i128((i128)T.nw, mm);
+        T.enm += shfl_xor_i128(T.enm, mm);
     }
     u64 *acc = I.acc + (blockIdx.x % NSHARD) * ACC_STRIDE;
     if (lane == 0) {
         limb_add(acc + ACC_NW, (i128)T.nw);
         limb_add(acc + ACC_ANN, T.ann);
+        limb_add(acc + ACC_ENUM, T.enm);
         if (T.rej) red_add(&acc[ACC_REJ], (u64)T.rej);
     }
     if (threadIdx.x == 0) {
@@ -1378,7 +1381,7 @@ __device__ void anni_bucket_3p(const DevInst &I, K3Shared &S, const Work3 &W, co
     double *nc = I.c[np], *nhd = I.hd[np];
     uint8_t *nfl = I.fl[np];
     u128 nw = 0;
-    double enm = 0.0, tnum = 0.0, tden = 0.0;
+    double tnum = 0.0, tden = 0.0;
     bool bad = false;
     for (int e0 = 0; e0 < E; e0 += K3_THREADS) {
         const int e = e0 + t;
@@ -1430,7 +1433,8 @@ __device__ void anni_bucket_3p(const DevInst &I, K3Shared &S, const Work3 &W, co
             if (f & EF_REF) I.st->e_den = accv;
             else {
                 const int lev = __popcll(k.x ^ I.ref_a) + __popcll(k.y ^ I.ref_b);
-                if (lev <= 4 && !is_zero(accv)) enm = enm + hoff_generic(I, k.x, k.y, I.ref_a, I.ref_b) * accv;
+                if (lev <= 4 && !is_zero(accv))  // E_num term on the grid 2^-Fe (R12)
+                    T.enm += to_fixed(hoff_generic(I, k.x, k.y, I.ref_a, I.ref_b) * accv, I.Fe);
             }
             if (f & EF_D) I.dc_buf[np][d_index_of(I, k.x, k.y)] = accv;
             if (I.trial_bits && !is_zero(accv)) {  // trial-wave-function estimator (Sec. IV)
@@ -1450,11 +1454,10 @@ __device__ void anni_bucket_3p(const DevInst &I, K3Shared &S, const Work3 &W, co
     }
     if (bad) atomicOr(&I.st->err, ERRB_NUMERIC);
     // bucket reductions (fixed order: lanes by xor tree, warps in index order)
-    // the integer totals stay in the thread (added to the run's accumulators
-    // when the block leaves the run); E_num and the trial sums are binary64,
-    // summed per bucket in a fixed order (lanes by xor tree, warps in index
-    // order; a warp or block whose terms are all +0 adds nothing, and none of
-    // these sums is ever -0)
+    // the integer totals (E_num's truncated terms among them) stay in the
+    // thread and are added to the run's accumulators when the block leaves
+    // the run; the trial sums are binary64, summed per bucket in a fixed order
+    // (lanes by xor tree, warps in index order)
     T.rej += rejected;
     T.ann += ann;
     T.nw += nw;
@@ -1463,10 +1466,7 @@ __device__ void anni_bucket_3p(const DevInst &I, K3Shared &S, const Work3 &W, co
             tnum = tnum + __shfl_xor_sync(0xffffffffu, tnum, mm);
             tden = tden + __shfl_xor_sync(0xffffffffu, tden, mm);
         }
-    if (__any_sync(0xffffffffu, dbits(enm) != 0))
-        for (int mm = 16; mm >= 1; mm >>= 1) enm = enm + __shfl_xor_sync(0xffffffffu, enm, mm);
     if (lane == 0) {
-        S.red_d[warp] = enm;
         S.red_t[warp][0] = tnum;
         S.red_t[warp][1] = tden;
     }
@@ -1474,16 +1474,13 @@ __device__ void anni_bucket_3p(const DevInst &I, K3Shared &S, const Work3 &W, co
     if (t == 0) {
         const int total = S.n_new;
         S.n_new = 0;  // next used after two more barriers
-        double e_sum = 0.0, tn = 0.0, td = 0.0;
-        for (int k = 0; k < K3_THREADS / 32; k++) {
-            if (dbits(S.red_d[k])) e_sum = e_sum + S.red_d[k];
-            if (I.trial_bits) {
+        double tn = 0.0, td = 0.0;
+        if (I.trial_bits)
+            for (int k = 0; k < K3_THREADS / 32; k++) {
                 tn = tn + S.red_t[k][0];
                 td = td + S.red_t[k][1];
             }
-        }
         if (total > CAP_M) { atomicOr(&I.st->err, ERRB_MAIN_CAP); atomicMax(&I.st->need_main, total); }
-        if (dbits(e_sum)) limb_add(I.acc + (b % NSHARD) * ACC_STRIDE + ACC_ENUM, to_fixed(e_sum, I.Fe));
         T.ndet += total;
         T.spawns += si + sn;
         if (I.trial_bits) {

@@ -39,13 +39,12 @@ def test_requests_in_the_mix_equal_alone():
         fq.fciqmc_step(alone, 300)
         en = fq.fciqmc_energy(alone)
         assert st["tau"] == fq.fciqmc_tau(alone)
-        # the walker dynamics (and so the shift) are bit-identical; E_proj and its
-        # error within the rounding of E_num's per-bucket binary64 sums, whose
-        # order follows the order in which spawns arrive (R12: 1e-11 per row)
+        # the walker dynamics, the shift and every statistics row (E_num an
+        # exact sum, R12) are bit-identical, and so are E_proj and its error
         assert st["shift"] == en["shift"]
         for k_srv, k_alone in [("energy", "e_proj_mean"), ("sigma", "e_proj_sigma")]:
             a, b = st[k_srv], en[k_alone]
-            assert (np.isnan(a) and np.isnan(b)) or abs(a - b) <= 1e-9 * max(abs(a), abs(b)), (k_srv, a, b)
+            assert (np.isnan(a) and np.isnan(b)) or a == b, (k_srv, a, b)
         assert st["attempts"] == en["attempts_total"]
         assert st["t_done"] >= st["t_start"] >= st["t_submit"] == st["t_arrival"]
 

@@ -262,6 +262,51 @@ def test_projected_energy_exact_for_eigenstate(which):
     assert abs(num / den - e0) < 1e-10 * max(1.0, abs(e0))
 
 
+def test_projected_energy_numerator_is_exact_sum_of_truncated_terms():
+    """Reading R12: E_num = sum_{j != ref} H_ref,j C_j with every binary64
+    product truncated toward zero to a multiple of 2^-Fe, summed exactly and
+    rounded once to nearest-even, Fe = min(64, 60 - m - ceil(log2(2n + 1)))
+    (m = floor(log2 max |integral|)).  Checked against exact rational
+    arithmetic on a list whose amplitudes span 1e-18 .. 1e6, so that some
+    products fall below the grid and the in-order binary64 sum differs."""
+    sysd = workloads.small_abinitio(8, 3, 3, seed=5)
+    s = oracle.system_from_workload(sysd)
+    h, eri = np.asarray(sysd["h1"]), np.asarray(sysd["eri"])
+    ints = np.concatenate([h.ravel(), eri, [float(sysd.get("ecore", 0.0))]])
+    m = max(math.frexp(float(x))[1] - 1 for x in ints if x != 0.0)
+    L = math.ceil(math.log2(2 * 6 + 1))
+    fe = min(64, 60 - m - L)
+    assert s.enum_grid == fe
+    dets = s.determinants()
+    rng = np.random.default_rng(2)
+    c = rng.choice([-1.0, 1.0], len(dets)) * 10.0 ** rng.uniform(-18, 6, len(dets))
+    r = oracle.Run(s)
+    r.import_state([d[0] for d in dets], [d[1] for d in dets], c, 0, 0.0)
+    num, den = r.proj_energy()
+    ra, rb = s.ref
+    grid = 2 ** fe
+    exact = Fraction(0)
+    seq = 0.0
+    below = 0
+    for (a, b), x in zip(dets, c):
+        if (a, b) == (ra, rb):
+            assert den == x
+            continue
+        if bin(a ^ ra).count("1") + bin(b ^ rb).count("1") > 4:
+            continue
+        p = s.hoff((a, b), (ra, rb)) * float(x)  # the binary64 product
+        if p == 0.0:
+            continue
+        f = Fraction(p)
+        t = Fraction(math.floor(abs(f) * grid), grid)
+        below += t == 0
+        exact += t if f > 0 else -t
+        seq = seq + p
+    assert below > 0
+    assert np.float64(num).view(np.uint64) == np.float64(float(exact)).view(np.uint64)
+    assert seq != num
+
+
 # ----------------------------------------------------------------- one projector step
 def _expected_step(s, dets, c, tau, S, n_a, Hrel):
     """E[C(t+dt)] for one iteration from amplitudes c (Eq. (4) with the
