@@ -1664,10 +1664,12 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k_annihilate_staged(const DevIn
         uint4 *tz = reinterpret_cast<uint4 *>(Sm.tab);
         for (int q = t; q < (int)(sizeof(Sm.tab) / sizeof(uint4)); q += K3_THREADS) tz[q] = make_uint4(0, 0, 0, 0);
     }
-    // thread 0 keeps the counts of the bucket whose copies go out next
+    // the last thread (the least loaded in the phases of a bucket) issues the
+    // copies and keeps the counts of the bucket whose copies go out next
+    constexpr int ISSUER = K3_THREADS - 1;
     StageMeta nxt;
     nxt.ii = -1;
-    if (t == 0) {
+    if (t == ISSUER) {
         S.n_new = 0;
         mbar_init(&Sm.bar[0], 1);
         mbar_init(&Sm.bar[1], 1);
@@ -1687,15 +1689,16 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k_annihilate_staged(const DevIn
     AnniTotals T;
     int q = 0, cur = -1;
     for (int u = blockIdx.x; u < n_units; u += gridDim.x, q ^= 1) {
-        // the next bucket's copies go out before this one is processed; its
+        // the next bucket's copies go out while this one is processed; its
         // stage was last read before the previous bucket's closing barrier
-        if (t == 0) {
+        auto issue_next = [&]() {
             stage_issue(insts, nxt, Sm, q ^ 1);
             const int un = u + 2 * (int)gridDim.x;
             meta_load(insts, unit_start, n_inst, un < n_units ? un : -1, nxt);
-        }
+        };
         const int b = Sm.binfo[q][0];
         if (b < 0) {
+            if (t == ISSUER) issue_next();
             __syncthreads();  // binfo[q ^ 1] is written before anyone reads it
             continue;
         }
@@ -1704,12 +1707,13 @@ __global__ void __launch_bounds__(K3_THREADS, 2) k_annihilate_staged(const DevIn
         const DevInst &I = insts[ii];
         if (__syncthreads_or(!ok)) {
             // the copies did not land within the bound: report, wait once
-            // more (bounded) for both stages' copies, stop
+            // more (bounded) for them, stop (stage q ^ 1 holds none: its
+            // last copies were waited for one bucket ago)
             if (t == 0) atomicOr(&I.st->err, ERRB_TIMEOUT);
             mbar_wait(&Sm.bar[q], phase[q]);
-            if (Sm.binfo[q ^ 1][0] >= 0) mbar_wait(&Sm.bar[q ^ 1], phase[q ^ 1]);
             return;
         }
+        if (t == ISSUER) issue_next();
         phase[q] ^= 1u;
         if (ii != cur) {  // a new run: the previous run's totals are complete
             if (cur >= 0) anni_flush(insts[cur], T);
@@ -2091,9 +2095,12 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn_draw(const DevInst *__r
     K7Smem &S = *reinterpret_cast<K7Smem *>(k7_raw);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     constexpr int PER = CAP_M / K1_THREADS;
+    // the last thread (its determinants are the last slots of a bucket, mostly
+    // empty) issues the copies and keeps the meta data of the next bucket
+    constexpr int ISSUER = K1_THREADS - 1;
     SpawnMeta nxt;
     nxt.ii = -1;
-    if (t == 0) {
+    if (t == ISSUER) {
         S.ndiv = 0;
         for (int k = 0; k < 2 * NQ; k++) S.qn[k / NQ][k % NQ] = 0;
         mbar_init(&S.bar[0], 1);
@@ -2187,7 +2194,7 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn_draw(const DevInst *__r
             mbar_wait(&S.bar[q], phase[q]);
             return;
         }
-        if (t == 0) {  // every thread is past the last reads of stage q ^ 1 (bucket u - grid)
+        if (t == ISSUER) {  // every thread is past the last reads of stage q ^ 1 (bucket u - grid)
             draw_stage_issue(insts, nxt, S, q ^ 1);
             const int un = u + 2 * (int)gridDim.x;
             spawn_meta_load(insts, unit_start, n_inst, un < n_units ? un : -1, nxt);
