@@ -2026,6 +2026,15 @@ struct K7Smem {
 };
 static_assert(3 * (sizeof(K7Smem) + 1024) <= 233472, "three draw blocks per SM");
 
+// Thread t of the draw block owns slots t, t + 256, t + 512, t + 768 of the
+// bucket (consecutive threads on consecutive slots: the per-determinant work
+// is spread over the block and the shared-memory accesses are conflict-free);
+// attempt offsets run over the owner-major order v = 4 t + j, j the slot's
+// round, so off[] is indexed by v and slot(v) = (v >> 2) + (v & 3) 256.
+__device__ __forceinline__ unsigned draw_slot(unsigned v) { return (v >> 2) + (v & 3u) * K1_THREADS; }
+__device__ __forceinline__ unsigned draw_order(unsigned d) { return (d % K1_THREADS) * 4u + d / K1_THREADS; }
+static_assert(CAP_M == 4 * K1_THREADS, "four slots per draw thread");
+
 struct DrawBucketMap {
     const K7Smem *S;
     int q;
@@ -2035,17 +2044,17 @@ struct DrawBucketMap {
         if (a < (unsigned)CHUNK_S) {
             const unsigned d = S->att_det[a];
             if (d != 0xffffu) {
-                k = a - S->off[d];
+                k = a - S->off[draw_order(d)];
                 return d;
             }
         }
-        int lo = 0, hi = CAP_M;  // largest d with off[d] <= a (determinants past the count hold the total)
+        int lo = 0, hi = CAP_M;  // largest v with off[v] <= a (slots past the count hold the total)
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
             if (S->off[mid] <= a) lo = mid; else hi = mid;
         }
         k = a - S->off[lo];
-        return (unsigned)lo;
+        return draw_slot((unsigned)lo);
     }
     __device__ ulonglong2 key(unsigned d) const { return S->skey[q][d]; }
     __device__ double cper(unsigned d) const { return S->sc[q][d]; }
@@ -2130,12 +2139,12 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn_draw(const DevInst *__r
             ii = S.binfo[q][2];
         }
         const DevInst &I = insts[ii];
-        // A: the bucket from the stage; thread t owns determinants PER*t .. PER*t+PER-1
+        // A: the bucket from the stage; thread t owns slots t + 256 j (draw_slot)
         long long att = 0;
         unsigned mine = 0;
         unsigned nl[PER];
         for (int j = 0; j < PER; j++) {
-            const int d = PER * t + j;
+            const int d = t + j * K1_THREADS;
             nl[j] = 0;
             bool dv = false;
             if (d < m && ok) {
@@ -2183,7 +2192,7 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn_draw(const DevInst *__r
             queue_div(S, dv, d, lane);
         }
         for (int a = t; a < CHUNK_S; a += K1_THREADS) S.att_det[a] = 0xffffu;
-        unsigned v = mine;  // inclusive warp scan of the light attempt counts in determinant order
+        unsigned v = mine;  // inclusive warp scan of the light attempt counts in owner-major order
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned y = __shfl_up_sync(0xffffffffu, v, o);
             if (lane >= o) v += y;
@@ -2222,7 +2231,7 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_spawn_draw(const DevInst *__r
         for (int j = 0; j < PER; j++) {
             S.off[PER * t + j] = ex;
             if (nl[j] <= 8u && ex + nl[j] <= (unsigned)CHUNK_S)
-                for (unsigned a = 0; a < nl[j]; a++) S.att_det[ex + a] = (unsigned short)(PER * t + j);
+                for (unsigned a = 0; a < nl[j]; a++) S.att_det[ex + a] = (unsigned short)(t + j * K1_THREADS);
             ex += nl[j];
         }
         divide_listed(S.divl, S.ndiv, S.sc[q], t, K1_THREADS);
