@@ -119,6 +119,20 @@ def oracle_rate(sysd, prm, state, shift, iters):
     return att / el, ann / el, att, el
 
 
+def kernels_code_hash():
+    """SHA-256 of the kernel source's code: kernels.cu with // comments,
+    trailing blanks and empty lines removed (a comment edit leaves it)."""
+    import hashlib
+    import re
+    out = []
+    with open(os.path.join(ROOT, "paper_2006_14956_gb300", "csrc", "kernels.cu"), encoding="utf-8") as f:
+        for line in f:
+            line = re.sub(r"//.*$", "", line.rstrip("\n")).rstrip()
+            if line:
+                out.append(line)
+    return hashlib.sha256("\n".join(out).encode()).hexdigest()
+
+
 def _oracle_job(job):
     sysd, prm, state, shift, iters = job
     return oracle_rate(sysd, prm, state, shift, iters)[2:]
@@ -518,10 +532,8 @@ def main():
     try:
         with open(os.path.join(ROOT, "profiles", "dram_traffic_%s.json" % args.workload)) as f:
             tr = json.load(f)
-        import hashlib
-        src = open(os.path.join(ROOT, "paper_2006_14956_gb300", "csrc", "kernels.cu"), "rb").read()
         # counters apply only to the kernels and the workload they were captured on
-        if (tr.get("kernels_sha256") == hashlib.sha256(src).hexdigest() and
+        if (tr.get("kernels_code_sha256") == kernels_code_hash() and
                 tr.get("bench_args") == {"workload": args.workload, "generator": args.generator}):
             traffic_rec = tr["kernels"]
     except Exception:

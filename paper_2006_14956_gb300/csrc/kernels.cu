@@ -1,21 +1,27 @@
 // kernels.cu -- the projector iteration of initiator-FCIQMC on GB300.
 //
-// One iteration (Eq. (4) of Guther et al. 2020) is six launches over the
-// bucketed walker list of every run in the batch:
-//   k_spawn        (a) spawning: ceil(|C_i|) attempts per determinant, one
-//                  Philox block, one excitation and one Slater-Condon element
-//                  per attempt; survivors of the rounding of Eq. (3) are
-//                  appended to the spawn bucket of their target.
+// One iteration (Eq. (4) of Guther et al. 2020) is a handful of launches over
+// the bucketed walker list of every run in the batch:
+//   spawning       (a) ceil(|C_i|) attempts per determinant, one Philox block,
+//                  one excitation and one Slater-Condon element per attempt;
+//                  survivors of the rounding of Eq. (3) are appended to the
+//                  spawn bucket of their target.  By default split in two:
+//                  k_spawn_draw (per bucket: attempts drawn, classified and
+//                  queued in global memory) and k_spawn_eval (one queued
+//                  attempt per thread); k_spawn_staged and k_spawn do both
+//                  halves inside one per-bucket block (bucket staged by bulk
+//                  copies, or loaded plainly).
 //   k_spawn_heavy  the same for determinants with more than HEAVY_ATT walkers,
 //                  split into fixed-size slices so no block waits on one
 //                  heavily populated determinant.
-//   k_annihilate   (b)+(c) per bucket: stage the bucket's walkers and spawns
-//                  in shared memory, group equal determinants in a shared
-//                  open-addressing table, apply death and rounding, sum the
-//                  spawns exactly, apply the initiator rule and rounding,
-//                  write the new bucket, list the new determinants, and
-//                  add the bucket's N_w, E_num (Eq. (9)) and counts to the
-//                  run's exact totals by global reductions.
+//   annihilation   (b)+(c) per bucket: the bucket's walkers and spawns in
+//                  shared memory (k_annihilate_staged: bulk copies one bucket
+//                  ahead; k_annihilate: plain loads), equal determinants
+//                  grouped in a shared open-addressing table, death and
+//                  rounding, the spawns summed exactly, the initiator rule and
+//                  rounding, the new bucket written, the new determinants
+//                  listed, and N_w, E_num (Eq. (9)) and the counts added to
+//                  the run's exact totals by global reductions.
 //   k_annihilate_big  the same for buckets too large for shared memory.
 //   k_new_diag     exact H_jj of the determinants created in the iteration.
 //   k_finalize     per run: read and clear the exact totals, update the
