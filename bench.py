@@ -180,9 +180,10 @@ def run_reference(args, rank, world):
     sysd, prm = workload_params(workload=args.workload if args.workload.startswith("abinitio") else "abinitio50",
                                 generator=args.generator)
     # bounded sample: the same system and parameters (semi-stochastic space
-    # off) from 2e5 walkers, so that one oracle iteration takes a fraction of
-    # a second
-    prm = dict(prm, initial_walkers=2e5, target_walkers=2e5, semistoch_size=0)
+    # off) from at most 2e5 walkers (one oracle iteration ~1 s), fewer when
+    # many steps are asked, so that the whole run stays near a minute or two
+    walkers = float(min(2e5, max(1e4, 1.2e7 / (args.steps + args.warmup))))
+    prm = dict(prm, initial_walkers=walkers, target_walkers=walkers, semistoch_size=0)
     import oracle
     r = oracle.Run(oracle.system_from_workload(sysd), **prm)
     r.step(args.warmup)
@@ -198,10 +199,11 @@ def run_reference(args, rank, world):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "annihilated_per_s": ann / el,
             "config": {"workload": WORKLOAD_NAMES[args.workload if args.workload in WORKLOAD_NAMES else "abinitio50"]
-                       + ", oracle sample", "tau": prm["tau"], "initiator_threshold": 3, "walkers": 2e5,
+                       + ", oracle sample", "tau": prm["tau"], "initiator_threshold": 3, "walkers": walkers,
                        "semistoch": "off in the sample"},
             "cpu_baseline": {"value": value, "unit": "spawn attempts/s", "cores": 1, "kind": "oracle",
-                             "sample": "%d oracle iterations from 2e5 walkers (semi-stochastic space off)" % args.steps},
+                             "sample": "%d oracle iterations from %.3g walkers (semi-stochastic space off)" %
+                                       (args.steps, walkers)},
             "e2e": {"value": value, "unit": "spawn attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
