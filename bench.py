@@ -404,7 +404,8 @@ def run_serving(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed iterations (default: 2000 for abinitio50, 200 for abinitio24, 100 for batch)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="abinitio50",
@@ -423,6 +424,8 @@ def main():
                     help="serving: trial-space size of ab initio requests")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.steps is None:
+        args.steps = {"abinitio50": 2000, "batch": 100}.get(args.workload, 200)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -564,9 +567,16 @@ def main():
                             "peak_source": "4 per SM per clock x %d SMs x the median SM clock under load" % n_sm}
         return out
 
+    # the device's nominal HBM bandwidth (double data rate x memory clock x bus width), stated beside the
+    # measured copy bandwidth the fractions use
+    props = torch.cuda.get_device_properties(local)
+    mclk, mbus = getattr(props, "memory_clock_rate", 0), getattr(props, "memory_bus_width", 0)
+    nominal = 2.0 * mclk * 1e3 * mbus / 8.0 / 1e9 if mclk and mbus else None
     dominant = max(tms, key=tms.get)  # the kernel with the longest launches
     other = "k_annihilate" if dominant == "k_spawn" else "k_spawn"
-    roofline = {"bound": "hbm", "peak": peak, "peak_source": peak_src + " hbm_gbs", "unit": "GB/s", **roof(dominant),
+    roofline = {"bound": "hbm", "peak": peak, "peak_source": peak_src + " hbm_gbs", "unit": "GB/s",
+                "peak_nominal_device": nominal,
+                "peak_nominal_source": "2 x memory clock x bus width (CUDA device properties)", **roof(dominant),
                 "iteration_frac": b_iter / (t_dev / args.steps) / 1e9 / peak, "other": roof(other)}
 
     # ---- end to end through the public API: restart from a pinned host checkpoint
