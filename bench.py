@@ -569,14 +569,16 @@ def main():
 
     # the device's nominal HBM bandwidth (double data rate x memory clock x bus width), stated beside the
     # measured copy bandwidth the fractions use
-    props = torch.cuda.get_device_properties(local)
-    mclk, mbus = getattr(props, "memory_clock_rate", 0), getattr(props, "memory_bus_width", 0)
+    try:
+        mclk, mbus = fq.fciqmc_device_memory(local)
+    except fq.FciqmcError:
+        mclk, mbus = 0, 0
     nominal = 2.0 * mclk * 1e3 * mbus / 8.0 / 1e9 if mclk and mbus else None
     dominant = max(tms, key=tms.get)  # the kernel with the longest launches
     other = "k_annihilate" if dominant == "k_spawn" else "k_spawn"
     roofline = {"bound": "hbm", "peak": peak, "peak_source": peak_src + " hbm_gbs", "unit": "GB/s",
                 "peak_nominal_device": nominal,
-                "peak_nominal_source": "2 x memory clock x bus width (CUDA device properties)", **roof(dominant),
+                "peak_nominal_source": "2 x peak memory clock x bus width (CUDA device attributes)", **roof(dominant),
                 "iteration_frac": b_iter / (t_dev / args.steps) / 1e9 / peak, "other": roof(other)}
 
     # ---- end to end through the public API: restart from a pinned host checkpoint

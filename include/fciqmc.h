@@ -475,6 +475,13 @@ int fciqmc_layout(fciqmc_handle *h, int64_t out[4]);
  * iterations replays the graph n times. */
 int32_t fciqmc_graph_kernels(fciqmc_handle *h);
 
+/* The device's memory interface, for the nominal HBM bandwidth
+ * 2 x clock x bus width: out[0] the peak memory clock in kHz, out[1] the
+ * global-memory bus width in bits, as the CUDA runtime reports them for
+ * `device`.  FCIQMC_ERR_INVALID_ARG for a NULL out, FCIQMC_ERR_CUDA when the
+ * runtime cannot answer (no such device). */
+int fciqmc_device_memory(int32_t device, int64_t out[2]);
+
 /* Size of the semi-stochastic space D (Sec. III) once it has been selected
  * (0 before), and in *nnz (may be NULL) the stored entries of H^D, whose CSR
  * the projection reads every iteration; FCIQMC_ERR_INVALID_ARG for NULL. */

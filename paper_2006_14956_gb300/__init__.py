@@ -134,6 +134,7 @@ _SIGS = {
     "fciqmc_ref_offdiag_sum_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                                  C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p]),
     "fciqmc_graph_kernels": (C.c_int32, [_H]),
+    "fciqmc_device_memory": (C.c_int, [C.c_int32, C.POINTER(C.c_int64)]),
     "fciqmc_set_launch_config": (C.c_int, [C.c_int32, C.c_int32, C.c_int32]),
     "fciqmc_get_launch_config": (C.c_int, [C.POINTER(C.c_int32)]),
     "fciqmc_semistoch_info": (C.c_int64, [_H, C.POINTER(C.c_int64)]),
@@ -395,6 +396,13 @@ def fciqmc_layout(handle):
 def fciqmc_graph_kernels(handle):
     """Kernel launches per iteration in the handle's captured graph."""
     return int(_lib.fciqmc_graph_kernels(handle.h))
+
+
+def fciqmc_device_memory(device=0):
+    """(peak memory clock in kHz, bus width in bits) of a CUDA device."""
+    out = (C.c_int64 * 2)()
+    _check(_lib.fciqmc_device_memory(int(device), out))
+    return int(out[0]), int(out[1])
 
 
 def fciqmc_semistoch_info(handle):

@@ -1176,6 +1176,20 @@ int fciqmc_layout(fciqmc_handle *h, int64_t out[4])
 
 int32_t fciqmc_graph_kernels(fciqmc_handle *h) { return h ? h->graph_kernels : -1; }
 
+int fciqmc_device_memory(int32_t device, int64_t out[2])
+{
+    if (!out) return FCIQMC_ERR_INVALID_ARG;
+    int clk = 0, bus = 0;
+    if (cudaDeviceGetAttribute(&clk, cudaDevAttrMemoryClockRate, device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&bus, cudaDevAttrGlobalMemoryBusWidth, device) != cudaSuccess) {
+        cudaGetLastError();
+        return FCIQMC_ERR_CUDA;
+    }
+    out[0] = clk;
+    out[1] = bus;
+    return FCIQMC_OK;
+}
+
 int fciqmc_set_launch_config(int32_t spawn, int32_t heavy, int32_t annihilate)
 {
     const bool sp_ok = spawn == 0 || spawn == 1 || spawn == 2 || spawn == 4 || spawn == 8 || spawn == 16;
