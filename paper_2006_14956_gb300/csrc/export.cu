@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(XS_THREADS) k_export_scatter(const u64 *__rest
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         if (valid && lane == __ffs(peers) - 1) s_w[warp][d] = __popc(peers);
         __syncthreads();
-        {  // thread t: digit t, prefix over the warps of this round
+        {  // thread t: digit t, prefix over the warps for this batch of keys
             int s = s_base[t];
             for (int w = 0; w < NW; w++) {
                 const int c = s_w[w][t];
