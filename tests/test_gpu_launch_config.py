@@ -77,3 +77,16 @@ def test_split_spawning_queue_growth_and_batch(config):
     fq.fciqmc_step(g, 20)
     o.step(20)
     assert_states_equal(fq.fciqmc_export_state(g), o.export())
+
+
+@pytest.mark.gpu
+def test_device_memory_interface_is_reported():
+    """fciqmc_device_memory: the peak memory clock (kHz) and bus width (bits)
+    the nominal HBM bandwidth of the bench line is computed from."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2006_14956_gb300 as fq
+    clk, bus = fq.fciqmc_device_memory(0)
+    assert clk > 0 and bus > 0 and bus % 64 == 0
+    assert 1e2 < 2.0 * clk * 1e3 * bus / 8 / 1e9 < 1e5  # GB/s
